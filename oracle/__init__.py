@@ -1,0 +1,319 @@
+"""Python access to the Flow Fields CPU oracle (``ffo.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
+baseline leg use this module; the GPU library never imports it. The oracle is a
+plain, slow restatement of the paper's method in C; see the comments in ffo.c for
+the passage each function follows.
+
+All arrays are numpy. Flows are int32 (..., 2) arrays of (dx, dy); images uint8
+(H, W, 3).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ffo.c")
+_LIB = os.path.join(_HERE, "libffo.so")
+_lock = threading.Lock()
+_lib = None
+
+COST_UNSET = 2**31 - 1
+
+
+def build(force=False):
+    """Compile ffo.c into libffo.so next to it (gcc, portable flags)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-shared", "-fPIC",
+                           "-o", tmp, _SRC, "-lm", "-lpthread"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in
+                ("k", "r", "r2", "leaf", "R", "eps", "e", "s", "tile", "n_rs", "K")] + \
+               [("seed", C.c_uint64)]
+
+
+def default_params(**kw):
+    """Sec. 4 parameters (k=3, R=1, l=8, r=8, r2=6; Sintel eps/e/s = 5/4/50),
+    tile T=32 for the parallel schedule, 3 random-search steps, no proposals."""
+    d = dict(k=3, r=8, r2=6, leaf=8, R=1, eps=5, e=4, s=50, tile=32, n_rs=3, K=0, seed=0)
+    d.update(kw)
+    return d
+
+
+def _p(a, t):
+    return a.ctypes.data_as(C.POINTER(t)) if a is not None else None
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            u8, i32, u32, i64 = (C.POINTER(C.c_uint8), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_uint32), C.POINTER(C.c_int64))
+            ci = C.c_int
+            L.ffo_area_down.argtypes = [u8, ci, ci, ci, u8]
+            L.ffo_lanczos_table.argtypes = [ci, i32, i32]
+            L.ffo_smooth.argtypes = [u8, ci, ci, ci, u8]
+            L.ffo_census.argtypes = [u8, ci, ci, ci, u32]
+            L.ffo_patch_cost.argtypes = [u32, u32, ci, ci, ci, ci, ci, ci, ci, ci]
+            L.ffo_patch_cost.restype = C.c_int32
+            L.ffo_wht_blocks.argtypes = [ci, i32]
+            L.ffo_wht_basis_1d.argtypes = [ci, ci, i32]
+            L.ffo_wht_features.argtypes = [u8, ci, ci, ci, i32, ci, i32]
+            L.ffo_wht_features_general.argtypes = [u8, ci, ci, ci, ci, i32, ci, i32]
+            L.ffo_kd_depth.argtypes = [ci, ci]
+            L.ffo_kd_build.argtypes = [i32, ci, ci, i32, i32, i32]
+            L.ffo_kd_leaf_range.argtypes = [ci, ci, ci, i32, i32]
+            L.ffo_kd_query.argtypes = [i32, i32, ci, i32]
+            L.ffo_kd_init.argtypes = [i32, u8, ci, ci, ci, ci, u32, u32, ci, i32, ci, i32, i32]
+            L.ffo_kd_init.restype = C.c_int64
+            L.ffo_splitmix64.argtypes = [C.c_uint64]
+            L.ffo_splitmix64.restype = C.c_uint64
+            L.ffo_rs_offset.argtypes = [C.c_uint64, ci, ci, ci, ci, ci, ci, i32]
+            L.ffo_search_level.argtypes = [u32, u32, ci, ci, ci, ci, i32, ci, ci, ci,
+                                           C.c_uint64, ci, i32, i32]
+            L.ffo_search_level.restype = C.c_int64
+            L.ffo_consistency.argtypes = [i32, i32, i32, ci, ci, ci, u8, i32]
+            L.ffo_region_filter.argtypes = [i32, u8, ci, ci, ci, u8]
+            L.ffo_sparsify.argtypes = [u8, i32, i32, ci, ci, ci, i32, u8]
+            L.ffo_flow_fields.argtypes = [u8, u8, ci, ci, C.POINTER(Params), i32, ci, i32, u8,
+                                          i32, i32, u8, i64]
+            _lib = L
+    return _lib
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def grid(W, H, n):
+    return (W + n - 1) // n, (H + n - 1) // n
+
+
+def area_down(img, n):
+    img = _c(img, np.uint8)
+    H, W = img.shape[:2]
+    out = np.empty(((H + n - 1) // n, (W + n - 1) // n, 3), np.uint8)
+    lib().ffo_area_down(_p(img, C.c_uint8), W, H, n, _p(out, C.c_uint8))
+    return out
+
+
+def lanczos_table(n):
+    base = np.empty(n, np.int32)
+    w = np.empty((n, 6), np.int32)
+    lib().ffo_lanczos_table(n, _p(base, C.c_int32), _p(w, C.c_int32))
+    return base, w
+
+
+def smooth(img, n):
+    img = _c(img, np.uint8)
+    out = np.empty_like(img)
+    lib().ffo_smooth(_p(img, C.c_uint8), img.shape[1], img.shape[0], n, _p(out, C.c_uint8))
+    return out
+
+
+def census(imgn, n):
+    imgn = _c(imgn, np.uint8)
+    H, W = imgn.shape[:2]
+    out = np.empty((H, W), np.uint32)
+    lib().ffo_census(_p(imgn, C.c_uint8), W, H, n, _p(out, C.c_uint32))
+    return out
+
+
+def patch_cost(Cs, Ct, n, r, p1, p2):
+    Cs, Ct = _c(Cs, np.uint32), _c(Ct, np.uint32)
+    H, W = Cs.shape
+    return int(lib().ffo_patch_cost(_p(Cs, C.c_uint32), _p(Ct, C.c_uint32), W, H, n, r,
+                                    int(p1[0]), int(p1[1]), int(p2[0]), int(p2[1])))
+
+
+def wht_blocks(L):
+    out = np.empty(4, np.int32)
+    lib().ffo_wht_blocks(L, _p(out, C.c_int32))
+    return out
+
+
+def wht_basis_1d(L, nb=3):
+    out = np.empty((nb, L), np.int32)
+    lib().ffo_wht_basis_1d(L, nb, _p(out, C.c_int32))
+    return out
+
+
+def wht_features(img, r, pts=None):
+    """Features (npts or H*W, 27) int32; pts: int32 (npts, 2) of (x, y)."""
+    img = _c(img, np.uint8)
+    H, W = img.shape[:2]
+    if pts is None:
+        out = np.empty((H * W, 27), np.int32)
+        lib().ffo_wht_features(_p(img, C.c_uint8), W, H, r, None, 0, _p(out, C.c_int32))
+    else:
+        pts = _c(pts, np.int32).reshape(-1, 2)
+        out = np.empty((len(pts), 27), np.int32)
+        lib().ffo_wht_features(_p(img, C.c_uint8), W, H, r, _p(pts, C.c_int32), len(pts),
+                               _p(out, C.c_int32))
+    return out
+
+
+def wht_features_general(img, L, nb, pts):
+    """Window of L pixels from x - (L-1)//2, nb x nb bases per channel:
+    returns (npts, 3, nb, nb)."""
+    img = _c(img, np.uint8)
+    H, W = img.shape[:2]
+    pts = _c(pts, np.int32).reshape(-1, 2)
+    out = np.empty((len(pts), 3, nb, nb), np.int32)
+    lib().ffo_wht_features_general(_p(img, C.c_uint8), W, H, L, nb, _p(pts, C.c_int32),
+                                   len(pts), _p(out, C.c_int32))
+    return out
+
+
+def kd_depth(N, leaf):
+    return int(lib().ffo_kd_depth(N, leaf))
+
+
+def kd_build(feat, leaf):
+    feat = _c(feat, np.int32)
+    N = feat.shape[0]
+    D = kd_depth(N, leaf)
+    perm = np.empty(N, np.int32)
+    sd = np.zeros((1 << D) + 1, np.int32)
+    sv = np.zeros((1 << D) + 1, np.int32)
+    lib().ffo_kd_build(_p(feat, C.c_int32), N, leaf, _p(perm, C.c_int32), _p(sd, C.c_int32),
+                       _p(sv, C.c_int32))
+    return dict(perm=perm, split_dim=sd[:(1 << D) - 1], split_val=sv[:(1 << D) - 1], D=D, N=N)
+
+
+def kd_leaf_range(N, D, leaf):
+    b, e = C.c_int32(), C.c_int32()
+    lib().ffo_kd_leaf_range(N, D, leaf, C.byref(b), C.byref(e))
+    return b.value, e.value
+
+
+def kd_query(tree, q):
+    q = _c(q, np.int32)
+    sd = _c(np.append(tree["split_dim"], 0), np.int32)
+    sv = _c(np.append(tree["split_val"], 0), np.int32)
+    return int(lib().ffo_kd_query(_p(sd, C.c_int32), _p(sv, C.c_int32), tree["D"],
+                                  _p(q, C.c_int32)))
+
+
+def kd_leaves(tree):
+    """List of sorted pixel-index arrays, one per leaf."""
+    out = []
+    for lf in range(1 << tree["D"]):
+        b, e = kd_leaf_range(tree["N"], tree["D"], lf)
+        out.append(np.sort(tree["perm"][b:e]))
+    return out
+
+
+def kd_init(tgt_feat, src_img, r, leaf, Cs, Ct, n, proposals=None):
+    """Top-level initialisation (Eq. 1/4). Returns flow (Gy, Gx, 2), cost (Gy, Gx), evals."""
+    src_img = _c(src_img, np.uint8)
+    H, W = src_img.shape[:2]
+    Gx, Gy = grid(W, H, n)
+    tgt_feat, Cs, Ct = _c(tgt_feat, np.int32), _c(Cs, np.uint32), _c(Ct, np.uint32)
+    flow = np.empty((Gy, Gx, 2), np.int32)
+    cost = np.empty((Gy, Gx), np.int32)
+    K = 0
+    if proposals is not None:
+        proposals = _c(proposals, np.int32)
+        K = proposals.shape[2]
+    ev = lib().ffo_kd_init(_p(tgt_feat, C.c_int32), _p(src_img, C.c_uint8), W, H, r, leaf,
+                           _p(Cs, C.c_uint32), _p(Ct, C.c_uint32), n,
+                           _p(proposals, C.c_int32), K, _p(flow, C.c_int32),
+                           _p(cost, C.c_int32))
+    return flow, cost, int(ev)
+
+
+def splitmix64(z):
+    return int(lib().ffo_splitmix64(C.c_uint64(z)))
+
+
+def rs_offset(seed, flow_id, level, step, gx, gy, Rn):
+    d = np.empty(2, np.int32)
+    lib().ffo_rs_offset(C.c_uint64(seed), flow_id, level, step, gx, gy, Rn, _p(d, C.c_int32))
+    return int(d[0]), int(d[1])
+
+
+def search_level(Cs, Ct, n, r, flow_coarse=None, flow=None, cost=None, tile=32, n_rs=3, R=1,
+                 seed=0, flow_id=0):
+    """One hierarchy level. With flow_coarse the level is seeded from it (Sec. 3.2);
+    without, (flow, cost) is the initial state (top level). Returns flow, cost, evals."""
+    Cs, Ct = _c(Cs, np.uint32), _c(Ct, np.uint32)
+    H, W = Cs.shape
+    Gx, Gy = grid(W, H, n)
+    if flow_coarse is not None:
+        fc = _c(flow_coarse, np.int32)
+        flow = np.empty((Gy, Gx, 2), np.int32)
+        cost = np.empty((Gy, Gx), np.int32)
+    else:
+        fc = None
+        flow = _c(flow, np.int32).copy()
+        cost = _c(cost, np.int32).copy()
+    ev = lib().ffo_search_level(_p(Cs, C.c_uint32), _p(Ct, C.c_uint32), W, H, n, r,
+                                _p(fc, C.c_int32), tile, n_rs, R, C.c_uint64(seed), flow_id,
+                                _p(flow, C.c_int32), _p(cost, C.c_int32))
+    return flow, cost, int(ev)
+
+
+def consistency(F, Fb1, Fb2, eps):
+    F, Fb1, Fb2 = _c(F, np.int32), _c(Fb1, np.int32), _c(Fb2, np.int32)
+    H, W = F.shape[:2]
+    v = np.empty((H, W), np.uint8)
+    e = np.empty((H, W), np.int32)
+    lib().ffo_consistency(_p(F, C.c_int32), _p(Fb1, C.c_int32), _p(Fb2, C.c_int32), W, H, eps,
+                          _p(v, C.c_uint8), _p(e, C.c_int32))
+    return v, e
+
+
+def region_filter(F, valid_cc, s):
+    F, valid_cc = _c(F, np.int32), _c(valid_cc, np.uint8)
+    H, W = valid_cc.shape
+    out = np.empty((H, W), np.uint8)
+    lib().ffo_region_filter(_p(F, C.c_int32), _p(valid_cc, C.c_uint8), W, H, s,
+                            _p(out, C.c_uint8))
+    return out
+
+
+def sparsify(valid, err_sum, F, e):
+    valid, err_sum, F = _c(valid, np.uint8), _c(err_sum, np.int32), _c(F, np.int32)
+    H, W = valid.shape
+    sp = np.empty((((W + 2) // 3) * ((H + 2) // 3), 4), np.int32)
+    mask = np.empty((H, W), np.uint8)
+    n = lib().ffo_sparsify(_p(valid, C.c_uint8), _p(err_sum, C.c_int32), _p(F, C.c_int32), W, H,
+                           e, _p(sp, C.c_int32), _p(mask, C.c_uint8))
+    return sp[:n].copy(), mask
+
+
+def flow_fields(I1, I2, params=None, proposals=None, threads=3):
+    """Whole pipeline. Returns dict(flows (3, H, W, 2), valid, err_sum, sparse, mask, evals)."""
+    P = default_params(**(params or {}))
+    if proposals is not None:
+        P["K"] = proposals.shape[2]
+    I1, I2 = _c(I1, np.uint8), _c(I2, np.uint8)
+    H, W = I1.shape[:2]
+    flows = np.empty((3, H, W, 2), np.int32)
+    valid = np.empty((H, W), np.uint8)
+    err = np.empty((H, W), np.int32)
+    sp = np.empty((((W + 2) // 3) * ((H + 2) // 3), 4), np.int32)
+    mask = np.empty((H, W), np.uint8)
+    ev = C.c_int64()
+    pr = _c(proposals, np.int32) if proposals is not None else None
+    n = lib().ffo_flow_fields(_p(I1, C.c_uint8), _p(I2, C.c_uint8), W, H, C.byref(Params(**P)),
+                              _p(pr, C.c_int32), threads, _p(flows, C.c_int32),
+                              _p(valid, C.c_uint8), _p(err, C.c_int32), _p(sp, C.c_int32),
+                              _p(mask, C.c_uint8), C.byref(ev))
+    return dict(flows=flows, valid=valid, err_sum=err, sparse=sp[:n].copy(), mask=mask,
+                evals=ev.value)

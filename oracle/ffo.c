@@ -1,0 +1,783 @@
+/*
+ * Flow Fields CPU oracle (Bailer, Taetz, Stricker, ICCV 2015).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the plain, slow, step-by-step statement
+ * of what the GPU library computes. Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark load it. It shares no code, header, table or
+ * generator with the CUDA library: every table it needs it derives itself.
+ *
+ * Every function names the passage of the paper it follows. Where the paper is
+ * silent or garbled the reading taken is stated beside the code.
+ *
+ * Conventions
+ *   images       uint8, H x W x 3 (RGB), row major
+ *   census       uint32 per pixel, H x W
+ *   level grids  at spacing n the grid has Gx = ceil(W/n) by Gy = ceil(H/n) points;
+ *                grid point (gx, gy) sits on pixel (n*gx, n*gy)
+ *   flows        int32 pairs (dx, dy) per grid point, target = pixel + flow
+ *   costs        int32 per grid point; COST_UNSET marks a point without a flow
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define COST_UNSET INT32_MAX
+#define NFEAT 27
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+static int imin(int a, int b) { return a < b ? a : b; }
+
+/* floor(a / b) for b > 0 */
+static int64_t floor_div(int64_t a, int64_t b) {
+  int64_t q = a / b;
+  if ((a % b != 0) && (a < 0)) q -= 1;
+  return q;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.2: the smoothed full-resolution image I^n. Area downsampling by n,  */
+/* then Lanczos upsampling back to full resolution.                          */
+/* ------------------------------------------------------------------------ */
+
+/* Area downsampling: the mean over the in-image part of each n x n block,
+ * rounded half up in integer arithmetic: (sum + cnt/2) / cnt. */
+void ffo_area_down(const uint8_t *img, int W, int H, int n, uint8_t *out) {
+  int Wc = (W + n - 1) / n, Hc = (H + n - 1) / n;
+  for (int j = 0; j < Hc; j++)
+    for (int i = 0; i < Wc; i++)
+      for (int c = 0; c < 3; c++) {
+        int sum = 0, cnt = 0;
+        for (int y = j * n; y < imin(j * n + n, H); y++)
+          for (int x = i * n; x < imin(i * n + n, W); x++) {
+            sum += img[((size_t)y * W + x) * 3 + c];
+            cnt++;
+          }
+        out[((size_t)j * Wc + i) * 3 + c] = (uint8_t)((sum + cnt / 2) / cnt);
+      }
+}
+
+/* Lanczos kernel with a = 3 (the paper does not give the order). */
+static double lanczos3(double t) {
+  if (t == 0.0) return 1.0;
+  if (fabs(t) >= 3.0) return 0.0;
+  double pt = M_PI * t;
+  return 3.0 * sin(pt) * sin(pt / 3.0) / (pt * pt);
+}
+
+/* Per-phase Lanczos taps for integer upsampling by n.
+ * Coarse sample j is centred on full-resolution position j*n + (n-1)/2, so the
+ * full-resolution pixel x sits at coarse coordinate u = (2x - n + 1) / (2n).
+ * With j0 = floor(u) and f = u - j0 the six taps are j0-2 .. j0+3 with weight
+ * L(f - k). The weights are normalised to sum 1, scaled to Q14 and rounded half
+ * away from zero; the tap of largest magnitude (first on ties) takes the
+ * residual so that each phase sums to exactly 16384.
+ * Outputs: base[phi] = j0 for x = phi (x = q*n + phi has base q + base[phi]),
+ *          w[phi*6 + (k+2)]. */
+void ffo_lanczos_table(int n, int32_t *base, int32_t *w) {
+  for (int phi = 0; phi < n; phi++) {
+    int64_t num = 2 * phi - n + 1, den = 2 * (int64_t)n;
+    int64_t j0 = floor_div(num, den);
+    double f = (double)(num - den * j0) / (double)den;
+    double wd[6], s = 0.0;
+    for (int k = -2; k <= 3; k++) {
+      wd[k + 2] = lanczos3(f - k);
+      s += wd[k + 2];
+    }
+    int32_t tot = 0;
+    int big = 0;
+    for (int t = 0; t < 6; t++) {
+      double v = 16384.0 * wd[t] / s;
+      int32_t q = (int32_t)(v >= 0 ? floor(v + 0.5) : -floor(-v + 0.5));
+      w[phi * 6 + t] = q;
+      tot += q;
+    }
+    for (int t = 1; t < 6; t++)
+      if (abs(w[phi * 6 + t]) > abs(w[phi * 6 + big])) big = t;
+    w[phi * 6 + big] += 16384 - tot;
+    base[phi] = (int32_t)j0;
+  }
+}
+
+/* I^n from I: area down by n, then separable Lanczos-3 up to W x H.
+ * Horizontal pass keeps an unrounded int32 Q14 value per coarse row; the vertical
+ * pass accumulates in int64 and rounds (acc + 2^27) >> 28, clamped to [0, 255].
+ * For n = 1 the image is copied. */
+void ffo_smooth(const uint8_t *img, int W, int H, int n, uint8_t *out) {
+  if (n == 1) {
+    memcpy(out, img, (size_t)W * H * 3);
+    return;
+  }
+  int Wc = (W + n - 1) / n, Hc = (H + n - 1) / n;
+  uint8_t *D = malloc((size_t)Wc * Hc * 3);
+  int32_t *hz = malloc(sizeof(int32_t) * (size_t)Hc * W * 3);
+  int32_t *base = malloc(sizeof(int32_t) * n), *wt = malloc(sizeof(int32_t) * 6 * n);
+  ffo_area_down(img, W, H, n, D);
+  ffo_lanczos_table(n, base, wt);
+  for (int yc = 0; yc < Hc; yc++)
+    for (int x = 0; x < W; x++) {
+      int phi = x % n, j0 = x / n + base[phi];
+      for (int c = 0; c < 3; c++) {
+        int32_t acc = 0;
+        for (int k = -2; k <= 3; k++) {
+          int j = clampi(j0 + k, 0, Wc - 1);
+          acc += wt[phi * 6 + k + 2] * (int32_t)D[((size_t)yc * Wc + j) * 3 + c];
+        }
+        hz[((size_t)yc * W + x) * 3 + c] = acc;
+      }
+    }
+  for (int y = 0; y < H; y++) {
+    int phi = y % n, j0 = y / n + base[phi];
+    for (int x = 0; x < W; x++)
+      for (int c = 0; c < 3; c++) {
+        int64_t acc = 0;
+        for (int k = -2; k <= 3; k++) {
+          int j = clampi(j0 + k, 0, Hc - 1);
+          acc += (int64_t)wt[phi * 6 + k + 2] * hz[((size_t)j * W + x) * 3 + c];
+        }
+        int64_t v = floor_div(acc + ((int64_t)1 << 27), (int64_t)1 << 28);
+        out[((size_t)y * W + x) * 3 + c] = (uint8_t)(v < 0 ? 0 : (v > 255 ? 255 : v));
+      }
+  }
+  free(D);
+  free(hz);
+  free(base);
+  free(wt);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.3: census transform data term.                                     */
+/* Reading: 3x3 census per colour channel on I^n with neighbour spacing n.   */
+/* Bit (8c + o) is set when channel c of neighbour o is darker than the      */
+/* centre; the 8 neighbours are taken in raster order skipping the centre;  */
+/* coordinates are clamped into the image.                                   */
+/* ------------------------------------------------------------------------ */
+void ffo_census(const uint8_t *imgn, int W, int H, int n, uint32_t *out) {
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++) {
+      uint32_t code = 0;
+      for (int c = 0; c < 3; c++) {
+        int centre = imgn[((size_t)y * W + x) * 3 + c];
+        int o = 0;
+        for (int dy = -1; dy <= 1; dy++)
+          for (int dx = -1; dx <= 1; dx++) {
+            if (dx == 0 && dy == 0) continue;
+            int xx = clampi(x + n * dx, 0, W - 1), yy = clampi(y + n * dy, 0, H - 1);
+            if (imgn[((size_t)yy * W + xx) * 3 + c] < centre) code |= 1u << (8 * c + o);
+            o++;
+          }
+      }
+      out[(size_t)y * W + x] = code;
+    }
+}
+
+static int popcount32(uint32_t v) { return __builtin_popcount(v); }
+
+/* E_d of Eq. 1/3/4 with the census data term: the summed census Hamming
+ * distance over the (2r+1)^2 taps of the subsampled patches P^n_r (Eq. 3),
+ * each tap clamped into the image. */
+int32_t ffo_patch_cost(const uint32_t *Cs, const uint32_t *Ct, int W, int H, int n, int r,
+                       int x1, int y1, int x2, int y2) {
+  int32_t e = 0;
+  for (int v = -r; v <= r; v++)
+    for (int u = -r; u <= r; u++) {
+      int xs = clampi(x1 + n * u, 0, W - 1), ys = clampi(y1 + n * v, 0, H - 1);
+      int xt = clampi(x2 + n * u, 0, W - 1), yt = clampi(y2 + n * v, 0, H - 1);
+      e += popcount32(Cs[(size_t)ys * W + xs] ^ Ct[(size_t)yt * W + xt]);
+    }
+  return e;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.1: Walsh-Hadamard patch features.                                 */
+/* Reading: the window of L = 2r+1 pixels is split into halves floor(L/2),  */
+/* ceil(L/2) (the paper's uneven r / r+1 split), and each half the same way,*/
+/* giving 4 blocks. The 1-D Walsh functions in sequency order over the 4    */
+/* blocks are (++++), (++--), (+--+), (+-+-). The 9 features per channel    */
+/* are rows-function i times columns-function j, i, j in {0, 1, 2}; feature */
+/* index 9c + 3i + j; pixels are read with clamped coordinates.             */
+/* ------------------------------------------------------------------------ */
+void ffo_wht_blocks(int L, int32_t *size4) {
+  int h0 = L / 2, h1 = L - h0;
+  size4[0] = h0 / 2;
+  size4[1] = h0 - h0 / 2;
+  size4[2] = h1 / 2;
+  size4[3] = h1 - h1 / 2;
+}
+
+/* nb (<= 4) 1-D Walsh functions over L pixels, out[i*L + t] in {-1, +1}. */
+void ffo_wht_basis_1d(int L, int nb, int32_t *out) {
+  static const int sgn[4][4] = {{1, 1, 1, 1}, {1, 1, -1, -1}, {1, -1, -1, 1}, {1, -1, 1, -1}};
+  int32_t sz[4];
+  ffo_wht_blocks(L, sz);
+  for (int i = 0; i < nb; i++) {
+    int t = 0;
+    for (int b = 0; b < 4; b++)
+      for (int k = 0; k < sz[b]; k++) out[i * L + t++] = sgn[i][b];
+  }
+}
+
+/* General form: window of L pixels starting at x - (L-1)/2 (centred for odd L),
+ * nb x nb bases per channel, out[k*3*nb*nb + c*nb*nb + i*nb + j]. The odd-L,
+ * nb = 3 case is the feature vector; L = 4 with nb = 4 is the complete
+ * Walsh-Hadamard transform of a 4x4 patch. */
+void ffo_wht_features_general(const uint8_t *img, int W, int H, int L, int nb,
+                              const int32_t *pts, int npts, int32_t *out) {
+  int h = (L - 1) / 2, nf = 3 * nb * nb;
+  int32_t *w = malloc(sizeof(int32_t) * nb * L);
+  int64_t *rowsum = malloc(sizeof(int64_t) * L * 3 * nb);
+  ffo_wht_basis_1d(L, nb, w);
+  int total = pts ? npts : W * H;
+  for (int k = 0; k < total; k++) {
+    int x = pts ? pts[2 * k] : k % W, y = pts ? pts[2 * k + 1] : k / W;
+    /* rowsum[v][c][j] = sum_u w_j(u) I_c(x - h + u, y - h + v) */
+    for (int v = 0; v < L; v++) {
+      int yy = clampi(y - h + v, 0, H - 1);
+      for (int c = 0; c < 3; c++)
+        for (int j = 0; j < nb; j++) {
+          int64_t s = 0;
+          for (int u = 0; u < L; u++) {
+            int xx = clampi(x - h + u, 0, W - 1);
+            s += (int64_t)w[j * L + u] * img[((size_t)yy * W + xx) * 3 + c];
+          }
+          rowsum[(v * 3 + c) * nb + j] = s;
+        }
+    }
+    for (int c = 0; c < 3; c++)
+      for (int i = 0; i < nb; i++)
+        for (int j = 0; j < nb; j++) {
+          int64_t s = 0;
+          for (int v = 0; v < L; v++) s += (int64_t)w[i * L + v] * rowsum[(v * 3 + c) * nb + j];
+          out[(size_t)k * nf + c * nb * nb + i * nb + j] = (int32_t)s;
+        }
+  }
+  free(w);
+  free(rowsum);
+}
+
+/* Features at the listed pixels (pts = NULL: every pixel in raster order).
+ * The patch P_r is the non-subsampled one (Sec. 3.2: WHTs use P_r even in the
+ * hierarchical search). out[k*27 + 9c + 3i + j]. */
+void ffo_wht_features(const uint8_t *img, int W, int H, int r, const int32_t *pts, int npts,
+                      int32_t *out) {
+  ffo_wht_features_general(img, W, H, 2 * r + 1, 3, pts, npts, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.1: kd-tree over the 27-D vectors of all target pixels, leaf size l, */
+/* split in the dimension of maximal spread at the median.                   */
+/* Reading: a perfect tree of depth D = smallest d with ceil(N / 2^d) <= l.  */
+/* Spread = max - min (lowest dimension on ties). A node of m points sends   */
+/* the first floor(m/2) under the order (value, pixel index) to the left;   */
+/* the split value is the value of the first point on the right. Nodes are  */
+/* in heap order (children of i are 2i+1, 2i+2).                            */
+/* ------------------------------------------------------------------------ */
+int ffo_kd_depth(int N, int leaf) {
+  int d = 0;
+  while (((int64_t)N + ((int64_t)1 << d) - 1) / ((int64_t)1 << d) > leaf) d++;
+  return d;
+}
+
+typedef struct {
+  int32_t value, idx;
+} kd_key;
+
+static int key_cmp(const void *a, const void *b) {
+  const kd_key *x = a, *y = b;
+  if (x->value != y->value) return x->value < y->value ? -1 : 1;
+  return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+static void kd_node(const int32_t *feat, int32_t *perm, kd_key *tmp, int begin, int end, int depth,
+                    int D, int node, int32_t *split_dim, int32_t *split_val) {
+  if (depth == D) return;
+  int m = end - begin, best = 0;
+  int64_t best_spread = -1;
+  for (int d = 0; d < NFEAT; d++) {
+    int32_t lo = INT32_MAX, hi = INT32_MIN;
+    for (int k = begin; k < end; k++) {
+      int32_t v = feat[(size_t)perm[k] * NFEAT + d];
+      if (v < lo) lo = v;
+      if (v > hi) hi = v;
+    }
+    if ((int64_t)hi - lo > best_spread) {
+      best_spread = (int64_t)hi - lo;
+      best = d;
+    }
+  }
+  for (int k = 0; k < m; k++) {
+    tmp[k].value = feat[(size_t)perm[begin + k] * NFEAT + best];
+    tmp[k].idx = perm[begin + k];
+  }
+  qsort(tmp, m, sizeof(kd_key), key_cmp);
+  for (int k = 0; k < m; k++) perm[begin + k] = tmp[k].idx;
+  int half = m / 2;
+  split_dim[node] = best;
+  split_val[node] = tmp[half].value;
+  kd_node(feat, perm, tmp, begin, begin + half, depth + 1, D, 2 * node + 1, split_dim, split_val);
+  kd_node(feat, perm, tmp, begin + half, end, depth + 1, D, 2 * node + 2, split_dim, split_val);
+}
+
+/* perm[N]: pixel indices grouped by leaf (leaf order = heap order of depth D);
+ * split_dim / split_val: 2^D - 1 internal nodes. Returns D. */
+int ffo_kd_build(const int32_t *feat, int N, int leaf, int32_t *perm, int32_t *split_dim,
+                 int32_t *split_val) {
+  int D = ffo_kd_depth(N, leaf);
+  kd_key *tmp = malloc(sizeof(kd_key) * (size_t)(N > 0 ? N : 1));
+  for (int k = 0; k < N; k++) perm[k] = k;
+  kd_node(feat, perm, tmp, 0, N, 0, D, 0, split_dim, split_val);
+  free(tmp);
+  return D;
+}
+
+/* Range of leaf `leaf` in perm: halve [0, N) D times along the leaf's path. */
+void ffo_kd_leaf_range(int N, int D, int leaf, int32_t *begin, int32_t *end) {
+  int b = 0, e = N;
+  for (int d = D - 1; d >= 0; d--) {
+    int half = (e - b) / 2;
+    if ((leaf >> d) & 1) b = b + half;
+    else e = b + half;
+  }
+  *begin = b;
+  *end = e;
+}
+
+/* Bounded-leaf query without backtracking: at each node go left iff the query
+ * value is below the split value. Returns the leaf index in [0, 2^D). */
+int ffo_kd_query(const int32_t *split_dim, const int32_t *split_val, int D, const int32_t *q) {
+  int node = 0;
+  for (int d = 0; d < D; d++)
+    node = (q[split_dim[node]] < split_val[node]) ? 2 * node + 1 : 2 * node + 2;
+  return node - ((1 << D) - 1);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Candidates. Reading: a candidate flow f at pixel p is applied with its     */
+/* target clamped into the image, f := clamp(p + f) - p, so every flow stays */
+/* valid. Replacement needs a strictly lower cost ("if the matching error   */
+/* decreases", Sec. 3.1); earlier candidates win ties.                      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const uint32_t *Cs, *Ct;
+  int W, H, n, r;
+  int64_t evals;
+} level_ctx;
+
+static void try_candidate(level_ctx *L, int px, int py, int fx, int fy, int32_t *flow,
+                          int32_t *cost) {
+  int tx = clampi(px + fx, 0, L->W - 1), ty = clampi(py + fy, 0, L->H - 1);
+  int32_t e = ffo_patch_cost(L->Cs, L->Ct, L->W, L->H, L->n, L->r, px, py, tx, ty);
+  L->evals++;
+  if (e < *cost) {
+    *cost = e;
+    flow[0] = tx - px;
+    flow[1] = ty - py;
+  }
+}
+
+/* Eq. 1 / Eq. 4: initial flow at the grid points of spacing n from the kd
+ * leaf of each point's WHT vector (features of the source image at that
+ * point, radius r), reranked by E_d on P^n_r. Leaf entries are scanned in
+ * ascending pixel index. Optional proposals (K per grid point, int32 pairs)
+ * are tried afterwards in index order under the same strict-less rule.
+ * tgt_feat: features of every target pixel; the tree is built here. */
+int64_t ffo_kd_init(const int32_t *tgt_feat, const uint8_t *src_img, int W, int H, int r,
+                    int leaf, const uint32_t *Cs, const uint32_t *Ct, int n,
+                    const int32_t *proposals, int K, int32_t *flow, int32_t *cost) {
+  int N = W * H, Gx = (W + n - 1) / n, Gy = (H + n - 1) / n, G = Gx * Gy;
+  int D = ffo_kd_depth(N, leaf);
+  int32_t *perm = malloc(sizeof(int32_t) * N);
+  int32_t *sd = malloc(sizeof(int32_t) * ((1 << D) + 1));
+  int32_t *sv = malloc(sizeof(int32_t) * ((1 << D) + 1));
+  int32_t *pts = malloc(sizeof(int32_t) * 2 * G), *qf = malloc(sizeof(int32_t) * NFEAT * G);
+  int32_t *cand = malloc(sizeof(int32_t) * (leaf + 1));
+  ffo_kd_build(tgt_feat, N, leaf, perm, sd, sv);
+  for (int g = 0; g < G; g++) {
+    pts[2 * g] = (g % Gx) * n;
+    pts[2 * g + 1] = (g / Gx) * n;
+  }
+  ffo_wht_features(src_img, W, H, r, pts, G, qf);
+  level_ctx L = {Cs, Ct, W, H, n, r, 0};
+  for (int g = 0; g < G; g++) {
+    int px = pts[2 * g], py = pts[2 * g + 1];
+    int lf = ffo_kd_query(sd, sv, D, qf + (size_t)g * NFEAT);
+    int32_t b, e;
+    ffo_kd_leaf_range(N, D, lf, &b, &e);
+    int m = e - b;
+    for (int k = 0; k < m; k++) cand[k] = perm[b + k];
+    /* ascending pixel index */
+    for (int i = 1; i < m; i++)
+      for (int j = i; j > 0 && cand[j - 1] > cand[j]; j--) {
+        int32_t t = cand[j];
+        cand[j] = cand[j - 1];
+        cand[j - 1] = t;
+      }
+    int32_t *f = flow + 2 * (size_t)g;
+    cost[g] = COST_UNSET;
+    f[0] = f[1] = 0;
+    for (int k = 0; k < m; k++)
+      try_candidate(&L, px, py, cand[k] % W - px, cand[k] / W - py, f, &cost[g]);
+    for (int k = 0; k < K; k++)
+      try_candidate(&L, px, py, proposals[((size_t)g * K + k) * 2],
+                    proposals[((size_t)g * K + k) * 2 + 1], f, &cost[g]);
+  }
+  free(perm);
+  free(sd);
+  free(sv);
+  free(pts);
+  free(qf);
+  free(cand);
+  return L.evals;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Counter-based random numbers for the random search (Sec. 3.1).            */
+/* SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): add the golden gamma, then   */
+/* the 64-bit finaliser. The key packs gx (bits 0-23), gy (24-47), the      */
+/* random-search step (48-49), log2 n (50-52) and the flow id (53-54), xored  */
+/* into the seed. Lemire's multiply-shift maps each 32-bit half to           */
+/* [0, 2R_n]; the low half gives dx, the high half dy.                       */
+/* ------------------------------------------------------------------------ */
+uint64_t ffo_splitmix64(uint64_t z) {
+  z += 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+void ffo_rs_offset(uint64_t seed, int flow_id, int level, int step, int gx, int gy, int Rn,
+                   int32_t *d) {
+  uint64_t key = seed ^ ((uint64_t)gx & 0xffffff) ^ (((uint64_t)gy & 0xffffff) << 24) ^
+                 ((uint64_t)(step & 3) << 48) ^ ((uint64_t)(level & 7) << 50) ^
+                 ((uint64_t)(flow_id & 3) << 53);
+  uint64_t z = ffo_splitmix64(key);
+  uint64_t span = 2 * (uint64_t)Rn + 1;
+  d[0] = (int32_t)((((z & 0xffffffffULL) * span) >> 32)) - Rn;
+  d[1] = (int32_t)((((z >> 32) * span) >> 32)) - Rn;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.1/3.2: propagation (Eq. 2) and random search on the grid of        */
+/* spacing n.                                                                 */
+/* Reading of Fig. 3c (missing from the text): pass 0 takes its sources from */
+/* (x-n, y), (x, y-n) and scans top-down, left to right; pass 1 from (x+n, y),*/
+/* (x, y+n), bottom-up, right to left; pass 2 from (x+n, y), (x, y-n),       */
+/* top-down, right to left; pass 3 from (x-n, y), (x, y+n), bottom-up, left  */
+/* to right. Candidates in order: current, horizontal source, vertical      */
+/* source. A source without a flow (COST_UNSET) or outside the grid is       */
+/* skipped.                                                                   */
+/*                                                                            */
+/* Schedules. tile == 0 is the paper's sequential scan over the whole grid.  */
+/* tile == T > 0 splits the grid into T x T tiles, with the tile origin      */
+/* shifted by T/2 on both axes in odd passes; inside a tile the pass is the  */
+/* sequential scan, and a source outside the tile is read from the state at  */
+/* the start of the pass.                                                    */
+/* ------------------------------------------------------------------------ */
+static const int PASS_SRC[4][2][2] = {
+    {{-1, 0}, {0, -1}}, {{1, 0}, {0, 1}}, {{1, 0}, {0, -1}}, {{-1, 0}, {0, 1}}};
+
+static void prop_pass(level_ctx *L, int s, int tile, int32_t *flow, int32_t *cost) {
+  int n = L->n, Gx = (L->W + n - 1) / n, Gy = (L->H + n - 1) / n, G = Gx * Gy;
+  int32_t *snap_f = malloc(sizeof(int32_t) * 2 * G), *snap_c = malloc(sizeof(int32_t) * G);
+  memcpy(snap_f, flow, sizeof(int32_t) * 2 * G);
+  memcpy(snap_c, cost, sizeof(int32_t) * G);
+  int T = tile, off = 0, ntx = 1, nty = 1;
+  if (T > 0) {
+    off = (s % 2) * (T / 2);
+    ntx = (Gx + off + T - 1) / T;
+    nty = (Gy + off + T - 1) / T;
+  }
+  int sx = PASS_SRC[s][0][0], sy = PASS_SRC[s][1][1]; /* scan direction = -source direction */
+  for (int ty = 0; ty < nty; ty++)
+    for (int tx = 0; tx < ntx; tx++) {
+      int x0 = 0, x1 = Gx, y0 = 0, y1 = Gy;
+      if (T > 0) {
+        x0 = tx * T - off;
+        x1 = x0 + T;
+        y0 = ty * T - off;
+        y1 = y0 + T;
+        if (x0 < 0) x0 = 0;
+        if (y0 < 0) y0 = 0;
+        if (x1 > Gx) x1 = Gx;
+        if (y1 > Gy) y1 = Gy;
+      }
+      for (int iy = 0; iy < y1 - y0; iy++) {
+        int gy = (sy < 0) ? y0 + iy : y1 - 1 - iy;
+        for (int ix = 0; ix < x1 - x0; ix++) {
+          int gx = (sx < 0) ? x0 + ix : x1 - 1 - ix;
+          int g = gy * Gx + gx;
+          for (int c = 0; c < 2; c++) {
+            int qx = gx + PASS_SRC[s][c][0], qy = gy + PASS_SRC[s][c][1];
+            if (qx < 0 || qx >= Gx || qy < 0 || qy >= Gy) continue;
+            int q = qy * Gx + qx;
+            int in_tile = qx >= x0 && qx < x1 && qy >= y0 && qy < y1;
+            const int32_t *fq = in_tile ? flow + 2 * (size_t)q : snap_f + 2 * (size_t)q;
+            int32_t cq = in_tile ? cost[q] : snap_c[q];
+            if (cq == COST_UNSET) continue;
+            try_candidate(L, gx * n, gy * n, fq[0], fq[1], flow + 2 * (size_t)g, &cost[g]);
+          }
+        }
+      }
+    }
+  free(snap_f);
+  free(snap_c);
+}
+
+/* Random search: F + O_rnd with O_rnd uniform in [-R_n, R_n]^2 (integer reading
+ * of the paper's subpixel offset), kept only if E_d decreases. */
+static void random_search(level_ctx *L, uint64_t seed, int flow_id, int level, int step, int Rn,
+                          int32_t *flow, int32_t *cost) {
+  int n = L->n, Gx = (L->W + n - 1) / n, Gy = (L->H + n - 1) / n;
+  for (int gy = 0; gy < Gy; gy++)
+    for (int gx = 0; gx < Gx; gx++) {
+      int g = gy * Gx + gx;
+      if (cost[g] == COST_UNSET) continue;
+      int32_t d[2];
+      ffo_rs_offset(seed, flow_id, level, step, gx, gy, Rn, d);
+      int32_t *f = flow + 2 * (size_t)g;
+      try_candidate(L, gx * n, gy * n, f[0] + d[0], f[1] + d[1], f, &cost[g]);
+    }
+}
+
+/* Sec. 3.2, level transition: a grid point (gx, gy) of spacing n with both
+ * coordinates even coincides with point (gx/2, gy/2) of spacing 2n and takes its
+ * flow as a seed, with the cost re-evaluated on P^n_r. All other points start
+ * without a flow and receive one in the first propagation pass. */
+static void seed_level(level_ctx *L, const int32_t *flow_coarse, int32_t *flow, int32_t *cost) {
+  int n = L->n, Gx = (L->W + n - 1) / n, Gy = (L->H + n - 1) / n;
+  int Gxc = (L->W + 2 * n - 1) / (2 * n);
+  for (int gy = 0; gy < Gy; gy++)
+    for (int gx = 0; gx < Gx; gx++) {
+      int g = gy * Gx + gx;
+      flow[2 * g] = flow[2 * g + 1] = 0;
+      cost[g] = COST_UNSET;
+      if ((gx % 2) == 0 && (gy % 2) == 0) {
+        const int32_t *fc = flow_coarse + 2 * ((size_t)(gy / 2) * Gxc + gx / 2);
+        try_candidate(L, gx * n, gy * n, fc[0], fc[1], flow + 2 * g, &cost[g]);
+      }
+    }
+}
+
+/* One hierarchy level: optional seeding from the coarser level, then the
+ * alternation P, RS, P, RS, P, RS, P (4 propagations, n_rs <= 3 random
+ * searches, Sec. 3.1) with R_n = R * n (Sec. 3.2). Returns the number of E_d
+ * evaluations (no candidate is skipped here). */
+int64_t ffo_search_level(const uint32_t *Cs, const uint32_t *Ct, int W, int H, int n, int r,
+                         const int32_t *flow_coarse, int tile, int n_rs, int R, uint64_t seed,
+                         int flow_id, int32_t *flow, int32_t *cost) {
+  level_ctx L = {Cs, Ct, W, H, n, r, 0};
+  int level = 0;
+  while ((1 << level) < n) level++;
+  if (flow_coarse) seed_level(&L, flow_coarse, flow, cost);
+  for (int s = 0; s < 4; s++) {
+    prop_pass(&L, s, tile, flow, cost);
+    if (s < 3 && s < n_rs) random_search(&L, seed, flow_id, level, s, R * n, flow, cost);
+  }
+  return L.evals;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.4: outlier filtering.                                               */
+/* Eq. 5 two-way check. Reading: the norm is Euclidean and compared strictly; */
+/* with integer flows |.|^2 < eps^2 is used. err_sum = e1 + e2 (squared      */
+/* errors), used by the sparsification. A target outside the image (never    */
+/* produced by the search) fails the check with err_sum = INT32_MAX.          */
+/* ------------------------------------------------------------------------ */
+void ffo_consistency(const int32_t *F, const int32_t *Fb1, const int32_t *Fb2, int W, int H,
+                     int eps, uint8_t *valid_cc, int32_t *err_sum) {
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++) {
+      size_t p = (size_t)y * W + x;
+      int qx = x + F[2 * p], qy = y + F[2 * p + 1];
+      if (qx < 0 || qx >= W || qy < 0 || qy >= H) {
+        valid_cc[p] = 0;
+        err_sum[p] = INT32_MAX;
+        continue;
+      }
+      size_t q = (size_t)qy * W + qx;
+      int64_t a0 = F[2 * p] + Fb1[2 * q], a1 = F[2 * p + 1] + Fb1[2 * q + 1];
+      int64_t b0 = F[2 * p] + Fb2[2 * q], b1 = F[2 * p + 1] + Fb2[2 * q + 1];
+      int64_t e1 = a0 * a0 + a1 * a1, e2 = b0 * b0 + b1 * b1;
+      valid_cc[p] = (e1 < (int64_t)eps * eps) && (e2 < (int64_t)eps * eps);
+      err_sum[p] = (int32_t)((e1 + e2) > INT32_MAX ? INT32_MAX : (e1 + e2));
+    }
+}
+
+static int close3(const int32_t *F, size_t p, size_t q) {
+  int64_t a = F[2 * p] - F[2 * q], b = F[2 * p + 1] - F[2 * q + 1];
+  return a * a + b * b < 9;
+}
+
+/* Region filter. Pixels kept by the consistency check form regions: 4-connected
+ * neighbours belong together when their flows differ by less than 3 px. A region
+ * with fewer than s pixels is deleted if one of its pixels has a 4-neighbour that
+ * the consistency check removed and whose (raw) flow is within 3 px of it, i.e.
+ * the region could absorb that outlier by the same rule. */
+void ffo_region_filter(const int32_t *F, const uint8_t *valid_cc, int W, int H, int s,
+                       uint8_t *valid) {
+  size_t N = (size_t)W * H;
+  int32_t *label = malloc(sizeof(int32_t) * N), *queue = malloc(sizeof(int32_t) * N);
+  static const int NB[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+  for (size_t p = 0; p < N; p++) label[p] = -1;
+  memcpy(valid, valid_cc, N);
+  for (size_t p0 = 0; p0 < N; p0++) {
+    if (!valid_cc[p0] || label[p0] >= 0) continue;
+    int head = 0, tail = 0, touches = 0;
+    queue[tail++] = (int32_t)p0;
+    label[p0] = (int32_t)p0;
+    while (head < tail) {
+      int p = queue[head++], x = p % W, y = p / W;
+      for (int k = 0; k < 4; k++) {
+        int xx = x + NB[k][0], yy = y + NB[k][1];
+        if (xx < 0 || xx >= W || yy < 0 || yy >= H) continue;
+        size_t q = (size_t)yy * W + xx;
+        if (!close3(F, p, q)) continue;
+        if (!valid_cc[q]) {
+          touches = 1;
+          continue;
+        }
+        if (label[q] < 0) {
+          label[q] = (int32_t)p0;
+          queue[tail++] = (int32_t)q;
+        }
+      }
+    }
+    if (tail < s && touches)
+      for (int k = 0; k < tail; k++) valid[queue[k]] = 0;
+  }
+  free(label);
+  free(queue);
+}
+
+/* Sec. 3.5 sparsification. Aligned 3x3 blocks (partial blocks at the right and
+ * bottom edge included); a block with at least e surviving pixels keeps the one
+ * with the smallest err_sum, the first in raster order within the block on
+ * ties. Output rows (x, y, dx, dy) in block raster order; mask marks them.
+ * Returns the number of rows. */
+int ffo_sparsify(const uint8_t *valid, const int32_t *err_sum, const int32_t *F, int W, int H,
+                 int e, int32_t *sparse, uint8_t *mask) {
+  int cnt_out = 0;
+  memset(mask, 0, (size_t)W * H);
+  for (int by = 0; by < (H + 2) / 3; by++)
+    for (int bx = 0; bx < (W + 2) / 3; bx++) {
+      int cnt = 0, best = -1;
+      for (int y = 3 * by; y < imin(3 * by + 3, H); y++)
+        for (int x = 3 * bx; x < imin(3 * bx + 3, W); x++) {
+          int p = y * W + x;
+          if (!valid[p]) continue;
+          cnt++;
+          if (best < 0 || err_sum[p] < err_sum[best]) best = p;
+        }
+      if (cnt >= e && best >= 0) {
+        mask[best] = 1;
+        sparse[4 * cnt_out] = best % W;
+        sparse[4 * cnt_out + 1] = best / W;
+        sparse[4 * cnt_out + 2] = F[2 * best];
+        sparse[4 * cnt_out + 3] = F[2 * best + 1];
+        cnt_out++;
+      }
+    }
+  return cnt_out;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Whole pipeline (Fig. 2 and Sec. 3.4/3.5): three flow fields (forward with   */
+/* radius r, backward with r, backward with r2), each from its own kd tree,   */
+/* then consistency check, region filter and sparsification.                 */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int k, r, r2, leaf, R, eps, e, s, tile, n_rs, K;
+  uint64_t seed;
+} ffo_params;
+
+typedef struct {
+  const uint8_t *src, *tgt;
+  uint32_t **Cs, **Ct; /* census per level index 0..k */
+  int W, H, r, flow_id;
+  const ffo_params *P;
+  const int32_t *proposals;
+  int32_t *flow_out; /* [H][W][2] */
+  int64_t evals;
+} flow_job;
+
+static void *run_flow(void *arg) {
+  flow_job *J = arg;
+  const ffo_params *P = J->P;
+  int W = J->W, H = J->H, N = W * H, ntop = 1 << P->k;
+  int32_t *tf = malloc(sizeof(int32_t) * NFEAT * (size_t)N);
+  ffo_wht_features(J->tgt, W, H, J->r, NULL, 0, tf);
+  int Gx = (W + ntop - 1) / ntop, Gy = (H + ntop - 1) / ntop;
+  int32_t *flow = malloc(sizeof(int32_t) * 2 * (size_t)Gx * Gy);
+  int32_t *cost = malloc(sizeof(int32_t) * (size_t)Gx * Gy);
+  J->evals = ffo_kd_init(tf, J->src, W, H, J->r, P->leaf, J->Cs[P->k], J->Ct[P->k], ntop,
+                         J->proposals, J->proposals ? P->K : 0, flow, cost);
+  free(tf);
+  J->evals += ffo_search_level(J->Cs[P->k], J->Ct[P->k], W, H, ntop, J->r, NULL, P->tile,
+                               P->n_rs, P->R, P->seed, J->flow_id, flow, cost);
+  for (int lv = P->k - 1; lv >= 0; lv--) {
+    int n = 1 << lv;
+    int gx = (W + n - 1) / n, gy = (H + n - 1) / n;
+    int32_t *f2 = malloc(sizeof(int32_t) * 2 * (size_t)gx * gy);
+    int32_t *c2 = malloc(sizeof(int32_t) * (size_t)gx * gy);
+    J->evals += ffo_search_level(J->Cs[lv], J->Ct[lv], W, H, n, J->r, flow, P->tile, P->n_rs,
+                                 P->R, P->seed, J->flow_id, f2, c2);
+    free(flow);
+    free(cost);
+    flow = f2;
+    cost = c2;
+  }
+  memcpy(J->flow_out, flow, sizeof(int32_t) * 2 * (size_t)N);
+  free(flow);
+  free(cost);
+  return NULL;
+}
+
+/* I1, I2: uint8 [H][W][3]. Outputs (all caller-allocated):
+ *   flows   int32 [3][H][W][2]  forward, backward (r), backward (r2)
+ *   valid   uint8 [H][W]        after consistency check and region filter
+ *   err_sum int32 [H][W]
+ *   sparse  int32 [ceil(W/3)*ceil(H/3)][4], mask uint8 [H][W]
+ * proposals: NULL or int32 [Gy][Gx][K][2] at the coarsest grid (forward flow
+ * only). threads > 1 runs the three flows concurrently. Returns the sparse
+ * count; evals (optional) receives the number of E_d evaluations. */
+int ffo_flow_fields(const uint8_t *I1, const uint8_t *I2, int W, int H, const ffo_params *P,
+                    const int32_t *proposals, int threads, int32_t *flows, uint8_t *valid,
+                    int32_t *err_sum, int32_t *sparse, uint8_t *mask, int64_t *evals) {
+  size_t N = (size_t)W * H;
+  int nl = P->k + 1;
+  uint32_t *C1[16], *C2[16];
+  uint8_t *sm = malloc(N * 3);
+  for (int lv = 0; lv < nl; lv++) {
+    int n = 1 << lv;
+    C1[lv] = malloc(sizeof(uint32_t) * N);
+    C2[lv] = malloc(sizeof(uint32_t) * N);
+    ffo_smooth(I1, W, H, n, sm);
+    ffo_census(sm, W, H, n, C1[lv]);
+    ffo_smooth(I2, W, H, n, sm);
+    ffo_census(sm, W, H, n, C2[lv]);
+  }
+  free(sm);
+  flow_job J[3] = {
+      {I1, I2, C1, C2, W, H, P->r, 0, P, proposals, flows, 0},
+      {I2, I1, C2, C1, W, H, P->r, 1, P, NULL, flows + 2 * N, 0},
+      {I2, I1, C2, C1, W, H, P->r2, 2, P, NULL, flows + 4 * N, 0},
+  };
+  if (threads > 1) {
+    pthread_t th[3];
+    for (int i = 0; i < 3; i++) pthread_create(&th[i], NULL, run_flow, &J[i]);
+    for (int i = 0; i < 3; i++) pthread_join(th[i], NULL);
+  } else {
+    for (int i = 0; i < 3; i++) run_flow(&J[i]);
+  }
+  for (int lv = 0; lv < nl; lv++) {
+    free(C1[lv]);
+    free(C2[lv]);
+  }
+  uint8_t *vcc = malloc(N);
+  ffo_consistency(flows, flows + 2 * N, flows + 4 * N, W, H, P->eps, vcc, err_sum);
+  ffo_region_filter(flows, vcc, W, H, P->s, valid);
+  free(vcc);
+  if (evals) *evals = J[0].evals + J[1].evals + J[2].evals;
+  return ffo_sparsify(valid, err_sum, flows, W, H, P->e, sparse, mask);
+}
