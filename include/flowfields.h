@@ -1,0 +1,207 @@
+/*
+ * flowfields.h -- C ABI of the GB300 Flow Fields library (libflowfields.so).
+ *
+ * Flow Fields: dense correspondence fields for large displacement optical flow
+ * (Bailer, Taetz, Stricker, ICCV 2015). The library computes, for a pair of 8-bit
+ * RGB images, the forward flow field and two backward flow fields by kd-tree
+ * initialisation and hierarchical propagation with random search (Sec. 3.1,
+ * 3.2), then removes outliers with the two-way consistency check and the region
+ * filter (Sec. 3.4) and sparsifies the result (Sec. 3.5). Interpolation of the
+ * sparse matches (EpicFlow) is not part of it.
+ *
+ * Conventions shared by every entry point
+ *   - Every pointer argument is DEVICE memory owned by the caller, unless the
+ *     description says otherwise. The library allocates no device memory; the
+ *     scratch it needs comes from the caller's workspace `ws` of `ws_bytes`
+ *     bytes (256-byte aligned), sized by the matching *_workspace_size call.
+ *   - Images are uint8, H x W x 3 (RGB), rows tightly packed.
+ *   - Flows are int16 pairs (dx, dy), interleaved, in full-resolution pixels;
+ *     the target of pixel p is p + flow and always lies inside the image.
+ *     A level-n flow field has one entry per grid point (n*gx, n*gy),
+ *     Gx = ceil(W/n) by Gy = ceil(H/n), row major.
+ *   - Costs are int32 E_d values; 0x7fffffff marks a grid point without a flow.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Every call
+ *     enqueues its work on it and returns without synchronising.
+ *   - Arguments are checked on the host before anything is enqueued; a failed
+ *     check returns an error and enqueues nothing. FF_ERR_CUDA reports a failed
+ *     launch. Nothing is thrown across this boundary.
+ *   - Results are a pure function of the inputs and ff_params; they do not
+ *     depend on streams, batch composition or execution tuning.
+ */
+#ifndef FLOWFIELDS_H
+#define FLOWFIELDS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FF_OK = 0,
+  FF_ERR_INVALID_ARG = 1, /* null pointer or parameter out of range */
+  FF_ERR_SHAPE = 2,       /* image size outside the supported range */
+  FF_ERR_WORKSPACE = 3,   /* workspace missing, misaligned or too small */
+  FF_ERR_CUDA = 4,        /* a CUDA runtime call or launch failed */
+  FF_ERR_DEVICE = 5       /* a device-side check failed (see ff_device_status) */
+} ff_status;
+
+/* Method parameters (Sec. 4 gives k=3, R=1, l=8, r=8, r2=6 and eps/e/s per
+ * dataset). tile is the tile edge T of the fixed parallel propagation schedule:
+ * grid points are processed in T x T tiles, sequentially inside a tile and from
+ * the start-of-pass state across tile borders; odd passes shift the tiles by
+ * T/2. T changes results (it is part of the method's definition here), the
+ * CUDA launch shapes do not. */
+typedef struct ff_params {
+  int32_t k;    /* hierarchy levels; the coarsest grid has spacing 2^k (0..4) */
+  int32_t r;    /* patch radius of the forward and first backward flow (1..8) */
+  int32_t r2;   /* patch radius of the second backward flow (1..8) */
+  int32_t leaf; /* kd-tree leaf size l (2..32) */
+  int32_t R;    /* random-search radius at full resolution; R_n = R*n (0..64) */
+  int32_t eps;  /* consistency threshold eps of Eq. 5, in pixels (1..1000) */
+  int32_t e;    /* minimum surviving pixels per 3x3 block (Sec. 3.5) (1..9) */
+  int32_t s;    /* region-size threshold of the region filter (Sec. 3.4) (>= 0) */
+  int32_t tile; /* tile edge T of the parallel schedule (even, 2..32) */
+  int32_t n_rs; /* random-search steps per level, after passes 0..n_rs-1 (0..3) */
+  int32_t K;    /* proposals per coarsest grid point for the forward flow (0..8) */
+  uint64_t seed; /* seed of the counter-based random search */
+} ff_params;
+
+enum { FF_PRESET_SINTEL = 0, FF_PRESET_MIDDLEBURY = 1, FF_PRESET_KITTI = 2 };
+
+/* Human-readable name of a status code (static string). */
+const char *ff_status_str(ff_status s);
+
+/* Fill *p with the parameters of Sec. 4 for a dataset preset: k=3, R=1, l=8,
+ * r=8, r2=6 and (eps, e, s) = (5, 4, 50) Sintel, (1, 7, 50) Middlebury,
+ * (1, 9, 150) KITTI; tile=32, n_rs=3, K=0, seed=0. */
+ff_status ff_params_preset(ff_params *p, int preset);
+
+/* Workspace bytes needed by ff_flow_fields for a W x H pair (host-only call). */
+ff_status ff_workspace_size(int W, int H, const ff_params *p, size_t *bytes);
+
+/* Sec. 3.2: the smoothed full-resolution image I^n: area downsampling by n
+ * (block mean, (sum + cnt/2) / cnt over the in-image part of each block),
+ * then separable Lanczos-3 upsampling back to W x H with Q14 weights (the
+ * coarse sample j is centred on pixel j*n + (n-1)/2; horizontal pass kept
+ * unrounded, vertical pass rounded (acc + 2^27) >> 28 and clamped to [0,255]).
+ * n is a power of two 1..16; n = 1 copies. img, out: W x H x 3. The workspace
+ * holds the coarse image and the horizontal pass (ff_smooth_workspace_size). */
+ff_status ff_smooth_workspace_size(int W, int H, int n, size_t *bytes);
+ff_status ff_smooth(const uint8_t *img, int W, int H, int n, uint8_t *out, void *ws,
+                    size_t ws_bytes, void *stream);
+
+/* Sec. 3.3: census transform of I^n with neighbour spacing n: bit 8c+o is set
+ * when channel c of the o-th neighbour (raster order of the 3x3 neighbourhood,
+ * centre skipped, coordinates clamped) is below the centre. out: H x W uint32. */
+ff_status ff_census(const uint8_t *img_n, int W, int H, int n, uint32_t *out, void *stream);
+
+/* Sec. 3.1: Walsh-Hadamard features of the (2r+1)^2 patch around each pixel:
+ * the window is split r | r+1 and again into 4 blocks per axis; the first three
+ * Walsh functions in sequency order ((++++), (++--), (+--+)) per axis give 9
+ * bases per channel, feature 9c + 3i + j with i the row function. Pixels are
+ * read with clamped coordinates; r is 1..8. pts (x, y int32 pairs, npts of them) selects
+ * the pixels; pts = NULL computes every pixel in raster order (npts ignored).
+ * feat: int32 rows of 28 (27 features + one zero pad), one row per pixel. */
+ff_status ff_features(const uint8_t *img, int W, int H, int r, const int32_t *pts, int npts,
+                      int32_t *feat, void *stream);
+
+/* Depth D of the kd tree over N points with leaf size `leaf` (the smallest d
+ * with ceil(N / 2^d) <= leaf) and the workspace ff_kdtree_build needs. Host. */
+ff_status ff_kdtree_size(int N, int leaf, int *depth, size_t *ws_bytes);
+
+/* Sec. 3.1: kd tree over feature rows feat[N][28] (as written by ff_features).
+ * Every node splits in the dimension of largest (max - min), lowest index on
+ * ties, at the median: the first floor(m/2) of its m points under the order
+ * (value, pixel index) go left, and the split value is the value of the first
+ * point on the right. Outputs, heap order (children of node i are 2i+1, 2i+2):
+ * split_dim[2^D - 1], split_val[2^D - 1]; perm[N] lists the point indices leaf
+ * by leaf, leaf j holding positions obtained by halving [0, N) along its path
+ * (the left half takes floor(m/2)). The order inside a leaf is unspecified. */
+ff_status ff_kdtree_build(const int32_t *feat, int N, int leaf, int32_t *perm, int32_t *split_dim,
+                          int32_t *split_val, void *ws, size_t ws_bytes, void *stream);
+
+/* Eq. 1 / Eq. 4: initial flow at the grid of spacing n. For each grid point
+ * its WHT vector (features of src_img at radius r) descends the tree built over
+ * the W*H target pixels (no backtracking: left iff value < split value); every
+ * pixel of the reached leaf is a candidate, and the one with the smallest E_d on
+ * P^n_r wins, ties to the lowest pixel index. Then the K proposals of the point
+ * (int16 pairs, [Gy][Gx][K][2], NULL when K = 0) are tried in order; a candidate
+ * replaces the current flow only when its E_d is strictly lower. Targets are
+ * clamped into the image. census_src / census_tgt: level-n census (H x W).
+ * Outputs flow [Gy][Gx][2], cost [Gy][Gx]. Workspace: ff_level_workspace_size. */
+ff_status ff_kdtree_init(const int32_t *perm, const int32_t *split_dim, const int32_t *split_val,
+                         int leaf, const uint8_t *src_img, const uint32_t *census_src,
+                         const uint32_t *census_tgt, int W, int H, int n, int r,
+                         const int16_t *proposals, int K, int16_t *flow, int32_t *cost, void *ws,
+                         size_t ws_bytes, void *stream);
+
+/* Workspace bytes of ff_search_level / ff_kdtree_init at spacing n (host). */
+ff_status ff_level_workspace_size(int W, int H, int n, size_t *bytes);
+
+/* Sec. 3.1 / 3.2: one hierarchy level at spacing n with patch radius r.
+ * If flow_coarse (level 2n, [ceil(H/2n)][ceil(W/2n)][2]) is given, grid points
+ * with both coordinates even take the coarse flow with E_d re-evaluated at this
+ * level and all others start without a flow; if it is NULL, (flow, cost) hold
+ * the initial state on entry. Then four propagation passes (Eq. 2), sources
+ * (x-n,y),(x,y-n) / (x+n,y),(x,y+n) / (x+n,y),(x,y-n) / (x-n,y),(x,y+n), each
+ * pass scanning away from its sources in the tiled schedule of ff_params.tile,
+ * and after passes 0..n_rs-1 a random search with an offset uniform in
+ * [-R*n, R*n]^2 drawn from SplitMix64 of (seed, flow_id, log2 n, step, gx, gy).
+ * A candidate wins only with strictly lower E_d; targets are clamped into the
+ * image. flow_id (0..3) separates the random streams of the three flows.
+ * Outputs flow [Gy][Gx][2] and cost [Gy][Gx] at this level. */
+ff_status ff_search_level(const uint32_t *census_src, const uint32_t *census_tgt, int W, int H,
+                          int n, int r, const int16_t *flow_coarse, const ff_params *p,
+                          int flow_id, int16_t *flow, int32_t *cost, void *ws, size_t ws_bytes,
+                          void *stream);
+
+/* Sec. 3.4 / 3.5: outlier filtering of the forward flow F against the backward
+ * flows Fb1 (radius r) and Fb2 (radius r2), all H x W x 2.
+ *   Eq. 5: e_j = |F(p) + Fb_j(p + F(p))|^2; the pixel passes when e_1 and e_2 are
+ *          both below eps^2; err_sum = e_1 + e_2.
+ *   Region filter: passing pixels whose 4-neighbours differ in flow by less than
+ *          3 px form regions; a region of fewer than s pixels is removed when one
+ *          of its pixels has a 4-neighbour rejected by Eq. 5 whose flow is within
+ *          3 px of it. Result: valid [H][W] (0/1).
+ *   Sparsification: in each aligned 3x3 block with at least e valid pixels the
+ *          one with the smallest err_sum (first in raster order on ties) is kept:
+ *          mask [H][W] and rows (x, y, dx, dy) int32 in block raster order in
+ *          sparse [ceil(W/3)*ceil(H/3)][4]; *n_sparse (device int32) = row count.
+ * Workspace: ff_filter_workspace_size. */
+ff_status ff_filter_workspace_size(int W, int H, size_t *bytes);
+ff_status ff_consistency_filter(const int16_t *F, const int16_t *Fb1, const int16_t *Fb2, int W,
+                                int H, const ff_params *p, uint8_t *valid, int32_t *err_sum,
+                                int32_t *sparse, int32_t *n_sparse, uint8_t *mask, void *ws,
+                                size_t ws_bytes, void *stream);
+
+/* The whole path for one pair (Fig. 2): smoothed images and census for both
+ * frames at every level, three flow fields (forward I1->I2 with r, backward
+ * I2->I1 with r and with r2; flow ids 0, 1, 2), each from its own kd tree, then
+ * ff_consistency_filter. proposals: NULL or int16 [ceil(H/2^k)][ceil(W/2^k)][K][2]
+ * for the forward flow. Outputs: flows [3][H][W][2], valid, err_sum, sparse,
+ * n_sparse (device int32), mask as in ff_consistency_filter. */
+ff_status ff_flow_fields(const uint8_t *I1, const uint8_t *I2, int W, int H, const ff_params *p,
+                         const int16_t *proposals, int16_t *flows, uint8_t *valid,
+                         int32_t *err_sum, int32_t *sparse, int32_t *n_sparse, uint8_t *mask,
+                         void *ws, size_t ws_bytes, void *stream);
+
+/* Device-side status word kept at the start of a workspace: 0 when every
+ * device check passed, else an error code with the grid coordinate where it was
+ * raised. Synchronises `stream`, then copies 16 bytes device->host. */
+ff_status ff_device_status(const void *ws, uint32_t *code, int32_t *x, int32_t *y, void *stream);
+
+/* Execution counters of the library, for benchmarking: kernels launched since
+ * the last reset, and (when enabled with ff_profile_enable(1)) the summed
+ * duration in ms and the launch count of the propagation kernel, measured with
+ * CUDA events on the stream each launch was issued on. Host-only calls;
+ * ff_profile_read synchronises the recorded events. */
+ff_status ff_profile_enable(int on);
+ff_status ff_profile_reset(void);
+ff_status ff_profile_read(uint64_t *launches, double *prop_ms, uint64_t *prop_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLOWFIELDS_H */

@@ -1,0 +1,215 @@
+// Sec. 3.4 outlier filtering and Sec. 3.5 sparsification.
+//
+//   consistency  Eq. 5 two-way check against two backward flows; per pixel.
+//   region       connected components of the surviving pixels (4-neighbours with
+//                flow difference below 3 px) by lock-free union-find: a link
+//                always hangs the larger root under the smaller one with one
+//                atomicCAS, so every component's root is its smallest pixel index
+//                and the labelling is unique. Components smaller than s that touch
+//                a consistency-rejected neighbour within 3 px are removed.
+//   sparsify     one pixel per aligned 3x3 block with >= e survivors (smallest
+//                e_1 + e_2, raster-first on ties), compacted in block raster order
+//                by one CTA (ordered scan, so the list is deterministic).
+#include "ff_internal.cuh"
+
+namespace ff {
+
+__device__ __forceinline__ bool close3(uint32_t a, uint32_t b) {
+  const int dx = flow_dx(a) - flow_dx(b), dy = flow_dy(a) - flow_dy(b);
+  return dx * dx + dy * dy < 9;
+}
+
+__global__ void k_consistency(const uint32_t *__restrict__ F, const uint32_t *__restrict__ Fb1,
+                              const uint32_t *__restrict__ Fb2, int W, int H, int eps,
+                              uint8_t *__restrict__ vcc, int32_t *__restrict__ err,
+                              int32_t *__restrict__ parent) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= W * H) return;
+  const int x = p % W, y = p / W;
+  const uint32_t f = F[p];
+  const int qx = x + flow_dx(f), qy = y + flow_dy(f);
+  uint8_t ok = 0;
+  int32_t es = 0x7fffffff;
+  if (qx >= 0 && qx < W && qy >= 0 && qy < H) {
+    const int q = qy * W + qx;
+    const uint32_t b1 = Fb1[q], b2 = Fb2[q];
+    const long long a0 = flow_dx(f) + flow_dx(b1), a1 = flow_dy(f) + flow_dy(b1);
+    const long long c0 = flow_dx(f) + flow_dx(b2), c1 = flow_dy(f) + flow_dy(b2);
+    const long long e1 = a0 * a0 + a1 * a1, e2 = c0 * c0 + c1 * c1, e2eps = (long long)eps * eps;
+    ok = (e1 < e2eps) && (e2 < e2eps);
+    es = (int32_t)min(e1 + e2, (long long)0x7fffffff);
+  }
+  vcc[p] = ok;
+  err[p] = es;
+  parent[p] = ok ? p : -1;
+}
+
+__device__ __forceinline__ int uf_find(const int32_t *parent, int x) {
+  int p = parent[x];
+  while (p != x) {
+    x = p;
+    p = parent[x];
+  }
+  return x;
+}
+
+__device__ void uf_unite(int32_t *parent, int a, int b) {
+  while (true) {
+    a = uf_find(parent, a);
+    b = uf_find(parent, b);
+    if (a == b) return;
+    if (a > b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    const int old = atomicCAS(&parent[b], b, a);
+    if (old == b) return;
+    b = old;
+  }
+}
+
+__global__ void k_union(const uint32_t *__restrict__ F, const uint8_t *__restrict__ vcc, int W, int H,
+                        int32_t *parent) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= W * H || !vcc[p]) return;
+  const int x = p % W, y = p / W;
+  const uint32_t f = F[p];
+  if (x + 1 < W && vcc[p + 1] && close3(f, F[p + 1])) uf_unite(parent, p, p + 1);
+  if (y + 1 < H && vcc[p + W] && close3(f, F[p + W])) uf_unite(parent, p, p + W);
+}
+
+__global__ void k_flatten(const uint8_t *__restrict__ vcc, int N, int32_t *parent,
+                          int32_t *__restrict__ size) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  size[p] = 0;
+  if (!vcc[p]) return;
+  parent[p] = uf_find(parent, p);
+}
+
+__global__ void k_region_stats(const uint32_t *__restrict__ F, const uint8_t *__restrict__ vcc, int W,
+                               int H, const int32_t *__restrict__ parent, int32_t *size,
+                               uint8_t *touch) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= W * H || !vcc[p]) return;
+  const int root = parent[p];
+  atomicAdd(&size[root], 1);
+  const int x = p % W, y = p / W;
+  const uint32_t f = F[p];
+  bool t = false;
+  if (x > 0 && !vcc[p - 1] && close3(f, F[p - 1])) t = true;
+  if (x + 1 < W && !vcc[p + 1] && close3(f, F[p + 1])) t = true;
+  if (y > 0 && !vcc[p - W] && close3(f, F[p - W])) t = true;
+  if (y + 1 < H && !vcc[p + W] && close3(f, F[p + W])) t = true;
+  if (t) touch[root] = 1;
+}
+
+__global__ void k_region_apply(const uint8_t *__restrict__ vcc, int N, int s,
+                               const int32_t *__restrict__ parent, const int32_t *__restrict__ size,
+                               const uint8_t *__restrict__ touch, uint8_t *__restrict__ valid,
+                               uint8_t *__restrict__ mask) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  mask[p] = 0;
+  uint8_t v = vcc[p];
+  if (v) {
+    const int root = parent[p];
+    if (size[root] < s && touch[root]) v = 0;
+  }
+  valid[p] = v;
+}
+
+// Per 3x3 block: survivor count and the smallest-err pixel (raster-first).
+__global__ void k_blocks(const uint8_t *__restrict__ valid, const int32_t *__restrict__ err, int W, int H,
+                         int e, int32_t *__restrict__ pick) {
+  const int BX = (W + 2) / 3, BY = (H + 2) / 3;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= BX * BY) return;
+  const int bx = b % BX, by = b / BX;
+  int cnt = 0, best = -1;
+  for (int y = 3 * by; y < min(3 * by + 3, H); y++)
+    for (int x = 3 * bx; x < min(3 * bx + 3, W); x++) {
+      const int p = y * W + x;
+      if (!valid[p]) continue;
+      cnt++;
+      if (best < 0 || err[p] < err[best]) best = p;
+    }
+  pick[b] = (cnt >= e) ? best : -1;
+}
+
+// One CTA: ordered compaction of the picks into (x, y, dx, dy) rows.
+__global__ void __launch_bounds__(1024) k_compact(const int32_t *__restrict__ pick, int nb, int W,
+                                                  const uint32_t *__restrict__ F,
+                                                  int32_t *__restrict__ sparse,
+                                                  int32_t *__restrict__ n_sparse,
+                                                  uint8_t *__restrict__ mask) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x, per = (nb + 1023) / 1024;
+  const int b0 = min(t * per, nb), b1 = min(b0 + per, nb);
+  int cnt = 0;
+  for (int b = b0; b < b1; b++) cnt += pick[b] >= 0;
+  part[t] = cnt;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan
+    const int v = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int out = part[t] - cnt;
+  for (int b = b0; b < b1; b++) {
+    const int p = pick[b];
+    if (p < 0) continue;
+    const uint32_t f = F[p];
+    sparse[4 * out] = p % W;
+    sparse[4 * out + 1] = p / W;
+    sparse[4 * out + 2] = flow_dx(f);
+    sparse[4 * out + 3] = flow_dy(f);
+    mask[p] = 1;
+    out++;
+  }
+  if (t == 1023) *n_sparse = part[1023];
+}
+
+size_t filter_scratch_bytes(int W, int H) {
+  const size_t N = (size_t)W * H, NB = (size_t)((W + 2) / 3) * ((H + 2) / 3);
+  Arena a;
+  a.take<uint8_t>(N);
+  a.take<int32_t>(N);
+  a.take<int32_t>(N);
+  a.take<uint8_t>(N);
+  a.take<int32_t>(NB);
+  return a.off;
+}
+
+ff_status launch_filter(const uint32_t *F, const uint32_t *Fb1, const uint32_t *Fb2, int W, int H,
+                        int eps, int e, int s, uint8_t *valid, int32_t *err_sum, int32_t *sparse,
+                        int32_t *n_sparse, uint8_t *mask, void *scratch, cudaStream_t st) {
+  const int N = W * H, NB = ((W + 2) / 3) * ((H + 2) / 3);
+  Arena a(scratch, (size_t)-1);
+  uint8_t *vcc = a.take<uint8_t>(N);
+  int32_t *parent = a.take<int32_t>(N);
+  int32_t *size = a.take<int32_t>(N);
+  uint8_t *touch = a.take<uint8_t>(N);
+  int32_t *pick = a.take<int32_t>(NB);
+  const int B = 256, g = (N + B - 1) / B;
+  if (cudaMemsetAsync(touch, 0, N, st) != cudaSuccess) return FF_ERR_CUDA;
+  k_consistency<<<g, B, 0, st>>>(F, Fb1, Fb2, W, H, eps, vcc, err_sum, parent);
+  FF_CHECK_LAUNCH();
+  k_union<<<g, B, 0, st>>>(F, vcc, W, H, parent);
+  FF_CHECK_LAUNCH();
+  k_flatten<<<g, B, 0, st>>>(vcc, N, parent, size);
+  FF_CHECK_LAUNCH();
+  k_region_stats<<<g, B, 0, st>>>(F, vcc, W, H, parent, size, touch);
+  FF_CHECK_LAUNCH();
+  k_region_apply<<<g, B, 0, st>>>(vcc, N, s, parent, size, touch, valid, mask);
+  FF_CHECK_LAUNCH();
+  k_blocks<<<(NB + B - 1) / B, B, 0, st>>>(valid, err_sum, W, H, e, pick);
+  FF_CHECK_LAUNCH();
+  k_compact<<<1, 1024, 0, st>>>(pick, NB, W, F, sparse, n_sparse, mask);
+  FF_CHECK_LAUNCH();
+  return FF_OK;
+}
+
+}  // namespace ff

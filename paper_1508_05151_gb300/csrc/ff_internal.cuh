@@ -1,0 +1,297 @@
+// Internal declarations of the GB300 Flow Fields library. Not part of the ABI.
+//
+// Data layout in HBM
+//   Census "phase planes". At spacing n the census image of a frame is stored as
+//   n*n planes, one per pixel phase (x mod n, y mod n). Plane (px, py) entry
+//   (i, j) holds the census of pixel (clamp(px + n*(i - P)), clamp(py + n*(j - P)))
+//   for i in [0, NX + 2P), j in [0, NY + 2P), NX = ceil(W/n), NY = ceil(H/n),
+//   P >= the largest patch radius. The taps of a subsampled patch P^n_r around
+//   any pixel (Eq. 3) then form a dense (2r+1)^2 block of one plane, already
+//   clamped at the image border, so every tap is a plain in-bounds load and each
+//   patch row is 2r+1 consecutive words. The row pitch is a multiple of 16 bytes.
+//
+//   Flows are packed int16 pairs in one uint32 (dx in the low half); costs int32.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "flowfields.h"
+
+namespace ff {
+
+constexpr int32_t COST_UNSET = 0x7fffffff;
+constexpr int NFEAT = 27;
+constexpr int FEAT_STRIDE = 28;  // int32 per feature row (27 + pad) = 112 bytes
+constexpr int PLANE_PAD = 8;     // P: supports patch radii up to 8
+constexpr int MAX_TILE = 32;
+constexpr int MAX_K = 8;
+
+// Device status word at the start of every workspace (16 bytes, first 256
+// reserved): code, x, y, spare.
+struct DeviceStatus {
+  uint32_t code;
+  int32_t x, y, spare;
+};
+constexpr size_t WS_HEADER = 256;
+enum : uint32_t { DEV_OK = 0, DEV_ERR_BOUNDS = 1, DEV_ERR_KD = 2, DEV_ERR_TIMEOUT = 3 };
+
+__device__ __forceinline__ void raise_status(DeviceStatus *st, uint32_t code, int x, int y) {
+  if (st && atomicCAS(&st->code, 0u, code) == 0u) {
+    st->x = x;
+    st->y = y;
+  }
+}
+
+// ---------------------------------------------------------------- flows ------
+__host__ __device__ __forceinline__ uint32_t pack_flow(int dx, int dy) {
+  return (uint32_t)(uint16_t)(int16_t)dx | ((uint32_t)(uint16_t)(int16_t)dy << 16);
+}
+__host__ __device__ __forceinline__ int flow_dx(uint32_t f) { return (int)(int16_t)(f & 0xffffu); }
+__host__ __device__ __forceinline__ int flow_dy(uint32_t f) { return (int)(int16_t)(f >> 16); }
+
+__host__ __device__ __forceinline__ int clampi(int v, int lo, int hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// ---------------------------------------------------------------- planes -----
+struct Planes {
+  uint32_t *base;  // plane (px, py) at base + (py * n + px) * plane_words
+  int W, H, n, log2n;
+  int NX, NY;       // ceil(W/n), ceil(H/n)
+  int pitch;        // words per padded row (>= NX + 2P, multiple of 4)
+  int rows;         // NY + 2P
+  size_t plane_words;  // pitch * rows
+};
+
+__host__ __device__ inline Planes make_planes(uint32_t *base, int W, int H, int n) {
+  Planes p;
+  p.base = base;
+  p.W = W;
+  p.H = H;
+  p.n = n;
+  int l = 0;
+  while ((1 << l) < n) l++;
+  p.log2n = l;
+  p.NX = (W + n - 1) / n;
+  p.NY = (H + n - 1) / n;
+  p.pitch = ((p.NX + 2 * PLANE_PAD) + 3) & ~3;
+  p.rows = p.NY + 2 * PLANE_PAD;
+  p.plane_words = (size_t)p.pitch * p.rows;
+  return p;
+}
+__host__ __device__ inline size_t planes_words(int W, int H, int n) {
+  Planes p = make_planes(nullptr, W, H, n);
+  return p.plane_words * (size_t)n * n;
+}
+
+// Address of the centre tap of the patch around pixel (x, y), inside the image.
+__device__ __forceinline__ const uint32_t *plane_centre(const Planes &P, int x, int y) {
+  int m = P.n - 1;
+  const uint32_t *pl = P.base + (size_t)(((y & m) << P.log2n) + (x & m)) * P.plane_words;
+  return pl + (size_t)((y >> P.log2n) + PLANE_PAD) * P.pitch + (x >> P.log2n) + PLANE_PAD;
+}
+
+// ------------------------------------------------------- patch cost ---------
+// E_d over the (2R+1)^2 taps of P^n_r (Eq. 3) with the census data term: a group
+// of 16 lanes (one half warp, mask gmask) splits the taps, tap t = lane + 16k in
+// row-major patch order, and the popcounts are summed with xor shuffles. Both
+// operands are given as the address of the patch centre and a row pitch in
+// words; the result is complete in every lane of the group.
+template <int R>
+__device__ __forceinline__ int group_cost(const uint32_t *sc, int spitch, const uint32_t *tc,
+                                          int tpitch, int l16, unsigned gmask) {
+  constexpr int L = 2 * R + 1, LL = L * L, KT = (LL + 15) / 16;
+  int acc = 0;
+#pragma unroll
+  for (int k = 0; k < KT; k++) {
+    const int t = l16 + 16 * k;
+    if (t < LL) {
+      const int v = t / L - R, u = t % L - R;
+      acc += __popc(sc[v * spitch + u] ^ __ldg(tc + v * tpitch + u));
+    }
+  }
+  acc += __shfl_xor_sync(gmask, acc, 8);
+  acc += __shfl_xor_sync(gmask, acc, 4);
+  acc += __shfl_xor_sync(gmask, acc, 2);
+  acc += __shfl_xor_sync(gmask, acc, 1);
+  return acc;
+}
+
+#define FF_DISPATCH_R(r, ...)                   \
+  switch (r) {                                  \
+    case 1: { constexpr int RR = 1; __VA_ARGS__; } break; \
+    case 2: { constexpr int RR = 2; __VA_ARGS__; } break; \
+    case 3: { constexpr int RR = 3; __VA_ARGS__; } break; \
+    case 4: { constexpr int RR = 4; __VA_ARGS__; } break; \
+    case 5: { constexpr int RR = 5; __VA_ARGS__; } break; \
+    case 6: { constexpr int RR = 6; __VA_ARGS__; } break; \
+    case 7: { constexpr int RR = 7; __VA_ARGS__; } break; \
+    case 8: { constexpr int RR = 8; __VA_ARGS__; } break; \
+    default: return FF_ERR_INVALID_ARG;         \
+  }
+
+// ------------------------------------------------------ descriptors ----------
+// Kernels read their problem descriptors from device memory. They are written
+// there, on the stream, by a small kernel that receives them as parameters.
+template <typename T, int CAP>
+struct DescChunk {
+  T d[CAP];
+};
+template <typename T, int CAP>
+__global__ void k_write_desc(DescChunk<T, CAP> c, int n, T *dst) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = c.d[i];
+}
+void count_launch(int n);
+template <typename T>
+inline ff_status upload_desc(const T *host, T *dev, int n, cudaStream_t st) {
+  constexpr int CAP = (3072 / sizeof(T)) > 0 ? (3072 / sizeof(T)) : 1;
+  for (int i = 0; i < n; i += CAP) {
+    DescChunk<T, CAP> c;
+    int m = n - i < CAP ? n - i : CAP;
+    for (int k = 0; k < m; k++) c.d[k] = host[i + k];
+    k_write_desc<T, CAP><<<1, 32, 0, st>>>(c, m, dev + i);
+    count_launch(1);
+    if (cudaPeekAtLastError() != cudaSuccess) {
+      (void)cudaGetLastError();
+      return FF_ERR_CUDA;
+    }
+  }
+  return FF_OK;
+}
+
+// ------------------------------------------------------------- RNG ------------
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): golden-gamma increment, then the
+// 64-bit finaliser. Key layout: gx bits 0-23, gy 24-47, step 48-49, log2 n 50-52,
+// flow id 53-54, xored into the seed. Lemire's multiply-shift maps the low and
+// high 32-bit halves to [0, 2 Rn] for dx and dy.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ void rs_offset(uint64_t seed, int flow_id, int level, int step,
+                                                   int gx, int gy, int Rn, int &dx, int &dy) {
+  uint64_t key = seed ^ ((uint64_t)gx & 0xffffffULL) ^ (((uint64_t)gy & 0xffffffULL) << 24) ^
+                 ((uint64_t)(step & 3) << 48) ^ ((uint64_t)(level & 7) << 50) ^
+                 ((uint64_t)(flow_id & 3) << 53);
+  uint64_t z = splitmix64(key);
+  uint64_t span = 2ull * (uint64_t)Rn + 1ull;
+  dx = (int)(((z & 0xffffffffULL) * span) >> 32) - Rn;
+  dy = (int)(((z >> 32) * span) >> 32) - Rn;
+}
+
+// --------------------------------------------------------- workspace ---------
+// Bump allocator over the caller's workspace; with base == nullptr it only
+// measures. Every block is 256-byte aligned.
+struct Arena {
+  char *base;
+  size_t cap, off;
+  explicit Arena(void *b = nullptr, size_t c = 0) : base((char *)b), cap(c), off(0) {}
+  template <typename T>
+  T *take(size_t count) {
+    size_t bytes = ((count * sizeof(T)) + 255) & ~(size_t)255;
+    T *p = base ? (T *)(base + off) : nullptr;
+    off += bytes;
+    return p;
+  }
+  bool fits() const { return base == nullptr || off <= cap; }
+};
+
+// ------------------------------------------------------- launch accounting ---
+void count_launch(int n);
+bool prof_enabled();
+void prof_begin(cudaStream_t s);
+void prof_end(cudaStream_t s);
+
+#define FF_CHECK_LAUNCH()                                     \
+  do {                                                        \
+    ::ff::count_launch(1);                                     \
+    if (cudaPeekAtLastError() != cudaSuccess) {               \
+      (void)cudaGetLastError();                               \
+      return FF_ERR_CUDA;                                     \
+    }                                                         \
+  } while (0)
+
+#define FF_TRY(expr)                      \
+  do {                                    \
+    ff_status _s = (expr);                \
+    if (_s != FF_OK) return _s;           \
+  } while (0)
+
+// ------------------------------------------------------------ pyramid --------
+struct LanczosTable {
+  int32_t base[16];
+  int32_t w[16][6];
+};
+void lanczos_table(int n, LanczosTable *t);  // host
+size_t smooth_scratch_bytes(int W, int H, int n);
+ff_status launch_smooth(const uint8_t *img, int W, int H, int n, uint8_t *out, void *scratch,
+                        cudaStream_t st);
+ff_status launch_census(const uint8_t *imgn, int W, int H, int n, uint32_t *out, cudaStream_t st);
+ff_status launch_planes(const uint32_t *census, Planes P, cudaStream_t st);
+
+// ----------------------------------------------------------- features --------
+// pts != NULL: explicit (x, y) list; else grid of spacing grid_n (1 = all pixels).
+ff_status launch_features(const uint8_t *img, int W, int H, int r, const int32_t *pts, int npts,
+                          int grid_n, int32_t *feat, cudaStream_t st);
+
+// ------------------------------------------------------------- kd tree -------
+struct KdBuild {
+  const int32_t *feat;  // [N][28]
+  int N, leaf, D;
+  int32_t *perm;        // [N] output
+  int32_t *split_dim, *split_val;  // [2^D - 1]
+  // scratch (from kd_scratch)
+  int32_t *perm_tmp;
+  int32_t *seg_off;    // offsets of all top-level segments
+  int32_t *mm;         // min/max per top-level segment and dim
+  uint32_t *hist;      // radix histograms
+  int32_t *sel;        // per-segment select state
+  int32_t *cnt;        // per-segment partition counters
+  int top_levels;      // levels built by the multi-block path
+  DeviceStatus *status;  // set if a partition count is inconsistent
+};
+int kd_depth(int N, int leaf);
+size_t kd_scratch_bytes(int N, int leaf);
+void kd_bind_scratch(KdBuild &b, Arena &a);
+// Builds `ntrees` trees in the same launches.
+ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev_desc, int ntrees, cudaStream_t st);
+
+struct KdQuery {
+  const int32_t *perm, *split_dim, *split_val;
+  int N, D, leaf;
+  const int32_t *qfeat;     // [G][28] features of the grid points
+  Planes src, tgt;          // level-n census planes
+  int r;
+  const uint32_t *proposals;  // [G][K] packed or nullptr
+  int K;
+  uint32_t *flow;  // [G]
+  int32_t *cost;   // [G]
+};
+ff_status launch_kd_query(const KdQuery *q, KdQuery *dev_desc, int nq, cudaStream_t st);
+
+// -------------------------------------------------------------- search -------
+struct SearchProblem {
+  Planes src, tgt;   // level-n census planes of the source and target frame
+  int r, flow_id;
+  const uint32_t *flow_coarse;  // seeding input (level 2n grid) or nullptr
+  uint32_t *flow_a, *flow_b;    // ping-pong state [G]
+  int32_t *cost_a, *cost_b;
+  uint32_t *flow_final;  // where the last pass writes (nullptr = ping-pong buffer)
+  int32_t *cost_final;
+};
+// Seeds (if flow_coarse) and runs the 4 passes with n_rs random searches.
+// After the call the state is in flow_final/cost_final when given, else in
+// flow_a/cost_a.
+ff_status run_level(const SearchProblem *probs, SearchProblem *dev_desc, int nprob, int tile,
+                    int n_rs, int R, uint64_t seed, cudaStream_t st);
+
+// -------------------------------------------------------------- filter -------
+size_t filter_scratch_bytes(int W, int H);
+ff_status launch_filter(const uint32_t *F, const uint32_t *Fb1, const uint32_t *Fb2, int W, int H,
+                        int eps, int e, int s, uint8_t *valid, int32_t *err_sum, int32_t *sparse,
+                        int32_t *n_sparse, uint8_t *mask, void *scratch, cudaStream_t st);
+
+}  // namespace ff

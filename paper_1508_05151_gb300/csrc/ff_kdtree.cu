@@ -1,0 +1,539 @@
+// Sec. 3.1: device kd tree over the 27-D WHT vectors of all target pixels, and
+// the bounded-leaf query + rerank that gives the initial flow (Eq. 1 / Eq. 4).
+//
+// Tree definition (shared with the CPU statement of the method): perfect tree of
+// depth D = min{d : ceil(N / 2^d) <= l}; a node of m points splits on the
+// dimension of largest (max - min) (lowest index on ties); the first floor(m/2)
+// points under the order (value, pixel index) go left; split value = value of the
+// first right point. Segments of a level are contiguous in `perm`, obtained by
+// halving [0, N) (left takes floor(m/2)).
+//
+// Build, level by level:
+//   top levels (segments > SUB_MAX points): multi-CTA passes per level
+//     minmax   per-segment per-dim min/max (lanes = dims, coalesced 108-B rows)
+//     sel_init dimension choice, key width
+//     4 x (hist, digit)  radix select of the rank-floor(m/2) key, 11-bit digits,
+//                        key = (value - min) << ibits | pixel index (unique)
+//     partition          key < selected key -> left child, else right
+//   bottom levels: one 1024-thread CTA per segment finishes its whole subtree in
+//     shared memory: per node exact ranks by counting (broadcast reads), each
+//     point moves to position node_begin + rank, i.e. the node ends up sorted by
+//     (value, index) and the left half is the first floor(m/2).
+#include "ff_internal.cuh"
+
+namespace ff {
+
+constexpr int SUB_MAX = 1024;  // largest segment finished by one CTA
+constexpr int DIGIT = 11;
+constexpr int NBINS = 1 << DIGIT;
+constexpr int MAX_PASSES = 4;  // 44 key bits: 20 value + 24 index bits
+
+int kd_depth(int N, int leaf) {
+  int d = 0;
+  while (((long long)N + (1ll << d) - 1) / (1ll << d) > leaf) d++;
+  return d;
+}
+
+static int kd_top_levels(int N, int D) {
+  int t = 0;
+  while (((long long)N + (1ll << t) - 1) / (1ll << t) > SUB_MAX) t++;
+  return t < D ? t : D;
+}
+
+__host__ __device__ static int bits_for(long long v) {  // bits to represent 0..v
+  int b = 0;
+  while ((1ll << b) <= v) b++;
+  return b;
+}
+
+size_t kd_scratch_bytes(int N, int leaf) {
+  KdBuild b{};
+  b.N = N;
+  b.leaf = leaf;
+  Arena a;
+  kd_bind_scratch(b, a);
+  return a.off;
+}
+
+void kd_bind_scratch(KdBuild &b, Arena &a) {
+  b.D = kd_depth(b.N, b.leaf);
+  b.top_levels = kd_top_levels(b.N, b.D);
+  int T = b.top_levels;
+  int segs = 1 << (T > 0 ? T - 1 : 0);  // widest top level processed
+  b.perm_tmp = a.take<int32_t>(b.N > 0 ? b.N : 1);
+  b.seg_off = a.take<int32_t>((size_t)(1 << (T + 1)) + T + 2);
+  b.mm = a.take<int32_t>((size_t)segs * NFEAT * 2);
+  b.hist = a.take<uint32_t>((size_t)segs * NBINS);
+  b.sel = a.take<int32_t>((size_t)segs * 8);
+  b.cnt = a.take<int32_t>((size_t)segs * 2);
+}
+
+// Offsets of segment i at depth d (i in [0, 2^d]) by halving along i's bits.
+__device__ __forceinline__ int seg_begin(int N, int d, int i) {
+  if (i >= (1 << d)) return N;
+  int b = 0, e = N;
+  for (int k = d - 1; k >= 0; k--) {
+    int half = (e - b) >> 1;
+    if ((i >> k) & 1) b += half;
+    else e = b + half;
+  }
+  return b;
+}
+__host__ __device__ __forceinline__ int seg_base(int d) { return (1 << d) - 1 + d; }
+
+__global__ void k_kd_seg_off(KdBuild *trees, int ntrees) {
+  KdBuild &T = trees[blockIdx.y];
+  for (int d = 0; d <= T.top_levels; d++) {
+    int cnt = (1 << d) + 1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+      T.seg_off[seg_base(d) + i] = seg_begin(T.N, d, i);
+  }
+}
+
+__global__ void k_kd_init_perm(KdBuild *trees) {
+  KdBuild &T = trees[blockIdx.y];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.N; i += gridDim.x * blockDim.x)
+    T.perm[i] = i;
+}
+
+// Segment containing position pos at depth d (binary search in seg_off).
+__device__ __forceinline__ int find_seg(const int32_t *off, int nseg, int pos) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= pos) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr int MM_CHUNK = 2048;  // positions per CTA in k_kd_minmax (spans <= 3 segments)
+
+__global__ void __launch_bounds__(256) k_kd_minmax(KdBuild *trees, int d) {
+  KdBuild &T = trees[blockIdx.y];
+  if (d >= T.top_levels) return;
+  int start = blockIdx.x * MM_CHUNK;
+  if (start >= T.N) return;
+  int nseg = 1 << d;
+  const int32_t *off = T.seg_off + seg_base(d);
+  __shared__ int smin[4][NFEAT], smax[4][NFEAT];
+  __shared__ int seg0;
+  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) seg0 = find_seg(off, nseg, start);
+  for (int t = tid; t < 4 * NFEAT; t += blockDim.x) {
+    smin[t / NFEAT][t % NFEAT] = INT32_MAX;
+    smax[t / NFEAT][t % NFEAT] = INT32_MIN;
+  }
+  __syncthreads();
+  int p0 = start + warp * (MM_CHUNK / 8), p1 = min(p0 + MM_CHUNK / 8, T.N);
+  if (p0 < p1) {
+    int seg = find_seg(off, nseg, p0), next = off[seg + 1];
+    int lo = INT32_MAX, hi = INT32_MIN;
+    for (int p = p0; p < p1; p++) {
+      if (p >= next) {
+        if (lane < NFEAT) {
+          atomicMin(&smin[seg - seg0][lane], lo);
+          atomicMax(&smax[seg - seg0][lane], hi);
+        }
+        lo = INT32_MAX;
+        hi = INT32_MIN;
+        while (p >= next) next = off[++seg + 1];
+      }
+      if (lane < NFEAT) {
+        int v = T.feat[(size_t)T.perm[p] * FEAT_STRIDE + lane];
+        lo = min(lo, v);
+        hi = max(hi, v);
+      }
+    }
+    if (lane < NFEAT) {
+      atomicMin(&smin[seg - seg0][lane], lo);
+      atomicMax(&smax[seg - seg0][lane], hi);
+    }
+  }
+  __syncthreads();
+  int last = find_seg(off, nseg, min(start + MM_CHUNK, T.N) - 1);
+  for (int t = tid; t < (last - seg0 + 1) * NFEAT; t += blockDim.x) {
+    int s = t / NFEAT, dim = t % NFEAT;
+    if (smin[s][dim] == INT32_MAX) continue;
+    atomicMin(&T.mm[((seg0 + s) * NFEAT + dim) * 2], smin[s][dim]);
+    atomicMax(&T.mm[((seg0 + s) * NFEAT + dim) * 2 + 1], smax[s][dim]);
+  }
+}
+
+__global__ void k_kd_mm_reset(KdBuild *trees, int d) {
+  KdBuild &T = trees[blockIdx.y];
+  if (d >= T.top_levels) return;
+  int n = (1 << d) * NFEAT;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    T.mm[2 * i] = INT32_MAX;
+    T.mm[2 * i + 1] = INT32_MIN;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (1 << d) * NBINS;
+       i += gridDim.x * blockDim.x)
+    T.hist[i] = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (1 << d) * 2; i += gridDim.x * blockDim.x)
+    T.cnt[i] = 0;
+}
+
+// sel state per segment: [0] dim, [1] vmin, [2] key bits B, [3] ibits,
+// [4] remaining rank k, [5] prefix lo, [6] prefix hi, [7] bits consumed
+__global__ void k_kd_sel_init(KdBuild *trees, int d) {
+  KdBuild &T = trees[blockIdx.y];
+  if (d >= T.top_levels) return;
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= (1 << d)) return;
+  const int32_t *off = T.seg_off + seg_base(d);
+  int m = off[s + 1] - off[s];
+  int best = 0;
+  long long bs = -1;
+  for (int dim = 0; dim < NFEAT; dim++) {
+    long long sp = (long long)T.mm[(s * NFEAT + dim) * 2 + 1] - T.mm[(s * NFEAT + dim) * 2];
+    if (sp > bs) {
+      bs = sp;
+      best = dim;
+    }
+  }
+  int vbits = bits_for(bs), ibits = bits_for(T.N - 1);
+  if (ibits < 1) ibits = 1;
+  int32_t *S = T.sel + s * 8;
+  S[0] = best;
+  S[1] = T.mm[(s * NFEAT + best) * 2];
+  S[2] = vbits + ibits;
+  S[3] = ibits;
+  S[4] = m / 2;
+  S[5] = 0;
+  S[6] = 0;
+  S[7] = 0;
+  int node = (1 << d) - 1 + s;
+  T.split_dim[node] = best;
+}
+
+__device__ __forceinline__ unsigned long long kd_key(const KdBuild &T, const int32_t *S, int idx) {
+  int v = T.feat[(size_t)idx * FEAT_STRIDE + S[0]];
+  return ((unsigned long long)(unsigned)(v - S[1]) << S[3]) | (unsigned)idx;
+}
+
+constexpr int HIST_CHUNK = 4096;
+
+__global__ void __launch_bounds__(256) k_kd_hist(KdBuild *trees, int d) {
+  KdBuild &T = trees[blockIdx.y];
+  if (d >= T.top_levels) return;
+  int start = blockIdx.x * HIST_CHUNK;
+  if (start >= T.N) return;
+  int end = min(start + HIST_CHUNK, T.N);
+  int nseg = 1 << d;
+  const int32_t *off = T.seg_off + seg_base(d);
+  __shared__ uint32_t sh[NBINS];
+  __shared__ int sseg0, sseg1;
+  if (threadIdx.x == 0) {
+    sseg0 = find_seg(off, nseg, start);
+    sseg1 = find_seg(off, nseg, end - 1);
+  }
+  for (int i = threadIdx.x; i < NBINS; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  bool single = sseg0 == sseg1;
+  for (int p = start + threadIdx.x; p < end; p += blockDim.x) {
+    int s = single ? sseg0 : find_seg(off, nseg, p);
+    const int32_t *S = T.sel + s * 8;
+    int B = S[2], used = S[7];
+    if (used >= B) continue;
+    int hi = B - used, lo = max(hi - DIGIT, 0);
+    unsigned long long K = kd_key(T, S, T.perm[p]);
+    unsigned long long pre = ((unsigned long long)(unsigned)S[6] << 32) | (unsigned)S[5];
+    if (hi < 64 && (K >> hi) != pre) continue;
+    unsigned dig = (unsigned)((K >> lo) & ((1ull << (hi - lo)) - 1));
+    if (single) atomicAdd(&sh[dig], 1u);
+    else atomicAdd(&T.hist[(size_t)s * NBINS + dig], 1u);
+  }
+  __syncthreads();
+  if (single)
+    for (int i = threadIdx.x; i < NBINS; i += blockDim.x)
+      if (sh[i]) atomicAdd(&T.hist[(size_t)sseg0 * NBINS + i], sh[i]);
+}
+
+// One CTA per segment: find the bin holding rank k, narrow the prefix, clear.
+__global__ void __launch_bounds__(256) k_kd_digit(KdBuild *trees, int d) {
+  KdBuild &T = trees[blockIdx.y];
+  if (d >= T.top_levels) return;
+  int s = blockIdx.x;
+  if (s >= (1 << d)) return;
+  int32_t *S = T.sel + s * 8;
+  int B = S[2], used = S[7];
+  uint32_t *h = T.hist + (size_t)s * NBINS;
+  if (used >= B) return;
+  int hi = B - used, lo = max(hi - DIGIT, 0), nb = 1 << (hi - lo);
+  __shared__ uint32_t part[256];
+  __shared__ int found_bin, found_before;
+  // each thread sums a run of NBINS/256 = 8 consecutive bins
+  const int per = NBINS / 256;
+  uint32_t mine = 0;
+  for (int i = 0; i < per; i++) {
+    int b = threadIdx.x * per + i;
+    mine += (b < nb) ? h[b] : 0;
+  }
+  part[threadIdx.x] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t k = (uint32_t)S[4], acc = 0;
+    int t = 0;
+    while (t < 255 && acc + part[t] <= k) acc += part[t++];
+    int b = t * per;
+    while (b < NBINS - 1 && acc + h[b] <= k) acc += h[b++];
+    found_bin = b;
+    found_before = (int)acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NBINS; i += blockDim.x) h[i] = 0;
+  if (threadIdx.x == 0) {
+    unsigned long long pre = ((unsigned long long)(unsigned)S[6] << 32) | (unsigned)S[5];
+    pre = (pre << (hi - lo)) | (unsigned)found_bin;
+    S[5] = (int32_t)(pre & 0xffffffffu);
+    S[6] = (int32_t)(pre >> 32);
+    S[4] -= found_before;
+    S[7] = used + (hi - lo);
+  }
+}
+
+// Partition: key < selected key goes to the left child; positions from per-
+// segment counters (order inside a child is unspecified). The selected point
+// writes the split value.
+__global__ void __launch_bounds__(256) k_kd_partition(KdBuild *trees, int d) {
+  KdBuild &T = trees[blockIdx.y];
+  if (d >= T.top_levels) return;
+  int nseg = 1 << d;
+  const int32_t *off = T.seg_off + seg_base(d);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < T.N; p += gridDim.x * blockDim.x) {
+    int s = find_seg(off, nseg, p);
+    const int32_t *S = T.sel + s * 8;
+    int idx = T.perm[p];
+    unsigned long long K = kd_key(T, S, idx);
+    unsigned long long sel = ((unsigned long long)(unsigned)S[6] << 32) | (unsigned)S[5];
+    int b = off[s], m = off[s + 1] - b, half = m >> 1;
+    int dst;
+    if (K < sel) {
+      const int k = atomicAdd(&T.cnt[2 * s], 1);
+      dst = k < half ? b + k : -1;
+    } else {
+      const int k = atomicAdd(&T.cnt[2 * s + 1], 1);
+      dst = k < m - half ? b + half + k : -1;
+      if (K == sel) T.split_val[(1 << d) - 1 + s] = T.feat[(size_t)idx * FEAT_STRIDE + S[0]];
+    }
+    if (dst >= 0) T.perm_tmp[dst] = idx;
+    else raise_status(T.status, DEV_ERR_KD, s, d);
+  }
+}
+
+__global__ void k_kd_copy_back(KdBuild *trees, int d) {
+  KdBuild &T = trees[blockIdx.y];
+  if (d >= T.top_levels) return;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < T.N; p += gridDim.x * blockDim.x)
+    T.perm[p] = T.perm_tmp[p];
+}
+
+// One 1024-thread CTA finishes the subtree of one segment at depth top_levels.
+__global__ void __launch_bounds__(1024) k_kd_subtree(KdBuild *trees) {
+  KdBuild &T = trees[blockIdx.y];
+  int d0 = T.top_levels;
+  if (blockIdx.x >= (1u << d0)) return;
+  const int b0 = seg_begin(T.N, d0, blockIdx.x), e0 = seg_begin(T.N, d0, blockIdx.x + 1);
+  const int m0 = e0 - b0;
+  extern __shared__ int32_t ssub[];
+  int32_t *sidx = ssub, *skey = ssub + SUB_MAX;
+  int(*smin)[NFEAT] = (int(*)[NFEAT])(ssub + 2 * SUB_MAX);  // per node of the sub-level
+  int(*smax)[NFEAT] = smin + SUB_MAX / 2;
+  int *sdim = (int *)(smax + SUB_MAX / 2);
+  const int t = threadIdx.x, lane = t & 31;
+  const bool act = t < m0;
+  if (act) sidx[t] = T.perm[b0 + t];
+  int nb = 0, ne = m0, nid = 0;  // my position's node (local) at this sub-depth
+  const int levels = T.D - d0;
+  for (int sd = 0; sd < levels; sd++) {
+    const int nnodes = 1 << sd;
+    for (int i = t; i < nnodes * NFEAT; i += blockDim.x) {
+      smin[i / NFEAT][i % NFEAT] = INT32_MAX;
+      smax[i / NFEAT][i % NFEAT] = INT32_MIN;
+    }
+    __syncthreads();
+    // per-node min/max: reduce over lanes of the same node, leader updates smem
+    int idx = act ? sidx[t] : 0;
+    const int32_t *row = T.feat + (size_t)idx * FEAT_STRIDE;
+    unsigned grp = __match_any_sync(0xffffffffu, act ? nid : -1);
+    bool leader = (__ffs(grp) - 1) == lane;
+    for (int dim = 0; dim < NFEAT; dim++) {
+      int v = act ? row[dim] : 0;
+      int lo = __reduce_min_sync(grp, v), hi = __reduce_max_sync(grp, v);
+      if (act && leader) {
+        atomicMin(&smin[nid][dim], lo);
+        atomicMax(&smax[nid][dim], hi);
+      }
+    }
+    __syncthreads();
+    for (int i = t; i < nnodes; i += blockDim.x) {
+      int best = 0;
+      long long bs = -1;
+      for (int dim = 0; dim < NFEAT; dim++) {
+        long long sp = (long long)smax[i][dim] - smin[i][dim];
+        if (sp > bs) {
+          bs = sp;
+          best = dim;
+        }
+      }
+      sdim[i] = best;
+    }
+    __syncthreads();
+    int dim = act ? sdim[nid] : 0;
+    int v = act ? row[dim] : 0;
+    if (act) skey[t] = v;
+    __syncthreads();
+    int rank = 0;
+    if (act) {
+      for (int u = nb; u < ne; u++) {
+        int kv = skey[u], ki = sidx[u];
+        rank += (kv < v) || (kv == v && ki < idx);
+      }
+    }
+    __syncthreads();
+    if (act) {
+      sidx[nb + rank] = idx;
+      int half = (ne - nb) >> 1;
+      if (rank == half) {
+        int node = (1 << (d0 + sd)) - 1 + (blockIdx.x << sd) + nid;
+        T.split_dim[node] = dim;
+        T.split_val[node] = v;
+      }
+      // my position t belongs to which child
+      if (t < nb + half) {
+        ne = nb + half;
+        nid = 2 * nid;
+      } else {
+        nb = nb + half;
+        nid = 2 * nid + 1;
+      }
+    }
+    __syncthreads();
+  }
+  if (act) T.perm[b0 + t] = sidx[t];
+}
+
+static size_t subtree_smem() {
+  return sizeof(int32_t) * (2 * SUB_MAX + 2 * (SUB_MAX / 2) * NFEAT + SUB_MAX / 2);
+}
+
+ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaStream_t st) {
+  if (ntrees <= 0) return FF_OK;
+  FF_TRY(upload_desc(trees, dev, ntrees, st));
+  int maxT = 0, maxN = 0, maxD = 0;
+  for (int i = 0; i < ntrees; i++) {
+    maxT = max(maxT, trees[i].top_levels);
+    maxN = max(maxN, trees[i].N);
+    maxD = max(maxD, trees[i].D);
+  }
+  if (maxN <= 0) return FF_OK;
+  const int B = 256;
+  int gN = min((maxN + B - 1) / B, 4096);
+  k_kd_init_perm<<<dim3(gN, ntrees), B, 0, st>>>(dev);
+  FF_CHECK_LAUNCH();
+  k_kd_seg_off<<<dim3(8, ntrees), B, 0, st>>>(dev, ntrees);
+  FF_CHECK_LAUNCH();
+  for (int d = 0; d < maxT; d++) {
+    int nseg = 1 << d;
+    k_kd_mm_reset<<<dim3(min((nseg * NBINS + B - 1) / B, 1024), ntrees), B, 0, st>>>(dev, d);
+    FF_CHECK_LAUNCH();
+    k_kd_minmax<<<dim3((maxN + MM_CHUNK - 1) / MM_CHUNK, ntrees), 256, 0, st>>>(dev, d);
+    FF_CHECK_LAUNCH();
+    k_kd_sel_init<<<dim3((nseg + 127) / 128, ntrees), 128, 0, st>>>(dev, d);
+    FF_CHECK_LAUNCH();
+    for (int pass = 0; pass < MAX_PASSES; pass++) {
+      k_kd_hist<<<dim3((maxN + HIST_CHUNK - 1) / HIST_CHUNK, ntrees), 256, 0, st>>>(dev, d);
+      FF_CHECK_LAUNCH();
+      k_kd_digit<<<dim3(nseg, ntrees), 256, 0, st>>>(dev, d);
+      FF_CHECK_LAUNCH();
+    }
+    k_kd_partition<<<dim3(gN, ntrees), B, 0, st>>>(dev, d);
+    FF_CHECK_LAUNCH();
+    k_kd_copy_back<<<dim3(gN, ntrees), B, 0, st>>>(dev, d);
+    FF_CHECK_LAUNCH();
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_kd_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)subtree_smem());
+    attr = true;
+  }
+  if (maxD > 0 || maxT >= 0) {
+    k_kd_subtree<<<dim3(1 << maxT, ntrees), SUB_MAX, subtree_smem(), st>>>(dev);
+    FF_CHECK_LAUNCH();
+  }
+  return FF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 1 / Eq. 4: per coarsest grid point, descend the tree with the point's WHT
+// vector (left iff value < split value, no backtracking), then rerank the leaf's
+// pixels by E_d on P^n_r: smallest cost wins, ties to the lowest pixel index.
+// Then the K proposals in order, each replacing only with strictly lower cost.
+// One half warp per grid point; lane 0 descends, the 16 lanes share each E_d.
+template <int R>
+__global__ void __launch_bounds__(256) k_kd_query(const KdQuery *qs) {
+  const KdQuery &Q = qs[blockIdx.y];
+  const int NX = Q.src.NX, G = NX * Q.src.NY, n = Q.src.n, W = Q.src.W, H = Q.src.H;
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const int l16 = threadIdx.x & 15;
+  const unsigned gmask = 0xffffu << (threadIdx.x & 16);
+  if (g >= G) return;  // uniform per half warp
+  const int px = (g % NX) * n, py = (g / NX) * n;
+  int leaf = 0;
+  if (l16 == 0) {
+    const int32_t *q = Q.qfeat + (size_t)g * FEAT_STRIDE;
+    int node = 0;
+    for (int d = 0; d < Q.D; d++)
+      node = (q[Q.split_dim[node]] < Q.split_val[node]) ? 2 * node + 1 : 2 * node + 2;
+    leaf = node - ((1 << Q.D) - 1);
+  }
+  leaf = __shfl_sync(gmask, leaf, threadIdx.x & 16);
+  const int b = seg_begin(Q.N, Q.D, leaf), e = seg_begin(Q.N, Q.D, leaf + 1);
+  const uint32_t *sc = plane_centre(Q.src, px, py);
+  int best = COST_UNSET, bidx = 0x7fffffff;
+  for (int c = b; c < e; c++) {
+    const int idx = Q.perm[c];
+    const int x2 = idx % W, y2 = idx / W;
+    const int cost = group_cost<R>(sc, Q.src.pitch, plane_centre(Q.tgt, x2, y2), Q.tgt.pitch, l16,
+                                   gmask);
+    if (cost < best || (cost == best && idx < bidx)) {
+      best = cost;
+      bidx = idx;
+    }
+  }
+  int fx = bidx % W - px, fy = bidx / W - py;
+  for (int k = 0; k < Q.K; k++) {
+    const uint32_t pr = Q.proposals[(size_t)g * Q.K + k];
+    const int tx = clampi(px + flow_dx(pr), 0, W - 1), ty = clampi(py + flow_dy(pr), 0, H - 1);
+    const int cost = group_cost<R>(sc, Q.src.pitch, plane_centre(Q.tgt, tx, ty), Q.tgt.pitch, l16,
+                                   gmask);
+    if (cost < best) {
+      best = cost;
+      fx = tx - px;
+      fy = ty - py;
+    }
+  }
+  if (l16 == 0) {
+    Q.flow[g] = pack_flow(fx, fy);
+    Q.cost[g] = best;
+  }
+}
+
+ff_status launch_kd_query(const KdQuery *q, KdQuery *dev, int nq, cudaStream_t st) {
+  if (nq <= 0) return FF_OK;
+  FF_TRY(upload_desc(q, dev, nq, st));
+  int r = q[0].r, maxG = 0;
+  for (int i = 0; i < nq; i++) {
+    if (q[i].r != r) return FF_ERR_INVALID_ARG;
+    maxG = max(maxG, q[i].src.NX * q[i].src.NY);
+  }
+  dim3 grid((maxG * 16 + 255) / 256, nq);
+  FF_DISPATCH_R(r, k_kd_query<RR><<<grid, 256, 0, st>>>(dev));
+  FF_CHECK_LAUNCH();
+  return FF_OK;
+}
+
+}  // namespace ff

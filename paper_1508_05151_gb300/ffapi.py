@@ -1,0 +1,301 @@
+"""Thin Python binding of the C ABI in include/flowfields.h.
+
+Functions carry the ABI's names. They take and return torch CUDA tensors, which
+serve only as device memory; every step runs in the library's CUDA kernels on
+torch's current stream. There is no CPU path: if the library is missing or no
+GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import torch
+
+from . import _build
+
+FF_OK = 0
+COST_UNSET = 2**31 - 1
+_STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported image shape",
+           3: "workspace missing, misaligned or too small", 4: "CUDA error",
+           5: "device-side check failed"}
+
+
+class FFError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn} failed: {_STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+class Params(C.Structure):
+    """ff_params; defaults are the Sintel preset of Sec. 4."""
+    _fields_ = [(n, C.c_int32) for n in
+                ("k", "r", "r2", "leaf", "R", "eps", "e", "s", "tile", "n_rs", "K")] + \
+               [("seed", C.c_uint64)]
+
+    def __init__(self, **kw):
+        d = dict(k=3, r=8, r2=6, leaf=8, R=1, eps=5, e=4, s=50, tile=32, n_rs=3, K=0, seed=0)
+        unknown = set(kw) - set(d)
+        if unknown:
+            raise TypeError(f"unknown parameters {sorted(unknown)}")
+        d.update(kw)
+        super().__init__(**d)
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_lib = None
+
+
+def header_functions():
+    """Names of the entry points declared in include/flowfields.h."""
+    with open(os.path.join(_build.INCLUDE, "flowfields.h")) as f:
+        txt = f.read()
+    return sorted(set(re.findall(r"^\s*(?:ff_status|const char \*)\s*(ff_\w+)\s*\(", txt, re.M)))
+
+
+def lib():
+    """Load libflowfields.so (building it first when sources changed)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        vp, sz, i32, u64 = C.c_void_p, C.c_size_t, C.c_int, C.c_uint64
+        P = C.POINTER(Params)
+        sig = {
+            "ff_status_str": ([i32], C.c_char_p),
+            "ff_params_preset": ([P, i32], i32),
+            "ff_workspace_size": ([i32, i32, P, C.POINTER(sz)], i32),
+            "ff_smooth_workspace_size": ([i32, i32, i32, C.POINTER(sz)], i32),
+            "ff_smooth": ([vp, i32, i32, i32, vp, vp, sz, vp], i32),
+            "ff_census": ([vp, i32, i32, i32, vp, vp], i32),
+            "ff_features": ([vp, i32, i32, i32, vp, i32, vp, vp], i32),
+            "ff_kdtree_size": ([i32, i32, C.POINTER(C.c_int), C.POINTER(sz)], i32),
+            "ff_kdtree_build": ([vp, i32, i32, vp, vp, vp, vp, sz, vp], i32),
+            "ff_kdtree_init": ([vp, vp, vp, i32, vp, vp, vp, i32, i32, i32, i32, vp, i32, vp, vp,
+                                vp, sz, vp], i32),
+            "ff_level_workspace_size": ([i32, i32, i32, C.POINTER(sz)], i32),
+            "ff_search_level": ([vp, vp, i32, i32, i32, i32, vp, P, i32, vp, vp, vp, sz, vp], i32),
+            "ff_filter_workspace_size": ([i32, i32, C.POINTER(sz)], i32),
+            "ff_consistency_filter": ([vp, vp, vp, i32, i32, P, vp, vp, vp, vp, vp, vp, sz, vp],
+                                      i32),
+            "ff_flow_fields": ([vp, vp, i32, i32, P, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], i32),
+            "ff_device_status": ([vp, C.POINTER(C.c_uint32), C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_int32), vp], i32),
+            "ff_profile_enable": ([i32], i32),
+            "ff_profile_reset": ([], i32),
+            "ff_profile_read": ([C.POINTER(u64), C.POINTER(C.c_double), C.POINTER(u64)], i32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(fn, code):
+    if code != FF_OK:
+        raise FFError(fn, code)
+
+
+def _dev(t):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _opt(t):
+    return C.c_void_p(None) if t is None else _dev(t)
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ws(nbytes, device):
+    # torch's allocator returns 512-byte aligned blocks; +256 guards the rounding
+    return torch.empty(max(int(nbytes), 1) + 256, dtype=torch.uint8, device=device)
+
+
+def _ws_ptr(ws):
+    p = ws.data_ptr()
+    return C.c_void_p((p + 255) & ~255), ws.numel() - (((p + 255) & ~255) - p)
+
+
+def _size(fn, *args):
+    out = C.c_size_t()
+    _check(fn, getattr(lib(), fn)(*args, C.byref(out)))
+    return out.value
+
+
+def _params(p):
+    if p is None:
+        return Params()
+    if isinstance(p, dict):
+        return Params(**p)
+    return p
+
+
+# ------------------------------------------------------------------ steps ----
+def ff_smooth(img, n):
+    H, W = img.shape[:2]
+    out = torch.empty_like(img)
+    ws = _ws(_size("ff_smooth_workspace_size", W, H, n), img.device)
+    wp, wn = _ws_ptr(ws)
+    _check("ff_smooth", lib().ff_smooth(_dev(img), W, H, n, _dev(out), wp, wn, _stream()))
+    return out
+
+
+def ff_census(img_n, n):
+    H, W = img_n.shape[:2]
+    out = torch.empty((H, W), dtype=torch.int32, device=img_n.device)
+    _check("ff_census", lib().ff_census(_dev(img_n), W, H, n, _dev(out), _stream()))
+    return out
+
+
+def ff_features(img, r, pts=None):
+    H, W = img.shape[:2]
+    npts = H * W if pts is None else int(pts.shape[0])
+    out = torch.empty((max(npts, 1), 28), dtype=torch.int32, device=img.device)
+    _check("ff_features", lib().ff_features(_dev(img), W, H, r, _opt(pts), npts, _dev(out),
+                                            _stream()))
+    return out[:npts]
+
+
+def ff_kdtree_build(feat, leaf):
+    N = int(feat.shape[0])
+    D = C.c_int()
+    nbytes = C.c_size_t()
+    _check("ff_kdtree_size", lib().ff_kdtree_size(N, leaf, C.byref(D), C.byref(nbytes)))
+    dev = feat.device
+    perm = torch.empty(N, dtype=torch.int32, device=dev)
+    nn = max((1 << D.value) - 1, 1)
+    sd = torch.zeros(nn, dtype=torch.int32, device=dev)
+    sv = torch.zeros(nn, dtype=torch.int32, device=dev)
+    ws = _ws(nbytes.value, dev)
+    wp, wn = _ws_ptr(ws)
+    _check("ff_kdtree_build", lib().ff_kdtree_build(_dev(feat), N, leaf, _dev(perm), _dev(sd),
+                                                    _dev(sv), wp, wn, _stream()))
+    return dict(perm=perm, split_dim=sd[:(1 << D.value) - 1], split_val=sv[:(1 << D.value) - 1],
+                D=D.value, N=N, _keep=(sd, sv))
+
+
+def _grid(W, H, n):
+    return (W + n - 1) // n, (H + n - 1) // n
+
+
+def ff_kdtree_init(tree, leaf, src_img, census_src, census_tgt, n, r, proposals=None):
+    H, W = src_img.shape[:2]
+    Gx, Gy = _grid(W, H, n)
+    dev = src_img.device
+    flow = torch.empty((Gy, Gx, 2), dtype=torch.int16, device=dev)
+    cost = torch.empty((Gy, Gx), dtype=torch.int32, device=dev)
+    ws = _ws(_size("ff_level_workspace_size", W, H, n), dev)
+    wp, wn = _ws_ptr(ws)
+    K = 0 if proposals is None else int(proposals.shape[2])
+    sd, sv = tree["_keep"]
+    _check("ff_kdtree_init", lib().ff_kdtree_init(
+        _dev(tree["perm"]), _dev(sd), _dev(sv), leaf, _dev(src_img), _dev(census_src),
+        _dev(census_tgt), W, H, n, r, _opt(proposals), K, _dev(flow), _dev(cost), wp, wn,
+        _stream()))
+    return flow, cost
+
+
+def ff_search_level(census_src, census_tgt, n, r, params=None, flow_id=0, flow_coarse=None,
+                    flow=None, cost=None):
+    """One level. With flow_coarse: seeded from it; else (flow, cost) is the initial
+    state and is updated in place. Returns (flow, cost)."""
+    H, W = census_src.shape
+    Gx, Gy = _grid(W, H, n)
+    dev = census_src.device
+    if flow_coarse is not None:
+        flow = torch.empty((Gy, Gx, 2), dtype=torch.int16, device=dev)
+        cost = torch.empty((Gy, Gx), dtype=torch.int32, device=dev)
+    P = _params(params)
+    ws = _ws(_size("ff_level_workspace_size", W, H, n), dev)
+    wp, wn = _ws_ptr(ws)
+    _check("ff_search_level", lib().ff_search_level(
+        _dev(census_src), _dev(census_tgt), W, H, n, r, _opt(flow_coarse), C.byref(P), flow_id,
+        _dev(flow), _dev(cost), wp, wn, _stream()))
+    return flow, cost
+
+
+def ff_consistency_filter(F, Fb1, Fb2, params=None):
+    H, W = F.shape[:2]
+    dev = F.device
+    P = _params(params)
+    valid = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    err = torch.empty((H, W), dtype=torch.int32, device=dev)
+    nb = ((W + 2) // 3) * ((H + 2) // 3)
+    sparse = torch.empty((nb, 4), dtype=torch.int32, device=dev)
+    ns = torch.zeros(1, dtype=torch.int32, device=dev)
+    mask = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    ws = _ws(_size("ff_filter_workspace_size", W, H), dev)
+    wp, wn = _ws_ptr(ws)
+    _check("ff_consistency_filter", lib().ff_consistency_filter(
+        _dev(F), _dev(Fb1), _dev(Fb2), W, H, C.byref(P), _dev(valid), _dev(err), _dev(sparse),
+        _dev(ns), _dev(mask), wp, wn, _stream()))
+    return dict(valid=valid, err_sum=err, sparse=sparse, n_sparse=ns, mask=mask)
+
+
+class FlowFields:
+    """The whole path for W x H pairs with one reusable workspace.
+
+    ``run(I1, I2)`` takes uint8 (H, W, 3) CUDA tensors and returns device tensors:
+    flows int16 (3, H, W, 2) (forward, backward r, backward r2), valid, err_sum,
+    sparse int32 (rows, 4) with the row count in n_sparse, mask.
+    """
+
+    def __init__(self, W, H, params=None, device="cuda"):
+        self.W, self.H = W, H
+        self.params = _params(params)
+        self.device = torch.device(device)
+        self.ws_bytes = _size("ff_workspace_size", W, H, C.byref(self.params))
+        self.ws = _ws(self.ws_bytes, self.device)
+        nb = ((W + 2) // 3) * ((H + 2) // 3)
+        d = self.device
+        self.flows = torch.empty((3, H, W, 2), dtype=torch.int16, device=d)
+        self.valid = torch.empty((H, W), dtype=torch.uint8, device=d)
+        self.err_sum = torch.empty((H, W), dtype=torch.int32, device=d)
+        self.sparse = torch.empty((nb, 4), dtype=torch.int32, device=d)
+        self.n_sparse = torch.zeros(1, dtype=torch.int32, device=d)
+        self.mask = torch.empty((H, W), dtype=torch.uint8, device=d)
+
+    def run(self, I1, I2, proposals=None):
+        wp, wn = _ws_ptr(self.ws)
+        _check("ff_flow_fields", lib().ff_flow_fields(
+            _dev(I1), _dev(I2), self.W, self.H, C.byref(self.params), _opt(proposals),
+            _dev(self.flows), _dev(self.valid), _dev(self.err_sum), _dev(self.sparse),
+            _dev(self.n_sparse), _dev(self.mask), wp, wn, _stream()))
+        return dict(flows=self.flows, valid=self.valid, err_sum=self.err_sum,
+                    sparse=self.sparse, n_sparse=self.n_sparse, mask=self.mask)
+
+    def device_status(self):
+        wp, _ = _ws_ptr(self.ws)
+        code, x, y = C.c_uint32(), C.c_int32(), C.c_int32()
+        lib().ff_device_status(wp, C.byref(code), C.byref(x), C.byref(y), _stream())
+        return code.value, x.value, y.value
+
+
+def ff_flow_fields(I1, I2, params=None, proposals=None):
+    H, W = I1.shape[:2]
+    return FlowFields(W, H, params, I1.device).run(I1, I2, proposals)
+
+
+def profile_enable(on=True):
+    _check("ff_profile_enable", lib().ff_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check("ff_profile_reset", lib().ff_profile_reset())
+
+
+def profile_read():
+    n, ms, pn = C.c_uint64(), C.c_double(), C.c_uint64()
+    _check("ff_profile_read", lib().ff_profile_read(C.byref(n), C.byref(ms), C.byref(pn)))
+    return dict(launches=n.value, prop_ms=ms.value, prop_launches=pn.value)

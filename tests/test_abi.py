@@ -1,0 +1,113 @@
+"""The C-ABI library builds, loads and exports every declared entry point; host-side
+argument checks and workspace planning behave as documented. No GPU needed."""
+import ctypes as C
+import re
+import subprocess
+
+import pytest
+
+from paper_1508_05151_gb300 import ffapi, _build
+
+
+@pytest.fixture(scope="module")
+def L():
+    return ffapi.lib()
+
+
+def test_header_declares_the_boundary():
+    names = ffapi.header_functions()
+    for must in ("ff_features", "ff_kdtree_build", "ff_kdtree_init", "ff_search_level",
+                 "ff_consistency_filter", "ff_flow_fields", "ff_smooth", "ff_census"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(ff_\w+)", out))
+    missing = set(ffapi.header_functions()) - exported
+    assert not missing, f"declared but not exported: {sorted(missing)}"
+    for n in ffapi.header_functions():
+        assert hasattr(L, n)
+
+
+def test_library_is_built_for_sm_103a():
+    out = subprocess.run(["/usr/local/cuda/bin/cuobjdump", "--list-elf", _build.LIB],
+                         capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_presets(L):
+    p = ffapi.Params()
+    assert L.ff_params_preset(C.byref(p), 0) == 0
+    assert (p.k, p.r, p.r2, p.leaf, p.R, p.eps, p.e, p.s) == (3, 8, 6, 8, 1, 5, 4, 50)
+    assert L.ff_params_preset(C.byref(p), 1) == 0 and (p.eps, p.e, p.s) == (1, 7, 50)
+    assert L.ff_params_preset(C.byref(p), 2) == 0 and (p.eps, p.e, p.s) == (1, 9, 150)
+    assert L.ff_params_preset(C.byref(p), 7) == 1
+    assert L.ff_params_preset(None, 0) == 1
+    assert L.ff_status_str(3) == b"workspace missing, misaligned or too small"
+
+
+def test_parameter_and_shape_checks(L):
+    sz = C.c_size_t()
+    ok = ffapi.Params()
+    assert L.ff_workspace_size(1024, 436, C.byref(ok), C.byref(sz)) == 0
+    assert sz.value > 0
+    for bad in [dict(k=5), dict(r=9), dict(r2=0), dict(leaf=1), dict(tile=31), dict(tile=64),
+                dict(n_rs=4), dict(K=9), dict(eps=0), dict(e=10), dict(R=-1)]:
+        p = ffapi.Params(**bad)
+        assert L.ff_workspace_size(64, 64, C.byref(p), C.byref(sz)) == 1, bad
+    for W, H in [(0, 5), (5, 0), (20000, 10), (5000, 5000)]:
+        assert L.ff_workspace_size(W, H, C.byref(ok), C.byref(sz)) == 2
+    assert L.ff_workspace_size(64, 64, None, C.byref(sz)) == 1
+
+
+def test_workspace_grows_with_size_and_levels(L):
+    a, b, c = C.c_size_t(), C.c_size_t(), C.c_size_t()
+    p = ffapi.Params()
+    L.ff_workspace_size(128, 96, C.byref(p), C.byref(a))
+    L.ff_workspace_size(1024, 436, C.byref(p), C.byref(b))
+    p0 = ffapi.Params(k=0)
+    L.ff_workspace_size(1024, 436, C.byref(p0), C.byref(c))
+    assert a.value < b.value
+    # 3 feature tables of 112 B per pixel dominate; the basic approach (k = 0)
+    # also queries every pixel, so it needs 3 more tables
+    assert b.value > 3 * 112 * 1024 * 436
+    assert c.value > b.value
+
+
+def test_calls_reject_null_and_unaligned_workspace_before_any_launch(L):
+    p = ffapi.Params()
+    fake = C.c_void_p(0x1000)
+    # null inputs
+    assert L.ff_flow_fields(None, fake, 64, 64, C.byref(p), None, fake, fake, fake, fake, fake,
+                            fake, fake, 1 << 30, None) == 1
+    # misaligned workspace
+    assert L.ff_flow_fields(fake, fake, 64, 64, C.byref(p), None, fake, fake, fake, fake, fake,
+                            fake, C.c_void_p(0x1001), 1 << 30, None) == 3
+    # too small workspace
+    assert L.ff_flow_fields(fake, fake, 64, 64, C.byref(p), None, fake, fake, fake, fake, fake,
+                            fake, C.c_void_p(0x100000), 16, None) == 3
+    # proposals required when K > 0
+    pk = ffapi.Params(K=2)
+    assert L.ff_flow_fields(fake, fake, 64, 64, C.byref(pk), None, fake, fake, fake, fake, fake,
+                            fake, C.c_void_p(0x100000), 1 << 40, None) == 1
+    # smooth: n must be a power of two
+    assert L.ff_smooth(fake, 64, 64, 3, fake, fake, 1 << 20, None) == 1
+    assert L.ff_census(fake, 64, 64, 0, fake, None) == 1
+    # kd: leaf range
+    d = C.c_int()
+    assert L.ff_kdtree_size(100, 1, C.byref(d), None) == 1
+    assert L.ff_kdtree_size(1024 * 436, 8, C.byref(d), None) == 0 and d.value == 16
+
+
+def test_kd_depth_matches_definition(L):
+    d = C.c_int()
+    for N, leaf in [(1, 2), (2, 2), (3, 2), (9, 8), (12288, 8), (446464, 8), (465750, 8),
+                    (1000, 31)]:
+        assert L.ff_kdtree_size(N, leaf, C.byref(d), None) == 0
+        D = d.value
+        assert -(-N // (1 << D)) <= leaf
+        assert D == 0 or -(-N // (1 << (D - 1))) > leaf

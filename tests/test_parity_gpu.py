@@ -1,0 +1,250 @@
+"""GPU parity: every step of the CUDA path, called through the C ABI, against the
+CPU oracle on the same seeded inputs. Everything on this path is integer, so the
+bar is bit-exact equality (the kd tree: equal leaf sets, split dimensions and split
+values; the order inside a leaf is unspecified by the ABI)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1508_05151_gb300 import ffapi, synth
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+DEV = torch.device("cuda:0")
+SIZES = [(1, 1), (5, 3), (17, 13), (33, 31), (128, 96), (300, 170)]
+
+
+def rimg(seed, H, W, flat=False):
+    rng = np.random.default_rng(seed)
+    img = rng.integers(0, 256, size=(H, W, 3), dtype=np.uint8)
+    if flat and H > 4 and W > 4:
+        img[H // 4:H // 2, W // 4:W // 2] = 90  # ties
+    return img
+
+
+def tg(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def cpu(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def gpu_census(img, n):
+    sm = ffapi.ff_smooth(tg(img), n)
+    return ffapi.ff_census(sm, n), sm
+
+
+# ------------------------------------------------------------------ A1/A2 -----
+@pytest.mark.parametrize("W,H", SIZES + [(1024, 436)])
+def test_smooth_and_census(W, H):
+    img = rimg(W * 7 + H, H, W)
+    for n in (1, 2, 4, 8):
+        C, sm = gpu_census(img, n)
+        ref_sm = O.smooth(img, n)
+        assert np.array_equal(cpu(sm), ref_sm), (W, H, n)
+        assert np.array_equal(cpu(C).view(np.uint32), O.census(ref_sm, n)), (W, H, n)
+
+
+# --------------------------------------------------------------------- A3 -----
+@pytest.mark.parametrize("W,H", SIZES + [(1024, 436)])
+def test_features_all_pixels(W, H):
+    img = rimg(W + 3 * H, H, W)
+    for r in ((8, 6, 2) if W * H < 100000 else (8,)):
+        f = cpu(ffapi.ff_features(tg(img), r))
+        ref = O.wht_features(img, r)
+        assert np.array_equal(f[:, :27], ref), (W, H, r)
+        assert (f[:, 27] == 0).all()
+
+
+def test_features_point_list():
+    img = rimg(5, 90, 110)
+    pts = np.array([[0, 0], [109, 89], [50, 3], [7, 88], [64, 40]], np.int32)
+    for r in (8, 6, 1):
+        f = cpu(ffapi.ff_features(tg(img), r, tg(pts)))
+        assert np.array_equal(f[:, :27], O.wht_features(img, r, pts))
+
+
+# --------------------------------------------------------------------- A4 -----
+def _leafsets(perm, N, D):
+    out = []
+    for lf in range(1 << D):
+        b, e = O.kd_leaf_range(N, D, lf)
+        out.append(np.sort(perm[b:e]))
+    return out
+
+
+@pytest.mark.parametrize("W,H,r,leaf,flat", [(17, 13, 2, 2, False), (33, 31, 3, 8, True),
+                                             (128, 96, 8, 8, False), (128, 96, 8, 8, True),
+                                             (301, 203, 6, 5, True), (1024, 436, 8, 8, False)])
+def test_kdtree_build(W, H, r, leaf, flat):
+    img = rimg(W * H, H, W, flat)
+    feat_g = ffapi.ff_features(tg(img), r)
+    feat = cpu(feat_g)[:, :27]
+    T = ffapi.ff_kdtree_build(feat_g, leaf)
+    ref = O.kd_build(feat, leaf)
+    assert T["D"] == ref["D"]
+    assert np.array_equal(cpu(T["split_dim"]), ref["split_dim"])
+    assert np.array_equal(cpu(T["split_val"]), ref["split_val"])
+    g, o = _leafsets(cpu(T["perm"]), ref["N"], ref["D"]), _leafsets(ref["perm"], ref["N"], ref["D"])
+    for a, b in zip(g, o):
+        assert np.array_equal(a, b)
+
+
+# --------------------------------------------------------------------- A5 -----
+@pytest.mark.parametrize("W,H,n,r,leaf,K", [(40, 30, 1, 3, 4, 0), (128, 96, 8, 8, 8, 0),
+                                           (128, 96, 8, 8, 8, 3), (130, 97, 4, 6, 8, 2),
+                                           (300, 170, 8, 8, 8, 4)])
+def test_kdtree_init(W, H, n, r, leaf, K):
+    p = synth.pair_shift(W + H, W=W, H=H, max_shift=(8, 8), square=min(16, W, H), square_move=6)
+    I1, I2 = p["I1"], p["I2"]
+    C1g, _ = gpu_census(I1, n)
+    C2g, _ = gpu_census(I2, n)
+    feat_g = ffapi.ff_features(tg(I2), r)
+    T = ffapi.ff_kdtree_build(feat_g, leaf)
+    Gx, Gy = O.grid(W, H, n)
+    prop = None
+    if K:
+        prop = np.random.default_rng(1).integers(-40, 41, size=(Gy, Gx, K, 2)).astype(np.int16)
+    f, c = ffapi.ff_kdtree_init(T, leaf, tg(I1), C1g, C2g, n, r,
+                                None if prop is None else tg(prop))
+    C1 = O.census(O.smooth(I1, n), n)
+    C2 = O.census(O.smooth(I2, n), n)
+    fr, cr, _ = O.kd_init(cpu(feat_g)[:, :27], I1, r, leaf, C1, C2, n,
+                          None if prop is None else prop.astype(np.int32))
+    assert np.array_equal(cpu(c), cr)
+    assert np.array_equal(cpu(f).astype(np.int32), fr)
+
+
+# ---------------------------------------------------------------- A7 / A8 -----
+@pytest.mark.parametrize("W,H,n,r,tile,n_rs", [(64, 48, 1, 3, 8, 3), (128, 96, 1, 8, 32, 3),
+                                               (128, 96, 2, 8, 32, 3), (128, 96, 4, 6, 32, 2),
+                                               (97, 71, 2, 4, 6, 3), (200, 150, 1, 6, 16, 1),
+                                               (33, 31, 8, 8, 2, 3), (300, 170, 2, 8, 32, 0)])
+def test_search_level_seeded(W, H, n, r, tile, n_rs):
+    p = synth.pair_shift(W * 3 + H, W=W, H=H, max_shift=(10, 10), square=min(24, W, H),
+                         square_move=9)
+    I1, I2 = p["I1"], p["I2"]
+    C1g, _ = gpu_census(I1, n)
+    C2g, _ = gpu_census(I2, n)
+    C1, C2 = cpu(C1g).view(np.uint32), cpu(C2g).view(np.uint32)
+    Gxc, Gyc = O.grid(W, H, 2 * n)
+    rng = np.random.default_rng(n * 100 + r)
+    coarse = rng.integers(-12, 13, size=(Gyc, Gxc, 2))
+    ys, xs = np.mgrid[0:Gyc, 0:Gxc] * (2 * n)
+    coarse[..., 0] = np.clip(xs + coarse[..., 0], 0, W - 1) - xs
+    coarse[..., 1] = np.clip(ys + coarse[..., 1], 0, H - 1) - ys
+    P = dict(tile=tile, n_rs=n_rs, seed=12345, R=1)
+    for fid in (0, 2):
+        f, c = ffapi.ff_search_level(C1g, C2g, n, r, P, flow_id=fid,
+                                     flow_coarse=tg(coarse.astype(np.int16)))
+        fr, cr, _ = O.search_level(C1, C2, n, r, flow_coarse=coarse.astype(np.int32), tile=tile,
+                                   n_rs=n_rs, R=1, seed=12345, flow_id=fid)
+        assert np.array_equal(cpu(c), cr)
+        assert np.array_equal(cpu(f).astype(np.int32), fr)
+
+
+@pytest.mark.parametrize("W,H,n,r,tile", [(128, 96, 8, 8, 32), (80, 60, 1, 3, 10)])
+def test_search_level_from_state(W, H, n, r, tile):
+    # top-level form: the state (including unset points) is the input
+    p = synth.pair_shift(7, W=W, H=H, max_shift=(6, 6), square=16, square_move=5)
+    C1g, _ = gpu_census(p["I1"], n)
+    C2g, _ = gpu_census(p["I2"], n)
+    C1, C2 = cpu(C1g).view(np.uint32), cpu(C2g).view(np.uint32)
+    Gx, Gy = O.grid(W, H, n)
+    rng = np.random.default_rng(3)
+    flow = np.zeros((Gy, Gx, 2), np.int32)
+    cost = np.full((Gy, Gx), O.COST_UNSET, np.int32)
+    for _ in range(max(2, Gx * Gy // 20)):
+        gx, gy = rng.integers(0, Gx), rng.integers(0, Gy)
+        x, y = gx * n, gy * n
+        tx, ty = np.clip(x + rng.integers(-9, 10), 0, W - 1), np.clip(y + rng.integers(-9, 10), 0, H - 1)
+        flow[gy, gx] = (tx - x, ty - y)
+        cost[gy, gx] = O.patch_cost(C1, C2, n, r, (x, y), (tx, ty))
+    fg, cg = tg(flow.astype(np.int16)), tg(cost)
+    ffapi.ff_search_level(C1g, C2g, n, r, dict(tile=tile), flow_id=1, flow=fg, cost=cg)
+    fr, cr, _ = O.search_level(C1, C2, n, r, flow=flow, cost=cost, tile=tile, flow_id=1)
+    assert np.array_equal(cpu(cg), cr)
+    assert np.array_equal(cpu(fg).astype(np.int32), fr)
+
+
+# ------------------------------------------------------------ A11 - A13 -------
+@pytest.mark.parametrize("seed", [1, 2])
+def test_consistency_filter(seed):
+    p = synth.pair_for_config(1, seed)
+    ref = O.flow_fields(p["I1"], p["I2"])
+    flows = ref["flows"].copy()
+    rng = np.random.default_rng(seed)
+    # perturb: random outliers and small shifts so every branch is exercised
+    m = rng.random(flows.shape[1:3]) < 0.05
+    flows[0][m] += rng.integers(-6, 7, size=(int(m.sum()), 2)).astype(np.int32)
+    H, W = flows.shape[1:3]
+    ys, xs = np.mgrid[0:H, 0:W]
+    flows[0][..., 0] = np.clip(xs + flows[0][..., 0], 0, W - 1) - xs
+    flows[0][..., 1] = np.clip(ys + flows[0][..., 1], 0, H - 1) - ys
+    for params in (dict(eps=5, e=4, s=50), dict(eps=1, e=7, s=50), dict(eps=2, e=1, s=500)):
+        g = ffapi.ff_consistency_filter(*(tg(flows[j].astype(np.int16)) for j in range(3)), params)
+        vcc, err = O.consistency(flows[0], flows[1], flows[2], params["eps"])
+        val = O.region_filter(flows[0], vcc, params["s"])
+        sp, mask = O.sparsify(val, err, flows[0], params["e"])
+        assert np.array_equal(cpu(g["err_sum"]), err)
+        assert np.array_equal(cpu(g["valid"]), val)
+        assert np.array_equal(cpu(g["mask"]), mask)
+        n = int(cpu(g["n_sparse"])[0])
+        assert n == len(sp)
+        assert np.array_equal(cpu(g["sparse"])[:n], sp)
+
+
+# ----------------------------------------------------------- whole path -------
+def _compare(out, ref):
+    assert np.array_equal(cpu(out["flows"]).astype(np.int32), ref["flows"])
+    assert np.array_equal(cpu(out["valid"]), ref["valid"])
+    assert np.array_equal(cpu(out["err_sum"]), ref["err_sum"])
+    assert np.array_equal(cpu(out["mask"]), ref["mask"])
+    n = int(cpu(out["n_sparse"])[0])
+    assert n == len(ref["sparse"])
+    assert np.array_equal(cpu(out["sparse"])[:n], ref["sparse"])
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_flow_fields_128x96(seed):
+    p = synth.pair_for_config(1, seed)
+    params = dict(seed=seed)
+    out = ffapi.ff_flow_fields(tg(p["I1"]), tg(p["I2"]), params)
+    _compare(out, O.flow_fields(p["I1"], p["I2"], params=params))
+
+
+@pytest.mark.parametrize("W,H,params", [(1, 1, dict(k=3)), (5, 3, dict(k=1, r=2, r2=1)),
+                                        (37, 29, dict(k=2, r=4, r2=3, tile=6)),
+                                        (64, 48, dict(k=0, r=5, r2=5, leaf=3)),
+                                        (150, 100, dict(k=4, tile=8, n_rs=1, R=2, leaf=12))])
+def test_flow_fields_edge_shapes(W, H, params):
+    p = synth.pair_shift(W + 11 * H, W=W, H=H, max_shift=(4, 4), square=min(8, W, H),
+                         square_move=3)
+    out = ffapi.ff_flow_fields(tg(p["I1"]), tg(p["I2"]), params)
+    _compare(out, O.flow_fields(p["I1"], p["I2"], params=params))
+
+
+def test_flow_fields_1024x436_full_size():
+    # the benchmark workload, whole-field bit-exact comparison
+    p = synth.pair_for_config(2, 1)
+    out = ffapi.ff_flow_fields(tg(p["I1"]), tg(p["I2"]))
+    _compare(out, O.flow_fields(p["I1"], p["I2"], threads=3))
+
+
+def test_flow_fields_is_deterministic_and_stream_independent():
+    p = synth.pair_for_config(1, 9)
+    ff = ffapi.FlowFields(128, 96)
+    a = {k: v.clone() for k, v in ff.run(tg(p["I1"]), tg(p["I2"])).items()}
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b = ff.run(tg(p["I1"]), tg(p["I2"]))
+    s.synchronize()
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+    assert ff.device_status() == (0, 0, 0)
