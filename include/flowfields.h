@@ -176,6 +176,31 @@ ff_status ff_consistency_filter(const int16_t *F, const int16_t *Fb1, const int1
                                 int32_t *sparse, int32_t *n_sparse, uint8_t *mask, void *ws,
                                 size_t ws_bytes, void *stream);
 
+/* Allocation-free variant of ff_consistency_filter (the paper has no
+ * counterpart; this exists for callers that cannot allocate device memory).
+ * Some callers cannot provide a workspace: a plugin running inside a framework
+ * that owns the whole device memory pool and exposes no allocator, or a
+ * real-time frame loop that reserves all memory at start-up and must not call
+ * cudaMalloc afterwards (it can synchronise the device and stall the loop).
+ * This call needs no workspace: its scratch is one static device array of
+ * 12 MiB inside the library, which every GPU that loads the library keeps until
+ * the process exits. Limits and behaviour:
+ *   - W * H <= 1,048,576 pixels; larger images return FF_ERR_SHAPE and enqueue
+ *     nothing. Inputs, outputs and results are exactly those of
+ *     ff_consistency_filter.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array and the array keeps the last call's
+ *     contents (the call clears what must start at zero itself): calls whose
+ *     work overlaps on the GPU (different streams, or several host threads)
+ *     race and corrupt each other's results. Serialise them, e.g. on one stream. */
+ff_status ff_consistency_filter_static(const int16_t *F, const int16_t *Fb1, const int16_t *Fb2,
+                                       int W, int H, const ff_params *p, uint8_t *valid,
+                                       int32_t *err_sum, int32_t *sparse, int32_t *n_sparse,
+                                       uint8_t *mask, void *stream);
+
 /* The whole path for one pair (Fig. 2): smoothed images and census for both
  * frames at every level, three flow fields (forward I1->I2 with r, backward
  * I2->I1 with r and with r2; flow ids 0, 1, 2), each from its own kd tree, then

@@ -81,6 +81,8 @@ def lib():
             "ff_filter_workspace_size": ([i32, i32, C.POINTER(sz)], i32),
             "ff_consistency_filter": ([vp, vp, vp, i32, i32, P, vp, vp, vp, vp, vp, vp, sz, vp],
                                       i32),
+            "ff_consistency_filter_static": ([vp, vp, vp, i32, i32, P, vp, vp, vp, vp, vp, vp],
+                                             i32),
             "ff_flow_fields": ([vp, vp, i32, i32, P, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], i32),
             "ff_device_status": ([vp, C.POINTER(C.c_uint32), C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int32), vp], i32),
@@ -241,6 +243,27 @@ def ff_consistency_filter(F, Fb1, Fb2, params=None):
         _dev(F), _dev(Fb1), _dev(Fb2), W, H, C.byref(P), _dev(valid), _dev(err), _dev(sparse),
         _dev(ns), _dev(mask), wp, wn, _stream()))
     return dict(valid=valid, err_sum=err, sparse=sparse, n_sparse=ns, mask=mask)
+
+
+def ff_consistency_filter_static(F, Fb1, Fb2, params=None, out=None):
+    """ff_consistency_filter without a workspace: the library's static scratch
+    array is used (images up to 2^20 pixels; calls must not overlap on the GPU).
+    Outputs may be passed preallocated in ``out`` (same keys as the result)."""
+    H, W = F.shape[:2]
+    dev = F.device
+    P = _params(params)
+    if out is None:
+        nb = ((W + 2) // 3) * ((H + 2) // 3)
+        out = dict(valid=torch.empty((H, W), dtype=torch.uint8, device=dev),
+                   err_sum=torch.empty((H, W), dtype=torch.int32, device=dev),
+                   sparse=torch.empty((nb, 4), dtype=torch.int32, device=dev),
+                   n_sparse=torch.zeros(1, dtype=torch.int32, device=dev),
+                   mask=torch.empty((H, W), dtype=torch.uint8, device=dev))
+    _check("ff_consistency_filter_static", lib().ff_consistency_filter_static(
+        _dev(F), _dev(Fb1), _dev(Fb2), W, H, C.byref(P), _dev(out["valid"]),
+        _dev(out["err_sum"]), _dev(out["sparse"]), _dev(out["n_sparse"]), _dev(out["mask"]),
+        _stream()))
+    return out
 
 
 class FlowFields:
