@@ -44,11 +44,16 @@ __global__ void k_consistency(const uint32_t *__restrict__ F, const uint32_t *__
   parent[p] = ok ? p : -1;
 }
 
-__device__ __forceinline__ int uf_find(const int32_t *parent, int x) {
+// Root of x with path halving. Every parent index is smaller than its child's
+// and only roots are ever relinked (by atomicCAS in uf_unite), so pointing a
+// non-root at its grandparent keeps it inside its set and is safe to race.
+__device__ __forceinline__ int uf_find(int32_t *parent, int x) {
   int p = parent[x];
   while (p != x) {
+    const int g = parent[p];
+    if (g != p) parent[x] = g;
     x = p;
-    p = parent[x];
+    p = g;
   }
   return x;
 }
@@ -79,13 +84,25 @@ __global__ void k_union(const uint32_t *__restrict__ F, const uint8_t *__restric
   if (y + 1 < H && vcc[p + W] && close3(f, F[p + W])) uf_unite(parent, p, p + W);
 }
 
+// Root without compression. In k_flatten each thread stores the root of its own
+// pixel; a compressing find there could overwrite another pixel's stored root
+// with a non-root ancestor after that pixel's thread has written it.
+__device__ __forceinline__ int uf_root(const int32_t *parent, int x) {
+  int p = parent[x];
+  while (p != x) {
+    x = p;
+    p = parent[x];
+  }
+  return x;
+}
+
 __global__ void k_flatten(const uint8_t *__restrict__ vcc, int N, int32_t *parent,
                           int32_t *__restrict__ size) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   size[p] = 0;
   if (!vcc[p]) return;
-  parent[p] = uf_find(parent, p);
+  parent[p] = uf_root(parent, p);
 }
 
 __global__ void k_region_stats(const uint32_t *__restrict__ F, const uint8_t *__restrict__ vcc, int W,

@@ -62,7 +62,7 @@ void kd_bind_scratch(KdBuild &b, Arena &a) {
   int segs = 1 << (T > 0 ? T - 1 : 0);  // widest top level processed
   b.perm_tmp = a.take<int32_t>(b.N > 0 ? b.N : 1);
   b.seg_off = a.take<int32_t>((size_t)(1 << (T + 1)) + T + 2);
-  b.mm = a.take<int32_t>((size_t)segs * NFEAT * 2);
+  b.mm = a.take<int32_t>((size_t)2 * segs * NFEAT * 2);  // two levels (ping-pong)
   b.hist = a.take<uint32_t>((size_t)segs * NBINS);
   b.sel = a.take<int32_t>((size_t)segs * 8);
   b.cnt = a.take<int32_t>((size_t)segs * 2);
@@ -80,6 +80,17 @@ __device__ __forceinline__ int seg_begin(int N, int d, int i) {
   return b;
 }
 __host__ __device__ __forceinline__ int seg_base(int d) { return (1 << d) - 1 + d; }
+
+// Levels ping-pong between perm and perm_tmp: level d reads cur_perm(d) and its
+// partition writes cur_perm(d + 1).
+__device__ __forceinline__ int32_t *cur_perm(const KdBuild &T, int d) {
+  return (d & 1) ? T.perm_tmp : T.perm;
+}
+// min/max of segment s at level d: two buffers alternate by level parity.
+__device__ __forceinline__ int32_t *mm_at(const KdBuild &T, int d, int s) {
+  const int segs = 1 << (T.top_levels > 0 ? T.top_levels - 1 : 0);
+  return T.mm + ((size_t)(d & 1) * segs + s) * NFEAT * 2;
+}
 
 __global__ void k_kd_seg_off(KdBuild *trees, int ntrees) {
   KdBuild &T = trees[blockIdx.y];
@@ -140,7 +151,7 @@ __global__ void __launch_bounds__(256) k_kd_minmax(KdBuild *trees, int d) {
         while (p >= next) next = off[++seg + 1];
       }
       if (lane < NFEAT) {
-        int v = T.feat[(size_t)T.perm[p] * FEAT_STRIDE + lane];
+        int v = T.feat[(size_t)cur_perm(T, d)[p] * FEAT_STRIDE + lane];
         lo = min(lo, v);
         hi = max(hi, v);
       }
@@ -155,24 +166,30 @@ __global__ void __launch_bounds__(256) k_kd_minmax(KdBuild *trees, int d) {
   for (int t = tid; t < (last - seg0 + 1) * NFEAT; t += blockDim.x) {
     int s = t / NFEAT, dim = t % NFEAT;
     if (smin[s][dim] == INT32_MAX) continue;
-    atomicMin(&T.mm[((seg0 + s) * NFEAT + dim) * 2], smin[s][dim]);
-    atomicMax(&T.mm[((seg0 + s) * NFEAT + dim) * 2 + 1], smax[s][dim]);
+    atomicMin(&mm_at(T, d, seg0 + s)[dim * 2], smin[s][dim]);
+    atomicMax(&mm_at(T, d, seg0 + s)[dim * 2 + 1], smax[s][dim]);
   }
 }
 
-__global__ void k_kd_mm_reset(KdBuild *trees, int d) {
+__global__ void k_kd_level_reset(KdBuild *trees, int d) {
   KdBuild &T = trees[blockIdx.y];
   if (d >= T.top_levels) return;
-  int n = (1 << d) * NFEAT;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    T.mm[2 * i] = INT32_MAX;
-    T.mm[2 * i + 1] = INT32_MIN;
-  }
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (1 << d) * NBINS;
-       i += gridDim.x * blockDim.x)
-    T.hist[i] = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (1 << d) * 2; i += gridDim.x * blockDim.x)
-    T.cnt[i] = 0;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (int i = tid; i < (1 << d) * NBINS; i += nth) T.hist[i] = 0;
+  for (int i = tid; i < (1 << d) * 2; i += nth) T.cnt[i] = 0;
+  const int lv = d + 1 < T.top_levels ? d + 1 : -1;
+  if (lv >= 0)
+    for (int i = tid; i < (1 << lv) * NFEAT; i += nth) {
+      int32_t *m = mm_at(T, lv, i / NFEAT) + (i % NFEAT) * 2;
+      m[0] = INT32_MAX;
+      m[1] = INT32_MIN;
+    }
+  if (d == 0)
+    for (int i = tid; i < NFEAT; i += nth) {
+      int32_t *m = mm_at(T, 0, 0) + i * 2;
+      m[0] = INT32_MAX;
+      m[1] = INT32_MIN;
+    }
 }
 
 // sel state per segment: [0] dim, [1] vmin, [2] key bits B, [3] ibits,
@@ -187,7 +204,7 @@ __global__ void k_kd_sel_init(KdBuild *trees, int d) {
   int best = 0;
   long long bs = -1;
   for (int dim = 0; dim < NFEAT; dim++) {
-    long long sp = (long long)T.mm[(s * NFEAT + dim) * 2 + 1] - T.mm[(s * NFEAT + dim) * 2];
+    long long sp = (long long)mm_at(T, d, s)[dim * 2 + 1] - mm_at(T, d, s)[dim * 2];
     if (sp > bs) {
       bs = sp;
       best = dim;
@@ -197,7 +214,7 @@ __global__ void k_kd_sel_init(KdBuild *trees, int d) {
   if (ibits < 1) ibits = 1;
   int32_t *S = T.sel + s * 8;
   S[0] = best;
-  S[1] = T.mm[(s * NFEAT + best) * 2];
+  S[1] = mm_at(T, d, s)[best * 2];
   S[2] = vbits + ibits;
   S[3] = ibits;
   S[4] = m / 2;
@@ -238,7 +255,7 @@ __global__ void __launch_bounds__(256) k_kd_hist(KdBuild *trees, int d) {
     int B = S[2], used = S[7];
     if (used >= B) continue;
     int hi = B - used, lo = max(hi - DIGIT, 0);
-    unsigned long long K = kd_key(T, S, T.perm[p]);
+    unsigned long long K = kd_key(T, S, cur_perm(T, d)[p]);
     unsigned long long pre = ((unsigned long long)(unsigned)S[6] << 32) | (unsigned)S[5];
     if (hi < 64 && (K >> hi) != pre) continue;
     unsigned dig = (unsigned)((K >> lo) & ((1ull << (hi - lo)) - 1));
@@ -294,58 +311,119 @@ __global__ void __launch_bounds__(256) k_kd_digit(KdBuild *trees, int d) {
   }
 }
 
-// Partition: key < selected key goes to the left child; positions from per-
-// segment counters (order inside a child is unspecified). The selected point
-// writes the split value.
+// Partition: key < selected key goes to the left child, else right. Positions
+// come from per-segment counters, aggregated per warp (match_any on the
+// destination) and per CTA, so a CTA issues at most one global atomic per
+// destination child (order inside a child is unspecified). The selected point
+// writes the split value. While the rows pass through, the per-dimension
+// min/max of the children (next level) is accumulated the same way.
+constexpr int PART_CHUNK = 2048;  // positions per CTA (spans <= 3 segments)
+constexpr int PART_ROUNDS = PART_CHUNK / 256;
+
 __global__ void __launch_bounds__(256) k_kd_partition(KdBuild *trees, int d) {
   KdBuild &T = trees[blockIdx.y];
   if (d >= T.top_levels) return;
-  int nseg = 1 << d;
+  const int start = blockIdx.x * PART_CHUNK;
+  if (start >= T.N) return;
+  const int end = min(start + PART_CHUNK, T.N);
+  const int nseg = 1 << d;
   const int32_t *off = T.seg_off + seg_base(d);
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < T.N; p += gridDim.x * blockDim.x) {
-    int s = find_seg(off, nseg, p);
-    const int32_t *S = T.sel + s * 8;
-    int idx = T.perm[p];
-    unsigned long long K = kd_key(T, S, idx);
-    unsigned long long sel = ((unsigned long long)(unsigned)S[6] << 32) | (unsigned)S[5];
-    int b = off[s], m = off[s + 1] - b, half = m >> 1;
-    int dst;
-    if (K < sel) {
-      const int k = atomicAdd(&T.cnt[2 * s], 1);
-      dst = k < half ? b + k : -1;
-    } else {
-      const int k = atomicAdd(&T.cnt[2 * s + 1], 1);
-      dst = k < m - half ? b + half + k : -1;
-      if (K == sel) T.split_val[(1 << d) - 1 + s] = T.feat[(size_t)idx * FEAT_STRIDE + S[0]];
+  const int32_t *src = cur_perm(T, d);
+  int32_t *dstp = cur_perm(T, d + 1);
+  const bool child_mm = d + 1 < T.top_levels;
+  __shared__ int s_seg0;
+  __shared__ int s_cnt[8], s_base[8];
+  __shared__ int s_min[8][NFEAT], s_max[8][NFEAT];
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) s_seg0 = find_seg(off, nseg, start);
+  if (tid < 8) s_cnt[tid] = 0;
+  for (int i = tid; i < 8 * NFEAT; i += 256) {
+    s_min[i / NFEAT][i % NFEAT] = INT32_MAX;
+    s_max[i / NFEAT][i % NFEAT] = INT32_MIN;
+  }
+  __syncthreads();
+  const int seg0 = s_seg0;
+  int combo[PART_ROUNDS], rank[PART_ROUNDS], idxs[PART_ROUNDS];
+#pragma unroll
+  for (int r = 0; r < PART_ROUNDS; r++) {
+    const int p = start + r * 256 + tid;
+    int c = -1, idx = 0;
+    if (p < end) {
+      const int sg = find_seg(off, nseg, p);
+      const int32_t *S = T.sel + sg * 8;
+      idx = src[p];
+      const unsigned long long K = kd_key(T, S, idx);
+      const unsigned long long sel = ((unsigned long long)(unsigned)S[6] << 32) | (unsigned)S[5];
+      c = 2 * (sg - seg0) + (K < sel ? 0 : 1);
+      if (K == sel) T.split_val[(1 << d) - 1 + sg] = T.feat[(size_t)idx * FEAT_STRIDE + S[0]];
     }
-    if (dst >= 0) T.perm_tmp[dst] = idx;
-    else raise_status(T.status, DEV_ERR_KD, s, d);
+    const unsigned grp = __match_any_sync(0xffffffffu, c);
+    const int leader = __ffs(grp) - 1;
+    int wbase = 0;
+    if (c >= 0 && lane == leader) wbase = atomicAdd(&s_cnt[c], __popc(grp));
+    wbase = __shfl_sync(0xffffffffu, wbase, leader);
+    combo[r] = c;
+    rank[r] = wbase + __popc(grp & ((1u << lane) - 1));
+    idxs[r] = idx;
+    if (child_mm) {  // child min/max over the full rows
+      int4 q[7];
+      const int4 *row = (const int4 *)(T.feat + (size_t)idx * FEAT_STRIDE);
+#pragma unroll
+      for (int k = 0; k < 7; k++) q[k] = c >= 0 ? row[k] : make_int4(0, 0, 0, 0);
+      const int *v = (const int *)q;
+#pragma unroll
+      for (int dim = 0; dim < NFEAT; dim++) {
+        const int lo = __reduce_min_sync(grp, v[dim]), hi = __reduce_max_sync(grp, v[dim]);
+        if (c >= 0 && lane == leader) {
+          atomicMin(&s_min[c][dim], lo);
+          atomicMax(&s_max[c][dim], hi);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (tid < 8 && s_cnt[tid] > 0 && seg0 + (tid >> 1) < nseg)
+    s_base[tid] = atomicAdd(&T.cnt[2 * (seg0 + (tid >> 1)) + (tid & 1)], s_cnt[tid]);
+  if (child_mm)
+    for (int i = tid; i < 8 * NFEAT; i += 256) {
+      const int c = i / NFEAT, dim = i % NFEAT;
+      if (s_min[c][dim] == INT32_MAX) continue;
+      int32_t *m = mm_at(T, d + 1, 2 * (seg0 + (c >> 1)) + (c & 1));
+      atomicMin(&m[dim * 2], s_min[c][dim]);
+      atomicMax(&m[dim * 2 + 1], s_max[c][dim]);
+    }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < PART_ROUNDS; r++) {
+    const int c = combo[r];
+    if (c < 0) continue;
+    const int sg = seg0 + (c >> 1), side = c & 1;
+    const int b = off[sg], m = off[sg + 1] - b, half = m >> 1;
+    const int k = s_base[c] + rank[r];
+    const int lim = side ? m - half : half;
+    if (k < lim) dstp[b + side * half + k] = idxs[r];
+    else raise_status(T.status, DEV_ERR_KD, sg, d);
   }
 }
 
-__global__ void k_kd_copy_back(KdBuild *trees, int d) {
-  KdBuild &T = trees[blockIdx.y];
-  if (d >= T.top_levels) return;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < T.N; p += gridDim.x * blockDim.x)
-    T.perm[p] = T.perm_tmp[p];
-}
-
 // One 1024-thread CTA finishes the subtree of one segment at depth top_levels.
-__global__ void __launch_bounds__(1024) k_kd_subtree(KdBuild *trees) {
+// Shared memory: point indices and keys (1024 each), and per node of the current
+// sub-level its per-dimension min/max and chosen dimension (max_nodes nodes).
+__global__ void __launch_bounds__(1024) k_kd_subtree(KdBuild *trees, int max_nodes) {
   KdBuild &T = trees[blockIdx.y];
-  int d0 = T.top_levels;
+  const int d0 = T.top_levels;
   if (blockIdx.x >= (1u << d0)) return;
   const int b0 = seg_begin(T.N, d0, blockIdx.x), e0 = seg_begin(T.N, d0, blockIdx.x + 1);
   const int m0 = e0 - b0;
   extern __shared__ int32_t ssub[];
   int32_t *sidx = ssub, *skey = ssub + SUB_MAX;
-  int(*smin)[NFEAT] = (int(*)[NFEAT])(ssub + 2 * SUB_MAX);  // per node of the sub-level
-  int(*smax)[NFEAT] = smin + SUB_MAX / 2;
-  int *sdim = (int *)(smax + SUB_MAX / 2);
+  int(*smin)[NFEAT] = (int(*)[NFEAT])(ssub + 2 * SUB_MAX);
+  int(*smax)[NFEAT] = smin + max_nodes;
+  int *sdim = (int *)(smax + max_nodes);
   const int t = threadIdx.x, lane = t & 31;
   const bool act = t < m0;
-  if (act) sidx[t] = T.perm[b0 + t];
-  int nb = 0, ne = m0, nid = 0;  // my position's node (local) at this sub-depth
+  if (act) sidx[t] = cur_perm(T, d0)[b0 + t];
+  int nb = 0, ne = m0, nid = 0;  // node (local) holding position t at this sub-depth
   const int levels = T.D - d0;
   for (int sd = 0; sd < levels; sd++) {
     const int nnodes = 1 << sd;
@@ -354,14 +432,17 @@ __global__ void __launch_bounds__(1024) k_kd_subtree(KdBuild *trees) {
       smax[i / NFEAT][i % NFEAT] = INT32_MIN;
     }
     __syncthreads();
-    // per-node min/max: reduce over lanes of the same node, leader updates smem
-    int idx = act ? sidx[t] : 0;
-    const int32_t *row = T.feat + (size_t)idx * FEAT_STRIDE;
-    unsigned grp = __match_any_sync(0xffffffffu, act ? nid : -1);
-    bool leader = (__ffs(grp) - 1) == lane;
+    const int idx = act ? sidx[t] : 0;
+    int4 q[7];
+    const int4 *row = (const int4 *)(T.feat + (size_t)idx * FEAT_STRIDE);
+#pragma unroll
+    for (int k = 0; k < 7; k++) q[k] = row[k];
+    const int *v = (const int *)q;
+    const unsigned grp = __match_any_sync(0xffffffffu, act ? nid : -1);
+    const bool leader = (__ffs(grp) - 1) == lane;
+#pragma unroll
     for (int dim = 0; dim < NFEAT; dim++) {
-      int v = act ? row[dim] : 0;
-      int lo = __reduce_min_sync(grp, v), hi = __reduce_max_sync(grp, v);
+      const int lo = __reduce_min_sync(grp, v[dim]), hi = __reduce_max_sync(grp, v[dim]);
       if (act && leader) {
         atomicMin(&smin[nid][dim], lo);
         atomicMax(&smax[nid][dim], hi);
@@ -372,7 +453,7 @@ __global__ void __launch_bounds__(1024) k_kd_subtree(KdBuild *trees) {
       int best = 0;
       long long bs = -1;
       for (int dim = 0; dim < NFEAT; dim++) {
-        long long sp = (long long)smax[i][dim] - smin[i][dim];
+        const long long sp = (long long)smax[i][dim] - smin[i][dim];
         if (sp > bs) {
           bs = sp;
           best = dim;
@@ -381,27 +462,28 @@ __global__ void __launch_bounds__(1024) k_kd_subtree(KdBuild *trees) {
       sdim[i] = best;
     }
     __syncthreads();
-    int dim = act ? sdim[nid] : 0;
-    int v = act ? row[dim] : 0;
-    if (act) skey[t] = v;
+    const int dim = act ? sdim[nid] : 0;
+    int key = 0;
+#pragma unroll
+    for (int k = 0; k < NFEAT; k++)
+      if (k == dim) key = v[k];
+    if (act) skey[t] = key;
     __syncthreads();
     int rank = 0;
-    if (act) {
+    if (act)
       for (int u = nb; u < ne; u++) {
-        int kv = skey[u], ki = sidx[u];
-        rank += (kv < v) || (kv == v && ki < idx);
+        const int kv = skey[u], ki = sidx[u];
+        rank += (kv < key) || (kv == key && ki < idx);
       }
-    }
     __syncthreads();
     if (act) {
       sidx[nb + rank] = idx;
-      int half = (ne - nb) >> 1;
+      const int half = (ne - nb) >> 1;
       if (rank == half) {
-        int node = (1 << (d0 + sd)) - 1 + (blockIdx.x << sd) + nid;
+        const int node = (1 << (d0 + sd)) - 1 + (blockIdx.x << sd) + nid;
         T.split_dim[node] = dim;
-        T.split_val[node] = v;
+        T.split_val[node] = key;
       }
-      // my position t belongs to which child
       if (t < nb + half) {
         ne = nb + half;
         nid = 2 * nid;
@@ -415,32 +497,34 @@ __global__ void __launch_bounds__(1024) k_kd_subtree(KdBuild *trees) {
   if (act) T.perm[b0 + t] = sidx[t];
 }
 
-static size_t subtree_smem() {
-  return sizeof(int32_t) * (2 * SUB_MAX + 2 * (SUB_MAX / 2) * NFEAT + SUB_MAX / 2);
+static size_t subtree_smem(int max_nodes) {
+  return sizeof(int32_t) * (2 * SUB_MAX + 2 * (size_t)max_nodes * NFEAT + max_nodes);
 }
 
 ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaStream_t st) {
   if (ntrees <= 0) return FF_OK;
   FF_TRY(upload_desc(trees, dev, ntrees, st));
-  int maxT = 0, maxN = 0, maxD = 0;
+  int maxT = 0, maxN = 0, maxSub = 0;
   for (int i = 0; i < ntrees; i++) {
     maxT = max(maxT, trees[i].top_levels);
     maxN = max(maxN, trees[i].N);
-    maxD = max(maxD, trees[i].D);
+    maxSub = max(maxSub, trees[i].D - trees[i].top_levels);
   }
   if (maxN <= 0) return FF_OK;
   const int B = 256;
-  int gN = min((maxN + B - 1) / B, 4096);
+  const int gN = min((maxN + B - 1) / B, 4096);
   k_kd_init_perm<<<dim3(gN, ntrees), B, 0, st>>>(dev);
   FF_CHECK_LAUNCH();
   k_kd_seg_off<<<dim3(8, ntrees), B, 0, st>>>(dev, ntrees);
   FF_CHECK_LAUNCH();
   for (int d = 0; d < maxT; d++) {
-    int nseg = 1 << d;
-    k_kd_mm_reset<<<dim3(min((nseg * NBINS + B - 1) / B, 1024), ntrees), B, 0, st>>>(dev, d);
+    const int nseg = 1 << d;
+    k_kd_level_reset<<<dim3(min((nseg * NBINS + B - 1) / B, 1024), ntrees), B, 0, st>>>(dev, d);
     FF_CHECK_LAUNCH();
-    k_kd_minmax<<<dim3((maxN + MM_CHUNK - 1) / MM_CHUNK, ntrees), 256, 0, st>>>(dev, d);
-    FF_CHECK_LAUNCH();
+    if (d == 0) {
+      k_kd_minmax<<<dim3((maxN + MM_CHUNK - 1) / MM_CHUNK, ntrees), 256, 0, st>>>(dev, d);
+      FF_CHECK_LAUNCH();
+    }
     k_kd_sel_init<<<dim3((nseg + 127) / 128, ntrees), 128, 0, st>>>(dev, d);
     FF_CHECK_LAUNCH();
     for (int pass = 0; pass < MAX_PASSES; pass++) {
@@ -449,21 +533,20 @@ ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaSt
       k_kd_digit<<<dim3(nseg, ntrees), 256, 0, st>>>(dev, d);
       FF_CHECK_LAUNCH();
     }
-    k_kd_partition<<<dim3(gN, ntrees), B, 0, st>>>(dev, d);
-    FF_CHECK_LAUNCH();
-    k_kd_copy_back<<<dim3(gN, ntrees), B, 0, st>>>(dev, d);
+    k_kd_partition<<<dim3((maxN + PART_CHUNK - 1) / PART_CHUNK, ntrees), 256, 0, st>>>(dev, d);
     FF_CHECK_LAUNCH();
   }
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_kd_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)subtree_smem());
-    attr = true;
+  const int max_nodes = maxSub > 0 ? 1 << (maxSub - 1) : 1;
+  const size_t smem = subtree_smem(max_nodes);
+  static size_t attr = 0;
+  if (smem > attr) {
+    if (cudaFuncSetAttribute(k_kd_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return FF_ERR_CUDA;
+    attr = smem;
   }
-  if (maxD > 0 || maxT >= 0) {
-    k_kd_subtree<<<dim3(1 << maxT, ntrees), SUB_MAX, subtree_smem(), st>>>(dev);
-    FF_CHECK_LAUNCH();
-  }
+  k_kd_subtree<<<dim3(1 << maxT, ntrees), SUB_MAX, smem, st>>>(dev, max_nodes);
+  FF_CHECK_LAUNCH();
   return FF_OK;
 }
 
