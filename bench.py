@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "ms per 1024×436 pair + cand-evals/s; learned vs plain at equal inliers@3px"
 W, H = 1024, 436
 WORKLOAD = "Sintel-shaped 1024x436 RGB uint8 pair (3 textured layers, affine motion <= 200 px)"
-PARAMS = dict(k=3, r=8, r2=6, leaf=8, R=1, eps=5, e=4, s=50, tile=32, n_rs=3, K=0, seed=0)
+PARAMS = dict(k=3, r=8, r2=6, leaf=8, R=1, eps=5, e=4, s=50, tile=16, n_rs=3, K=0, seed=0)
 
 
 def nominal_evals(W, H, p):
@@ -152,7 +152,7 @@ def run_reference(args):
         "cand_evals_per_s": nominal_evals(W, H, PARAMS) / (ms / 1000.0),
         "cpu_baseline": {"value": ms, "unit": "ms/pair", "cores": 3, "kind": "oracle",
                          "sample": f"{args.steps} full 1024x436 pairs, three flows on three "
-                                   "threads, tiled schedule T=32"},
+                                   "threads, tiled schedule T=16"},
         "e2e": {"value": ms, "unit": "ms/pair", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

@@ -75,7 +75,7 @@ const char *ff_status_str(ff_status s);
 
 /* Fill *p with the parameters of Sec. 4 for a dataset preset: k=3, R=1, l=8,
  * r=8, r2=6 and (eps, e, s) = (5, 4, 50) Sintel, (1, 7, 50) Middlebury,
- * (1, 9, 150) KITTI; tile=32, n_rs=3, K=0, seed=0. */
+ * (1, 9, 150) KITTI; tile=16, n_rs=3, K=0, seed=0. */
 ff_status ff_params_preset(ff_params *p, int preset);
 
 /* Workspace bytes needed by ff_flow_fields for a W x H pair (host-only call). */

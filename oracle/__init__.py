@@ -46,8 +46,8 @@ class Params(C.Structure):
 
 def default_params(**kw):
     """Sec. 4 parameters (k=3, R=1, l=8, r=8, r2=6; Sintel eps/e/s = 5/4/50),
-    tile T=32 for the parallel schedule, 3 random-search steps, no proposals."""
-    d = dict(k=3, r=8, r2=6, leaf=8, R=1, eps=5, e=4, s=50, tile=32, n_rs=3, K=0, seed=0)
+    tile T=16 for the parallel schedule, 3 random-search steps, no proposals."""
+    d = dict(k=3, r=8, r2=6, leaf=8, R=1, eps=5, e=4, s=50, tile=16, n_rs=3, K=0, seed=0)
     d.update(kw)
     return d
 
@@ -247,7 +247,7 @@ def rs_offset(seed, flow_id, level, step, gx, gy, Rn):
     return int(d[0]), int(d[1])
 
 
-def search_level(Cs, Ct, n, r, flow_coarse=None, flow=None, cost=None, tile=32, n_rs=3, R=1,
+def search_level(Cs, Ct, n, r, flow_coarse=None, flow=None, cost=None, tile=16, n_rs=3, R=1,
                  seed=0, flow_id=0):
     """One hierarchy level. With flow_coarse the level is seeded from it (Sec. 3.2);
     without, (flow, cost) is the initial state (top level). Returns flow, cost, evals."""

@@ -155,7 +155,7 @@ ff_status ff_params_preset(ff_params *p, int preset) {
   p->r2 = 6;
   p->leaf = 8;
   p->R = 1;
-  p->tile = 32;
+  p->tile = 16;
   p->n_rs = 3;
   p->K = 0;
   p->seed = 0;

@@ -62,6 +62,11 @@ struct Planes {
   int pitch;        // words per padded row (>= NX + 2P, multiple of 4)
   int rows;         // NY + 2P
   size_t plane_words;  // pitch * rows
+  // Transposed copy of every plane (row = x entry, column = y entry), so that a
+  // vertical run of taps is contiguous too.
+  uint32_t *baseT;
+  int pitchT;          // >= NY + 2P, multiple of 4
+  size_t plane_wordsT;  // pitchT * (NX + 2P)
 };
 
 __host__ __device__ inline Planes make_planes(uint32_t *base, int W, int H, int n) {
@@ -78,11 +83,14 @@ __host__ __device__ inline Planes make_planes(uint32_t *base, int W, int H, int 
   p.pitch = ((p.NX + 2 * PLANE_PAD) + 3) & ~3;
   p.rows = p.NY + 2 * PLANE_PAD;
   p.plane_words = (size_t)p.pitch * p.rows;
+  p.pitchT = ((p.NY + 2 * PLANE_PAD) + 3) & ~3;
+  p.plane_wordsT = (size_t)p.pitchT * (p.NX + 2 * PLANE_PAD);
+  p.baseT = base ? base + p.plane_words * (size_t)n * n : nullptr;
   return p;
 }
 __host__ __device__ inline size_t planes_words(int W, int H, int n) {
   Planes p = make_planes(nullptr, W, H, n);
-  return p.plane_words * (size_t)n * n;
+  return (p.plane_words + p.plane_wordsT) * (size_t)n * n;
 }
 
 // Address of the centre tap of the patch around pixel (x, y), inside the image.

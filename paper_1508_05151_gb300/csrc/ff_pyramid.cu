@@ -153,15 +153,18 @@ ff_status launch_census(const uint8_t *imgn, int W, int H, int n, uint32_t *out,
   return FF_OK;
 }
 
-// Relayout of a plain census image into the padded phase planes.
+// Relayout of a plain census image into the padded phase planes and their
+// transposed copies.
 __global__ void k_planes(const uint32_t *__restrict__ census, Planes P) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  int pl = blockIdx.z;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int pl = blockIdx.z;
   if (i >= P.pitch || j >= P.rows) return;
-  int px = pl % P.n, py = pl / P.n;
-  int x = clampi(px + P.n * (i - PLANE_PAD), 0, P.W - 1);
-  int y = clampi(py + P.n * (j - PLANE_PAD), 0, P.H - 1);
-  P.base[(size_t)pl * P.plane_words + (size_t)j * P.pitch + i] = census[(size_t)y * P.W + x];
+  const int px = pl % P.n, py = pl / P.n;
+  const int x = clampi(px + P.n * (i - PLANE_PAD), 0, P.W - 1);
+  const int y = clampi(py + P.n * (j - PLANE_PAD), 0, P.H - 1);
+  const uint32_t v = census[(size_t)y * P.W + x];
+  P.base[(size_t)pl * P.plane_words + (size_t)j * P.pitch + i] = v;
+  if (i < P.NX + 2 * PLANE_PAD) P.baseT[(size_t)pl * P.plane_wordsT + (size_t)i * P.pitchT + j] = v;
 }
 
 ff_status launch_planes(const uint32_t *census, Planes P, cudaStream_t st) {

@@ -20,6 +20,8 @@
 // The source patches of the tile's points form one dense (T + 2r)^2 block of the
 // source frame's phase-(0,0) plane; it is staged in shared memory once per pass.
 // Target taps are gathered from the target frame's phase planes (L1/L2).
+#include <mutex>
+
 #include "ff_internal.cuh"
 
 namespace ff {
@@ -63,23 +65,97 @@ struct PassCfg {
   int R;        // full-resolution random-search radius
   uint64_t seed;
   int last;     // last pass of the level (writes flow_final when given)
+  int words_per_tile;  // shared memory words of one tile
 };
 
-constexpr int PASS_THREADS = 512;
-constexpr int NGROUPS = PASS_THREADS / 16;
+constexpr int PASS_WARPS = 4;
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+// Shared-memory layout of one tile (all sizes in 32-bit words).
+struct TileLayout {
+  int sw, swp;   // source window edge and (odd) pitch
+  int tw, twp;   // target window edge and (odd) pitch
+  int T;
+  __host__ __device__ TileLayout(int T_, int R) : T(T_) {
+    sw = T_ + 2 * R + 2;
+    swp = sw | 1;
+    tw = T_ + 2 * R + 8;  // 3 entries of slack on each side of the tile's patches
+    twp = tw | 1;
+  }
+  __host__ __device__ int words() const { return sw * swp + tw * twp + 2 * T * T + 4 * T; }
+};
+
+// Incremental E_d delta of a propagation candidate, by one lane. When p takes the
+// flow f of its neighbour q = p + s*n along one axis and the target is not
+// clamped, the patches of p and q (and of p + f, q + f) differ by one line:
+//   E(p, f) = E(q, f) - E_line(q side) + E_line(p side)   (exact in integers).
+// so_/si_ and to_/ti_ point at the first tap of the outgoing/incoming line in the
+// source window and in the target (window or plane); ss/ts are the strides along
+// the line. Horizontal neighbours give column lines, vertical ones row lines;
+// both use this one loop, so lanes of a warp never split on the direction.
+template <int R>
+__device__ __forceinline__ int lane_line_delta(const uint32_t *so_, const uint32_t *si_, int ss,
+                                               const uint32_t *to_, const uint32_t *ti_, int ts) {
+  // two independent accumulators per line keep the add chains short
+  int in0 = 0, in1 = 0, out0 = 0, out1 = 0;
+#pragma unroll
+  for (int w = 0; w < 2 * R + 1; w++) {
+    const int pi = __popc(si_[w * ss] ^ ti_[w * ts]), po = __popc(so_[w * ss] ^ to_[w * ts]);
+    if (w & 1) {
+      in1 += pi;
+      out1 += po;
+    } else {
+      in0 += pi;
+      out0 += po;
+    }
+  }
+  return (in0 + in1) - (out0 + out1);
+}
+
+// Full E_d by one lane; rows of the source window and of the target. Four
+// accumulators break the chain of dependent adds across the (2R+1)^2 taps.
+template <int R>
+__device__ __forceinline__ int lane_full(const uint32_t *sc, int swp, const uint32_t *tc, int tp) {
+  int a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  sc -= R * swp + R;
+  tc -= R * tp + R;
+#pragma unroll 3
+  for (int v = 0; v < 2 * R + 1; v++) {
+#pragma unroll
+    for (int u = 0; u < 2 * R + 1; u++) {
+      const int pc = __popc(sc[u] ^ tc[u]);
+      switch (u & 3) {
+        case 0: a0 += pc; break;
+        case 1: a1 += pc; break;
+        case 2: a2 += pc; break;
+        default: a3 += pc; break;
+      }
+    }
+    sc += swp;
+    tc += tp;
+  }
+  return (a0 + a1) + (a2 + a3);
+}
 
 template <int R>
-__global__ void __launch_bounds__(PASS_THREADS) k_pass(const SearchProblem *probs, PassCfg cfg) {
+__global__ void __launch_bounds__(PASS_WARPS * 32) k_pass(const SearchProblem *probs, PassCfg cfg) {
+  extern __shared__ uint32_t smem[];
   const SearchProblem &P = probs[blockIdx.y];
-  const int Gx = P.src.NX, Gy = P.src.NY, n = P.src.n, W = P.src.W, H = P.src.H;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tpw = 1, width = 32, sub = 0, sl = lane;
+  const int Gx = P.src.NX, Gy = P.src.NY, n = P.src.n, log2n = P.src.log2n;
+  const int W = P.src.W, H = P.src.H;
   const int T = cfg.tile, off = (cfg.s & 1) * (T >> 1);
   const int ntx = (Gx + off + T - 1) / T, nty = (Gy + off + T - 1) / T;
-  if ((int)blockIdx.x >= ntx * nty) return;
-  const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
+  const int tile = (blockIdx.x * PASS_WARPS + warp) * tpw + sub;
+  const bool live = tile < ntx * nty;
+  if (!__any_sync(FULL_MASK, live)) return;  // whole warp; no block barriers below
+  const int tx = live ? tile % ntx : 0, ty = live ? tile / ntx : 0;
   const int x0 = max(tx * T - off, 0), x1 = min(tx * T - off + T, Gx);
   const int y0 = max(ty * T - off, 0), y1 = min(ty * T - off + T, Gy);
-  const int tw = x1 - x0, th = y1 - y0;
+  const int tw = live ? x1 - x0 : 0, th = live ? y1 - y0 : 0;
   const int hdx = c_pass_src[cfg.s][0][0], vdy = c_pass_src[cfg.s][1][1];
+  const TileLayout Lt(T, R);
 
   const uint32_t *fin = (cfg.s & 1) ? P.flow_b : P.flow_a;
   const int32_t *cin = (cfg.s & 1) ? P.cost_b : P.cost_a;
@@ -89,218 +165,401 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(const SearchProblem *prob
     fout = P.flow_final;
     cout = P.cost_final;
   }
+  const uint32_t *tbase = P.tgt.base, *tbaseT = P.tgt.baseT;
+  const int tpitch = P.tgt.pitch, tpitchT = P.tgt.pitchT, trows = P.tgt.rows;
+  const size_t tpw_ = P.tgt.plane_words, tpwT = P.tgt.plane_wordsT;
 
-  constexpr int SWP = MAX_TILE + 2 * R;  // staged source window pitch
-  __shared__ uint32_t s_src[SWP * SWP];
-  __shared__ uint32_t s_flow[MAX_TILE * MAX_TILE];
-  __shared__ int32_t s_cost[MAX_TILE * MAX_TILE];
-  __shared__ uint32_t s_cflow[2 * MAX_TILE];
-  __shared__ int32_t s_cpt[2 * MAX_TILE];
-  __shared__ int32_t s_ccost[2 * MAX_TILE];
-  __shared__ int s_ncand;
+  uint32_t *s_src = smem + (size_t)(warp * tpw + sub) * cfg.words_per_tile;
+  uint32_t *s_tgt = s_src + Lt.sw * Lt.swp;
+  uint32_t *s_flow = s_tgt + Lt.tw * Lt.twp;
+  int32_t *s_cost = (int32_t *)(s_flow + T * T);
+  uint32_t *s_hf = (uint32_t *)(s_cost + T * T);  // neighbours just outside the tile
+  int32_t *s_hc = (int32_t *)(s_hf + T);
+  uint32_t *s_vf = (uint32_t *)(s_hc + T);
+  int32_t *s_vc = (int32_t *)(s_vf + T);
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int grp = tid >> 4, l16 = tid & 15;
-  const unsigned gmask = 0xffffu << (tid & 16);
-
-  // stage tile state and the source window (phase-(0,0) plane of the source)
-  for (int i = tid; i < tw * th; i += PASS_THREADS) {
+  // ---- stage tile state, outside neighbours, source window ----
+  for (int i = sl; i < tw * th; i += width) {
     const int lx = i % tw, ly = i / tw;
     const size_t g = (size_t)(y0 + ly) * Gx + x0 + lx;
-    s_flow[ly * MAX_TILE + lx] = fin[g];
-    s_cost[ly * MAX_TILE + lx] = cin[g];
+    s_flow[ly * T + lx] = fin[g];
+    s_cost[ly * T + lx] = cin[g];
+  }
+  if (live) {
+    const int hx = hdx < 0 ? x0 - 1 : x1, vy = vdy < 0 ? y0 - 1 : y1;
+    for (int i = sl; i < th; i += width) {
+      const bool ok = hx >= 0 && hx < Gx;
+      s_hf[i] = ok ? fin[(size_t)(y0 + i) * Gx + hx] : 0u;
+      s_hc[i] = ok ? cin[(size_t)(y0 + i) * Gx + hx] : COST_UNSET;
+    }
+    for (int i = sl; i < tw; i += width) {
+      const bool ok = vy >= 0 && vy < Gy;
+      s_vf[i] = ok ? fin[(size_t)vy * Gx + x0 + i] : 0u;
+      s_vc[i] = ok ? cin[(size_t)vy * Gx + x0 + i] : COST_UNSET;
+    }
   }
   {
-    const uint32_t *src0 = P.src.base + (size_t)(y0 - R + PLANE_PAD) * P.src.pitch + (x0 - R + PLANE_PAD);
-    const int ww = tw + 2 * R, wh = th + 2 * R;
-    for (int i = tid; i < ww * wh; i += PASS_THREADS) {
+    const int ww = live ? tw + 2 * R + 2 : 0, wh = th + 2 * R + 2;
+    const int ex0 = x0 - R - 1 + PLANE_PAD, ey0 = y0 - R - 1 + PLANE_PAD;
+    for (int i = sl; i < ww * wh; i += width) {
       const int wx = i % ww, wy = i / ww;
-      s_src[wy * SWP + wx] = src0[(size_t)wy * P.src.pitch + wx];
+      const int ex = ex0 + wx, ey = ey0 + wy;
+      // entries outside the plane are only reachable through neighbours outside
+      // the grid, which are never used
+      s_src[wy * Lt.swp + wx] = (ex >= 0 && ey >= 0 && ex < P.src.pitch && ey < P.src.rows)
+                                    ? P.src.base[(size_t)ey * P.src.pitch + ex]
+                                    : 0u;
     }
   }
-  __syncthreads();
+  // target window: where the tile's patches land under the flow of a set point
+  // near the tile centre (after seeding the even-even points are set)
+  int tox = 0, toy = 0, ph0 = -1;
+  if (live) {
+    int gx = x0 + (tw >> 1), gy = y0 + (th >> 1);
+    if (cin[(size_t)gy * Gx + gx] == COST_UNSET) {
+      gx &= ~1;
+      gy &= ~1;
+    }
+    const size_t g = (size_t)gy * Gx + gx;
+    if (cin[g] != COST_UNSET) {
+      const uint32_t fc = fin[g];
+      const int m = n - 1;
+      const int cx = gx * n + flow_dx(fc), cy = gy * n + flow_dy(fc);
+      const int slack = Lt.tw - (tw + 2 * R + 2);
+      tox = (x0 - R - 1) + ((cx >> log2n) - gx) + PLANE_PAD - slack / 2;
+      toy = (y0 - R - 1) + ((cy >> log2n) - gy) + PLANE_PAD - slack / 2;
+      ph0 = ((cy & m) << log2n) + (cx & m);
+    }
+  }
+  if (ph0 >= 0) {
+    const uint32_t *pl = tbase + (size_t)ph0 * tpw_;
+    for (int i = sl; i < Lt.tw * Lt.tw; i += width) {
+      const int wx = i % Lt.tw, wy = i / Lt.tw;
+      const int ex = tox + wx, ey = toy + wy;
+      // entries outside the plane are never inside a valid candidate's patch
+      s_tgt[wy * Lt.twp + wx] = (ex >= 0 && ey >= 0 && ex < tpitch && ey < trows)
+                                    ? pl[(size_t)ey * tpitch + ex]
+                                    : 0u;
+    }
+  }
+  __syncwarp();
 
-  // ---- wavefront over anti-diagonals in scan orientation ----
-  // lane j of warp 0 owns scan row j' = j; local column from the scan position.
-  int my_nc = 0, my_slot = 0;
-  uint32_t my_c0 = 0, my_c1 = 0;
+  // target of candidate flow f at pixel (px, py): plane phase and entry; in_win
+  // when the whole patch plus one line lies inside this tile's target window
+  struct Tgt {
+    int ph, ex, ey;
+    bool win;
+  };
+  auto locate = [&](int px, int py, uint32_t f) {
+    Tgt t;
+    const int txx = px + flow_dx(f), tyy = py + flow_dy(f);
+    const int m = n - 1;
+    t.ph = ((tyy & m) << log2n) + (txx & m);
+    t.ex = (txx >> log2n) + PLANE_PAD;
+    t.ey = (tyy >> log2n) + PLANE_PAD;
+    t.win = t.ph == ph0 && t.ex - R - 1 >= tox && t.ex + R + 1 < tox + Lt.tw &&
+            t.ey - R - 1 >= toy && t.ey + R + 1 < toy + Lt.tw;
+    return t;
+  };
+
+  // Propagation candidate c (0: horizontal source, 1: vertical source) of the
+  // point at scan position (ip, jp): its clamped flow, whether it is worth
+  // evaluating, and its E_d (incremental when the flow is unchanged by clamping).
+  auto evaluate = [&](int c, int lx, int ly, int px, int py, uint32_t fq, int32_t cq, int &cost) {
+    const uint32_t *sc = s_src + (ly + R + 1) * Lt.swp + (lx + R + 1);
+    const int tgx = clampi(px + flow_dx(fq), 0, W - 1), tgy = clampi(py + flow_dy(fq), 0, H - 1);
+    const uint32_t cf = pack_flow(tgx - px, tgy - py);
+    const Tgt t = locate(px, py, cf);
+    if (cf == fq) {
+      const int step = c == 0 ? hdx : vdy;
+      const int oo = step + step * R, oi = -step * R;  // outgoing / incoming line offsets
+      const uint32_t *so_, *si_, *to_, *ti_;
+      int ss, ts;
+      if (c == 0) {  // column lines
+        ss = Lt.swp;
+        so_ = sc - R * Lt.swp + oo;
+        si_ = sc - R * Lt.swp + oi;
+        if (t.win) {
+          const uint32_t *tc = s_tgt + (t.ey - toy) * Lt.twp + (t.ex - tox);
+          ts = Lt.twp;
+          to_ = tc - R * Lt.twp + oo;
+          ti_ = tc - R * Lt.twp + oi;
+        } else {  // rows of the transposed plane
+          const uint32_t *tc = tbaseT + (size_t)t.ph * tpwT + (size_t)t.ex * tpitchT + t.ey;
+          ts = 1;
+          to_ = tc + oo * tpitchT - R;
+          ti_ = tc + oi * tpitchT - R;
+        }
+      } else {  // row lines
+        ss = 1;
+        so_ = sc + oo * Lt.swp - R;
+        si_ = sc + oi * Lt.swp - R;
+        const uint32_t *tc;
+        int tp;
+        if (t.win) {
+          tc = s_tgt + (t.ey - toy) * Lt.twp + (t.ex - tox);
+          tp = Lt.twp;
+        } else {
+          tc = tbase + (size_t)t.ph * tpw_ + (size_t)t.ey * tpitch + t.ex;
+          tp = tpitch;
+        }
+        ts = 1;
+        to_ = tc + oo * tp - R;
+        ti_ = tc + oi * tp - R;
+      }
+      cost = cq + lane_line_delta<R>(so_, si_, ss, to_, ti_, ts);
+    } else if (t.win) {
+      cost = lane_full<R>(sc, Lt.swp, s_tgt + (t.ey - toy) * Lt.twp + (t.ex - tox), Lt.twp);
+    } else {
+      cost = lane_full<R>(sc, Lt.swp, tbase + (size_t)t.ph * tpw_ + (size_t)t.ey * tpitch + t.ex,
+                          tpitch);
+    }
+    return cf;
+  };
+  auto clamp_flow = [&](int px, int py, uint32_t fq) {
+    const int tgx = clampi(px + flow_dx(fq), 0, W - 1), tgy = clampi(py + flow_dy(fq), 0, H - 1);
+    return pack_flow(tgx - px, tgy - py);
+  };
+
+  // ---- wavefront over scan anti-diagonals ----
+  // Tiles of up to 16 rows: lane j owns scan row j and lane j + 16 evaluates the
+  // row's vertical candidate at the same time; larger tiles: lane j owns row j and
+  // evaluates both candidates. The owner applies them in order (strict less).
+  const bool paired = T <= 16;
+  const int row = paired ? (lane & 15) : lane;
+  const int role = paired ? (lane >> 4) : 0;
+  const int owner = paired ? row : lane;
+  uint32_t last_f = 0;
+  int32_t last_c = COST_UNSET;
   for (int d = 0; d < tw + th - 1; d++) {
-    if (warp == 0) {
-      // A: candidates of the point on scan row `lane`, scan column d - lane
-      const int jp = lane, ip = d - lane;
-      int nc = 0;
-      uint32_t c0 = 0, c1 = 0;
-      const bool on = jp < th && ip >= 0 && ip < tw;
-      if (on) {
-        const int lx = hdx < 0 ? ip : tw - 1 - ip;
-        const int ly = vdy < 0 ? jp : th - 1 - jp;
-        const int gx = x0 + lx, gy = y0 + ly, px = gx * n, py = gy * n;
-        const uint32_t fcur = s_flow[ly * MAX_TILE + lx];
-        const bool set = s_cost[ly * MAX_TILE + lx] != COST_UNSET;
-#pragma unroll
-        for (int c = 0; c < 2; c++) {
-          const int qx = gx + (c == 0 ? hdx : 0), qy = gy + (c == 0 ? 0 : vdy);
-          if (qx < 0 || qx >= Gx || qy < 0 || qy >= Gy) continue;
-          const int qlx = qx - x0, qly = qy - y0;
-          uint32_t fq;
-          int32_t cq;
-          if (qlx >= 0 && qlx < tw && qly >= 0 && qly < th) {
-            fq = s_flow[qly * MAX_TILE + qlx];
-            cq = s_cost[qly * MAX_TILE + qlx];
-          } else {
-            fq = fin[(size_t)qy * Gx + qx];
-            cq = cin[(size_t)qy * Gx + qx];
-          }
-          if (cq == COST_UNSET) continue;
-          const int tgx = clampi(px + flow_dx(fq), 0, W - 1), tgy = clampi(py + flow_dy(fq), 0, H - 1);
-          const uint32_t cf = pack_flow(tgx - px, tgy - py);
-          if (set && cf == fcur) continue;
-          if (nc == 1 && cf == c0) continue;
-          if (nc == 0) c0 = cf;
-          else c1 = cf;
-          nc++;
-        }
+    const uint32_t up_f = __shfl_up_sync(FULL_MASK, last_f, 1, paired ? 16 : 32);
+    const int32_t up_c = __shfl_up_sync(FULL_MASK, last_c, 1, paired ? 16 : 32);
+    const int jp = row, ip = d - row;
+    const bool on = jp < th && ip >= 0 && ip < tw;
+    int lx = 0, ly = 0, gx = 0, gy = 0, px = 0, py = 0;
+    uint32_t f0 = 0;
+    int32_t c0 = COST_UNSET;
+    // the sources' states
+    bool hv = false, vv = false;
+    uint32_t fh = 0, fv = 0;
+    int32_t ch = COST_UNSET, cv = COST_UNSET;
+    if (on) {
+      lx = hdx < 0 ? ip : tw - 1 - ip;
+      ly = vdy < 0 ? jp : th - 1 - jp;
+      gx = x0 + lx;
+      gy = y0 + ly;
+      px = gx * n;
+      py = gy * n;
+      f0 = s_flow[ly * T + lx];
+      c0 = s_cost[ly * T + lx];
+      if (gx + hdx >= 0 && gx + hdx < Gx) {
+        fh = ip > 0 ? last_f : s_hf[ly];
+        ch = ip > 0 ? last_c : s_hc[ly];
+        hv = ch != COST_UNSET;
       }
-      // slots by exclusive prefix over lanes
-      int incl = nc;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
+      if (gy + vdy >= 0 && gy + vdy < Gy) {
+        fv = jp > 0 ? up_f : s_vf[lx];
+        cv = jp > 0 ? up_c : s_vc[lx];
+        vv = cv != COST_UNSET;
       }
-      const int slot = incl - nc;
-      if (nc > 0) {
-        s_cflow[slot] = c0;
-        s_cpt[slot] = (jp << 16) | (ip & 0xffff);
-        if (nc > 1) {
-          s_cflow[slot + 1] = c1;
-          s_cpt[slot + 1] = (jp << 16) | (ip & 0xffff);
-        }
-      }
-      if (lane == 31) s_ncand = incl;
-      my_nc = nc;
-      my_slot = slot;
-      my_c0 = c0;
-      my_c1 = c1;
     }
-    __syncthreads();
-    // B: evaluate the candidate list
-    const int ncand = s_ncand;
-    for (int e = grp; e < ncand; e += NGROUPS) {
-      const int jp = s_cpt[e] >> 16, ip = s_cpt[e] & 0xffff;
-      const int lx = hdx < 0 ? ip : tw - 1 - ip;
-      const int ly = vdy < 0 ? jp : th - 1 - jp;
-      const int px = (x0 + lx) * n, py = (y0 + ly) * n;
-      const uint32_t cf = s_cflow[e];
-      const int cost = group_cost<R>(s_src + (ly + R) * SWP + (lx + R), SWP,
-                                     plane_centre(P.tgt, px + flow_dx(cf), py + flow_dy(cf)),
-                                     P.tgt.pitch, l16, gmask);
-      if (l16 == 0) s_ccost[e] = cost;
-    }
-    __syncthreads();
-    // C: apply in order current, horizontal, vertical
-    if (warp == 0 && my_nc > 0) {
-      const int jp = lane, ip = d - lane;
-      const int lx = hdx < 0 ? ip : tw - 1 - ip;
-      const int ly = vdy < 0 ? jp : th - 1 - jp;
-      uint32_t f = s_flow[ly * MAX_TILE + lx];
-      int32_t c = s_cost[ly * MAX_TILE + lx];
-      const int32_t e0 = s_ccost[my_slot];
-      if (e0 < c) {
-        c = e0;
-        f = my_c0;
+    const bool set = c0 != COST_UNSET;
+    uint32_t nf = f0;
+    int32_t nc = c0;
+    if (paired) {
+      // owner: horizontal candidate; helper: vertical candidate (deduplicated
+      // against the horizontal one, which would be evaluated first)
+      const uint32_t cfh = hv ? clamp_flow(px, py, fh) : 0u;
+      const bool useh = hv && !(set && cfh == f0);
+      const uint32_t cfv = vv ? clamp_flow(px, py, fv) : 0u;
+      const bool usev = vv && !(set && cfv == f0) && !(useh && cfv == cfh);
+      int cost = COST_UNSET;
+      if (role == 0 && useh) evaluate(0, lx, ly, px, py, fh, ch, cost);
+      if (role == 1 && usev) evaluate(1, lx, ly, px, py, fv, cv, cost);
+      const int cost_v = __shfl_sync(FULL_MASK, cost, row + 16);
+      if (role == 0 && on) {
+        if (useh && cost < nc) {
+          nc = cost;
+          nf = cfh;
+        }
+        if (usev && cost_v < nc) {
+          nc = cost_v;
+          nf = cfv;
+        }
+        s_flow[ly * T + lx] = nf;
+        s_cost[ly * T + lx] = nc;
       }
-      if (my_nc > 1) {
-        const int32_t e1 = s_ccost[my_slot + 1];
-        if (e1 < c) {
-          c = e1;
-          f = my_c1;
+    } else if (on) {
+      uint32_t first = 0;
+      bool have_first = false;
+#pragma unroll
+      for (int c = 0; c < 2; c++) {
+        const bool ok = c == 0 ? hv : vv;
+        if (!ok) continue;
+        const uint32_t fq = c == 0 ? fh : fv;
+        const uint32_t cf = clamp_flow(px, py, fq);
+        if (set && cf == f0) continue;
+        if (have_first && cf == first) continue;
+        first = cf;
+        have_first = true;
+        int cost;
+        evaluate(c, lx, ly, px, py, fq, c == 0 ? ch : cv, cost);
+        if (cost < nc) {
+          nc = cost;
+          nf = cf;
         }
       }
-      s_flow[ly * MAX_TILE + lx] = f;
-      s_cost[ly * MAX_TILE + lx] = c;
+      s_flow[ly * T + lx] = nf;
+      s_cost[ly * T + lx] = nc;
+    }
+    // the row's last state, identical in the owner and its helper
+    const uint32_t lf = on ? nf : last_f;
+    const int32_t lc = on ? nc : last_c;
+    last_f = __shfl_sync(FULL_MASK, lf, owner);
+    last_c = __shfl_sync(FULL_MASK, lc, owner);
+  }
+  __syncwarp();
+
+  // ---- random search: every lane evaluates the candidates of its own points ----
+  if (cfg.do_rs) {
+    const int Rn = cfg.R * n;
+    for (int i = sl; i < tw * th; i += width) {
+      const int lx = i % tw, ly = i / tw;
+      const uint32_t cur = s_flow[ly * T + lx];
+      const int32_t cc = s_cost[ly * T + lx];
+      if (cc == COST_UNSET) continue;
+      const int gx = x0 + lx, gy = y0 + ly, px = gx * n, py = gy * n;
+      int ox, oy;
+      rs_offset(cfg.seed, P.flow_id, log2n, cfg.s, gx, gy, Rn, ox, oy);
+      const int tgx = clampi(px + flow_dx(cur) + ox, 0, W - 1);
+      const int tgy = clampi(py + flow_dy(cur) + oy, 0, H - 1);
+      const uint32_t cf = pack_flow(tgx - px, tgy - py);
+      if (cf == cur) continue;
+      const Tgt t = locate(px, py, cf);
+      const uint32_t *sc = s_src + (ly + R + 1) * Lt.swp + (lx + R + 1);
+      const int cost = t.win ? lane_full<R>(sc, Lt.swp, s_tgt + (t.ey - toy) * Lt.twp + (t.ex - tox), Lt.twp)
+                             : lane_full<R>(sc, Lt.swp, tbase + (size_t)t.ph * tpw_ + (size_t)t.ey * tpitch + t.ex, tpitch);
+      if (cost < cc) {
+        s_flow[ly * T + lx] = cf;
+        s_cost[ly * T + lx] = cost;
+      }
     }
     __syncwarp();
   }
-  __syncthreads();
 
-  // ---- random search of this pass: one group per point ----
-  if (cfg.do_rs) {
-    const int Rn = cfg.R * n;
-    for (int i = grp; i < tw * th; i += NGROUPS) {
-      const int lx = i % tw, ly = i / tw;
-      const uint32_t f = s_flow[ly * MAX_TILE + lx];
-      const int32_t c = s_cost[ly * MAX_TILE + lx];
-      if (c == COST_UNSET) continue;
-      const int gx = x0 + lx, gy = y0 + ly, px = gx * n, py = gy * n;
-      int ox, oy;
-      rs_offset(cfg.seed, P.flow_id, P.src.log2n, cfg.s, gx, gy, Rn, ox, oy);
-      const int tgx = clampi(px + flow_dx(f) + ox, 0, W - 1), tgy = clampi(py + flow_dy(f) + oy, 0, H - 1);
-      const uint32_t cf = pack_flow(tgx - px, tgy - py);
-      if (cf == f) continue;
-      const int cost = group_cost<R>(s_src + (ly + R) * SWP + (lx + R), SWP,
-                                     plane_centre(P.tgt, tgx, tgy), P.tgt.pitch, l16, gmask);
-      if (l16 == 0 && cost < c) {
-        s_flow[ly * MAX_TILE + lx] = cf;
-        s_cost[ly * MAX_TILE + lx] = cost;
-      }
-    }
-    __syncthreads();
-  }
-
-  for (int i = tid; i < tw * th; i += PASS_THREADS) {
+  for (int i = sl; i < tw * th; i += width) {
     const int lx = i % tw, ly = i / tw;
     const size_t g = (size_t)(y0 + ly) * Gx + x0 + lx;
-    fout[g] = s_flow[ly * MAX_TILE + lx];
-    cout[g] = s_cost[ly * MAX_TILE + lx];
+    fout[g] = s_flow[ly * T + lx];
+    cout[g] = s_cost[ly * T + lx];
   }
+}
+
+// One side stream per device, created on first use, lets problems of a second
+// patch radius (a separate kernel instantiation) run concurrently with the first:
+// fork with an event recorded on the caller's stream, join with one recorded on
+// the side stream. Both directions are stream-ordered, so the call stays
+// asynchronous and capturable.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+static SideStream g_side[64];
+static std::mutex g_side_mu, g_side_enqueue_mu;
+
+static ff_status side_stream(SideStream **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FF_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_side_mu);
+  SideStream &S = g_side[dev];
+  if (!S.s) {
+    if (cudaStreamCreateWithFlags(&S.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S.join, cudaEventDisableTiming) != cudaSuccess)
+      return FF_ERR_CUDA;
+  }
+  *out = &S;
+  return FF_OK;
+}
+
+// Opt in to more than 48 KB of dynamic shared memory when a tile needs it.
+static ff_status set_pass_smem(int r, size_t bytes) {
+  static size_t done[9] = {0};
+  if (r < 1 || r > 8) return FF_ERR_INVALID_ARG;
+  if (bytes <= done[r]) return FF_OK;
+  cudaError_t e = cudaSuccess;
+  FF_DISPATCH_R(r, e = cudaFuncSetAttribute(k_pass<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)bytes));
+  if (e != cudaSuccess) return FF_ERR_CUDA;
+  done[r] = bytes;
+  return FF_OK;
+}
+
+static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d, int np, int r,
+                              int tile, int n_rs, int R, uint64_t seed, cudaStream_t st) {
+  int maxG = 0, maxT = 0;
+  for (int j = 0; j < np; j++) {
+    const Planes &S = probs[j].src;
+    maxG = max(maxG, S.NX * S.NY);
+    const int half = tile / 2;
+    maxT = max(maxT, ((S.NX + half + tile - 1) / tile) * ((S.NY + half + tile - 1) / tile));
+  }
+  if (probs[0].flow_coarse) {
+    dim3 g((maxG * 16 + 255) / 256, np);
+    FF_DISPATCH_R(r, k_seed<RR><<<g, 256, 0, st>>>(d));
+    FF_CHECK_LAUNCH();
+  }
+  const TileLayout lay(tile, r);
+  const int tpw = 1;
+  const size_t smem = sizeof(uint32_t) * (size_t)lay.words() * PASS_WARPS * tpw;
+  FF_TRY(set_pass_smem(r, smem));
+  for (int s = 0; s < 4; s++) {
+    PassCfg cfg{s, tile, (s < 3 && s < n_rs) ? 1 : 0, R, seed, s == 3, lay.words()};
+    dim3 g((maxT + PASS_WARPS * tpw - 1) / (PASS_WARPS * tpw), np);
+    if (prof_enabled()) prof_begin(st);
+    FF_DISPATCH_R(r, k_pass<RR><<<g, PASS_WARPS * 32, smem, st>>>(d, cfg));
+    FF_CHECK_LAUNCH();
+    if (prof_enabled()) prof_end(st);
+  }
+  return FF_OK;
 }
 
 ff_status run_level(const SearchProblem *probs, SearchProblem *dev, int nprob, int tile, int n_rs,
                     int R, uint64_t seed, cudaStream_t st) {
   if (nprob <= 0) return FF_OK;
   FF_TRY(upload_desc(probs, dev, nprob, st));
-  // problems with different radii run as separate launches of the same kernels
-  int radii[8], nr = 0;
-  for (int i = 0; i < nprob; i++) {
-    bool seen = false;
-    for (int k = 0; k < nr; k++) seen |= radii[k] == probs[i].r;
-    if (!seen) radii[nr++] = probs[i].r;
+  // contiguous runs of equal radius; the first runs on the caller's stream, the
+  // others on the side stream concurrently
+  int starts[16], counts[16], nruns = 0;
+  for (int i = 0; i < nprob;) {
+    int j = i;
+    while (j < nprob && probs[j].r == probs[i].r) j++;
+    if (nruns == 16) return FF_ERR_INVALID_ARG;
+    starts[nruns] = i;
+    counts[nruns++] = j - i;
+    i = j;
   }
-  for (int k = 0; k < nr; k++) {
-    const int r = radii[k];
-    // contiguous runs of problems with this radius
-    for (int i = 0; i < nprob;) {
-      if (probs[i].r != r) {
-        i++;
-        continue;
-      }
-      int j = i;
-      int maxG = 0, maxT = 0;
-      while (j < nprob && probs[j].r == r) {
-        const Planes &S = probs[j].src;
-        maxG = max(maxG, S.NX * S.NY);
-        const int half = tile / 2;
-        maxT = max(maxT, ((S.NX + half + tile - 1) / tile) * ((S.NY + half + tile - 1) / tile));
-        j++;
-      }
-      const SearchProblem *d = dev + i;
-      const int np = j - i;
-      if (probs[i].flow_coarse) {
-        dim3 g((maxG * 16 + 255) / 256, np);
-        FF_DISPATCH_R(r, k_seed<RR><<<g, 256, 0, st>>>(d));
-        FF_CHECK_LAUNCH();
-      }
-      for (int s = 0; s < 4; s++) {
-        PassCfg cfg{s, tile, (s < 3 && s < n_rs) ? 1 : 0, R, seed, s == 3};
-        dim3 g(maxT, np);
-        if (prof_enabled()) prof_begin(st);
-        FF_DISPATCH_R(r, k_pass<RR><<<g, PASS_THREADS, 0, st>>>(d, cfg));
-        FF_CHECK_LAUNCH();
-        if (prof_enabled()) prof_end(st);
-      }
-      i = j;
-    }
+  SideStream *side = nullptr;
+  // the side stream and its events are shared per device: hold the lock while
+  // this call enqueues its fork, launches and join, so calls from several host
+  // threads cannot interleave their event records
+  std::unique_lock<std::mutex> hold(g_side_enqueue_mu, std::defer_lock);
+  if (nruns > 1) {
+    hold.lock();
+    FF_TRY(side_stream(&side));
+    if (cudaEventRecord(side->fork, st) != cudaSuccess ||
+        cudaStreamWaitEvent(side->s, side->fork, 0) != cudaSuccess)
+      return FF_ERR_CUDA;
+  }
+  for (int k = 0; k < nruns; k++) {
+    cudaStream_t use = (k == 0) ? st : side->s;
+    FF_TRY(launch_group(probs + starts[k], dev + starts[k], counts[k], probs[starts[k]].r, tile,
+                        n_rs, R, seed, use));
+  }
+  if (nruns > 1) {
+    if (cudaEventRecord(side->join, side->s) != cudaSuccess ||
+        cudaStreamWaitEvent(st, side->join, 0) != cudaSuccess)
+      return FF_ERR_CUDA;
   }
   return FF_OK;
 }

@@ -35,7 +35,7 @@ class Params(C.Structure):
                [("seed", C.c_uint64)]
 
     def __init__(self, **kw):
-        d = dict(k=3, r=8, r2=6, leaf=8, R=1, eps=5, e=4, s=50, tile=32, n_rs=3, K=0, seed=0)
+        d = dict(k=3, r=8, r2=6, leaf=8, R=1, eps=5, e=4, s=50, tile=16, n_rs=3, K=0, seed=0)
         unknown = set(kw) - set(d)
         if unknown:
             raise TypeError(f"unknown parameters {sorted(unknown)}")
