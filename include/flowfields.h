@@ -212,6 +212,51 @@ ff_status ff_flow_fields(const uint8_t *I1, const uint8_t *I2, int W, int H, con
                          int32_t *err_sum, int32_t *sparse, int32_t *n_sparse, uint8_t *mask,
                          void *ws, size_t ws_bytes, void *stream);
 
+/* Batched form (not in the paper): many pairs, possibly of different sizes, in
+ * one call. Each pair's results equal those of ff_flow_fields on that pair. The
+ * per-image steps run per pair; the kd builds, kd queries and every propagation
+ * pass take the three flows of all pairs in the same launches. The ff_pair array
+ * is host memory; its buffers are device memory as in ff_flow_fields. */
+#define FF_MAX_BATCH 256
+typedef struct ff_pair {
+  const uint8_t *I1, *I2; /* H x W x 3 */
+  int W, H;
+  const int16_t *proposals; /* NULL or as in ff_flow_fields */
+  int16_t *flows;           /* [3][H][W][2] */
+  uint8_t *valid;           /* [H][W] */
+  int32_t *err_sum;         /* [H][W] */
+  int32_t *sparse;          /* [ceil(W/3)*ceil(H/3)][4] */
+  int32_t *n_sparse;        /* device int32 */
+  uint8_t *mask;            /* [H][W] */
+} ff_pair;
+ff_status ff_batch_workspace_size(int npairs, const ff_pair *pairs, const ff_params *p,
+                                  size_t *bytes);
+ff_status ff_flow_fields_batch(int npairs, const ff_pair *pairs, const ff_params *p, void *ws,
+                               size_t ws_bytes, void *stream);
+
+/* CUDA graph of one batch: captures the launches of ff_flow_fields_batch for
+ * these pairs, buffers and workspace (on `stream`, which must not be the legacy
+ * default stream) and instantiates them once; ff_graph_launch replays the whole
+ * batch with one call. The buffers' contents may change between launches, their
+ * addresses may not. ff_graph_kernel_count gives the kernels one launch runs. */
+typedef struct ff_graph ff_graph;
+ff_status ff_graph_create(int npairs, const ff_pair *pairs, const ff_params *p, void *ws,
+                          size_t ws_bytes, void *stream, ff_graph **out);
+ff_status ff_graph_launch(ff_graph *g, void *stream);
+ff_status ff_graph_kernel_count(const ff_graph *g, uint64_t *kernels);
+ff_status ff_graph_destroy(ff_graph *g);
+
+/* Execution parameters: launch shapes that change speed but never results
+ * (the autotuner in the Python package picks them per GPU and workload).
+ * Process-wide; set them between calls, not while work is being enqueued.
+ *   pass_warps  tiles (one warp each) per CTA of the propagation kernel, 1..8 */
+typedef struct ff_exec_params {
+  int32_t pass_warps;
+  int32_t reserved[7];
+} ff_exec_params;
+ff_status ff_set_exec_params(const ff_exec_params *e);
+ff_status ff_get_exec_params(ff_exec_params *e);
+
 /* Device-side status word kept at the start of a workspace: 0 when every
  * device check passed, else an error code with the grid coordinate where it was
  * raised. Synchronises `stream`, then copies 16 bytes device->host. */

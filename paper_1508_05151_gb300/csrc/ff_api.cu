@@ -6,6 +6,7 @@
 // radius, seeding and passes take an array of problems and index it with
 // blockIdx.y, so one pair costs the same number of launches as one flow.
 #include <atomic>
+#include <utility>
 #include <vector>
 
 #include "ff_internal.cuh"
@@ -17,6 +18,9 @@ static std::atomic<uint64_t> g_launches{0};
 static bool g_prof = false;
 static std::vector<cudaEvent_t> g_ev;  // pairs (begin, end)
 static size_t g_ev_used = 0;
+
+static ff_exec_params g_exec = {4, {0, 0, 0, 0, 0, 0, 0}};
+const ff_exec_params &exec_params() { return g_exec; }
 
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 bool prof_enabled() { return g_prof; }
@@ -84,14 +88,11 @@ struct PairPlan {
   uint32_t *fa[3], *fb[3];
   int32_t *ca[3], *cb[3];
   void *filter_scratch;
-  KdBuild *d_kd;
-  KdQuery *d_q;
-  SearchProblem *d_sp;
 };
 
-static void plan_pair(Arena &a, int W, int H, const ff_params *p, PairPlan &P) {
+// Per-pair scratch (everything but the workspace header and the descriptors).
+static void plan_pair_body(Arena &a, int W, int H, const ff_params *p, PairPlan &P) {
   const size_t N = (size_t)W * H;
-  a.take<char>(WS_HEADER);
   for (int f = 0; f < 2; f++)
     for (int lv = 0; lv <= p->k; lv++) P.planes[f][lv] = a.take<uint32_t>(planes_words(W, H, 1 << lv));
   P.sm = a.take<uint8_t>(N * 3);
@@ -124,9 +125,204 @@ static void plan_pair(Arena &a, int W, int H, const ff_params *p, PairPlan &P) {
     P.cb[j] = a.take<int32_t>(N);
   }
   P.filter_scratch = a.take<char>(filter_scratch_bytes(W, H));
-  P.d_kd = a.take<KdBuild>(3);
-  P.d_q = a.take<KdQuery>(3);
-  P.d_sp = a.take<SearchProblem>(3 * MAXLV);
+}
+
+// Workspace of a batch: header, every pair's scratch, then the descriptor
+// arrays of the batched launches (3 flows per pair).
+struct BatchDesc {
+  KdBuild *d_kd;
+  KdQuery *d_q;
+  SearchProblem *d_sp;
+};
+static BatchDesc plan_batch(Arena &a, int np, const int *Ws, const int *Hs, const ff_params *p,
+                            PairPlan *plans) {
+  a.take<char>(WS_HEADER);
+  for (int i = 0; i < np; i++) plan_pair_body(a, Ws[i], Hs[i], p, plans[i]);
+  BatchDesc d;
+  d.d_kd = a.take<KdBuild>(3 * (size_t)np);
+  d.d_q = a.take<KdQuery>(3 * (size_t)np);
+  d.d_sp = a.take<SearchProblem>(3 * (size_t)np * MAXLV);
+  return d;
+}
+
+// One image pair's device buffers.
+struct PairIO {
+  const uint8_t *I1, *I2;
+  int W, H;
+  const int16_t *proposals;
+  int16_t *flows;
+  uint8_t *valid;
+  int32_t *err_sum, *sparse, *n_sparse;
+  uint8_t *mask;
+};
+
+// The whole path for np pairs (Fig. 2). Per-image kernels (smoothing, census,
+// features, filtering) run per pair; the kd builds, kd queries and every search
+// level take the three flows of all pairs in the same launches, problems of
+// one patch radius per launch, the two radii concurrently.
+static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *ws, size_t ws_bytes,
+                           cudaStream_t st) {
+  std::vector<int> Ws(np), Hs(np);
+  for (int i = 0; i < np; i++) {
+    Ws[i] = io[i].W;
+    Hs[i] = io[i].H;
+  }
+  std::vector<PairPlan> plans(np);
+  Arena a(ws, ws_bytes);
+  const BatchDesc bd = plan_batch(a, np, Ws.data(), Hs.data(), p, plans.data());
+  if (!a.fits()) return FF_ERR_WORKSPACE;
+  FF_TRY(clear_status(ws, st));
+  const int k = p->k, ntop = 1 << k;
+  const int srcf[3] = {0, 1, 1}, tgtf[3] = {1, 0, 0}, rad[3] = {p->r, p->r, p->r2};
+
+  // smoothed images, census planes and WHT features of every pair
+  for (int i = 0; i < np; i++) {
+    const PairPlan &P = plans[i];
+    const int W = io[i].W, H = io[i].H;
+    const uint8_t *img[2] = {io[i].I1, io[i].I2};
+    for (int f = 0; f < 2; f++)
+      for (int lv = 0; lv <= k; lv++) {
+        const int n = 1 << lv;
+        const uint8_t *src = img[f];
+        if (n > 1) {
+          FF_TRY(launch_smooth(img[f], W, H, n, P.sm, P.smooth_scratch, st));
+          src = P.sm;
+        }
+        FF_TRY(launch_census(src, W, H, n, P.census, st));
+        FF_TRY(launch_planes(P.census, make_planes(P.planes[f][lv], W, H, n), st));
+      }
+    for (int j = 0; j < 3; j++) {
+      FF_TRY(launch_features(img[tgtf[j]], W, H, rad[j], nullptr, 0, 1, P.feat[j], st));
+      FF_TRY(launch_features(img[srcf[j]], W, H, rad[j], nullptr, 0, ntop, P.qfeat[j], st));
+    }
+  }
+
+  // kd trees of all flows of all pairs
+  std::vector<KdBuild> trees(3 * (size_t)np);
+  for (int i = 0; i < np; i++)
+    for (int j = 0; j < 3; j++) trees[3 * i + j] = plans[i].kd[j];
+  FF_TRY(launch_kd_build(trees.data(), bd.d_kd, 3 * np, st));
+
+  // problem order: all flows with radius r (forward, backward r) of every pair,
+  // then the backward r2 flows, so each radius is one contiguous run
+  std::vector<int> order_pair, order_flow;
+  for (int i = 0; i < np; i++)
+    for (int j = 0; j < 2; j++) {
+      order_pair.push_back(i);
+      order_flow.push_back(j);
+    }
+  for (int i = 0; i < np; i++) {
+    order_pair.push_back(i);
+    order_flow.push_back(2);
+  }
+  const int nprob = (int)order_pair.size();  // 3 * np
+
+  std::vector<KdQuery> q(nprob);
+  for (int t = 0; t < nprob; t++) {
+    const int i = order_pair[t], j = order_flow[t];
+    const PairPlan &P = plans[i];
+    const int W = io[i].W, H = io[i].H;
+    KdQuery &Q = q[t];
+    Q = KdQuery{};
+    Q.perm = P.perm[j];
+    Q.split_dim = P.split_dim[j];
+    Q.split_val = P.split_val[j];
+    Q.N = W * H;
+    Q.D = P.kd[j].D;
+    Q.leaf = p->leaf;
+    Q.qfeat = P.qfeat[j];
+    Q.src = make_planes(P.planes[srcf[j]][k], W, H, ntop);
+    Q.tgt = make_planes(P.planes[tgtf[j]][k], W, H, ntop);
+    Q.r = rad[j];
+    Q.proposals = (j == 0 && p->K > 0) ? (const uint32_t *)io[i].proposals : nullptr;
+    Q.K = (j == 0) ? p->K : 0;
+    Q.flow = P.fa[j];
+    Q.cost = P.ca[j];
+  }
+  for (int t0 = 0; t0 < nprob;) {  // one launch per run of equal radius
+    int t1 = t0;
+    while (t1 < nprob && q[t1].r == q[t0].r) t1++;
+    FF_TRY(launch_kd_query(q.data() + t0, bd.d_q + t0, t1 - t0, st));
+    t0 = t1;
+  }
+
+  // levels n = 2^k .. 1; the state alternates between the two buffers per level
+  std::vector<uint32_t *> cur(nprob), oth(nprob);
+  std::vector<int32_t *> ccur(nprob), coth(nprob);
+  for (int t = 0; t < nprob; t++) {
+    const PairPlan &P = plans[order_pair[t]];
+    const int j = order_flow[t];
+    cur[t] = P.fa[j];
+    oth[t] = P.fb[j];
+    ccur[t] = P.ca[j];
+    coth[t] = P.cb[j];
+  }
+  std::vector<SearchProblem> sp(nprob);
+  for (int lv = k; lv >= 0; lv--) {
+    const int n = 1 << lv;
+    for (int t = 0; t < nprob; t++) {
+      const int i = order_pair[t], j = order_flow[t];
+      const PairPlan &P = plans[i];
+      const int W = io[i].W, H = io[i].H;
+      SearchProblem &s = sp[t];
+      s = SearchProblem{};
+      s.src = make_planes(P.planes[srcf[j]][lv], W, H, n);
+      s.tgt = make_planes(P.planes[tgtf[j]][lv], W, H, n);
+      s.r = rad[j];
+      s.flow_id = j;
+      if (lv == k) {
+        s.flow_coarse = nullptr;
+        s.flow_a = cur[t];
+        s.cost_a = ccur[t];
+        s.flow_b = oth[t];
+        s.cost_b = coth[t];
+      } else {  // seed from the coarser state (in cur) into the other buffer
+        s.flow_coarse = cur[t];
+        s.flow_a = oth[t];
+        s.cost_a = coth[t];
+        s.flow_b = cur[t];
+        s.cost_b = ccur[t];
+      }
+      if (lv == 0) {
+        s.flow_final = (uint32_t *)(io[i].flows + 2 * (size_t)W * H * j);
+        s.cost_final = s.cost_a;
+      }
+    }
+    FF_TRY(run_level(sp.data(), bd.d_sp + (size_t)nprob * lv, nprob, p->tile, p->n_rs, p->R,
+                     p->seed, st));
+    if (lv != k)
+      for (int t = 0; t < nprob; t++) {
+        std::swap(cur[t], oth[t]);
+        std::swap(ccur[t], coth[t]);
+      }
+  }
+
+  for (int i = 0; i < np; i++) {
+    const size_t N = (size_t)io[i].W * io[i].H;
+    FF_TRY(launch_filter((const uint32_t *)io[i].flows, (const uint32_t *)(io[i].flows + 2 * N),
+                         (const uint32_t *)(io[i].flows + 4 * N), io[i].W, io[i].H, p->eps, p->e,
+                         p->s, io[i].valid, io[i].err_sum, io[i].sparse, io[i].n_sparse,
+                         io[i].mask, plans[i].filter_scratch, st));
+  }
+  return FF_OK;
+}
+
+static size_t batch_ws_bytes(int np, const int *Ws, const int *Hs, const ff_params *p) {
+  std::vector<PairPlan> plans(np);
+  Arena a;
+  plan_batch(a, np, Ws, Hs, p, plans.data());
+  return a.off;
+}
+
+static ff_status check_pair(const PairIO &io, const ff_params *p) {
+  FF_TRY(check_shape(io.W, io.H));
+  if (!io.I1 || !io.I2 || !io.flows || !io.valid || !io.err_sum || !io.sparse || !io.n_sparse ||
+      !io.mask)
+    return FF_ERR_INVALID_ARG;
+  if (!aligned(io.flows, 4) || (p->K > 0 && !io.proposals) ||
+      (io.proposals && !aligned(io.proposals, 4)))
+    return FF_ERR_INVALID_ARG;
+  return FF_OK;
 }
 
 }  // namespace ff
@@ -172,10 +368,7 @@ ff_status ff_workspace_size(int W, int H, const ff_params *p, size_t *bytes) {
   FF_TRY(check_params(p));
   FF_TRY(check_shape(W, H));
   if (!bytes) return FF_ERR_INVALID_ARG;
-  Arena a;
-  PairPlan P;
-  plan_pair(a, W, H, p, P);
-  *bytes = a.off;
+  *bytes = batch_ws_bytes(1, &W, &H, p);
   return FF_OK;
 }
 
@@ -384,122 +577,120 @@ ff_status ff_flow_fields(const uint8_t *I1, const uint8_t *I2, int W, int H, con
                          const int16_t *proposals, int16_t *flows, uint8_t *valid,
                          int32_t *err_sum, int32_t *sparse, int32_t *n_sparse, uint8_t *mask,
                          void *ws, size_t ws_bytes, void *stream) {
-  FF_TRY(check_shape(W, H));
   FF_TRY(check_params(p));
-  if (!I1 || !I2 || !flows || !valid || !err_sum || !sparse || !n_sparse || !mask)
-    return FF_ERR_INVALID_ARG;
-  if (!aligned(flows, 4) || (p->K > 0 && !proposals) || (proposals && !aligned(proposals, 4)))
-    return FF_ERR_INVALID_ARG;
+  const PairIO io{I1, I2, W, H, proposals, flows, valid, err_sum, sparse, n_sparse, mask};
+  FF_TRY(check_pair(io, p));
+  FF_TRY(check_ws(ws, ws_bytes, batch_ws_bytes(1, &W, &H, p)));
+  return run_pairs(1, &io, p, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+static ff_status batch_io(int npairs, const ff_pair *pairs, const ff_params *p,
+                          std::vector<PairIO> &io) {
+  FF_TRY(check_params(p));
+  if (npairs < 1 || npairs > FF_MAX_BATCH || !pairs) return FF_ERR_INVALID_ARG;
+  io.resize(npairs);
+  for (int i = 0; i < npairs; i++) {
+    const ff_pair &q = pairs[i];
+    io[i] = PairIO{q.I1, q.I2, q.W, q.H, q.proposals, q.flows, q.valid, q.err_sum, q.sparse,
+                   q.n_sparse, q.mask};
+    FF_TRY(check_pair(io[i], p));
+  }
+  return FF_OK;
+}
+
+ff_status ff_batch_workspace_size(int npairs, const ff_pair *pairs, const ff_params *p,
+                                  size_t *bytes) {
+  FF_TRY(check_params(p));
+  if (npairs < 1 || npairs > FF_MAX_BATCH || !pairs || !bytes) return FF_ERR_INVALID_ARG;
+  std::vector<int> Ws(npairs), Hs(npairs);
+  for (int i = 0; i < npairs; i++) {
+    FF_TRY(check_shape(pairs[i].W, pairs[i].H));
+    Ws[i] = pairs[i].W;
+    Hs[i] = pairs[i].H;
+  }
+  *bytes = batch_ws_bytes(npairs, Ws.data(), Hs.data(), p);
+  return FF_OK;
+}
+
+ff_status ff_flow_fields_batch(int npairs, const ff_pair *pairs, const ff_params *p, void *ws,
+                               size_t ws_bytes, void *stream) {
+  std::vector<PairIO> io;
+  FF_TRY(batch_io(npairs, pairs, p, io));
   size_t need;
-  FF_TRY(ff_workspace_size(W, H, p, &need));
+  FF_TRY(ff_batch_workspace_size(npairs, pairs, p, &need));
+  FF_TRY(check_ws(ws, ws_bytes, need));
+  return run_pairs(npairs, io.data(), p, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+struct ff_graph {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  size_t kernels;
+};
+
+ff_status ff_graph_create(int npairs, const ff_pair *pairs, const ff_params *p, void *ws,
+                          size_t ws_bytes, void *stream, ff_graph **out) {
+  if (!out) return FF_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::vector<PairIO> io;
+  FF_TRY(batch_io(npairs, pairs, p, io));
+  size_t need;
+  FF_TRY(ff_batch_workspace_size(npairs, pairs, p, &need));
   FF_TRY(check_ws(ws, ws_bytes, need));
   cudaStream_t st = (cudaStream_t)stream;
-  Arena a(ws, ws_bytes);
-  PairPlan P;
-  plan_pair(a, W, H, p, P);
-  FF_TRY(clear_status(ws, st));
-  const size_t N = (size_t)W * H;
-  const int k = p->k, ntop = 1 << k;
-
-  // smoothed images, census and phase planes of both frames at every level
-  const uint8_t *img[2] = {I1, I2};
-  for (int f = 0; f < 2; f++)
-    for (int lv = 0; lv <= k; lv++) {
-      const int n = 1 << lv;
-      const uint8_t *src = img[f];
-      if (n > 1) {
-        FF_TRY(launch_smooth(img[f], W, H, n, P.sm, P.smooth_scratch, st));
-        src = P.sm;
-      }
-      FF_TRY(launch_census(src, W, H, n, P.census, st));
-      FF_TRY(launch_planes(P.census, make_planes(P.planes[f][lv], W, H, n), st));
+  if (!st) return FF_ERR_INVALID_ARG;  // the legacy default stream cannot be captured
+  const bool prof = g_prof;
+  g_prof = false;  // timing events cannot be read back from a graph
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    g_prof = prof;
+    return FF_ERR_CUDA;
+  }
+  const ff_status rs = run_pairs(npairs, io.data(), p, ws, ws_bytes, st);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+  g_prof = prof;
+  if (rs != FF_OK || ce != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    (void)cudaGetLastError();
+    return rs != FF_OK ? rs : FF_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return FF_ERR_CUDA;
+  }
+  size_t nn = 0;
+  cudaGraphGetNodes(graph, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  size_t kern = 0;
+  if (nn && cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+    for (size_t i = 0; i < nn; i++) {
+      cudaGraphNodeType ty;
+      if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) kern++;
     }
+  *out = new ff_graph{graph, exec, kern};
+  return FF_OK;
+}
 
-  // flow j: (source frame, target frame, radius): forward, backward r, backward r2
-  const int srcf[3] = {0, 1, 1}, tgtf[3] = {1, 0, 0}, rad[3] = {p->r, p->r, p->r2};
-  for (int j = 0; j < 3; j++) {
-    FF_TRY(launch_features(img[tgtf[j]], W, H, rad[j], nullptr, 0, 1, P.feat[j], st));
-    FF_TRY(launch_features(img[srcf[j]], W, H, rad[j], nullptr, 0, ntop, P.qfeat[j], st));
-  }
-  FF_TRY(launch_kd_build(P.kd, P.d_kd, 3, st));
+ff_status ff_graph_launch(ff_graph *g, void *stream) {
+  if (!g) return FF_ERR_INVALID_ARG;
+  if (cudaGraphLaunch(g->exec, (cudaStream_t)stream) != cudaSuccess) return FF_ERR_CUDA;
+  count_launch((int)g->kernels);
+  return FF_OK;
+}
 
-  KdQuery q[3];
-  for (int j = 0; j < 3; j++) {
-    q[j] = KdQuery{};
-    q[j].perm = P.perm[j];
-    q[j].split_dim = P.split_dim[j];
-    q[j].split_val = P.split_val[j];
-    q[j].N = (int)N;
-    q[j].D = P.kd[j].D;
-    q[j].leaf = p->leaf;
-    q[j].qfeat = P.qfeat[j];
-    q[j].src = make_planes(P.planes[srcf[j]][k], W, H, ntop);
-    q[j].tgt = make_planes(P.planes[tgtf[j]][k], W, H, ntop);
-    q[j].r = rad[j];
-    q[j].proposals = (j == 0 && p->K > 0) ? (const uint32_t *)proposals : nullptr;
-    q[j].K = (j == 0) ? p->K : 0;
-    q[j].flow = P.fa[j];
-    q[j].cost = P.ca[j];
-  }
-  if (p->r == p->r2) {
-    FF_TRY(launch_kd_query(q, P.d_q, 3, st));
-  } else {
-    FF_TRY(launch_kd_query(q, P.d_q, 2, st));
-    FF_TRY(launch_kd_query(q + 2, P.d_q + 2, 1, st));
-  }
+ff_status ff_graph_kernel_count(const ff_graph *g, uint64_t *kernels) {
+  if (!g || !kernels) return FF_ERR_INVALID_ARG;
+  *kernels = g->kernels;
+  return FF_OK;
+}
 
-  // levels n = 2^k .. 1; the state alternates between the two buffers per level
-  uint32_t *cur[3], *oth[3];
-  int32_t *ccur[3], *coth[3];
-  for (int j = 0; j < 3; j++) {
-    cur[j] = P.fa[j];
-    oth[j] = P.fb[j];
-    ccur[j] = P.ca[j];
-    coth[j] = P.cb[j];
-  }
-  for (int lv = k; lv >= 0; lv--) {
-    const int n = 1 << lv;
-    SearchProblem sp[3];
-    for (int j = 0; j < 3; j++) {
-      SearchProblem &s = sp[j];
-      s = SearchProblem{};
-      s.src = make_planes(P.planes[srcf[j]][lv], W, H, n);
-      s.tgt = make_planes(P.planes[tgtf[j]][lv], W, H, n);
-      s.r = rad[j];
-      s.flow_id = j;
-      if (lv == k) {
-        s.flow_coarse = nullptr;
-        s.flow_a = cur[j];
-        s.cost_a = ccur[j];
-        s.flow_b = oth[j];
-        s.cost_b = coth[j];
-      } else {  // seed from the coarser state (in cur) into the other buffer
-        s.flow_coarse = cur[j];
-        s.flow_a = oth[j];
-        s.cost_a = coth[j];
-        s.flow_b = cur[j];
-        s.cost_b = ccur[j];
-      }
-      if (lv == 0) {
-        s.flow_final = (uint32_t *)(flows + 2 * N * j);
-        s.cost_final = s.cost_a;
-      }
-    }
-    FF_TRY(run_level(sp, P.d_sp + 3 * lv, 3, p->tile, p->n_rs, p->R, p->seed, st));
-    if (lv != k)
-      for (int j = 0; j < 3; j++) {
-        uint32_t *t = cur[j];
-        cur[j] = oth[j];
-        oth[j] = t;
-        int32_t *c = ccur[j];
-        ccur[j] = coth[j];
-        coth[j] = c;
-      }
-  }
-
-  return launch_filter((const uint32_t *)flows, (const uint32_t *)(flows + 2 * N),
-                       (const uint32_t *)(flows + 4 * N), W, H, p->eps, p->e, p->s, valid,
-                       err_sum, sparse, n_sparse, mask, P.filter_scratch, st);
+ff_status ff_graph_destroy(ff_graph *g) {
+  if (!g) return FF_OK;
+  cudaGraphExecDestroy(g->exec);
+  cudaGraphDestroy(g->graph);
+  delete g;
+  return FF_OK;
 }
 
 ff_status ff_device_status(const void *ws, uint32_t *code, int32_t *x, int32_t *y, void *stream) {
@@ -512,6 +703,18 @@ ff_status ff_device_status(const void *ws, uint32_t *code, int32_t *x, int32_t *
   if (x) *x = h.x;
   if (y) *y = h.y;
   return h.code == DEV_OK ? FF_OK : FF_ERR_DEVICE;
+}
+
+ff_status ff_set_exec_params(const ff_exec_params *e) {
+  if (!e || e->pass_warps < 1 || e->pass_warps > 8) return FF_ERR_INVALID_ARG;
+  g_exec = *e;
+  return FF_OK;
+}
+
+ff_status ff_get_exec_params(ff_exec_params *e) {
+  if (!e) return FF_ERR_INVALID_ARG;
+  *e = g_exec;
+  return FF_OK;
 }
 
 ff_status ff_profile_enable(int on) {

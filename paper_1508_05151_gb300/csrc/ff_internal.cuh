@@ -207,6 +207,10 @@ struct Arena {
   bool fits() const { return base == nullptr || off <= cap; }
 };
 
+// ---------------------------------------------------- execution parameters ---
+// Launch shapes that do not change results (set by the autotuner).
+const ff_exec_params &exec_params();
+
 // ------------------------------------------------------- launch accounting ---
 void count_launch(int n);
 bool prof_enabled();

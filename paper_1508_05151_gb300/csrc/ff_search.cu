@@ -68,7 +68,7 @@ struct PassCfg {
   int words_per_tile;  // shared memory words of one tile
 };
 
-constexpr int PASS_WARPS = 4;
+constexpr int PASS_MAX_WARPS = 8;  // tiles per CTA: an execution parameter, 1..8
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
 // Shared-memory layout of one tile (all sizes in 32-bit words).
@@ -138,7 +138,7 @@ __device__ __forceinline__ int lane_full(const uint32_t *sc, int swp, const uint
 }
 
 template <int R>
-__global__ void __launch_bounds__(PASS_WARPS * 32) k_pass(const SearchProblem *probs, PassCfg cfg) {
+__global__ void __launch_bounds__(PASS_MAX_WARPS * 32) k_pass(const SearchProblem *probs, PassCfg cfg) {
   extern __shared__ uint32_t smem[];
   const SearchProblem &P = probs[blockIdx.y];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(PASS_WARPS * 32) k_pass(const SearchProblem *p
   const int W = P.src.W, H = P.src.H;
   const int T = cfg.tile, off = (cfg.s & 1) * (T >> 1);
   const int ntx = (Gx + off + T - 1) / T, nty = (Gy + off + T - 1) / T;
-  const int tile = (blockIdx.x * PASS_WARPS + warp) * tpw + sub;
+  const int tile = (blockIdx.x * (blockDim.x >> 5) + warp) * tpw + sub;
   const bool live = tile < ntx * nty;
   if (!__any_sync(FULL_MASK, live)) return;  // whole warp; no block barriers below
   const int tx = live ? tile % ntx : 0, ty = live ? tile / ntx : 0;
@@ -510,14 +510,15 @@ static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d
     FF_CHECK_LAUNCH();
   }
   const TileLayout lay(tile, r);
-  const int tpw = 1;
-  const size_t smem = sizeof(uint32_t) * (size_t)lay.words() * PASS_WARPS * tpw;
+  int pw = exec_params().pass_warps;
+  while (pw > 1 && sizeof(uint32_t) * (size_t)lay.words() * pw > 227u * 1024u) pw--;
+  const size_t smem = sizeof(uint32_t) * (size_t)lay.words() * pw;
   FF_TRY(set_pass_smem(r, smem));
   for (int s = 0; s < 4; s++) {
     PassCfg cfg{s, tile, (s < 3 && s < n_rs) ? 1 : 0, R, seed, s == 3, lay.words()};
-    dim3 g((maxT + PASS_WARPS * tpw - 1) / (PASS_WARPS * tpw), np);
+    dim3 g((maxT + pw - 1) / pw, np);
     if (prof_enabled()) prof_begin(st);
-    FF_DISPATCH_R(r, k_pass<RR><<<g, PASS_WARPS * 32, smem, st>>>(d, cfg));
+    FF_DISPATCH_R(r, k_pass<RR><<<g, pw * 32, smem, st>>>(d, cfg));
     FF_CHECK_LAUNCH();
     if (prof_enabled()) prof_end(st);
   }

@@ -28,6 +28,19 @@ class FFError(RuntimeError):
         self.code = code
 
 
+class Pair(C.Structure):
+    """ff_pair: one image pair of a batch (device pointers)."""
+    _fields_ = [("I1", C.c_void_p), ("I2", C.c_void_p), ("W", C.c_int), ("H", C.c_int),
+                ("proposals", C.c_void_p), ("flows", C.c_void_p), ("valid", C.c_void_p),
+                ("err_sum", C.c_void_p), ("sparse", C.c_void_p), ("n_sparse", C.c_void_p),
+                ("mask", C.c_void_p)]
+
+
+class ExecParams(C.Structure):
+    """ff_exec_params: launch shapes that never change results."""
+    _fields_ = [("pass_warps", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
 class Params(C.Structure):
     """ff_params; defaults are the Sintel preset of Sec. 4."""
     _fields_ = [(n, C.c_int32) for n in
@@ -84,6 +97,14 @@ def lib():
             "ff_consistency_filter_static": ([vp, vp, vp, i32, i32, P, vp, vp, vp, vp, vp, vp],
                                              i32),
             "ff_flow_fields": ([vp, vp, i32, i32, P, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], i32),
+            "ff_batch_workspace_size": ([i32, C.POINTER(Pair), P, C.POINTER(sz)], i32),
+            "ff_flow_fields_batch": ([i32, C.POINTER(Pair), P, vp, sz, vp], i32),
+            "ff_graph_create": ([i32, C.POINTER(Pair), P, vp, sz, vp, C.POINTER(vp)], i32),
+            "ff_graph_launch": ([vp, vp], i32),
+            "ff_graph_kernel_count": ([vp, C.POINTER(u64)], i32),
+            "ff_graph_destroy": ([vp], i32),
+            "ff_set_exec_params": ([C.POINTER(ExecParams)], i32),
+            "ff_get_exec_params": ([C.POINTER(ExecParams)], i32),
             "ff_device_status": ([vp, C.POINTER(C.c_uint32), C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int32), vp], i32),
             "ff_profile_enable": ([i32], i32),
@@ -322,3 +343,105 @@ def profile_read():
     n, ms, pn = C.c_uint64(), C.c_double(), C.c_uint64()
     _check("ff_profile_read", lib().ff_profile_read(C.byref(n), C.byref(ms), C.byref(pn)))
     return dict(launches=n.value, prop_ms=ms.value, prop_launches=pn.value)
+
+
+def set_exec_params(pass_warps=4):
+    e = ExecParams(pass_warps=pass_warps)
+    _check("ff_set_exec_params", lib().ff_set_exec_params(C.byref(e)))
+
+
+def get_exec_params():
+    e = ExecParams()
+    _check("ff_get_exec_params", lib().ff_get_exec_params(C.byref(e)))
+    return dict(pass_warps=e.pass_warps)
+
+
+class FlowFieldsBatch:
+    """Batched form: many pairs of (possibly) different sizes per call.
+
+    ``sizes``: list of (W, H). ``run(frames)`` takes a list of (I1, I2) uint8 CUDA
+    tensors and returns one result dict per pair (views of preallocated output
+    tensors). With ``graph=True`` the first run captures the whole batch into a
+    CUDA graph bound to the input buffers given by ``bind`` and later runs replay
+    it; inputs are then copied into those buffers.
+    """
+
+    def __init__(self, sizes, params=None, device="cuda", graph=False):
+        self.sizes = [tuple(map(int, s)) for s in sizes]
+        self.params = _params(params)
+        self.device = torch.device(device)
+        d = self.device
+        self.out = []
+        self.inp = []
+        for (W, H) in self.sizes:
+            nb = ((W + 2) // 3) * ((H + 2) // 3)
+            self.out.append(dict(
+                flows=torch.empty((3, H, W, 2), dtype=torch.int16, device=d),
+                valid=torch.empty((H, W), dtype=torch.uint8, device=d),
+                err_sum=torch.empty((H, W), dtype=torch.int32, device=d),
+                sparse=torch.empty((nb, 4), dtype=torch.int32, device=d),
+                n_sparse=torch.zeros(1, dtype=torch.int32, device=d),
+                mask=torch.empty((H, W), dtype=torch.uint8, device=d)))
+            self.inp.append((torch.empty((H, W, 3), dtype=torch.uint8, device=d),
+                             torch.empty((H, W, 3), dtype=torch.uint8, device=d)))
+        self.pairs = (Pair * len(self.sizes))()
+        self._fill_pairs(self.inp)
+        n = C.c_size_t()
+        _check("ff_batch_workspace_size", lib().ff_batch_workspace_size(
+            len(self.sizes), self.pairs, C.byref(self.params), C.byref(n)))
+        self.ws = _ws(n.value, d)
+        self.use_graph = graph
+        self.graph = None
+        # graphs are captured and replayed on a stream of their own (the legacy
+        # default stream cannot be captured), ordered after the caller's stream
+        self.stream = torch.cuda.Stream(device=d) if graph else None
+
+    def _fill_pairs(self, frames, proposals=None):
+        for i, ((W, H), (a, b)) in enumerate(zip(self.sizes, frames)):
+            o = self.out[i]
+            if tuple(a.shape[:2]) != (H, W) or tuple(b.shape[:2]) != (H, W):
+                raise ValueError(f"pair {i}: expected {W}x{H}")
+            pr = proposals[i] if proposals is not None else None
+            self.pairs[i] = Pair(a.data_ptr(), b.data_ptr(), W, H,
+                                 pr.data_ptr() if pr is not None else None,
+                                 o["flows"].data_ptr(), o["valid"].data_ptr(),
+                                 o["err_sum"].data_ptr(), o["sparse"].data_ptr(),
+                                 o["n_sparse"].data_ptr(), o["mask"].data_ptr())
+
+    def run(self, frames, proposals=None):
+        wp, wn = _ws_ptr(self.ws)
+        if self.use_graph:
+            if proposals is not None:
+                raise ValueError("graph mode takes no proposals")
+            caller = torch.cuda.current_stream()
+            self.stream.wait_stream(caller)
+            with torch.cuda.stream(self.stream):
+                for (a, b), (da, db) in zip(frames, self.inp):
+                    da.copy_(a, non_blocking=True)
+                    db.copy_(b, non_blocking=True)
+                if self.graph is None:
+                    self._fill_pairs(self.inp)
+                    g = C.c_void_p()
+                    _check("ff_graph_create", lib().ff_graph_create(
+                        len(self.sizes), self.pairs, C.byref(self.params), wp, wn, _stream(),
+                        C.byref(g)))
+                    self.graph = g
+                _check("ff_graph_launch", lib().ff_graph_launch(self.graph, _stream()))
+            caller.wait_stream(self.stream)
+        else:
+            self._fill_pairs(frames, proposals)
+            _check("ff_flow_fields_batch", lib().ff_flow_fields_batch(
+                len(self.sizes), self.pairs, C.byref(self.params), wp, wn, _stream()))
+        return self.out
+
+    def graph_kernels(self):
+        if self.graph is None:
+            return 0
+        k = C.c_uint64()
+        _check("ff_graph_kernel_count", lib().ff_graph_kernel_count(self.graph, C.byref(k)))
+        return k.value
+
+    def __del__(self):
+        if getattr(self, "graph", None) is not None and _lib is not None:
+            _lib.ff_graph_destroy(self.graph)
+            self.graph = None

@@ -111,3 +111,35 @@ def test_kd_depth_matches_definition(L):
         D = d.value
         assert -(-N // (1 << D)) <= leaf
         assert D == 0 or -(-N // (1 << (D - 1))) > leaf
+
+
+def test_batch_argument_checks(L):
+    p = ffapi.Params()
+    sz = C.c_size_t()
+    pairs = (ffapi.Pair * 2)()
+    for i in range(2):
+        pairs[i] = ffapi.Pair(0x1000, 0x1000, 128, 96, None, 0x1000, 0x1000, 0x1000, 0x1000,
+                              0x1000, 0x1000)
+    assert L.ff_batch_workspace_size(2, pairs, C.byref(p), C.byref(sz)) == 0
+    one = C.c_size_t()
+    L.ff_workspace_size(128, 96, C.byref(p), C.byref(one))
+    assert sz.value > one.value
+    assert L.ff_batch_workspace_size(0, pairs, C.byref(p), C.byref(sz)) == 1
+    assert L.ff_batch_workspace_size(2, None, C.byref(p), C.byref(sz)) == 1
+    pairs[1].W = 0
+    assert L.ff_batch_workspace_size(2, pairs, C.byref(p), C.byref(sz)) == 2
+    pairs[1].W = 128
+    pairs[0].I1 = None
+    assert L.ff_flow_fields_batch(2, pairs, C.byref(p), C.c_void_p(0x100000), 1 << 40, None) == 1
+    g = C.c_void_p()
+    assert L.ff_graph_create(2, pairs, C.byref(p), C.c_void_p(0x100000), 1 << 40, None,
+                             C.byref(g)) == 1
+    assert L.ff_graph_destroy(None) == 0
+
+
+def test_exec_params_checks(L):
+    e = ffapi.ExecParams()
+    assert L.ff_get_exec_params(C.byref(e)) == 0 and 1 <= e.pass_warps <= 8
+    bad = ffapi.ExecParams(pass_warps=9)
+    assert L.ff_set_exec_params(C.byref(bad)) == 1
+    assert L.ff_set_exec_params(None) == 1

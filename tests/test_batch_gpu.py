@@ -1,0 +1,87 @@
+"""Batched form (mixed sizes, one launch set per level), CUDA-graph replay and the
+autotuner's execution parameters: every result equals the single-pair path and
+the CPU oracle bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1508_05151_gb300 import ffapi, synth, tune
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+SIZES = [(128, 96), (97, 71), (160, 120), (64, 48)]
+
+
+def _frames(seed0=0):
+    pairs = [synth.pair_shift(seed0 + i, W=W, H=H, max_shift=(W // 6, H // 6), square=min(24, W, H),
+                              square_move=8) for i, (W, H) in enumerate(SIZES)]
+    frames = [(torch.from_numpy(p["I1"]).cuda(), torch.from_numpy(p["I2"]).cuda()) for p in pairs]
+    return pairs, frames
+
+
+def _same(a, b):
+    torch.cuda.synchronize()
+    for k in ("flows", "valid", "err_sum", "mask", "n_sparse"):
+        assert torch.equal(a[k], b[k]), k
+    n = int(a["n_sparse"].item())
+    assert torch.equal(a["sparse"][:n], b["sparse"][:n])
+
+
+def test_batch_equals_single_pairs_and_oracle():
+    pairs, frames = _frames(10)
+    batch = ffapi.FlowFieldsBatch(SIZES)
+    outs = batch.run(frames)
+    torch.cuda.synchronize()
+    for i, ((W, H), (a, b)) in enumerate(zip(SIZES, frames)):
+        single = ffapi.FlowFields(W, H).run(a, b)
+        _same(outs[i], single)
+    for i in (0, 2):  # oracle on two of the pairs
+        ref = O.flow_fields(pairs[i]["I1"], pairs[i]["I2"])
+        assert np.array_equal(outs[i]["flows"].cpu().numpy().astype(np.int32), ref["flows"])
+        assert np.array_equal(outs[i]["valid"].cpu().numpy(), ref["valid"])
+
+
+def test_graph_replay_equals_direct_run():
+    _, frames1 = _frames(20)
+    _, frames2 = _frames(30)
+    direct = ffapi.FlowFieldsBatch(SIZES)
+    graphed = ffapi.FlowFieldsBatch(SIZES, graph=True)
+    for frames in (frames1, frames2, frames1):  # capture on first run, then replay
+        d = [{k: v.clone() for k, v in o.items()} for o in direct.run(frames)]
+        g = graphed.run(frames)
+        for a, b in zip(d, g):
+            _same(a, b)
+    assert graphed.graph_kernels() > 50
+
+
+def test_execution_parameters_do_not_change_results():
+    _, frames = _frames(40)
+    batch = ffapi.FlowFieldsBatch(SIZES)
+    ref = [{k: v.clone() for k, v in o.items()} for o in batch.run(frames)]
+    before = ffapi.get_exec_params()
+    try:
+        for pw in (1, 2, 8):
+            ffapi.set_exec_params(pass_warps=pw)
+            got = batch.run(frames)
+            for a, b in zip(ref, got):
+                _same(a, b)
+    finally:
+        ffapi.set_exec_params(**before)
+
+
+def test_autotuner_picks_a_candidate(tmp_path, monkeypatch):
+    monkeypatch.setattr(tune, "_CACHE", str(tmp_path / "t.json"))
+    before = ffapi.get_exec_params()
+    try:
+        r = tune.tune([(128, 96), (97, 71)], reps=1)
+        assert not r["cached"]
+        assert r["choice"]["pass_warps"] in tune.CANDIDATES["pass_warps"]
+        assert ffapi.get_exec_params()["pass_warps"] == r["choice"]["pass_warps"]
+        r2 = tune.tune([(128, 96), (97, 71)], reps=1)
+        assert r2["cached"] and r2["choice"] == r["choice"]
+    finally:
+        ffapi.set_exec_params(**before)

@@ -242,6 +242,7 @@ def test_flow_fields_is_deterministic_and_stream_independent():
     ff = ffapi.FlowFields(128, 96)
     a = {k: v.clone() for k, v in ff.run(tg(p["I1"]), tg(p["I2"])).items()}
     s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())  # calls are ordered only by their stream
     with torch.cuda.stream(s):
         b = ff.run(tg(p["I1"]), tg(p["I2"]))
     s.synchronize()
