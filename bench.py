@@ -20,7 +20,6 @@ import os
 import statistics
 import subprocess
 import sys
-import threading
 import time
 
 import numpy as np
@@ -158,6 +157,51 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _time_steps(run, steps, flush, stream):
+    """Per-step CUDA-event times (ms) with an L2 flush before every step."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(i & 0xff)
+        ev[i][0].record(stream)
+        run(i)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def batch_measure(dev, params, reps=3):
+    """Mixed-size batch: 16 pairs each of 640x480, 584x388, 1024x436, 1242x375
+    (one synthetic pair per size, repeated), one CUDA graph per batch."""
+    import torch
+    from paper_1508_05151_gb300 import ffapi, synth
+    sizes, frames = [], []
+    for k, (W, H) in enumerate(synth.BATCH_SIZES):
+        p = synth.pair_for_config(3, 500 + k, (W, H))
+        a, b = torch.from_numpy(p["I1"]).to(dev), torch.from_numpy(p["I2"]).to(dev)
+        for _ in range(16):
+            sizes.append((W, H))
+            frames.append((a, b))
+    batch = ffapi.FlowFieldsBatch(sizes, params, dev, graph=True)
+    batch.run(frames)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        batch.run(frames)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = sorted(ts)[len(ts) // 2]
+    evals = sum(nominal_evals(W, H, params) for W, H in sizes)
+    return {"pairs": len(sizes), "sizes": [list(x) for x in synth.BATCH_SIZES],
+            "ms_per_batch": round(ms, 3), "ms_per_pair": round(ms / len(sizes), 4),
+            "cand_evals_per_s": round(evals / (ms / 1e3), 1),
+            "graph_kernels": batch.graph_kernels()}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -176,46 +220,51 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
+    def max_over_ranks(x):
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     pairs = [synth.pair_for_config(2, 1000 + 2 * rank + i) for i in range(2)]
     dI = [(torch.from_numpy(p["I1"]).to(dev), torch.from_numpy(p["I2"]).to(dev)) for p in pairs]
-    ff = ffapi.FlowFields(W, H, PARAMS, dev)
     flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
-
+    # the public paths: one pair as a captured CUDA graph (headline) and the
+    # direct call (also timed, with per-launch events for the roofline)
+    graph = ffapi.FlowFieldsBatch([(W, H)], PARAMS, dev, graph=True)
+    direct = ffapi.FlowFields(W, H, PARAMS, dev)
     for i in range(args.warmup):
-        ff.run(*dI[i % 2])
+        graph.run([dI[i % 2]])
+        direct.run(*dI[i % 2])
     torch.cuda.synchronize()
 
-    # ---- device-resident timed region ----
-    ffapi.profile_enable(True)
+    # ---- timed region A: device-resident inputs, graph replay per pair ----
     ffapi.profile_reset()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         t0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.fill_(i & 0xff)
-            ev[i][0].record(stream)
-            ff.run(*dI[i % 2])
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
+        step_ms = _time_steps(lambda i: graph.run([dI[i % 2]]), args.steps, flush, stream)
         wall = time.perf_counter() - t0
     barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    prof = ffapi.profile_read()
-    ffapi.profile_enable(False)
-    local_ms = sum(step_ms)
-    t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    launches = ffapi.profile_read()["launches"]
+    total_ms = max_over_ranks(sum(step_ms))
     ms_per_step = total_ms / args.steps
     pairs_total = args.steps * world
     value = total_ms / pairs_total  # whole-job ms per pair
 
-    # ---- end to end through the public API with host buffers ----
+    # ---- timed region B: direct call, propagation launches timed by events ----
+    ffapi.profile_enable(True)
+    ffapi.profile_reset()
+    barrier()
+    torch.cuda.synchronize()
+    direct_ms = _time_steps(lambda i: direct.run(*dI[i % 2]), args.steps, flush, stream)
+    prof = ffapi.profile_read()
+    ffapi.profile_enable(False)
+    direct_value = max_over_ranks(sum(direct_ms)) / pairs_total
+
+    # ---- end to end through the public graph API with host buffers ----
     hI = [(torch.from_numpy(p["I1"]).pin_memory(), torch.from_numpy(p["I2"]).pin_memory())
           for p in pairs]
     nb = ((W + 2) // 3) * ((H + 2) // 3)
@@ -223,37 +272,25 @@ def run_ours(args):
     h_valid = torch.empty((H, W), dtype=torch.uint8).pin_memory()
     h_sparse = torch.empty((nb, 4), dtype=torch.int32).pin_memory()
     h_ns = torch.empty(1, dtype=torch.int32).pin_memory()
-    dbuf = [(torch.empty_like(dI[0][0]), torch.empty_like(dI[0][1])) for _ in range(2)]
     h2d = 2 * W * H * 3
     d2h = h_flow.numel() * 2 + h_valid.numel() + h_sparse.numel() * 4 + 4
-    for i in range(2):
-        dbuf[i][0].copy_(hI[i][0], non_blocking=True)
-        dbuf[i][1].copy_(hI[i][1], non_blocking=True)
-        out = ff.run(*dbuf[i])
-    torch.cuda.synchronize()
-    barrier()
-    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.fill_(i & 0xff)
-        e_ev[i][0].record(stream)
-        a, b = dbuf[i % 2]
-        a.copy_(hI[i % 2][0], non_blocking=True)
-        b.copy_(hI[i % 2][1], non_blocking=True)
-        out = ff.run(a, b)
+
+    def e2e_step(i):
+        out = graph.run([hI[i % 2]])[0]  # H2D copies into the graph's input buffers
         h_flow.copy_(out["flows"][0], non_blocking=True)
         h_valid.copy_(out["valid"], non_blocking=True)
         h_sparse.copy_(out["sparse"], non_blocking=True)
         h_ns.copy_(out["n_sparse"], non_blocking=True)
-        e_ev[i][1].record(stream)
+
+    for i in range(2):
+        e2e_step(i)
     torch.cuda.synchronize()
-    e2e_local = sum(a.elapsed_time(b) for a, b in e_ev)
-    te = torch.tensor([e2e_local], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = float(te.item()) / pairs_total
+    barrier()
+    e2e_ms = _time_steps(e2e_step, args.steps, flush, stream)
+    e2e_value = max_over_ranks(sum(e2e_ms)) / pairs_total
     assert int(h_ns.item()) > 0
 
+    batch = batch_measure(dev, PARAMS) if (rank == 0 and not args.no_batch) else None
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -269,9 +306,10 @@ def run_ours(args):
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": None,
             "peak_kind": f"{kind} HBM copy bandwidth",
-            "prop_ms_per_pair": prof["prop_ms"] / args.steps,
-            "note": "achieved = nominal target-tap bytes ((2r+1)^2 x 4 B per candidate) / "
-                    "mean launch time; the taps are served mostly by L1/L2"}
+            "prop_ms_per_pair": round(prof["prop_ms"] / args.steps, 4),
+            "measured_in": "timed region B (direct call), CUDA events around every k_pass launch",
+            "note": "achieved = nominal target-tap bytes ((2r+1)^2 x 4 B per candidate) / mean "
+                    "launch time; taps are served by shared memory and L1/L2"}
 
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "ms/pair", "n_gpus": world,
@@ -279,15 +317,20 @@ def run_ours(args):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "W": W, "H": H, **PARAMS, "pairs_per_rank": args.steps,
+                   "path": "one pair per CUDA-graph replay (ff_graph_launch)",
                    "l2": "flushed between steps (256 MB write)"},
         "cand_evals_per_s": round(nominal_evals(W, H, PARAMS) * pairs_total / (total_ms / 1e3), 1),
+        "direct_call_ms_per_pair": round(direct_value, 4),
         "wall_s_timed_region": round(wall, 4),
-        "gpu_launches": int(prof["launches"]),
+        "gpu_launches": int(launches),
         "roofline": roof,
         "e2e": {"value": round(e2e_value, 4), "unit": "ms/pair", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clk.summary(),
+        "exec_params": ffapi.get_exec_params(),
     }
+    if batch is not None:
+        line["batch_64_mixed"] = batch
     if not args.no_cpu_baseline:
         ms = 1000.0 * cpu_oracle_pair(pairs[0], PARAMS)
         line["cpu_baseline"] = {"value": round(ms, 1), "unit": "ms/pair", "cores": 3,
@@ -305,6 +348,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-pair batch line")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
