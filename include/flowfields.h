@@ -257,6 +257,51 @@ typedef struct ff_exec_params {
 ff_status ff_set_exec_params(const ff_exec_params *e);
 ff_status ff_get_exec_params(ff_exec_params *e);
 
+/* Learned proposal net (not in the paper). A small convolutional net reads the
+ * 1/8-scale images of both frames and emits K flow candidates per point of the
+ * coarsest search grid (spacing 8, k = 3); they are passed to ff_flow_fields as
+ * `proposals` and tried after the kd-tree candidates under the exact integer
+ * data term (strict-less), so they can only replace a kd result with a lower E_d.
+ * Layers: four 3x3 convolutions with dilations dil[0..3] and zero padding,
+ * channels 6 -> c1 -> c2 -> c3 -> 2K (each <= 64), ReLU between layers, BF16
+ * operands and FP32 accumulation on the tensor cores. Parameters are one FP32
+ * vector, per layer W[cout][cin][3][3] then b[cout]. Tensors are NCHW fp32:
+ * x [B][6][Gy][Gx], out [B][2K][Gy][Gx] with Gx = ceil(W/8), Gy = ceil(H/8);
+ * out channel 2k (2k+1) is the x (y) flow of candidate k in units of
+ * flow_scale pixels. */
+typedef struct ff_net_desc {
+  int32_t cin, c1, c2, c3, k;
+  int32_t dil[4];
+} ff_net_desc;
+ff_status ff_net_param_count(const ff_net_desc *d, size_t *n);
+ff_status ff_net_workspace_size(const ff_net_desc *d, int B, int Gx, int Gy, size_t *bytes);
+/* x from B pairs of W x H frames stored back to back ([B][H][W][3] each): the
+ * rounded mean of every 8x8 block per channel (as in ff_smooth's area step),
+ * scaled to v/255 - 0.5; channels 0-2 frame 1, 3-5 frame 2. */
+ff_status ff_net_input(const uint8_t *I1, const uint8_t *I2, int B, int W, int H, float *x,
+                       void *stream);
+/* Forward pass; keeps the activations in ws for ff_net_backward. */
+ff_status ff_net_forward(const ff_net_desc *d, const float *params, const float *x, int B, int Gx,
+                         int Gy, float *out, void *ws, size_t ws_bytes, void *stream);
+/* Relaxed winner-takes-all L1 loss: for every labelled point (valid != 0) the
+ * candidate nearest to the label (L1, first on ties) has weight 1 - alpha, the
+ * others alpha / (K - 1); the loss is averaged over labelled points. label:
+ * int16 [B][Gy][Gx][2] in pixels. Writes *loss (device float), dout = dloss/dout
+ * and *count (device int32, labelled points). */
+ff_status ff_net_loss(const ff_net_desc *d, const float *out, const int16_t *label,
+                      const uint8_t *valid, int B, int Gx, int Gy, float flow_scale, float alpha,
+                      float *loss, float *dout, int32_t *count, void *stream);
+/* Backward pass of the last forward (same ws): grads = dloss/dparams. Weight
+ * gradients are summed with atomics, so their FP32 rounding order varies. */
+ff_status ff_net_backward(const ff_net_desc *d, const float *params, const float *dout, int B,
+                          int Gx, int Gy, float *grads, void *ws, size_t ws_bytes, void *stream);
+/* Adam (Kingma and Ba, 2015) step `step` (1-based) with bias correction. */
+ff_status ff_net_adam(size_t n, float *params, const float *grads, float *m, float *v, int step,
+                      float lr, float b1, float b2, float eps, void *stream);
+/* Integer proposals rint(out * flow_scale), int16 [B][Gy][Gx][K][2]. */
+ff_status ff_net_proposals(const ff_net_desc *d, const float *out, int B, int Gx, int Gy,
+                           float flow_scale, int16_t *proposals, void *stream);
+
 /* Device-side status word kept at the start of a workspace: 0 when every
  * device check passed, else an error code with the grid coordinate where it was
  * raised. Synchronises `stream`, then copies 16 bytes device->host. */

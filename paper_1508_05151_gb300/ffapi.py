@@ -41,6 +41,12 @@ class ExecParams(C.Structure):
     _fields_ = [("pass_warps", C.c_int32), ("reserved", C.c_int32 * 7)]
 
 
+class NetDesc(C.Structure):
+    """ff_net_desc: proposal-net shape."""
+    _fields_ = [("cin", C.c_int32), ("c1", C.c_int32), ("c2", C.c_int32), ("c3", C.c_int32),
+                ("k", C.c_int32), ("dil", C.c_int32 * 4)]
+
+
 class Params(C.Structure):
     """ff_params; defaults are the Sintel preset of Sec. 4."""
     _fields_ = [(n, C.c_int32) for n in
@@ -104,6 +110,16 @@ def lib():
             "ff_graph_kernel_count": ([vp, C.POINTER(u64)], i32),
             "ff_graph_destroy": ([vp], i32),
             "ff_set_exec_params": ([C.POINTER(ExecParams)], i32),
+            "ff_net_param_count": ([C.POINTER(NetDesc), C.POINTER(sz)], i32),
+            "ff_net_workspace_size": ([C.POINTER(NetDesc), i32, i32, i32, C.POINTER(sz)], i32),
+            "ff_net_input": ([vp, vp, i32, i32, i32, vp, vp], i32),
+            "ff_net_forward": ([C.POINTER(NetDesc), vp, vp, i32, i32, i32, vp, vp, sz, vp], i32),
+            "ff_net_loss": ([C.POINTER(NetDesc), vp, vp, vp, i32, i32, i32, C.c_float, C.c_float,
+                             vp, vp, vp, vp], i32),
+            "ff_net_backward": ([C.POINTER(NetDesc), vp, vp, i32, i32, i32, vp, vp, sz, vp], i32),
+            "ff_net_adam": ([sz, vp, vp, vp, vp, i32, C.c_float, C.c_float, C.c_float, C.c_float,
+                             vp], i32),
+            "ff_net_proposals": ([C.POINTER(NetDesc), vp, i32, i32, i32, C.c_float, vp, vp], i32),
             "ff_get_exec_params": ([C.POINTER(ExecParams)], i32),
             "ff_device_status": ([vp, C.POINTER(C.c_uint32), C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int32), vp], i32),
@@ -362,8 +378,8 @@ class FlowFieldsBatch:
     ``sizes``: list of (W, H). ``run(frames)`` takes a list of (I1, I2) uint8 CUDA
     tensors and returns one result dict per pair (views of preallocated output
     tensors). With ``graph=True`` the first run captures the whole batch into a
-    CUDA graph bound to the input buffers given by ``bind`` and later runs replay
-    it; inputs are then copied into those buffers.
+    CUDA graph bound to internal input buffers and later runs replay it; inputs
+    (and, when ``params.K > 0``, the proposals) are copied into those buffers.
     """
 
     def __init__(self, sizes, params=None, device="cuda", graph=False):
@@ -384,8 +400,12 @@ class FlowFieldsBatch:
                 mask=torch.empty((H, W), dtype=torch.uint8, device=d)))
             self.inp.append((torch.empty((H, W, 3), dtype=torch.uint8, device=d),
                              torch.empty((H, W, 3), dtype=torch.uint8, device=d)))
+        # graph mode binds proposal buffers too when the forward flow takes K of them
+        K, n = self.params.K, 1 << self.params.k
+        self.prop = [torch.zeros(((H + n - 1) // n, (W + n - 1) // n, K, 2), dtype=torch.int16,
+                                 device=d) for (W, H) in self.sizes] if (graph and K > 0) else None
         self.pairs = (Pair * len(self.sizes))()
-        self._fill_pairs(self.inp)
+        self._fill_pairs(self.inp, self.prop)
         n = C.c_size_t()
         _check("ff_batch_workspace_size", lib().ff_batch_workspace_size(
             len(self.sizes), self.pairs, C.byref(self.params), C.byref(n)))
@@ -411,16 +431,19 @@ class FlowFieldsBatch:
     def run(self, frames, proposals=None):
         wp, wn = _ws_ptr(self.ws)
         if self.use_graph:
-            if proposals is not None:
-                raise ValueError("graph mode takes no proposals")
+            if (proposals is None) != (self.prop is None):
+                raise ValueError("graph mode takes proposals exactly when params.K > 0")
             caller = torch.cuda.current_stream()
             self.stream.wait_stream(caller)
             with torch.cuda.stream(self.stream):
                 for (a, b), (da, db) in zip(frames, self.inp):
                     da.copy_(a, non_blocking=True)
                     db.copy_(b, non_blocking=True)
+                if proposals is not None:
+                    for src, dst in zip(proposals, self.prop):
+                        dst.copy_(src.reshape(dst.shape), non_blocking=True)
                 if self.graph is None:
-                    self._fill_pairs(self.inp)
+                    self._fill_pairs(self.inp, self.prop)
                     g = C.c_void_p()
                     _check("ff_graph_create", lib().ff_graph_create(
                         len(self.sizes), self.pairs, C.byref(self.params), wp, wn, _stream(),
@@ -445,3 +468,73 @@ class FlowFieldsBatch:
         if getattr(self, "graph", None) is not None and _lib is not None:
             _lib.ff_graph_destroy(self.graph)
             self.graph = None
+
+
+# ------------------------------------------------------------- proposal net ----
+def net_desc(c1=32, c2=64, c3=64, k=4, dil=(1, 2, 4, 8)):
+    return NetDesc(6, c1, c2, c3, k, (C.c_int32 * 4)(*dil))
+
+
+def ff_net_param_count(desc):
+    n = C.c_size_t()
+    _check("ff_net_param_count", lib().ff_net_param_count(C.byref(desc), C.byref(n)))
+    return n.value
+
+
+def ff_net_input(I1, I2):
+    """I1, I2: uint8 [B][H][W][3] CUDA tensors -> x float32 [B][6][Gy][Gx]."""
+    B, H, W = I1.shape[:3]
+    x = torch.empty((B, 6, (H + 7) // 8, (W + 7) // 8), dtype=torch.float32, device=I1.device)
+    _check("ff_net_input", lib().ff_net_input(_dev(I1), _dev(I2), B, W, H, _dev(x), _stream()))
+    return x
+
+
+class NetRunner:
+    """Workspace-holding wrapper of the net entry points for one batch shape."""
+
+    def __init__(self, desc, B, Gx, Gy, device="cuda"):
+        self.desc, self.B, self.Gx, self.Gy = desc, B, Gx, Gy
+        n = C.c_size_t()
+        _check("ff_net_workspace_size", lib().ff_net_workspace_size(C.byref(desc), B, Gx, Gy,
+                                                                    C.byref(n)))
+        self.ws = _ws(n.value, device)
+        d = torch.device(device)
+        self.out = torch.empty((B, 2 * desc.k, Gy, Gx), dtype=torch.float32, device=d)
+        self.dout = torch.empty_like(self.out)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=d)
+        self.count = torch.zeros(1, dtype=torch.int32, device=d)
+
+    def forward(self, params, x):
+        wp, wn = _ws_ptr(self.ws)
+        _check("ff_net_forward", lib().ff_net_forward(
+            C.byref(self.desc), _dev(params), _dev(x), self.B, self.Gx, self.Gy, _dev(self.out),
+            wp, wn, _stream()))
+        return self.out
+
+    def loss_grad(self, label, valid, flow_scale, alpha):
+        _check("ff_net_loss", lib().ff_net_loss(
+            C.byref(self.desc), _dev(self.out), _dev(label), _dev(valid), self.B, self.Gx,
+            self.Gy, flow_scale, alpha, _dev(self.loss), _dev(self.dout), _dev(self.count),
+            _stream()))
+        return self.loss, self.dout
+
+    def backward(self, params, grads, dout=None):
+        wp, wn = _ws_ptr(self.ws)
+        _check("ff_net_backward", lib().ff_net_backward(
+            C.byref(self.desc), _dev(params), _dev(self.dout if dout is None else dout), self.B,
+            self.Gx, self.Gy, _dev(grads), wp, wn, _stream()))
+        return grads
+
+    def proposals(self, flow_scale, out=None):
+        o = self.out if out is None else out
+        prop = torch.empty((self.B, self.Gy, self.Gx, self.desc.k, 2), dtype=torch.int16,
+                           device=o.device)
+        _check("ff_net_proposals", lib().ff_net_proposals(
+            C.byref(self.desc), _dev(o), self.B, self.Gx, self.Gy, flow_scale, _dev(prop),
+            _stream()))
+        return prop
+
+
+def ff_net_adam(params, grads, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+    _check("ff_net_adam", lib().ff_net_adam(params.numel(), _dev(params), _dev(grads), _dev(m),
+                                            _dev(v), step, lr, b1, b2, eps, _stream()))

@@ -48,13 +48,9 @@ def value_noise(rng, h, w, c=3, lattices=(32, 16, 8, 4),
         fy, fx = ys / s, xs / s
         iy, ix = np.floor(fy).astype(np.int64), np.floor(fx).astype(np.int64)
         ty, tx = _smooth(fy - iy)[:, None, None], _smooth(fx - ix)[None, :, None]
-        g00 = g[iy][:, ix]
-        g01 = g[iy][:, ix + 1]
-        g10 = g[iy + 1][:, ix]
-        g11 = g[iy + 1][:, ix + 1]
-        top = g00 * (1 - tx) + g01 * tx
-        bot = g10 * (1 - tx) + g11 * tx
-        out += a * (top * (1 - ty) + bot * ty)
+        # separable: interpolate every lattice row along x, then rows along y
+        gx = g[:, ix] * (1 - tx) + g[:, ix + 1] * tx
+        out += a * (gx[iy] * (1 - ty) + gx[iy + 1] * ty)
     lo = out.min(axis=(0, 1), keepdims=True)
     hi = out.max(axis=(0, 1), keepdims=True)
     return (out - lo) / np.maximum(hi - lo, 1e-12)
