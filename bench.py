@@ -202,6 +202,26 @@ def batch_measure(dev, params, reps=3):
             "graph_kernels": batch.graph_kernels()}
 
 
+def learned_measure(train_pairs=256, epochs=40, eval_pairs=32):
+    """Learned proposals vs plain search on KITTI-shaped 1242x375 pairs (ground
+    plane with radial expansion up to 300 px, textureless sky band, moving boxes).
+
+    The net is trained here on `train_pairs` generated pairs labelled by the plain
+    search (seeds disjoint from the evaluation pairs), then both arms run on
+    `eval_pairs` held-out pairs as batched CUDA-graph replays at random-search
+    budgets n_rs = 1, 2, 3; the learned arm's time includes the net."""
+    from paper_1508_05151_gb300 import train
+    net, info = train.train_for(5, train_pairs, epochs, batch=32, seed=2000)
+    E1, E2, gt, occ = train.make_pairs(5, range(3000, 3000 + eval_pairs))
+    ev = train.evaluate(net, E1, E2, gt, occ, (1, 2, 3), batch=eval_pairs)
+    return {"workload": f"{eval_pairs} KITTI-shaped 1242x375 pairs (radial expansion <= 300 px, "
+                        "sky band, moving boxes), one batch per CUDA-graph replay",
+            "train": info, "coarse_data_cost": ev["coarse"], "arms": ev["arms"],
+            "equal_inliers": train.equal_inlier_point(ev),
+            "note": "inliers_3px / epe of the raw forward flow vs ground truth on non-occluded "
+                    "pixels; equal_inliers = cheapest learned arm reaching plain_rs3's inliers"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -291,6 +311,7 @@ def run_ours(args):
     assert int(h_ns.item()) > 0
 
     batch = batch_measure(dev, PARAMS) if (rank == 0 and not args.no_batch) else None
+    learned = learned_measure() if (rank == 0 and not args.no_learned) else None
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -331,6 +352,8 @@ def run_ours(args):
     }
     if batch is not None:
         line["batch_64_mixed"] = batch
+    if learned is not None:
+        line["learned_vs_plain"] = learned
     if not args.no_cpu_baseline:
         ms = 1000.0 * cpu_oracle_pair(pairs[0], PARAMS)
         line["cpu_baseline"] = {"value": round(ms, 1), "unit": "ms/pair", "cores": 3,
@@ -349,6 +372,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-pair batch line")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip training and evaluating the proposal net")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -249,10 +249,19 @@ ff_status ff_graph_destroy(ff_graph *g);
 /* Execution parameters: launch shapes that change speed but never results
  * (the autotuner in the Python package picks them per GPU and workload).
  * Process-wide; set them between calls, not while work is being enqueued.
- *   pass_warps  tiles (one warp each) per CTA of the propagation kernel, 1..8 */
+ *   pass_warps  most tiles (one warp each) per CTA of the propagation kernel,
+ *               1..8; a level with few tiles uses fewer so that its CTAs
+ *               cover the SMs
+ *   rs_min_n    0: every random search runs inside the propagation kernel on
+ *               the tile's shared-memory state; else levels with spacing
+ *               n >= rs_min_n (a power of two, 1..128) run it as a separate
+ *               kernel with one 16-lane group per grid point. Each point's
+ *               random search depends only on its own state after the pass,
+ *               so both forms give the same result. */
 typedef struct ff_exec_params {
   int32_t pass_warps;
-  int32_t reserved[7];
+  int32_t rs_min_n;
+  int32_t reserved[6];
 } ff_exec_params;
 ff_status ff_set_exec_params(const ff_exec_params *e);
 ff_status ff_get_exec_params(ff_exec_params *e);

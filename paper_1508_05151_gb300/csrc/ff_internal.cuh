@@ -262,6 +262,7 @@ struct KdBuild {
   uint32_t *hist;      // radix histograms
   int32_t *sel;        // per-segment select state
   int32_t *cnt;        // per-segment partition counters
+  unsigned long long *keys;  // [N] select keys of the current level, by position
   int top_levels;      // levels built by the multi-block path
   DeviceStatus *status;  // set if a partition count is inconsistent
 };

@@ -13,12 +13,13 @@
 //     minmax   per-segment per-dim min/max (lanes = dims, coalesced 108-B rows)
 //     sel_init dimension choice, key width
 //     4 x (hist, digit)  radix select of the rank-floor(m/2) key, 11-bit digits,
-//                        key = (value - min) << ibits | pixel index (unique)
+//                        key = (value - min) << ibits | pixel index (unique);
+//                        the first pass caches every position's key
 //     partition          key < selected key -> left child, else right
-//   bottom levels: one 1024-thread CTA per segment finishes its whole subtree in
-//     shared memory: per node exact ranks by counting (broadcast reads), each
-//     point moves to position node_begin + rank, i.e. the node ends up sorted by
-//     (value, index) and the left half is the first floor(m/2).
+//   bottom levels: one 1024-thread CTA per segment finishes its whole subtree:
+//     per sub-level one CTA-wide bitonic sort of (node, value, pixel-index rank)
+//     keys sorts every node by (value, index), so the left half is the first
+//     floor(m/2).
 #include "ff_internal.cuh"
 
 namespace ff {
@@ -66,6 +67,7 @@ void kd_bind_scratch(KdBuild &b, Arena &a) {
   b.hist = a.take<uint32_t>((size_t)segs * NBINS);
   b.sel = a.take<int32_t>((size_t)segs * 8);
   b.cnt = a.take<int32_t>((size_t)segs * 2);
+  b.keys = a.take<unsigned long long>(b.N > 0 && T > 0 ? b.N : 1);
 }
 
 // Offsets of segment i at depth d (i in [0, 2^d]) by halving along i's bits.
@@ -255,7 +257,15 @@ __global__ void __launch_bounds__(256) k_kd_hist(KdBuild *trees, int d) {
     int B = S[2], used = S[7];
     if (used >= B) continue;
     int hi = B - used, lo = max(hi - DIGIT, 0);
-    unsigned long long K = kd_key(T, S, cur_perm(T, d)[p]);
+    // the first pass of a level gathers the point's value and caches its key;
+    // later passes read the cache (coalesced)
+    unsigned long long K;
+    if (used == 0) {
+      K = kd_key(T, S, cur_perm(T, d)[p]);
+      T.keys[p] = K;
+    } else {
+      K = T.keys[p];
+    }
     unsigned long long pre = ((unsigned long long)(unsigned)S[6] << 32) | (unsigned)S[5];
     if (hi < 64 && (K >> hi) != pre) continue;
     unsigned dig = (unsigned)((K >> lo) & ((1ull << (hi - lo)) - 1));
@@ -406,24 +416,71 @@ __global__ void __launch_bounds__(256) k_kd_partition(KdBuild *trees, int d) {
   }
 }
 
+// Ascending bitonic sort of one 64-bit key per thread over the CTA's SUB_MAX
+// threads (thread t ends with the t-th smallest key). Exchanges with partners
+// inside the warp use shuffles; wider ones go through shared memory (two
+// buffers, so one barrier per step suffices).
+__device__ __forceinline__ unsigned long long bitonic_sort_cta(unsigned long long c,
+                                                               unsigned long long *buf) {
+  const int t = threadIdx.x;
+  int flip = 0;
+  for (int k = 2; k <= SUB_MAX; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      unsigned long long o;
+      if (j >= 32) {
+        unsigned long long *b = buf + flip * SUB_MAX;
+        b[t] = c;
+        __syncthreads();
+        o = b[t ^ j];
+        flip ^= 1;
+      } else {
+        o = __shfl_xor_sync(0xffffffffu, c, j);
+      }
+      const bool up = (t & k) == 0, lower = (t & j) == 0;
+      c = (lower == up) ? (o < c ? o : c) : (o > c ? o : c);
+    }
+  }
+  return c;
+}
+
 // One 1024-thread CTA finishes the subtree of one segment at depth top_levels.
-// Shared memory: point indices and keys (1024 each), and per node of the current
-// sub-level its per-dimension min/max and chosen dimension (max_nodes nodes).
+// Thread t owns the segment's t-th smallest pixel index for all sub-levels and
+// keeps its 27 features in registers. Per sub-level: the node min/max per
+// dimension (warp reductions over threads of one node, then shared atomics), the
+// split dimension, then one CTA-wide sort of the keys
+//   (node << 54) | (value - node min) << 10 | t,
+// which orders every node's points by (value, pixel index) in place, because the
+// owners are numbered in pixel-index order. A point's sorted position gives its
+// rank in the node; the rank-floor(m/2) point is the split.
 __global__ void __launch_bounds__(1024) k_kd_subtree(KdBuild *trees, int max_nodes) {
   KdBuild &T = trees[blockIdx.y];
   const int d0 = T.top_levels;
   if (blockIdx.x >= (1u << d0)) return;
   const int b0 = seg_begin(T.N, d0, blockIdx.x), e0 = seg_begin(T.N, d0, blockIdx.x + 1);
   const int m0 = e0 - b0;
-  extern __shared__ int32_t ssub[];
-  int32_t *sidx = ssub, *skey = ssub + SUB_MAX;
-  int(*smin)[NFEAT] = (int(*)[NFEAT])(ssub + 2 * SUB_MAX);
+  extern __shared__ __align__(16) int32_t ssub[];
+  unsigned long long *sbuf = (unsigned long long *)ssub;  // 2 x SUB_MAX
+  int32_t *spos = ssub + 4 * SUB_MAX;                     // SUB_MAX
+  int(*smin)[NFEAT] = (int(*)[NFEAT])(spos + SUB_MAX);
   int(*smax)[NFEAT] = smin + max_nodes;
   int *sdim = (int *)(smax + max_nodes);
   const int t = threadIdx.x, lane = t & 31;
   const bool act = t < m0;
-  if (act) sidx[t] = cur_perm(T, d0)[b0 + t];
-  int nb = 0, ne = m0, nid = 0;  // node (local) holding position t at this sub-depth
+  // owners in pixel-index order
+  const unsigned long long raw = act ? (unsigned long long)(uint32_t)cur_perm(T, d0)[b0 + t] : ~0ull;
+  const unsigned long long srt = bitonic_sort_cta(raw, sbuf);
+  const int idx = act ? (int)srt : 0;
+  int4 q[7];
+  if (act) {
+    const int4 *row = (const int4 *)(T.feat + (size_t)idx * FEAT_STRIDE);
+#pragma unroll
+    for (int k = 0; k < 7; k++) q[k] = row[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 7; k++) q[k] = make_int4(0, 0, 0, 0);
+  }
+  const int *v = (const int *)q;
+  int nb = 0, ne = m0, nid = 0, pos = t;  // this point's node and position
   const int levels = T.D - d0;
   for (int sd = 0; sd < levels; sd++) {
     const int nnodes = 1 << sd;
@@ -432,12 +489,6 @@ __global__ void __launch_bounds__(1024) k_kd_subtree(KdBuild *trees, int max_nod
       smax[i / NFEAT][i % NFEAT] = INT32_MIN;
     }
     __syncthreads();
-    const int idx = act ? sidx[t] : 0;
-    int4 q[7];
-    const int4 *row = (const int4 *)(T.feat + (size_t)idx * FEAT_STRIDE);
-#pragma unroll
-    for (int k = 0; k < 7; k++) q[k] = row[k];
-    const int *v = (const int *)q;
     const unsigned grp = __match_any_sync(0xffffffffu, act ? nid : -1);
     const bool leader = (__ffs(grp) - 1) == lane;
 #pragma unroll
@@ -467,24 +518,22 @@ __global__ void __launch_bounds__(1024) k_kd_subtree(KdBuild *trees, int max_nod
 #pragma unroll
     for (int k = 0; k < NFEAT; k++)
       if (k == dim) key = v[k];
-    if (act) skey[t] = key;
-    __syncthreads();
-    int rank = 0;
-    if (act)
-      for (int u = nb; u < ne; u++) {
-        const int kv = skey[u], ki = sidx[u];
-        rank += (kv < key) || (kv == key && ki < idx);
-      }
+    const unsigned long long c =
+        act ? ((unsigned long long)nid << 54) |
+                  ((unsigned long long)(uint32_t)(key - smin[nid][dim]) << 10) | (unsigned)t
+            : ~0ull;
+    const unsigned long long sorted = bitonic_sort_cta(c, sbuf);
+    if (t < m0) spos[(int)(sorted & 1023u)] = t;
     __syncthreads();
     if (act) {
-      sidx[nb + rank] = idx;
-      const int half = (ne - nb) >> 1;
+      pos = spos[t];
+      const int half = (ne - nb) >> 1, rank = pos - nb;
       if (rank == half) {
         const int node = (1 << (d0 + sd)) - 1 + (blockIdx.x << sd) + nid;
         T.split_dim[node] = dim;
         T.split_val[node] = key;
       }
-      if (t < nb + half) {
+      if (rank < half) {
         ne = nb + half;
         nid = 2 * nid;
       } else {
@@ -494,11 +543,11 @@ __global__ void __launch_bounds__(1024) k_kd_subtree(KdBuild *trees, int max_nod
     }
     __syncthreads();
   }
-  if (act) T.perm[b0 + t] = sidx[t];
+  if (act) T.perm[b0 + pos] = idx;
 }
 
 static size_t subtree_smem(int max_nodes) {
-  return sizeof(int32_t) * (2 * SUB_MAX + 2 * (size_t)max_nodes * NFEAT + max_nodes);
+  return sizeof(int32_t) * (5 * SUB_MAX + 2 * (size_t)max_nodes * NFEAT + max_nodes);
 }
 
 ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaStream_t st) {

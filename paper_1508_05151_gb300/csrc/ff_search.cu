@@ -4,22 +4,26 @@
 // flow of the coarser level with E_d re-evaluated here; every other point starts
 // without a flow (cost 0x7fffffff).
 //
-// Pass kernel, one CTA per T x T tile of grid points, 512 threads = 32 groups of
-// 16 lanes. The fixed parallel schedule: inside the tile the pass is exactly the
-// sequential scan (processed as anti-diagonal wavefronts, since a point depends
-// only on its left/top -- in scan orientation -- neighbours), and a source
-// outside the tile is read from the state at the start of the pass. Odd passes
-// shift the tile origin by T/2. Per diagonal:
-//   A  warp 0, lane = row: build the point's candidates (its two sources' flows,
-//      target clamped into the image), dropping ones equal to the current flow or
-//      to the first candidate (they cannot win under strict-less replacement)
-//   B  all 32 groups evaluate the candidate list (E_d, 16 lanes per candidate)
-//   C  warp 0 applies them in order current, horizontal, vertical (strict less)
-// After the wavefront the random search of the pass (if any) runs on all tile
-// points in parallel, one group per point.
-// The source patches of the tile's points form one dense (T + 2r)^2 block of the
-// source frame's phase-(0,0) plane; it is staged in shared memory once per pass.
-// Target taps are gathered from the target frame's phase planes (L1/L2).
+// Pass kernel: one warp per T x T tile of grid points, pass_warps tiles per CTA
+// (an execution parameter). The fixed parallel schedule: inside the tile the pass
+// is exactly the sequential scan of the pass's direction, and a source outside
+// the tile is read from the state at the start of the pass; odd passes shift the
+// tile origin by T/2. Since a point depends only on its two source neighbours,
+// the scan is run as anti-diagonal wavefronts: lane j owns scan row j (for
+// T <= 16 lane j + 16 evaluates that row's vertical candidate concurrently), and
+// one diagonal step per lane evaluates the candidates of its point and applies
+// them in the order current, horizontal, vertical with strict-less replacement.
+// A propagation candidate whose target is not clamped is costed incrementally:
+// the patch of p under q's flow differs from q's by one line, so
+// E(p, f) = E(q, f) - outgoing line + incoming line, exactly. After the wavefront
+// the random search of the pass (if any) runs on all tile points, one lane per
+// point, with offsets from the counter-based generator.
+// Per tile and pass, shared memory holds: the source window (the tile's patches
+// in the source frame's phase-(0,0) plane), a target window around where the
+// tile centre's flow lands (hit by most candidates of a coherent field), the tile
+// state and the state of the neighbours just outside the tile. Targets outside
+// the window are gathered from the census phase planes (column lines from the
+// transposed planes), through L1/L2.
 #include <mutex>
 
 #include "ff_internal.cuh"
@@ -55,6 +59,39 @@ __global__ void __launch_bounds__(256) k_seed(const SearchProblem *probs) {
   if (l16 == 0) {
     P.flow_a[g] = pack_flow(tx - px, ty - py);
     P.cost_a[g] = cost;
+  }
+}
+
+// Random search of pass s as a kernel of its own (levels where the execution
+// parameters ask for it): one 16-lane group per grid point, in place on the
+// pass's output. A point's random search reads and writes only its own state, so
+// this equals the in-pass form exactly.
+template <int R>
+__global__ void __launch_bounds__(256) k_rs(const SearchProblem *probs, int s, int Rfull,
+                                            uint64_t seed) {
+  const SearchProblem &P = probs[blockIdx.y];
+  const int NX = P.src.NX, G = NX * P.src.NY, n = P.src.n, log2n = P.src.log2n;
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const int l16 = threadIdx.x & 15;
+  const unsigned gmask = 0xffffu << (threadIdx.x & 16);
+  if (g >= G) return;
+  uint32_t *fl = (s & 1) ? P.flow_a : P.flow_b;  // the pass's output buffers
+  int32_t *co = (s & 1) ? P.cost_a : P.cost_b;
+  const int32_t cc = co[g];
+  if (cc == COST_UNSET) return;
+  const uint32_t cur = fl[g];
+  const int gx = g % NX, gy = g / NX, px = gx * n, py = gy * n;
+  int ox, oy;
+  rs_offset(seed, P.flow_id, log2n, s, gx, gy, Rfull * n, ox, oy);
+  const int tx = clampi(px + flow_dx(cur) + ox, 0, P.src.W - 1);
+  const int ty = clampi(py + flow_dy(cur) + oy, 0, P.src.H - 1);
+  const uint32_t cf = pack_flow(tx - px, ty - py);
+  if (cf == cur) return;
+  const int cost = group_cost<R>(plane_centre(P.src, px, py), P.src.pitch,
+                                 plane_centre(P.tgt, tx, ty), P.tgt.pitch, l16, gmask);
+  if (l16 == 0 && cost < cc) {
+    fl[g] = cf;
+    co[g] = cost;
   }
 }
 
@@ -495,6 +532,21 @@ static ff_status set_pass_smem(int r, size_t bytes) {
   return FF_OK;
 }
 
+// Multiprocessor count of the current device, looked up once per device.
+static ff_status sm_count(int *out) {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FF_ERR_CUDA;
+  if (!cache[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+      return FF_ERR_CUDA;
+    cache[dev] = v;
+  }
+  *out = cache[dev];
+  return FF_OK;
+}
+
 static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d, int np, int r,
                               int tile, int n_rs, int R, uint64_t seed, cudaStream_t st) {
   int maxG = 0, maxT = 0;
@@ -512,15 +564,28 @@ static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d
   const TileLayout lay(tile, r);
   int pw = exec_params().pass_warps;
   while (pw > 1 && sizeof(uint32_t) * (size_t)lay.words() * pw > 227u * 1024u) pw--;
+  // a level with few tiles spreads them over the SMs (one CTA per SM at least)
+  int nsm = 0;
+  FF_TRY(sm_count(&nsm));
+  const long tiles = (long)maxT * np;
+  while (pw > 1 && (tiles + pw - 1) / pw < nsm) pw--;
   const size_t smem = sizeof(uint32_t) * (size_t)lay.words() * pw;
   FF_TRY(set_pass_smem(r, smem));
+  const int rs_min_n = exec_params().rs_min_n;
+  const bool rs_kernel = rs_min_n > 0 && probs[0].src.n >= rs_min_n;
   for (int s = 0; s < 4; s++) {
-    PassCfg cfg{s, tile, (s < 3 && s < n_rs) ? 1 : 0, R, seed, s == 3, lay.words()};
+    const bool do_rs = s < 3 && s < n_rs;
+    PassCfg cfg{s, tile, (do_rs && !rs_kernel) ? 1 : 0, R, seed, s == 3, lay.words()};
     dim3 g((maxT + pw - 1) / pw, np);
     if (prof_enabled()) prof_begin(st);
     FF_DISPATCH_R(r, k_pass<RR><<<g, pw * 32, smem, st>>>(d, cfg));
     FF_CHECK_LAUNCH();
     if (prof_enabled()) prof_end(st);
+    if (do_rs && rs_kernel) {
+      dim3 gr((maxG * 16 + 255) / 256, np);
+      FF_DISPATCH_R(r, k_rs<RR><<<gr, 256, 0, st>>>(d, s, R, seed));
+      FF_CHECK_LAUNCH();
+    }
   }
   return FF_OK;
 }

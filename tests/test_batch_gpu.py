@@ -64,8 +64,10 @@ def test_execution_parameters_do_not_change_results():
     ref = [{k: v.clone() for k, v in o.items()} for o in batch.run(frames)]
     before = ffapi.get_exec_params()
     try:
-        for pw in (1, 2, 8):
-            ffapi.set_exec_params(pass_warps=pw)
+        # tiles per CTA, and the random search inside the pass kernel or as its
+        # own kernel from some level on
+        for pw, rs in ((1, 0), (2, 1), (8, 2), (4, 8), (4, 64)):
+            ffapi.set_exec_params(pass_warps=pw, rs_min_n=rs)
             got = batch.run(frames)
             for a, b in zip(ref, got):
                 _same(a, b)
@@ -80,7 +82,8 @@ def test_autotuner_picks_a_candidate(tmp_path, monkeypatch):
         r = tune.tune([(128, 96), (97, 71)], reps=1)
         assert not r["cached"]
         assert r["choice"]["pass_warps"] in tune.CANDIDATES["pass_warps"]
-        assert ffapi.get_exec_params()["pass_warps"] == r["choice"]["pass_warps"]
+        assert r["choice"]["rs_min_n"] in tune.CANDIDATES["rs_min_n"]
+        assert ffapi.get_exec_params() == r["choice"]
         r2 = tune.tune([(128, 96), (97, 71)], reps=1)
         assert r2["cached"] and r2["choice"] == r["choice"]
     finally:

@@ -149,6 +149,37 @@ def test_search_level_seeded(W, H, n, r, tile, n_rs):
         assert np.array_equal(cpu(f).astype(np.int32), fr)
 
 
+@pytest.mark.parametrize("W,H,n,r,tile,pw,rs_min_n", [(128, 96, 1, 8, 16, 1, 1),
+                                                       (200, 150, 4, 6, 16, 8, 2),
+                                                       (97, 71, 2, 8, 6, 3, 2)])
+def test_search_level_random_search_kernel(W, H, n, r, tile, pw, rs_min_n):
+    """The random search as a kernel of its own (execution parameter) equals the
+    oracle's in-pass order."""
+    p = synth.pair_shift(W + 11 * H, W=W, H=H, max_shift=(10, 10), square=min(24, W, H),
+                         square_move=9)
+    C1g, _ = gpu_census(p["I1"], n)
+    C2g, _ = gpu_census(p["I2"], n)
+    C1, C2 = cpu(C1g).view(np.uint32), cpu(C2g).view(np.uint32)
+    Gxc, Gyc = O.grid(W, H, 2 * n)
+    rng = np.random.default_rng(n + r)
+    coarse = rng.integers(-12, 13, size=(Gyc, Gxc, 2))
+    ys, xs = np.mgrid[0:Gyc, 0:Gxc] * (2 * n)
+    coarse[..., 0] = np.clip(xs + coarse[..., 0], 0, W - 1) - xs
+    coarse[..., 1] = np.clip(ys + coarse[..., 1], 0, H - 1) - ys
+    before = ffapi.get_exec_params()
+    try:
+        ffapi.set_exec_params(pass_warps=pw, rs_min_n=rs_min_n)
+        f, c = ffapi.ff_search_level(C1g, C2g, n, r, dict(tile=tile, seed=77), flow_id=1,
+                                     flow_coarse=tg(coarse.astype(np.int16)))
+        torch.cuda.synchronize()
+    finally:
+        ffapi.set_exec_params(**before)
+    fr, cr, _ = O.search_level(C1, C2, n, r, flow_coarse=coarse.astype(np.int32), tile=tile,
+                               seed=77, flow_id=1)
+    assert np.array_equal(cpu(c), cr)
+    assert np.array_equal(cpu(f).astype(np.int32), fr)
+
+
 @pytest.mark.parametrize("W,H,n,r,tile", [(128, 96, 8, 8, 32), (80, 60, 1, 3, 10)])
 def test_search_level_from_state(W, H, n, r, tile):
     # top-level form: the state (including unset points) is the input
