@@ -175,7 +175,7 @@ def batch_measure(dev, params, reps=3):
     """Mixed-size batch: 16 pairs each of 640x480, 584x388, 1024x436, 1242x375
     (one synthetic pair per size, repeated), one CUDA graph per batch."""
     import torch
-    from paper_1508_05151_gb300 import ffapi, synth
+    from paper_1508_05151_gb300 import ffapi, synth, tune
     sizes, frames = [], []
     for k, (W, H) in enumerate(synth.BATCH_SIZES):
         p = synth.pair_for_config(3, 500 + k, (W, H))
@@ -183,6 +183,7 @@ def batch_measure(dev, params, reps=3):
         for _ in range(16):
             sizes.append((W, H))
             frames.append((a, b))
+    tuned = tune.tune(sizes, params, frames=frames, reps=2, use_cache=False)
     batch = ffapi.FlowFieldsBatch(sizes, params, dev, graph=True)
     batch.run(frames)
     torch.cuda.synchronize()
@@ -199,7 +200,7 @@ def batch_measure(dev, params, reps=3):
     return {"pairs": len(sizes), "sizes": [list(x) for x in synth.BATCH_SIZES],
             "ms_per_batch": round(ms, 3), "ms_per_pair": round(ms / len(sizes), 4),
             "cand_evals_per_s": round(evals / (ms / 1e3), 1),
-            "graph_kernels": batch.graph_kernels()}
+            "graph_kernels": batch.graph_kernels(), "exec_params": tuned["choice"]}
 
 
 def learned_measure(train_pairs=256, epochs=40, eval_pairs=32):
@@ -226,7 +227,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_1508_05151_gb300 import ffapi, synth
+    from paper_1508_05151_gb300 import ffapi, synth, tune
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -250,6 +251,8 @@ def run_ours(args):
     dI = [(torch.from_numpy(p["I1"]).to(dev), torch.from_numpy(p["I2"]).to(dev)) for p in pairs]
     flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
+    # result-neutral launch shapes picked by the autotuner for this workload
+    tuned = tune.tune([(W, H)], PARAMS, frames=[dI[0]], reps=5, use_cache=False)
     # the public paths: one pair as a captured CUDA graph (headline) and the
     # direct call (also timed, with per-launch events for the roofline)
     graph = ffapi.FlowFieldsBatch([(W, H)], PARAMS, dev, graph=True)
@@ -348,7 +351,7 @@ def run_ours(args):
         "e2e": {"value": round(e2e_value, 4), "unit": "ms/pair", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clk.summary(),
-        "exec_params": ffapi.get_exec_params(),
+        "exec_params": tuned["choice"],
     }
     if batch is not None:
         line["batch_64_mixed"] = batch

@@ -257,11 +257,16 @@ ff_status ff_graph_destroy(ff_graph *g);
  *               n >= rs_min_n (a power of two, 1..128) run it as a separate
  *               kernel with one 16-lane group per grid point. Each point's
  *               random search depends only on its own state after the pass,
- *               so both forms give the same result. */
+ *               so both forms give the same result.
+ *   wide_min_n  0: every level runs the propagation with one warp per tile; else
+ *               levels with spacing n >= wide_min_n (a power of two, 1..128; only
+ *               for tiles of edge <= 16) run it with one 128-thread CTA per tile,
+ *               eight threads per scan row (same schedule, same results). */
 typedef struct ff_exec_params {
   int32_t pass_warps;
   int32_t rs_min_n;
-  int32_t reserved[6];
+  int32_t wide_min_n;
+  int32_t reserved[5];
 } ff_exec_params;
 ff_status ff_set_exec_params(const ff_exec_params *e);
 ff_status ff_get_exec_params(ff_exec_params *e);

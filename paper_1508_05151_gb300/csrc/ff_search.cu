@@ -122,6 +122,110 @@ struct TileLayout {
   __host__ __device__ int words() const { return sw * swp + tw * twp + 2 * T * T + 4 * T; }
 };
 
+// Shared-memory regions of one tile (all sizes in 32-bit words): source window,
+// target window, tile state, and the state of the neighbours just outside the
+// tile (horizontal: one per row, vertical: one per column).
+struct TileSmem {
+  uint32_t *src, *tgt, *flow;
+  int32_t *cost;
+  uint32_t *hf;
+  int32_t *hc;
+  uint32_t *vf;
+  int32_t *vc;
+};
+
+__device__ __forceinline__ TileSmem carve_tile(uint32_t *base, const TileLayout &Lt, int T) {
+  TileSmem S;
+  S.src = base;
+  S.tgt = S.src + Lt.sw * Lt.swp;
+  S.flow = S.tgt + Lt.tw * Lt.twp;
+  S.cost = (int32_t *)(S.flow + T * T);
+  S.hf = (uint32_t *)(S.cost + T * T);
+  S.hc = (int32_t *)(S.hf + T);
+  S.vf = (uint32_t *)(S.hc + T);
+  S.vc = (int32_t *)(S.vf + T);
+  return S;
+}
+
+// Copies a tile's state, its outside neighbours, its source window and its
+// target window into shared memory; threads sl, sl + width, ... share the work.
+// The target window is where the tile's patches land under the flow of a set
+// point near the tile centre (after seeding the even-even points are set); it
+// is one phase plane's window, ph0 < 0 when there is none.
+template <int R>
+__device__ __forceinline__ void stage_tile(const SearchProblem &P, const TileLayout &Lt, int T,
+                                           bool live, int x0, int y0, int x1, int y1, int hdx,
+                                           int vdy, const uint32_t *fin, const int32_t *cin,
+                                           const TileSmem &S, int sl, int width, int &tox,
+                                           int &toy, int &ph0) {
+  const int Gx = P.src.NX, Gy = P.src.NY, n = P.src.n, log2n = P.src.log2n;
+  const int tw = live ? x1 - x0 : 0, th = live ? y1 - y0 : 0;
+  for (int i = sl; i < tw * th; i += width) {
+    const int lx = i % tw, ly = i / tw;
+    const size_t g = (size_t)(y0 + ly) * Gx + x0 + lx;
+    S.flow[ly * T + lx] = fin[g];
+    S.cost[ly * T + lx] = cin[g];
+  }
+  if (live) {
+    const int hx = hdx < 0 ? x0 - 1 : x1, vy = vdy < 0 ? y0 - 1 : y1;
+    for (int i = sl; i < th; i += width) {
+      const bool ok = hx >= 0 && hx < Gx;
+      S.hf[i] = ok ? fin[(size_t)(y0 + i) * Gx + hx] : 0u;
+      S.hc[i] = ok ? cin[(size_t)(y0 + i) * Gx + hx] : COST_UNSET;
+    }
+    for (int i = sl; i < tw; i += width) {
+      const bool ok = vy >= 0 && vy < Gy;
+      S.vf[i] = ok ? fin[(size_t)vy * Gx + x0 + i] : 0u;
+      S.vc[i] = ok ? cin[(size_t)vy * Gx + x0 + i] : COST_UNSET;
+    }
+  }
+  {
+    const int ww = live ? tw + 2 * R + 2 : 0, wh = th + 2 * R + 2;
+    const int ex0 = x0 - R - 1 + PLANE_PAD, ey0 = y0 - R - 1 + PLANE_PAD;
+    for (int i = sl; i < ww * wh; i += width) {
+      const int wx = i % ww, wy = i / ww;
+      const int ex = ex0 + wx, ey = ey0 + wy;
+      // entries outside the plane are only reachable through neighbours outside
+      // the grid, which are never used
+      S.src[wy * Lt.swp + wx] = (ex >= 0 && ey >= 0 && ex < P.src.pitch && ey < P.src.rows)
+                                    ? P.src.base[(size_t)ey * P.src.pitch + ex]
+                                    : 0u;
+    }
+  }
+  tox = 0;
+  toy = 0;
+  ph0 = -1;
+  if (live) {
+    int gx = x0 + (tw >> 1), gy = y0 + (th >> 1);
+    if (cin[(size_t)gy * Gx + gx] == COST_UNSET) {
+      gx &= ~1;
+      gy &= ~1;
+    }
+    const size_t g = (size_t)gy * Gx + gx;
+    if (cin[g] != COST_UNSET) {
+      const uint32_t fc = fin[g];
+      const int m = n - 1;
+      const int cx = gx * n + flow_dx(fc), cy = gy * n + flow_dy(fc);
+      const int slack = Lt.tw - (tw + 2 * R + 2);
+      tox = (x0 - R - 1) + ((cx >> log2n) - gx) + PLANE_PAD - slack / 2;
+      toy = (y0 - R - 1) + ((cy >> log2n) - gy) + PLANE_PAD - slack / 2;
+      ph0 = ((cy & m) << log2n) + (cx & m);
+    }
+  }
+  if (ph0 >= 0) {
+    const uint32_t *pl = P.tgt.base + (size_t)ph0 * P.tgt.plane_words;
+    const int tpitch = P.tgt.pitch, trows = P.tgt.rows;
+    for (int i = sl; i < Lt.tw * Lt.tw; i += width) {
+      const int wx = i % Lt.tw, wy = i / Lt.tw;
+      const int ex = tox + wx, ey = toy + wy;
+      // entries outside the plane are never inside a valid candidate's patch
+      S.tgt[wy * Lt.twp + wx] = (ex >= 0 && ey >= 0 && ex < tpitch && ey < trows)
+                                    ? pl[(size_t)ey * tpitch + ex]
+                                    : 0u;
+    }
+  }
+}
+
 // Incremental E_d delta of a propagation candidate, by one lane. When p takes the
 // flow f of its neighbour q = p + s*n along one axis and the target is not
 // clamped, the patches of p and q (and of p + f, q + f) differ by one line:
@@ -203,82 +307,16 @@ __global__ void __launch_bounds__(PASS_MAX_WARPS * 32) k_pass(const SearchProble
     cout = P.cost_final;
   }
   const uint32_t *tbase = P.tgt.base, *tbaseT = P.tgt.baseT;
-  const int tpitch = P.tgt.pitch, tpitchT = P.tgt.pitchT, trows = P.tgt.rows;
+  const int tpitch = P.tgt.pitch, tpitchT = P.tgt.pitchT;
   const size_t tpw_ = P.tgt.plane_words, tpwT = P.tgt.plane_wordsT;
 
-  uint32_t *s_src = smem + (size_t)(warp * tpw + sub) * cfg.words_per_tile;
-  uint32_t *s_tgt = s_src + Lt.sw * Lt.swp;
-  uint32_t *s_flow = s_tgt + Lt.tw * Lt.twp;
-  int32_t *s_cost = (int32_t *)(s_flow + T * T);
-  uint32_t *s_hf = (uint32_t *)(s_cost + T * T);  // neighbours just outside the tile
-  int32_t *s_hc = (int32_t *)(s_hf + T);
-  uint32_t *s_vf = (uint32_t *)(s_hc + T);
-  int32_t *s_vc = (int32_t *)(s_vf + T);
-
-  // ---- stage tile state, outside neighbours, source window ----
-  for (int i = sl; i < tw * th; i += width) {
-    const int lx = i % tw, ly = i / tw;
-    const size_t g = (size_t)(y0 + ly) * Gx + x0 + lx;
-    s_flow[ly * T + lx] = fin[g];
-    s_cost[ly * T + lx] = cin[g];
-  }
-  if (live) {
-    const int hx = hdx < 0 ? x0 - 1 : x1, vy = vdy < 0 ? y0 - 1 : y1;
-    for (int i = sl; i < th; i += width) {
-      const bool ok = hx >= 0 && hx < Gx;
-      s_hf[i] = ok ? fin[(size_t)(y0 + i) * Gx + hx] : 0u;
-      s_hc[i] = ok ? cin[(size_t)(y0 + i) * Gx + hx] : COST_UNSET;
-    }
-    for (int i = sl; i < tw; i += width) {
-      const bool ok = vy >= 0 && vy < Gy;
-      s_vf[i] = ok ? fin[(size_t)vy * Gx + x0 + i] : 0u;
-      s_vc[i] = ok ? cin[(size_t)vy * Gx + x0 + i] : COST_UNSET;
-    }
-  }
-  {
-    const int ww = live ? tw + 2 * R + 2 : 0, wh = th + 2 * R + 2;
-    const int ex0 = x0 - R - 1 + PLANE_PAD, ey0 = y0 - R - 1 + PLANE_PAD;
-    for (int i = sl; i < ww * wh; i += width) {
-      const int wx = i % ww, wy = i / ww;
-      const int ex = ex0 + wx, ey = ey0 + wy;
-      // entries outside the plane are only reachable through neighbours outside
-      // the grid, which are never used
-      s_src[wy * Lt.swp + wx] = (ex >= 0 && ey >= 0 && ex < P.src.pitch && ey < P.src.rows)
-                                    ? P.src.base[(size_t)ey * P.src.pitch + ex]
-                                    : 0u;
-    }
-  }
-  // target window: where the tile's patches land under the flow of a set point
-  // near the tile centre (after seeding the even-even points are set)
+  const TileSmem S = carve_tile(smem + (size_t)(warp * tpw + sub) * cfg.words_per_tile, Lt, T);
+  uint32_t *s_src = S.src, *s_tgt = S.tgt, *s_flow = S.flow;
+  int32_t *s_cost = S.cost;
+  const uint32_t *s_hf = S.hf, *s_vf = S.vf;
+  const int32_t *s_hc = S.hc, *s_vc = S.vc;
   int tox = 0, toy = 0, ph0 = -1;
-  if (live) {
-    int gx = x0 + (tw >> 1), gy = y0 + (th >> 1);
-    if (cin[(size_t)gy * Gx + gx] == COST_UNSET) {
-      gx &= ~1;
-      gy &= ~1;
-    }
-    const size_t g = (size_t)gy * Gx + gx;
-    if (cin[g] != COST_UNSET) {
-      const uint32_t fc = fin[g];
-      const int m = n - 1;
-      const int cx = gx * n + flow_dx(fc), cy = gy * n + flow_dy(fc);
-      const int slack = Lt.tw - (tw + 2 * R + 2);
-      tox = (x0 - R - 1) + ((cx >> log2n) - gx) + PLANE_PAD - slack / 2;
-      toy = (y0 - R - 1) + ((cy >> log2n) - gy) + PLANE_PAD - slack / 2;
-      ph0 = ((cy & m) << log2n) + (cx & m);
-    }
-  }
-  if (ph0 >= 0) {
-    const uint32_t *pl = tbase + (size_t)ph0 * tpw_;
-    for (int i = sl; i < Lt.tw * Lt.tw; i += width) {
-      const int wx = i % Lt.tw, wy = i / Lt.tw;
-      const int ex = tox + wx, ey = toy + wy;
-      // entries outside the plane are never inside a valid candidate's patch
-      s_tgt[wy * Lt.twp + wx] = (ex >= 0 && ey >= 0 && ex < tpitch && ey < trows)
-                                    ? pl[(size_t)ey * tpitch + ex]
-                                    : 0u;
-    }
-  }
+  stage_tile<R>(P, Lt, T, live, x0, y0, x1, y1, hdx, vdy, fin, cin, S, sl, width, tox, toy, ph0);
   __syncwarp();
 
   // target of candidate flow f at pixel (px, py): plane phase and entry; in_win
@@ -492,6 +530,231 @@ __global__ void __launch_bounds__(PASS_MAX_WARPS * 32) k_pass(const SearchProble
   }
 }
 
+// Pass kernel for levels with few tiles (T <= 16): one 128-thread CTA per tile,
+// so that each diagonal step of the wavefront is spread over 8 threads per scan
+// row instead of one or two lanes. Thread t serves row j = t / 8: threads 0-3 of
+// the row evaluate its horizontal candidate and threads 4-7 its vertical one,
+// each over every fourth patch line (incremental) or row (full E_d), and the
+// row's first thread applies both in order (strict less). Sources are read from
+// the tile state in shared memory, one barrier per diagonal. Same schedule and
+// results as k_pass.
+constexpr int WIDE_THREADS = 128;
+constexpr int WIDE_SPLIT = 4;  // threads per candidate
+
+template <int R>
+__device__ __forceinline__ int part_line_delta(const uint32_t *so_, const uint32_t *si_, int ss,
+                                               const uint32_t *to_, const uint32_t *ti_, int ts,
+                                               int u) {
+  int acc = 0;
+#pragma unroll
+  for (int k = 0; k < (2 * R + WIDE_SPLIT) / WIDE_SPLIT; k++) {
+    const int w = u + WIDE_SPLIT * k;
+    if (w <= 2 * R)
+      acc += __popc(si_[w * ss] ^ ti_[w * ts]) - __popc(so_[w * ss] ^ to_[w * ts]);
+  }
+  return acc;
+}
+
+template <int R>
+__device__ __forceinline__ int part_full(const uint32_t *sc, int swp, const uint32_t *tc, int tp,
+                                         int u) {
+  int a0 = 0, a1 = 0;
+#pragma unroll
+  for (int k = 0; k < (2 * R + WIDE_SPLIT) / WIDE_SPLIT; k++) {
+    const int v = u + WIDE_SPLIT * k;
+    if (v <= 2 * R) {
+      const uint32_t *sr = sc + (v - R) * swp - R, *tr = tc + (v - R) * tp - R;
+#pragma unroll
+      for (int x = 0; x < 2 * R + 1; x++) {
+        const int pc = __popc(sr[x] ^ tr[x]);
+        if (x & 1) a1 += pc;
+        else a0 += pc;
+      }
+    }
+  }
+  return a0 + a1;
+}
+
+template <int R>
+__global__ void __launch_bounds__(WIDE_THREADS) k_pass_wide(const SearchProblem *probs, PassCfg cfg) {
+  extern __shared__ uint32_t smem[];
+  const SearchProblem &P = probs[blockIdx.y];
+  const int t = threadIdx.x, lane = t & 31;
+  const int Gx = P.src.NX, Gy = P.src.NY, n = P.src.n, log2n = P.src.log2n;
+  const int W = P.src.W, H = P.src.H;
+  const int T = cfg.tile, off = (cfg.s & 1) * (T >> 1);
+  const int ntx = (Gx + off + T - 1) / T, nty = (Gy + off + T - 1) / T;
+  if ((int)blockIdx.x >= ntx * nty) return;  // whole CTA
+  const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
+  const int x0 = max(tx * T - off, 0), x1 = min(tx * T - off + T, Gx);
+  const int y0 = max(ty * T - off, 0), y1 = min(ty * T - off + T, Gy);
+  const int tw = x1 - x0, th = y1 - y0;
+  const int hdx = c_pass_src[cfg.s][0][0], vdy = c_pass_src[cfg.s][1][1];
+  const TileLayout Lt(T, R);
+  const uint32_t *fin = (cfg.s & 1) ? P.flow_b : P.flow_a;
+  const int32_t *cin = (cfg.s & 1) ? P.cost_b : P.cost_a;
+  uint32_t *fout = (cfg.s & 1) ? P.flow_a : P.flow_b;
+  int32_t *cout = (cfg.s & 1) ? P.cost_a : P.cost_b;
+  if (cfg.last && P.flow_final) {
+    fout = P.flow_final;
+    cout = P.cost_final;
+  }
+  const uint32_t *tbase = P.tgt.base, *tbaseT = P.tgt.baseT;
+  const int tpitch = P.tgt.pitch, tpitchT = P.tgt.pitchT;
+  const size_t tpw_ = P.tgt.plane_words, tpwT = P.tgt.plane_wordsT;
+  const TileSmem S = carve_tile(smem, Lt, T);
+  int tox, toy, ph0;
+  stage_tile<R>(P, Lt, T, true, x0, y0, x1, y1, hdx, vdy, fin, cin, S, t, WIDE_THREADS, tox, toy,
+                ph0);
+  __syncthreads();
+
+  // target window hit: the whole patch plus one line inside the staged window
+  auto in_win = [&](int ph, int ex, int ey) {
+    return ph == ph0 && ex - R - 1 >= tox && ex + R + 1 < tox + Lt.tw && ey - R - 1 >= toy &&
+           ey + R + 1 < toy + Lt.tw;
+  };
+  auto clamp_flow = [&](int px, int py, uint32_t fq) {
+    const int tgx = clampi(px + flow_dx(fq), 0, W - 1), tgy = clampi(py + flow_dy(fq), 0, H - 1);
+    return pack_flow(tgx - px, tgy - py);
+  };
+
+  const int row = t >> 3, cand = (t >> 2) & 1, u = t & (WIDE_SPLIT - 1);
+  const int rbase = lane & ~7;
+  for (int d = 0; d < tw + th - 1; d++) {
+    const int jp = row, ip = d - row;
+    const bool on = jp < th && ip >= 0 && ip < tw;
+    int lx = 0, ly = 0, px = 0, py = 0;
+    uint32_t f0 = 0, fh = 0, fv = 0;
+    int32_t c0 = COST_UNSET, ch = COST_UNSET, cv = COST_UNSET;
+    bool hv = false, vv = false;
+    if (on) {
+      lx = hdx < 0 ? ip : tw - 1 - ip;
+      ly = vdy < 0 ? jp : th - 1 - jp;
+      const int gx = x0 + lx, gy = y0 + ly;
+      px = gx * n;
+      py = gy * n;
+      f0 = S.flow[ly * T + lx];
+      c0 = S.cost[ly * T + lx];
+      if (gx + hdx >= 0 && gx + hdx < Gx) {
+        fh = ip > 0 ? S.flow[ly * T + lx + hdx] : S.hf[ly];
+        ch = ip > 0 ? S.cost[ly * T + lx + hdx] : S.hc[ly];
+        hv = ch != COST_UNSET;
+      }
+      if (gy + vdy >= 0 && gy + vdy < Gy) {
+        fv = jp > 0 ? S.flow[(ly + vdy) * T + lx] : S.vf[lx];
+        cv = jp > 0 ? S.cost[(ly + vdy) * T + lx] : S.vc[lx];
+        vv = cv != COST_UNSET;
+      }
+    }
+    const bool set = c0 != COST_UNSET;
+    const uint32_t cfh = hv ? clamp_flow(px, py, fh) : 0u;
+    const bool useh = hv && !(set && cfh == f0);
+    const uint32_t cfv = vv ? clamp_flow(px, py, fv) : 0u;
+    const bool usev = vv && !(set && cfv == f0) && !(useh && cfv == cfh);
+    int part = 0;
+    if (on && (cand == 0 ? useh : usev)) {
+      const uint32_t fq = cand == 0 ? fh : fv, cf = cand == 0 ? cfh : cfv;
+      const int32_t cq = cand == 0 ? ch : cv;
+      const uint32_t *sc = S.src + (ly + R + 1) * Lt.swp + (lx + R + 1);
+      const int txx = px + flow_dx(cf), tyy = py + flow_dy(cf), m = n - 1;
+      const int ph = ((tyy & m) << log2n) + (txx & m);
+      const int ex = (txx >> log2n) + PLANE_PAD, ey = (tyy >> log2n) + PLANE_PAD;
+      const bool win = in_win(ph, ex, ey);
+      if (cf == fq) {  // incremental: E(q, f) - outgoing line + incoming line
+        const int step = cand == 0 ? hdx : vdy;
+        const int oo = step + step * R, oi = -step * R;
+        const uint32_t *so_, *si_, *to_, *ti_;
+        int ss, ts;
+        if (cand == 0) {  // column lines
+          ss = Lt.swp;
+          so_ = sc - R * Lt.swp + oo;
+          si_ = sc - R * Lt.swp + oi;
+          if (win) {
+            const uint32_t *tc = S.tgt + (ey - toy) * Lt.twp + (ex - tox);
+            ts = Lt.twp;
+            to_ = tc - R * Lt.twp + oo;
+            ti_ = tc - R * Lt.twp + oi;
+          } else {  // rows of the transposed plane
+            const uint32_t *tc = tbaseT + (size_t)ph * tpwT + (size_t)ex * tpitchT + ey;
+            ts = 1;
+            to_ = tc + oo * tpitchT - R;
+            ti_ = tc + oi * tpitchT - R;
+          }
+        } else {  // row lines
+          ss = 1;
+          so_ = sc + oo * Lt.swp - R;
+          si_ = sc + oi * Lt.swp - R;
+          const uint32_t *tc = win ? S.tgt + (ey - toy) * Lt.twp + (ex - tox)
+                                   : tbase + (size_t)ph * tpw_ + (size_t)ey * tpitch + ex;
+          const int tp = win ? Lt.twp : tpitch;
+          ts = 1;
+          to_ = tc + oo * tp - R;
+          ti_ = tc + oi * tp - R;
+        }
+        part = part_line_delta<R>(so_, si_, ss, to_, ti_, ts, u) + (u == 0 ? cq : 0);
+      } else if (win) {
+        part = part_full<R>(sc, Lt.swp, S.tgt + (ey - toy) * Lt.twp + (ex - tox), Lt.twp, u);
+      } else {
+        part = part_full<R>(sc, Lt.swp, tbase + (size_t)ph * tpw_ + (size_t)ey * tpitch + ex,
+                            tpitch, u);
+      }
+    }
+    part += __shfl_xor_sync(FULL_MASK, part, 1);
+    part += __shfl_xor_sync(FULL_MASK, part, 2);
+    const int cost_h = __shfl_sync(FULL_MASK, part, rbase), cost_v = __shfl_sync(FULL_MASK, part, rbase | 4);
+    if (on && (t & 7) == 0) {
+      uint32_t nf = f0;
+      int32_t nc = c0;
+      if (useh && cost_h < nc) {
+        nc = cost_h;
+        nf = cfh;
+      }
+      if (usev && cost_v < nc) {
+        nc = cost_v;
+        nf = cfv;
+      }
+      S.flow[ly * T + lx] = nf;
+      S.cost[ly * T + lx] = nc;
+    }
+    __syncthreads();
+  }
+
+  if (cfg.do_rs) {  // random search, one thread per point
+    const int Rn = cfg.R * n;
+    for (int i = t; i < tw * th; i += WIDE_THREADS) {
+      const int lx = i % tw, ly = i / tw;
+      const uint32_t cur = S.flow[ly * T + lx];
+      const int32_t cc = S.cost[ly * T + lx];
+      if (cc == COST_UNSET) continue;
+      const int gx = x0 + lx, gy = y0 + ly, px = gx * n, py = gy * n;
+      int ox, oy;
+      rs_offset(cfg.seed, P.flow_id, log2n, cfg.s, gx, gy, Rn, ox, oy);
+      const int tgx = clampi(px + flow_dx(cur) + ox, 0, W - 1);
+      const int tgy = clampi(py + flow_dy(cur) + oy, 0, H - 1);
+      const uint32_t cf = pack_flow(tgx - px, tgy - py);
+      if (cf == cur) continue;
+      const int m = n - 1, ph = ((tgy & m) << log2n) + (tgx & m);
+      const int ex = (tgx >> log2n) + PLANE_PAD, ey = (tgy >> log2n) + PLANE_PAD;
+      const uint32_t *sc = S.src + (ly + R + 1) * Lt.swp + (lx + R + 1);
+      const int cost = in_win(ph, ex, ey)
+                           ? lane_full<R>(sc, Lt.swp, S.tgt + (ey - toy) * Lt.twp + (ex - tox), Lt.twp)
+                           : lane_full<R>(sc, Lt.swp, tbase + (size_t)ph * tpw_ + (size_t)ey * tpitch + ex,
+                                          tpitch);
+      if (cost < cc) {
+        S.flow[ly * T + lx] = cf;
+        S.cost[ly * T + lx] = cost;
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = t; i < tw * th; i += WIDE_THREADS) {
+    const int lx = i % tw, ly = i / tw;
+    const size_t g = (size_t)(y0 + ly) * Gx + x0 + lx;
+    fout[g] = S.flow[ly * T + lx];
+    cout[g] = S.cost[ly * T + lx];
+  }
+}
+
 // One side stream per device, created on first use, lets problems of a second
 // patch radius (a separate kernel instantiation) run concurrently with the first:
 // fork with an event recorded on the caller's stream, join with one recorded on
@@ -520,15 +783,20 @@ static ff_status side_stream(SideStream **out) {
 }
 
 // Opt in to more than 48 KB of dynamic shared memory when a tile needs it.
-static ff_status set_pass_smem(int r, size_t bytes) {
-  static size_t done[9] = {0};
+static ff_status set_pass_smem(int r, size_t bytes, bool wide) {
+  static size_t done[2][9] = {{0}};
   if (r < 1 || r > 8) return FF_ERR_INVALID_ARG;
-  if (bytes <= done[r]) return FF_OK;
+  if (bytes <= done[wide][r]) return FF_OK;
   cudaError_t e = cudaSuccess;
-  FF_DISPATCH_R(r, e = cudaFuncSetAttribute(k_pass<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)bytes));
+  if (wide) {
+    FF_DISPATCH_R(r, e = cudaFuncSetAttribute(k_pass_wide<RR>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  } else {
+    FF_DISPATCH_R(r, e = cudaFuncSetAttribute(k_pass<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)bytes));
+  }
   if (e != cudaSuccess) return FF_ERR_CUDA;
-  done[r] = bytes;
+  done[wide][r] = bytes;
   return FF_OK;
 }
 
@@ -562,6 +830,8 @@ static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d
     FF_CHECK_LAUNCH();
   }
   const TileLayout lay(tile, r);
+  const int wide_min_n = exec_params().wide_min_n;
+  const bool wide = wide_min_n > 0 && probs[0].src.n >= wide_min_n && tile <= 16;
   int pw = exec_params().pass_warps;
   while (pw > 1 && sizeof(uint32_t) * (size_t)lay.words() * pw > 227u * 1024u) pw--;
   // a level with few tiles spreads them over the SMs (one CTA per SM at least)
@@ -569,8 +839,9 @@ static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d
   FF_TRY(sm_count(&nsm));
   const long tiles = (long)maxT * np;
   while (pw > 1 && (tiles + pw - 1) / pw < nsm) pw--;
+  if (wide) pw = 1;
   const size_t smem = sizeof(uint32_t) * (size_t)lay.words() * pw;
-  FF_TRY(set_pass_smem(r, smem));
+  FF_TRY(set_pass_smem(r, smem, wide));
   const int rs_min_n = exec_params().rs_min_n;
   const bool rs_kernel = rs_min_n > 0 && probs[0].src.n >= rs_min_n;
   for (int s = 0; s < 4; s++) {
@@ -578,7 +849,11 @@ static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d
     PassCfg cfg{s, tile, (do_rs && !rs_kernel) ? 1 : 0, R, seed, s == 3, lay.words()};
     dim3 g((maxT + pw - 1) / pw, np);
     if (prof_enabled()) prof_begin(st);
-    FF_DISPATCH_R(r, k_pass<RR><<<g, pw * 32, smem, st>>>(d, cfg));
+    if (wide) {
+      FF_DISPATCH_R(r, k_pass_wide<RR><<<g, WIDE_THREADS, smem, st>>>(d, cfg));
+    } else {
+      FF_DISPATCH_R(r, k_pass<RR><<<g, pw * 32, smem, st>>>(d, cfg));
+    }
     FF_CHECK_LAUNCH();
     if (prof_enabled()) prof_end(st);
     if (do_rs && rs_kernel) {

@@ -38,7 +38,8 @@ class Pair(C.Structure):
 
 class ExecParams(C.Structure):
     """ff_exec_params: launch shapes that never change results."""
-    _fields_ = [("pass_warps", C.c_int32), ("rs_min_n", C.c_int32), ("reserved", C.c_int32 * 6)]
+    _fields_ = [("pass_warps", C.c_int32), ("rs_min_n", C.c_int32), ("wide_min_n", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class NetDesc(C.Structure):
@@ -361,18 +362,19 @@ def profile_read():
     return dict(launches=n.value, prop_ms=ms.value, prop_launches=pn.value)
 
 
-def set_exec_params(pass_warps=None, rs_min_n=None):
+def set_exec_params(pass_warps=None, rs_min_n=None, wide_min_n=None):
     """Set execution parameters; arguments left as None keep their current value."""
     cur = get_exec_params()
     e = ExecParams(pass_warps=cur["pass_warps"] if pass_warps is None else pass_warps,
-                   rs_min_n=cur["rs_min_n"] if rs_min_n is None else rs_min_n)
+                   rs_min_n=cur["rs_min_n"] if rs_min_n is None else rs_min_n,
+                   wide_min_n=cur["wide_min_n"] if wide_min_n is None else wide_min_n)
     _check("ff_set_exec_params", lib().ff_set_exec_params(C.byref(e)))
 
 
 def get_exec_params():
     e = ExecParams()
     _check("ff_get_exec_params", lib().ff_get_exec_params(C.byref(e)))
-    return dict(pass_warps=e.pass_warps, rs_min_n=e.rs_min_n)
+    return dict(pass_warps=e.pass_warps, rs_min_n=e.rs_min_n, wide_min_n=e.wide_min_n)
 
 
 class FlowFieldsBatch:

@@ -2,10 +2,11 @@
 
 It times candidate launch shapes on the caller's workload and keeps the fastest.
 Only parameters that leave every result unchanged are tuned: tiles per CTA of the
-propagation kernel, and from which level spacing on the random search runs as a
-kernel of its own. The tile edge T of the parallel schedule is part of the
-method's definition and stays as given. The search is coordinate-wise: tiles per
-CTA first (random search in the pass kernel), then the random-search split. Choices are cached in a small JSON file
+propagation kernel, from which level spacing on the random search runs as a
+kernel of its own, and from which spacing on the propagation runs one CTA per
+tile. The tile edge T of the parallel schedule is part of the method's
+definition and stays as given. The search is coordinate-wise, one parameter at a
+time in that order. Choices are cached in a small JSON file
 keyed by GPU name, image sizes and method parameters.
 """
 from __future__ import annotations
@@ -17,7 +18,7 @@ import torch
 
 from . import ffapi, synth
 
-CANDIDATES = dict(pass_warps=(1, 2, 4, 8), rs_min_n=(0, 1, 2, 4, 8))
+CANDIDATES = dict(pass_warps=(1, 2, 4, 8), rs_min_n=(0, 1, 2, 4, 8), wide_min_n=(0, 1, 2, 4, 8))
 _CACHE = os.environ.get("FF_TUNE_CACHE",
                         os.path.join(os.path.expanduser("~"), ".cache", "flowfields_tune.json"))
 
@@ -83,20 +84,17 @@ def tune(sizes, params=None, frames=None, reps=3, use_cache=True, seed=0):
     batch = ffapi.FlowFieldsBatch(sizes, params)
     before = ffapi.get_exec_params()
     timings = {}
-    best_pw, best_t = None, None
-    for pw in CANDIDATES["pass_warps"]:
-        ffapi.set_exec_params(pass_warps=pw, rs_min_n=0)
-        t = timings[f"pass_warps={pw},rs_min_n=0"] = time_batch(batch, frames, reps)
-        if best_t is None or t < best_t:
-            best_pw, best_t = pw, t
-    choice = dict(pass_warps=best_pw, rs_min_n=0)
-    for rs in CANDIDATES["rs_min_n"]:
-        if rs == 0:
-            continue
-        ffapi.set_exec_params(pass_warps=best_pw, rs_min_n=rs)
-        t = timings[f"pass_warps={best_pw},rs_min_n={rs}"] = time_batch(batch, frames, reps)
-        if t < best_t:
-            choice, best_t = dict(pass_warps=best_pw, rs_min_n=rs), t
+    choice = dict(pass_warps=4, rs_min_n=0, wide_min_n=0)
+    best_t = None
+    for name in ("pass_warps", "rs_min_n", "wide_min_n"):  # one parameter at a time
+        for v in CANDIDATES[name]:
+            trial = dict(choice, **{name: v})
+            tk = ",".join(f"{k}={trial[k]}" for k in sorted(trial))
+            if tk not in timings:
+                ffapi.set_exec_params(**trial)
+                timings[tk] = time_batch(batch, frames, reps)
+            if best_t is None or timings[tk] < best_t:
+                choice, best_t = trial, timings[tk]
     ffapi.set_exec_params(**choice)
     rec = dict(choice=choice, timings=timings, before=before)
     if use_cache:
