@@ -252,7 +252,10 @@ def run_ours(args):
     flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
     # result-neutral launch shapes picked by the autotuner for this workload
-    tuned = tune.tune([(W, H)], PARAMS, frames=[dI[0]], reps=5, use_cache=False)
+    if args.no_tune:
+        tuned = {"choice": ffapi.get_exec_params()}
+    else:
+        tuned = tune.tune([(W, H)], PARAMS, frames=[dI[0]], reps=5, use_cache=False)
     # the public paths: one pair as a captured CUDA graph (headline) and the
     # direct call (also timed, with per-launch events for the roofline)
     graph = ffapi.FlowFieldsBatch([(W, H)], PARAMS, dev, graph=True)
@@ -377,6 +380,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-pair batch line")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip training and evaluating the proposal net")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the library's default execution parameters (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

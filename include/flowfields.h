@@ -260,13 +260,17 @@ ff_status ff_graph_destroy(ff_graph *g);
  *               so both forms give the same result.
  *   wide_min_n  0: every level runs the propagation with one warp per tile; else
  *               levels with spacing n >= wide_min_n (a power of two, 1..128; only
- *               for tiles of edge <= 16) run it with one 128-thread CTA per tile,
- *               eight threads per scan row (same schedule, same results). */
+ *               for tiles of edge <= 16) run it with one CTA per tile and
+ *               8 threads per scan row (same schedule, same results)
+ *   split8_min_n  0: that form uses 4 threads per candidate (128-thread CTAs);
+ *               else levels with n >= split8_min_n (a power of two, 1..128) use 8
+ *               (256-thread CTAs, 16 threads per scan row) */
 typedef struct ff_exec_params {
   int32_t pass_warps;
   int32_t rs_min_n;
   int32_t wide_min_n;
-  int32_t reserved[5];
+  int32_t split8_min_n;
+  int32_t reserved[4];
 } ff_exec_params;
 ff_status ff_set_exec_params(const ff_exec_params *e);
 ff_status ff_get_exec_params(ff_exec_params *e);

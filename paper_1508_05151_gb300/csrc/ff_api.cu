@@ -19,7 +19,7 @@ static bool g_prof = false;
 static std::vector<cudaEvent_t> g_ev;  // pairs (begin, end)
 static size_t g_ev_used = 0;
 
-static ff_exec_params g_exec = {4, 0, 1, {0, 0, 0, 0, 0}};
+static ff_exec_params g_exec = {4, 0, 1, 2, {0, 0, 0, 0}};
 const ff_exec_params &exec_params() { return g_exec; }
 
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
@@ -708,7 +708,7 @@ ff_status ff_device_status(const void *ws, uint32_t *code, int32_t *x, int32_t *
 ff_status ff_set_exec_params(const ff_exec_params *e) {
   auto pow2_or_0 = [](int v) { return v >= 0 && v <= 128 && (v & (v - 1)) == 0; };
   if (!e || e->pass_warps < 1 || e->pass_warps > 8 || !pow2_or_0(e->rs_min_n) ||
-      !pow2_or_0(e->wide_min_n))
+      !pow2_or_0(e->wide_min_n) || !pow2_or_0(e->split8_min_n))
     return FF_ERR_INVALID_ARG;
   g_exec = *e;
   return FF_OK;

@@ -109,11 +109,18 @@ __global__ void __launch_bounds__(512) k_features_all(const uint8_t *__restrict_
 }
 
 // Features at a point list or at the grid of spacing grid_n; direct block sums.
-__global__ void k_features_pts(const uint8_t *__restrict__ img, int W, int H, int r,
-                               const int32_t *__restrict__ pts, int npts, int grid_n, int Gx,
-                               int32_t *__restrict__ feat) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= npts) return;
+// Point-list kernel: one warp per point. Lanes 0..15 each sum one of the 4 x 4
+// blocks (a = lane / 4 rows, b = lane % 4 columns) for the three channels, then
+// lanes 0..2 combine their channel's 16 sums into its 9 features.
+constexpr int PTS_WARPS = 4;
+
+__global__ void __launch_bounds__(PTS_WARPS * 32) k_features_pts(
+    const uint8_t *__restrict__ img, int W, int H, int r, const int32_t *__restrict__ pts, int npts,
+    int grid_n, int Gx, int32_t *__restrict__ feat) {
+  __shared__ int sS[PTS_WARPS][3][4][4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * PTS_WARPS + warp;
+  if (k >= npts) return;  // whole warp
   int x, y;
   if (pts) {
     x = pts[2 * k];
@@ -127,25 +134,30 @@ __global__ void k_features_pts(const uint8_t *__restrict__ img, int W, int H, in
   wht_blocks(L, sz);
   st[0] = 0;
   for (int a = 0; a < 4; a++) st[a + 1] = st[a] + sz[a];
-  int32_t out[FEAT_STRIDE];
-  for (int c = 0; c < 3; c++) {
-    int S[4][4];
-    for (int a = 0; a < 4; a++)
-      for (int b = 0; b < 4; b++) {
-        int s = 0;
-        for (int v = st[a]; v < st[a + 1]; v++) {
-          int yy = clampi(y - r + v, 0, H - 1);
-          for (int u = st[b]; u < st[b + 1]; u++) {
-            int xx = clampi(x - r + u, 0, W - 1);
-            s += img[((size_t)yy * W + xx) * 3 + c];
-          }
-        }
-        S[a][b] = s;
+  if (lane < 16) {
+    const int a = lane >> 2, b = lane & 3;
+    int s0 = 0, s1 = 0, s2 = 0;
+    for (int v = st[a]; v < st[a + 1]; v++) {
+      const int yy = clampi(y - r + v, 0, H - 1);
+      for (int u = st[b]; u < st[b + 1]; u++) {
+        const uint8_t *q = img + ((size_t)yy * W + clampi(x - r + u, 0, W - 1)) * 3;
+        s0 += q[0];
+        s1 += q[1];
+        s2 += q[2];
       }
-    combine9(S, out + 9 * c);
+    }
+    sS[warp][0][a][b] = s0;
+    sS[warp][1][a][b] = s1;
+    sS[warp][2][a][b] = s2;
   }
-  out[27] = 0;
-  for (int q = 0; q < FEAT_STRIDE; q++) feat[(size_t)k * FEAT_STRIDE + q] = out[q];
+  __syncwarp();
+  if (lane < 3) {
+    int32_t out[9];
+    combine9(sS[warp][lane], out);
+    for (int q = 0; q < 9; q++) feat[(size_t)k * FEAT_STRIDE + 9 * lane + q] = out[q];
+  } else if (lane == 3) {
+    feat[(size_t)k * FEAT_STRIDE + 27] = 0;
+  }
 }
 
 ff_status launch_features(const uint8_t *img, int W, int H, int r, const int32_t *pts, int npts,
@@ -166,7 +178,8 @@ ff_status launch_features(const uint8_t *img, int W, int H, int r, const int32_t
   int Gx = (W + grid_n - 1) / grid_n;
   if (!pts) npts = Gx * ((H + grid_n - 1) / grid_n);
   if (npts <= 0) return FF_OK;
-  k_features_pts<<<(npts + 127) / 128, 128, 0, st>>>(img, W, H, r, pts, npts, grid_n, Gx, feat);
+  k_features_pts<<<(npts + PTS_WARPS - 1) / PTS_WARPS, PTS_WARPS * 32, 0, st>>>(img, W, H, r, pts,
+                                                                                 npts, grid_n, Gx, feat);
   FF_CHECK_LAUNCH();
   return FF_OK;
 }

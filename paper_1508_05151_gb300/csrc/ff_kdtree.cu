@@ -16,10 +16,10 @@
 //                        key = (value - min) << ibits | pixel index (unique);
 //                        the first pass caches every position's key
 //     partition          key < selected key -> left child, else right
-//   bottom levels: one 1024-thread CTA per segment finishes its whole subtree:
-//     per sub-level one CTA-wide bitonic sort of (node, value, pixel-index rank)
-//     keys sorts every node by (value, index), so the left half is the first
-//     floor(m/2).
+//   bottom levels: one 1024-thread CTA per segment finishes its whole subtree in
+//     shared memory: nodes own aligned power-of-two slot blocks; per sub-level a
+//     bitonic sort of each block by (value, pixel-index rank) puts the left child
+//     first, then the right child moves to the block's second half.
 #include "ff_internal.cuh"
 
 namespace ff {
@@ -416,15 +416,16 @@ __global__ void __launch_bounds__(256) k_kd_partition(KdBuild *trees, int d) {
   }
 }
 
-// Ascending bitonic sort of one 64-bit key per thread over the CTA's SUB_MAX
-// threads (thread t ends with the t-th smallest key). Exchanges with partners
-// inside the warp use shuffles; wider ones go through shared memory (two
-// buffers, so one barrier per step suffices).
-__device__ __forceinline__ unsigned long long bitonic_sort_cta(unsigned long long c,
-                                                               unsigned long long *buf) {
+// Ascending bitonic sort of one 64-bit key per thread within aligned blocks of
+// B threads (B a power of two, 2..SUB_MAX): thread t ends with the (t mod B)-th
+// smallest key of its block. Exchanges with partners inside the warp use
+// shuffles; wider ones go through shared memory (two buffers, so one barrier per
+// step suffices). Every thread of the CTA must call it with the same B.
+__device__ __forceinline__ unsigned long long bitonic_sort_blocks(unsigned long long c, int B,
+                                                                  unsigned long long *buf) {
   const int t = threadIdx.x;
   int flip = 0;
-  for (int k = 2; k <= SUB_MAX; k <<= 1) {
+  for (int k = 2; k <= B; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       unsigned long long o;
       if (j >= 32) {
@@ -436,7 +437,7 @@ __device__ __forceinline__ unsigned long long bitonic_sort_cta(unsigned long lon
       } else {
         o = __shfl_xor_sync(0xffffffffu, c, j);
       }
-      const bool up = (t & k) == 0, lower = (t & j) == 0;
+      const bool up = (k == B) || ((t & k) == 0), lower = (t & j) == 0;
       c = (lower == up) ? (o < c ? o : c) : (o > c ? o : c);
     }
   }
@@ -444,110 +445,153 @@ __device__ __forceinline__ unsigned long long bitonic_sort_cta(unsigned long lon
 }
 
 // One 1024-thread CTA finishes the subtree of one segment at depth top_levels.
-// Thread t owns the segment's t-th smallest pixel index for all sub-levels and
-// keeps its 27 features in registers. Per sub-level: the node min/max per
-// dimension (warp reductions over threads of one node, then shared atomics), the
-// split dimension, then one CTA-wide sort of the keys
-//   (node << 54) | (value - node min) << 10 | t,
-// which orders every node's points by (value, pixel index) in place, because the
-// owners are numbered in pixel-index order. A point's sorted position gives its
-// rank in the node; the rank-floor(m/2) point is the split.
-__global__ void __launch_bounds__(1024) k_kd_subtree(KdBuild *trees, int max_nodes) {
+// The segment's points live in shared memory with their 27 features; at
+// sub-level sd node j owns the aligned slot block [j B, j B + B), B = 1024 >> sd,
+// its m_j points first. Per sub-level: per-node min/max of every dimension
+// (segmented warp reductions, then shared atomics across warps), the split
+// dimension, a bitonic sort of each block by (value - node min, pixel-index
+// rank, slot), and one move of every point to its child's block: the first
+// floor(m/2) stay, the others go to the second half. The first point of the
+// right half is the split. The pixel-index rank (0..1023) breaks ties exactly as
+// the pixel index does; it is set once by sorting the segment's indices.
+constexpr int SUB_SD_SMEM_NODES = SUB_MAX / 64;  // nodes with blocks wider than a warp
+
+__global__ void __launch_bounds__(SUB_MAX) k_kd_subtree(KdBuild *trees) {
   KdBuild &T = trees[blockIdx.y];
   const int d0 = T.top_levels;
   if (blockIdx.x >= (1u << d0)) return;
   const int b0 = seg_begin(T.N, d0, blockIdx.x), e0 = seg_begin(T.N, d0, blockIdx.x + 1);
   const int m0 = e0 - b0;
   extern __shared__ __align__(16) int32_t ssub[];
-  unsigned long long *sbuf = (unsigned long long *)ssub;  // 2 x SUB_MAX
-  int32_t *spos = ssub + 4 * SUB_MAX;                     // SUB_MAX
-  int(*smin)[NFEAT] = (int(*)[NFEAT])(spos + SUB_MAX);
-  int(*smax)[NFEAT] = smin + max_nodes;
-  int *sdim = (int *)(smax + max_nodes);
+  unsigned long long *sbuf = (unsigned long long *)ssub;  // 2 x SUB_MAX sort buffers
+  unsigned long long *ssorted = sbuf + 2 * SUB_MAX;       // SUB_MAX sorted keys
+  int32_t *sF = (int32_t *)(ssorted + SUB_MAX);           // SUB_MAX x NFEAT features
+  int32_t *sidx = sF + SUB_MAX * NFEAT;                    // pixel index per slot
+  int32_t *srank = sidx + SUB_MAX;                         // pixel-index rank per slot
+  int32_t *ssize = srank + SUB_MAX;                        // 2 x SUB_MAX node sizes (ping-pong)
+  int32_t *sstart = ssize + 2 * SUB_MAX;                   // 2 x SUB_MAX node starts
+  int32_t *smin = sstart + 2 * SUB_MAX;                    // SUB_SD_SMEM_NODES x NFEAT
+  int32_t *smax = smin + SUB_SD_SMEM_NODES * NFEAT;
   const int t = threadIdx.x, lane = t & 31;
-  const bool act = t < m0;
-  // owners in pixel-index order
-  const unsigned long long raw = act ? (unsigned long long)(uint32_t)cur_perm(T, d0)[b0 + t] : ~0ull;
-  const unsigned long long srt = bitonic_sort_cta(raw, sbuf);
-  const int idx = act ? (int)srt : 0;
-  int4 q[7];
-  if (act) {
-    const int4 *row = (const int4 *)(T.feat + (size_t)idx * FEAT_STRIDE);
+  // slots in pixel-index order: slot t holds the t-th smallest index, rank t
+  {
+    const unsigned long long raw =
+        t < m0 ? (unsigned long long)(uint32_t)cur_perm(T, d0)[b0 + t] : ~0ull;
+    const unsigned long long srt = bitonic_sort_blocks(raw, SUB_MAX, sbuf);
+    if (t < m0) {
+      const int idx = (int)srt;
+      sidx[t] = idx;
+      srank[t] = t;
+      const int32_t *row = T.feat + (size_t)idx * FEAT_STRIDE;
 #pragma unroll
-    for (int k = 0; k < 7; k++) q[k] = row[k];
-  } else {
-#pragma unroll
-    for (int k = 0; k < 7; k++) q[k] = make_int4(0, 0, 0, 0);
+      for (int k = 0; k < NFEAT; k++) sF[t * NFEAT + k] = row[k];
+    }
+    if (t == 0) {
+      ssize[0] = m0;
+      sstart[0] = 0;
+    }
   }
-  const int *v = (const int *)q;
-  int nb = 0, ne = m0, nid = 0, pos = t;  // this point's node and position
   const int levels = T.D - d0;
+  int pp = 0;  // ping-pong half of the node arrays
   for (int sd = 0; sd < levels; sd++) {
-    const int nnodes = 1 << sd;
-    for (int i = t; i < nnodes * NFEAT; i += blockDim.x) {
-      smin[i / NFEAT][i % NFEAT] = INT32_MAX;
-      smax[i / NFEAT][i % NFEAT] = INT32_MIN;
-    }
-    __syncthreads();
-    const unsigned grp = __match_any_sync(0xffffffffu, act ? nid : -1);
-    const bool leader = (__ffs(grp) - 1) == lane;
-#pragma unroll
-    for (int dim = 0; dim < NFEAT; dim++) {
-      const int lo = __reduce_min_sync(grp, v[dim]), hi = __reduce_max_sync(grp, v[dim]);
-      if (act && leader) {
-        atomicMin(&smin[nid][dim], lo);
-        atomicMax(&smax[nid][dim], hi);
+    const int B = SUB_MAX >> sd, j = t / B, o = t & (B - 1);
+    if (B > 32)
+      for (int i = t; i < (SUB_MAX / B) * NFEAT; i += SUB_MAX) {
+        smin[i] = INT32_MAX;
+        smax[i] = INT32_MIN;
       }
-    }
     __syncthreads();
-    for (int i = t; i < nnodes; i += blockDim.x) {
-      int best = 0;
-      long long bs = -1;
-      for (int dim = 0; dim < NFEAT; dim++) {
-        const long long sp = (long long)smax[i][dim] - smin[i][dim];
-        if (sp > bs) {
-          bs = sp;
-          best = dim;
+    const int m = ssize[pp * SUB_MAX + j], st = sstart[pp * SUB_MAX + j];
+    const bool valid = o < m;
+    // per-node min/max of every dimension and the split dimension
+    const unsigned bmask = B >= 32 ? 0xffffffffu : (((1u << B) - 1u) << (lane & ~(B - 1)));
+    int dim = 0, dmin = 0;
+    {
+      long long best = -1;
+#pragma unroll 1
+      for (int k = 0; k < NFEAT; k++) {
+        const int v = valid ? sF[t * NFEAT + k] : 0;
+        const int lo = __reduce_min_sync(bmask, valid ? v : INT32_MAX);
+        const int hi = __reduce_max_sync(bmask, valid ? v : INT32_MIN);
+        if (B > 32) {
+          if (lane == 0) {
+            atomicMin(&smin[j * NFEAT + k], lo);
+            atomicMax(&smax[j * NFEAT + k], hi);
+          }
+        } else if (m > 0 && (long long)hi - lo > best) {
+          best = (long long)hi - lo;
+          dim = k;
+          dmin = lo;
         }
       }
-      sdim[i] = best;
+      if (B > 32) {
+        __syncthreads();
+        for (int k = 0; k < NFEAT; k++) {
+          const long long sp = (long long)smax[j * NFEAT + k] - smin[j * NFEAT + k];
+          if (sp > best) {
+            best = sp;
+            dim = k;
+            dmin = smin[j * NFEAT + k];
+          }
+        }
+      }
     }
+    const unsigned long long key =
+        valid ? ((unsigned long long)(uint32_t)(sF[t * NFEAT + dim] - dmin) << 20) |
+                    ((unsigned long long)srank[t] << 10) | (unsigned)t
+              : ~0ull;
+    const unsigned long long sorted = bitonic_sort_blocks(key, B, sbuf);
+    ssorted[t] = sorted;
     __syncthreads();
-    const int dim = act ? sdim[nid] : 0;
-    int key = 0;
+    // move: the first floor(m/2) stay at the front of the block, the others go
+    // to the front of its second half
+    const int h = m >> 1, half = B >> 1;
+    const int sp = o < half ? o : h + (o - half);
+    const bool take = o < half ? o < h : sp < m;
+    int32_t f[NFEAT];
+    int pidx = 0, prank = 0;
+    if (take) {
+      const int src = (int)(ssorted[j * B + sp] & 1023u);
 #pragma unroll
-    for (int k = 0; k < NFEAT; k++)
-      if (k == dim) key = v[k];
-    const unsigned long long c =
-        act ? ((unsigned long long)nid << 54) |
-                  ((unsigned long long)(uint32_t)(key - smin[nid][dim]) << 10) | (unsigned)t
-            : ~0ull;
-    const unsigned long long sorted = bitonic_sort_cta(c, sbuf);
-    if (t < m0) spos[(int)(sorted & 1023u)] = t;
-    __syncthreads();
-    if (act) {
-      pos = spos[t];
-      const int half = (ne - nb) >> 1, rank = pos - nb;
-      if (rank == half) {
-        const int node = (1 << (d0 + sd)) - 1 + (blockIdx.x << sd) + nid;
-        T.split_dim[node] = dim;
-        T.split_val[node] = key;
-      }
-      if (rank < half) {
-        ne = nb + half;
-        nid = 2 * nid;
-      } else {
-        nb = nb + half;
-        nid = 2 * nid + 1;
-      }
+      for (int k = 0; k < NFEAT; k++) f[k] = sF[src * NFEAT + k];
+      pidx = sidx[src];
+      prank = srank[src];
     }
     __syncthreads();
+    if (take) {
+#pragma unroll
+      for (int k = 0; k < NFEAT; k++) sF[t * NFEAT + k] = f[k];
+      sidx[t] = pidx;
+      srank[t] = prank;
+      if (o == half) {  // the first point of the right child is the split
+        const int node = (1 << (d0 + sd)) - 1 + (blockIdx.x << sd) + j;
+        T.split_dim[node] = dim;
+        int sv = 0;
+#pragma unroll
+        for (int k = 0; k < NFEAT; k++)
+          if (k == dim) sv = f[k];
+        T.split_val[node] = sv;
+      }
+    }
+    if (o == 0) {
+      const int q = (pp ^ 1) * SUB_MAX + 2 * j;
+      ssize[q] = h;
+      ssize[q + 1] = m - h;
+      sstart[q] = st;
+      sstart[q + 1] = st + h;
+    }
+    pp ^= 1;
   }
-  if (act) T.perm[b0 + pos] = idx;
+  __syncthreads();
+  {
+    const int B = SUB_MAX >> levels, j = t / B, o = t & (B - 1);
+    if (o < ssize[pp * SUB_MAX + j]) T.perm[b0 + sstart[pp * SUB_MAX + j] + o] = sidx[t];
+  }
 }
 
-static size_t subtree_smem(int max_nodes) {
-  return sizeof(int32_t) * (5 * SUB_MAX + 2 * (size_t)max_nodes * NFEAT + max_nodes);
+static size_t subtree_smem() {
+  return sizeof(unsigned long long) * 3 * SUB_MAX +
+         sizeof(int32_t) * ((size_t)SUB_MAX * NFEAT + 6 * SUB_MAX + 2 * SUB_SD_SMEM_NODES * NFEAT);
 }
 
 ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaStream_t st) {
@@ -585,8 +629,8 @@ ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaSt
     k_kd_partition<<<dim3((maxN + PART_CHUNK - 1) / PART_CHUNK, ntrees), 256, 0, st>>>(dev, d);
     FF_CHECK_LAUNCH();
   }
-  const int max_nodes = maxSub > 0 ? 1 << (maxSub - 1) : 1;
-  const size_t smem = subtree_smem(max_nodes);
+  if (maxSub > 10) return FF_ERR_INVALID_ARG;  // segments <= SUB_MAX points, leaf >= 1
+  const size_t smem = subtree_smem();
   static size_t attr = 0;
   if (smem > attr) {
     if (cudaFuncSetAttribute(k_kd_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -594,7 +638,7 @@ ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaSt
       return FF_ERR_CUDA;
     attr = smem;
   }
-  k_kd_subtree<<<dim3(1 << maxT, ntrees), SUB_MAX, smem, st>>>(dev, max_nodes);
+  k_kd_subtree<<<dim3(1 << maxT, ntrees), SUB_MAX, smem, st>>>(dev);
   FF_CHECK_LAUNCH();
   return FF_OK;
 }

@@ -34,31 +34,35 @@ namespace ff {
 __constant__ int c_pass_src[4][2][2] = {
     {{-1, 0}, {0, -1}}, {{1, 0}, {0, 1}}, {{1, 0}, {0, -1}}, {{-1, 0}, {0, 1}}};
 
+// Level seeding. One 16-lane group per 2x2 block of grid points (grid-stride):
+// the even-even point takes the coarse flow and its E_d at this level, the other
+// three start unset.
 template <int R>
 __global__ void __launch_bounds__(256) k_seed(const SearchProblem *probs) {
   const SearchProblem &P = probs[blockIdx.y];
-  const int NX = P.src.NX, G = NX * P.src.NY, n = P.src.n;
-  const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const int NX = P.src.NX, NY = P.src.NY, n = P.src.n;
+  const int NXc = (NX + 1) >> 1, Gc = NXc * ((NY + 1) >> 1);  // = the coarse grid
   const int l16 = threadIdx.x & 15;
   const unsigned gmask = 0xffffu << (threadIdx.x & 16);
-  if (g >= G) return;
-  const int gx = g % NX, gy = g / NX;
-  if ((gx | gy) & 1) {
-    if (l16 == 0) {
-      P.flow_a[g] = 0;
-      P.cost_a[g] = COST_UNSET;
+  const int stride = (gridDim.x * blockDim.x) >> 4;
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 4; c < Gc; c += stride) {
+    const int gx = (c % NXc) * 2, gy = (c / NXc) * 2;
+    if (l16 >= 1 && l16 <= 3) {
+      const int ox = gx + (l16 & 1), oy = gy + (l16 >> 1);
+      if (ox < NX && oy < NY) {
+        P.flow_a[(size_t)oy * NX + ox] = 0;
+        P.cost_a[(size_t)oy * NX + ox] = COST_UNSET;
+      }
     }
-    return;
-  }
-  const int NXc = (P.src.W + 2 * n - 1) / (2 * n);
-  const uint32_t f = P.flow_coarse[(size_t)(gy >> 1) * NXc + (gx >> 1)];
-  const int px = gx * n, py = gy * n;
-  const int tx = clampi(px + flow_dx(f), 0, P.src.W - 1), ty = clampi(py + flow_dy(f), 0, P.src.H - 1);
-  const int cost = group_cost<R>(plane_centre(P.src, px, py), P.src.pitch,
-                                 plane_centre(P.tgt, tx, ty), P.tgt.pitch, l16, gmask);
-  if (l16 == 0) {
-    P.flow_a[g] = pack_flow(tx - px, ty - py);
-    P.cost_a[g] = cost;
+    const uint32_t f = P.flow_coarse[c];
+    const int px = gx * n, py = gy * n;
+    const int tx = clampi(px + flow_dx(f), 0, P.src.W - 1), ty = clampi(py + flow_dy(f), 0, P.src.H - 1);
+    const int cost = group_cost<R>(plane_centre(P.src, px, py), P.src.pitch,
+                                   plane_centre(P.tgt, tx, ty), P.tgt.pitch, l16, gmask);
+    if (l16 == 0) {
+      P.flow_a[(size_t)gy * NX + gx] = pack_flow(tx - px, ty - py);
+      P.cost_a[(size_t)gy * NX + gx] = cost;
+    }
   }
 }
 
@@ -530,38 +534,37 @@ __global__ void __launch_bounds__(PASS_MAX_WARPS * 32) k_pass(const SearchProble
   }
 }
 
-// Pass kernel for levels with few tiles (T <= 16): one 128-thread CTA per tile,
-// so that each diagonal step of the wavefront is spread over 8 threads per scan
-// row instead of one or two lanes. Thread t serves row j = t / 8: threads 0-3 of
-// the row evaluate its horizontal candidate and threads 4-7 its vertical one,
-// each over every fourth patch line (incremental) or row (full E_d), and the
-// row's first thread applies both in order (strict less). Sources are read from
-// the tile state in shared memory, one barrier per diagonal. Same schedule and
+// Pass kernel with one CTA per tile (T <= 16): each diagonal step of the
+// wavefront is spread over 2 * SPLIT threads per scan row instead of one or two
+// lanes. Thread t serves row j = t / (2 SPLIT): the first SPLIT threads of the
+// row evaluate its horizontal candidate and the next SPLIT its vertical one, each
+// over every SPLIT-th patch line (incremental) or row (full E_d), and the row's
+// first thread applies both in order (strict less). Sources are read from the
+// tile state in shared memory, one barrier per diagonal. Same schedule and
 // results as k_pass.
-constexpr int WIDE_THREADS = 128;
-constexpr int WIDE_SPLIT = 4;  // threads per candidate
-
-template <int R>
+// SPLIT threads per candidate (4 or 8, an execution parameter): 32 * SPLIT
+// threads per CTA.
+template <int R, int SPLIT>
 __device__ __forceinline__ int part_line_delta(const uint32_t *so_, const uint32_t *si_, int ss,
                                                const uint32_t *to_, const uint32_t *ti_, int ts,
                                                int u) {
   int acc = 0;
 #pragma unroll
-  for (int k = 0; k < (2 * R + WIDE_SPLIT) / WIDE_SPLIT; k++) {
-    const int w = u + WIDE_SPLIT * k;
+  for (int k = 0; k < (2 * R + SPLIT) / SPLIT; k++) {
+    const int w = u + SPLIT * k;
     if (w <= 2 * R)
       acc += __popc(si_[w * ss] ^ ti_[w * ts]) - __popc(so_[w * ss] ^ to_[w * ts]);
   }
   return acc;
 }
 
-template <int R>
+template <int R, int SPLIT>
 __device__ __forceinline__ int part_full(const uint32_t *sc, int swp, const uint32_t *tc, int tp,
                                          int u) {
   int a0 = 0, a1 = 0;
 #pragma unroll
-  for (int k = 0; k < (2 * R + WIDE_SPLIT) / WIDE_SPLIT; k++) {
-    const int v = u + WIDE_SPLIT * k;
+  for (int k = 0; k < (2 * R + SPLIT) / SPLIT; k++) {
+    const int v = u + SPLIT * k;
     if (v <= 2 * R) {
       const uint32_t *sr = sc + (v - R) * swp - R, *tr = tc + (v - R) * tp - R;
 #pragma unroll
@@ -575,8 +578,9 @@ __device__ __forceinline__ int part_full(const uint32_t *sc, int swp, const uint
   return a0 + a1;
 }
 
-template <int R>
-__global__ void __launch_bounds__(WIDE_THREADS) k_pass_wide(const SearchProblem *probs, PassCfg cfg) {
+template <int R, int SPLIT>
+__global__ void __launch_bounds__(32 * SPLIT) k_pass_wide(const SearchProblem *probs, PassCfg cfg) {
+  constexpr int WIDE_THREADS = 32 * SPLIT;
   extern __shared__ uint32_t smem[];
   const SearchProblem &P = probs[blockIdx.y];
   const int t = threadIdx.x, lane = t & 31;
@@ -618,8 +622,8 @@ __global__ void __launch_bounds__(WIDE_THREADS) k_pass_wide(const SearchProblem 
     return pack_flow(tgx - px, tgy - py);
   };
 
-  const int row = t >> 3, cand = (t >> 2) & 1, u = t & (WIDE_SPLIT - 1);
-  const int rbase = lane & ~7;
+  const int row = t / (2 * SPLIT), cand = (t / SPLIT) & 1, u = t & (SPLIT - 1);
+  const int rbase = lane & ~(2 * SPLIT - 1);
   for (int d = 0; d < tw + th - 1; d++) {
     const int jp = row, ip = d - row;
     const bool on = jp < th && ip >= 0 && ip < tw;
@@ -691,18 +695,19 @@ __global__ void __launch_bounds__(WIDE_THREADS) k_pass_wide(const SearchProblem 
           to_ = tc + oo * tp - R;
           ti_ = tc + oi * tp - R;
         }
-        part = part_line_delta<R>(so_, si_, ss, to_, ti_, ts, u) + (u == 0 ? cq : 0);
+        part = part_line_delta<R, SPLIT>(so_, si_, ss, to_, ti_, ts, u) + (u == 0 ? cq : 0);
       } else if (win) {
-        part = part_full<R>(sc, Lt.swp, S.tgt + (ey - toy) * Lt.twp + (ex - tox), Lt.twp, u);
+        part = part_full<R, SPLIT>(sc, Lt.swp, S.tgt + (ey - toy) * Lt.twp + (ex - tox), Lt.twp, u);
       } else {
-        part = part_full<R>(sc, Lt.swp, tbase + (size_t)ph * tpw_ + (size_t)ey * tpitch + ex,
-                            tpitch, u);
+        part = part_full<R, SPLIT>(sc, Lt.swp, tbase + (size_t)ph * tpw_ + (size_t)ey * tpitch + ex,
+                                   tpitch, u);
       }
     }
-    part += __shfl_xor_sync(FULL_MASK, part, 1);
-    part += __shfl_xor_sync(FULL_MASK, part, 2);
-    const int cost_h = __shfl_sync(FULL_MASK, part, rbase), cost_v = __shfl_sync(FULL_MASK, part, rbase | 4);
-    if (on && (t & 7) == 0) {
+#pragma unroll
+    for (int o = 1; o < SPLIT; o <<= 1) part += __shfl_xor_sync(FULL_MASK, part, o);
+    const int cost_h = __shfl_sync(FULL_MASK, part, rbase);
+    const int cost_v = __shfl_sync(FULL_MASK, part, rbase | SPLIT);
+    if (on && (t & (2 * SPLIT - 1)) == 0) {
       uint32_t nf = f0;
       int32_t nc = c0;
       if (useh && cost_h < nc) {
@@ -783,13 +788,16 @@ static ff_status side_stream(SideStream **out) {
 }
 
 // Opt in to more than 48 KB of dynamic shared memory when a tile needs it.
-static ff_status set_pass_smem(int r, size_t bytes, bool wide) {
-  static size_t done[2][9] = {{0}};
-  if (r < 1 || r > 8) return FF_ERR_INVALID_ARG;
+static ff_status set_pass_smem(int r, size_t bytes, int wide) {
+  static size_t done[3][9] = {{0}};
+  if (r < 1 || r > 8 || wide < 0 || wide > 2) return FF_ERR_INVALID_ARG;
   if (bytes <= done[wide][r]) return FF_OK;
   cudaError_t e = cudaSuccess;
-  if (wide) {
-    FF_DISPATCH_R(r, e = cudaFuncSetAttribute(k_pass_wide<RR>,
+  if (wide == 1) {
+    FF_DISPATCH_R(r, e = cudaFuncSetAttribute(k_pass_wide<RR, 4>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  } else if (wide == 2) {
+    FF_DISPATCH_R(r, e = cudaFuncSetAttribute(k_pass_wide<RR, 8>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   } else {
     FF_DISPATCH_R(r, e = cudaFuncSetAttribute(k_pass<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -824,24 +832,27 @@ static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d
     const int half = tile / 2;
     maxT = max(maxT, ((S.NX + half + tile - 1) / tile) * ((S.NY + half + tile - 1) / tile));
   }
+  int nsm = 0;
+  FF_TRY(sm_count(&nsm));
   if (probs[0].flow_coarse) {
-    dim3 g((maxG * 16 + 255) / 256, np);
+    const int blocks = (int)min(((long)(maxG + 3) / 4 * 16 + 255) / 256, (long)nsm * 8);
+    dim3 g(max(blocks, 1), np);
     FF_DISPATCH_R(r, k_seed<RR><<<g, 256, 0, st>>>(d));
     FF_CHECK_LAUNCH();
   }
   const TileLayout lay(tile, r);
   const int wide_min_n = exec_params().wide_min_n;
   const bool wide = wide_min_n > 0 && probs[0].src.n >= wide_min_n && tile <= 16;
+  const int s8 = exec_params().split8_min_n;
+  const int split = (s8 > 0 && probs[0].src.n >= s8) ? 8 : 4;
   int pw = exec_params().pass_warps;
   while (pw > 1 && sizeof(uint32_t) * (size_t)lay.words() * pw > 227u * 1024u) pw--;
   // a level with few tiles spreads them over the SMs (one CTA per SM at least)
-  int nsm = 0;
-  FF_TRY(sm_count(&nsm));
   const long tiles = (long)maxT * np;
   while (pw > 1 && (tiles + pw - 1) / pw < nsm) pw--;
   if (wide) pw = 1;
   const size_t smem = sizeof(uint32_t) * (size_t)lay.words() * pw;
-  FF_TRY(set_pass_smem(r, smem, wide));
+  FF_TRY(set_pass_smem(r, smem, wide ? (split == 8 ? 2 : 1) : 0));
   const int rs_min_n = exec_params().rs_min_n;
   const bool rs_kernel = rs_min_n > 0 && probs[0].src.n >= rs_min_n;
   for (int s = 0; s < 4; s++) {
@@ -849,8 +860,10 @@ static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d
     PassCfg cfg{s, tile, (do_rs && !rs_kernel) ? 1 : 0, R, seed, s == 3, lay.words()};
     dim3 g((maxT + pw - 1) / pw, np);
     if (prof_enabled()) prof_begin(st);
-    if (wide) {
-      FF_DISPATCH_R(r, k_pass_wide<RR><<<g, WIDE_THREADS, smem, st>>>(d, cfg));
+    if (wide && split == 8) {
+      FF_DISPATCH_R(r, (k_pass_wide<RR, 8><<<g, 256, smem, st>>>(d, cfg)));
+    } else if (wide) {
+      FF_DISPATCH_R(r, (k_pass_wide<RR, 4><<<g, 128, smem, st>>>(d, cfg)));
     } else {
       FF_DISPATCH_R(r, k_pass<RR><<<g, pw * 32, smem, st>>>(d, cfg));
     }

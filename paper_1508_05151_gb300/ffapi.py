@@ -39,7 +39,7 @@ class Pair(C.Structure):
 class ExecParams(C.Structure):
     """ff_exec_params: launch shapes that never change results."""
     _fields_ = [("pass_warps", C.c_int32), ("rs_min_n", C.c_int32), ("wide_min_n", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("split8_min_n", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class NetDesc(C.Structure):
@@ -362,19 +362,24 @@ def profile_read():
     return dict(launches=n.value, prop_ms=ms.value, prop_launches=pn.value)
 
 
-def set_exec_params(pass_warps=None, rs_min_n=None, wide_min_n=None):
-    """Set execution parameters; arguments left as None keep their current value."""
+EXEC_FIELDS = ("pass_warps", "rs_min_n", "wide_min_n", "split8_min_n")
+
+
+def set_exec_params(**kw):
+    """Set execution parameters (names of EXEC_FIELDS); the others keep their value."""
+    unknown = set(kw) - set(EXEC_FIELDS)
+    if unknown:
+        raise TypeError(f"unknown execution parameters {sorted(unknown)}")
     cur = get_exec_params()
-    e = ExecParams(pass_warps=cur["pass_warps"] if pass_warps is None else pass_warps,
-                   rs_min_n=cur["rs_min_n"] if rs_min_n is None else rs_min_n,
-                   wide_min_n=cur["wide_min_n"] if wide_min_n is None else wide_min_n)
+    cur.update({k: v for k, v in kw.items() if v is not None})
+    e = ExecParams(**cur)
     _check("ff_set_exec_params", lib().ff_set_exec_params(C.byref(e)))
 
 
 def get_exec_params():
     e = ExecParams()
     _check("ff_get_exec_params", lib().ff_get_exec_params(C.byref(e)))
-    return dict(pass_warps=e.pass_warps, rs_min_n=e.rs_min_n, wide_min_n=e.wide_min_n)
+    return {k: getattr(e, k) for k in EXEC_FIELDS}
 
 
 class FlowFieldsBatch:

@@ -4,9 +4,9 @@ It times candidate launch shapes on the caller's workload and keeps the fastest.
 Only parameters that leave every result unchanged are tuned: tiles per CTA of the
 propagation kernel, from which level spacing on the random search runs as a
 kernel of its own, and from which spacing on the propagation runs one CTA per
-tile. The tile edge T of the parallel schedule is part of the method's
-definition and stays as given. The search is coordinate-wise, one parameter at a
-time in that order. Choices are cached in a small JSON file
+tile (and with how many threads per candidate). The tile edge T of the parallel
+schedule is part of the method's definition and stays as given. The search is
+coordinate-wise, one parameter at a time in the order of CANDIDATES. Choices are cached in a small JSON file
 keyed by GPU name, image sizes and method parameters.
 """
 from __future__ import annotations
@@ -18,7 +18,8 @@ import torch
 
 from . import ffapi, synth
 
-CANDIDATES = dict(pass_warps=(1, 2, 4, 8), rs_min_n=(0, 1, 2, 4, 8), wide_min_n=(0, 1, 2, 4, 8))
+CANDIDATES = dict(wide_min_n=(0, 1, 2, 4, 8), split8_min_n=(0, 1, 2, 4, 8), pass_warps=(1, 2, 4, 8),
+                  rs_min_n=(0, 1, 2, 4, 8))
 _CACHE = os.environ.get("FF_TUNE_CACHE",
                         os.path.join(os.path.expanduser("~"), ".cache", "flowfields_tune.json"))
 
@@ -84,9 +85,9 @@ def tune(sizes, params=None, frames=None, reps=3, use_cache=True, seed=0):
     batch = ffapi.FlowFieldsBatch(sizes, params)
     before = ffapi.get_exec_params()
     timings = {}
-    choice = dict(pass_warps=4, rs_min_n=0, wide_min_n=0)
+    choice = dict(pass_warps=4, rs_min_n=0, wide_min_n=1, split8_min_n=0)
     best_t = None
-    for name in ("pass_warps", "rs_min_n", "wide_min_n"):  # one parameter at a time
+    for name in CANDIDATES:  # one parameter at a time
         for v in CANDIDATES[name]:
             trial = dict(choice, **{name: v})
             tk = ",".join(f"{k}={trial[k]}" for k in sorted(trial))

@@ -66,8 +66,9 @@ def test_execution_parameters_do_not_change_results():
     try:
         # tiles per CTA, and the random search inside the pass kernel or as its
         # own kernel from some level on
-        for pw, rs, wide in ((1, 0, 0), (2, 1, 0), (8, 2, 0), (4, 8, 1), (4, 64, 2), (8, 0, 4)):
-            ffapi.set_exec_params(pass_warps=pw, rs_min_n=rs, wide_min_n=wide)
+        for pw, rs, wide, s8 in ((1, 0, 0, 0), (2, 1, 0, 0), (8, 2, 0, 0), (4, 8, 1, 0),
+                                 (4, 64, 2, 2), (8, 0, 4, 0), (4, 0, 1, 1), (4, 0, 1, 4)):
+            ffapi.set_exec_params(pass_warps=pw, rs_min_n=rs, wide_min_n=wide, split8_min_n=s8)
             got = batch.run(frames)
             for a, b in zip(ref, got):
                 _same(a, b)
@@ -84,6 +85,7 @@ def test_autotuner_picks_a_candidate(tmp_path, monkeypatch):
         assert r["choice"]["pass_warps"] in tune.CANDIDATES["pass_warps"]
         assert r["choice"]["rs_min_n"] in tune.CANDIDATES["rs_min_n"]
         assert r["choice"]["wide_min_n"] in tune.CANDIDATES["wide_min_n"]
+        assert r["choice"]["split8_min_n"] in tune.CANDIDATES["split8_min_n"]
         assert ffapi.get_exec_params() == r["choice"]
         r2 = tune.tune([(128, 96), (97, 71)], reps=1)
         assert r2["cached"] and r2["choice"] == r["choice"]
