@@ -197,14 +197,10 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
     }
   }
 
-  // kd trees of all flows of all pairs
-  std::vector<KdBuild> trees(3 * (size_t)np);
-  for (int i = 0; i < np; i++)
-    for (int j = 0; j < 3; j++) trees[3 * i + j] = plans[i].kd[j];
-  FF_TRY(launch_kd_build(trees.data(), bd.d_kd, 3 * np, st));
-
   // problem order: all flows with radius r (forward, backward r) of every pair,
-  // then the backward r2 flows, so each radius is one contiguous run
+  // then the backward r2 flows. Each radius group builds its trees, queries them
+  // and searches on a stream of its own (the r2 group on the side stream), so the
+  // latency-bound kd build of one group overlaps the other group's work.
   std::vector<int> order_pair, order_flow;
   for (int i = 0; i < np; i++)
     for (int j = 0; j < 2; j++) {
@@ -216,12 +212,21 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
     order_flow.push_back(2);
   }
   const int nprob = (int)order_pair.size();  // 3 * np
+  const bool two_groups = p->r != p->r2;
+  const int gstart[2] = {0, two_groups ? 2 * np : nprob}, gend[2] = {gstart[1], nprob};
+  SideSection sec;
+  if (two_groups) FF_TRY(sec.begin(st));
 
+  std::vector<KdBuild> trees(nprob);
   std::vector<KdQuery> q(nprob);
+  std::vector<uint32_t *> cur(nprob), oth(nprob);
+  std::vector<int32_t *> ccur(nprob), coth(nprob);
+  std::vector<SearchProblem> sp(nprob);
   for (int t = 0; t < nprob; t++) {
     const int i = order_pair[t], j = order_flow[t];
     const PairPlan &P = plans[i];
     const int W = io[i].W, H = io[i].H;
+    trees[t] = P.kd[j];
     KdQuery &Q = q[t];
     Q = KdQuery{};
     Q.perm = P.perm[j];
@@ -238,64 +243,64 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
     Q.K = (j == 0) ? p->K : 0;
     Q.flow = P.fa[j];
     Q.cost = P.ca[j];
-  }
-  for (int t0 = 0; t0 < nprob;) {  // one launch per run of equal radius
-    int t1 = t0;
-    while (t1 < nprob && q[t1].r == q[t0].r) t1++;
-    FF_TRY(launch_kd_query(q.data() + t0, bd.d_q + t0, t1 - t0, st));
-    t0 = t1;
-  }
-
-  // levels n = 2^k .. 1; the state alternates between the two buffers per level
-  std::vector<uint32_t *> cur(nprob), oth(nprob);
-  std::vector<int32_t *> ccur(nprob), coth(nprob);
-  for (int t = 0; t < nprob; t++) {
-    const PairPlan &P = plans[order_pair[t]];
-    const int j = order_flow[t];
     cur[t] = P.fa[j];
     oth[t] = P.fb[j];
     ccur[t] = P.ca[j];
     coth[t] = P.cb[j];
   }
-  std::vector<SearchProblem> sp(nprob);
-  for (int lv = k; lv >= 0; lv--) {
-    const int n = 1 << lv;
-    for (int t = 0; t < nprob; t++) {
-      const int i = order_pair[t], j = order_flow[t];
-      const PairPlan &P = plans[i];
-      const int W = io[i].W, H = io[i].H;
-      SearchProblem &s = sp[t];
-      s = SearchProblem{};
-      s.src = make_planes(P.planes[srcf[j]][lv], W, H, n);
-      s.tgt = make_planes(P.planes[tgtf[j]][lv], W, H, n);
-      s.r = rad[j];
-      s.flow_id = j;
-      if (lv == k) {
-        s.flow_coarse = nullptr;
-        s.flow_a = cur[t];
-        s.cost_a = ccur[t];
-        s.flow_b = oth[t];
-        s.cost_b = coth[t];
-      } else {  // seed from the coarser state (in cur) into the other buffer
-        s.flow_coarse = cur[t];
-        s.flow_a = oth[t];
-        s.cost_a = coth[t];
-        s.flow_b = cur[t];
-        s.cost_b = ccur[t];
-      }
-      if (lv == 0) {
-        s.flow_final = (uint32_t *)(io[i].flows + 2 * (size_t)W * H * j);
-        s.cost_final = s.cost_a;
-      }
+  for (int g = 0; g < 2; g++) {
+    const int t0 = gstart[g], cnt = gend[g] - gstart[g];
+    if (cnt <= 0) continue;
+    cudaStream_t gs = g == 0 ? st : sec.side;
+    FF_TRY(launch_kd_build(trees.data() + t0, bd.d_kd + t0, cnt, gs));
+    // kd query: one launch per run of equal radius
+    for (int a0 = t0; a0 < t0 + cnt;) {
+      int a1 = a0;
+      while (a1 < t0 + cnt && q[a1].r == q[a0].r) a1++;
+      FF_TRY(launch_kd_query(q.data() + a0, bd.d_q + a0, a1 - a0, gs));
+      a0 = a1;
     }
-    FF_TRY(run_level(sp.data(), bd.d_sp + (size_t)nprob * lv, nprob, p->tile, p->n_rs, p->R,
-                     p->seed, st));
-    if (lv != k)
-      for (int t = 0; t < nprob; t++) {
-        std::swap(cur[t], oth[t]);
-        std::swap(ccur[t], coth[t]);
+    // levels n = 2^k .. 1; the state alternates between the two buffers per level
+    for (int lv = k; lv >= 0; lv--) {
+      const int n = 1 << lv;
+      for (int t = t0; t < t0 + cnt; t++) {
+        const int i = order_pair[t], j = order_flow[t];
+        const PairPlan &P = plans[i];
+        const int W = io[i].W, H = io[i].H;
+        SearchProblem &s = sp[t];
+        s = SearchProblem{};
+        s.src = make_planes(P.planes[srcf[j]][lv], W, H, n);
+        s.tgt = make_planes(P.planes[tgtf[j]][lv], W, H, n);
+        s.r = rad[j];
+        s.flow_id = j;
+        if (lv == k) {
+          s.flow_coarse = nullptr;
+          s.flow_a = cur[t];
+          s.cost_a = ccur[t];
+          s.flow_b = oth[t];
+          s.cost_b = coth[t];
+        } else {  // seed from the coarser state (in cur) into the other buffer
+          s.flow_coarse = cur[t];
+          s.flow_a = oth[t];
+          s.cost_a = coth[t];
+          s.flow_b = cur[t];
+          s.cost_b = ccur[t];
+        }
+        if (lv == 0) {
+          s.flow_final = (uint32_t *)(io[i].flows + 2 * (size_t)W * H * j);
+          s.cost_final = s.cost_a;
+        }
       }
+      FF_TRY(run_level_on(sp.data() + t0, bd.d_sp + (size_t)nprob * lv + t0, cnt, p->tile,
+                          p->n_rs, p->R, p->seed, gs));
+      if (lv != k)
+        for (int t = t0; t < t0 + cnt; t++) {
+          std::swap(cur[t], oth[t]);
+          std::swap(ccur[t], coth[t]);
+        }
+    }
   }
+  if (two_groups) FF_TRY(sec.end());
 
   for (int i = 0; i < np; i++) {
     const size_t N = (size_t)io[i].W * io[i].H;

@@ -298,6 +298,23 @@ struct SearchProblem {
 // Seeds (if flow_coarse) and runs the 4 passes with n_rs random searches.
 // After the call the state is in flow_final/cost_final when given, else in
 // flow_a/cost_a.
+// Problems of one patch radius, all on stream st (no side stream).
+ff_status run_level_on(const SearchProblem *probs, SearchProblem *dev_desc, int nprob, int tile,
+                       int n_rs, int R, uint64_t seed, cudaStream_t st);
+// A fork/join section on the per-device side stream: begin() makes the side
+// stream wait for the work enqueued so far on st, end() makes st wait for the
+// side stream. Host threads are serialised between begin() and end(); the
+// destructor ends an open section (error paths).
+struct SideSection {
+  cudaStream_t main = nullptr, side = nullptr;
+  cudaEvent_t join = nullptr;
+  bool locked = false;
+  ff_status begin(cudaStream_t st);
+  ff_status end();
+  ~SideSection() {
+    if (locked) end();
+  }
+};
 ff_status run_level(const SearchProblem *probs, SearchProblem *dev_desc, int nprob, int tile,
                     int n_rs, int R, uint64_t seed, cudaStream_t st);
 

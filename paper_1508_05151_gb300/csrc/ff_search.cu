@@ -878,6 +878,41 @@ static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d
   return FF_OK;
 }
 
+ff_status SideSection::begin(cudaStream_t st) {
+  g_side_enqueue_mu.lock();
+  locked = true;
+  SideStream *S = nullptr;
+  FF_TRY(side_stream(&S));
+  if (cudaEventRecord(S->fork, st) != cudaSuccess || cudaStreamWaitEvent(S->s, S->fork, 0) != cudaSuccess)
+    return FF_ERR_CUDA;
+  main = st;
+  side = S->s;
+  join = S->join;
+  return FF_OK;
+}
+
+ff_status SideSection::end() {
+  ff_status r = FF_OK;
+  if (side && (cudaEventRecord(join, side) != cudaSuccess ||
+               cudaStreamWaitEvent(main, join, 0) != cudaSuccess))
+    r = FF_ERR_CUDA;
+  side = nullptr;
+  if (locked) {
+    locked = false;
+    g_side_enqueue_mu.unlock();
+  }
+  return r;
+}
+
+ff_status run_level_on(const SearchProblem *probs, SearchProblem *dev, int nprob, int tile,
+                       int n_rs, int R, uint64_t seed, cudaStream_t st) {
+  if (nprob <= 0) return FF_OK;
+  for (int i = 1; i < nprob; i++)
+    if (probs[i].r != probs[0].r) return FF_ERR_INVALID_ARG;
+  FF_TRY(upload_desc(probs, dev, nprob, st));
+  return launch_group(probs, dev, nprob, probs[0].r, tile, n_rs, R, seed, st);
+}
+
 ff_status run_level(const SearchProblem *probs, SearchProblem *dev, int nprob, int tile, int n_rs,
                     int R, uint64_t seed, cudaStream_t st) {
   if (nprob <= 0) return FF_OK;
