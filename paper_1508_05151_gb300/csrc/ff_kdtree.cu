@@ -232,7 +232,25 @@ __device__ __forceinline__ unsigned long long kd_key(const KdBuild &T, const int
   return ((unsigned long long)(unsigned)(v - S[1]) << S[3]) | (unsigned)idx;
 }
 
-constexpr int HIST_CHUNK = 4096;
+constexpr int HIST_CHUNK = 2048;  // positions per CTA (segments > SUB_MAX: spans <= 3)
+constexpr int CHUNK_SEGS = 4;     // segment slots per chunk
+
+// The segments a chunk of positions touches (top levels: at most CHUNK_SEGS):
+// first segment and the begin offsets of the following ones, in shared memory.
+__device__ __forceinline__ void chunk_segments(const int32_t *off, int nseg, int start, int *sseg0,
+                                               int *sbound) {
+  if (threadIdx.x == 0) {
+    const int s0 = find_seg(off, nseg, start);
+    *sseg0 = s0;
+    for (int i = 0; i < CHUNK_SEGS - 1; i++) sbound[i] = s0 + 1 + i <= nseg ? off[s0 + 1 + i] : INT32_MAX;
+  }
+}
+__device__ __forceinline__ int seg_of(int p, int seg0, const int *sbound) {
+  int s = seg0;
+#pragma unroll
+  for (int i = 0; i < CHUNK_SEGS - 1; i++) s += p >= sbound[i];
+  return s;
+}
 
 __global__ void __launch_bounds__(256) k_kd_hist(KdBuild *trees, int d) {
   KdBuild &T = trees[blockIdx.y];
@@ -243,16 +261,14 @@ __global__ void __launch_bounds__(256) k_kd_hist(KdBuild *trees, int d) {
   int nseg = 1 << d;
   const int32_t *off = T.seg_off + seg_base(d);
   __shared__ uint32_t sh[NBINS];
-  __shared__ int sseg0, sseg1;
-  if (threadIdx.x == 0) {
-    sseg0 = find_seg(off, nseg, start);
-    sseg1 = find_seg(off, nseg, end - 1);
-  }
+  __shared__ int sseg0, sbound[CHUNK_SEGS - 1];
+  chunk_segments(off, nseg, start, &sseg0, sbound);
   for (int i = threadIdx.x; i < NBINS; i += blockDim.x) sh[i] = 0;
   __syncthreads();
-  bool single = sseg0 == sseg1;
+  const int seg0 = sseg0;
+  const bool single = sbound[0] >= end;
   for (int p = start + threadIdx.x; p < end; p += blockDim.x) {
-    int s = single ? sseg0 : find_seg(off, nseg, p);
+    int s = single ? seg0 : seg_of(p, seg0, sbound);
     const int32_t *S = T.sel + s * 8;
     int B = S[2], used = S[7];
     if (used >= B) continue;
@@ -275,7 +291,7 @@ __global__ void __launch_bounds__(256) k_kd_hist(KdBuild *trees, int d) {
   __syncthreads();
   if (single)
     for (int i = threadIdx.x; i < NBINS; i += blockDim.x)
-      if (sh[i]) atomicAdd(&T.hist[(size_t)sseg0 * NBINS + i], sh[i]);
+      if (sh[i]) atomicAdd(&T.hist[(size_t)seg0 * NBINS + i], sh[i]);
 }
 
 // One CTA per segment: find the bin holding rank k, narrow the prefix, clear.
@@ -327,7 +343,7 @@ __global__ void __launch_bounds__(256) k_kd_digit(KdBuild *trees, int d) {
 // destination child (order inside a child is unspecified). The selected point
 // writes the split value. While the rows pass through, the per-dimension
 // min/max of the children (next level) is accumulated the same way.
-constexpr int PART_CHUNK = 2048;  // positions per CTA (spans <= 3 segments)
+constexpr int PART_CHUNK = 2048;  // positions per CTA (spans <= 3 segments at top levels)
 constexpr int PART_ROUNDS = PART_CHUNK / 256;
 
 __global__ void __launch_bounds__(256) k_kd_partition(KdBuild *trees, int d) {
@@ -341,11 +357,11 @@ __global__ void __launch_bounds__(256) k_kd_partition(KdBuild *trees, int d) {
   const int32_t *src = cur_perm(T, d);
   int32_t *dstp = cur_perm(T, d + 1);
   const bool child_mm = d + 1 < T.top_levels;
-  __shared__ int s_seg0;
+  __shared__ int s_seg0, s_bound[CHUNK_SEGS - 1];
   __shared__ int s_cnt[8], s_base[8];
   __shared__ int s_min[8][NFEAT], s_max[8][NFEAT];
   const int tid = threadIdx.x, lane = tid & 31;
-  if (tid == 0) s_seg0 = find_seg(off, nseg, start);
+  chunk_segments(off, nseg, start, &s_seg0, s_bound);
   if (tid < 8) s_cnt[tid] = 0;
   for (int i = tid; i < 8 * NFEAT; i += 256) {
     s_min[i / NFEAT][i % NFEAT] = INT32_MAX;
@@ -359,13 +375,13 @@ __global__ void __launch_bounds__(256) k_kd_partition(KdBuild *trees, int d) {
     const int p = start + r * 256 + tid;
     int c = -1, idx = 0;
     if (p < end) {
-      const int sg = find_seg(off, nseg, p);
+      const int sg = seg_of(p, seg0, s_bound);
       const int32_t *S = T.sel + sg * 8;
       idx = src[p];
-      const unsigned long long K = kd_key(T, S, idx);
+      const unsigned long long K = T.keys[p];  // cached by the level's first histogram pass
       const unsigned long long sel = ((unsigned long long)(unsigned)S[6] << 32) | (unsigned)S[5];
       c = 2 * (sg - seg0) + (K < sel ? 0 : 1);
-      if (K == sel) T.split_val[(1 << d) - 1 + sg] = T.feat[(size_t)idx * FEAT_STRIDE + S[0]];
+      if (K == sel) T.split_val[(1 << d) - 1 + sg] = (int)(K >> S[3]) + S[1];
     }
     const unsigned grp = __match_any_sync(0xffffffffu, c);
     const int leader = __ffs(grp) - 1;
