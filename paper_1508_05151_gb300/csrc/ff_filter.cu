@@ -9,7 +9,7 @@
 //                a consistency-rejected neighbour within 3 px are removed.
 //   sparsify     one pixel per aligned 3x3 block with >= e survivors (smallest
 //                e_1 + e_2, raster-first on ties), compacted in block raster order
-//                by one CTA (ordered scan, so the list is deterministic).
+//                (per-CTA counts, their scan, then ranked writes: deterministic).
 #include "ff_internal.cuh"
 
 namespace ff {
@@ -109,9 +109,12 @@ __global__ void k_region_stats(const uint32_t *__restrict__ F, const uint8_t *__
                                int H, const int32_t *__restrict__ parent, int32_t *size,
                                uint8_t *touch) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= W * H || !vcc[p]) return;
-  const int root = parent[p];
-  atomicAdd(&size[root], 1);
+  const bool act = p < W * H && vcc[p];
+  const int root = act ? parent[p] : -1;
+  // neighbouring pixels mostly share a region: one atomic per root and warp
+  const unsigned grp = __match_any_sync(0xffffffffu, root);
+  if (act && (__ffs(grp) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&size[root], __popc(grp));
+  if (!act) return;
   const int x = p % W, y = p / W;
   const uint32_t f = F[p];
   bool t = false;
@@ -138,34 +141,61 @@ __global__ void k_region_apply(const uint8_t *__restrict__ vcc, int N, int s,
 }
 
 // Per 3x3 block: survivor count and the smallest-err pixel (raster-first).
-__global__ void k_blocks(const uint8_t *__restrict__ valid, const int32_t *__restrict__ err, int W, int H,
-                         int e, int32_t *__restrict__ pick) {
-  const int BX = (W + 2) / 3, BY = (H + 2) / 3;
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= BX * BY) return;
-  const int bx = b % BX, by = b / BX;
-  int cnt = 0, best = -1;
-  for (int y = 3 * by; y < min(3 * by + 3, H); y++)
-    for (int x = 3 * bx; x < min(3 * bx + 3, W); x++) {
-      const int p = y * W + x;
-      if (!valid[p]) continue;
-      cnt++;
-      if (best < 0 || err[p] < err[best]) best = p;
-    }
-  pick[b] = (cnt >= e) ? best : -1;
+// Sec. 3.5 sparsification, in three parallel steps that keep the output in block
+// raster order: k_blocks picks each aligned 3x3 block's survivor (>= e valid
+// points, smallest err_sum, raster-first on ties) and counts the picks of its
+// CTA; k_pick_scan turns the per-CTA counts into offsets; k_pick_write writes
+// every pick at its CTA's offset plus its rank inside the CTA.
+constexpr int PICK_CTA = 256;
+
+__device__ __forceinline__ int cta_exclusive_rank(bool flag, int *s_warp, int &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned b = __ballot_sync(0xffffffffu, flag);
+  if (lane == 0) s_warp[warp] = __popc(b);
+  __syncthreads();
+  int before = 0;
+  total = 0;
+  for (int w = 0; w < PICK_CTA / 32; w++) {
+    if (w < warp) before += s_warp[w];
+    total += s_warp[w];
+  }
+  return before + __popc(b & ((1u << lane) - 1));
 }
 
-// One CTA: ordered compaction of the picks into (x, y, dx, dy) rows.
-__global__ void __launch_bounds__(1024) k_compact(const int32_t *__restrict__ pick, int nb, int W,
-                                                  const uint32_t *__restrict__ F,
-                                                  int32_t *__restrict__ sparse,
-                                                  int32_t *__restrict__ n_sparse,
-                                                  uint8_t *__restrict__ mask) {
+__global__ void __launch_bounds__(PICK_CTA) k_blocks(const uint8_t *__restrict__ valid,
+                                                     const int32_t *__restrict__ err, int W, int H,
+                                                     int e, int32_t *__restrict__ pick,
+                                                     int32_t *__restrict__ cta_count) {
+  __shared__ int s_warp[PICK_CTA / 32];
+  const int BX = (W + 2) / 3, BY = (H + 2) / 3;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  int sel = -1;
+  if (b < BX * BY) {
+    const int bx = b % BX, by = b / BX;
+    int cnt = 0, best = -1;
+    for (int y = 3 * by; y < min(3 * by + 3, H); y++)
+      for (int x = 3 * bx; x < min(3 * bx + 3, W); x++) {
+        const int p = y * W + x;
+        if (!valid[p]) continue;
+        cnt++;
+        if (best < 0 || err[p] < err[best]) best = p;
+      }
+    sel = (cnt >= e) ? best : -1;
+    pick[b] = sel;
+  }
+  int total;
+  cta_exclusive_rank(sel >= 0, s_warp, total);
+  if (threadIdx.x == 0) cta_count[blockIdx.x] = total;
+}
+
+// One CTA: exclusive scan of the per-CTA pick counts (in place) and the total.
+__global__ void __launch_bounds__(1024) k_pick_scan(int32_t *__restrict__ cta_count, int n,
+                                                    int32_t *__restrict__ n_sparse) {
   __shared__ int part[1024];
-  const int t = threadIdx.x, per = (nb + 1023) / 1024;
-  const int b0 = min(t * per, nb), b1 = min(b0 + per, nb);
+  const int t = threadIdx.x, per = (n + 1023) / 1024;
+  const int b0 = min(t * per, n), b1 = min(b0 + per, n);
   int cnt = 0;
-  for (int b = b0; b < b1; b++) cnt += pick[b] >= 0;
+  for (int b = b0; b < b1; b++) cnt += cta_count[b];
   part[t] = cnt;
   __syncthreads();
   for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan
@@ -174,19 +204,33 @@ __global__ void __launch_bounds__(1024) k_compact(const int32_t *__restrict__ pi
     part[t] += v;
     __syncthreads();
   }
-  int out = part[t] - cnt;
+  int run = part[t] - cnt;
   for (int b = b0; b < b1; b++) {
-    const int p = pick[b];
-    if (p < 0) continue;
-    const uint32_t f = F[p];
-    sparse[4 * out] = p % W;
-    sparse[4 * out + 1] = p / W;
-    sparse[4 * out + 2] = flow_dx(f);
-    sparse[4 * out + 3] = flow_dy(f);
-    mask[p] = 1;
-    out++;
+    const int c = cta_count[b];
+    cta_count[b] = run;
+    run += c;
   }
   if (t == 1023) *n_sparse = part[1023];
+}
+
+__global__ void __launch_bounds__(PICK_CTA) k_pick_write(const int32_t *__restrict__ pick, int nb,
+                                                         int W, const uint32_t *__restrict__ F,
+                                                         const int32_t *__restrict__ cta_offset,
+                                                         int32_t *__restrict__ sparse,
+                                                         uint8_t *__restrict__ mask) {
+  __shared__ int s_warp[PICK_CTA / 32];
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = b < nb ? pick[b] : -1;
+  int total;
+  const int r = cta_exclusive_rank(p >= 0, s_warp, total);
+  if (p < 0) return;
+  const int out = cta_offset[blockIdx.x] + r;
+  const uint32_t f = F[p];
+  sparse[4 * out] = p % W;
+  sparse[4 * out + 1] = p / W;
+  sparse[4 * out + 2] = flow_dx(f);
+  sparse[4 * out + 3] = flow_dy(f);
+  mask[p] = 1;
 }
 
 size_t filter_scratch_bytes(int W, int H) {
@@ -197,6 +241,7 @@ size_t filter_scratch_bytes(int W, int H) {
   a.take<int32_t>(N);
   a.take<uint8_t>(N);
   a.take<int32_t>(NB);
+  a.take<int32_t>((NB + PICK_CTA - 1) / PICK_CTA);
   return a.off;
 }
 
@@ -210,6 +255,8 @@ ff_status launch_filter(const uint32_t *F, const uint32_t *Fb1, const uint32_t *
   int32_t *size = a.take<int32_t>(N);
   uint8_t *touch = a.take<uint8_t>(N);
   int32_t *pick = a.take<int32_t>(NB);
+  const int ncta = (NB + PICK_CTA - 1) / PICK_CTA;
+  int32_t *cta_count = a.take<int32_t>(ncta);
   const int B = 256, g = (N + B - 1) / B;
   if (cudaMemsetAsync(touch, 0, N, st) != cudaSuccess) return FF_ERR_CUDA;
   k_consistency<<<g, B, 0, st>>>(F, Fb1, Fb2, W, H, eps, vcc, err_sum, parent);
@@ -222,9 +269,11 @@ ff_status launch_filter(const uint32_t *F, const uint32_t *Fb1, const uint32_t *
   FF_CHECK_LAUNCH();
   k_region_apply<<<g, B, 0, st>>>(vcc, N, s, parent, size, touch, valid, mask);
   FF_CHECK_LAUNCH();
-  k_blocks<<<(NB + B - 1) / B, B, 0, st>>>(valid, err_sum, W, H, e, pick);
+  k_blocks<<<ncta, PICK_CTA, 0, st>>>(valid, err_sum, W, H, e, pick, cta_count);
   FF_CHECK_LAUNCH();
-  k_compact<<<1, 1024, 0, st>>>(pick, NB, W, F, sparse, n_sparse, mask);
+  k_pick_scan<<<1, 1024, 0, st>>>(cta_count, ncta, n_sparse);
+  FF_CHECK_LAUNCH();
+  k_pick_write<<<ncta, PICK_CTA, 0, st>>>(pick, NB, W, F, cta_count, sparse, mask);
   FF_CHECK_LAUNCH();
   return FF_OK;
 }

@@ -10,7 +10,8 @@
 //
 // Build, level by level:
 //   top levels (segments > SUB_MAX points): multi-CTA passes per level
-//     minmax   per-segment per-dim min/max (lanes = dims, coalesced 108-B rows)
+//     minmax   per-dim min/max of the root (rows in memory order); deeper
+//              levels get their children's min/max from the partition
 //     sel_init dimension choice, key width
 //     4 x (hist, digit)  radix select of the rank-floor(m/2) key, 11-bit digits,
 //                        key = (value - min) << ibits | pixel index (unique);
@@ -120,56 +121,40 @@ __device__ __forceinline__ int find_seg(const int32_t *off, int nseg, int pos) {
   return lo;
 }
 
-constexpr int MM_CHUNK = 2048;  // positions per CTA in k_kd_minmax (spans <= 3 segments)
+// Per-dimension min/max of the root (all N feature rows): the rows are read in
+// memory order, each warp walks a strided set of rows with lanes = dimensions
+// and four rows in flight, then warp results merge in shared memory and once per
+// CTA in global memory.
+constexpr int MM_ROWS_PER_WARP = 64;
 
-__global__ void __launch_bounds__(256) k_kd_minmax(KdBuild *trees, int d) {
+__global__ void __launch_bounds__(256) k_kd_minmax_root(KdBuild *trees) {
   KdBuild &T = trees[blockIdx.y];
-  if (d >= T.top_levels) return;
-  int start = blockIdx.x * MM_CHUNK;
-  if (start >= T.N) return;
-  int nseg = 1 << d;
-  const int32_t *off = T.seg_off + seg_base(d);
-  __shared__ int smin[4][NFEAT], smax[4][NFEAT];
-  __shared__ int seg0;
-  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) seg0 = find_seg(off, nseg, start);
-  for (int t = tid; t < 4 * NFEAT; t += blockDim.x) {
-    smin[t / NFEAT][t % NFEAT] = INT32_MAX;
-    smax[t / NFEAT][t % NFEAT] = INT32_MIN;
+  if (T.top_levels <= 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r0 = (blockIdx.x * 8 + warp) * MM_ROWS_PER_WARP;
+  __shared__ int smin[NFEAT], smax[NFEAT];
+  if (tid < NFEAT) {
+    smin[tid] = INT32_MAX;
+    smax[tid] = INT32_MIN;
   }
   __syncthreads();
-  int p0 = start + warp * (MM_CHUNK / 8), p1 = min(p0 + MM_CHUNK / 8, T.N);
-  if (p0 < p1) {
-    int seg = find_seg(off, nseg, p0), next = off[seg + 1];
+  if (r0 < T.N && lane < NFEAT) {
+    const int r1 = min(r0 + MM_ROWS_PER_WARP, T.N);
     int lo = INT32_MAX, hi = INT32_MIN;
-    for (int p = p0; p < p1; p++) {
-      if (p >= next) {
-        if (lane < NFEAT) {
-          atomicMin(&smin[seg - seg0][lane], lo);
-          atomicMax(&smax[seg - seg0][lane], hi);
-        }
-        lo = INT32_MAX;
-        hi = INT32_MIN;
-        while (p >= next) next = off[++seg + 1];
-      }
-      if (lane < NFEAT) {
-        int v = T.feat[(size_t)cur_perm(T, d)[p] * FEAT_STRIDE + lane];
-        lo = min(lo, v);
-        hi = max(hi, v);
-      }
+    const int32_t *col = T.feat + lane;
+#pragma unroll 4
+    for (int r = r0; r < r1; r++) {
+      const int v = col[(size_t)r * FEAT_STRIDE];
+      lo = min(lo, v);
+      hi = max(hi, v);
     }
-    if (lane < NFEAT) {
-      atomicMin(&smin[seg - seg0][lane], lo);
-      atomicMax(&smax[seg - seg0][lane], hi);
-    }
+    atomicMin(&smin[lane], lo);
+    atomicMax(&smax[lane], hi);
   }
   __syncthreads();
-  int last = find_seg(off, nseg, min(start + MM_CHUNK, T.N) - 1);
-  for (int t = tid; t < (last - seg0 + 1) * NFEAT; t += blockDim.x) {
-    int s = t / NFEAT, dim = t % NFEAT;
-    if (smin[s][dim] == INT32_MAX) continue;
-    atomicMin(&mm_at(T, d, seg0 + s)[dim * 2], smin[s][dim]);
-    atomicMax(&mm_at(T, d, seg0 + s)[dim * 2 + 1], smax[s][dim]);
+  if (tid < NFEAT && smin[tid] != INT32_MAX) {
+    atomicMin(&mm_at(T, 0, 0)[tid * 2], smin[tid]);
+    atomicMax(&mm_at(T, 0, 0)[tid * 2 + 1], smax[tid]);
   }
 }
 
@@ -631,7 +616,8 @@ ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaSt
     k_kd_level_reset<<<dim3(min((nseg * NBINS + B - 1) / B, 1024), ntrees), B, 0, st>>>(dev, d);
     FF_CHECK_LAUNCH();
     if (d == 0) {
-      k_kd_minmax<<<dim3((maxN + MM_CHUNK - 1) / MM_CHUNK, ntrees), 256, 0, st>>>(dev, d);
+      const int rows_per_cta = 8 * MM_ROWS_PER_WARP;
+      k_kd_minmax_root<<<dim3((maxN + rows_per_cta - 1) / rows_per_cta, ntrees), 256, 0, st>>>(dev);
       FF_CHECK_LAUNCH();
     }
     k_kd_sel_init<<<dim3((nseg + 127) / 128, ntrees), 128, 0, st>>>(dev, d);

@@ -18,8 +18,8 @@ namespace ff {
 
 // Largest image handled: 1,048,576 pixels (e.g. 1024 x 1024, 1280 x 720).
 constexpr long long STATIC_MAX_PIXELS = 1ll << 20;
-// filter_scratch_bytes() is at most 10 B per pixel plus 4 B per 3x3 block (at
-// most N/3 + 2 blocks) plus block alignment: under 12 MiB for 2^20 pixels.
+// filter_scratch_bytes() is at most 10 B per pixel plus 4 B per 3x3 block and 4 B
+// per 256 blocks, plus block alignment: under 12 MiB for 2^20 pixels.
 constexpr size_t STATIC_SCRATCH_BYTES = 12u << 20;
 
 static __device__ __align__(256) unsigned char g_filter_scratch[STATIC_SCRATCH_BYTES];
