@@ -157,6 +157,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ multi-rank ----
+def rank_pair_seeds(rank, count=2, base=1000):
+    """Seeds of the synthetic pairs one rank times: disjoint across ranks (each rank
+    processes its own pairs; nothing is exchanged on the data path)."""
+    return [base + count * rank + i for i in range(count)]
+
+
+def max_over_ranks(x, world, device=None):
+    """Largest per-rank value (a time); one all-reduce outside any timed region."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_ms_per_pair(max_rank_ms, steps, world):
+    """Weak scaling: every rank times `steps` pairs; the job processed steps x world
+    pairs in the slowest rank's time."""
+    return max_rank_ms / (steps * world)
+
+
 def _time_steps(run, steps, flush, stream):
     """Per-step CUDA-event times (ms) with an L2 flush before every step."""
     import torch
@@ -241,13 +264,10 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x):
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def rank_max(x):
+        return max_over_ranks(x, world, dev)
 
-    pairs = [synth.pair_for_config(2, 1000 + 2 * rank + i) for i in range(2)]
+    pairs = [synth.pair_for_config(2, sd) for sd in rank_pair_seeds(rank)]
     dI = [(torch.from_numpy(p["I1"]).to(dev), torch.from_numpy(p["I2"]).to(dev)) for p in pairs]
     flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
@@ -275,10 +295,10 @@ def run_ours(args):
         wall = time.perf_counter() - t0
     barrier()
     launches = ffapi.profile_read()["launches"]
-    total_ms = max_over_ranks(sum(step_ms))
+    total_ms = rank_max(sum(step_ms))
     ms_per_step = total_ms / args.steps
     pairs_total = args.steps * world
-    value = total_ms / pairs_total  # whole-job ms per pair
+    value = whole_job_ms_per_pair(total_ms, args.steps, world)
 
     # ---- timed region B: direct call, propagation launches timed by events ----
     ffapi.profile_enable(True)
@@ -288,7 +308,7 @@ def run_ours(args):
     direct_ms = _time_steps(lambda i: direct.run(*dI[i % 2]), args.steps, flush, stream)
     prof = ffapi.profile_read()
     ffapi.profile_enable(False)
-    direct_value = max_over_ranks(sum(direct_ms)) / pairs_total
+    direct_value = whole_job_ms_per_pair(rank_max(sum(direct_ms)), args.steps, world)
 
     # ---- end to end through the public graph API with host buffers ----
     hI = [(torch.from_numpy(p["I1"]).pin_memory(), torch.from_numpy(p["I2"]).pin_memory())
@@ -313,7 +333,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     e2e_ms = _time_steps(e2e_step, args.steps, flush, stream)
-    e2e_value = max_over_ranks(sum(e2e_ms)) / pairs_total
+    e2e_value = whole_job_ms_per_pair(rank_max(sum(e2e_ms)), args.steps, world)
     assert int(h_ns.item()) > 0
 
     batch = batch_measure(dev, PARAMS) if (rank == 0 and not args.no_batch) else None

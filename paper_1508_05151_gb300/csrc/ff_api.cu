@@ -113,6 +113,14 @@ static void plan_pair_body(Arena &a, int W, int H, const ff_params *p, PairPlan 
     b = KdBuild{};
     b.N = (int)N;
     b.leaf = p->leaf;
+    // WHT features of radius r: every dimension spans at most (2r+1)^2 * 255
+    {
+      const int rj = j == 2 ? p->r2 : p->r;
+      const long long span = (long long)(2 * rj + 1) * (2 * rj + 1) * 255;
+      int vb = 0;
+      while ((1ll << vb) <= span) vb++;
+      b.value_bits = vb;
+    }
     kd_bind_scratch(b, a);
     b.feat = P.feat[j];
     b.perm = P.perm[j];

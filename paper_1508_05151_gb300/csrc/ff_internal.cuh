@@ -263,6 +263,7 @@ struct KdBuild {
   int32_t *sel;        // per-segment select state
   int32_t *cnt;        // per-segment partition counters
   unsigned long long *keys;  // [N] select keys of the current level, by position
+  int value_bits;      // bound on the bits of any dimension's spread (0: unknown)
   int top_levels;      // levels built by the multi-block path
   DeviceStatus *status;  // set if a partition count is inconsistent
 };

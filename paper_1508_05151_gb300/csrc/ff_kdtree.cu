@@ -13,7 +13,8 @@
 //     minmax   per-dim min/max of the root (rows in memory order); deeper
 //              levels get their children's min/max from the partition
 //     sel_init dimension choice, key width
-//     4 x (hist, digit)  radix select of the rank-floor(m/2) key, 11-bit digits,
+//     passes x (hist, digit)  radix select of the rank-floor(m/2) key, 12-bit digits
+//                        (as many passes as the widest key needs),
 //                        key = (value - min) << ibits | pixel index (unique);
 //                        the first pass caches every position's key
 //     partition          key < selected key -> left child, else right
@@ -26,9 +27,8 @@
 namespace ff {
 
 constexpr int SUB_MAX = 1024;  // largest segment finished by one CTA
-constexpr int DIGIT = 11;
+constexpr int DIGIT = 12;
 constexpr int NBINS = 1 << DIGIT;
-constexpr int MAX_PASSES = 4;  // 44 key bits: 20 value + 24 index bits
 
 int kd_depth(int N, int leaf) {
   int d = 0;
@@ -605,6 +605,14 @@ ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaSt
     maxSub = max(maxSub, trees[i].D - trees[i].top_levels);
   }
   if (maxN <= 0) return FF_OK;
+  // radix-select passes: enough digits for the widest key (value spread bits +
+  // index bits) of any tree
+  int passes = 1;
+  for (int i = 0; i < ntrees; i++) {
+    const int vb = trees[i].value_bits > 0 ? trees[i].value_bits : 33;
+    const int ib = max(bits_for(trees[i].N - 1), 1);
+    passes = max(passes, (vb + ib + DIGIT - 1) / DIGIT);
+  }
   const int B = 256;
   const int gN = min((maxN + B - 1) / B, 4096);
   k_kd_init_perm<<<dim3(gN, ntrees), B, 0, st>>>(dev);
@@ -622,7 +630,7 @@ ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaSt
     }
     k_kd_sel_init<<<dim3((nseg + 127) / 128, ntrees), 128, 0, st>>>(dev, d);
     FF_CHECK_LAUNCH();
-    for (int pass = 0; pass < MAX_PASSES; pass++) {
+    for (int pass = 0; pass < passes; pass++) {
       k_kd_hist<<<dim3((maxN + HIST_CHUNK - 1) / HIST_CHUNK, ntrees), 256, 0, st>>>(dev, d);
       FF_CHECK_LAUNCH();
       k_kd_digit<<<dim3(nseg, ntrees), 256, 0, st>>>(dev, d);
