@@ -124,6 +124,29 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# DRAM traffic of the pass kernels per launch, from one ncu capture of this
+# benchmark's pair (dram__bytes_read.sum + dram__bytes_write.sum averaged over the
+# 32 pass launches of one pair; profiles/k_pass_wide_levels_1_and_8_1024x436.md).
+# It is reported only while the kernel sources hash to what was profiled.
+PASS_TRAFFIC = {"bytes_per_launch": None, "sources_sha256": None}
+PASS_SOURCES = ("paper_1508_05151_gb300/csrc/ff_search.cu", "paper_1508_05151_gb300/csrc/ff_internal.cuh")
+
+
+def pass_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in PASS_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def pass_traffic():
+    if PASS_TRAFFIC["bytes_per_launch"] is None:
+        return None
+    return PASS_TRAFFIC["bytes_per_launch"] if pass_sources_sha256() == PASS_TRAFFIC["sources_sha256"] else None
+
+
 def cpu_oracle_pair(pair, params):
     import oracle
     t = time.perf_counter()
@@ -351,7 +374,7 @@ def run_ours(args):
     achieved = bytes_per_launch / (prop_ms_per_launch * 1e-3) / 1e9
     roof = {"kernel": "k_pass (tiled wavefront propagation + random search)",
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": None,
+            "frac": round(achieved / hbm, 4), "traffic": pass_traffic(),
             "peak_kind": f"{kind} HBM copy bandwidth",
             "prop_ms_per_pair": round(prof["prop_ms"] / args.steps, 4),
             "measured_in": "timed region B (direct call), CUDA events around every k_pass launch",

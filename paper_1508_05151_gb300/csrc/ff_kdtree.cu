@@ -449,7 +449,7 @@ __device__ __forceinline__ unsigned long long bitonic_sort_blocks(unsigned long 
 // The segment's points live in shared memory with their 27 features; at
 // sub-level sd node j owns the aligned slot block [j B, j B + B), B = 1024 >> sd,
 // its m_j points first. Per sub-level: per-node min/max of every dimension
-// (segmented warp reductions, then shared atomics across warps), the split
+// (segmented warp reductions, then across the node's warps), the split
 // dimension, a bitonic sort of each block by (value - node min, pixel-index
 // rank, slot), and one move of every point to its child's block: the first
 // floor(m/2) stay, the others go to the second half. The first point of the
@@ -473,6 +473,10 @@ __global__ void __launch_bounds__(SUB_MAX) k_kd_subtree(KdBuild *trees) {
   int32_t *sstart = ssize + 2 * SUB_MAX;                   // 2 x SUB_MAX node starts
   int32_t *smin = sstart + 2 * SUB_MAX;                    // SUB_SD_SMEM_NODES x NFEAT
   int32_t *smax = smin + SUB_SD_SMEM_NODES * NFEAT;
+  int32_t *swmin = smax + SUB_SD_SMEM_NODES * NFEAT;       // per warp x NFEAT
+  int32_t *swmax = swmin + (SUB_MAX / 32) * NFEAT;
+  int32_t *sdim = swmax + (SUB_MAX / 32) * NFEAT;          // SUB_SD_SMEM_NODES
+  int32_t *sdmin = sdim + SUB_SD_SMEM_NODES;
   const int t = threadIdx.x, lane = t & 31;
   // slots in pixel-index order: slot t holds the t-th smallest index, rank t
   {
@@ -496,46 +500,68 @@ __global__ void __launch_bounds__(SUB_MAX) k_kd_subtree(KdBuild *trees) {
   int pp = 0;  // ping-pong half of the node arrays
   for (int sd = 0; sd < levels; sd++) {
     const int B = SUB_MAX >> sd, j = t / B, o = t & (B - 1);
-    if (B > 32)
-      for (int i = t; i < (SUB_MAX / B) * NFEAT; i += SUB_MAX) {
-        smin[i] = INT32_MAX;
-        smax[i] = INT32_MIN;
-      }
     __syncthreads();
     const int m = ssize[pp * SUB_MAX + j], st = sstart[pp * SUB_MAX + j];
     const bool valid = o < m;
-    // per-node min/max of every dimension and the split dimension
-    const unsigned bmask = B >= 32 ? 0xffffffffu : (((1u << B) - 1u) << (lane & ~(B - 1)));
+    // per-node min/max of every dimension and the split dimension (largest
+    // max - min, lowest dimension on ties)
     int dim = 0, dmin = 0;
-    {
+    if (B <= 32) {  // the node is a segment of a warp: reductions in registers
+      const unsigned bmask = B == 32 ? 0xffffffffu : (((1u << B) - 1u) << (lane & ~(B - 1)));
       long long best = -1;
-#pragma unroll 1
+#pragma unroll 9
       for (int k = 0; k < NFEAT; k++) {
         const int v = valid ? sF[t * NFEAT + k] : 0;
         const int lo = __reduce_min_sync(bmask, valid ? v : INT32_MAX);
         const int hi = __reduce_max_sync(bmask, valid ? v : INT32_MIN);
-        if (B > 32) {
-          if (lane == 0) {
-            atomicMin(&smin[j * NFEAT + k], lo);
-            atomicMax(&smax[j * NFEAT + k], hi);
-          }
-        } else if (m > 0 && (long long)hi - lo > best) {
+        if (m > 0 && (long long)hi - lo > best) {
           best = (long long)hi - lo;
           dim = k;
           dmin = lo;
         }
       }
-      if (B > 32) {
-        __syncthreads();
-        for (int k = 0; k < NFEAT; k++) {
-          const long long sp = (long long)smax[j * NFEAT + k] - smin[j * NFEAT + k];
-          if (sp > best) {
-            best = sp;
-            dim = k;
-            dmin = smin[j * NFEAT + k];
-          }
+    } else {  // per-warp results, then one thread per (node, dimension), then per node
+      const int warp = t >> 5;
+#pragma unroll 9
+      for (int k = 0; k < NFEAT; k++) {
+        const int v = valid ? sF[t * NFEAT + k] : 0;
+        const int lo = __reduce_min_sync(0xffffffffu, valid ? v : INT32_MAX);
+        const int hi = __reduce_max_sync(0xffffffffu, valid ? v : INT32_MIN);
+        if (lane == 0) {
+          swmin[warp * NFEAT + k] = lo;
+          swmax[warp * NFEAT + k] = hi;
         }
       }
+      __syncthreads();
+      const int nn = SUB_MAX / B, wpn = B / 32;
+      if (t < nn * NFEAT) {
+        const int node = t / NFEAT, k = t % NFEAT;
+        int lo = INT32_MAX, hi = INT32_MIN;
+        for (int w = node * wpn; w < (node + 1) * wpn; w++) {
+          lo = min(lo, swmin[w * NFEAT + k]);
+          hi = max(hi, swmax[w * NFEAT + k]);
+        }
+        smin[t] = lo;
+        smax[t] = hi;
+      }
+      __syncthreads();
+      if (t < nn) {
+        long long best = -1;
+        int bd = 0, bm = 0;
+        for (int k = 0; k < NFEAT; k++) {
+          const long long sp = (long long)smax[t * NFEAT + k] - smin[t * NFEAT + k];
+          if (sp > best) {
+            best = sp;
+            bd = k;
+            bm = smin[t * NFEAT + k];
+          }
+        }
+        sdim[t] = bd;
+        sdmin[t] = bm;
+      }
+      __syncthreads();
+      dim = sdim[j];
+      dmin = sdmin[j];
     }
     const unsigned long long key =
         valid ? ((unsigned long long)(uint32_t)(sF[t * NFEAT + dim] - dmin) << 20) |
@@ -592,7 +618,8 @@ __global__ void __launch_bounds__(SUB_MAX) k_kd_subtree(KdBuild *trees) {
 
 static size_t subtree_smem() {
   return sizeof(unsigned long long) * 3 * SUB_MAX +
-         sizeof(int32_t) * ((size_t)SUB_MAX * NFEAT + 6 * SUB_MAX + 2 * SUB_SD_SMEM_NODES * NFEAT);
+         sizeof(int32_t) * ((size_t)SUB_MAX * NFEAT + 6 * SUB_MAX + 2 * SUB_SD_SMEM_NODES * NFEAT +
+                            2 * (SUB_MAX / 32) * NFEAT + 2 * SUB_SD_SMEM_NODES);
 }
 
 ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaStream_t st) {
