@@ -128,7 +128,8 @@ def peaks():
 # benchmark's pair (dram__bytes_read.sum + dram__bytes_write.sum averaged over the
 # 32 pass launches of one pair; profiles/k_pass_wide_levels_1_and_8_1024x436.md).
 # It is reported only while the kernel sources hash to what was profiled.
-PASS_TRAFFIC = {"bytes_per_launch": None, "sources_sha256": None}
+PASS_TRAFFIC = {"bytes_per_launch": 6397312,
+                "sources_sha256": "186c62fa169f25ca85b0ac3601890d1d1a42c0befaff0528fc4f2153d6674356"}
 PASS_SOURCES = ("paper_1508_05151_gb300/csrc/ff_search.cu", "paper_1508_05151_gb300/csrc/ff_internal.cuh")
 
 
@@ -372,12 +373,12 @@ def run_ours(args):
     launches_per_pair = prof["prop_launches"] / args.steps
     bytes_per_launch = gather_bytes_prop(W, H, PARAMS) / launches_per_pair
     achieved = bytes_per_launch / (prop_ms_per_launch * 1e-3) / 1e9
-    roof = {"kernel": "k_pass (tiled wavefront propagation + random search)",
+    roof = {"kernel": "pass kernels (k_pass_wide by default: tiled wavefront propagation + random search)",
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": pass_traffic(),
             "peak_kind": f"{kind} HBM copy bandwidth",
             "prop_ms_per_pair": round(prof["prop_ms"] / args.steps, 4),
-            "measured_in": "timed region B (direct call), CUDA events around every k_pass launch",
+            "measured_in": "timed region B (direct call), CUDA events around every pass-kernel launch",
             "note": "achieved = nominal target-tap bytes ((2r+1)^2 x 4 B per candidate) / mean "
                     "launch time; taps are served by shared memory and L1/L2"}
 

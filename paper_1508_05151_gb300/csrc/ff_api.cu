@@ -183,7 +183,7 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
   const int k = p->k, ntop = 1 << k;
   const int srcf[3] = {0, 1, 1}, tgtf[3] = {1, 0, 0}, rad[3] = {p->r, p->r, p->r2};
 
-  // smoothed images, census planes and WHT features of every pair
+  // smoothed images and census planes of every pair (shared by all flows)
   for (int i = 0; i < np; i++) {
     const PairPlan &P = plans[i];
     const int W = io[i].W, H = io[i].H;
@@ -199,31 +199,23 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
         FF_TRY(launch_census(src, W, H, n, P.census, st));
         FF_TRY(launch_planes(P.census, make_planes(P.planes[f][lv], W, H, n), st));
       }
-    for (int j = 0; j < 3; j++) {
-      FF_TRY(launch_features(img[tgtf[j]], W, H, rad[j], nullptr, 0, 1, P.feat[j], st));
-      FF_TRY(launch_features(img[srcf[j]], W, H, rad[j], nullptr, 0, ntop, P.qfeat[j], st));
-    }
   }
 
-  // problem order: all flows with radius r (forward, backward r) of every pair,
-  // then the backward r2 flows. Each radius group builds its trees, queries them
-  // and searches on a stream of its own (the r2 group on the side stream), so the
-  // latency-bound kd build of one group overlaps the other group's work.
+  // problem order: the forward flows of every pair, then the first backward flows,
+  // then the second backward flows. Each of these three groups computes its
+  // features, builds its trees, queries them and searches on a stream of its own
+  // (the caller's and two side streams), so the latency-bound kd builds and
+  // searches of the three flows overlap.
   std::vector<int> order_pair, order_flow;
-  for (int i = 0; i < np; i++)
-    for (int j = 0; j < 2; j++) {
+  for (int j = 0; j < 3; j++)
+    for (int i = 0; i < np; i++) {
       order_pair.push_back(i);
       order_flow.push_back(j);
     }
-  for (int i = 0; i < np; i++) {
-    order_pair.push_back(i);
-    order_flow.push_back(2);
-  }
   const int nprob = (int)order_pair.size();  // 3 * np
-  const bool two_groups = p->r != p->r2;
-  const int gstart[2] = {0, two_groups ? 2 * np : nprob}, gend[2] = {gstart[1], nprob};
+  const int ngroups = 3;
   SideSection sec;
-  if (two_groups) FF_TRY(sec.begin(st));
+  FF_TRY(sec.begin(st, 2));
 
   std::vector<KdBuild> trees(nprob);
   std::vector<KdQuery> q(nprob);
@@ -256,10 +248,17 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
     ccur[t] = P.ca[j];
     coth[t] = P.cb[j];
   }
-  for (int g = 0; g < 2; g++) {
-    const int t0 = gstart[g], cnt = gend[g] - gstart[g];
-    if (cnt <= 0) continue;
-    cudaStream_t gs = g == 0 ? st : sec.side;
+  for (int g = 0; g < ngroups; g++) {
+    const int t0 = g * np, cnt = np;
+    cudaStream_t gs = g == 0 ? st : sec.side[g - 1];
+    // WHT features of the group's target frames (all pixels) and source grid points
+    for (int t = t0; t < t0 + cnt; t++) {
+      const int i = order_pair[t], j = order_flow[t];
+      const uint8_t *img[2] = {io[i].I1, io[i].I2};
+      FF_TRY(launch_features(img[tgtf[j]], io[i].W, io[i].H, rad[j], nullptr, 0, 1, plans[i].feat[j], gs));
+      FF_TRY(launch_features(img[srcf[j]], io[i].W, io[i].H, rad[j], nullptr, 0, ntop,
+                             plans[i].qfeat[j], gs));
+    }
     FF_TRY(launch_kd_build(trees.data() + t0, bd.d_kd + t0, cnt, gs));
     // kd query: one launch per run of equal radius
     for (int a0 = t0; a0 < t0 + cnt;) {
@@ -308,7 +307,7 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
         }
     }
   }
-  if (two_groups) FF_TRY(sec.end());
+  FF_TRY(sec.end());
 
   for (int i = 0; i < np; i++) {
     const size_t N = (size_t)io[i].W * io[i].H;

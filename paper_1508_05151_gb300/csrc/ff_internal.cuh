@@ -302,15 +302,15 @@ struct SearchProblem {
 // Problems of one patch radius, all on stream st (no side stream).
 ff_status run_level_on(const SearchProblem *probs, SearchProblem *dev_desc, int nprob, int tile,
                        int n_rs, int R, uint64_t seed, cudaStream_t st);
-// A fork/join section on the per-device side stream: begin() makes the side
-// stream wait for the work enqueued so far on st, end() makes st wait for the
-// side stream. Host threads are serialised between begin() and end(); the
+// A fork/join section on the per-device side streams: begin() makes nside (1 or
+// 2) side streams wait for the work enqueued so far on st, end() makes st wait
+// for them. Host threads are serialised between begin() and end(); the
 // destructor ends an open section (error paths).
 struct SideSection {
-  cudaStream_t main = nullptr, side = nullptr;
-  cudaEvent_t join = nullptr;
+  cudaStream_t main = nullptr, side[2] = {nullptr, nullptr};
+  cudaEvent_t join[2] = {nullptr, nullptr};
   bool locked = false;
-  ff_status begin(cudaStream_t st);
+  ff_status begin(cudaStream_t st, int nside);
   ff_status end();
   ~SideSection() {
     if (locked) end();

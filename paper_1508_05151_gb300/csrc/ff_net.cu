@@ -115,27 +115,49 @@ __global__ void __launch_bounds__(128) k_conv_gemm(ConvArgs a) {
   float acc[8][4];
 #pragma unroll
   for (int j = 0; j < 8; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-  for (int k0 = 0; k0 < a.Kp; k0 += 16) {
-    // A tile: 64 pixels x 16 k (im2col gather, zero padded)
-    for (int i = tid; i < 64 * 16; i += 128) {
-      const int r = i >> 4, kk = i & 15;
-      const int m = m0 + r, k = k0 + kk;
-      __nv_bfloat16 v = __float2bfloat16(0.f);
-      if (m < M && k < a.K) {
-        const int b = m / HW, p = m % HW, y = p / a.W, x = p % a.W;
-        const int c = k / 9, tap = k % 9;
-        const int yy = y + a.sign * ((tap / 3) - 1) * a.dil, xx = x + a.sign * ((tap % 3) - 1) * a.dil;
-        if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
-          v = a.act[((size_t)b * a.C + c) * HW + (size_t)yy * a.W + xx];
-      }
-      sA[r * SP + kk] = v;
+  // Each thread stages column kk = tid % 16 of the A and B^T tiles for rows
+  // tid / 16 + 8 j (j = 0..7); the pixel coordinates of its A rows are computed
+  // once, and the next k chunk is loaded into registers while the current one
+  // is multiplied.
+  const int kk = tid & 15, r0 = tid >> 4;
+  int rb[8], ry[8], rx[8];
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int m = m0 + r0 + 8 * j;
+    if (m < M) {
+      const int b = m / HW, p = m - b * HW;
+      rb[j] = b;
+      ry[j] = p / a.W;
+      rx[j] = p - ry[j] * a.W;
+    } else {
+      rb[j] = -1;
+      ry[j] = rx[j] = 0;
     }
-    // B^T tile: 64 n x 16 k
-    for (int i = tid; i < 64 * 16; i += 128) {
-      const int nn = i >> 4, kk = i & 15;
-      sB[nn * SP + kk] = a.Bmat[(size_t)(k0 + kk) * a.Np + n0 + nn];
+  }
+  __nv_bfloat16 va[8], vb[8];
+  auto load_chunk = [&](int k0) {
+    const int k = k0 + kk;
+    const bool kin = k < a.K;
+    const int c = kin ? k / 9 : 0, tap = kin ? k - 9 * (k / 9) : 0;
+    const int dy = a.sign * ((tap / 3) - 1) * a.dil, dx = a.sign * ((tap % 3) - 1) * a.dil;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const int yy = ry[j] + dy, xx = rx[j] + dx;
+      va[j] = (kin && rb[j] >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
+                  ? a.act[((size_t)rb[j] * a.C + c) * HW + (size_t)yy * a.W + xx]
+                  : __float2bfloat16(0.f);
+      vb[j] = a.Bmat[(size_t)k * a.Np + n0 + r0 + 8 * j];  // zero rows pad K up to Kp
+    }
+  };
+  load_chunk(0);
+  for (int k0 = 0; k0 < a.Kp; k0 += 16) {
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      sA[(r0 + 8 * j) * SP + kk] = va[j];
+      sB[(r0 + 8 * j) * SP + kk] = vb[j];
     }
     __syncthreads();
+    if (k0 + 16 < a.Kp) load_chunk(k0 + 16);
     tile_mma(sA, sB, acc, warp, lane);
     __syncthreads();
   }
@@ -179,25 +201,44 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(WgradArgs a) {
   float acc[8][4];
 #pragma unroll
   for (int j = 0; j < 8; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+  // Each thread stages pixel column kk = tid % 16 for rows tid / 16 + 8 j: the
+  // (channel, tap) of its eight k rows are fixed, its pixel changes per chunk,
+  // and the next chunk is loaded into registers while the current one is used.
+  const int kk = tid & 15, r0 = tid >> 4;
+  int kc[8], kdy[8], kdx[8];
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int k = kcol0 + r0 + 8 * j;
+    const int tap = k % 9;
+    kc[j] = k < a.K ? k / 9 : -1;
+    kdy[j] = ((tap / 3) - 1) * a.dil;
+    kdx[j] = ((tap % 3) - 1) * a.dil;
+  }
+  __nv_bfloat16 vg[8], va[8];
+  auto load_chunk = [&](int q0) {
+    const int m = q0 + kk;
+    const bool in = m < p1;
+    const int b = in ? m / HW : 0, p = in ? m - b * HW : 0;
+    const int y = p / a.W, x = p - y * a.W;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const int r = r0 + 8 * j;
+      vg[j] = (in && r < a.N) ? a.g[((size_t)b * a.N + r) * HW + p] : __float2bfloat16(0.f);
+      const int yy = y + kdy[j], xx = x + kdx[j];
+      va[j] = (in && kc[j] >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
+                  ? a.act[((size_t)b * a.C + kc[j]) * HW + (size_t)yy * a.W + xx]
+                  : __float2bfloat16(0.f);
+    }
+  };
+  if (p0 < p1) load_chunk(p0);
   for (int q0 = p0; q0 < p1; q0 += 16) {
-    for (int i = tid; i < 64 * 16; i += 128) {
-      const int r = i >> 4, kk = i & 15, m = q0 + kk;
-      __nv_bfloat16 gv = __float2bfloat16(0.f), av = __float2bfloat16(0.f);
-      if (m < p1) {
-        const int b = m / HW, p = m % HW;
-        if (r < a.N) gv = a.g[((size_t)b * a.N + r) * HW + p];
-        const int k = kcol0 + r;
-        if (k < a.K) {
-          const int y = p / a.W, x = p % a.W, c = k / 9, tap = k % 9;
-          const int yy = y + ((tap / 3) - 1) * a.dil, xx = x + ((tap % 3) - 1) * a.dil;
-          if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
-            av = a.act[((size_t)b * a.C + c) * HW + (size_t)yy * a.W + xx];
-        }
-      }
-      sA[r * SP + kk] = gv;
-      sB[r * SP + kk] = av;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      sA[(r0 + 8 * j) * SP + kk] = vg[j];
+      sB[(r0 + 8 * j) * SP + kk] = va[j];
     }
     __syncthreads();
+    if (q0 + 16 < p1) load_chunk(q0 + 16);
     tile_mma(sA, sB, acc, warp, lane);
     __syncthreads();
   }

@@ -766,8 +766,8 @@ __global__ void __launch_bounds__(32 * SPLIT) k_pass_wide(const SearchProblem *p
 // the side stream. Both directions are stream-ordered, so the call stays
 // asynchronous and capturable.
 struct SideStream {
-  cudaStream_t s = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t s = nullptr, s2 = nullptr;  // s2: second side stream of a SideSection
+  cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
 };
 static SideStream g_side[64];
 static std::mutex g_side_mu, g_side_enqueue_mu;
@@ -779,8 +779,10 @@ static ff_status side_stream(SideStream **out) {
   SideStream &S = g_side[dev];
   if (!S.s) {
     if (cudaStreamCreateWithFlags(&S.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S.s2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&S.join, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&S.join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S.join2, cudaEventDisableTiming) != cudaSuccess)
       return FF_ERR_CUDA;
   }
   *out = &S;
@@ -878,25 +880,32 @@ static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d
   return FF_OK;
 }
 
-ff_status SideSection::begin(cudaStream_t st) {
+ff_status SideSection::begin(cudaStream_t st, int nside) {
   g_side_enqueue_mu.lock();
   locked = true;
   SideStream *S = nullptr;
   FF_TRY(side_stream(&S));
-  if (cudaEventRecord(S->fork, st) != cudaSuccess || cudaStreamWaitEvent(S->s, S->fork, 0) != cudaSuccess)
-    return FF_ERR_CUDA;
+  if (nside < 1 || nside > 2) return FF_ERR_INVALID_ARG;
+  if (cudaEventRecord(S->fork, st) != cudaSuccess) return FF_ERR_CUDA;
   main = st;
-  side = S->s;
-  join = S->join;
+  const cudaStream_t ss[2] = {S->s, S->s2};
+  const cudaEvent_t js[2] = {S->join, S->join2};
+  for (int i = 0; i < nside; i++) {
+    if (cudaStreamWaitEvent(ss[i], S->fork, 0) != cudaSuccess) return FF_ERR_CUDA;
+    side[i] = ss[i];
+    join[i] = js[i];
+  }
   return FF_OK;
 }
 
 ff_status SideSection::end() {
   ff_status r = FF_OK;
-  if (side && (cudaEventRecord(join, side) != cudaSuccess ||
-               cudaStreamWaitEvent(main, join, 0) != cudaSuccess))
-    r = FF_ERR_CUDA;
-  side = nullptr;
+  for (int i = 0; i < 2; i++) {
+    if (side[i] && (cudaEventRecord(join[i], side[i]) != cudaSuccess ||
+                    cudaStreamWaitEvent(main, join[i], 0) != cudaSuccess))
+      r = FF_ERR_CUDA;
+    side[i] = nullptr;
+  }
   if (locked) {
     locked = false;
     g_side_enqueue_mu.unlock();
