@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(256) k_kd_digit(KdBuild *trees, int d) {
   int hi = B - used, lo = max(hi - DIGIT, 0), nb = 1 << (hi - lo);
   __shared__ uint32_t part[256];
   __shared__ int found_bin, found_before;
-  // each thread sums a run of NBINS/256 = 8 consecutive bins
+  // each thread sums a run of NBINS / 256 consecutive bins
   const int per = NBINS / 256;
   uint32_t mine = 0;
   for (int i = 0; i < per; i++) {
@@ -301,14 +301,47 @@ __global__ void __launch_bounds__(256) k_kd_digit(KdBuild *trees, int d) {
   }
   part[threadIdx.x] = mine;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t k = (uint32_t)S[4], acc = 0;
-    int t = 0;
-    while (t < 255 && acc + part[t] <= k) acc += part[t++];
-    int b = t * per;
-    while (b < NBINS - 1 && acc + h[b] <= k) acc += h[b++];
-    found_bin = b;
-    found_before = (int)acc;
+  // the run holding rank k: inclusive prefix sums of the 256 runs by warp 0 (8
+  // runs per lane), then the bin inside that run by lane 0
+  if (threadIdx.x < 32) {
+    const uint32_t k = (uint32_t)S[4];
+    const int lane = threadIdx.x;
+    uint32_t v[8], sum = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) sum += (v[i] = part[lane * 8 + i]);
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    uint32_t acc = incl - sum;  // runs before this lane's eight
+    int t = -1;
+    uint32_t before = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      if (t < 0 && acc + v[i] > k) {
+        t = lane * 8 + i;
+        before = acc;
+      }
+      acc += v[i];
+    }
+    const unsigned hit = __ballot_sync(0xffffffffu, t >= 0);
+    const int src = hit ? __ffs(hit) - 1 : 31;
+    int tt = __shfl_sync(0xffffffffu, t, src);
+    before = __shfl_sync(0xffffffffu, before, src);
+    const uint32_t last = __shfl_sync(0xffffffffu, v[7], 31), total = __shfl_sync(0xffffffffu, incl, 31);
+    if (!hit) {  // rank beyond the total: the last run, as a sequential scan would stop
+      tt = 255;
+      before = total - last;
+    }
+    if (lane == 0) {
+      int b = tt * per;
+      uint32_t a2 = before;
+      while (b < tt * per + per - 1 && a2 + h[b] <= k) a2 += h[b++];
+      found_bin = b;
+      found_before = (int)a2;
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < NBINS; i += blockDim.x) h[i] = 0;
