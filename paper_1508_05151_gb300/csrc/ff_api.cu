@@ -183,24 +183,6 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
   const int k = p->k, ntop = 1 << k;
   const int srcf[3] = {0, 1, 1}, tgtf[3] = {1, 0, 0}, rad[3] = {p->r, p->r, p->r2};
 
-  // smoothed images and census planes of every pair (shared by all flows)
-  for (int i = 0; i < np; i++) {
-    const PairPlan &P = plans[i];
-    const int W = io[i].W, H = io[i].H;
-    const uint8_t *img[2] = {io[i].I1, io[i].I2};
-    for (int f = 0; f < 2; f++)
-      for (int lv = 0; lv <= k; lv++) {
-        const int n = 1 << lv;
-        const uint8_t *src = img[f];
-        if (n > 1) {
-          FF_TRY(launch_smooth(img[f], W, H, n, P.sm, P.smooth_scratch, st));
-          src = P.sm;
-        }
-        FF_TRY(launch_census(src, W, H, n, P.census, st));
-        FF_TRY(launch_planes(P.census, make_planes(P.planes[f][lv], W, H, n), st));
-      }
-  }
-
   // problem order: the forward flows of every pair, then the first backward flows,
   // then the second backward flows. Each of these three groups computes its
   // features, builds its trees, queries them and searches on a stream of its own
@@ -216,6 +198,28 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
   const int ngroups = 3;
   SideSection sec;
   FF_TRY(sec.begin(st, 2));
+  // smoothed images and census planes of every pair (shared by all flows), on
+  // the second side stream; the other groups wait for them only before their
+  // kd queries, so the pyramid overlaps their features and kd builds
+  const cudaStream_t ps = sec.side[1];
+  for (int i = 0; i < np; i++) {
+    const PairPlan &P = plans[i];
+    const int W = io[i].W, H = io[i].H;
+    const uint8_t *img[2] = {io[i].I1, io[i].I2};
+    for (int f = 0; f < 2; f++)
+      for (int lv = 0; lv <= k; lv++) {
+        const int n = 1 << lv;
+        const uint8_t *src = img[f];
+        if (n > 1) {
+          FF_TRY(launch_smooth(img[f], W, H, n, P.sm, P.smooth_scratch, ps));
+          src = P.sm;
+        }
+        FF_TRY(launch_census(src, W, H, n, P.census, ps));
+        FF_TRY(launch_planes(P.census, make_planes(P.planes[f][lv], W, H, n), ps));
+      }
+  }
+
+  FF_TRY(sec.signal_side(1));
 
   std::vector<KdBuild> trees(nprob);
   std::vector<KdQuery> q(nprob);
@@ -260,6 +264,7 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
                              plans[i].qfeat[j], gs));
     }
     FF_TRY(launch_kd_build(trees.data() + t0, bd.d_kd + t0, cnt, gs));
+    if (g != 2) FF_TRY(sec.wait_signal(gs));  // census planes ready
     // kd query: one launch per run of equal radius
     for (int a0 = t0; a0 < t0 + cnt;) {
       int a1 = a0;

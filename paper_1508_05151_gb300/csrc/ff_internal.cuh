@@ -309,8 +309,12 @@ ff_status run_level_on(const SearchProblem *probs, SearchProblem *dev_desc, int 
 struct SideSection {
   cudaStream_t main = nullptr, side[2] = {nullptr, nullptr};
   cudaEvent_t join[2] = {nullptr, nullptr};
+  cudaEvent_t signal = nullptr;
   bool locked = false;
   ff_status begin(cudaStream_t st, int nside);
+  // mark the point reached on side stream i; wait_signal makes s wait for it
+  ff_status signal_side(int i);
+  ff_status wait_signal(cudaStream_t s);
   ff_status end();
   ~SideSection() {
     if (locked) end();

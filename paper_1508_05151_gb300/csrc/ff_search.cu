@@ -767,7 +767,7 @@ __global__ void __launch_bounds__(32 * SPLIT) k_pass_wide(const SearchProblem *p
 // asynchronous and capturable.
 struct SideStream {
   cudaStream_t s = nullptr, s2 = nullptr;  // s2: second side stream of a SideSection
-  cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr, signal = nullptr;
 };
 static SideStream g_side[64];
 static std::mutex g_side_mu, g_side_enqueue_mu;
@@ -782,7 +782,8 @@ static ff_status side_stream(SideStream **out) {
         cudaStreamCreateWithFlags(&S.s2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&S.join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&S.join2, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&S.join2, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S.signal, cudaEventDisableTiming) != cudaSuccess)
       return FF_ERR_CUDA;
   }
   *out = &S;
@@ -888,6 +889,7 @@ ff_status SideSection::begin(cudaStream_t st, int nside) {
   if (nside < 1 || nside > 2) return FF_ERR_INVALID_ARG;
   if (cudaEventRecord(S->fork, st) != cudaSuccess) return FF_ERR_CUDA;
   main = st;
+  signal = S->signal;
   const cudaStream_t ss[2] = {S->s, S->s2};
   const cudaEvent_t js[2] = {S->join, S->join2};
   for (int i = 0; i < nside; i++) {
@@ -896,6 +898,15 @@ ff_status SideSection::begin(cudaStream_t st, int nside) {
     join[i] = js[i];
   }
   return FF_OK;
+}
+
+ff_status SideSection::signal_side(int i) {
+  if (i < 0 || i > 1 || !side[i]) return FF_ERR_INVALID_ARG;
+  return cudaEventRecord(signal, side[i]) == cudaSuccess ? FF_OK : FF_ERR_CUDA;
+}
+
+ff_status SideSection::wait_signal(cudaStream_t s) {
+  return cudaStreamWaitEvent(s, signal, 0) == cudaSuccess ? FF_OK : FF_ERR_CUDA;
 }
 
 ff_status SideSection::end() {
