@@ -125,11 +125,11 @@ def peaks():
 
 
 # DRAM traffic of the pass kernels per launch, from one ncu capture of this
-# benchmark's pair (dram__bytes_read.sum + dram__bytes_write.sum averaged over the
-# 32 pass launches of one pair; profiles/k_pass_wide_levels_1_and_8_1024x436.md).
+# benchmark's pair (dram__bytes_read.sum + dram__bytes_write.sum averaged over 32
+# consecutive pass launches; profiles/flow_fields_1024x436_launch_list.md).
 # It is reported only while the kernel sources hash to what was profiled.
-PASS_TRAFFIC = {"bytes_per_launch": 6397312,
-                "sources_sha256": "186c62fa169f25ca85b0ac3601890d1d1a42c0befaff0528fc4f2153d6674356"}
+PASS_TRAFFIC = {"bytes_per_launch": 4663528,
+                "sources_sha256": "e4dc0712ad1d626aacf913f52c304edf6301c31992c1b91a1298e82978a6b0f3"}
 PASS_SOURCES = ("paper_1508_05151_gb300/csrc/ff_search.cu", "paper_1508_05151_gb300/csrc/ff_internal.cuh")
 
 
