@@ -12,7 +12,7 @@ library's kernels; this module only schedules calls (no autograd).
 At inference the candidates become the `proposals` input of the search (params.K
 = K). They are tried after the kd-tree candidates under the exact integer data
 term and replace the kd result only on a strictly lower E_d (Eq. 1/4 rerank), so
-the plain search stays both the fallback and the judge of every candidate.
+the plain search stays both the fallback and the arbiter of every candidate.
 """
 from __future__ import annotations
 

@@ -96,6 +96,26 @@ def test_kdtree_build(W, H, r, leaf, flat):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("N,leaf", [(3000, 4), (70001, 8)])
+def test_kdtree_build_arbitrary_features(N, leaf):
+    """The public kd build on feature rows that no WHT produces: spreads up to
+    2^31 (keys wider than the WHT bound, more radix passes) and heavy ties."""
+    rng = np.random.default_rng(N)
+    feat = np.zeros((N, 28), np.int32)
+    feat[:, :9] = rng.integers(-2**30, 2**30, size=(N, 9))
+    feat[:, 9:18] = rng.integers(-3, 4, size=(N, 9)) * (2**28)  # few values, many ties
+    feat[:, 18:27] = rng.integers(0, 5, size=(N, 9))
+    fg = tg(feat)
+    T = ffapi.ff_kdtree_build(fg, leaf)
+    ref = O.kd_build(feat[:, :27], leaf)
+    assert T["D"] == ref["D"]
+    assert np.array_equal(cpu(T["split_dim"]), ref["split_dim"])
+    assert np.array_equal(cpu(T["split_val"]), ref["split_val"])
+    g, o = _leafsets(cpu(T["perm"]), ref["N"], ref["D"]), _leafsets(ref["perm"], ref["N"], ref["D"])
+    for a, b in zip(g, o):
+        assert np.array_equal(a, b)
+
+
 # --------------------------------------------------------------------- A5 -----
 @pytest.mark.parametrize("W,H,n,r,leaf,K", [(40, 30, 1, 3, 4, 0), (128, 96, 8, 8, 8, 0),
                                            (128, 96, 8, 8, 8, 3), (130, 97, 4, 6, 8, 2),
