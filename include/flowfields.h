@@ -282,7 +282,9 @@ ff_status ff_get_exec_params(ff_exec_params *e);
  * data term (strict-less), so they can only replace a kd result with a lower E_d.
  * Layers: four 3x3 convolutions with dilations dil[0..3] and zero padding,
  * channels 6 -> c1 -> c2 -> c3 -> 2K (each <= 64), ReLU between layers, BF16
- * operands and FP32 accumulation on the tensor cores. Parameters are one FP32
+ * operands and FP32 accumulation on the tensor cores (tcgen05, accumulator in
+ * tensor memory). Every wait inside those kernels is bounded; one that runs out
+ * sets the device status word at the start of the workspace (ff_device_status). Parameters are one FP32
  * vector, per layer W[cout][cin][3][3] then b[cout]. Tensors are NCHW fp32:
  * x [B][6][Gy][Gx], out [B][2K][Gy][Gx] with Gx = ceil(W/8), Gy = ceil(H/8);
  * out channel 2k (2k+1) is the x (y) flow of candidate k in units of

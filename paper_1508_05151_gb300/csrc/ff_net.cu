@@ -9,14 +9,18 @@
 // Activations are NCHW; every convolution input is BF16 and accumulates in FP32.
 // Parameters (FP32 master copy) per layer: W [cout][cin][3][3], then b [cout].
 //
-// All three convolution products are implicit GEMMs on the tensor cores
-// (mma.sync m16n8k16, BF16 x BF16 -> FP32):
+// All three convolution products are implicit GEMMs on the 5th-generation
+// tensor cores (tcgen05.mma kind::f16, BF16 x BF16 -> FP32 accumulator in tensor
+// memory):
 //   forward   out[m][n]  = sum_k A[m][k] B[k][n],  m = pixel, n = cout, k = (cin, tap)
 //   dgrad     din[m][n]  = sum_k G[m][k] Bd[k][n], m = pixel, n = cin,  k = (cout, tap), taps mirrored
 //   wgrad     dW[n][k]   = sum_m G[m][n] A[m][k]   (reduction over pixels, split across CTAs)
 // where A is the im2col view of the layer input and G the gradient at the
-// pre-activation. One CTA computes a 64 x 64 output tile with 4 warps (16 rows
-// each, 8 n-tiles of 8); K is staged in shared memory 16 at a time.
+// pre-activation. A CTA of 128 threads computes a 128 x 64 tile: the threads
+// stage both operands 16 deep in shared memory, one thread issues the MMA, an
+// mbarrier reports its completion, and the epilogue reads the accumulator back
+// with tcgen05.ld. Waits are bounded; a wait that runs out sets the device status
+// word at the start of the workspace.
 #include <cuda_bf16.h>
 
 #include "ff_internal.cuh"
@@ -52,43 +56,6 @@ static bool net_shape(const ff_net_desc *d, NetShape &s) {
 static int pad16(int v) { return (v + 15) & ~15; }
 static int pad64(int v) { return (v + 63) & ~63; }
 
-// ---------------------------------------------------------------- mma -------
-__device__ __forceinline__ void mma_bf16(float *c, const uint32_t *a, const uint32_t *b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-// 64x64 tile of out = A B with A[64][16] and B^T[64][16] staged per K step.
-// sA: [64][24] bf16 (row = m), sB: [64][24] bf16 (row = n); the pitch 24 keeps
-// the 32-bit fragment loads conflict-free.
-constexpr int SP = 24;
-
-__device__ __forceinline__ void tile_mma(const __nv_bfloat16 *sA, const __nv_bfloat16 *sB,
-                                         float acc[8][4], int warp, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  const __nv_bfloat16 *ar = sA + (warp * 16 + g) * SP;
-  uint32_t a[4];
-  a[0] = *(const uint32_t *)(ar + 2 * t);
-  a[1] = *(const uint32_t *)(ar + 8 * SP + 2 * t);
-  a[2] = *(const uint32_t *)(ar + 2 * t + 8);
-  a[3] = *(const uint32_t *)(ar + 8 * SP + 2 * t + 8);
-#pragma unroll
-  for (int j = 0; j < 8; j++) {
-    const __nv_bfloat16 *br = sB + (8 * j + g) * SP;
-    uint32_t b[2];
-    b[0] = *(const uint32_t *)(br + 2 * t);
-    b[1] = *(const uint32_t *)(br + 2 * t + 8);
-    mma_bf16(acc[j], a, b);
-  }
-}
-
 // ------------------------------------------------------- forward / dgrad -----
 // out[b][n][y][x] = bias[n] + sum_{c, tap} Bmat[(c,tap)][n] * act[b][c][y + s*oy][x + s*ox]
 // with (oy, ox) = ((tap/3)-1, (tap%3)-1) * dil and s = +1 (forward) or -1 (dgrad).
@@ -106,23 +73,93 @@ struct ConvArgs {
   int relu;
 };
 
-__global__ void __launch_bounds__(128) k_conv_gemm(ConvArgs a) {
-  __shared__ __align__(16) __nv_bfloat16 sA[64 * SP];
-  __shared__ __align__(16) __nv_bfloat16 sB[64 * SP];
+// ------------------------------------------------ forward / dgrad, tcgen05 --
+// The same product on the 5th-generation tensor cores: one CTA (128 threads)
+// computes a 128-pixel x 64-column tile. Per K step of 16 the threads stage the
+// A tile (128 x 16, im2col gather) and the B^T tile (64 x 16) in shared memory
+// in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core
+// matrix; the two core matrices of a row group are 128 B apart along K, row
+// groups 256 B apart), one thread issues tcgen05.mma (BF16 x BF16 -> FP32, the
+// accumulator in tensor memory) and tcgen05.commit signals an mbarrier when the
+// MMA has consumed the tiles. Two stages: the next tiles are gathered while the
+// previous MMA runs. The epilogue reads the accumulator with tcgen05.ld (warp w
+// owns TMEM lanes = tile rows 32w..32w+31).
+constexpr int UMMA_M = 128, UMMA_N = 64, UMMA_K = 16;
+constexpr int UMMA_A_BYTES = UMMA_M * UMMA_K * 2, UMMA_B_BYTES = UMMA_N * UMMA_K * 2;
+constexpr unsigned UMMA_WAIT_LIMIT = 1u << 22;  // bounded mbarrier waits (polls)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading (K-direction) and
+// stride (row-group) byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t umma_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// byte offset of element (row, k) of a K-major tile with 16-element rows
+__device__ __forceinline__ int umma_off(int row, int k) {
+  return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (unsigned it = 0; it < UMMA_WAIT_LIMIT; it++) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(128) k_conv_umma(ConvArgs a, DeviceStatus *status) {
+  __shared__ __align__(1024) uint8_t sA[2][UMMA_A_BYTES];
+  __shared__ __align__(1024) uint8_t sB[2][UMMA_B_BYTES];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_holder;
+  __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int HW = a.H * a.W, M = a.B * HW;
-  const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
-  float acc[8][4];
-#pragma unroll
-  for (int j = 0; j < 8; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-  // Each thread stages column kk = tid % 16 of the A and B^T tiles for rows
-  // tid / 16 + 8 j (j = 0..7); the pixel coordinates of its A rows are computed
-  // once, and the next k chunk is loaded into registers while the current one
-  // is multiplied.
+  const int m0 = blockIdx.x * UMMA_M, n0 = blockIdx.y * UMMA_N;
+
+  if (warp == 0) {  // 64 TMEM columns hold the 128 x 64 FP32 accumulator
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&tmem_holder)),
+                 "r"(UMMA_N)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    s_fail = 0;
+    for (int i = 0; i < 2; i++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_holder;
+
+  // this thread's A rows: pixel r0 + 8 j (j < 16), column kk; B rows r0 + 8 j (j < 8)
   const int kk = tid & 15, r0 = tid >> 4;
-  int rb[8], ry[8], rx[8];
+  int rb[16], ry[16], rx[16];
 #pragma unroll
-  for (int j = 0; j < 8; j++) {
+  for (int j = 0; j < 16; j++) {
     const int m = m0 + r0 + 8 * j;
     if (m < M) {
       const int b = m / HW, p = m - b * HW;
@@ -134,54 +171,95 @@ __global__ void __launch_bounds__(128) k_conv_gemm(ConvArgs a) {
       ry[j] = rx[j] = 0;
     }
   }
-  __nv_bfloat16 va[8], vb[8];
-  auto load_chunk = [&](int k0) {
-    const int k = k0 + kk;
-    const bool kin = k < a.K;
-    const int c = kin ? k / 9 : 0, tap = kin ? k - 9 * (k / 9) : 0;
-    const int dy = a.sign * ((tap / 3) - 1) * a.dil, dx = a.sign * ((tap % 3) - 1) * a.dil;
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-      const int yy = ry[j] + dy, xx = rx[j] + dx;
-      va[j] = (kin && rb[j] >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
-                  ? a.act[((size_t)rb[j] * a.C + c) * HW + (size_t)yy * a.W + xx]
-                  : __float2bfloat16(0.f);
-      vb[j] = a.Bmat[(size_t)k * a.Np + n0 + r0 + 8 * j];  // zero rows pad K up to Kp
+  const uint32_t idesc = umma_idesc(UMMA_M, UMMA_N);
+  const int nsteps = a.Kp / UMMA_K;
+  uint32_t phase[2] = {0u, 0u};
+  for (int step = 0; step < nsteps; step++) {
+    const int st = step & 1, k0 = step * UMMA_K;
+    if (step >= 2) {  // the MMA issued two steps ago has released this stage
+      if (!mbar_wait(smem_u32(&mbar[st]), phase[st])) s_fail = 1;
+      phase[st] ^= 1u;
     }
-  };
-  load_chunk(0);
-  for (int k0 = 0; k0 < a.Kp; k0 += 16) {
+    {
+      const int k = k0 + kk;
+      const bool kin = k < a.K;
+      const int c = kin ? k / 9 : 0, tap = kin ? k - 9 * (k / 9) : 0;
+      const int dy = a.sign * ((tap / 3) - 1) * a.dil, dx = a.sign * ((tap % 3) - 1) * a.dil;
 #pragma unroll
-    for (int j = 0; j < 8; j++) {
-      sA[(r0 + 8 * j) * SP + kk] = va[j];
-      sB[(r0 + 8 * j) * SP + kk] = vb[j];
+      for (int j = 0; j < 16; j++) {
+        const int yy = ry[j] + dy, xx = rx[j] + dx;
+        const __nv_bfloat16 v = (kin && rb[j] >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
+                                    ? a.act[((size_t)rb[j] * a.C + c) * HW + (size_t)yy * a.W + xx]
+                                    : __float2bfloat16(0.f);
+        *(__nv_bfloat16 *)(sA[st] + umma_off(r0 + 8 * j, kk)) = v;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; j++)
+        *(__nv_bfloat16 *)(sB[st] + umma_off(r0 + 8 * j, kk)) = a.Bmat[(size_t)k * a.Np + n0 + r0 + 8 * j];
     }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
-    if (k0 + 16 < a.Kp) load_chunk(k0 + 16);
-    tile_mma(sA, sB, acc, warp, lane);
-    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint64_t adesc = umma_desc(smem_u32(sA[st]), 128, 256);
+      const uint64_t bdesc = umma_desc(smem_u32(sB[st]), 128, 256);
+      const uint32_t acc = step > 0 ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+          : "memory");
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_u32(&mbar[st]))
+                   : "memory");
+    }
   }
-  // epilogue: rows g, g+8 of this warp's 16; columns 8j + 2t, +1
-  const int g = lane >> 2, t = lane & 3;
+  // wait for the last MMA of each stage still in flight
+  for (int st = 0; st < 2; st++) {
+    const int uses = (nsteps - st + 1) / 2;  // MMAs issued on this stage; all but the last waited
+    if (uses > 0) {
+      if (!mbar_wait(smem_u32(&mbar[st]), phase[st])) s_fail = 1;
+      phase[st] ^= 1u;
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  const bool ok = s_fail == 0;
+  if (!ok && tid == 0) raise_status(status, DEV_ERR_TIMEOUT, blockIdx.x, blockIdx.y);
+
+  // epilogue: row m0 + 32 warp + lane, eight columns per tcgen05.ld
+  const int m = m0 + warp * 32 + lane;
+  const int b = m / HW, p = m - b * HW;
+#pragma unroll 1
+  for (int c0 = 0; c0 < UMMA_N; c0 += 8) {
+    uint32_t r[8];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+    if (!ok || m >= M) continue;
 #pragma unroll
-  for (int j = 0; j < 8; j++)
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int m = m0 + warp * 16 + g + (q >> 1) * 8, n = n0 + 8 * j + 2 * t + (q & 1);
-      if (m >= M || n >= a.N) continue;
-      const int b = m / HW, p = m % HW;
+    for (int j = 0; j < 8; j++) {
+      const int n = n0 + c0 + j;
+      if (n >= a.N) continue;
       const size_t o = ((size_t)b * a.N + n) * HW + p;
-      float v = acc[j][q] + (a.bias ? a.bias[n] : 0.f);
+      float v = __uint_as_float(r[j]) + (a.bias ? a.bias[n] : 0.f);
       if (a.mask_pre && !(a.mask_pre[o] > 0.f)) v = 0.f;
       if (a.out) a.out[o] = v;
       if (a.out_bf) a.out_bf[o] = __float2bfloat16(a.relu ? fmaxf(v, 0.f) : v);
     }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(UMMA_N)
+                 : "memory");
 }
 
 // ------------------------------------------------------------------ wgrad ---
-// dW[n][k] += sum_m G[m][n] A[m][k] over the pixels of this CTA's chunk;
-// n = cout (rows of the tile), k = (cin, tap) (columns). Partial sums are added
-// into dW with atomics (the FP32 summation order is unspecified).
 struct WgradArgs {
   const __nv_bfloat16 *g;    // [B][N][H][W] gradient at the pre-activation
   const __nv_bfloat16 *act;  // [B][C][H][W] layer input
@@ -191,75 +269,148 @@ struct WgradArgs {
   int pix_per_cta;
 };
 
-__global__ void __launch_bounds__(128) k_conv_wgrad(WgradArgs a) {
-  __shared__ __align__(16) __nv_bfloat16 sA[64 * SP];  // rows n, cols 16 pixels
-  __shared__ __align__(16) __nv_bfloat16 sB[64 * SP];  // rows k, cols 16 pixels
+// Weight gradient on tcgen05: the transposed product D[k][n] = sum_m A[m][k] G[m][n]
+// (k = (cin, tap) rows, 128 per CTA; n = cout columns, 64; the reduction runs over
+// the CTA's pixel range, 16 pixels per MMA). A^T tile row k = the layer input at
+// tap(k) of channel c(k) for 16 consecutive pixels; G^T tile row n = the gradient
+// of channel n for the same pixels. Both are K-major (pixels contiguous) in the
+// same core-matrix layout as the forward kernel; the FP32 result is added into
+// dW with atomics (the summation order over CTAs is unspecified).
+__global__ void __launch_bounds__(128) k_wgrad_umma(WgradArgs a, DeviceStatus *status) {
+  __shared__ __align__(1024) uint8_t sA[2][UMMA_A_BYTES];
+  __shared__ __align__(1024) uint8_t sB[2][UMMA_B_BYTES];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_holder;
+  __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int HW = a.H * a.W, M = a.B * HW;
-  const int kcol0 = blockIdx.y * 64;
+  const int kt0 = blockIdx.y * UMMA_M;
   const int p0 = blockIdx.x * a.pix_per_cta, p1 = min(p0 + a.pix_per_cta, M);
-  float acc[8][4];
-#pragma unroll
-  for (int j = 0; j < 8; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-  // Each thread stages pixel column kk = tid % 16 for rows tid / 16 + 8 j: the
-  // (channel, tap) of its eight k rows are fixed, its pixel changes per chunk,
-  // and the next chunk is loaded into registers while the current one is used.
-  const int kk = tid & 15, r0 = tid >> 4;
-  int kc[8], kdy[8], kdx[8];
-#pragma unroll
-  for (int j = 0; j < 8; j++) {
-    const int k = kcol0 + r0 + 8 * j;
-    const int tap = k % 9;
-    kc[j] = k < a.K ? k / 9 : -1;
-    kdy[j] = ((tap / 3) - 1) * a.dil;
-    kdx[j] = ((tap % 3) - 1) * a.dil;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&tmem_holder)),
+                 "r"(UMMA_N)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
-  __nv_bfloat16 vg[8], va[8];
-  auto load_chunk = [&](int q0) {
-    const int m = q0 + kk;
-    const bool in = m < p1;
-    const int b = in ? m / HW : 0, p = in ? m - b * HW : 0;
-    const int y = p / a.W, x = p - y * a.W;
+  if (tid == 0) {
+    s_fail = 0;
+    for (int i = 0; i < 2; i++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_holder;
+
+  // this thread's A^T row (k) and its tap; its G^T row (n) and pixel half
+  const int k = kt0 + tid;
+  const bool kin = k < a.K;
+  const int kc = kin ? k / 9 : 0, ktap = kin ? k - 9 * (k / 9) : 0;
+  const int kdy = ((ktap / 3) - 1) * a.dil, kdx = ((ktap % 3) - 1) * a.dil;
+  const int gn = tid & 63, gh = tid >> 6;
+  const uint32_t idesc = umma_idesc(UMMA_M, UMMA_N);
+  const int nsteps = (p1 - p0 + UMMA_K - 1) / UMMA_K;
+  uint32_t phase[2] = {0u, 0u};
+  for (int step = 0; step < nsteps; step++) {
+    const int st = step & 1, q0 = p0 + step * UMMA_K;
+    if (step >= 2) {
+      if (!mbar_wait(smem_u32(&mbar[st]), phase[st])) s_fail = 1;
+      phase[st] ^= 1u;
+    }
+    // pixel coordinates of q0, then stepped pixel by pixel
+    int b = q0 / HW, pp = q0 - b * HW, y = pp / a.W, x = pp - y * a.W;
+#pragma unroll
+    for (int j = 0; j < UMMA_K; j++) {
+      const int m = q0 + j;
+      __nv_bfloat16 av = __float2bfloat16(0.f);
+      if (kin && m < p1) {
+        const int yy = y + kdy, xx = x + kdx;
+        if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
+          av = a.act[((size_t)b * a.C + kc) * HW + (size_t)yy * a.W + xx];
+      }
+      *(__nv_bfloat16 *)(sA[st] + umma_off(tid, j)) = av;
+      if ((j >> 3) == gh) {
+        const __nv_bfloat16 gv = (gn < a.N && m < p1) ? a.g[((size_t)b * a.N + gn) * HW + pp]
+                                                      : __float2bfloat16(0.f);
+        *(__nv_bfloat16 *)(sB[st] + umma_off(gn, j)) = gv;
+      }
+      // next pixel
+      pp++;
+      x++;
+      if (x == a.W) {
+        x = 0;
+        y++;
+      }
+      if (pp == HW) {
+        pp = 0;
+        y = 0;
+        b++;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint64_t adesc = umma_desc(smem_u32(sA[st]), 128, 256);
+      const uint64_t bdesc = umma_desc(smem_u32(sB[st]), 128, 256);
+      const uint32_t acc = step > 0 ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+          : "memory");
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_u32(&mbar[st]))
+                   : "memory");
+    }
+  }
+  for (int st = 0; st < 2; st++) {
+    const int uses = (nsteps - st + 1) / 2;  // MMAs issued on this stage; all but the last waited
+    if (uses > 0) {
+      if (!mbar_wait(smem_u32(&mbar[st]), phase[st])) s_fail = 1;
+      phase[st] ^= 1u;
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  const bool ok = s_fail == 0 && nsteps > 0;
+  if (s_fail && tid == 0) raise_status(status, DEV_ERR_TIMEOUT, blockIdx.x, blockIdx.y);
+  const int kr = kt0 + warp * 32 + lane;  // this thread's accumulator row
+#pragma unroll 1
+  for (int c0 = 0; c0 < UMMA_N; c0 += 8) {
+    uint32_t r[8];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+    if (!ok || kr >= a.K) continue;
 #pragma unroll
     for (int j = 0; j < 8; j++) {
-      const int r = r0 + 8 * j;
-      vg[j] = (in && r < a.N) ? a.g[((size_t)b * a.N + r) * HW + p] : __float2bfloat16(0.f);
-      const int yy = y + kdy[j], xx = x + kdx[j];
-      va[j] = (in && kc[j] >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
-                  ? a.act[((size_t)b * a.C + kc[j]) * HW + (size_t)yy * a.W + xx]
-                  : __float2bfloat16(0.f);
+      const int n = c0 + j;
+      if (n < a.N) atomicAdd(&a.dW[(size_t)n * a.K + kr], __uint_as_float(r[j]));
     }
-  };
-  if (p0 < p1) load_chunk(p0);
-  for (int q0 = p0; q0 < p1; q0 += 16) {
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-      sA[(r0 + 8 * j) * SP + kk] = vg[j];
-      sB[(r0 + 8 * j) * SP + kk] = va[j];
-    }
-    __syncthreads();
-    if (q0 + 16 < p1) load_chunk(q0 + 16);
-    tile_mma(sA, sB, acc, warp, lane);
-    __syncthreads();
   }
-  const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int j = 0; j < 8; j++)
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int n = warp * 16 + g + (q >> 1) * 8, k = kcol0 + 8 * j + 2 * t + (q & 1);
-      if (n < a.N && k < a.K) atomicAdd(&a.dW[(size_t)n * a.K + k], acc[j][q]);
-    }
-  // bias gradient from the first column block only
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(UMMA_N)
+                 : "memory");
+  // bias gradient from the first row block only
   if (blockIdx.y == 0 && a.db)
     for (int n = warp; n < a.N; n += 4) {
-      float s = 0.f;
+      float sum = 0.f;
       for (int m = p0 + lane; m < p1; m += 32) {
-        const int b = m / HW, p = m % HW;
-        s += __bfloat162float(a.g[((size_t)b * a.N + n) * HW + p]);
+        const int bb = m / HW, q = m - bb * HW;
+        sum += __bfloat162float(a.g[((size_t)bb * a.N + n) * HW + q]);
       }
-      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) atomicAdd(&a.db[n], s);
+      for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0) atomicAdd(&a.db[n], sum);
     }
 }
 
@@ -404,9 +555,9 @@ static NetWs net_ws(Arena &a, const NetShape &s, int B, int Gx, int Gy) {
   return w;
 }
 
-static ff_status launch_conv(const ConvArgs &c, int M, cudaStream_t st) {
-  dim3 g((M + 63) / 64, c.Np / 64);
-  k_conv_gemm<<<g, 128, 0, st>>>(c);
+static ff_status launch_conv(const ConvArgs &c, int M, DeviceStatus *status, cudaStream_t st) {
+  dim3 g((M + UMMA_M - 1) / UMMA_M, c.Np / UMMA_N);
+  k_conv_umma<<<g, 128, 0, st>>>(c, status);
   FF_CHECK_LAUNCH();
   return FF_OK;
 }
@@ -453,6 +604,7 @@ ff_status ff_net_forward(const ff_net_desc *d, const float *params, const float 
   FF_TRY(ff_net_workspace_size(d, B, Gx, Gy, &need));
   if (!ws || ((uintptr_t)ws & 255) || ws_bytes < need) return FF_ERR_WORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(ws, 0, sizeof(DeviceStatus), st) != cudaSuccess) return FF_ERR_CUDA;
   Arena a(ws, ws_bytes);
   a.take<char>(WS_HEADER);
   NetWs w = net_ws(a, s, B, Gx, Gy);
@@ -483,7 +635,7 @@ ff_status ff_net_forward(const ff_net_desc *d, const float *params, const float 
     c.out = last ? out : w.pre[l];
     c.out_bf = last ? nullptr : w.act[l + 1];
     c.relu = last ? 0 : 1;
-    FF_TRY(launch_conv(c, (int)P, st));
+    FF_TRY(launch_conv(c, (int)P, (DeviceStatus *)ws, st));
   }
   return FF_OK;
 }
@@ -502,6 +654,7 @@ ff_status ff_net_backward(const ff_net_desc *d, const float *params, const float
   NetWs w = net_ws(a, s, B, Gx, Gy);
   const size_t P = (size_t)B * Gx * Gy;
   if (cudaMemsetAsync(grads, 0, sizeof(float) * s.nparams, st) != cudaSuccess) return FF_ERR_CUDA;
+  if (cudaMemsetAsync(ws, 0, sizeof(DeviceStatus), st) != cudaSuccess) return FF_ERR_CUDA;
   // gradient at the last pre-activation (the output has no ReLU)
   const int L = NET_LAYERS - 1;
   k_to_bf16<<<(unsigned)((P * s.cout[L] + 255) / 256), 256, 0, st>>>(dout, P * s.cout[L], w.gbf[L]);
@@ -520,8 +673,8 @@ ff_status ff_net_backward(const ff_net_desc *d, const float *params, const float
     wa.dW = grads + s.woff[l];
     wa.db = grads + s.boff[l];
     wa.pix_per_cta = 512;
-    dim3 gw((unsigned)((P + wa.pix_per_cta - 1) / wa.pix_per_cta), (wa.K + 63) / 64);
-    k_conv_wgrad<<<gw, 128, 0, st>>>(wa);
+    dim3 gw((unsigned)((P + wa.pix_per_cta - 1) / wa.pix_per_cta), (wa.K + UMMA_M - 1) / UMMA_M);
+    k_wgrad_umma<<<gw, 128, 0, st>>>(wa, (DeviceStatus *)ws);
     FF_CHECK_LAUNCH();
     if (l == 0) break;
     // dgrad: gradient at the input of layer l, masked by the ReLU of layer l-1
@@ -543,7 +696,7 @@ ff_status ff_net_backward(const ff_net_desc *d, const float *params, const float
     c.out_bf = w.gbf[l - 1];
     c.mask_pre = w.pre[l - 1];
     c.relu = 0;
-    FF_TRY(launch_conv(c, (int)P, st));
+    FF_TRY(launch_conv(c, (int)P, (DeviceStatus *)ws, st));
   }
   return FF_OK;
 }
