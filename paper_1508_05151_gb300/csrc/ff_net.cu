@@ -155,22 +155,19 @@ __global__ void __launch_bounds__(128) k_conv_umma(ConvArgs a, DeviceStatus *sta
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_holder;
 
-  // this thread's A rows: pixel r0 + 8 j (j < 16), column kk; B rows r0 + 8 j (j < 8)
-  const int kk = tid & 15, r0 = tid >> 4;
-  int rb[16], ry[16], rx[16];
-#pragma unroll
-  for (int j = 0; j < 16; j++) {
-    const int m = m0 + r0 + 8 * j;
-    if (m < M) {
-      const int b = m / HW, p = m - b * HW;
-      rb[j] = b;
-      ry[j] = p / a.W;
-      rx[j] = p - ry[j] * a.W;
-    } else {
-      rb[j] = -1;
-      ry[j] = rx[j] = 0;
-    }
+  // thread t stages row t of the A tile (pixel m0 + t, 16 consecutive k: each
+  // warp load reads 32 neighbouring pixels of one channel and tap) as two
+  // 16-byte shared stores, and half a row of the B^T tile (row t % 64)
+  const int ms = m0 + tid;
+  int pb = -1, py = 0, px = 0;
+  if (ms < M) {
+    pb = ms / HW;
+    const int p = ms - pb * HW;
+    py = p / a.W;
+    px = p - py * a.W;
   }
+  const int bn = tid & 63, bh = tid >> 6;
+  const __nv_bfloat16 *actb = pb >= 0 ? a.act + (size_t)pb * a.C * HW : a.act;
   const uint32_t idesc = umma_idesc(UMMA_M, UMMA_N);
   const int nsteps = a.Kp / UMMA_K;
   uint32_t phase[2] = {0u, 0u};
@@ -181,21 +178,33 @@ __global__ void __launch_bounds__(128) k_conv_umma(ConvArgs a, DeviceStatus *sta
       phase[st] ^= 1u;
     }
     {
-      const int k = k0 + kk;
-      const bool kin = k < a.K;
-      const int c = kin ? k / 9 : 0, tap = kin ? k - 9 * (k / 9) : 0;
-      const int dy = a.sign * ((tap / 3) - 1) * a.dil, dx = a.sign * ((tap % 3) - 1) * a.dil;
+      uint32_t pk[8];
 #pragma unroll
-      for (int j = 0; j < 16; j++) {
-        const int yy = ry[j] + dy, xx = rx[j] + dx;
-        const __nv_bfloat16 v = (kin && rb[j] >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
-                                    ? a.act[((size_t)rb[j] * a.C + c) * HW + (size_t)yy * a.W + xx]
-                                    : __float2bfloat16(0.f);
-        *(__nv_bfloat16 *)(sA[st] + umma_off(r0 + 8 * j, kk)) = v;
+      for (int kk = 0; kk < UMMA_K; kk += 2) {
+        unsigned short h2[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          const int k = k0 + kk + u;
+          __nv_bfloat16 v = __float2bfloat16(0.f);
+          if (k < a.K && pb >= 0) {
+            const int c = k / 9, tap = k - 9 * c;
+            const int yy = py + a.sign * ((tap / 3) - 1) * a.dil, xx = px + a.sign * ((tap % 3) - 1) * a.dil;
+            if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) v = actb[(size_t)c * HW + (size_t)yy * a.W + xx];
+          }
+          h2[u] = __bfloat16_as_ushort(v);
+        }
+        pk[kk >> 1] = (uint32_t)h2[0] | ((uint32_t)h2[1] << 16);
       }
+      *(uint4 *)(sA[st] + umma_off(tid, 0)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      *(uint4 *)(sA[st] + umma_off(tid, 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      uint32_t qb[4];
 #pragma unroll
-      for (int j = 0; j < 8; j++)
-        *(__nv_bfloat16 *)(sB[st] + umma_off(r0 + 8 * j, kk)) = a.Bmat[(size_t)k * a.Np + n0 + r0 + 8 * j];
+      for (int i = 0; i < 4; i++) {
+        const int k = k0 + 8 * bh + 2 * i;
+        const __nv_bfloat16 lo = a.Bmat[(size_t)k * a.Np + n0 + bn], hi = a.Bmat[(size_t)(k + 1) * a.Np + n0 + bn];
+        qb[i] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+      }
+      *(uint4 *)(sB[st] + umma_off(bn, 8 * bh)) = make_uint4(qb[0], qb[1], qb[2], qb[3]);
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
