@@ -280,17 +280,21 @@ struct WgradArgs {
 
 // Weight gradient on tcgen05: the transposed product D[k][n] = sum_m A[m][k] G[m][n]
 // (k = (cin, tap) rows, 128 per CTA; n = cout columns, 64; the reduction runs over
-// the CTA's pixel range, 16 pixels per MMA). A^T tile row k = the layer input at
-// tap(k) of channel c(k) for 16 consecutive pixels; G^T tile row n = the gradient
-// of channel n for the same pixels. Both are K-major (pixels contiguous) in the
-// same core-matrix layout as the forward kernel; the FP32 result is added into
-// dW with atomics (the summation order over CTAs is unspecified).
-__global__ void __launch_bounds__(128) k_wgrad_umma(WgradArgs a, DeviceStatus *status) {
-  __shared__ __align__(1024) uint8_t sA[2][UMMA_A_BYTES];
-  __shared__ __align__(1024) uint8_t sB[2][UMMA_B_BYTES];
+// the CTA's pixel range, WG_PIX pixels per stage = two MMAs of 16). A^T tile row k =
+// the layer input at tap(k) of channel c(k) for the stage's pixels; G^T tile row n =
+// the gradient of channel n for the same pixels. Lane = pixel when staging, so each
+// warp load reads 64 contiguous bytes of one row. Each 16-pixel half of a tile is
+// K-major in the same core-matrix layout as the forward kernel; the FP32 result is
+// added into dW with atomics (the summation order over CTAs is unspecified).
+constexpr int WG_PIX = 32;
+constexpr int WG_A_HALF = UMMA_M * 16 * 2, WG_B_HALF = UMMA_N * 16 * 2;
+__global__ void __launch_bounds__(128, 8) k_wgrad_umma(WgradArgs a, DeviceStatus *status) {
+  __shared__ __align__(1024) uint8_t sA[2][2 * WG_A_HALF];
+  __shared__ __align__(1024) uint8_t sB[2][2 * WG_B_HALF];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_holder;
   __shared__ int s_fail;
+  __shared__ int s_koff[UMMA_M], s_kdy[UMMA_M], s_kdx[UMMA_M];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int HW = a.H * a.W, M = a.B * HW;
   const int kt0 = blockIdx.y * UMMA_M;
@@ -309,68 +313,67 @@ __global__ void __launch_bounds__(128) k_wgrad_umma(WgradArgs a, DeviceStatus *s
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[i])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  {  // per A^T row: channel offset (-1 past K) and tap displacement
+    const int k = kt0 + tid, tap = k % 9;
+    s_koff[tid] = k < a.K ? (k / 9) * HW : -1;
+    s_kdy[tid] = ((tap / 3) - 1) * a.dil;
+    s_kdx[tid] = ((tap % 3) - 1) * a.dil;
+  }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_holder;
 
-  // this thread's A^T row (k) and its tap; its G^T row (n) and pixel half
-  const int k = kt0 + tid;
-  const bool kin = k < a.K;
-  const int kc = kin ? k / 9 : 0, ktap = kin ? k - 9 * (k / 9) : 0;
-  const int kdy = ((ktap / 3) - 1) * a.dil, kdx = ((ktap % 3) - 1) * a.dil;
-  const int gn = tid & 63, gh = tid >> 6;
+  // staging: lane = pixel of the stage; warp w fills A^T rows 32w..32w+31 and
+  // G^T rows 16w..16w+15. Byte offset of (row, pixel lane) inside a stage tile:
+  const int a_lane = (lane >> 4) * WG_A_HALF, b_lane = (lane >> 4) * WG_B_HALF;
   const uint32_t idesc = umma_idesc(UMMA_M, UMMA_N);
-  const int nsteps = (p1 - p0 + UMMA_K - 1) / UMMA_K;
+  const int nsteps = (p1 - p0 + WG_PIX - 1) / WG_PIX;
+  float bsum[16];  // this lane's share of the bias gradient of G^T rows 16w..16w+15
+#pragma unroll
+  for (int i = 0; i < 16; i++) bsum[i] = 0.f;
   uint32_t phase[2] = {0u, 0u};
   for (int step = 0; step < nsteps; step++) {
-    const int st = step & 1, q0 = p0 + step * UMMA_K;
+    const int st = step & 1;
     if (step >= 2) {
       if (!mbar_wait(smem_u32(&mbar[st]), phase[st])) s_fail = 1;
       phase[st] ^= 1u;
     }
-    // pixel coordinates of q0, then stepped pixel by pixel
-    int b = q0 / HW, pp = q0 - b * HW, y = pp / a.W, x = pp - y * a.W;
+    const int m = p0 + step * WG_PIX + lane;
+    const bool pin = m < p1;
+    const int b = pin ? m / HW : 0, pp = m - b * HW, y = pp / a.W, x = pp - y * a.W;
+    const __nv_bfloat16 *actp = a.act + (size_t)b * a.C * HW + pp;
+    const __nv_bfloat16 *gp = a.g + (size_t)b * a.N * HW + pp;
+#pragma unroll 8
+    for (int i = 0; i < 32; i++) {
+      const int row = warp * 32 + i, koff = s_koff[row], dy = s_kdy[row], dx = s_kdx[row];
+      __nv_bfloat16 v = __float2bfloat16(0.f);
+      if (pin && koff >= 0 && (unsigned)(y + dy) < (unsigned)a.H && (unsigned)(x + dx) < (unsigned)a.W)
+        v = actp[koff + dy * a.W + dx];
+      *(__nv_bfloat16 *)(sA[st] + a_lane + umma_off(row, lane & 15)) = v;
+    }
 #pragma unroll
-    for (int j = 0; j < UMMA_K; j++) {
-      const int m = q0 + j;
-      __nv_bfloat16 av = __float2bfloat16(0.f);
-      if (kin && m < p1) {
-        const int yy = y + kdy, xx = x + kdx;
-        if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
-          av = a.act[((size_t)b * a.C + kc) * HW + (size_t)yy * a.W + xx];
-      }
-      *(__nv_bfloat16 *)(sA[st] + umma_off(tid, j)) = av;
-      if ((j >> 3) == gh) {
-        const __nv_bfloat16 gv = (gn < a.N && m < p1) ? a.g[((size_t)b * a.N + gn) * HW + pp]
-                                                      : __float2bfloat16(0.f);
-        *(__nv_bfloat16 *)(sB[st] + umma_off(gn, j)) = gv;
-      }
-      // next pixel
-      pp++;
-      x++;
-      if (x == a.W) {
-        x = 0;
-        y++;
-      }
-      if (pp == HW) {
-        pp = 0;
-        y = 0;
-        b++;
-      }
+    for (int i = 0; i < 16; i++) {
+      const int n = warp * 16 + i;
+      const __nv_bfloat16 v = (pin && n < a.N) ? gp[(size_t)n * HW] : __float2bfloat16(0.f);
+      *(__nv_bfloat16 *)(sB[st] + b_lane + umma_off(n, lane & 15)) = v;
+      bsum[i] += __bfloat162float(v);
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint64_t adesc = umma_desc(smem_u32(sA[st]), 128, 256);
-      const uint64_t bdesc = umma_desc(smem_u32(sB[st]), 128, 256);
-      const uint32_t acc = step > 0 ? 1u : 0u;
-      asm volatile(
-          "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-          "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-          : "memory");
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const uint64_t adesc = umma_desc(smem_u32(sA[st] + h * WG_A_HALF), 128, 256);
+        const uint64_t bdesc = umma_desc(smem_u32(sB[st] + h * WG_B_HALF), 128, 256);
+        const uint32_t acc = (step > 0 || h > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+      }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                        smem_u32(&mbar[st]))
                    : "memory");
@@ -410,17 +413,16 @@ __global__ void __launch_bounds__(128) k_wgrad_umma(WgradArgs a, DeviceStatus *s
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(UMMA_N)
                  : "memory");
-  // bias gradient from the first row block only
-  if (blockIdx.y == 0 && a.db)
-    for (int n = warp; n < a.N; n += 4) {
-      float sum = 0.f;
-      for (int m = p0 + lane; m < p1; m += 32) {
-        const int bb = m / HW, q = m - bb * HW;
-        sum += __bfloat162float(a.g[((size_t)bb * a.N + n) * HW + q]);
-      }
-      for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-      if (lane == 0) atomicAdd(&a.db[n], sum);
+  // bias gradient (first row block only): the sums of the staged G^T values
+  if (blockIdx.y == 0 && a.db) {
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      float v = bsum[i];
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      const int n = warp * 16 + i;
+      if (lane == 0 && n < a.N) atomicAdd(&a.db[n], v);
     }
+  }
 }
 
 // ------------------------------------------------------------- helpers ------
@@ -662,6 +664,10 @@ ff_status ff_net_backward(const ff_net_desc *d, const float *params, const float
   a.take<char>(WS_HEADER);
   NetWs w = net_ws(a, s, B, Gx, Gy);
   const size_t P = (size_t)B * Gx * Gy;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+    return FF_ERR_CUDA;
   if (cudaMemsetAsync(grads, 0, sizeof(float) * s.nparams, st) != cudaSuccess) return FF_ERR_CUDA;
   if (cudaMemsetAsync(ws, 0, sizeof(DeviceStatus), st) != cudaSuccess) return FF_ERR_CUDA;
   // gradient at the last pre-activation (the output has no ReLU)
@@ -681,8 +687,14 @@ ff_status ff_net_backward(const ff_net_desc *d, const float *params, const float
     wa.K = s.cin[l] * 9;
     wa.dW = grads + s.woff[l];
     wa.db = grads + s.boff[l];
-    wa.pix_per_cta = 512;
-    dim3 gw((unsigned)((P + wa.pix_per_cta - 1) / wa.pix_per_cta), (wa.K + UMMA_M - 1) / UMMA_M);
+    // pixel range per CTA: about eight CTAs per SM over the whole grid (the
+    // staging is load-latency bound), whole 32-pixel stages, at least 64 pixels
+    const int ky = (wa.K + UMMA_M - 1) / UMMA_M;
+    const long long want = (long long)nsm * 8;
+    long long ppc = ((long long)P * ky + want - 1) / want;
+    ppc = ((ppc + WG_PIX - 1) / WG_PIX) * WG_PIX;
+    wa.pix_per_cta = (int)(ppc < 64 ? 64 : ppc);
+    dim3 gw((unsigned)((P + wa.pix_per_cta - 1) / wa.pix_per_cta), ky);
     k_wgrad_umma<<<gw, 128, 0, st>>>(wa, (DeviceStatus *)ws);
     FF_CHECK_LAUNCH();
     if (l == 0) break;
