@@ -176,6 +176,18 @@ def flow_quality(flow, gt, occ):
     return float((e[m] <= 3.0).mean()), float(e[m].mean())
 
 
+def paired_inlier_delta(flow_a, flow_b, gt, occ):
+    """Per-pair difference of inliers@3px, arm a minus arm b, over the same pairs:
+    mean and standard error of the mean (n - 1 in the variance; 0 for one pair)."""
+    d = []
+    for j in range(len(gt)):
+        d.append(flow_quality(flow_a[j:j + 1], gt[j:j + 1], occ[j:j + 1])[0]
+                 - flow_quality(flow_b[j:j + 1], gt[j:j + 1], occ[j:j + 1])[0])
+    d = np.asarray(d, np.float64)
+    se = float(d.std(ddof=1) / np.sqrt(len(d))) if len(d) > 1 else 0.0
+    return dict(mean=float(d.mean()), se=se, pairs=len(d))
+
+
 def run_arm(net, I1, I2, params, batch=32, device="cuda", reps=5):
     """Forward flows of all pairs with one arm (plain if params.K == 0, else with
     the net's proposals) and the device time per pair (ms, CUDA events, median over
@@ -247,7 +259,8 @@ def evaluate(net, I1, I2, gt, occ, n_rs_list=(1, 2, 3), params=None, batch=32,
              device="cuda", reps=5):
     """Plain search vs search with the net's proposals on the same pairs, at each
     random-search budget n_rs. Per arm and budget: ms per pair, inliers@3px, EPE;
-    per budget the fraction of pixels where the two forward flows differ; and the
+    per budget the fraction of pixels where the two forward flows differ and the
+    per-pair inlier difference (learned - plain, mean and standard error); and the
     proposals' data-cost delta at the coarsest level."""
     base = ffapi._params(params).as_dict()
     out = dict(coarse=coarse_cost_delta(net, I1, I2, base, device), arms={})
@@ -262,6 +275,10 @@ def evaluate(net, I1, I2, gt, occ, n_rs_list=(1, 2, 3), params=None, batch=32,
             fl[name] = f
         d = np.abs(fl["learned"].astype(np.int32) - fl["plain"].astype(np.int32)).sum(-1)
         out["arms"][f"changed_rs{n_rs}"] = round(float((d > 0).mean()), 5)
+        m = fl["plain"].shape[0]
+        dl = paired_inlier_delta(fl["learned"], fl["plain"], gt[:m], occ[:m])
+        out["arms"][f"inlier_delta_rs{n_rs}"] = {k: (round(v, 6) if isinstance(v, float) else v)
+                                                 for k, v in dl.items()}
     return out
 
 
@@ -277,6 +294,52 @@ def equal_inlier_point(ev, ref="plain_rs3"):
     ms, k = min(ok)
     return dict(arm=k, ms_per_pair=ms, ref=ref, ref_ms_per_pair=arms[ref]["ms_per_pair"],
                 speedup=round(arms[ref]["ms_per_pair"] / ms, 4))
+
+
+def forward_flow_levels(I1, I2, budgets, proposals=None, params=None):
+    """Forward flow of one pair (uint8 [H][W][3] CUDA tensors) composed from the
+    per-level entry points, with its own random-search budget per level:
+    budgets[i] is n_rs at the level of spacing 2^(k-i) (coarsest first). Features
+    of I2, the kd tree, the kd init (with the net's proposals if given) and the
+    top level in place, then each finer level seeded from the one above (Sec. 3.2,
+    Fig. 2). With a uniform budget this is ff_flow_fields' forward flow."""
+    P = ffapi._params(params).as_dict()
+    k, r, leaf = P["k"], P["r"], P["leaf"]
+    if len(budgets) != k + 1:
+        raise ValueError(f"need {k + 1} budgets, one per level")
+    tree = ffapi.ff_kdtree_build(ffapi.ff_features(I2, r), leaf)
+    flow = cost = None
+    for i in range(k + 1):
+        n = 1 << (k - i)
+        a = ffapi.ff_smooth(I1, n) if n > 1 else I1
+        b = ffapi.ff_smooth(I2, n) if n > 1 else I2
+        C1, C2 = ffapi.ff_census(a, n), ffapi.ff_census(b, n)
+        Pl = dict(P, n_rs=int(budgets[i]))
+        if i == 0:
+            flow, cost = ffapi.ff_kdtree_init(tree, leaf, I1, C1, C2, n, r, proposals)
+            ffapi.ff_search_level(C1, C2, n, r, Pl, flow_id=0, flow=flow, cost=cost)
+        else:
+            flow, _ = ffapi.ff_search_level(C1, C2, n, r, Pl, flow_id=0, flow_coarse=flow)
+    return flow
+
+
+def level_budget_study(net, I1, I2, gt, occ, budgets, params=None, device="cuda"):
+    """Inliers@3px and EPE of the forward flow for per-level random-search budgets
+    (tuples, coarsest level first), plain and with the net's proposals. Shows
+    which levels' random search the flow quality depends on."""
+    a = torch.as_tensor(I1).to(device)
+    b = torch.as_tensor(I2).to(device)
+    prop = net.infer(a, b) if net is not None else None
+    out = {}
+    for bud in budgets:
+        arms = (("plain", None),) + ((("learned", prop),) if prop is not None else ())
+        for name, pr in arms:
+            fl = [forward_flow_levels(a[j], b[j], bud, None if pr is None else pr[j].contiguous(),
+                                      params).cpu().numpy() for j in range(a.shape[0])]
+            inl, epe = flow_quality(np.stack(fl), gt, occ)
+            out[f"{name}_{''.join(str(int(v)) for v in bud)}"] = dict(
+                inliers_3px=round(inl, 5), epe=round(epe, 4))
+    return out
 
 
 def train_for(config, n_train, epochs, batch=64, lr=2e-3, seed=1000, size=None, log=None):
@@ -314,6 +377,9 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=1000)
     ap.add_argument("--save", default=None, help="checkpoint path (.npz)")
     ap.add_argument("--load", default=None, help="skip training, load this checkpoint")
+    ap.add_argument("--level-budgets", default=None,
+                    help="per-level n_rs study on the eval pairs, e.g. 3333,1333,3331 "
+                         "(coarsest level first)")
     a = ap.parse_args(argv)
     if a.load:
         net, info = ProposalNet.load(a.load), dict(loaded=a.load)
@@ -323,7 +389,11 @@ def main(argv=None):
         net.save(a.save)
     E1, E2, Egt, Eocc = make_pairs(a.config, range(a.seed + 10**6, a.seed + 10**6 + a.eval))
     ev = evaluate(net, E1, E2, Egt, Eocc, tuple(int(v) for v in a.n_rs.split(",")))
-    print(json.dumps(dict(train=info, eval=ev, equal_inliers=equal_inlier_point(ev))))
+    res = dict(train=info, eval=ev, equal_inliers=equal_inlier_point(ev))
+    if a.level_budgets:
+        buds = [tuple(int(c) for c in w) for w in a.level_budgets.split(",")]
+        res["level_budgets"] = level_budget_study(net, E1, E2, Egt, Eocc, buds)
+    print(json.dumps(res))
 
 
 if __name__ == "__main__":

@@ -302,3 +302,33 @@ def test_flow_fields_is_deterministic_and_stream_independent():
     for k in a:
         assert torch.equal(a[k], b[k]), k
     assert ff.device_status() == (0, 0, 0)
+
+
+# ------------------------------------------- per-level budget composition -----
+def test_forward_flow_levels_composition():
+    """The per-level composition used by the random-search budget study: with a
+    uniform budget it is ff_flow_fields' forward flow; with a different n_rs per
+    level it is bit-exact against the oracle composed the same way."""
+    from paper_1508_05151_gb300 import train
+    W, H = 150, 101
+    p = synth.pair_shift(4242, W=W, H=H, max_shift=(12, 9), square=32, square_move=10)
+    I1, I2 = p["I1"], p["I2"]
+    a, b = tg(I1), tg(I2)
+    full = ffapi.FlowFields(W, H).run(a, b)
+    assert torch.equal(train.forward_flow_levels(a, b, (3, 3, 3, 3)), full["flows"][0])
+    bud = (1, 3, 0, 2)
+    got = cpu(train.forward_flow_levels(a, b, bud)).astype(np.int32)
+    P = O.default_params()
+    r, leaf = P["r"], P["leaf"]
+    feat = O.wht_features(I2, r)
+    kw = dict(tile=P["tile"], R=P["R"], seed=P["seed"], flow_id=0)
+    flow = None
+    for i, n in enumerate((8, 4, 2, 1)):
+        C1 = O.census(O.smooth(I1, n) if n > 1 else I1, n)
+        C2 = O.census(O.smooth(I2, n) if n > 1 else I2, n)
+        if i == 0:
+            flow, cost, _ = O.kd_init(feat, I1, r, leaf, C1, C2, n)
+            flow, cost, _ = O.search_level(C1, C2, n, r, flow=flow, cost=cost, n_rs=bud[i], **kw)
+        else:
+            flow, cost, _ = O.search_level(C1, C2, n, r, flow_coarse=flow, n_rs=bud[i], **kw)
+    assert np.array_equal(got, flow)
