@@ -478,6 +478,29 @@ __device__ __forceinline__ unsigned long long bitonic_sort_blocks(unsigned long 
   return c;
 }
 
+// The same for 32-bit keys (one shuffle per exchange).
+__device__ __forceinline__ uint32_t bitonic_sort_blocks32(uint32_t c, int B, uint32_t *buf) {
+  const int t = threadIdx.x;
+  int flip = 0;
+  for (int k = 2; k <= B; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      uint32_t o;
+      if (j >= 32) {
+        uint32_t *b = buf + flip * SUB_MAX;
+        b[t] = c;
+        __syncthreads();
+        o = b[t ^ j];
+        flip ^= 1;
+      } else {
+        o = __shfl_xor_sync(0xffffffffu, c, j);
+      }
+      const bool up = (k == B) || ((t & k) == 0), lower = (t & j) == 0;
+      c = (lower == up) ? min(o, c) : max(o, c);
+    }
+  }
+  return c;
+}
+
 // One 1024-thread CTA finishes the subtree of one segment at depth top_levels.
 // The segment's points live in shared memory with their 27 features; at
 // sub-level sd node j owns the aligned slot block [j B, j B + B), B = 1024 >> sd,
@@ -487,7 +510,11 @@ __device__ __forceinline__ unsigned long long bitonic_sort_blocks(unsigned long 
 // rank, slot), and one move of every point to its child's block: the first
 // floor(m/2) stay, the others go to the second half. The first point of the
 // right half is the split. The pixel-index rank (0..1023) breaks ties exactly as
-// the pixel index does; it is set once by sorting the segment's indices.
+// the pixel index does; it is set once by sorting the segment's indices. When
+// every node's spread in its split dimension is below 2^21 (always for WHT
+// features, |value| <= 289 * 255) the sort key is the 32-bit (value - node min,
+// rank) and a rank -> slot table finds each key's point; otherwise the 64-bit
+// key carries the slot itself.
 constexpr int SUB_SD_SMEM_NODES = SUB_MAX / 64;  // nodes with blocks wider than a warp
 
 __global__ void __launch_bounds__(SUB_MAX) k_kd_subtree(KdBuild *trees) {
@@ -498,8 +525,9 @@ __global__ void __launch_bounds__(SUB_MAX) k_kd_subtree(KdBuild *trees) {
   const int m0 = e0 - b0;
   extern __shared__ __align__(16) int32_t ssub[];
   unsigned long long *sbuf = (unsigned long long *)ssub;  // 2 x SUB_MAX sort buffers
-  unsigned long long *ssorted = sbuf + 2 * SUB_MAX;       // SUB_MAX sorted keys
-  int32_t *sF = (int32_t *)(ssorted + SUB_MAX);           // SUB_MAX x NFEAT features
+  int32_t *ssorted = (int32_t *)(sbuf + 2 * SUB_MAX);      // SUB_MAX: source slot of sorted key
+  int32_t *sslot = ssorted + SUB_MAX;                      // SUB_MAX: slot of each rank
+  int32_t *sF = sslot + SUB_MAX;                           // SUB_MAX x NFEAT features
   int32_t *sidx = sF + SUB_MAX * NFEAT;                    // pixel index per slot
   int32_t *srank = sidx + SUB_MAX;                         // pixel-index rank per slot
   int32_t *ssize = srank + SUB_MAX;                        // 2 x SUB_MAX node sizes (ping-pong)
@@ -513,13 +541,13 @@ __global__ void __launch_bounds__(SUB_MAX) k_kd_subtree(KdBuild *trees) {
   const int t = threadIdx.x, lane = t & 31;
   // slots in pixel-index order: slot t holds the t-th smallest index, rank t
   {
-    const unsigned long long raw =
-        t < m0 ? (unsigned long long)(uint32_t)cur_perm(T, d0)[b0 + t] : ~0ull;
-    const unsigned long long srt = bitonic_sort_blocks(raw, SUB_MAX, sbuf);
+    const uint32_t raw = t < m0 ? (uint32_t)cur_perm(T, d0)[b0 + t] : 0xffffffffu;  // idx < 2^31
+    const uint32_t srt = bitonic_sort_blocks32(raw, SUB_MAX, (uint32_t *)sbuf);
     if (t < m0) {
       const int idx = (int)srt;
       sidx[t] = idx;
       srank[t] = t;
+      sslot[t] = t;
       const int32_t *row = T.feat + (size_t)idx * FEAT_STRIDE;
 #pragma unroll
       for (int k = 0; k < NFEAT; k++) sF[t * NFEAT + k] = row[k];
@@ -596,12 +624,18 @@ __global__ void __launch_bounds__(SUB_MAX) k_kd_subtree(KdBuild *trees) {
       dim = sdim[j];
       dmin = sdmin[j];
     }
-    const unsigned long long key =
-        valid ? ((unsigned long long)(uint32_t)(sF[t * NFEAT + dim] - dmin) << 20) |
-                    ((unsigned long long)srank[t] << 10) | (unsigned)t
-              : ~0ull;
-    const unsigned long long sorted = bitonic_sort_blocks(key, B, sbuf);
-    ssorted[t] = sorted;
+    const uint32_t vrel = valid ? (uint32_t)(sF[t * NFEAT + dim] - dmin) : 0u;
+    if (__syncthreads_or(vrel >= (1u << 21)) == 0) {  // valid keys < 2^31: never the sentinel
+      const uint32_t key = valid ? (vrel << 10) | (uint32_t)srank[t] : 0xffffffffu;
+      const uint32_t sorted = bitonic_sort_blocks32(key, B, (uint32_t *)sbuf);
+      ssorted[t] = sorted == 0xffffffffu ? 0 : sslot[sorted & 1023u];
+    } else {
+      const unsigned long long key =
+          valid ? ((unsigned long long)vrel << 20) | ((unsigned long long)srank[t] << 10) | (unsigned)t
+                : ~0ull;
+      const unsigned long long sorted = bitonic_sort_blocks(key, B, sbuf);
+      ssorted[t] = (int)(sorted & 1023u);
+    }
     __syncthreads();
     // move: the first floor(m/2) stay at the front of the block, the others go
     // to the front of its second half
@@ -611,7 +645,7 @@ __global__ void __launch_bounds__(SUB_MAX) k_kd_subtree(KdBuild *trees) {
     int32_t f[NFEAT];
     int pidx = 0, prank = 0;
     if (take) {
-      const int src = (int)(ssorted[j * B + sp] & 1023u);
+      const int src = ssorted[j * B + sp];
 #pragma unroll
       for (int k = 0; k < NFEAT; k++) f[k] = sF[src * NFEAT + k];
       pidx = sidx[src];
@@ -623,6 +657,7 @@ __global__ void __launch_bounds__(SUB_MAX) k_kd_subtree(KdBuild *trees) {
       for (int k = 0; k < NFEAT; k++) sF[t * NFEAT + k] = f[k];
       sidx[t] = pidx;
       srank[t] = prank;
+      sslot[prank] = t;
       if (o == half) {  // the first point of the right child is the split
         const int node = (1 << (d0 + sd)) - 1 + (blockIdx.x << sd) + j;
         T.split_dim[node] = dim;
@@ -650,8 +685,8 @@ __global__ void __launch_bounds__(SUB_MAX) k_kd_subtree(KdBuild *trees) {
 }
 
 static size_t subtree_smem() {
-  return sizeof(unsigned long long) * 3 * SUB_MAX +
-         sizeof(int32_t) * ((size_t)SUB_MAX * NFEAT + 6 * SUB_MAX + 2 * SUB_SD_SMEM_NODES * NFEAT +
+  return sizeof(unsigned long long) * 2 * SUB_MAX +
+         sizeof(int32_t) * ((size_t)SUB_MAX * NFEAT + 8 * SUB_MAX + 2 * SUB_SD_SMEM_NODES * NFEAT +
                             2 * (SUB_MAX / 32) * NFEAT + 2 * SUB_SD_SMEM_NODES);
 }
 

@@ -116,6 +116,34 @@ def test_kdtree_build_arbitrary_features(N, leaf):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("N,leaf", [(1000, 4), (5000, 4)])
+def test_kdtree_build_mixed_key_widths(N, leaf):
+    """Subtree levels whose nodes need 64-bit sort keys (a split-dimension spread
+    >= 2^21) and levels that use 32-bit keys, in one tree. Dimension 0 splits the
+    root into its two value groups exactly; dimension 2 spreads exactly 2^21 in one
+    child only; all others stay below 2^21. With N = 1000 the whole tree is one
+    subtree CTA: levels 0-1 take 64-bit keys (level 1 with one wide and one narrow
+    node), the deeper levels 32-bit keys."""
+    rng = np.random.default_rng(N + 7)
+    feat = np.zeros((N, 28), np.int32)
+    hi = rng.permutation(N)[: N - N // 2]
+    feat[hi, 0] = 2**25
+    lo = np.setdiff1d(np.arange(N), hi)
+    feat[rng.permutation(lo)[: len(lo) // 2], 2] = 2**21
+    feat[:, 1] = rng.integers(0, 2**21, size=N)
+    feat[:, 3:27] = rng.integers(0, 2**19, size=(N, 24))
+    T = ffapi.ff_kdtree_build(tg(feat), leaf)
+    ref = O.kd_build(feat[:, :27], leaf)
+    assert T["D"] == ref["D"]
+    assert np.array_equal(cpu(T["split_dim"]), ref["split_dim"])
+    assert np.array_equal(cpu(T["split_val"]), ref["split_val"])
+    g, o = _leafsets(cpu(T["perm"]), ref["N"], ref["D"]), _leafsets(ref["perm"], ref["N"], ref["D"])
+    for a, b in zip(g, o):
+        assert np.array_equal(a, b)
+    sd = ref["split_dim"]
+    assert sd[0] == 0 and 2 in sd[1:3] and (sd[3:] != 0).all() and (sd[3:] != 2).all()
+
+
 # --------------------------------------------------------------------- A5 -----
 @pytest.mark.parametrize("W,H,n,r,leaf,K", [(40, 30, 1, 3, 4, 0), (128, 96, 8, 8, 8, 0),
                                            (128, 96, 8, 8, 8, 3), (130, 97, 4, 6, 8, 2),
