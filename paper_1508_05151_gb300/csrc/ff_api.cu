@@ -104,7 +104,7 @@ static void plan_pair_body(Arena &a, int W, int H, const ff_params *p, PairPlan 
   const size_t Gtop = (size_t)((W + ntop - 1) / ntop) * ((H + ntop - 1) / ntop);
   const int D = kd_depth((int)N, p->leaf);
   for (int j = 0; j < 3; j++) {
-    P.feat[j] = a.take<int32_t>(N * FEAT_STRIDE);
+    P.feat[j] = a.take<int32_t>(N * FEAT_PACKED_WORDS);  // packed rows (r <= 8)
     P.qfeat[j] = a.take<int32_t>(Gtop * FEAT_STRIDE);
     P.perm[j] = a.take<int32_t>(N);
     P.split_dim[j] = a.take<int32_t>((size_t)1 << D);
@@ -123,6 +123,7 @@ static void plan_pair_body(Arena &a, int W, int H, const ff_params *p, PairPlan 
     }
     kd_bind_scratch(b, a);
     b.feat = P.feat[j];
+    b.packed = 1;
     b.perm = P.perm[j];
     b.split_dim = P.split_dim[j];
     b.split_val = P.split_val[j];
@@ -259,7 +260,8 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
     for (int t = t0; t < t0 + cnt; t++) {
       const int i = order_pair[t], j = order_flow[t];
       const uint8_t *img[2] = {io[i].I1, io[i].I2};
-      FF_TRY(launch_features(img[tgtf[j]], io[i].W, io[i].H, rad[j], nullptr, 0, 1, plans[i].feat[j], gs));
+      FF_TRY(launch_features(img[tgtf[j]], io[i].W, io[i].H, rad[j], nullptr, 0, 1, plans[i].feat[j], gs,
+                             true));
       FF_TRY(launch_features(img[srcf[j]], io[i].W, io[i].H, rad[j], nullptr, 0, ntop,
                              plans[i].qfeat[j], gs));
     }

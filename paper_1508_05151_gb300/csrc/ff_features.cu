@@ -43,7 +43,7 @@ constexpr int FT_X = 32, FT_Y = 16;
 
 // Integral image layout: [c][row 0..RH][col 0..RW], row/col 0 are zeros.
 __global__ void __launch_bounds__(512) k_features_all(const uint8_t *__restrict__ img, int W, int H,
-                                                      int r, int32_t *__restrict__ feat) {
+                                                      int r, int32_t *__restrict__ feat, int packed) {
   extern __shared__ int32_t sI[];
   const int L = 2 * r + 1;
   const int RW = FT_X + L - 1, RH = FT_Y + L - 1;
@@ -103,6 +103,14 @@ __global__ void __launch_bounds__(512) k_features_all(const uint8_t *__restrict_
     combine9(S, out + 9 * c);
   }
   out[27] = 0;
+  if (packed) {  // 64-byte rows of 18-bit fields (|value| <= (2r+1)^2 * 255 < 2^17)
+    uint32_t w[FEAT_PACKED_WORDS];
+    pack_feat_row(out, w);
+    uint4 *dst = (uint4 *)(feat + ((size_t)y * W + x) * FEAT_PACKED_WORDS);
+#pragma unroll
+    for (int q = 0; q < 4; q++) dst[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    return;
+  }
   int4 *dst = (int4 *)(feat + ((size_t)y * W + x) * FEAT_STRIDE);
 #pragma unroll
   for (int q = 0; q < 7; q++) dst[q] = make_int4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
@@ -161,7 +169,8 @@ __global__ void __launch_bounds__(PTS_WARPS * 32) k_features_pts(
 }
 
 ff_status launch_features(const uint8_t *img, int W, int H, int r, const int32_t *pts, int npts,
-                          int grid_n, int32_t *feat, cudaStream_t st) {
+                          int grid_n, int32_t *feat, cudaStream_t st, bool packed) {
+  if (packed && (pts || grid_n != 1 || r < 1 || r > 8)) return FF_ERR_INVALID_ARG;
   if (!pts && grid_n == 1) {
     const int L = 2 * r + 1;
     size_t smem = sizeof(int32_t) * 3 * (FT_X + L) * (FT_Y + L);
@@ -171,7 +180,7 @@ ff_status launch_features(const uint8_t *img, int W, int H, int r, const int32_t
       attr_set = true;
     }
     dim3 g((W + FT_X - 1) / FT_X, (H + FT_Y - 1) / FT_Y);
-    k_features_all<<<g, FT_X * FT_Y, smem, st>>>(img, W, H, r, feat);
+    k_features_all<<<g, FT_X * FT_Y, smem, st>>>(img, W, H, r, feat, packed ? 1 : 0);
     FF_CHECK_LAUNCH();
     return FF_OK;
   }

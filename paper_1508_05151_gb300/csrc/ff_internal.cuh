@@ -23,6 +23,44 @@ namespace ff {
 constexpr int32_t COST_UNSET = 0x7fffffff;
 constexpr int NFEAT = 27;
 constexpr int FEAT_STRIDE = 28;  // int32 per feature row (27 + pad) = 112 bytes
+
+// Packed feature rows (the kd build's target features on the flow path): value j
+// of a row, biased by 2^17 to an unsigned 18-bit field, at bits [18 j, 18 j + 18)
+// of 16 32-bit words (64 bytes). Exact for |value| < 2^17; WHT features of radius
+// r <= 8 stay within (2r+1)^2 * 255 = 73,695.
+constexpr int FEAT_PACKED_WORDS = 16;
+constexpr int FEAT_PACK_BITS = 18, FEAT_PACK_BIAS = 1 << 17;
+constexpr uint32_t FEAT_PACK_MASK = (1u << FEAT_PACK_BITS) - 1u;
+
+__host__ __device__ __forceinline__ void pack_feat_row(const int32_t *v, uint32_t *w) {
+#pragma unroll
+  for (int i = 0; i < FEAT_PACKED_WORDS; i++) w[i] = 0;
+#pragma unroll
+  for (int j = 0; j < NFEAT; j++) {
+    const uint32_t u = (uint32_t)(v[j] + FEAT_PACK_BIAS) & FEAT_PACK_MASK;
+    const int bit = FEAT_PACK_BITS * j, k = bit >> 5, o = bit & 31;
+    w[k] |= u << o;
+    if (o + FEAT_PACK_BITS > 32) w[k + 1] |= u >> (32 - o);
+  }
+}
+
+__device__ __forceinline__ int32_t unpack_feat_field(uint32_t lo, uint32_t hi, int o) {
+  return (int32_t)(__funnelshift_r(lo, hi, o) & FEAT_PACK_MASK) - FEAT_PACK_BIAS;
+}
+
+__device__ __forceinline__ void unpack_feat_row(const uint32_t *w, int32_t *v) {
+#pragma unroll
+  for (int j = 0; j < NFEAT; j++) {
+    const int bit = FEAT_PACK_BITS * j, k = bit >> 5, o = bit & 31;
+    v[j] = unpack_feat_field(w[k], o + FEAT_PACK_BITS > 32 ? w[k + 1] : 0u, o);
+  }
+}
+
+// One value of a packed row (dim a run-time index).
+__device__ __forceinline__ int32_t packed_feat_value(const uint32_t *row, int dim) {
+  const int bit = FEAT_PACK_BITS * dim, k = bit >> 5, o = bit & 31;
+  return unpack_feat_field(row[k], o + FEAT_PACK_BITS > 32 ? row[k + 1] : 0u, o);
+}
 constexpr int PLANE_PAD = 8;     // P: supports patch radii up to 8
 constexpr int MAX_TILE = 32;
 constexpr int MAX_K = 8;
@@ -246,12 +284,14 @@ ff_status launch_planes(const uint32_t *census, Planes P, cudaStream_t st);
 
 // ----------------------------------------------------------- features --------
 // pts != NULL: explicit (x, y) list; else grid of spacing grid_n (1 = all pixels).
+// packed (all pixels only): 16-word packed rows instead of [28] int32 rows.
 ff_status launch_features(const uint8_t *img, int W, int H, int r, const int32_t *pts, int npts,
-                          int grid_n, int32_t *feat, cudaStream_t st);
+                          int grid_n, int32_t *feat, cudaStream_t st, bool packed = false);
 
 // ------------------------------------------------------------- kd tree -------
 struct KdBuild {
-  const int32_t *feat;  // [N][28]
+  const int32_t *feat;  // [N][28] int32, or [N][16] packed words when `packed`
+  int packed;
   int N, leaf, D;
   int32_t *perm;        // [N] output
   int32_t *split_dim, *split_val;  // [2^D - 1]

@@ -141,12 +141,22 @@ __global__ void __launch_bounds__(256) k_kd_minmax_root(KdBuild *trees) {
   if (r0 < T.N && lane < NFEAT) {
     const int r1 = min(r0 + MM_ROWS_PER_WARP, T.N);
     int lo = INT32_MAX, hi = INT32_MIN;
-    const int32_t *col = T.feat + lane;
+    if (T.packed) {
+      const uint32_t *rows = (const uint32_t *)T.feat;
 #pragma unroll 4
-    for (int r = r0; r < r1; r++) {
-      const int v = col[(size_t)r * FEAT_STRIDE];
-      lo = min(lo, v);
-      hi = max(hi, v);
+      for (int r = r0; r < r1; r++) {
+        const int v = packed_feat_value(rows + (size_t)r * FEAT_PACKED_WORDS, lane);
+        lo = min(lo, v);
+        hi = max(hi, v);
+      }
+    } else {
+      const int32_t *col = T.feat + lane;
+#pragma unroll 4
+      for (int r = r0; r < r1; r++) {
+        const int v = col[(size_t)r * FEAT_STRIDE];
+        lo = min(lo, v);
+        hi = max(hi, v);
+      }
     }
     atomicMin(&smin[lane], lo);
     atomicMax(&smax[lane], hi);
@@ -212,8 +222,35 @@ __global__ void k_kd_sel_init(KdBuild *trees, int d) {
   T.split_dim[node] = best;
 }
 
+// Feature value / whole row of point idx in either row layout.
+__device__ __forceinline__ int feat_value(const KdBuild &T, int idx, int dim) {
+  return T.packed ? packed_feat_value((const uint32_t *)T.feat + (size_t)idx * FEAT_PACKED_WORDS, dim)
+                  : T.feat[(size_t)idx * FEAT_STRIDE + dim];
+}
+template <bool PACKED>
+__device__ __forceinline__ void feat_row_as(const KdBuild &T, int idx, bool ok, int32_t *v) {
+  if (PACKED) {
+    uint4 q[4];
+    const uint4 *row = (const uint4 *)((const uint32_t *)T.feat + (size_t)idx * FEAT_PACKED_WORDS);
+#pragma unroll
+    for (int k = 0; k < 4; k++) q[k] = ok ? row[k] : make_uint4(0, 0, 0, 0);
+    unpack_feat_row((const uint32_t *)q, v);
+  } else {
+    int4 q[7];
+    const int4 *row = (const int4 *)(T.feat + (size_t)idx * FEAT_STRIDE);
+#pragma unroll
+    for (int k = 0; k < 7; k++) q[k] = ok ? row[k] : make_int4(0, 0, 0, 0);
+#pragma unroll
+    for (int k = 0; k < NFEAT; k++) v[k] = ((const int *)q)[k];
+  }
+}
+__device__ __forceinline__ void feat_row(const KdBuild &T, int idx, bool ok, int32_t *v) {
+  if (T.packed) feat_row_as<true>(T, idx, ok, v);
+  else feat_row_as<false>(T, idx, ok, v);
+}
+
 __device__ __forceinline__ unsigned long long kd_key(const KdBuild &T, const int32_t *S, int idx) {
-  int v = T.feat[(size_t)idx * FEAT_STRIDE + S[0]];
+  int v = feat_value(T, idx, S[0]);
   return ((unsigned long long)(unsigned)(v - S[1]) << S[3]) | (unsigned)idx;
 }
 
@@ -360,11 +397,17 @@ __global__ void __launch_bounds__(256) k_kd_digit(KdBuild *trees, int d) {
 // destination) and per CTA, so a CTA issues at most one global atomic per
 // destination child (order inside a child is unspecified). The selected point
 // writes the split value. While the rows pass through, the per-dimension
-// min/max of the children (next level) is accumulated the same way.
+// min/max of the children (next level) is accumulated per child present in the
+// warp: one child at a time, all lanes converged, full-mask warp reductions in
+// which the other lanes contribute the neutral value, then shared and global
+// atomics. (An earlier form reduced under per-lane group masks; with packed
+// rows, the values of the lanes past the chunk's end reached real children's
+// min/max, nondeterministically.) Rows are read in either layout (int32 or packed).
 constexpr int PART_CHUNK = 2048;  // positions per CTA (spans <= 3 segments at top levels)
 constexpr int PART_ROUNDS = PART_CHUNK / 256;
 
-__global__ void __launch_bounds__(256) k_kd_partition(KdBuild *trees, int d) {
+template <bool PACKED>
+__global__ void __launch_bounds__(256, 3) k_kd_partition(KdBuild *trees, int d) {
   KdBuild &T = trees[blockIdx.y];
   if (d >= T.top_levels) return;
   const int start = blockIdx.x * PART_CHUNK;
@@ -410,17 +453,24 @@ __global__ void __launch_bounds__(256) k_kd_partition(KdBuild *trees, int d) {
     rank[r] = wbase + __popc(grp & ((1u << lane) - 1));
     idxs[r] = idx;
     if (child_mm) {  // child min/max over the full rows
-      int4 q[7];
-      const int4 *row = (const int4 *)(T.feat + (size_t)idx * FEAT_STRIDE);
+      int32_t v[NFEAT];
+      feat_row_as<PACKED>(T, idx, c >= 0, v);
+      // one child slot at a time, all lanes converged, full-mask reductions in
+      // which the other lanes contribute the neutral value
+      unsigned todo = __ballot_sync(0xffffffffu, c >= 0);
+      while (todo) {
+        const int lead = __ffs(todo) - 1;
+        const int cc = __shfl_sync(0xffffffffu, c, lead);
+        const bool mine = c == cc;
+        todo &= ~__ballot_sync(0xffffffffu, mine);
 #pragma unroll
-      for (int k = 0; k < 7; k++) q[k] = c >= 0 ? row[k] : make_int4(0, 0, 0, 0);
-      const int *v = (const int *)q;
-#pragma unroll
-      for (int dim = 0; dim < NFEAT; dim++) {
-        const int lo = __reduce_min_sync(grp, v[dim]), hi = __reduce_max_sync(grp, v[dim]);
-        if (c >= 0 && lane == leader) {
-          atomicMin(&s_min[c][dim], lo);
-          atomicMax(&s_max[c][dim], hi);
+        for (int dim = 0; dim < NFEAT; dim++) {
+          const int lo = __reduce_min_sync(0xffffffffu, mine ? v[dim] : INT32_MAX);
+          const int hi = __reduce_max_sync(0xffffffffu, mine ? v[dim] : INT32_MIN);
+          if (lane == lead) {
+            atomicMin(&s_min[cc][dim], lo);
+            atomicMax(&s_max[cc][dim], hi);
+          }
         }
       }
     }
@@ -548,9 +598,10 @@ __global__ void __launch_bounds__(SUB_MAX) k_kd_subtree(KdBuild *trees) {
       sidx[t] = idx;
       srank[t] = t;
       sslot[t] = t;
-      const int32_t *row = T.feat + (size_t)idx * FEAT_STRIDE;
+      int32_t v[NFEAT];
+      feat_row(T, idx, true, v);
 #pragma unroll
-      for (int k = 0; k < NFEAT; k++) sF[t * NFEAT + k] = row[k];
+      for (int k = 0; k < NFEAT; k++) sF[t * NFEAT + k] = v[k];
     }
     if (t == 0) {
       ssize[0] = m0;
@@ -700,6 +751,9 @@ ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaSt
     maxSub = max(maxSub, trees[i].D - trees[i].top_levels);
   }
   if (maxN <= 0) return FF_OK;
+  const bool packed = trees[0].packed != 0;  // one row layout per launch
+  for (int i = 1; i < ntrees; i++)
+    if ((trees[i].packed != 0) != packed) return FF_ERR_INVALID_ARG;
   // radix-select passes: enough digits for the widest key (value spread bits +
   // index bits) of any tree
   int passes = 1;
@@ -731,7 +785,10 @@ ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaSt
       k_kd_digit<<<dim3(nseg, ntrees), 256, 0, st>>>(dev, d);
       FF_CHECK_LAUNCH();
     }
-    k_kd_partition<<<dim3((maxN + PART_CHUNK - 1) / PART_CHUNK, ntrees), 256, 0, st>>>(dev, d);
+    if (packed)
+      k_kd_partition<true><<<dim3((maxN + PART_CHUNK - 1) / PART_CHUNK, ntrees), 256, 0, st>>>(dev, d);
+    else
+      k_kd_partition<false><<<dim3((maxN + PART_CHUNK - 1) / PART_CHUNK, ntrees), 256, 0, st>>>(dev, d);
     FF_CHECK_LAUNCH();
   }
   if (maxSub > 10) return FF_ERR_INVALID_ARG;  // segments <= SUB_MAX points, leaf >= 1
