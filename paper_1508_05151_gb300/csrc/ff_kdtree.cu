@@ -104,10 +104,21 @@ __global__ void k_kd_seg_off(KdBuild *trees, int ntrees) {
   }
 }
 
+// Identity permutation; zero radix histograms (each digit pass clears the bins it
+// used, so this is their only reset) and the root's min/max sentinels.
 __global__ void k_kd_init_perm(KdBuild *trees) {
   KdBuild &T = trees[blockIdx.y];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.N; i += gridDim.x * blockDim.x)
-    T.perm[i] = i;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (int i = tid; i < T.N; i += nth) T.perm[i] = i;
+  if (T.top_levels > 0) {
+    const size_t nbins = ((size_t)1 << (T.top_levels - 1)) * NBINS;
+    for (size_t i = tid; i < nbins; i += nth) T.hist[i] = 0;
+    for (int i = tid; i < NFEAT; i += nth) {
+      int32_t *m = mm_at(T, 0, 0) + i * 2;
+      m[0] = INT32_MAX;
+      m[1] = INT32_MIN;
+    }
+  }
 }
 
 // Segment containing position pos at depth d (binary search in seg_off).
@@ -168,27 +179,6 @@ __global__ void __launch_bounds__(256) k_kd_minmax_root(KdBuild *trees) {
   }
 }
 
-__global__ void k_kd_level_reset(KdBuild *trees, int d) {
-  KdBuild &T = trees[blockIdx.y];
-  if (d >= T.top_levels) return;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  for (int i = tid; i < (1 << d) * NBINS; i += nth) T.hist[i] = 0;
-  for (int i = tid; i < (1 << d) * 2; i += nth) T.cnt[i] = 0;
-  const int lv = d + 1 < T.top_levels ? d + 1 : -1;
-  if (lv >= 0)
-    for (int i = tid; i < (1 << lv) * NFEAT; i += nth) {
-      int32_t *m = mm_at(T, lv, i / NFEAT) + (i % NFEAT) * 2;
-      m[0] = INT32_MAX;
-      m[1] = INT32_MIN;
-    }
-  if (d == 0)
-    for (int i = tid; i < NFEAT; i += nth) {
-      int32_t *m = mm_at(T, 0, 0) + i * 2;
-      m[0] = INT32_MAX;
-      m[1] = INT32_MIN;
-    }
-}
-
 // sel state per segment: [0] dim, [1] vmin, [2] key bits B, [3] ibits,
 // [4] remaining rank k, [5] prefix lo, [6] prefix hi, [7] bits consumed
 __global__ void k_kd_sel_init(KdBuild *trees, int d) {
@@ -220,6 +210,19 @@ __global__ void k_kd_sel_init(KdBuild *trees, int d) {
   S[7] = 0;
   int node = (1 << d) - 1 + s;
   T.split_dim[node] = best;
+  // what this segment's partition needs: zero counters and the min/max sentinels
+  // of its two children (the other ping-pong half, read last at level d - 1)
+  T.cnt[2 * s] = 0;
+  T.cnt[2 * s + 1] = 0;
+  if (d + 1 < T.top_levels)
+    for (int c = 0; c < 2; c++) {
+      int32_t *m = mm_at(T, d + 1, 2 * s + c);
+#pragma unroll 9
+      for (int k = 0; k < NFEAT; k++) {
+        m[2 * k] = INT32_MAX;
+        m[2 * k + 1] = INT32_MIN;
+      }
+    }
 }
 
 // Feature value / whole row of point idx in either row layout.
@@ -770,8 +773,6 @@ ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaSt
   FF_CHECK_LAUNCH();
   for (int d = 0; d < maxT; d++) {
     const int nseg = 1 << d;
-    k_kd_level_reset<<<dim3(min((nseg * NBINS + B - 1) / B, 1024), ntrees), B, 0, st>>>(dev, d);
-    FF_CHECK_LAUNCH();
     if (d == 0) {
       const int rows_per_cta = 8 * MM_ROWS_PER_WARP;
       k_kd_minmax_root<<<dim3((maxN + rows_per_cta - 1) / rows_per_cta, ntrees), 256, 0, st>>>(dev);
