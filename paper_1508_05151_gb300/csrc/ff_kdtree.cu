@@ -181,47 +181,55 @@ __global__ void __launch_bounds__(256) k_kd_minmax_root(KdBuild *trees) {
 
 // sel state per segment: [0] dim, [1] vmin, [2] key bits B, [3] ibits,
 // [4] remaining rank k, [5] prefix lo, [6] prefix hi, [7] bits consumed
-__global__ void k_kd_sel_init(KdBuild *trees, int d) {
+// One warp per segment: lane k reads dimension k's min/max; the split dimension
+// (largest max - min, lowest dimension on ties) by one warp max over the key
+// (spread << 5) | (31 - lane).
+constexpr int SEL_WARPS = 4;
+__global__ void __launch_bounds__(SEL_WARPS * 32) k_kd_sel_init(KdBuild *trees, int d) {
   KdBuild &T = trees[blockIdx.y];
   if (d >= T.top_levels) return;
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= (1 << d)) return;
-  const int32_t *off = T.seg_off + seg_base(d);
-  int m = off[s + 1] - off[s];
-  int best = 0;
-  long long bs = -1;
-  for (int dim = 0; dim < NFEAT; dim++) {
-    long long sp = (long long)mm_at(T, d, s)[dim * 2 + 1] - mm_at(T, d, s)[dim * 2];
-    if (sp > bs) {
-      bs = sp;
-      best = dim;
-    }
+  const int lane = threadIdx.x & 31;
+  const int s = blockIdx.x * SEL_WARPS + (threadIdx.x >> 5);
+  if (s >= (1 << d)) return;  // whole warp
+  const int32_t *mm = mm_at(T, d, s);
+  long long key = -1;
+  if (lane < NFEAT) {
+    const long long sp = (long long)mm[lane * 2 + 1] - mm[lane * 2];  // < 2^32
+    if (sp >= 0) key = (sp << 5) | (31 - lane);
   }
-  int vbits = bits_for(bs), ibits = bits_for(T.N - 1);
-  if (ibits < 1) ibits = 1;
-  int32_t *S = T.sel + s * 8;
-  S[0] = best;
-  S[1] = mm_at(T, d, s)[best * 2];
-  S[2] = vbits + ibits;
-  S[3] = ibits;
-  S[4] = m / 2;
-  S[5] = 0;
-  S[6] = 0;
-  S[7] = 0;
-  int node = (1 << d) - 1 + s;
-  T.split_dim[node] = best;
-  // what this segment's partition needs: zero counters and the min/max sentinels
-  // of its two children (the other ping-pong half, read last at level d - 1)
-  T.cnt[2 * s] = 0;
-  T.cnt[2 * s + 1] = 0;
-  if (d + 1 < T.top_levels)
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const long long y = __shfl_xor_sync(0xffffffffu, key, o);
+    key = y > key ? y : key;
+  }
+  const int best = key >= 0 ? 31 - (int)(key & 31) : 0;
+  const long long bs = key >= 0 ? key >> 5 : -1;
+  if (lane == 0) {
+    const int32_t *off = T.seg_off + seg_base(d);
+    const int m = off[s + 1] - off[s];
+    int vbits = bits_for(bs), ibits = bits_for(T.N - 1);
+    if (ibits < 1) ibits = 1;
+    int32_t *S = T.sel + s * 8;
+    S[0] = best;
+    S[1] = mm[best * 2];
+    S[2] = vbits + ibits;
+    S[3] = ibits;
+    S[4] = m / 2;
+    S[5] = 0;
+    S[6] = 0;
+    S[7] = 0;
+    T.split_dim[(1 << d) - 1 + s] = best;
+    // what this segment's partition needs: zero counters (and below, the min/max
+    // sentinels of its two children: the other ping-pong half, read last at
+    // level d - 1)
+    T.cnt[2 * s] = 0;
+    T.cnt[2 * s + 1] = 0;
+  }
+  if (d + 1 < T.top_levels && lane < NFEAT)
     for (int c = 0; c < 2; c++) {
       int32_t *m = mm_at(T, d + 1, 2 * s + c);
-#pragma unroll 9
-      for (int k = 0; k < NFEAT; k++) {
-        m[2 * k] = INT32_MAX;
-        m[2 * k + 1] = INT32_MIN;
-      }
+      m[2 * lane] = INT32_MAX;
+      m[2 * lane + 1] = INT32_MIN;
     }
 }
 
@@ -778,7 +786,7 @@ ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaSt
       k_kd_minmax_root<<<dim3((maxN + rows_per_cta - 1) / rows_per_cta, ntrees), 256, 0, st>>>(dev);
       FF_CHECK_LAUNCH();
     }
-    k_kd_sel_init<<<dim3((nseg + 127) / 128, ntrees), 128, 0, st>>>(dev, d);
+    k_kd_sel_init<<<dim3((nseg + SEL_WARPS - 1) / SEL_WARPS, ntrees), SEL_WARPS * 32, 0, st>>>(dev, d);
     FF_CHECK_LAUNCH();
     for (int pass = 0; pass < passes; pass++) {
       k_kd_hist<<<dim3((maxN + HIST_CHUNK - 1) / HIST_CHUNK, ntrees), 256, 0, st>>>(dev, d);
