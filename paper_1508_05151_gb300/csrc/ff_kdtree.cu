@@ -339,24 +339,39 @@ __global__ void __launch_bounds__(256) k_kd_digit(KdBuild *trees, int d) {
   if (used >= B) return;
   int hi = B - used, lo = max(hi - DIGIT, 0), nb = 1 << (hi - lo);
   __shared__ uint32_t part[256];
-  __shared__ int found_bin, found_before;
-  // each thread sums a run of NBINS / 256 consecutive bins
-  const int per = NBINS / 256;
+  __shared__ int found_bin, found_before, s_tt;
+  __shared__ uint32_t s_before;
+  // each thread holds a run of NBINS / 256 consecutive bins in registers (four
+  // 16-byte loads) and sums it
+  constexpr int per = NBINS / 256;
+  uint32_t v[per];
+  {
+    const uint4 *h4 = (const uint4 *)(h + threadIdx.x * per);
+#pragma unroll
+    for (int q = 0; q < per / 4; q++) {
+      const uint4 x = h4[q];
+      v[4 * q] = x.x;
+      v[4 * q + 1] = x.y;
+      v[4 * q + 2] = x.z;
+      v[4 * q + 3] = x.w;
+    }
+  }
   uint32_t mine = 0;
+#pragma unroll
   for (int i = 0; i < per; i++) {
-    int b = threadIdx.x * per + i;
-    mine += (b < nb) ? h[b] : 0;
+    if ((int)threadIdx.x * per + i >= nb) v[i] = 0;
+    mine += v[i];
   }
   part[threadIdx.x] = mine;
   __syncthreads();
+  const uint32_t k = (uint32_t)S[4];
   // the run holding rank k: inclusive prefix sums of the 256 runs by warp 0 (8
-  // runs per lane), then the bin inside that run by lane 0
+  // runs per lane)
   if (threadIdx.x < 32) {
-    const uint32_t k = (uint32_t)S[4];
     const int lane = threadIdx.x;
-    uint32_t v[8], sum = 0;
+    uint32_t w[8], sum = 0;
 #pragma unroll
-    for (int i = 0; i < 8; i++) sum += (v[i] = part[lane * 8 + i]);
+    for (int i = 0; i < 8; i++) sum += (w[i] = part[lane * 8 + i]);
     uint32_t incl = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -368,31 +383,53 @@ __global__ void __launch_bounds__(256) k_kd_digit(KdBuild *trees, int d) {
     uint32_t before = 0;
 #pragma unroll
     for (int i = 0; i < 8; i++) {
-      if (t < 0 && acc + v[i] > k) {
+      if (t < 0 && acc + w[i] > k) {
         t = lane * 8 + i;
         before = acc;
       }
-      acc += v[i];
+      acc += w[i];
     }
     const unsigned hit = __ballot_sync(0xffffffffu, t >= 0);
     const int src = hit ? __ffs(hit) - 1 : 31;
     int tt = __shfl_sync(0xffffffffu, t, src);
     before = __shfl_sync(0xffffffffu, before, src);
-    const uint32_t last = __shfl_sync(0xffffffffu, v[7], 31), total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t last = __shfl_sync(0xffffffffu, w[7], 31), total = __shfl_sync(0xffffffffu, incl, 31);
     if (!hit) {  // rank beyond the total: the last run, as a sequential scan would stop
       tt = 255;
       before = total - last;
     }
     if (lane == 0) {
-      int b = tt * per;
-      uint32_t a2 = before;
-      while (b < tt * per + per - 1 && a2 + h[b] <= k) a2 += h[b++];
-      found_bin = b;
-      found_before = (int)a2;
+      s_tt = tt;
+      s_before = before;
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < NBINS; i += blockDim.x) h[i] = 0;
+  // the run's owner finds the bin inside it from its registers: advance while the
+  // bin still lies before rank k (at most per - 1 bins)
+  if ((int)threadIdx.x == s_tt) {
+    uint32_t a2 = s_before;
+    int at = per - 1;
+    bool stop = false;
+#pragma unroll
+    for (int i = 0; i < per - 1; i++) {
+      if (!stop) {
+        if (a2 + v[i] <= k) {
+          a2 += v[i];
+        } else {
+          at = i;
+          stop = true;
+        }
+      }
+    }
+    found_bin = s_tt * per + at;
+    found_before = (int)a2;
+  }
+  __syncthreads();
+  {  // each thread clears the run it read
+    uint4 *h4 = (uint4 *)(h + threadIdx.x * per);
+#pragma unroll
+    for (int q = 0; q < per / 4; q++) h4[q] = make_uint4(0, 0, 0, 0);
+  }
   if (threadIdx.x == 0) {
     unsigned long long pre = ((unsigned long long)(unsigned)S[6] << 32) | (unsigned)S[5];
     pre = (pre << (hi - lo)) | (unsigned)found_bin;
