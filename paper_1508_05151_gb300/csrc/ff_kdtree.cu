@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(256) k_kd_digit(KdBuild *trees, int d) {
 // atomics. (An earlier form reduced under per-lane group masks; with packed
 // rows, the values of the lanes past the chunk's end reached real children's
 // min/max, nondeterministically.) Rows are read in either layout (int32 or packed).
-constexpr int PART_CHUNK = 2048;  // positions per CTA (spans <= 3 segments at top levels)
+constexpr int PART_CHUNK = 1024;  // positions per CTA (spans <= 2 segments at top levels)
 constexpr int PART_ROUNDS = PART_CHUNK / 256;
 
 template <bool PACKED>
