@@ -265,7 +265,7 @@ __device__ __forceinline__ unsigned long long kd_key(const KdBuild &T, const int
   return ((unsigned long long)(unsigned)(v - S[1]) << S[3]) | (unsigned)idx;
 }
 
-constexpr int HIST_CHUNK = 2048;  // positions per CTA (segments > SUB_MAX: spans <= 3)
+constexpr int HIST_CHUNK = 1024;  // positions per CTA (segments > SUB_MAX: spans <= 2)
 constexpr int CHUNK_SEGS = 4;     // segment slots per chunk
 
 // The segments a chunk of positions touches (top levels: at most CHUNK_SEGS):
