@@ -167,8 +167,8 @@ struct PairIO {
 
 // The whole path for np pairs (Fig. 2). Per-image kernels (smoothing, census,
 // features, filtering) run per pair; the kd builds, kd queries and every search
-// level take the three flows of all pairs in the same launches, problems of
-// one patch radius per launch, the two radii concurrently.
+// level of one flow (forward r, backward r, backward r2) take that flow's problems
+// of all pairs in the same launches, each flow on a stream of its own.
 static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *ws, size_t ws_bytes,
                            cudaStream_t st) {
   std::vector<int> Ws(np), Hs(np);
