@@ -215,7 +215,9 @@ ff_status ff_flow_fields(const uint8_t *I1, const uint8_t *I2, int W, int H, con
 /* Batched form (not in the paper): many pairs, possibly of different sizes, in
  * one call. Each pair's results equal those of ff_flow_fields on that pair. The
  * per-image steps run per pair; the kd builds, kd queries and every propagation
- * pass take the three flows of all pairs in the same launches. The ff_pair array
+ * pass of one flow take that flow's problems of all pairs in the same launches,
+ * the three flows on streams of their own (joined back into `stream` before the
+ * call's last work, so the call stays stream-ordered). The ff_pair array
  * is host memory; its buffers are device memory as in ff_flow_fields. */
 #define FF_MAX_BATCH 256
 typedef struct ff_pair {
