@@ -8,11 +8,15 @@
 // first right point. Segments of a level are contiguous in `perm`, obtained by
 // halving [0, N) (left takes floor(m/2)).
 //
+// Feature rows come as int32 [28] (the public build) or packed 64-byte rows of
+// 18-bit fields (the flow path; see ff_internal.cuh).
+//
 // Build, level by level:
 //   top levels (segments > SUB_MAX points): multi-CTA passes per level
 //     minmax   per-dim min/max of the root (rows in memory order); deeper
 //              levels get their children's min/max from the partition
-//     sel_init dimension choice, key width
+//     sel_init dimension choice, key width (a warp per segment); it also zeroes
+//              the segment's partition counters and its children's min/max
 //     passes x (hist, digit)  radix select of the rank-floor(m/2) key, 12-bit digits
 //                        (as many passes as the widest key needs),
 //                        key = (value - min) << ibits | pixel index (unique);
