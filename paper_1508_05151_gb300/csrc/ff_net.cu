@@ -17,8 +17,9 @@
 //   wgrad     dW[n][k]   = sum_m G[m][n] A[m][k]   (reduction over pixels, split across CTAs)
 // where A is the im2col view of the layer input and G the gradient at the
 // pre-activation. A CTA of 128 threads computes a 128 x 64 tile: the threads
-// stage both operands 16 deep in shared memory, one thread issues the MMA, an
-// mbarrier reports its completion, and the epilogue reads the accumulator back
+// stage both operands in shared memory (16 deep for the convolutions; 32 pixels,
+// two MMAs, per stage for the weight gradient), one thread issues the MMAs, an
+// mbarrier reports their completion, and the epilogue reads the accumulator back
 // with tcgen05.ld. Waits are bounded; a wait that runs out sets the device status
 // word at the start of the workspace.
 #include <cuda_bf16.h>
