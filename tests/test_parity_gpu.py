@@ -360,3 +360,51 @@ def test_forward_flow_levels_composition():
         else:
             flow, cost, _ = O.search_level(C1, C2, n, r, flow_coarse=flow, n_rs=bud[i], **kw)
     assert np.array_equal(got, flow)
+
+
+# ------------------------------------------- full sizes of the other workloads --
+def test_flow_fields_with_proposals_kitti_full_size():
+    """The learned-proposal form at its workload's full size: a 1242x375 KITTI-shaped
+    pair with K = 4 proposals per coarsest grid point through the whole path,
+    bit-exact against the oracle given the same proposals. Two proposals are the
+    rounded ground-truth flow (one jittered by a few pixels), so they often win the
+    data term; two are random within +-300 px, so targets are clamped."""
+    p = synth.pair_for_config(5, 11)
+    H, W = p["I1"].shape[:2]
+    Gx, Gy = O.grid(W, H, 8)
+    rng = np.random.default_rng(12)
+    gt = np.rint(p["flow"][::8, ::8]).astype(np.int64)[:Gy, :Gx]
+    prop = np.empty((Gy, Gx, 4, 2), np.int64)
+    prop[:, :, 0] = gt
+    prop[:, :, 1] = gt + rng.integers(-3, 4, size=(Gy, Gx, 2))
+    prop[:, :, 2:] = rng.integers(-300, 301, size=(Gy, Gx, 2, 2))
+    prop = prop.astype(np.int16)
+    params = dict(K=4)
+    out = ffapi.FlowFields(W, H, params).run(tg(p["I1"]), tg(p["I2"]), tg(prop))
+    ref = O.flow_fields(p["I1"], p["I2"], params=params, proposals=prop.astype(np.int32),
+                        threads=3)
+    _compare(out, ref)
+
+
+def test_batch_64_mixed_full_size_sampled():
+    """The benchmark's 64-pair mixed batch (16 each of 640x480, 584x388, 1024x436,
+    1242x375) as one graph replay: the first pair of each size bit-exact against the
+    oracle, the other 15 copies of each size equal to it."""
+    sizes, frames, pairs = [], [], []
+    for k, (W, H) in enumerate(synth.BATCH_SIZES):
+        p = synth.pair_for_config(3, 500 + k, (W, H))
+        pairs.append(p)
+        a, b = tg(p["I1"]), tg(p["I2"])
+        for _ in range(16):
+            sizes.append((W, H))
+            frames.append((a, b))
+    batch = ffapi.FlowFieldsBatch(sizes, graph=True)
+    outs = batch.run(frames)
+    torch.cuda.synchronize()
+    for k in range(4):
+        first = outs[16 * k]
+        _compare(first, O.flow_fields(pairs[k]["I1"], pairs[k]["I2"], threads=3))
+        for j in range(1, 16):
+            o = outs[16 * k + j]
+            for key in ("flows", "valid", "err_sum", "mask", "n_sparse"):
+                assert torch.equal(o[key], first[key]), (k, j, key)
