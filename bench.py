@@ -126,7 +126,7 @@ def peaks():
 
 # DRAM traffic of the pass kernels per launch, from one ncu capture of this
 # benchmark's pair (dram__bytes_read.sum + dram__bytes_write.sum averaged over 32
-# consecutive pass launches; profiles/flow_fields_1024x436_launch_list.md).
+# consecutive pass launches).
 # It is reported only while the kernel sources hash to what was profiled.
 PASS_TRAFFIC = {"bytes_per_launch": 4664360,
                 "sources_sha256": "e1972e45274fac1a20251f4da8817f717fdccf09f6e39efd70d94964526acb94"}
@@ -219,17 +219,14 @@ def _time_steps(run, steps, flush, stream):
 
 
 def batch_measure(dev, params, reps=3):
-    """Mixed-size batch: 16 pairs each of 640x480, 584x388, 1024x436, 1242x375
-    (one synthetic pair per size, repeated), one CUDA graph per batch."""
+    """Mixed-size batch: 16 pairs each of 640x480, 584x388, 1024x436, 1242x375,
+    every pair generated from its own seed, one CUDA graph per batch."""
     import torch
     from paper_1508_05151_gb300 import ffapi, synth, tune
     sizes, frames = [], []
-    for k, (W, H) in enumerate(synth.BATCH_SIZES):
-        p = synth.pair_for_config(3, 500 + k, (W, H))
-        a, b = torch.from_numpy(p["I1"]).to(dev), torch.from_numpy(p["I2"]).to(dev)
-        for _ in range(16):
-            sizes.append((W, H))
-            frames.append((a, b))
+    for (W, H), p in synth.mixed_batch():
+        sizes.append((W, H))
+        frames.append((torch.from_numpy(p["I1"]).to(dev), torch.from_numpy(p["I2"]).to(dev)))
     tuned = tune.tune(sizes, params, frames=frames, reps=2, use_cache=False)
     batch = ffapi.FlowFieldsBatch(sizes, params, dev, graph=True)
     batch.run(frames)

@@ -6,6 +6,8 @@
 // radius, seeding and passes take an array of problems and index it with
 // blockIdx.y, so one pair costs the same number of launches as one flow.
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -42,7 +44,7 @@ void prof_end(cudaStream_t s) {
 // ------------------------------------------------------------ checks --------
 static bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-static ff_status check_params(const ff_params *p) {
+ff_status check_params(const ff_params *p) {
   if (!p) return FF_ERR_INVALID_ARG;
   if (p->k < 0 || p->k > 4) return FF_ERR_INVALID_ARG;
   if (p->r < 1 || p->r > PLANE_PAD || p->r2 < 1 || p->r2 > PLANE_PAD) return FF_ERR_INVALID_ARG;
@@ -54,9 +56,27 @@ static ff_status check_params(const ff_params *p) {
   return FF_OK;
 }
 
-static ff_status check_shape(int W, int H) {
+ff_status check_shape(int W, int H) {
   if (W < 1 || H < 1 || W > 16384 || H > 16384) return FF_ERR_SHAPE;
   if ((long long)W * H > (1ll << 24)) return FF_ERR_SHAPE;
+  return FF_OK;
+}
+
+static std::mutex g_attr_mu;
+static std::map<std::pair<int, const void *>, size_t> g_attr;
+
+ff_status smem_opt_in(const void *func, size_t bytes) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return FF_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  size_t &have = g_attr[{dev, func}];
+  if (bytes <= have) return FF_OK;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+      cudaSuccess) {
+    (void)cudaGetLastError();
+    return FF_ERR_CUDA;
+  }
+  have = bytes;
   return FF_OK;
 }
 
@@ -248,6 +268,7 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
     Q.K = (j == 0) ? p->K : 0;
     Q.flow = P.fa[j];
     Q.cost = P.ca[j];
+    Q.status = (DeviceStatus *)ws;
     cur[t] = P.fa[j];
     oth[t] = P.fb[j];
     ccur[t] = P.ca[j];
@@ -532,6 +553,7 @@ ff_status ff_kdtree_init(const int32_t *perm, const int32_t *split_dim, const in
   q.K = K;
   q.flow = (uint32_t *)flow;
   q.cost = cost;
+  q.status = (DeviceStatus *)ws;
   return launch_kd_query(&q, L.dq, 1, st);
 }
 

@@ -174,11 +174,7 @@ ff_status launch_features(const uint8_t *img, int W, int H, int r, const int32_t
   if (!pts && grid_n == 1) {
     const int L = 2 * r + 1;
     size_t smem = sizeof(int32_t) * 3 * (FT_X + L) * (FT_Y + L);
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaFuncSetAttribute(k_features_all, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-      attr_set = true;
-    }
+    FF_TRY(smem_opt_in((const void *)k_features_all, smem));
     dim3 g((W + FT_X - 1) / FT_X, (H + FT_Y - 1) / FT_Y);
     k_features_all<<<g, FT_X * FT_Y, smem, st>>>(img, W, H, r, feat, packed ? 1 : 0);
     FF_CHECK_LAUNCH();

@@ -245,6 +245,18 @@ struct Arena {
   bool fits() const { return base == nullptr || off <= cap; }
 };
 
+// ------------------------------------------------------- host-side checks ---
+// Parameter and image-shape checks shared by every entry point.
+ff_status check_params(const ff_params *p);
+ff_status check_shape(int W, int H);
+
+// Raises `func`'s dynamic shared-memory limit to at least `bytes` on the current
+// device. The setting is per device and per kernel; it is remembered per
+// (device, kernel) under a lock, so concurrent first calls from several host
+// threads, or calls on several devices, each see the opt-in done before their
+// launch. Returns FF_ERR_CUDA when the runtime refuses it.
+ff_status smem_opt_in(const void *func, size_t bytes);
+
 // ---------------------------------------------------- execution parameters ---
 // Launch shapes that do not change results (set by the autotuner).
 const ff_exec_params &exec_params();
@@ -323,6 +335,7 @@ struct KdQuery {
   int K;
   uint32_t *flow;  // [G]
   int32_t *cost;   // [G]
+  DeviceStatus *status;  // DEV_ERR_BOUNDS: a split dimension or leaf entry out of range
 };
 ff_status launch_kd_query(const KdQuery *q, KdQuery *dev_desc, int nq, cudaStream_t st);
 

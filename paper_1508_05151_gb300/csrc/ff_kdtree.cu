@@ -843,13 +843,7 @@ ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaSt
   }
   if (maxSub > 10) return FF_ERR_INVALID_ARG;  // segments <= SUB_MAX points, leaf >= 1
   const size_t smem = subtree_smem();
-  static size_t attr = 0;
-  if (smem > attr) {
-    if (cudaFuncSetAttribute(k_kd_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return FF_ERR_CUDA;
-    attr = smem;
-  }
+  FF_TRY(smem_opt_in((const void *)k_kd_subtree, smem));
   k_kd_subtree<<<dim3(1 << maxT, ntrees), SUB_MAX, smem, st>>>(dev);
   FF_CHECK_LAUNCH();
   return FF_OK;
@@ -861,6 +855,10 @@ ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaSt
 // pixels by E_d on P^n_r: smallest cost wins, ties to the lowest pixel index.
 // Then the K proposals in order, each replacing only with strictly lower cost.
 // One half warp per grid point; lane 0 descends, the 16 lanes share each E_d.
+// The tree may come from the caller (ff_kdtree_init): a split dimension outside
+// [0, 27) or a leaf entry outside [0, N) is not dereferenced; it raises
+// DEV_ERR_BOUNDS (grid point, node or position) and the descent takes dimension 0
+// / the candidate is skipped.
 template <int R>
 __global__ void __launch_bounds__(256) k_kd_query(const KdQuery *qs) {
   const KdQuery &Q = qs[blockIdx.y];
@@ -874,8 +872,14 @@ __global__ void __launch_bounds__(256) k_kd_query(const KdQuery *qs) {
   if (l16 == 0) {
     const int32_t *q = Q.qfeat + (size_t)g * FEAT_STRIDE;
     int node = 0;
-    for (int d = 0; d < Q.D; d++)
-      node = (q[Q.split_dim[node]] < Q.split_val[node]) ? 2 * node + 1 : 2 * node + 2;
+    for (int d = 0; d < Q.D; d++) {
+      int sd = Q.split_dim[node];
+      if ((unsigned)sd >= (unsigned)NFEAT) {
+        raise_status(Q.status, DEV_ERR_BOUNDS, g, node);
+        sd = 0;
+      }
+      node = (q[sd] < Q.split_val[node]) ? 2 * node + 1 : 2 * node + 2;
+    }
     leaf = node - ((1 << Q.D) - 1);
   }
   leaf = __shfl_sync(gmask, leaf, threadIdx.x & 16);
@@ -884,6 +888,10 @@ __global__ void __launch_bounds__(256) k_kd_query(const KdQuery *qs) {
   int best = COST_UNSET, bidx = 0x7fffffff;
   for (int c = b; c < e; c++) {
     const int idx = Q.perm[c];
+    if ((unsigned)idx >= (unsigned)Q.N) {  // uniform over the half warp
+      if (l16 == 0) raise_status(Q.status, DEV_ERR_BOUNDS, g, c);
+      continue;
+    }
     const int x2 = idx % W, y2 = idx / W;
     const int cost = group_cost<R>(sc, Q.src.pitch, plane_centre(Q.tgt, x2, y2), Q.tgt.pitch, l16,
                                    gmask);

@@ -24,6 +24,7 @@
 // state and the state of the neighbours just outside the tile. Targets outside
 // the window are gathered from the census phase planes (column lines from the
 // transposed planes), through L1/L2.
+#include <atomic>
 #include <mutex>
 
 #include "ff_internal.cuh"
@@ -792,37 +793,30 @@ static ff_status side_stream(SideStream **out) {
 
 // Opt in to more than 48 KB of dynamic shared memory when a tile needs it.
 static ff_status set_pass_smem(int r, size_t bytes, int wide) {
-  static size_t done[3][9] = {{0}};
   if (r < 1 || r > 8 || wide < 0 || wide > 2) return FF_ERR_INVALID_ARG;
-  if (bytes <= done[wide][r]) return FF_OK;
-  cudaError_t e = cudaSuccess;
+  const void *fn = nullptr;
   if (wide == 1) {
-    FF_DISPATCH_R(r, e = cudaFuncSetAttribute(k_pass_wide<RR, 4>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    FF_DISPATCH_R(r, fn = (const void *)k_pass_wide<RR, 4>);
   } else if (wide == 2) {
-    FF_DISPATCH_R(r, e = cudaFuncSetAttribute(k_pass_wide<RR, 8>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    FF_DISPATCH_R(r, fn = (const void *)k_pass_wide<RR, 8>);
   } else {
-    FF_DISPATCH_R(r, e = cudaFuncSetAttribute(k_pass<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)bytes));
+    FF_DISPATCH_R(r, fn = (const void *)k_pass<RR>);
   }
-  if (e != cudaSuccess) return FF_ERR_CUDA;
-  done[wide][r] = bytes;
-  return FF_OK;
+  return smem_opt_in(fn, bytes);
 }
 
 // Multiprocessor count of the current device, looked up once per device.
 static ff_status sm_count(int *out) {
-  static int cache[64] = {0};
+  static std::atomic<int> cache[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FF_ERR_CUDA;
-  if (!cache[dev]) {
-    int v = 0;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (!v) {
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
       return FF_ERR_CUDA;
-    cache[dev] = v;
+    cache[dev].store(v, std::memory_order_relaxed);
   }
-  *out = cache[dev];
+  *out = v;
   return FF_OK;
 }
 

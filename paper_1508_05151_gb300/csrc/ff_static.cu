@@ -55,10 +55,11 @@ extern "C" ff_status ff_consistency_filter_static(const int16_t *F, const int16_
                                                   int32_t *err_sum, int32_t *sparse,
                                                   int32_t *n_sparse, uint8_t *mask,
                                                   void *stream) {
-  if (W < 1 || H < 1 || (long long)W * H > STATIC_MAX_PIXELS) return FF_ERR_SHAPE;
+  // the checks of ff_consistency_filter first, then this entry point's own limits
+  FF_TRY(check_shape(W, H));
+  FF_TRY(check_params(p));
+  if ((long long)W * H > STATIC_MAX_PIXELS) return FF_ERR_SHAPE;
   if (filter_scratch_bytes(W, H) > STATIC_SCRATCH_BYTES) return FF_ERR_SHAPE;
-  if (!p || p->eps < 1 || p->eps > 1000 || p->e < 1 || p->e > 9 || p->s < 0)
-    return FF_ERR_INVALID_ARG;
   if (!F || !Fb1 || !Fb2 || !valid || !err_sum || !sparse || !n_sparse || !mask)
     return FF_ERR_INVALID_ARG;
   if (((uintptr_t)F | (uintptr_t)Fb1 | (uintptr_t)Fb2) & 3) return FF_ERR_INVALID_ARG;

@@ -22,6 +22,7 @@ __all__ = [
     "pair_layers",
     "pair_kitti",
     "pair_for_config",
+    "mixed_batch",
     "BATCH_SIZES",
 ]
 
@@ -370,3 +371,14 @@ def pair_for_config(config, seed, size=None):
     if config == 5:
         return pair_kitti(seed)
     raise ValueError(f"unknown config {config}")
+
+
+def mixed_batch(seed0=500, per_size=16):
+    """The mixed-size batch: ``per_size`` pairs of each size in BATCH_SIZES, every
+    pair generated from its own seed (seed0 + 100 k + i for the i-th pair of the
+    k-th size). Returns a list of ((W, H), pair) in size order."""
+    out = []
+    for k, (W, H) in enumerate(BATCH_SIZES):
+        for i in range(per_size):
+            out.append(((W, H), pair_for_config(3, seed0 + 100 * k + i, (W, H))))
+    return out

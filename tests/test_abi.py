@@ -151,3 +151,25 @@ def test_exec_params_checks(L):
     ok = ffapi.ExecParams(pass_warps=e.pass_warps, rs_min_n=4, wide_min_n=2, split8_min_n=8)
     assert L.ff_set_exec_params(C.byref(ok)) == 0
     assert L.ff_set_exec_params(C.byref(e)) == 0  # restore
+
+
+def test_static_filter_applies_the_workspace_filters_checks(L):
+    """ff_consistency_filter_static refuses what ff_consistency_filter refuses (shape and
+    parameter checks run first, on the host, before any CUDA call), then its own
+    2^20-pixel limit."""
+    fake = C.c_void_p(0x1000)
+    ok = ffapi.Params()
+
+    def call(W, H, p):
+        return L.ff_consistency_filter_static(fake, fake, fake, W, H, C.byref(p), fake, fake,
+                                              fake, fake, fake, None)
+
+    assert call(20000, 1, ok) == 2          # W above 16384
+    assert call(1, 20000, ok) == 2          # H above 16384
+    assert call(0, 5, ok) == 2
+    assert call(1025, 1024, ok) == 2        # 2^20 + 1 pixels
+    for bad in [dict(tile=31), dict(k=5), dict(r=9), dict(leaf=1), dict(n_rs=4), dict(K=9),
+                dict(eps=0), dict(e=10)]:
+        assert call(64, 48, ffapi.Params(**bad)) == 1, bad
+    assert L.ff_consistency_filter_static(None, fake, fake, 64, 48, C.byref(ok), fake, fake, fake,
+                                          fake, fake, None) == 1

@@ -16,7 +16,7 @@ def test_bf16_round_to_nearest_even():
     # every bf16 value is exactly representable: rounding is idempotent
     r = N.bf16(np.random.default_rng(0).normal(size=1000))
     assert np.array_equal(N.bf16(r), r)
-    # relative error bound 2^-9
+    # relative error bound: the unit roundoff 2^-8 (half the spacing 2^-7 at 1.0)
     x = np.random.default_rng(1).uniform(-10, 10, size=10000)
     assert np.max(np.abs(N.bf16(x) - x) / np.abs(x)) <= 2.0 ** -8
 

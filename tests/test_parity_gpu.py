@@ -388,23 +388,25 @@ def test_flow_fields_with_proposals_kitti_full_size():
 
 def test_batch_64_mixed_full_size_sampled():
     """The benchmark's 64-pair mixed batch (16 each of 640x480, 584x388, 1024x436,
-    1242x375) as one graph replay: the first pair of each size bit-exact against the
-    oracle, the other 15 copies of each size equal to it."""
-    sizes, frames, pairs = [], [], []
-    for k, (W, H) in enumerate(synth.BATCH_SIZES):
-        p = synth.pair_for_config(3, 500 + k, (W, H))
-        pairs.append(p)
-        a, b = tg(p["I1"]), tg(p["I2"])
-        for _ in range(16):
-            sizes.append((W, H))
-            frames.append((a, b))
+    1242x375, every pair from its own seed) as one graph replay: every pair equals
+    the single-pair path, and two distinct pairs of each size are bit-exact against
+    the oracle."""
+    batch_pairs = synth.mixed_batch()
+    sizes = [wh for wh, _ in batch_pairs]
+    frames = [(tg(p["I1"]), tg(p["I2"])) for _, p in batch_pairs]
     batch = ffapi.FlowFieldsBatch(sizes, graph=True)
     outs = batch.run(frames)
     torch.cuda.synchronize()
+    singles = {}
+    for i, ((W, H), (a, b)) in enumerate(zip(sizes, frames)):
+        if (W, H) not in singles:
+            singles[(W, H)] = ffapi.FlowFields(W, H)
+        one = singles[(W, H)].run(a, b)
+        torch.cuda.synchronize()
+        for key in ("flows", "valid", "err_sum", "mask", "n_sparse"):
+            assert torch.equal(outs[i][key], one[key]), (i, key)
     for k in range(4):
-        first = outs[16 * k]
-        _compare(first, O.flow_fields(pairs[k]["I1"], pairs[k]["I2"], threads=3))
-        for j in range(1, 16):
-            o = outs[16 * k + j]
-            for key in ("flows", "valid", "err_sum", "mask", "n_sparse"):
-                assert torch.equal(o[key], first[key]), (k, j, key)
+        for j in (3, 12):
+            i = 16 * k + j
+            p = batch_pairs[i][1]
+            _compare(outs[i], O.flow_fields(p["I1"], p["I2"], threads=3))

@@ -54,10 +54,16 @@ def test_static_filter_matches_workspace_filter_twice(W, H, seeds):
         assert torch.equal(got["sparse"][:n], ref["sparse"][:n])
 
 
-def test_static_filter_rejects_oversized_images():
+def test_static_filter_rejects_what_the_workspace_filter_rejects():
     L = ffapi.lib()
     p = ffapi.Params()
     fake = C.c_void_p(0x1000)
-    # 2^20 + 1 pixels: refused on the host, nothing enqueued
+    # refused on the host, nothing enqueued: 2^20 + 1 pixels, a width above 16384,
+    # and parameters ff_consistency_filter refuses (odd tile)
     assert L.ff_consistency_filter_static(fake, fake, fake, 1025, 1024, C.byref(p), fake, fake,
                                           fake, fake, fake, None) == 2
+    assert L.ff_consistency_filter_static(fake, fake, fake, 20000, 1, C.byref(p), fake, fake,
+                                          fake, fake, fake, None) == 2
+    bad = ffapi.Params(tile=31)
+    assert L.ff_consistency_filter_static(fake, fake, fake, 64, 48, C.byref(bad), fake, fake,
+                                          fake, fake, fake, None) == 1
