@@ -130,6 +130,8 @@ ff_status ff_kdtree_build(const int32_t *feat, int N, int leaf, int32_t *perm, i
  * (int16 pairs, [Gy][Gx][K][2], NULL when K = 0) are tried in order; a candidate
  * replaces the current flow only when its E_d is strictly lower. Targets are
  * clamped into the image. census_src / census_tgt: level-n census (H x W).
+ * A split dimension outside [0, 27) or a perm entry outside [0, W*H) is not
+ * dereferenced: it sets device status code 1 (ff_device_status).
  * Outputs flow [Gy][Gx][2], cost [Gy][Gx]. Workspace: ff_level_workspace_size. */
 ff_status ff_kdtree_init(const int32_t *perm, const int32_t *split_dim, const int32_t *split_val,
                          int leaf, const uint8_t *src_img, const uint32_t *census_src,
@@ -266,13 +268,17 @@ ff_status ff_graph_destroy(ff_graph *g);
  *               8 threads per scan row (same schedule, same results)
  *   split8_min_n  0: that form uses 4 threads per candidate (128-thread CTAs);
  *               else levels with n >= split8_min_n (a power of two, 1..128) use 8
- *               (256-thread CTAs, 16 threads per scan row) */
+ *               (256-thread CTAs, 16 threads per scan row)
+ *   serial_flows  0: the three flows of a pair (and the image pyramid) run on
+ *               three streams concurrently; 1: all on the caller's stream, one
+ *               after another (so that one kernel can be timed alone) */
 typedef struct ff_exec_params {
   int32_t pass_warps;
   int32_t rs_min_n;
   int32_t wide_min_n;
   int32_t split8_min_n;
-  int32_t reserved[4];
+  int32_t serial_flows;
+  int32_t reserved[3];
 } ff_exec_params;
 ff_status ff_set_exec_params(const ff_exec_params *e);
 ff_status ff_get_exec_params(ff_exec_params *e);
@@ -325,18 +331,59 @@ ff_status ff_net_proposals(const ff_net_desc *d, const float *out, int B, int Gx
                            float flow_scale, int16_t *proposals, void *stream);
 
 /* Device-side status word kept at the start of a workspace: 0 when every
- * device check passed, else an error code with the grid coordinate where it was
- * raised. Synchronises `stream`, then copies 16 bytes device->host. */
+ * device check passed, else the first error code raised with two coordinates
+ * saying where: 1 an index out of range that was skipped instead of read (a
+ * kd-tree split dimension outside [0, 27) or leaf entry outside [0, W*H) given to
+ * ff_kdtree_init: grid point, node or leaf position), 2 an inconsistent kd
+ * partition count (node, level), 3 a bounded wait that ran out (block
+ * coordinates). Synchronises `stream`, then copies 16 bytes device->host. */
 ff_status ff_device_status(const void *ws, uint32_t *code, int32_t *x, int32_t *y, void *stream);
 
-/* Execution counters of the library, for benchmarking: kernels launched since
- * the last reset, and (when enabled with ff_profile_enable(1)) the summed
- * duration in ms and the launch count of the propagation kernel, measured with
- * CUDA events on the stream each launch was issued on. Host-only calls;
- * ff_profile_read synchronises the recorded events. */
+/* Execution counters of the library, for benchmarking (not in the paper).
+ * ff_profile_enable(on): bit 0 records CUDA events around every propagation
+ * kernel launch (on the stream it was issued on); bit 1 counts the propagation
+ * kernels' candidate evaluations on the device. Neither is recorded inside
+ * ff_graph_create. Host-only calls, not thread-safe against concurrent library
+ * calls.
+ *   ff_profile_reset     clears the launch counter and the recorded events, and
+ *                        (bit 1 set) the evaluation counters (synchronous memset)
+ *   ff_profile_read      kernels launched since the reset; summed duration (ms)
+ *                        and count of the recorded propagation launches
+ *                        (synchronises the recorded events)
+ *   ff_profile_levels    the same per level: ms[l], launches[l] for spacing
+ *                        n = 2^l, l = 0..4 (5 entries each)
+ *   ff_profile_evals     counts[r][l][kind], r = 0..8 (patch radius; 0 unused),
+ *                        l = 0..4 (n = 2^l), kinds: 0 incremental with the target
+ *                        in the kernel's staged shared-memory window, 1 incremental
+ *                        with the target gathered from the census planes, 2 full
+ *                        E_d in the window, 3 full E_d gathered; 180 uint64 in
+ *                        total. An incremental evaluation reads 2 (2r+1) target
+ *                        taps, a full one (2r+1)^2. Synchronises the device. */
 ff_status ff_profile_enable(int on);
 ff_status ff_profile_reset(void);
 ff_status ff_profile_read(uint64_t *launches, double *prop_ms, uint64_t *prop_launches);
+ff_status ff_profile_levels(double *ms, uint64_t *launches);
+ff_status ff_profile_evals(uint64_t *counts);
+
+/* Measurement probes (not in the paper): the roofline denominators of the search
+ * kernels, measured on the running GPU. Each enqueues `blocks` CTAs of 256
+ * threads on `stream` and returns at once; the caller times the launch with CUDA
+ * events. sink: device uint32 [blocks * 256], overwritten (keeps the work live).
+ *   ff_probe_popc       8 independent xor/popcount/add chains per thread on
+ *                       registers: 4096 * iters popcounts per CTA
+ *   ff_probe_smem_taps  census taps with both words from shared memory,
+ *                       conflict-free: 4096 * iters taps per CTA
+ *   ff_probe_l2_gather  reads of buf (device, 16-byte aligned, `words` a power
+ *                       of two >= 1024; L2-resident when smaller than the L2)
+ *                       through ld.global.cg, 8 loads in flight per thread:
+ *                       mode 0 a random 4-byte word per lane, mode 1 a random
+ *                       16-byte line per lane, mode 2 512 contiguous bytes per
+ *                       warp at a random aligned position. *bytes (host, may be
+ *                       NULL) = bytes the launch reads. */
+ff_status ff_probe_popc(uint32_t *sink, int blocks, int iters, void *stream);
+ff_status ff_probe_smem_taps(uint32_t *sink, int blocks, int iters, void *stream);
+ff_status ff_probe_l2_gather(const uint32_t *buf, size_t words, int mode, uint32_t *sink,
+                             int blocks, int iters, uint64_t *bytes, void *stream);
 
 #ifdef __cplusplus
 }

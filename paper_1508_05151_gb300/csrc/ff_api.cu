@@ -17,23 +17,55 @@ namespace ff {
 
 // ------------------------------------------------------------ accounting -----
 static std::atomic<uint64_t> g_launches{0};
-static bool g_prof = false;
+static int g_prof = 0;  // bit 0: pass-kernel events, bit 1: evaluation counters
 static std::vector<cudaEvent_t> g_ev;  // pairs (begin, end)
+static std::vector<int> g_ev_tag;      // level (log2 n) of each pair
 static size_t g_ev_used = 0;
 
-static ff_exec_params g_exec = {4, 0, 1, 2, {0, 0, 0, 0}};
+// Candidate evaluations of the pass kernels, counted when profiling asks for it:
+// [radius r][log2 n][kind], kinds as in PassCfg::evals. One array per device,
+// filled by atomics at the end of every counted launch.
+static __device__ unsigned long long g_evals[9 * PROF_LEVELS * 4];
+static void *g_evals_ptr[64];
+static std::mutex g_evals_mu;
+
+static ff_status evals_ptr(unsigned long long **out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FF_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_evals_mu);
+  if (!g_evals_ptr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_evals) != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      return FF_ERR_CUDA;
+    }
+    g_evals_ptr[dev] = p;
+  }
+  *out = (unsigned long long *)g_evals_ptr[dev];
+  return FF_OK;
+}
+
+static ff_exec_params g_exec = {4, 0, 1, 2, 0, {0, 0, 0}};
 const ff_exec_params &exec_params() { return g_exec; }
 
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
-bool prof_enabled() { return g_prof; }
-void prof_begin(cudaStream_t s) {
+bool prof_enabled() { return (g_prof & 1) != 0; }
+unsigned long long *prof_evals(int r, int log2n) {
+  if (!(g_prof & 2) || r < 1 || r > 8 || log2n < 0 || log2n >= PROF_LEVELS) return nullptr;
+  unsigned long long *p = nullptr;
+  if (evals_ptr(&p) != FF_OK) return nullptr;
+  return p + ((size_t)r * PROF_LEVELS + log2n) * 4;
+}
+void prof_begin(cudaStream_t s, int tag) {
   if (g_ev_used + 2 > g_ev.size()) {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     g_ev.push_back(a);
     g_ev.push_back(b);
+    g_ev_tag.push_back(0);
   }
+  g_ev_tag[g_ev_used / 2] = tag;
   cudaEventRecord(g_ev[g_ev_used], s);
 }
 void prof_end(cudaStream_t s) {
@@ -217,12 +249,14 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
     }
   const int nprob = (int)order_pair.size();  // 3 * np
   const int ngroups = 3;
+  // serial_flows (an execution parameter): every group on the caller's stream
+  const bool serial = exec_params().serial_flows != 0;
   SideSection sec;
-  FF_TRY(sec.begin(st, 2));
+  if (!serial) FF_TRY(sec.begin(st, 2));
   // smoothed images and census planes of every pair (shared by all flows), on
   // the second side stream; the other groups wait for them only before their
   // kd queries, so the pyramid overlaps their features and kd builds
-  const cudaStream_t ps = sec.side[1];
+  const cudaStream_t ps = serial ? st : sec.side[1];
   for (int i = 0; i < np; i++) {
     const PairPlan &P = plans[i];
     const int W = io[i].W, H = io[i].H;
@@ -240,7 +274,7 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
       }
   }
 
-  FF_TRY(sec.signal_side(1));
+  if (!serial) FF_TRY(sec.signal_side(1));
 
   std::vector<KdBuild> trees(nprob);
   std::vector<KdQuery> q(nprob);
@@ -276,7 +310,7 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
   }
   for (int g = 0; g < ngroups; g++) {
     const int t0 = g * np, cnt = np;
-    cudaStream_t gs = g == 0 ? st : sec.side[g - 1];
+    cudaStream_t gs = (g == 0 || serial) ? st : sec.side[g - 1];
     // WHT features of the group's target frames (all pixels) and source grid points
     for (int t = t0; t < t0 + cnt; t++) {
       const int i = order_pair[t], j = order_flow[t];
@@ -287,7 +321,7 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
                              plans[i].qfeat[j], gs));
     }
     FF_TRY(launch_kd_build(trees.data() + t0, bd.d_kd + t0, cnt, gs));
-    if (g != 2) FF_TRY(sec.wait_signal(gs));  // census planes ready
+    if (g != 2 && !serial) FF_TRY(sec.wait_signal(gs));  // census planes ready
     // kd query: one launch per run of equal radius
     for (int a0 = t0; a0 < t0 + cnt;) {
       int a1 = a0;
@@ -335,7 +369,7 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
         }
     }
   }
-  FF_TRY(sec.end());
+  if (!serial) FF_TRY(sec.end());
 
   for (int i = 0; i < np; i++) {
     const size_t N = (size_t)io[i].W * io[i].H;
@@ -680,8 +714,8 @@ ff_status ff_graph_create(int npairs, const ff_pair *pairs, const ff_params *p, 
   FF_TRY(check_ws(ws, ws_bytes, need));
   cudaStream_t st = (cudaStream_t)stream;
   if (!st) return FF_ERR_INVALID_ARG;  // the legacy default stream cannot be captured
-  const bool prof = g_prof;
-  g_prof = false;  // timing events cannot be read back from a graph
+  const int prof = g_prof;
+  g_prof = 0;  // timing events cannot be read back from a graph
   if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
     g_prof = prof;
     return FF_ERR_CUDA;
@@ -749,7 +783,8 @@ ff_status ff_device_status(const void *ws, uint32_t *code, int32_t *x, int32_t *
 ff_status ff_set_exec_params(const ff_exec_params *e) {
   auto pow2_or_0 = [](int v) { return v >= 0 && v <= 128 && (v & (v - 1)) == 0; };
   if (!e || e->pass_warps < 1 || e->pass_warps > 8 || !pow2_or_0(e->rs_min_n) ||
-      !pow2_or_0(e->wide_min_n) || !pow2_or_0(e->split8_min_n))
+      !pow2_or_0(e->wide_min_n) || !pow2_or_0(e->split8_min_n) || e->serial_flows < 0 ||
+      e->serial_flows > 1)
     return FF_ERR_INVALID_ARG;
   g_exec = *e;
   return FF_OK;
@@ -762,13 +797,27 @@ ff_status ff_get_exec_params(ff_exec_params *e) {
 }
 
 ff_status ff_profile_enable(int on) {
-  g_prof = on != 0;
+  if (on < 0 || on > 3) return FF_ERR_INVALID_ARG;
+  g_prof = on;
   return FF_OK;
 }
 
 ff_status ff_profile_reset(void) {
   g_launches.store(0);
   g_ev_used = 0;
+  if (g_prof & 2) {
+    unsigned long long *p = nullptr;
+    FF_TRY(evals_ptr(&p));
+    if (cudaMemset(p, 0, sizeof(g_evals)) != cudaSuccess) return FF_ERR_CUDA;
+  }
+  return FF_OK;
+}
+
+static ff_status event_ms(size_t i, double *ms) {
+  if (cudaEventSynchronize(g_ev[i + 1]) != cudaSuccess) return FF_ERR_CUDA;
+  float f = 0.f;
+  if (cudaEventElapsedTime(&f, g_ev[i], g_ev[i + 1]) != cudaSuccess) return FF_ERR_CUDA;
+  *ms = f;
   return FF_OK;
 }
 
@@ -776,13 +825,39 @@ ff_status ff_profile_read(uint64_t *launches, double *prop_ms, uint64_t *prop_la
   if (launches) *launches = g_launches.load();
   double tot = 0.0;
   for (size_t i = 0; i + 1 < g_ev_used; i += 2) {
-    if (cudaEventSynchronize(g_ev[i + 1]) != cudaSuccess) return FF_ERR_CUDA;
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, g_ev[i], g_ev[i + 1]) != cudaSuccess) return FF_ERR_CUDA;
+    double ms;
+    FF_TRY(event_ms(i, &ms));
     tot += ms;
   }
   if (prop_ms) *prop_ms = tot;
   if (prop_launches) *prop_launches = g_ev_used / 2;
+  return FF_OK;
+}
+
+ff_status ff_profile_levels(double *ms, uint64_t *launches) {
+  if (!ms || !launches) return FF_ERR_INVALID_ARG;
+  for (int l = 0; l < PROF_LEVELS; l++) {
+    ms[l] = 0.0;
+    launches[l] = 0;
+  }
+  for (size_t i = 0; i + 1 < g_ev_used; i += 2) {
+    const int l = g_ev_tag[i / 2];
+    if (l < 0 || l >= PROF_LEVELS) continue;
+    double t;
+    FF_TRY(event_ms(i, &t));
+    ms[l] += t;
+    launches[l] += 1;
+  }
+  return FF_OK;
+}
+
+ff_status ff_profile_evals(uint64_t *counts) {
+  if (!counts) return FF_ERR_INVALID_ARG;
+  unsigned long long *p = nullptr;
+  FF_TRY(evals_ptr(&p));
+  if (cudaDeviceSynchronize() != cudaSuccess) return FF_ERR_CUDA;
+  if (cudaMemcpy(counts, p, sizeof(g_evals), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FF_ERR_CUDA;
   return FF_OK;
 }
 

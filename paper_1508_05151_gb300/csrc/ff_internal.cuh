@@ -262,10 +262,14 @@ ff_status smem_opt_in(const void *func, size_t bytes);
 const ff_exec_params &exec_params();
 
 // ------------------------------------------------------- launch accounting ---
+constexpr int PROF_LEVELS = 5;  // levels n = 1, 2, 4, 8, 16 in the per-level profile
 void count_launch(int n);
 bool prof_enabled();
-void prof_begin(cudaStream_t s);
+void prof_begin(cudaStream_t s, int tag);  // tag: log2 n of the launch's level
 void prof_end(cudaStream_t s);
+// Counter block [4] of the pass kernels' evaluations at radius r and level log2n
+// when evaluation counting is on, else nullptr.
+unsigned long long *prof_evals(int r, int log2n);
 
 #define FF_CHECK_LAUNCH()                                     \
   do {                                                        \

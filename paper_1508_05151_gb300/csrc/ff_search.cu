@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) k_seed(const SearchProblem *probs) {
 // this equals the in-pass form exactly.
 template <int R>
 __global__ void __launch_bounds__(256) k_rs(const SearchProblem *probs, int s, int Rfull,
-                                            uint64_t seed) {
+                                            uint64_t seed, unsigned long long *evals) {
   const SearchProblem &P = probs[blockIdx.y];
   const int NX = P.src.NX, G = NX * P.src.NY, n = P.src.n, log2n = P.src.log2n;
   const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(256) k_rs(const SearchProblem *probs, int s, i
     fl[g] = cf;
     co[g] = cost;
   }
+  if (evals && l16 == 0) atomicAdd(evals + 3, 1ull);
 }
 
 struct PassCfg {
@@ -108,7 +109,21 @@ struct PassCfg {
   uint64_t seed;
   int last;     // last pass of the level (writes flow_final when given)
   int words_per_tile;  // shared memory words of one tile
+  // nullptr, or counters this launch adds its candidate evaluations to, by kind:
+  // [0] incremental with the target in the staged window, [1] incremental with
+  // the target read from the planes, [2] full E_d in the window, [3] full E_d
+  // from the planes (an incremental evaluation reads 2 (2r+1) target taps, a full
+  // one (2r+1)^2)
+  unsigned long long *evals;
 };
+
+// Evaluation counting (profiling only): a launch with cfg.evals set adds every
+// evaluation to four shared-memory counters (kinds as above) placed after the
+// tiles, and flushes them to cfg.evals at its end; without it the kernels only
+// test the uniform pointer.
+__device__ __forceinline__ void count_eval(unsigned *scnt, bool full, bool window) {
+  atomicAdd(scnt + (full ? 2 : 0) + (window ? 0 : 1), 1u);
+}
 
 constexpr int PASS_MAX_WARPS = 8;  // tiles per CTA: an execution parameter, 1..8
 constexpr unsigned FULL_MASK = 0xffffffffu;
@@ -345,11 +360,15 @@ __global__ void __launch_bounds__(PASS_MAX_WARPS * 32) k_pass(const SearchProble
   // Propagation candidate c (0: horizontal source, 1: vertical source) of the
   // point at scan position (ip, jp): its clamped flow, whether it is worth
   // evaluating, and its E_d (incremental when the flow is unchanged by clamping).
+  // evaluation counters (PassCfg::evals): four words per warp after the CTA's tiles
+  unsigned *scnt = smem + (size_t)(blockDim.x >> 5) * tpw * cfg.words_per_tile + 4 * warp;
+  if (cfg.evals && lane < 4) scnt[lane] = 0;
   auto evaluate = [&](int c, int lx, int ly, int px, int py, uint32_t fq, int32_t cq, int &cost) {
     const uint32_t *sc = s_src + (ly + R + 1) * Lt.swp + (lx + R + 1);
     const int tgx = clampi(px + flow_dx(fq), 0, W - 1), tgy = clampi(py + flow_dy(fq), 0, H - 1);
     const uint32_t cf = pack_flow(tgx - px, tgy - py);
     const Tgt t = locate(px, py, cf);
+    if (cfg.evals) count_eval(scnt, cf != fq, t.win);
     if (cf == fq) {
       const int step = c == 0 ? hdx : vdy;
       const int oo = step + step * R, oi = -step * R;  // outgoing / incoming line offsets
@@ -516,6 +535,7 @@ __global__ void __launch_bounds__(PASS_MAX_WARPS * 32) k_pass(const SearchProble
       const uint32_t cf = pack_flow(tgx - px, tgy - py);
       if (cf == cur) continue;
       const Tgt t = locate(px, py, cf);
+      if (cfg.evals) count_eval(scnt, true, t.win);
       const uint32_t *sc = s_src + (ly + R + 1) * Lt.swp + (lx + R + 1);
       const int cost = t.win ? lane_full<R>(sc, Lt.swp, s_tgt + (t.ey - toy) * Lt.twp + (t.ex - tox), Lt.twp)
                              : lane_full<R>(sc, Lt.swp, tbase + (size_t)t.ph * tpw_ + (size_t)t.ey * tpitch + t.ex, tpitch);
@@ -532,6 +552,10 @@ __global__ void __launch_bounds__(PASS_MAX_WARPS * 32) k_pass(const SearchProble
     const size_t g = (size_t)(y0 + ly) * Gx + x0 + lx;
     fout[g] = s_flow[ly * T + lx];
     cout[g] = s_cost[ly * T + lx];
+  }
+  if (cfg.evals) {
+    __syncwarp();
+    if (lane < 4 && scnt[lane]) atomicAdd(cfg.evals + lane, (unsigned long long)scnt[lane]);
   }
 }
 
@@ -580,7 +604,7 @@ __device__ __forceinline__ int part_full(const uint32_t *sc, int swp, const uint
 }
 
 template <int R, int SPLIT>
-__global__ void __launch_bounds__(32 * SPLIT) k_pass_wide(const SearchProblem *probs, PassCfg cfg) {
+__global__ void __launch_bounds__(32 * SPLIT, 32 / SPLIT) k_pass_wide(const SearchProblem *probs, PassCfg cfg) {
   constexpr int WIDE_THREADS = 32 * SPLIT;
   extern __shared__ uint32_t smem[];
   const SearchProblem &P = probs[blockIdx.y];
@@ -608,6 +632,8 @@ __global__ void __launch_bounds__(32 * SPLIT) k_pass_wide(const SearchProblem *p
   const int tpitch = P.tgt.pitch, tpitchT = P.tgt.pitchT;
   const size_t tpw_ = P.tgt.plane_words, tpwT = P.tgt.plane_wordsT;
   const TileSmem S = carve_tile(smem, Lt, T);
+  unsigned *scnt = smem + cfg.words_per_tile;  // evaluation counters (PassCfg::evals)
+  if (cfg.evals && t < 4) scnt[t] = 0;
   int tox, toy, ph0;
   stage_tile<R>(P, Lt, T, true, x0, y0, x1, y1, hdx, vdy, fin, cin, S, t, WIDE_THREADS, tox, toy,
                 ph0);
@@ -665,6 +691,7 @@ __global__ void __launch_bounds__(32 * SPLIT) k_pass_wide(const SearchProblem *p
       const int ph = ((tyy & m) << log2n) + (txx & m);
       const int ex = (txx >> log2n) + PLANE_PAD, ey = (tyy >> log2n) + PLANE_PAD;
       const bool win = in_win(ph, ex, ey);
+      if (cfg.evals && u == 0) count_eval(scnt, cf != fq, win);
       if (cf == fq) {  // incremental: E(q, f) - outgoing line + incoming line
         const int step = cand == 0 ? hdx : vdy;
         const int oo = step + step * R, oi = -step * R;
@@ -742,7 +769,9 @@ __global__ void __launch_bounds__(32 * SPLIT) k_pass_wide(const SearchProblem *p
       const int m = n - 1, ph = ((tgy & m) << log2n) + (tgx & m);
       const int ex = (tgx >> log2n) + PLANE_PAD, ey = (tgy >> log2n) + PLANE_PAD;
       const uint32_t *sc = S.src + (ly + R + 1) * Lt.swp + (lx + R + 1);
-      const int cost = in_win(ph, ex, ey)
+      const bool win = in_win(ph, ex, ey);
+      if (cfg.evals) count_eval(scnt, true, win);
+      const int cost = win
                            ? lane_full<R>(sc, Lt.swp, S.tgt + (ey - toy) * Lt.twp + (ex - tox), Lt.twp)
                            : lane_full<R>(sc, Lt.swp, tbase + (size_t)ph * tpw_ + (size_t)ey * tpitch + ex,
                                           tpitch);
@@ -758,6 +787,10 @@ __global__ void __launch_bounds__(32 * SPLIT) k_pass_wide(const SearchProblem *p
     const size_t g = (size_t)(y0 + ly) * Gx + x0 + lx;
     fout[g] = S.flow[ly * T + lx];
     cout[g] = S.cost[ly * T + lx];
+  }
+  if (cfg.evals) {
+    __syncthreads();
+    if (t < 4 && scnt[t]) atomicAdd(cfg.evals + t, (unsigned long long)scnt[t]);
   }
 }
 
@@ -843,20 +876,23 @@ static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d
   const int s8 = exec_params().split8_min_n;
   const int split = (s8 > 0 && probs[0].src.n >= s8) ? 8 : 4;
   int pw = exec_params().pass_warps;
-  while (pw > 1 && sizeof(uint32_t) * (size_t)lay.words() * pw > 227u * 1024u) pw--;
+  while (pw > 1 && sizeof(uint32_t) * ((size_t)lay.words() + 4) * pw > 227u * 1024u) pw--;
   // a level with few tiles spreads them over the SMs (one CTA per SM at least)
   const long tiles = (long)maxT * np;
   while (pw > 1 && (tiles + pw - 1) / pw < nsm) pw--;
   if (wide) pw = 1;
-  const size_t smem = sizeof(uint32_t) * (size_t)lay.words() * pw;
+  // the tiles, then four evaluation counters per warp (k_pass) or per CTA
+  const size_t smem = sizeof(uint32_t) * ((size_t)lay.words() * pw + 4 * pw);
   FF_TRY(set_pass_smem(r, smem, wide ? (split == 8 ? 2 : 1) : 0));
   const int rs_min_n = exec_params().rs_min_n;
   const bool rs_kernel = rs_min_n > 0 && probs[0].src.n >= rs_min_n;
+  const int log2n = probs[0].src.log2n;
+  unsigned long long *evals = prof_evals(r, log2n);
   for (int s = 0; s < 4; s++) {
     const bool do_rs = s < 3 && s < n_rs;
-    PassCfg cfg{s, tile, (do_rs && !rs_kernel) ? 1 : 0, R, seed, s == 3, lay.words()};
+    PassCfg cfg{s, tile, (do_rs && !rs_kernel) ? 1 : 0, R, seed, s == 3, lay.words(), evals};
     dim3 g((maxT + pw - 1) / pw, np);
-    if (prof_enabled()) prof_begin(st);
+    if (prof_enabled()) prof_begin(st, log2n);
     if (wide && split == 8) {
       FF_DISPATCH_R(r, (k_pass_wide<RR, 8><<<g, 256, smem, st>>>(d, cfg)));
     } else if (wide) {
@@ -868,7 +904,7 @@ static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d
     if (prof_enabled()) prof_end(st);
     if (do_rs && rs_kernel) {
       dim3 gr((maxG * 16 + 255) / 256, np);
-      FF_DISPATCH_R(r, k_rs<RR><<<gr, 256, 0, st>>>(d, s, R, seed));
+      FF_DISPATCH_R(r, k_rs<RR><<<gr, 256, 0, st>>>(d, s, R, seed, evals));
       FF_CHECK_LAUNCH();
     }
   }

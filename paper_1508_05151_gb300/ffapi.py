@@ -39,7 +39,8 @@ class Pair(C.Structure):
 class ExecParams(C.Structure):
     """ff_exec_params: launch shapes that never change results."""
     _fields_ = [("pass_warps", C.c_int32), ("rs_min_n", C.c_int32), ("wide_min_n", C.c_int32),
-                ("split8_min_n", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("split8_min_n", C.c_int32), ("serial_flows", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class NetDesc(C.Structure):
@@ -127,6 +128,11 @@ def lib():
             "ff_profile_enable": ([i32], i32),
             "ff_profile_reset": ([], i32),
             "ff_profile_read": ([C.POINTER(u64), C.POINTER(C.c_double), C.POINTER(u64)], i32),
+            "ff_profile_levels": ([C.POINTER(C.c_double), C.POINTER(u64)], i32),
+            "ff_profile_evals": ([C.POINTER(u64)], i32),
+            "ff_probe_popc": ([vp, i32, i32, vp], i32),
+            "ff_probe_smem_taps": ([vp, i32, i32, vp], i32),
+            "ff_probe_l2_gather": ([vp, sz, i32, vp, i32, i32, C.POINTER(u64), vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -348,8 +354,10 @@ def ff_flow_fields(I1, I2, params=None, proposals=None):
     return FlowFields(W, H, params, I1.device).run(I1, I2, proposals)
 
 
-def profile_enable(on=True):
-    _check("ff_profile_enable", lib().ff_profile_enable(1 if on else 0))
+def profile_enable(on=True, count_evals=False):
+    """Events around every propagation launch (on), device counters of the
+    propagation kernels' candidate evaluations (count_evals)."""
+    _check("ff_profile_enable", lib().ff_profile_enable((1 if on else 0) | (2 if count_evals else 0)))
 
 
 def profile_reset():
@@ -362,7 +370,59 @@ def profile_read():
     return dict(launches=n.value, prop_ms=ms.value, prop_launches=pn.value)
 
 
-EXEC_FIELDS = ("pass_warps", "rs_min_n", "wide_min_n", "split8_min_n")
+def profile_levels():
+    """Per level l (spacing 2^l, l = 0..4): summed propagation-launch ms, launches."""
+    ms = (C.c_double * 5)()
+    n = (C.c_uint64 * 5)()
+    _check("ff_profile_levels", lib().ff_profile_levels(ms, n))
+    return [dict(ms=ms[l], launches=n[l]) for l in range(5)]
+
+
+EVAL_KINDS = ("inc_window", "inc_planes", "full_window", "full_planes")
+
+
+def profile_evals():
+    """Candidate evaluations counted since the last reset: {(r, l): {kind: count}}
+    for every radius r and level l (spacing 2^l) with a non-zero count."""
+    c = (C.c_uint64 * (9 * 5 * 4))()
+    _check("ff_profile_evals", lib().ff_profile_evals(c))
+    out = {}
+    for r in range(9):
+        for l in range(5):
+            v = [c[(r * 5 + l) * 4 + k] for k in range(4)]
+            if any(v):
+                out[(r, l)] = dict(zip(EVAL_KINDS, v))
+    return out
+
+
+def eval_taps(r, counts):
+    """Target taps read for evaluation counts of radius r: an incremental
+    evaluation reads two patch lines (2 (2r+1) taps), a full one (2r+1)^2."""
+    L = 2 * r + 1
+    inc = counts["inc_window"] + counts["inc_planes"]
+    full = counts["full_window"] + counts["full_planes"]
+    planes = 2 * L * counts["inc_planes"] + L * L * counts["full_planes"]
+    return dict(taps=2 * L * inc + L * L * full, taps_from_planes=planes)
+
+
+def probe_popc(sink, blocks, iters):
+    _check("ff_probe_popc", lib().ff_probe_popc(_dev(sink), blocks, iters, _stream()))
+    return 4096 * iters * blocks
+
+
+def probe_smem_taps(sink, blocks, iters):
+    _check("ff_probe_smem_taps", lib().ff_probe_smem_taps(_dev(sink), blocks, iters, _stream()))
+    return 4096 * iters * blocks
+
+
+def probe_l2_gather(buf, mode, sink, blocks, iters):
+    nb = C.c_uint64()
+    _check("ff_probe_l2_gather", lib().ff_probe_l2_gather(_dev(buf), buf.numel(), mode, _dev(sink),
+                                                          blocks, iters, C.byref(nb), _stream()))
+    return nb.value
+
+
+EXEC_FIELDS = ("pass_warps", "rs_min_n", "wide_min_n", "split8_min_n", "serial_flows")
 
 
 def set_exec_params(**kw):

@@ -6,6 +6,7 @@ import subprocess
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
 
 
 def test_reference_arm_json_line():
@@ -25,3 +26,6 @@ def test_reference_arm_json_line():
     assert d["e2e"] == {"value": d["value"], "unit": "ms/pair", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert d["config"]["W"] == 1024 and d["config"]["H"] == 436
+    # both arms describe the workload with the same config object
+    import bench
+    assert d["config"] == json.loads(json.dumps(bench.bench_config(1)))
