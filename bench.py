@@ -501,6 +501,28 @@ def learned_measure(config, train_pairs=256, epochs=40, eval_pairs=32):
                     "error); equal_inliers = cheapest learned arm reaching plain_rs3's inliers"}
 
 
+def phase_timeline(run, flush, stream, reps=5):
+    """Live phase timeline of one step: the time (ms, median over `reps` steps)
+    at which each flow's stream finished each phase, from timing events recorded
+    by the library at the phase boundaries."""
+    from paper_1508_05151_gb300 import ffapi
+    import torch
+    runs = []
+    for i in range(reps):
+        flush.fill_(i & 0xff)
+        ffapi.profile_enable(False, marks=True)
+        ffapi.profile_reset()
+        run(i)
+        torch.cuda.synchronize()
+        runs.append(ffapi.profile_marks())
+        ffapi.profile_enable(False)
+    out = {}
+    for j, (g, ph, _) in enumerate(runs[0]):
+        vals = sorted(r[j][2] for r in runs if len(r) > j)
+        out.setdefault(g, {})[ph] = round(vals[len(vals) // 2], 3)
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -564,6 +586,7 @@ def run_ours(args):
     pr = pass_roofline(lambda i: direct.run(*dI[i % 2]), args.steps, flush, stream,
                        pk["popc_per_s"] if pk else 1.0,
                        pk["l2_word_gather_gbs"] if pk else 1.0)
+    timeline = phase_timeline(lambda i: direct.run(*dI[i % 2]), flush, stream)
 
     # ---- end to end through the public graph API with host buffers ----
     hI = [(torch.from_numpy(p["I1"]).pin_memory(), torch.from_numpy(p["I2"]).pin_memory())
@@ -643,6 +666,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h},
         "clocks": clk.summary(),
         "exec_params": tuned["choice"],
+        "phase_timeline_ms": timeline,
     }
     if batch is not None:
         line["batch_64_mixed"] = batch

@@ -342,9 +342,10 @@ ff_status ff_device_status(const void *ws, uint32_t *code, int32_t *x, int32_t *
 /* Execution counters of the library, for benchmarking (not in the paper).
  * ff_profile_enable(on): bit 0 records CUDA events around every propagation
  * kernel launch (on the stream it was issued on); bit 1 counts the propagation
- * kernels' candidate evaluations on the device. Neither is recorded inside
- * ff_graph_create. Host-only calls, not thread-safe against concurrent library
- * calls.
+ * kernels' candidate evaluations on the device; bit 2 records a timing event at
+ * every phase boundary of ff_flow_fields / ff_flow_fields_batch on the stream
+ * that ran the phase. None is recorded inside ff_graph_create. Host-only calls,
+ * not thread-safe against concurrent library calls.
  *   ff_profile_reset     clears the launch counter and the recorded events, and
  *                        (bit 1 set) the evaluation counters (synchronous memset)
  *   ff_profile_read      kernels launched since the reset; summed duration (ms)
@@ -352,6 +353,13 @@ ff_status ff_device_status(const void *ws, uint32_t *code, int32_t *x, int32_t *
  *                        (synchronises the recorded events)
  *   ff_profile_levels    the same per level: ms[l], launches[l] for spacing
  *                        n = 2^l, l = 0..4 (5 entries each)
+ *   ff_profile_marks     the recorded phase marks in order (at most cap): tags[i]
+ *                        = 100 * group + phase, ms[i] = time since the first
+ *                        mark; group 0/1/2 = forward / first / second backward
+ *                        flow, 3 = shared work; phase 0 start, 1 pyramid done,
+ *                        2 features, 3 kd build, 4 kd query, 10 + l level 2^l
+ *                        searched, 20 flows joined, 21 filter done; *n = marks
+ *                        recorded (synchronises them)
  *   ff_profile_evals     counts[r][l][kind], r = 0..8 (patch radius; 0 unused),
  *                        l = 0..4 (n = 2^l), kinds: 0 incremental with the target
  *                        in the kernel's staged shared-memory window, 1 incremental
@@ -363,6 +371,7 @@ ff_status ff_profile_enable(int on);
 ff_status ff_profile_reset(void);
 ff_status ff_profile_read(uint64_t *launches, double *prop_ms, uint64_t *prop_launches);
 ff_status ff_profile_levels(double *ms, uint64_t *launches);
+ff_status ff_profile_marks(int32_t *tags, double *ms, int cap, int *n);
 ff_status ff_profile_evals(uint64_t *counts);
 
 /* Measurement probes (not in the paper): the roofline denominators of the search

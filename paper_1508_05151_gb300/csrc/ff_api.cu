@@ -17,7 +17,7 @@ namespace ff {
 
 // ------------------------------------------------------------ accounting -----
 static std::atomic<uint64_t> g_launches{0};
-static int g_prof = 0;  // bit 0: pass-kernel events, bit 1: evaluation counters
+static int g_prof = 0;  // bit 0: pass-kernel events, bit 1: evaluation counters, bit 2: phase marks
 static std::vector<cudaEvent_t> g_ev;  // pairs (begin, end)
 static std::vector<int> g_ev_tag;      // level (log2 n) of each pair
 static size_t g_ev_used = 0;
@@ -72,6 +72,25 @@ void prof_end(cudaStream_t s) {
   cudaEventRecord(g_ev[g_ev_used + 1], s);
   g_ev_used += 2;
 }
+
+// Phase marks of run_pairs: one timing event per phase boundary on the stream
+// that ran the phase, tagged 100 * group + phase (group 3: the shared work).
+static std::vector<cudaEvent_t> g_mark;
+static std::vector<int> g_mark_tag;
+static size_t g_mark_used = 0;
+static void mark(cudaStream_t s, int group, int phase) {
+  if (!(g_prof & 4)) return;
+  if (g_mark_used == g_mark.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    g_mark.push_back(e);
+    g_mark_tag.push_back(0);
+  }
+  g_mark_tag[g_mark_used] = 100 * group + phase;
+  cudaEventRecord(g_mark[g_mark_used++], s);
+}
+enum { MK_START = 0, MK_PYRAMID = 1, MK_FEATURES = 2, MK_KD_BUILD = 3, MK_KD_QUERY = 4,
+       MK_LEVEL = 10, MK_JOINED = 20, MK_FILTER = 21 };
 
 // ------------------------------------------------------------ checks --------
 static bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
@@ -257,6 +276,7 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
   // the second side stream; the other groups wait for them only before their
   // kd queries, so the pyramid overlaps their features and kd builds
   const cudaStream_t ps = serial ? st : sec.side[1];
+  mark(st, 3, MK_START);
   for (int i = 0; i < np; i++) {
     const PairPlan &P = plans[i];
     const int W = io[i].W, H = io[i].H;
@@ -274,6 +294,7 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
       }
   }
 
+  mark(ps, 3, MK_PYRAMID);
   if (!serial) FF_TRY(sec.signal_side(1));
 
   std::vector<KdBuild> trees(nprob);
@@ -320,7 +341,9 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
       FF_TRY(launch_features(img[srcf[j]], io[i].W, io[i].H, rad[j], nullptr, 0, ntop,
                              plans[i].qfeat[j], gs));
     }
+    mark(gs, g, MK_FEATURES);
     FF_TRY(launch_kd_build(trees.data() + t0, bd.d_kd + t0, cnt, gs));
+    mark(gs, g, MK_KD_BUILD);
     if (g != 2 && !serial) FF_TRY(sec.wait_signal(gs));  // census planes ready
     // kd query: one launch per run of equal radius
     for (int a0 = t0; a0 < t0 + cnt;) {
@@ -329,6 +352,7 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
       FF_TRY(launch_kd_query(q.data() + a0, bd.d_q + a0, a1 - a0, gs));
       a0 = a1;
     }
+    mark(gs, g, MK_KD_QUERY);
     // levels n = 2^k .. 1; the state alternates between the two buffers per level
     for (int lv = k; lv >= 0; lv--) {
       const int n = 1 << lv;
@@ -362,6 +386,7 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
       }
       FF_TRY(run_level_on(sp.data() + t0, bd.d_sp + (size_t)nprob * lv + t0, cnt, p->tile,
                           p->n_rs, p->R, p->seed, gs));
+      mark(gs, g, MK_LEVEL + lv);
       if (lv != k)
         for (int t = t0; t < t0 + cnt; t++) {
           std::swap(cur[t], oth[t]);
@@ -370,6 +395,7 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
     }
   }
   if (!serial) FF_TRY(sec.end());
+  mark(st, 3, MK_JOINED);
 
   for (int i = 0; i < np; i++) {
     const size_t N = (size_t)io[i].W * io[i].H;
@@ -378,6 +404,7 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
                          p->s, io[i].valid, io[i].err_sum, io[i].sparse, io[i].n_sparse,
                          io[i].mask, plans[i].filter_scratch, st));
   }
+  mark(st, 3, MK_FILTER);
   return FF_OK;
 }
 
@@ -797,7 +824,7 @@ ff_status ff_get_exec_params(ff_exec_params *e) {
 }
 
 ff_status ff_profile_enable(int on) {
-  if (on < 0 || on > 3) return FF_ERR_INVALID_ARG;
+  if (on < 0 || on > 7) return FF_ERR_INVALID_ARG;
   g_prof = on;
   return FF_OK;
 }
@@ -805,6 +832,7 @@ ff_status ff_profile_enable(int on) {
 ff_status ff_profile_reset(void) {
   g_launches.store(0);
   g_ev_used = 0;
+  g_mark_used = 0;
   if (g_prof & 2) {
     unsigned long long *p = nullptr;
     FF_TRY(evals_ptr(&p));
@@ -847,6 +875,21 @@ ff_status ff_profile_levels(double *ms, uint64_t *launches) {
     FF_TRY(event_ms(i, &t));
     ms[l] += t;
     launches[l] += 1;
+  }
+  return FF_OK;
+}
+
+ff_status ff_profile_marks(int32_t *tags, double *ms, int cap, int *n) {
+  if (!n || cap < 0 || (cap > 0 && (!tags || !ms))) return FF_ERR_INVALID_ARG;
+  *n = (int)g_mark_used;
+  if (g_mark_used == 0) return FF_OK;
+  if (cudaEventSynchronize(g_mark[g_mark_used - 1]) != cudaSuccess) return FF_ERR_CUDA;
+  for (size_t i = 0; i < g_mark_used && (int)i < cap; i++) {
+    if (cudaEventSynchronize(g_mark[i]) != cudaSuccess) return FF_ERR_CUDA;
+    float f = 0.f;
+    if (cudaEventElapsedTime(&f, g_mark[0], g_mark[i]) != cudaSuccess) return FF_ERR_CUDA;
+    tags[i] = g_mark_tag[i];
+    ms[i] = f;
   }
   return FF_OK;
 }

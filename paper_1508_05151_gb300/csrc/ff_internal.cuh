@@ -314,11 +314,14 @@ struct KdBuild {
   // scratch (from kd_scratch)
   int32_t *perm_tmp;
   int32_t *seg_off;    // offsets of all top-level segments
-  int32_t *mm;         // min/max per top-level segment and dim
-  uint32_t *hist;      // radix histograms
-  int32_t *sel;        // per-segment select state
-  int32_t *cnt;        // per-segment partition counters
+  int32_t *mm;         // min/max per top-level segment and dim (two levels)
+  uint32_t *hist;      // radix histograms of the first digit
+  int32_t *sel;        // per-segment select state (two levels)
+  int32_t *cnt;        // per-segment partition counters (two levels)
+  int32_t *ccnt;       // per-segment collected-key counts (two levels)
+  int32_t *arrive;     // per-segment count of chunk CTAs done with the current step
   unsigned long long *keys;  // [N] select keys of the current level, by position
+  unsigned long long *coll;  // [N] keys of each segment's median bucket, at the segment's positions
   int value_bits;      // bound on the bits of any dimension's spread (0: unknown)
   int top_levels;      // levels built by the multi-block path
   DeviceStatus *status;  // set if a partition count is inconsistent

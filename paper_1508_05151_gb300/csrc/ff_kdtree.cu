@@ -12,16 +12,25 @@
 // 18-bit fields (the flow path; see ff_internal.cuh).
 //
 // Build, level by level:
-//   top levels (segments > SUB_MAX points): multi-CTA passes per level
-//     minmax   per-dim min/max of the root (rows in memory order); deeper
-//              levels get their children's min/max from the partition
-//     sel_init dimension choice, key width (a warp per segment); it also zeroes
-//              the segment's partition counters and its children's min/max
-//     passes x (hist, digit)  radix select of the rank-floor(m/2) key, 12-bit digits
-//                        (as many passes as the widest key needs),
-//                        key = (value - min) << ibits | pixel index (unique);
-//                        the first pass caches every position's key
-//     partition          key < selected key -> left child, else right
+//   top levels (segments > SUB_MAX points): three multi-CTA kernels per level,
+//   each over chunks of KD_CHUNK positions. The CTA that finishes the last chunk
+//   of a segment (a per-segment arrival count after a memory fence; nothing
+//   waits) runs that segment's next step, so a level needs no further launches:
+//     hist      key = (value - min) << ibits | pixel index (unique), cached per
+//               position; 12-bit histogram of the key's top digit. Last CTA of a
+//               segment: the bin holding the rank-floor(m/2) key.
+//     collect   the keys in that bin are appended to the segment's list (stored
+//               at the segment's own positions, so it always fits). Last CTA: the
+//               exact key of the remaining rank in the list (bitonic sort in
+//               shared memory; radix passes over the list when it is long, e.g.
+//               for heavily tied features).
+//     partition key < selected key -> left child, else right; the children's
+//               per-dimension min/max. Last CTA: the children's split dimension
+//               and key width (the next level's select state).
+//   The per-level state (select state, counters, min/max) alternates between two
+//   buffers by level parity, so a segment that finished can prepare its children
+//   while other segments of the level are still being partitioned. The root's
+//   min/max and select state come from one pass over all rows.
 //   bottom levels: one 1024-thread CTA per segment finishes its whole subtree in
 //     shared memory: nodes own aligned power-of-two slot blocks; per sub-level a
 //     bitonic sort of each block by (value, pixel-index rank) puts the left child
@@ -33,6 +42,8 @@ namespace ff {
 constexpr int SUB_MAX = 1024;  // largest segment finished by one CTA
 constexpr int DIGIT = 12;
 constexpr int NBINS = 1 << DIGIT;
+constexpr int KD_CHUNK = 1024;      // positions per CTA of the top-level kernels (<= 2 segments)
+constexpr int SEL_SORT_MAX = 2048;  // longest collected list selected by a shared-memory sort
 
 int kd_depth(int N, int leaf) {
   int d = 0;
@@ -66,13 +77,17 @@ void kd_bind_scratch(KdBuild &b, Arena &a) {
   b.top_levels = kd_top_levels(b.N, b.D);
   int T = b.top_levels;
   int segs = 1 << (T > 0 ? T - 1 : 0);  // widest top level processed
-  b.perm_tmp = a.take<int32_t>(b.N > 0 ? b.N : 1);
+  const size_t n1 = b.N > 0 ? b.N : 1;
+  b.perm_tmp = a.take<int32_t>(n1);
   b.seg_off = a.take<int32_t>((size_t)(1 << (T + 1)) + T + 2);
   b.mm = a.take<int32_t>((size_t)2 * segs * NFEAT * 2);  // two levels (ping-pong)
   b.hist = a.take<uint32_t>((size_t)segs * NBINS);
-  b.sel = a.take<int32_t>((size_t)segs * 8);
-  b.cnt = a.take<int32_t>((size_t)segs * 2);
-  b.keys = a.take<unsigned long long>(b.N > 0 && T > 0 ? b.N : 1);
+  b.sel = a.take<int32_t>((size_t)2 * segs * 8);
+  b.cnt = a.take<int32_t>((size_t)2 * segs * 2);
+  b.ccnt = a.take<int32_t>((size_t)2 * segs);
+  b.arrive = a.take<int32_t>((size_t)segs);
+  b.keys = a.take<unsigned long long>(T > 0 ? n1 : 1);
+  b.coll = a.take<unsigned long long>(T > 0 ? n1 : 1);
 }
 
 // Offsets of segment i at depth d (i in [0, 2^d]) by halving along i's bits.
@@ -93,10 +108,26 @@ __host__ __device__ __forceinline__ int seg_base(int d) { return (1 << d) - 1 + 
 __device__ __forceinline__ int32_t *cur_perm(const KdBuild &T, int d) {
   return (d & 1) ? T.perm_tmp : T.perm;
 }
-// min/max of segment s at level d: two buffers alternate by level parity.
+__device__ __forceinline__ int top_segs(const KdBuild &T) {
+  return 1 << (T.top_levels > 0 ? T.top_levels - 1 : 0);
+}
+// Per-level state of segment s at level d: two buffers alternate by level parity.
 __device__ __forceinline__ int32_t *mm_at(const KdBuild &T, int d, int s) {
-  const int segs = 1 << (T.top_levels > 0 ? T.top_levels - 1 : 0);
-  return T.mm + ((size_t)(d & 1) * segs + s) * NFEAT * 2;
+  return T.mm + ((size_t)(d & 1) * top_segs(T) + s) * NFEAT * 2;
+}
+// select state: [0] dim, [1] vmin, [2] key bits B, [3] ibits, [4] remaining rank
+// k, [5] prefix lo, [6] prefix hi, [7] bits consumed (B once the key is exact)
+__device__ __forceinline__ int32_t *sel_at(const KdBuild &T, int d, int s) {
+  return T.sel + ((size_t)(d & 1) * top_segs(T) + s) * 8;
+}
+__device__ __forceinline__ int32_t *cnt_at(const KdBuild &T, int d, int s) {
+  return T.cnt + ((size_t)(d & 1) * top_segs(T) + s) * 2;
+}
+__device__ __forceinline__ int32_t *ccnt_at(const KdBuild &T, int d, int s) {
+  return T.ccnt + (size_t)(d & 1) * top_segs(T) + s;
+}
+__device__ __forceinline__ unsigned long long sel_key(const int32_t *S) {
+  return ((unsigned long long)(unsigned)S[6] << 32) | (unsigned)S[5];
 }
 
 __global__ void k_kd_seg_off(KdBuild *trees, int ntrees) {
@@ -108,15 +139,18 @@ __global__ void k_kd_seg_off(KdBuild *trees, int ntrees) {
   }
 }
 
-// Identity permutation; zero radix histograms (each digit pass clears the bins it
-// used, so this is their only reset) and the root's min/max sentinels.
+// Identity permutation; zero the radix histograms (each digit step clears the
+// bins it used, so this is their only reset), the arrival counts, and the root's
+// min/max sentinels.
 __global__ void k_kd_init_perm(KdBuild *trees) {
   KdBuild &T = trees[blockIdx.y];
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   for (int i = tid; i < T.N; i += nth) T.perm[i] = i;
   if (T.top_levels > 0) {
-    const size_t nbins = ((size_t)1 << (T.top_levels - 1)) * NBINS;
+    const int segs = top_segs(T);
+    const size_t nbins = (size_t)segs * NBINS;
     for (size_t i = tid; i < nbins; i += nth) T.hist[i] = 0;
+    for (int i = tid; i < segs; i += nth) T.arrive[i] = 0;
     for (int i = tid; i < NFEAT; i += nth) {
       int32_t *m = mm_at(T, 0, 0) + i * 2;
       m[0] = INT32_MAX;
@@ -136,10 +170,88 @@ __device__ __forceinline__ int find_seg(const int32_t *off, int nseg, int pos) {
   return lo;
 }
 
+// Select state of segment s at level d from its min/max (read through L2: other
+// CTAs produced them), by one warp: lane k reads dimension k's min/max; the
+// split dimension (largest max - min, lowest dimension on ties) by one warp max
+// over the key (spread << 5) | (31 - lane). It also zeroes the segment's
+// counters and, below the last top level, resets its children's min/max.
+__device__ void seg_sel_init(KdBuild &T, int d, int s) {
+  const int lane = threadIdx.x & 31;
+  const int32_t *mm = mm_at(T, d, s);
+  long long key = -1;
+  if (lane < NFEAT) {
+    const long long sp = (long long)__ldcg(mm + lane * 2 + 1) - __ldcg(mm + lane * 2);  // < 2^32
+    if (sp >= 0) key = (sp << 5) | (31 - lane);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const long long y = __shfl_xor_sync(0xffffffffu, key, o);
+    key = y > key ? y : key;
+  }
+  const int best = key >= 0 ? 31 - (int)(key & 31) : 0;
+  const long long bs = key >= 0 ? key >> 5 : -1;
+  if (lane == 0) {
+    const int32_t *off = T.seg_off + seg_base(d);
+    const int m = off[s + 1] - off[s];
+    int vbits = bits_for(bs), ibits = bits_for(T.N - 1);
+    if (ibits < 1) ibits = 1;
+    int32_t *S = sel_at(T, d, s);
+    S[0] = best;
+    S[1] = __ldcg(mm + best * 2);
+    S[2] = vbits + ibits;
+    S[3] = ibits;
+    S[4] = m / 2;
+    S[5] = 0;
+    S[6] = 0;
+    S[7] = 0;
+    T.split_dim[(1 << d) - 1 + s] = best;
+    cnt_at(T, d, s)[0] = 0;
+    cnt_at(T, d, s)[1] = 0;
+    *ccnt_at(T, d, s) = 0;
+  }
+  if (d + 1 < T.top_levels && lane < NFEAT)
+    for (int c = 0; c < 2; c++) {
+      int32_t *m = mm_at(T, d + 1, 2 * s + c);
+      m[2 * lane] = INT32_MAX;
+      m[2 * lane + 1] = INT32_MIN;
+    }
+}
+
+// Arrival bookkeeping of a chunk CTA at level d: after the CTA's global updates
+// for the segments [seg0, seg_of(end - 1)] it touched, one fence and one
+// increment per segment; returns the mask (bit i: segment seg0 + i) of segments
+// whose last chunk this CTA was, their counts reset for the next kernel. Every
+// thread of the CTA must call it. Nothing waits: the CTA that completes a
+// segment sees every other chunk's updates through the fences.
+__device__ __forceinline__ int chunks_of(const int32_t *off, int s) {
+  const int b = off[s], e = off[s + 1];
+  return e > b ? (e - 1) / KD_CHUNK - b / KD_CHUNK + 1 : 0;
+}
+__device__ unsigned finish_chunk(KdBuild &T, const int32_t *off, int nseg, int end, int seg0) {
+  __shared__ unsigned s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned last = 0;
+    const int s1 = find_seg(off, nseg, end - 1);
+    for (int sg = seg0; sg <= s1 && sg - seg0 < 32; sg++) {
+      if (atomicAdd(&T.arrive[sg], 1) == chunks_of(off, sg) - 1) {
+        last |= 1u << (sg - seg0);
+        T.arrive[sg] = 0;
+      }
+    }
+    s_last = last;
+  }
+  __syncthreads();
+  const unsigned last = s_last;
+  if (last) __threadfence();
+  return last;
+}
+
 // Per-dimension min/max of the root (all N feature rows): the rows are read in
 // memory order, each warp walks a strided set of rows with lanes = dimensions
 // and four rows in flight, then warp results merge in shared memory and once per
-// CTA in global memory.
+// CTA in global memory. The last CTA of a tree sets up the root's select state.
 constexpr int MM_ROWS_PER_WARP = 64;
 
 __global__ void __launch_bounds__(256) k_kd_minmax_root(KdBuild *trees) {
@@ -148,6 +260,7 @@ __global__ void __launch_bounds__(256) k_kd_minmax_root(KdBuild *trees) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r0 = (blockIdx.x * 8 + warp) * MM_ROWS_PER_WARP;
   __shared__ int smin[NFEAT], smax[NFEAT];
+  __shared__ int s_last;
   if (tid < NFEAT) {
     smin[tid] = INT32_MAX;
     smax[tid] = INT32_MIN;
@@ -181,60 +294,17 @@ __global__ void __launch_bounds__(256) k_kd_minmax_root(KdBuild *trees) {
     atomicMin(&mm_at(T, 0, 0)[tid * 2], smin[tid]);
     atomicMax(&mm_at(T, 0, 0)[tid * 2 + 1], smax[tid]);
   }
-}
-
-// sel state per segment: [0] dim, [1] vmin, [2] key bits B, [3] ibits,
-// [4] remaining rank k, [5] prefix lo, [6] prefix hi, [7] bits consumed
-// One warp per segment: lane k reads dimension k's min/max; the split dimension
-// (largest max - min, lowest dimension on ties) by one warp max over the key
-// (spread << 5) | (31 - lane).
-constexpr int SEL_WARPS = 4;
-__global__ void __launch_bounds__(SEL_WARPS * 32) k_kd_sel_init(KdBuild *trees, int d) {
-  KdBuild &T = trees[blockIdx.y];
-  if (d >= T.top_levels) return;
-  const int lane = threadIdx.x & 31;
-  const int s = blockIdx.x * SEL_WARPS + (threadIdx.x >> 5);
-  if (s >= (1 << d)) return;  // whole warp
-  const int32_t *mm = mm_at(T, d, s);
-  long long key = -1;
-  if (lane < NFEAT) {
-    const long long sp = (long long)mm[lane * 2 + 1] - mm[lane * 2];  // < 2^32
-    if (sp >= 0) key = (sp << 5) | (31 - lane);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    s_last = atomicAdd(&T.arrive[0], 1) == (int)gridDim.x - 1;
+    if (s_last) T.arrive[0] = 0;
   }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const long long y = __shfl_xor_sync(0xffffffffu, key, o);
-    key = y > key ? y : key;
+  __syncthreads();
+  if (s_last && warp == 0) {
+    __threadfence();
+    seg_sel_init(T, 0, 0);
   }
-  const int best = key >= 0 ? 31 - (int)(key & 31) : 0;
-  const long long bs = key >= 0 ? key >> 5 : -1;
-  if (lane == 0) {
-    const int32_t *off = T.seg_off + seg_base(d);
-    const int m = off[s + 1] - off[s];
-    int vbits = bits_for(bs), ibits = bits_for(T.N - 1);
-    if (ibits < 1) ibits = 1;
-    int32_t *S = T.sel + s * 8;
-    S[0] = best;
-    S[1] = mm[best * 2];
-    S[2] = vbits + ibits;
-    S[3] = ibits;
-    S[4] = m / 2;
-    S[5] = 0;
-    S[6] = 0;
-    S[7] = 0;
-    T.split_dim[(1 << d) - 1 + s] = best;
-    // what this segment's partition needs: zero counters (and below, the min/max
-    // sentinels of its two children: the other ping-pong half, read last at
-    // level d - 1)
-    T.cnt[2 * s] = 0;
-    T.cnt[2 * s + 1] = 0;
-  }
-  if (d + 1 < T.top_levels && lane < NFEAT)
-    for (int c = 0; c < 2; c++) {
-      int32_t *m = mm_at(T, d + 1, 2 * s + c);
-      m[2 * lane] = INT32_MAX;
-      m[2 * lane + 1] = INT32_MIN;
-    }
 }
 
 // Feature value / whole row of point idx in either row layout.
@@ -269,8 +339,7 @@ __device__ __forceinline__ unsigned long long kd_key(const KdBuild &T, const int
   return ((unsigned long long)(unsigned)(v - S[1]) << S[3]) | (unsigned)idx;
 }
 
-constexpr int HIST_CHUNK = 1024;  // positions per CTA (segments > SUB_MAX: spans <= 2)
-constexpr int CHUNK_SEGS = 4;     // segment slots per chunk
+constexpr int CHUNK_SEGS = 4;  // segment slots per chunk
 
 // The segments a chunk of positions touches (top levels: at most CHUNK_SEGS):
 // first segment and the begin offsets of the following ones, in shared memory.
@@ -289,59 +358,15 @@ __device__ __forceinline__ int seg_of(int p, int seg0, const int *sbound) {
   return s;
 }
 
-__global__ void __launch_bounds__(256) k_kd_hist(KdBuild *trees, int d) {
-  KdBuild &T = trees[blockIdx.y];
-  if (d >= T.top_levels) return;
-  int start = blockIdx.x * HIST_CHUNK;
-  if (start >= T.N) return;
-  int end = min(start + HIST_CHUNK, T.N);
-  int nseg = 1 << d;
-  const int32_t *off = T.seg_off + seg_base(d);
-  __shared__ uint32_t sh[NBINS];
-  __shared__ int sseg0, sbound[CHUNK_SEGS - 1];
-  chunk_segments(off, nseg, start, &sseg0, sbound);
-  for (int i = threadIdx.x; i < NBINS; i += blockDim.x) sh[i] = 0;
-  __syncthreads();
-  const int seg0 = sseg0;
-  const bool single = sbound[0] >= end;
-  for (int p = start + threadIdx.x; p < end; p += blockDim.x) {
-    int s = single ? seg0 : seg_of(p, seg0, sbound);
-    const int32_t *S = T.sel + s * 8;
-    int B = S[2], used = S[7];
-    if (used >= B) continue;
-    int hi = B - used, lo = max(hi - DIGIT, 0);
-    // the first pass of a level gathers the point's value and caches its key;
-    // later passes read the cache (coalesced)
-    unsigned long long K;
-    if (used == 0) {
-      K = kd_key(T, S, cur_perm(T, d)[p]);
-      T.keys[p] = K;
-    } else {
-      K = T.keys[p];
-    }
-    unsigned long long pre = ((unsigned long long)(unsigned)S[6] << 32) | (unsigned)S[5];
-    if (hi < 64 && (K >> hi) != pre) continue;
-    unsigned dig = (unsigned)((K >> lo) & ((1ull << (hi - lo)) - 1));
-    if (single) atomicAdd(&sh[dig], 1u);
-    else atomicAdd(&T.hist[(size_t)s * NBINS + dig], 1u);
-  }
-  __syncthreads();
-  if (single)
-    for (int i = threadIdx.x; i < NBINS; i += blockDim.x)
-      if (sh[i]) atomicAdd(&T.hist[(size_t)seg0 * NBINS + i], sh[i]);
-}
-
-// One CTA per segment: find the bin holding rank k, narrow the prefix, clear.
-__global__ void __launch_bounds__(256) k_kd_digit(KdBuild *trees, int d) {
-  KdBuild &T = trees[blockIdx.y];
-  if (d >= T.top_levels) return;
-  int s = blockIdx.x;
-  if (s >= (1 << d)) return;
-  int32_t *S = T.sel + s * 8;
-  int B = S[2], used = S[7];
+// Digit step of segment s at level d (its histogram complete, read through L2):
+// the bin holding rank k, the narrowed prefix, the bins cleared for the next
+// level. Run by all 256 threads of one CTA.
+__device__ void seg_digit(KdBuild &T, int d, int s) {
+  int32_t *S = sel_at(T, d, s);
+  const int B = S[2], used = S[7];
   uint32_t *h = T.hist + (size_t)s * NBINS;
-  if (used >= B) return;
-  int hi = B - used, lo = max(hi - DIGIT, 0), nb = 1 << (hi - lo);
+  if (used >= B) return;  // uniform
+  const int hi = B - used, lo = max(hi - DIGIT, 0), nb = 1 << (hi - lo);
   __shared__ uint32_t part[256];
   __shared__ int found_bin, found_before, s_tt;
   __shared__ uint32_t s_before;
@@ -353,7 +378,7 @@ __global__ void __launch_bounds__(256) k_kd_digit(KdBuild *trees, int d) {
     const uint4 *h4 = (const uint4 *)(h + threadIdx.x * per);
 #pragma unroll
     for (int q = 0; q < per / 4; q++) {
-      const uint4 x = h4[q];
+      const uint4 x = __ldcg(h4 + q);
       v[4 * q] = x.x;
       v[4 * q + 1] = x.y;
       v[4 * q + 2] = x.z;
@@ -435,13 +460,167 @@ __global__ void __launch_bounds__(256) k_kd_digit(KdBuild *trees, int d) {
     for (int q = 0; q < per / 4; q++) h4[q] = make_uint4(0, 0, 0, 0);
   }
   if (threadIdx.x == 0) {
-    unsigned long long pre = ((unsigned long long)(unsigned)S[6] << 32) | (unsigned)S[5];
+    unsigned long long pre = sel_key(S);
     pre = (pre << (hi - lo)) | (unsigned)found_bin;
     S[5] = (int32_t)(pre & 0xffffffffu);
     S[6] = (int32_t)(pre >> 32);
     S[4] -= found_before;
     S[7] = used + (hi - lo);
   }
+  __syncthreads();
+}
+
+// Level d's radix pass over the top digit: every position's key (gathered from
+// its feature row, cached in T.keys) counted in its segment's histogram; the last
+// chunk of a segment runs its digit step.
+__global__ void __launch_bounds__(256) k_kd_hist(KdBuild *trees, int d) {
+  KdBuild &T = trees[blockIdx.y];
+  if (d >= T.top_levels) return;
+  const int start = blockIdx.x * KD_CHUNK;
+  if (start >= T.N) return;
+  const int end = min(start + KD_CHUNK, T.N);
+  const int nseg = 1 << d;
+  const int32_t *off = T.seg_off + seg_base(d);
+  __shared__ uint32_t sh[NBINS];
+  __shared__ int sseg0, sbound[CHUNK_SEGS - 1];
+  chunk_segments(off, nseg, start, &sseg0, sbound);
+  for (int i = threadIdx.x; i < NBINS; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const int seg0 = sseg0;
+  const bool single = sbound[0] >= end;
+  for (int p = start + threadIdx.x; p < end; p += blockDim.x) {
+    const int s = single ? seg0 : seg_of(p, seg0, sbound);
+    const int32_t *S = sel_at(T, d, s);
+    const int B = S[2], lo = max(B - DIGIT, 0);
+    const unsigned long long K = kd_key(T, S, cur_perm(T, d)[p]);
+    T.keys[p] = K;
+    const unsigned dig = (unsigned)((K >> lo) & ((1ull << (B - lo)) - 1));
+    if (single) atomicAdd(&sh[dig], 1u);
+    else atomicAdd(&T.hist[(size_t)s * NBINS + dig], 1u);
+  }
+  __syncthreads();
+  if (single)
+    for (int i = threadIdx.x; i < NBINS; i += blockDim.x)
+      if (sh[i]) atomicAdd(&T.hist[(size_t)seg0 * NBINS + i], sh[i]);
+  const unsigned last = finish_chunk(T, off, nseg, end, seg0);
+  for (int i = 0; i < CHUNK_SEGS; i++)
+    if (last & (1u << i)) seg_digit(T, d, seg0 + i);
+}
+
+// Exact key of the remaining rank S[4] among segment s's collected keys (the
+// bucket of the top digit), by all 256 threads of one CTA: a bitonic sort in
+// shared memory for lists of up to SEL_SORT_MAX keys, else radix passes of DIGIT
+// bits over the list in global memory. The result becomes the selected key.
+__device__ void seg_select(KdBuild &T, int d, int s) {
+  int32_t *S = sel_at(T, d, s);
+  const int B = S[2];
+  if (S[7] >= B) return;  // uniform: the top digit already fixed the key
+  const int32_t *off = T.seg_off + seg_base(d);
+  const int c = min(__ldcg(ccnt_at(T, d, s)), off[s + 1] - off[s]);  // the list fits its segment
+  const unsigned long long *list = T.coll + off[s];
+  const int tid = threadIdx.x;
+  __shared__ unsigned long long sk[SEL_SORT_MAX];
+  __shared__ unsigned long long s_key, s_pre;
+  __shared__ uint32_t hs[NBINS];
+  __shared__ uint32_t s_k;
+  __shared__ int s_used;
+  const uint32_t k0 = (uint32_t)S[4];
+  if (c <= SEL_SORT_MAX) {
+    int n2 = 1;
+    while (n2 < c) n2 <<= 1;
+    for (int i = tid; i < n2; i += blockDim.x) sk[i] = i < c ? __ldcg(list + i) : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < n2; i += blockDim.x) {
+          const int ij = i ^ j;
+          if (ij > i) {
+            const unsigned long long a = sk[i], b = sk[ij];
+            if ((a > b) == ((i & k) == 0)) {
+              sk[i] = b;
+              sk[ij] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    if (tid == 0) s_key = sk[k0 < (uint32_t)c ? k0 : (uint32_t)(c > 0 ? c - 1 : 0)];
+  } else {
+    if (tid == 0) {
+      s_pre = sel_key(S);
+      s_k = k0;
+      s_used = S[7];
+    }
+    __syncthreads();
+    while (s_used < B) {  // s_used is shared: the loop is uniform
+      const int hi = B - s_used, lo = max(hi - DIGIT, 0), nb = 1 << (hi - lo);
+      const unsigned long long pre = s_pre;
+      for (int i = tid; i < NBINS; i += blockDim.x) hs[i] = 0;
+      __syncthreads();
+      for (int i = tid; i < c; i += blockDim.x) {
+        const unsigned long long K = __ldcg(list + i);
+        if ((K >> hi) == pre) atomicAdd(&hs[(unsigned)((K >> lo) & (unsigned long long)(nb - 1))], 1u);
+      }
+      __syncthreads();
+      if (tid == 0) {  // the bin holding rank s_k
+        uint32_t acc = 0;
+        int bin = nb - 1;
+        for (int i = 0; i < nb; i++) {
+          if (acc + hs[i] > s_k) {
+            bin = i;
+            break;
+          }
+          acc += hs[i];
+        }
+        s_pre = (pre << (hi - lo)) | (unsigned)bin;
+        s_k -= acc;
+        s_used += hi - lo;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) s_key = s_pre;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned long long key = s_key;
+    S[5] = (int32_t)(key & 0xffffffffu);
+    S[6] = (int32_t)(key >> 32);
+    S[4] = 0;
+    S[7] = B;
+  }
+  __syncthreads();
+}
+
+// Collect: the cached keys that fall in the bin the top digit chose are appended
+// to their segment's list; the last chunk of a segment selects its exact median
+// key from the list.
+__global__ void __launch_bounds__(256) k_kd_collect(KdBuild *trees, int d) {
+  KdBuild &T = trees[blockIdx.y];
+  if (d >= T.top_levels) return;
+  const int start = blockIdx.x * KD_CHUNK;
+  if (start >= T.N) return;
+  const int end = min(start + KD_CHUNK, T.N);
+  const int nseg = 1 << d;
+  const int32_t *off = T.seg_off + seg_base(d);
+  __shared__ int sseg0, sbound[CHUNK_SEGS - 1];
+  chunk_segments(off, nseg, start, &sseg0, sbound);
+  __syncthreads();
+  const int seg0 = sseg0;
+  for (int p = start + threadIdx.x; p < end; p += blockDim.x) {
+    const int s = seg_of(p, seg0, sbound);
+    const int32_t *S = sel_at(T, d, s);
+    const int B = S[2], used = S[7];
+    if (used >= B) continue;
+    const unsigned long long K = T.keys[p];
+    if ((K >> (B - used)) == sel_key(S)) {
+      const int slot = atomicAdd(ccnt_at(T, d, s), 1);
+      if (slot < off[s + 1] - off[s]) T.coll[off[s] + slot] = K;
+      else raise_status(T.status, DEV_ERR_KD, s, d);
+    }
+  }
+  const unsigned last = finish_chunk(T, off, nseg, end, seg0);
+  for (int i = 0; i < CHUNK_SEGS; i++)
+    if (last & (1u << i)) seg_select(T, d, seg0 + i);
 }
 
 // Partition: key < selected key goes to the left child, else right. Positions
@@ -452,19 +631,17 @@ __global__ void __launch_bounds__(256) k_kd_digit(KdBuild *trees, int d) {
 // min/max of the children (next level) is accumulated per child present in the
 // warp: one child at a time, all lanes converged, full-mask warp reductions in
 // which the other lanes contribute the neutral value, then shared and global
-// atomics. (An earlier form reduced under per-lane group masks; with packed
-// rows, the values of the lanes past the chunk's end reached real children's
-// min/max, nondeterministically.) Rows are read in either layout (int32 or packed).
-constexpr int PART_CHUNK = 1024;  // positions per CTA (spans <= 2 segments at top levels)
-constexpr int PART_ROUNDS = PART_CHUNK / 256;
+// atomics. The last chunk of a segment sets up its two children's select state
+// for the next level. Rows are read in either layout (int32 or packed).
+constexpr int PART_ROUNDS = KD_CHUNK / 256;
 
 template <bool PACKED>
 __global__ void __launch_bounds__(256, 3) k_kd_partition(KdBuild *trees, int d) {
   KdBuild &T = trees[blockIdx.y];
   if (d >= T.top_levels) return;
-  const int start = blockIdx.x * PART_CHUNK;
+  const int start = blockIdx.x * KD_CHUNK;
   if (start >= T.N) return;
-  const int end = min(start + PART_CHUNK, T.N);
+  const int end = min(start + KD_CHUNK, T.N);
   const int nseg = 1 << d;
   const int32_t *off = T.seg_off + seg_base(d);
   const int32_t *src = cur_perm(T, d);
@@ -489,10 +666,10 @@ __global__ void __launch_bounds__(256, 3) k_kd_partition(KdBuild *trees, int d) 
     int c = -1, idx = 0;
     if (p < end) {
       const int sg = seg_of(p, seg0, s_bound);
-      const int32_t *S = T.sel + sg * 8;
+      const int32_t *S = sel_at(T, d, sg);
       idx = src[p];
-      const unsigned long long K = T.keys[p];  // cached by the level's first histogram pass
-      const unsigned long long sel = ((unsigned long long)(unsigned)S[6] << 32) | (unsigned)S[5];
+      const unsigned long long K = T.keys[p];  // cached by the level's histogram pass
+      const unsigned long long sel = sel_key(S);
       c = 2 * (sg - seg0) + (K < sel ? 0 : 1);
       if (K == sel) T.split_val[(1 << d) - 1 + sg] = (int)(K >> S[3]) + S[1];
     }
@@ -529,7 +706,7 @@ __global__ void __launch_bounds__(256, 3) k_kd_partition(KdBuild *trees, int d) 
   }
   __syncthreads();
   if (tid < 8 && s_cnt[tid] > 0 && seg0 + (tid >> 1) < nseg)
-    s_base[tid] = atomicAdd(&T.cnt[2 * (seg0 + (tid >> 1)) + (tid & 1)], s_cnt[tid]);
+    s_base[tid] = atomicAdd(&cnt_at(T, d, seg0 + (tid >> 1))[tid & 1], s_cnt[tid]);
   if (child_mm)
     for (int i = tid; i < 8 * NFEAT; i += 256) {
       const int c = i / NFEAT, dim = i % NFEAT;
@@ -549,6 +726,13 @@ __global__ void __launch_bounds__(256, 3) k_kd_partition(KdBuild *trees, int d) 
     const int lim = side ? m - half : half;
     if (k < lim) dstp[b + side * half + k] = idxs[r];
     else raise_status(T.status, DEV_ERR_KD, sg, d);
+  }
+  if (child_mm) {
+    const unsigned last = finish_chunk(T, off, nseg, end, seg0);
+    // warps 2i and 2i + 1 set up the two children of the i-th completed segment
+    const int warp = tid >> 5;
+    if (warp < 2 * CHUNK_SEGS && (last & (1u << (warp >> 1))))
+      seg_sel_init(T, d + 1, 2 * (seg0 + (warp >> 1)) + (warp & 1));
   }
 }
 
@@ -806,39 +990,29 @@ ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaSt
   const bool packed = trees[0].packed != 0;  // one row layout per launch
   for (int i = 1; i < ntrees; i++)
     if ((trees[i].packed != 0) != packed) return FF_ERR_INVALID_ARG;
-  // radix-select passes: enough digits for the widest key (value spread bits +
-  // index bits) of any tree
-  int passes = 1;
-  for (int i = 0; i < ntrees; i++) {
-    const int vb = trees[i].value_bits > 0 ? trees[i].value_bits : 33;
-    const int ib = max(bits_for(trees[i].N - 1), 1);
-    passes = max(passes, (vb + ib + DIGIT - 1) / DIGIT);
-  }
   const int B = 256;
   const int gN = min((maxN + B - 1) / B, 4096);
   k_kd_init_perm<<<dim3(gN, ntrees), B, 0, st>>>(dev);
   FF_CHECK_LAUNCH();
   k_kd_seg_off<<<dim3(8, ntrees), B, 0, st>>>(dev, ntrees);
   FF_CHECK_LAUNCH();
+  // three launches per top level; the last chunk CTA of each segment chains the
+  // segment's next step (digit, select, children's split dimension)
+  const int chunks = (maxN + KD_CHUNK - 1) / KD_CHUNK;
   for (int d = 0; d < maxT; d++) {
-    const int nseg = 1 << d;
     if (d == 0) {
       const int rows_per_cta = 8 * MM_ROWS_PER_WARP;
       k_kd_minmax_root<<<dim3((maxN + rows_per_cta - 1) / rows_per_cta, ntrees), 256, 0, st>>>(dev);
       FF_CHECK_LAUNCH();
     }
-    k_kd_sel_init<<<dim3((nseg + SEL_WARPS - 1) / SEL_WARPS, ntrees), SEL_WARPS * 32, 0, st>>>(dev, d);
+    k_kd_hist<<<dim3(chunks, ntrees), 256, 0, st>>>(dev, d);
     FF_CHECK_LAUNCH();
-    for (int pass = 0; pass < passes; pass++) {
-      k_kd_hist<<<dim3((maxN + HIST_CHUNK - 1) / HIST_CHUNK, ntrees), 256, 0, st>>>(dev, d);
-      FF_CHECK_LAUNCH();
-      k_kd_digit<<<dim3(nseg, ntrees), 256, 0, st>>>(dev, d);
-      FF_CHECK_LAUNCH();
-    }
+    k_kd_collect<<<dim3(chunks, ntrees), 256, 0, st>>>(dev, d);
+    FF_CHECK_LAUNCH();
     if (packed)
-      k_kd_partition<true><<<dim3((maxN + PART_CHUNK - 1) / PART_CHUNK, ntrees), 256, 0, st>>>(dev, d);
+      k_kd_partition<true><<<dim3(chunks, ntrees), 256, 0, st>>>(dev, d);
     else
-      k_kd_partition<false><<<dim3((maxN + PART_CHUNK - 1) / PART_CHUNK, ntrees), 256, 0, st>>>(dev, d);
+      k_kd_partition<false><<<dim3(chunks, ntrees), 256, 0, st>>>(dev, d);
     FF_CHECK_LAUNCH();
   }
   if (maxSub > 10) return FF_ERR_INVALID_ARG;  // segments <= SUB_MAX points, leaf >= 1

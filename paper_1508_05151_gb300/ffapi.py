@@ -130,6 +130,8 @@ def lib():
             "ff_profile_read": ([C.POINTER(u64), C.POINTER(C.c_double), C.POINTER(u64)], i32),
             "ff_profile_levels": ([C.POINTER(C.c_double), C.POINTER(u64)], i32),
             "ff_profile_evals": ([C.POINTER(u64)], i32),
+            "ff_profile_marks": ([C.POINTER(C.c_int32), C.POINTER(C.c_double), i32,
+                                  C.POINTER(C.c_int)], i32),
             "ff_probe_popc": ([vp, i32, i32, vp], i32),
             "ff_probe_smem_taps": ([vp, i32, i32, vp], i32),
             "ff_probe_l2_gather": ([vp, sz, i32, vp, i32, i32, C.POINTER(u64), vp], i32),
@@ -354,10 +356,31 @@ def ff_flow_fields(I1, I2, params=None, proposals=None):
     return FlowFields(W, H, params, I1.device).run(I1, I2, proposals)
 
 
-def profile_enable(on=True, count_evals=False):
+def profile_enable(on=True, count_evals=False, marks=False):
     """Events around every propagation launch (on), device counters of the
-    propagation kernels' candidate evaluations (count_evals)."""
-    _check("ff_profile_enable", lib().ff_profile_enable((1 if on else 0) | (2 if count_evals else 0)))
+    propagation kernels' candidate evaluations (count_evals), timing events at the
+    phase boundaries of a pair (marks)."""
+    _check("ff_profile_enable", lib().ff_profile_enable(
+        (1 if on else 0) | (2 if count_evals else 0) | (4 if marks else 0)))
+
+
+MARK_PHASES = {0: "start", 1: "pyramid", 2: "features", 3: "kd_build", 4: "kd_query",
+               20: "joined", 21: "filter"}
+MARK_GROUPS = {0: "fwd", 1: "bwd1", 2: "bwd2", 3: "shared"}
+
+
+def profile_marks(cap=4096):
+    """Recorded phase marks: list of (group, phase, ms since the first mark)."""
+    tags = (C.c_int32 * cap)()
+    ms = (C.c_double * cap)()
+    n = C.c_int()
+    _check("ff_profile_marks", lib().ff_profile_marks(tags, ms, cap, C.byref(n)))
+    out = []
+    for i in range(min(n.value, cap)):
+        g, ph = divmod(tags[i], 100)
+        name = MARK_PHASES.get(ph, f"level{1 << (ph - 10)}" if 10 <= ph < 20 else str(ph))
+        out.append((MARK_GROUPS.get(g, str(g)), name, ms[i]))
+    return out
 
 
 def profile_reset():
