@@ -269,16 +269,20 @@ ff_status ff_graph_destroy(ff_graph *g);
  *   split8_min_n  0: that form uses 4 threads per candidate (128-thread CTAs);
  *               else levels with n >= split8_min_n (a power of two, 1..128) use 8
  *               (256-thread CTAs, 16 threads per scan row)
- *   serial_flows  0: the three flows of a pair (and the image pyramid) run on
- *               three streams concurrently; 1: all on the caller's stream, one
- *               after another (so that one kernel can be timed alone) */
+ *   serial_flows  0: the three flows of a pair and the image pyramid run on
+ *               four streams concurrently; 1: all on the caller's stream, one
+ *               after another (so that one kernel can be timed alone)
+ *   kd_merge    0: each flow builds its kd trees on its own stream; 1: the trees
+ *               of all flows are built in one launch chain (every launch over
+ *               all trees) before the flows fork */
 typedef struct ff_exec_params {
   int32_t pass_warps;
   int32_t rs_min_n;
   int32_t wide_min_n;
   int32_t split8_min_n;
   int32_t serial_flows;
-  int32_t reserved[3];
+  int32_t kd_merge;
+  int32_t reserved[2];
 } ff_exec_params;
 ff_status ff_set_exec_params(const ff_exec_params *e);
 ff_status ff_get_exec_params(ff_exec_params *e);

@@ -45,7 +45,7 @@ static ff_status evals_ptr(unsigned long long **out) {
   return FF_OK;
 }
 
-static ff_exec_params g_exec = {4, 0, 1, 2, 0, {0, 0, 0}};
+static ff_exec_params g_exec = {4, 0, 1, 2, 0, 0, {0, 0}};
 const ff_exec_params &exec_params() { return g_exec; }
 
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
@@ -268,14 +268,18 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
     }
   const int nprob = (int)order_pair.size();  // 3 * np
   const int ngroups = 3;
-  // serial_flows (an execution parameter): every group on the caller's stream
+  // serial_flows (an execution parameter): every group on the caller's stream;
+  // kd_merge: the kd trees of all groups are built in one launch chain on the
+  // caller's stream before the groups fork
   const bool serial = exec_params().serial_flows != 0;
+  const bool kd_merge = exec_params().kd_merge != 0;
   SideSection sec;
-  if (!serial) FF_TRY(sec.begin(st, 2));
-  // smoothed images and census planes of every pair (shared by all flows), on
-  // the second side stream; the other groups wait for them only before their
-  // kd queries, so the pyramid overlaps their features and kd builds
-  const cudaStream_t ps = serial ? st : sec.side[1];
+  if (!serial) FF_TRY(sec.begin(st, 3));
+  auto group_stream = [&](int g) { return (g == 0 || serial) ? st : sec.side[g - 1]; };
+  // smoothed images and census planes of every pair (shared by all flows), on a
+  // side stream of their own; the groups wait for them only before their kd
+  // queries, so the pyramid overlaps their features and kd builds
+  const cudaStream_t ps = serial ? st : sec.side[2];
   mark(st, 3, MK_START);
   for (int i = 0; i < np; i++) {
     const PairPlan &P = plans[i];
@@ -295,7 +299,7 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
   }
 
   mark(ps, 3, MK_PYRAMID);
-  if (!serial) FF_TRY(sec.signal_side(1));
+  if (!serial) FF_TRY(sec.signal(0, ps));
 
   std::vector<KdBuild> trees(nprob);
   std::vector<KdQuery> q(nprob);
@@ -329,22 +333,37 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
     ccur[t] = P.ca[j];
     coth[t] = P.cb[j];
   }
-  for (int g = 0; g < ngroups; g++) {
-    const int t0 = g * np, cnt = np;
-    cudaStream_t gs = (g == 0 || serial) ? st : sec.side[g - 1];
-    // WHT features of the group's target frames (all pixels) and source grid points
-    for (int t = t0; t < t0 + cnt; t++) {
+  // WHT features of a group's target frames (all pixels) and source grid points
+  auto group_features = [&](int g, cudaStream_t s) -> ff_status {
+    for (int t = g * np; t < (g + 1) * np; t++) {
       const int i = order_pair[t], j = order_flow[t];
       const uint8_t *img[2] = {io[i].I1, io[i].I2};
-      FF_TRY(launch_features(img[tgtf[j]], io[i].W, io[i].H, rad[j], nullptr, 0, 1, plans[i].feat[j], gs,
-                             true));
+      FF_TRY(launch_features(img[tgtf[j]], io[i].W, io[i].H, rad[j], nullptr, 0, 1,
+                             plans[i].feat[j], s, true));
       FF_TRY(launch_features(img[srcf[j]], io[i].W, io[i].H, rad[j], nullptr, 0, ntop,
-                             plans[i].qfeat[j], gs));
+                             plans[i].qfeat[j], s));
     }
-    mark(gs, g, MK_FEATURES);
-    FF_TRY(launch_kd_build(trees.data() + t0, bd.d_kd + t0, cnt, gs));
-    mark(gs, g, MK_KD_BUILD);
-    if (g != 2 && !serial) FF_TRY(sec.wait_signal(gs));  // census planes ready
+    return FF_OK;
+  };
+  if (kd_merge) {  // every tree in one launch chain, then the groups fork
+    for (int g = 0; g < ngroups; g++) FF_TRY(group_features(g, st));
+    mark(st, 3, MK_FEATURES);
+    FF_TRY(launch_kd_build(trees.data(), bd.d_kd, nprob, st));
+    mark(st, 3, MK_KD_BUILD);
+    if (!serial) FF_TRY(sec.signal(1, st));
+  }
+  for (int g = 0; g < ngroups; g++) {
+    const int t0 = g * np, cnt = np;
+    cudaStream_t gs = group_stream(g);
+    if (!kd_merge) {
+      FF_TRY(group_features(g, gs));
+      mark(gs, g, MK_FEATURES);
+      FF_TRY(launch_kd_build(trees.data() + t0, bd.d_kd + t0, cnt, gs));
+      mark(gs, g, MK_KD_BUILD);
+    } else if (g != 0 && !serial) {
+      FF_TRY(sec.wait(1, gs));  // trees built
+    }
+    if (!serial) FF_TRY(sec.wait(0, gs));  // census planes ready
     // kd query: one launch per run of equal radius
     for (int a0 = t0; a0 < t0 + cnt;) {
       int a1 = a0;
@@ -811,7 +830,7 @@ ff_status ff_set_exec_params(const ff_exec_params *e) {
   auto pow2_or_0 = [](int v) { return v >= 0 && v <= 128 && (v & (v - 1)) == 0; };
   if (!e || e->pass_warps < 1 || e->pass_warps > 8 || !pow2_or_0(e->rs_min_n) ||
       !pow2_or_0(e->wide_min_n) || !pow2_or_0(e->split8_min_n) || e->serial_flows < 0 ||
-      e->serial_flows > 1)
+      e->serial_flows > 1 || e->kd_merge < 0 || e->kd_merge > 1)
     return FF_ERR_INVALID_ARG;
   g_exec = *e;
   return FF_OK;

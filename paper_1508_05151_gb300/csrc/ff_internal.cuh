@@ -362,19 +362,20 @@ struct SearchProblem {
 // Problems of one patch radius, all on stream st (no side stream).
 ff_status run_level_on(const SearchProblem *probs, SearchProblem *dev_desc, int nprob, int tile,
                        int n_rs, int R, uint64_t seed, cudaStream_t st);
-// A fork/join section on the per-device side streams: begin() makes nside (1 or
-// 2) side streams wait for the work enqueued so far on st, end() makes st wait
-// for them. Host threads are serialised between begin() and end(); the
+// A fork/join section on the per-device side streams: begin() makes nside (1..3)
+// side streams wait for the work enqueued so far on st, end() makes st wait
+// for them. Two signal events order work between the streams inside the
+// section: signal(k, s) marks the point reached on stream s, wait(k, s) makes s
+// wait for it. Host threads are serialised between begin() and end(); the
 // destructor ends an open section (error paths).
 struct SideSection {
-  cudaStream_t main = nullptr, side[2] = {nullptr, nullptr};
-  cudaEvent_t join[2] = {nullptr, nullptr};
-  cudaEvent_t signal = nullptr;
+  cudaStream_t main = nullptr, side[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t join[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t sig[2] = {nullptr, nullptr};
   bool locked = false;
   ff_status begin(cudaStream_t st, int nside);
-  // mark the point reached on side stream i; wait_signal makes s wait for it
-  ff_status signal_side(int i);
-  ff_status wait_signal(cudaStream_t s);
+  ff_status signal(int k, cudaStream_t s);
+  ff_status wait(int k, cudaStream_t s);
   ff_status end();
   ~SideSection() {
     if (locked) end();

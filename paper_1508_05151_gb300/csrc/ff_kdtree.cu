@@ -716,6 +716,13 @@ __global__ void __launch_bounds__(256, 3) k_kd_partition(KdBuild *trees, int d) 
       atomicMax(&m[dim * 2 + 1], s_max[c][dim]);
     }
   __syncthreads();
+  if (child_mm) {  // before the scatter: the fence then covers only the atomics above
+    const unsigned last = finish_chunk(T, off, nseg, end, seg0);
+    // warps 2i and 2i + 1 set up the two children of the i-th completed segment
+    const int warp = tid >> 5;
+    if (warp < 2 * CHUNK_SEGS && (last & (1u << (warp >> 1))))
+      seg_sel_init(T, d + 1, 2 * (seg0 + (warp >> 1)) + (warp & 1));
+  }
 #pragma unroll
   for (int r = 0; r < PART_ROUNDS; r++) {
     const int c = combo[r];
@@ -726,13 +733,6 @@ __global__ void __launch_bounds__(256, 3) k_kd_partition(KdBuild *trees, int d) 
     const int lim = side ? m - half : half;
     if (k < lim) dstp[b + side * half + k] = idxs[r];
     else raise_status(T.status, DEV_ERR_KD, sg, d);
-  }
-  if (child_mm) {
-    const unsigned last = finish_chunk(T, off, nseg, end, seg0);
-    // warps 2i and 2i + 1 set up the two children of the i-th completed segment
-    const int warp = tid >> 5;
-    if (warp < 2 * CHUNK_SEGS && (last & (1u << (warp >> 1))))
-      seg_sel_init(T, d + 1, 2 * (seg0 + (warp >> 1)) + (warp & 1));
   }
 }
 

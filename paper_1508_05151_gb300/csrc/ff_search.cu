@@ -800,8 +800,9 @@ __global__ void __launch_bounds__(32 * SPLIT, 32 / SPLIT) k_pass_wide(const Sear
 // the side stream. Both directions are stream-ordered, so the call stays
 // asynchronous and capturable.
 struct SideStream {
-  cudaStream_t s = nullptr, s2 = nullptr;  // s2: second side stream of a SideSection
-  cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr, signal = nullptr;
+  cudaStream_t s = nullptr, s2 = nullptr, s3 = nullptr;  // s2, s3: more streams of a SideSection
+  cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr, join3 = nullptr;
+  cudaEvent_t sig[2] = {nullptr, nullptr};
 };
 static SideStream g_side[64];
 static std::mutex g_side_mu, g_side_enqueue_mu;
@@ -814,10 +815,13 @@ static ff_status side_stream(SideStream **out) {
   if (!S.s) {
     if (cudaStreamCreateWithFlags(&S.s, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&S.s2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S.s3, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&S.join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&S.join2, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&S.signal, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&S.join3, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S.sig[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S.sig[1], cudaEventDisableTiming) != cudaSuccess)
       return FF_ERR_CUDA;
   }
   *out = &S;
@@ -916,12 +920,13 @@ ff_status SideSection::begin(cudaStream_t st, int nside) {
   locked = true;
   SideStream *S = nullptr;
   FF_TRY(side_stream(&S));
-  if (nside < 1 || nside > 2) return FF_ERR_INVALID_ARG;
+  if (nside < 1 || nside > 3) return FF_ERR_INVALID_ARG;
   if (cudaEventRecord(S->fork, st) != cudaSuccess) return FF_ERR_CUDA;
   main = st;
-  signal = S->signal;
-  const cudaStream_t ss[2] = {S->s, S->s2};
-  const cudaEvent_t js[2] = {S->join, S->join2};
+  sig[0] = S->sig[0];
+  sig[1] = S->sig[1];
+  const cudaStream_t ss[3] = {S->s, S->s2, S->s3};
+  const cudaEvent_t js[3] = {S->join, S->join2, S->join3};
   for (int i = 0; i < nside; i++) {
     if (cudaStreamWaitEvent(ss[i], S->fork, 0) != cudaSuccess) return FF_ERR_CUDA;
     side[i] = ss[i];
@@ -930,18 +935,19 @@ ff_status SideSection::begin(cudaStream_t st, int nside) {
   return FF_OK;
 }
 
-ff_status SideSection::signal_side(int i) {
-  if (i < 0 || i > 1 || !side[i]) return FF_ERR_INVALID_ARG;
-  return cudaEventRecord(signal, side[i]) == cudaSuccess ? FF_OK : FF_ERR_CUDA;
+ff_status SideSection::signal(int k, cudaStream_t s) {
+  if (k < 0 || k > 1 || !sig[k]) return FF_ERR_INVALID_ARG;
+  return cudaEventRecord(sig[k], s) == cudaSuccess ? FF_OK : FF_ERR_CUDA;
 }
 
-ff_status SideSection::wait_signal(cudaStream_t s) {
-  return cudaStreamWaitEvent(s, signal, 0) == cudaSuccess ? FF_OK : FF_ERR_CUDA;
+ff_status SideSection::wait(int k, cudaStream_t s) {
+  if (k < 0 || k > 1 || !sig[k]) return FF_ERR_INVALID_ARG;
+  return cudaStreamWaitEvent(s, sig[k], 0) == cudaSuccess ? FF_OK : FF_ERR_CUDA;
 }
 
 ff_status SideSection::end() {
   ff_status r = FF_OK;
-  for (int i = 0; i < 2; i++) {
+  for (int i = 0; i < 3; i++) {
     if (side[i] && (cudaEventRecord(join[i], side[i]) != cudaSuccess ||
                     cudaStreamWaitEvent(main, join[i], 0) != cudaSuccess))
       r = FF_ERR_CUDA;

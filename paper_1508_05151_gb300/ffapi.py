@@ -40,7 +40,7 @@ class ExecParams(C.Structure):
     """ff_exec_params: launch shapes that never change results."""
     _fields_ = [("pass_warps", C.c_int32), ("rs_min_n", C.c_int32), ("wide_min_n", C.c_int32),
                 ("split8_min_n", C.c_int32), ("serial_flows", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("kd_merge", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class NetDesc(C.Structure):
@@ -445,7 +445,8 @@ def probe_l2_gather(buf, mode, sink, blocks, iters):
     return nb.value
 
 
-EXEC_FIELDS = ("pass_warps", "rs_min_n", "wide_min_n", "split8_min_n", "serial_flows")
+EXEC_FIELDS = ("pass_warps", "rs_min_n", "wide_min_n", "split8_min_n", "serial_flows",
+               "kd_merge")
 
 
 def set_exec_params(**kw):

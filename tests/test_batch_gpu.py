@@ -72,6 +72,14 @@ def test_execution_parameters_do_not_change_results():
             got = batch.run(frames)
             for a, b in zip(ref, got):
                 _same(a, b)
+        # stream layouts: flows serialised on one stream, kd trees of all flows in
+        # one launch chain, both
+        ffapi.set_exec_params(**before)
+        for serial, merge in ((1, 0), (0, 1), (1, 1)):
+            ffapi.set_exec_params(serial_flows=serial, kd_merge=merge)
+            got = batch.run(frames)
+            for a, b in zip(ref, got):
+                _same(a, b)
     finally:
         ffapi.set_exec_params(**before)
 
@@ -86,6 +94,8 @@ def test_autotuner_picks_a_candidate(tmp_path, monkeypatch):
         assert r["choice"]["rs_min_n"] in tune.CANDIDATES["rs_min_n"]
         assert r["choice"]["wide_min_n"] in tune.CANDIDATES["wide_min_n"]
         assert r["choice"]["split8_min_n"] in tune.CANDIDATES["split8_min_n"]
+        assert r["choice"]["serial_flows"] in tune.CANDIDATES["serial_flows"]
+        assert r["choice"]["kd_merge"] in tune.CANDIDATES["kd_merge"]
         assert ffapi.get_exec_params() == r["choice"]
         r2 = tune.tune([(128, 96), (97, 71)], reps=1)
         assert r2["cached"] and r2["choice"] == r["choice"]
