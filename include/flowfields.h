@@ -274,7 +274,14 @@ ff_status ff_graph_destroy(ff_graph *g);
  *               after another (so that one kernel can be timed alone)
  *   kd_merge    0: each flow builds its kd trees on its own stream; 1: the trees
  *               of all flows are built in one launch chain (every launch over
- *               all trees) before the flows fork */
+ *               all trees) before the flows fork
+ *   persist_levels  0: every level runs a seeding launch and four pass launches
+ *               per flow; 1 (tiles of edge <= 16): one persistent cooperative
+ *               launch per level runs the seeding and all four passes of every
+ *               pair and flow, over a work list of (pair, flow, tile) items,
+ *               with a grid-wide barrier between the phases whose wait is
+ *               bounded (a wait that runs out sets device status code 3 and the
+ *               launch returns; ff_device_status reports it) */
 typedef struct ff_exec_params {
   int32_t pass_warps;
   int32_t rs_min_n;
@@ -282,9 +289,16 @@ typedef struct ff_exec_params {
   int32_t split8_min_n;
   int32_t serial_flows;
   int32_t kd_merge;
-  int32_t reserved[2];
+  int32_t persist_levels;
+  int32_t reserved[1];
 } ff_exec_params;
 ff_status ff_set_exec_params(const ff_exec_params *e);
+/* Test hook of the persistent level kernel (not in the paper): limit of every
+ * grid-barrier wait in clock cycles (0: the default, 2^31, about a second) and
+ * the index of a block that never reaches the launch's first barrier (-1: none),
+ * so that the other blocks' waits run out. Process-wide, like the execution
+ * parameters. It exists to test the bounded-wait path without faulting the GPU. */
+ff_status ff_set_barrier_test(long long budget_cycles, int skip_block);
 ff_status ff_get_exec_params(ff_exec_params *e);
 
 /* Learned proposal net (not in the paper). A small convolutional net reads the

@@ -45,7 +45,7 @@ static ff_status evals_ptr(unsigned long long **out) {
   return FF_OK;
 }
 
-static ff_exec_params g_exec = {4, 0, 1, 2, 0, 0, {0, 0}};
+static ff_exec_params g_exec = {4, 0, 1, 2, 0, 0, 0, {0}};
 const ff_exec_params &exec_params() { return g_exec; }
 
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
@@ -213,6 +213,8 @@ struct BatchDesc {
   KdBuild *d_kd;
   KdQuery *d_q;
   SearchProblem *d_sp;
+  int32_t *tile_base;  // per level: tile prefix sums of the persistent level kernel
+  unsigned *bar;       // per level: its grid-barrier counter (64 words apart)
 };
 static BatchDesc plan_batch(Arena &a, int np, const int *Ws, const int *Hs, const ff_params *p,
                             PairPlan *plans) {
@@ -222,6 +224,8 @@ static BatchDesc plan_batch(Arena &a, int np, const int *Ws, const int *Hs, cons
   d.d_kd = a.take<KdBuild>(3 * (size_t)np);
   d.d_q = a.take<KdQuery>(3 * (size_t)np);
   d.d_sp = a.take<SearchProblem>(3 * (size_t)np * MAXLV);
+  d.tile_base = a.take<int32_t>((size_t)MAXLV * 2 * (3 * (size_t)np + 1));
+  d.bar = a.take<unsigned>((size_t)MAXLV * 64);
   return d;
 }
 
@@ -273,6 +277,9 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
   // caller's stream before the groups fork
   const bool serial = exec_params().serial_flows != 0;
   const bool kd_merge = exec_params().kd_merge != 0;
+  // persist_levels: one persistent launch per level over all problems (tiles of
+  // edge <= 16, the CTA-per-tile pass form)
+  const bool persist = exec_params().persist_levels != 0 && p->tile <= 16;
   SideSection sec;
   if (!serial) FF_TRY(sec.begin(st, 3));
   auto group_stream = [&](int g) { return (g == 0 || serial) ? st : sec.side[g - 1]; };
@@ -333,6 +340,36 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
     ccur[t] = P.ca[j];
     coth[t] = P.cb[j];
   }
+  // problem t's state at level lv: seeded from the coarser state (in cur) into the
+  // other buffer below the coarsest level; the finest level writes the output flow
+  auto level_problem = [&](int t, int lv) {
+    const int i = order_pair[t], j = order_flow[t], n = 1 << lv;
+    const PairPlan &P = plans[i];
+    const int W = io[i].W, H = io[i].H;
+    SearchProblem &s = sp[t];
+    s = SearchProblem{};
+    s.src = make_planes(P.planes[srcf[j]][lv], W, H, n);
+    s.tgt = make_planes(P.planes[tgtf[j]][lv], W, H, n);
+    s.r = rad[j];
+    s.flow_id = j;
+    if (lv == k) {
+      s.flow_coarse = nullptr;
+      s.flow_a = cur[t];
+      s.cost_a = ccur[t];
+      s.flow_b = oth[t];
+      s.cost_b = coth[t];
+    } else {
+      s.flow_coarse = cur[t];
+      s.flow_a = oth[t];
+      s.cost_a = coth[t];
+      s.flow_b = cur[t];
+      s.cost_b = ccur[t];
+    }
+    if (lv == 0) {
+      s.flow_final = (uint32_t *)(io[i].flows + 2 * (size_t)W * H * j);
+      s.cost_final = s.cost_a;
+    }
+  };
   // WHT features of a group's target frames (all pixels) and source grid points
   auto group_features = [&](int g, cudaStream_t s) -> ff_status {
     for (int t = g * np; t < (g + 1) * np; t++) {
@@ -372,37 +409,10 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
       a0 = a1;
     }
     mark(gs, g, MK_KD_QUERY);
+    if (persist) continue;  // the levels of all groups run below, one launch each
     // levels n = 2^k .. 1; the state alternates between the two buffers per level
     for (int lv = k; lv >= 0; lv--) {
-      const int n = 1 << lv;
-      for (int t = t0; t < t0 + cnt; t++) {
-        const int i = order_pair[t], j = order_flow[t];
-        const PairPlan &P = plans[i];
-        const int W = io[i].W, H = io[i].H;
-        SearchProblem &s = sp[t];
-        s = SearchProblem{};
-        s.src = make_planes(P.planes[srcf[j]][lv], W, H, n);
-        s.tgt = make_planes(P.planes[tgtf[j]][lv], W, H, n);
-        s.r = rad[j];
-        s.flow_id = j;
-        if (lv == k) {
-          s.flow_coarse = nullptr;
-          s.flow_a = cur[t];
-          s.cost_a = ccur[t];
-          s.flow_b = oth[t];
-          s.cost_b = coth[t];
-        } else {  // seed from the coarser state (in cur) into the other buffer
-          s.flow_coarse = cur[t];
-          s.flow_a = oth[t];
-          s.cost_a = coth[t];
-          s.flow_b = cur[t];
-          s.cost_b = ccur[t];
-        }
-        if (lv == 0) {
-          s.flow_final = (uint32_t *)(io[i].flows + 2 * (size_t)W * H * j);
-          s.cost_final = s.cost_a;
-        }
-      }
+      for (int t = t0; t < t0 + cnt; t++) level_problem(t, lv);
       FF_TRY(run_level_on(sp.data() + t0, bd.d_sp + (size_t)nprob * lv + t0, cnt, p->tile,
                           p->n_rs, p->R, p->seed, gs));
       mark(gs, g, MK_LEVEL + lv);
@@ -414,6 +424,20 @@ static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *w
     }
   }
   if (!serial) FF_TRY(sec.end());
+  if (persist) {  // one persistent launch per level over every problem of the batch
+    for (int lv = k; lv >= 0; lv--) {
+      for (int t = 0; t < nprob; t++) level_problem(t, lv);
+      FF_TRY(run_level_persistent(sp.data(), bd.d_sp + (size_t)nprob * lv, nprob,
+                                  bd.tile_base + (size_t)lv * 2 * (nprob + 1), bd.bar + 64 * lv,
+                                  (DeviceStatus *)ws, p->tile, p->n_rs, p->R, p->seed, st));
+      mark(st, 3, MK_LEVEL + lv);
+      if (lv != k)
+        for (int t = 0; t < nprob; t++) {
+          std::swap(cur[t], oth[t]);
+          std::swap(ccur[t], coth[t]);
+        }
+    }
+  }
   mark(st, 3, MK_JOINED);
 
   for (int i = 0; i < np; i++) {
@@ -830,9 +854,16 @@ ff_status ff_set_exec_params(const ff_exec_params *e) {
   auto pow2_or_0 = [](int v) { return v >= 0 && v <= 128 && (v & (v - 1)) == 0; };
   if (!e || e->pass_warps < 1 || e->pass_warps > 8 || !pow2_or_0(e->rs_min_n) ||
       !pow2_or_0(e->wide_min_n) || !pow2_or_0(e->split8_min_n) || e->serial_flows < 0 ||
-      e->serial_flows > 1 || e->kd_merge < 0 || e->kd_merge > 1)
+      e->serial_flows > 1 || e->kd_merge < 0 || e->kd_merge > 1 || e->persist_levels < 0 ||
+      e->persist_levels > 1)
     return FF_ERR_INVALID_ARG;
   g_exec = *e;
+  return FF_OK;
+}
+
+ff_status ff_set_barrier_test(long long budget_cycles, int skip_block) {
+  if (budget_cycles < 0 || skip_block < -1) return FF_ERR_INVALID_ARG;
+  set_barrier_test(budget_cycles, skip_block);
   return FF_OK;
 }
 

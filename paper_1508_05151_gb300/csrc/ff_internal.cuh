@@ -381,6 +381,15 @@ struct SideSection {
     if (locked) end();
   }
 };
+// One persistent cooperative launch for the whole level of every problem (tile
+// <= 16): seeding, four passes with the random searches, bounded grid barriers.
+// tile_base: device int32 [2 (nprob + 1)] scratch; bar: a device counter.
+ff_status run_level_persistent(const SearchProblem *probs, SearchProblem *dev_desc, int nprob,
+                               int32_t *tile_base, unsigned *bar, DeviceStatus *status, int tile,
+                               int n_rs, int R, uint64_t seed, cudaStream_t st);
+// Test hook of the persistent kernel's barrier: wait limit in clock cycles (0:
+// the default) and a block that never reaches the first barrier (-1: none).
+void set_barrier_test(long long budget_cycles, int skip_block);
 ff_status run_level(const SearchProblem *probs, SearchProblem *dev_desc, int nprob, int tile,
                     int n_rs, int R, uint64_t seed, cudaStream_t st);
 

@@ -26,6 +26,8 @@
 // transposed planes), through L1/L2.
 #include <atomic>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "ff_internal.cuh"
 
@@ -37,34 +39,43 @@ __constant__ int c_pass_src[4][2][2] = {
 
 // Level seeding. One 16-lane group per 2x2 block of grid points (grid-stride):
 // the even-even point takes the coarse flow and its E_d at this level, the other
-// three start unset.
+// three start unset. seed_block handles block c (coarse grid point c) of P.
+template <int R>
+__device__ __forceinline__ void seed_block(const SearchProblem &P, int c, int l16, unsigned gmask) {
+  const int NX = P.src.NX, NY = P.src.NY, n = P.src.n;
+  const int NXc = (NX + 1) >> 1;
+  const int gx = (c % NXc) * 2, gy = (c / NXc) * 2;
+  if (l16 >= 1 && l16 <= 3) {
+    const int ox = gx + (l16 & 1), oy = gy + (l16 >> 1);
+    if (ox < NX && oy < NY) {
+      P.flow_a[(size_t)oy * NX + ox] = 0;
+      P.cost_a[(size_t)oy * NX + ox] = COST_UNSET;
+    }
+  }
+  const uint32_t f = P.flow_coarse[c];
+  const int px = gx * n, py = gy * n;
+  const int tx = clampi(px + flow_dx(f), 0, P.src.W - 1), ty = clampi(py + flow_dy(f), 0, P.src.H - 1);
+  const int cost = group_cost<R>(plane_centre(P.src, px, py), P.src.pitch,
+                                 plane_centre(P.tgt, tx, ty), P.tgt.pitch, l16, gmask);
+  if (l16 == 0) {
+    P.flow_a[(size_t)gy * NX + gx] = pack_flow(tx - px, ty - py);
+    P.cost_a[(size_t)gy * NX + gx] = cost;
+  }
+}
+// Coarse grid points (= 2x2 blocks of this level) of a seeded problem.
+__device__ __forceinline__ int seed_blocks(const SearchProblem &P) {
+  return ((P.src.NX + 1) >> 1) * ((P.src.NY + 1) >> 1);
+}
+
 template <int R>
 __global__ void __launch_bounds__(256) k_seed(const SearchProblem *probs) {
   const SearchProblem &P = probs[blockIdx.y];
-  const int NX = P.src.NX, NY = P.src.NY, n = P.src.n;
-  const int NXc = (NX + 1) >> 1, Gc = NXc * ((NY + 1) >> 1);  // = the coarse grid
+  const int Gc = seed_blocks(P);
   const int l16 = threadIdx.x & 15;
   const unsigned gmask = 0xffffu << (threadIdx.x & 16);
   const int stride = (gridDim.x * blockDim.x) >> 4;
-  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 4; c < Gc; c += stride) {
-    const int gx = (c % NXc) * 2, gy = (c / NXc) * 2;
-    if (l16 >= 1 && l16 <= 3) {
-      const int ox = gx + (l16 & 1), oy = gy + (l16 >> 1);
-      if (ox < NX && oy < NY) {
-        P.flow_a[(size_t)oy * NX + ox] = 0;
-        P.cost_a[(size_t)oy * NX + ox] = COST_UNSET;
-      }
-    }
-    const uint32_t f = P.flow_coarse[c];
-    const int px = gx * n, py = gy * n;
-    const int tx = clampi(px + flow_dx(f), 0, P.src.W - 1), ty = clampi(py + flow_dy(f), 0, P.src.H - 1);
-    const int cost = group_cost<R>(plane_centre(P.src, px, py), P.src.pitch,
-                                   plane_centre(P.tgt, tx, ty), P.tgt.pitch, l16, gmask);
-    if (l16 == 0) {
-      P.flow_a[(size_t)gy * NX + gx] = pack_flow(tx - px, ty - py);
-      P.cost_a[(size_t)gy * NX + gx] = cost;
-    }
-  }
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 4; c < Gc; c += stride)
+    seed_block<R>(P, c, l16, gmask);
 }
 
 // Random search of pass s as a kernel of its own (levels where the execution
@@ -603,18 +614,25 @@ __device__ __forceinline__ int part_full(const uint32_t *sc, int swp, const uint
   return a0 + a1;
 }
 
+// Tiles of pass s of problem P (the odd passes' tiles are shifted by T/2).
+__device__ __forceinline__ int pass_tiles(const SearchProblem &P, int T, int s) {
+  const int off = (s & 1) * (T >> 1);
+  return ((P.src.NX + off + T - 1) / T) * ((P.src.NY + off + T - 1) / T);
+}
+
+// One tile (index `tile` < pass_tiles) of pass cfg.s of problem P by the whole
+// CTA (32 * SPLIT threads); smem holds the tile layout and then four evaluation
+// counters.
 template <int R, int SPLIT>
-__global__ void __launch_bounds__(32 * SPLIT, 32 / SPLIT) k_pass_wide(const SearchProblem *probs, PassCfg cfg) {
+__device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg &cfg, int tile,
+                                          uint32_t *smem) {
   constexpr int WIDE_THREADS = 32 * SPLIT;
-  extern __shared__ uint32_t smem[];
-  const SearchProblem &P = probs[blockIdx.y];
   const int t = threadIdx.x, lane = t & 31;
   const int Gx = P.src.NX, Gy = P.src.NY, n = P.src.n, log2n = P.src.log2n;
   const int W = P.src.W, H = P.src.H;
   const int T = cfg.tile, off = (cfg.s & 1) * (T >> 1);
-  const int ntx = (Gx + off + T - 1) / T, nty = (Gy + off + T - 1) / T;
-  if ((int)blockIdx.x >= ntx * nty) return;  // whole CTA
-  const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
+  const int ntx = (Gx + off + T - 1) / T;
+  const int tx = tile % ntx, ty = tile / ntx;
   const int x0 = max(tx * T - off, 0), x1 = min(tx * T - off + T, Gx);
   const int y0 = max(ty * T - off, 0), y1 = min(ty * T - off + T, Gy);
   const int tw = x1 - x0, th = y1 - y0;
@@ -794,6 +812,118 @@ __global__ void __launch_bounds__(32 * SPLIT, 32 / SPLIT) k_pass_wide(const Sear
   }
 }
 
+template <int R, int SPLIT>
+__global__ void __launch_bounds__(32 * SPLIT, 32 / SPLIT) k_pass_wide(const SearchProblem *probs, PassCfg cfg) {
+  extern __shared__ uint32_t smem[];
+  const SearchProblem &P = probs[blockIdx.y];
+  if ((int)blockIdx.x >= pass_tiles(P, cfg.tile, cfg.s)) return;  // whole CTA
+  wide_tile<R, SPLIT>(P, cfg, blockIdx.x, smem);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent per-level kernel (batched form): one cooperative launch runs a whole
+// hierarchy level for every problem (pair and flow) of a batch: the seeding of
+// all problems, then pass 0 .. 3 over a work list of (problem, tile) items (the
+// random searches inside the passes), a grid-wide barrier between phases. Items
+// are taken in blockIdx order with a grid stride; problems of two patch radii
+// RA and RB (the r and r2 flows) share the launch. The tiled schedule and the
+// results are those of the per-pass kernels.
+struct LevelCfg {
+  int nprob;
+  const int32_t *tile_base;  // [2][nprob + 1]: prefix sums of the tiles of even / odd passes
+  int tile, n_rs, R;
+  uint64_t seed;
+  int words_per_tile;        // shared words of the larger of the two tile layouts
+  int seeded;                // 1: problems are seeded from flow_coarse first
+  unsigned *bar;             // grid-barrier arrival counter, zero at launch
+  long long budget;          // clock cycles one barrier wait may take
+  int skip_block;            // test hook: this block never reaches the first barrier (-1: none)
+  DeviceStatus *status;
+  unsigned long long *evals_a, *evals_b;  // evaluation counters of radius RA / RB, or nullptr
+};
+
+// Grid-wide barrier number k (1-based) of the launch: every CTA adds one to the
+// counter and waits until k * gridDim.x arrivals. The wait is bounded by
+// lc.budget cycles: when it runs out the CTA raises DEV_ERR_TIMEOUT (block,
+// barrier) and gets false, so it can leave. Every thread of the CTA calls it.
+__device__ bool grid_barrier(const LevelCfg &lc, int k) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(lc.bar, 1u);
+    const unsigned target = (unsigned)k * gridDim.x;
+    const long long t0 = clock64();
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(lc.bar) : "memory");
+      if (v >= target) break;
+      if (clock64() - t0 > lc.budget) {
+        ok = 0;
+        raise_status(lc.status, DEV_ERR_TIMEOUT, blockIdx.x, k);
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Register budget: 85 per thread (6 CTAs of 128 threads or 3 of 256 per SM): the
+// two radii's tile paths in one function need more than the per-pass kernels' 64.
+template <int RA, int RB, int SPLIT>
+__global__ void __launch_bounds__(32 * SPLIT, 24 / SPLIT) k_level(const SearchProblem *probs, LevelCfg lc) {
+  extern __shared__ uint32_t smem[];
+  int nbar = 0;
+  if (lc.seeded) {
+    const int l16 = threadIdx.x & 15;
+    const unsigned gmask = 0xffffu << (threadIdx.x & 16);
+    const int g0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 4, ng = (gridDim.x * blockDim.x) >> 4;
+    for (int j = 0; j < lc.nprob; j++) {
+      const SearchProblem &P = probs[j];
+      const int Gc = seed_blocks(P);
+      if (RA == RB || P.r == RA) {
+        for (int c = g0; c < Gc; c += ng) seed_block<RA>(P, c, l16, gmask);
+      } else {
+        for (int c = g0; c < Gc; c += ng) seed_block<RB>(P, c, l16, gmask);
+      }
+    }
+    if ((int)blockIdx.x == lc.skip_block) return;
+    if (!grid_barrier(lc, ++nbar)) return;
+  }
+  for (int s = 0; s < 4; s++) {
+    PassCfg cfg{s, lc.tile, (s < 3 && s < lc.n_rs) ? 1 : 0, lc.R, lc.seed, s == 3, lc.words_per_tile,
+                nullptr};
+    const int32_t *tb = lc.tile_base + (s & 1) * (lc.nprob + 1);
+    const int total = tb[lc.nprob];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+      int lo = 0, hi = lc.nprob - 1;  // the problem holding the item: last j with tb[j] <= item
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tb[mid] <= item) lo = mid;
+        else hi = mid - 1;
+      }
+      const SearchProblem &P = probs[lo];
+      if (RA == RB || P.r == RA) {
+        cfg.evals = lc.evals_a;
+        wide_tile<RA, SPLIT>(P, cfg, item - tb[lo], smem);
+      } else {
+        cfg.evals = lc.evals_b;
+        wide_tile<RB, SPLIT>(P, cfg, item - tb[lo], smem);
+      }
+      __syncthreads();  // the tile's shared memory is reused by the next item
+    }
+    if (s < 3) {
+      if (!lc.seeded && s == 0 && (int)blockIdx.x == lc.skip_block) return;
+      if (!grid_barrier(lc, ++nbar)) return;
+    }
+  }
+}
+
 // One side stream per device, created on first use, lets problems of a second
 // patch radius (a separate kernel instantiation) run concurrently with the first:
 // fork with an event recorded on the caller's stream, join with one recorded on
@@ -958,6 +1088,129 @@ ff_status SideSection::end() {
     g_side_enqueue_mu.unlock();
   }
   return r;
+}
+
+// ---------------------------------------------------------- persistent level --
+static std::atomic<long long> g_bar_budget{0};
+static std::atomic<int> g_bar_skip{-1};
+constexpr long long BAR_BUDGET_DEFAULT = 1ll << 31;  // clock cycles, about a second
+
+void set_barrier_test(long long budget_cycles, int skip_block) {
+  g_bar_budget.store(budget_cycles);
+  g_bar_skip.store(skip_block);
+}
+
+// k_level<RA, RB, SPLIT> for one radius (RA == RB, r = 1..8) or the paper's pair
+// (8, 6); nullptr for other pairs.
+template <int SPLIT>
+static const void *level_kernel_split(int ra, int rb) {
+  if (ra == rb) {
+    switch (ra) {
+      case 1: return (const void *)k_level<1, 1, SPLIT>;
+      case 2: return (const void *)k_level<2, 2, SPLIT>;
+      case 3: return (const void *)k_level<3, 3, SPLIT>;
+      case 4: return (const void *)k_level<4, 4, SPLIT>;
+      case 5: return (const void *)k_level<5, 5, SPLIT>;
+      case 6: return (const void *)k_level<6, 6, SPLIT>;
+      case 7: return (const void *)k_level<7, 7, SPLIT>;
+      case 8: return (const void *)k_level<8, 8, SPLIT>;
+      default: return nullptr;
+    }
+  }
+  if (ra == 8 && rb == 6) return (const void *)k_level<8, 6, SPLIT>;
+  return nullptr;
+}
+static const void *level_kernel(int ra, int rb, int split) {
+  return split == 8 ? level_kernel_split<8>(ra, rb) : level_kernel_split<4>(ra, rb);
+}
+
+ff_status run_level_persistent(const SearchProblem *probs, SearchProblem *dev, int nprob,
+                               int32_t *tile_base, unsigned *bar, DeviceStatus *status, int tile,
+                               int n_rs, int R, uint64_t seed, cudaStream_t st) {
+  if (nprob <= 0) return FF_OK;
+  if (tile > 16 || tile < 2) return FF_ERR_INVALID_ARG;
+  int ra = probs[0].r, rb = ra;
+  for (int j = 1; j < nprob; j++)
+    if (probs[j].r != ra) {
+      if (rb != ra && probs[j].r != rb) return FF_ERR_INVALID_ARG;  // at most two radii
+      rb = probs[j].r;
+    }
+  if (ra < rb) std::swap(ra, rb);
+  const int log2n = probs[0].src.log2n;
+  const int s8 = exec_params().split8_min_n;
+  const int split = (s8 > 0 && probs[0].src.n >= s8) ? 8 : 4;
+  const void *fn = level_kernel(ra, rb, split);
+  if (!fn) {  // no fused kernel for these two radii: one launch per run of equal radius
+    for (int i = 0; i < nprob;) {
+      int j = i;
+      while (j < nprob && probs[j].r == probs[i].r) j++;
+      FF_TRY(run_level_persistent(probs + i, dev + i, j - i, tile_base, bar, status, tile, n_rs, R,
+                                  seed, st));
+      i = j;
+    }
+    return FF_OK;
+  }
+  FF_TRY(upload_desc(probs, dev, nprob, st));
+  std::vector<int32_t> tb(2 * (size_t)(nprob + 1));
+  for (int par = 0; par < 2; par++) {
+    int32_t *b = tb.data() + par * (nprob + 1);
+    b[0] = 0;
+    for (int j = 0; j < nprob; j++) {
+      const int off = par * (tile >> 1);
+      b[j + 1] = b[j] + ((probs[j].src.NX + off + tile - 1) / tile) *
+                            ((probs[j].src.NY + off + tile - 1) / tile);
+    }
+  }
+  FF_TRY(upload_desc(tb.data(), tile_base, 2 * (nprob + 1), st));
+  const int words = max(TileLayout(tile, ra).words(), TileLayout(tile, rb).words());
+  const size_t smem = sizeof(uint32_t) * ((size_t)words + 4);
+  FF_TRY(smem_opt_in(fn, smem));
+  int nsm = 0, occ = 0;
+  FF_TRY(sm_count(&nsm));
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * split, smem) != cudaSuccess ||
+      occ < 1) {
+    (void)cudaGetLastError();
+    return FF_ERR_CUDA;
+  }
+  const int items = max(tb[nprob], tb[2 * nprob + 1]);
+  const int grid = max(1, min(items, occ * nsm));
+  if (cudaMemsetAsync(bar, 0, sizeof(unsigned), st) != cudaSuccess) return FF_ERR_CUDA;
+  LevelCfg lc{};
+  lc.nprob = nprob;
+  lc.tile_base = tile_base;
+  lc.tile = tile;
+  lc.n_rs = n_rs;
+  lc.R = R;
+  lc.seed = seed;
+  lc.words_per_tile = words;
+  lc.seeded = probs[0].flow_coarse != nullptr;
+  lc.bar = bar;
+  const long long bud = g_bar_budget.load();
+  lc.budget = bud > 0 ? bud : BAR_BUDGET_DEFAULT;
+  lc.skip_block = g_bar_skip.load();
+  lc.status = status;
+  lc.evals_a = prof_evals(ra, log2n);
+  lc.evals_b = prof_evals(rb, log2n);
+  const SearchProblem *dp = dev;
+  void *args[] = {(void *)&dp, (void *)&lc};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(32 * split);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // every block resident: the barriers can complete
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (prof_enabled()) prof_begin(st, log2n);
+  if (cudaLaunchKernelExC(&cfg, fn, args) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return FF_ERR_CUDA;
+  }
+  count_launch(1);
+  if (prof_enabled()) prof_end(st);
+  return FF_OK;
 }
 
 ff_status run_level_on(const SearchProblem *probs, SearchProblem *dev, int nprob, int tile,

@@ -40,7 +40,8 @@ class ExecParams(C.Structure):
     """ff_exec_params: launch shapes that never change results."""
     _fields_ = [("pass_warps", C.c_int32), ("rs_min_n", C.c_int32), ("wide_min_n", C.c_int32),
                 ("split8_min_n", C.c_int32), ("serial_flows", C.c_int32),
-                ("kd_merge", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("kd_merge", C.c_int32), ("persist_levels", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 class NetDesc(C.Structure):
@@ -123,6 +124,7 @@ def lib():
                              vp], i32),
             "ff_net_proposals": ([C.POINTER(NetDesc), vp, i32, i32, i32, C.c_float, vp, vp], i32),
             "ff_get_exec_params": ([C.POINTER(ExecParams)], i32),
+            "ff_set_barrier_test": ([C.c_longlong, i32], i32),
             "ff_device_status": ([vp, C.POINTER(C.c_uint32), C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int32), vp], i32),
             "ff_profile_enable": ([i32], i32),
@@ -446,7 +448,7 @@ def probe_l2_gather(buf, mode, sink, blocks, iters):
 
 
 EXEC_FIELDS = ("pass_warps", "rs_min_n", "wide_min_n", "split8_min_n", "serial_flows",
-               "kd_merge")
+               "kd_merge", "persist_levels")
 
 
 def set_exec_params(**kw):

@@ -3,8 +3,10 @@
 It times candidate launch shapes on the caller's workload and keeps the fastest.
 Only parameters that leave every result unchanged are tuned: tiles per CTA of the
 propagation kernel, from which level spacing on the random search runs as a
-kernel of its own, and from which spacing on the propagation runs one CTA per
-tile (and with how many threads per candidate). The tile edge T of the parallel
+kernel of its own, from which spacing on the propagation runs one CTA per tile
+(and with how many threads per candidate), and the launch layout: flows on one or
+several streams, the kd trees of all flows in one launch chain, one persistent
+launch per level. The tile edge T of the parallel
 schedule is part of the method's definition and stays as given. The search is
 coordinate-wise, one parameter at a time in the order of CANDIDATES. Choices are cached in a small JSON file
 keyed by GPU name, image sizes and method parameters.
@@ -19,7 +21,8 @@ import torch
 from . import ffapi, synth
 
 CANDIDATES = dict(wide_min_n=(0, 1, 2, 4, 8), split8_min_n=(0, 1, 2, 4, 8), pass_warps=(1, 2, 4, 8),
-                  rs_min_n=(0, 1, 2, 4, 8), serial_flows=(0, 1), kd_merge=(0, 1))
+                  rs_min_n=(0, 1, 2, 4, 8), serial_flows=(0, 1), kd_merge=(0, 1),
+                  persist_levels=(0, 1))
 _CACHE = os.environ.get("FF_TUNE_CACHE",
                         os.path.join(os.path.expanduser("~"), ".cache", "flowfields_tune.json"))
 
@@ -86,7 +89,7 @@ def tune(sizes, params=None, frames=None, reps=3, use_cache=True, seed=0):
     before = ffapi.get_exec_params()
     timings = {}
     choice = dict(pass_warps=4, rs_min_n=0, wide_min_n=1, split8_min_n=0, serial_flows=0,
-                  kd_merge=0)
+                  kd_merge=0, persist_levels=0)
     best_t = None
     for name in CANDIDATES:  # one parameter at a time
         for v in CANDIDATES[name]:

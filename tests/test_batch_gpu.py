@@ -80,6 +80,14 @@ def test_execution_parameters_do_not_change_results():
             got = batch.run(frames)
             for a, b in zip(ref, got):
                 _same(a, b)
+        # one persistent launch per level (4 and 8 threads per candidate), alone and
+        # with the other stream layouts
+        for s8, serial, merge in ((0, 0, 0), (1, 0, 0), (2, 0, 1), (4, 1, 0)):
+            ffapi.set_exec_params(persist_levels=1, split8_min_n=s8, serial_flows=serial,
+                                  kd_merge=merge)
+            got = batch.run(frames)
+            for a, b in zip(ref, got):
+                _same(a, b)
     finally:
         ffapi.set_exec_params(**before)
 
@@ -96,8 +104,59 @@ def test_autotuner_picks_a_candidate(tmp_path, monkeypatch):
         assert r["choice"]["split8_min_n"] in tune.CANDIDATES["split8_min_n"]
         assert r["choice"]["serial_flows"] in tune.CANDIDATES["serial_flows"]
         assert r["choice"]["kd_merge"] in tune.CANDIDATES["kd_merge"]
+        assert r["choice"]["persist_levels"] in tune.CANDIDATES["persist_levels"]
         assert ffapi.get_exec_params() == r["choice"]
         r2 = tune.tune([(128, 96), (97, 71)], reps=1)
         assert r2["cached"] and r2["choice"] == r["choice"]
     finally:
+        ffapi.set_exec_params(**before)
+
+
+def test_persistent_levels_graph_and_radius_mix():
+    """The persistent level kernel inside a captured graph equals the direct
+    per-pass form, for the paper's radii (8, 6: one fused launch per level) and
+    for a radius pair without a fused kernel (5, 3: one launch per radius)."""
+    _, frames = _frames(50)
+    before = ffapi.get_exec_params()
+    try:
+        for params in (None, dict(r=5, r2=3)):
+            ffapi.set_exec_params(**before)
+            ref = [{k: v.clone() for k, v in o.items()}
+                   for o in ffapi.FlowFieldsBatch(SIZES, params).run(frames)]
+            ffapi.set_exec_params(persist_levels=1)
+            g = ffapi.FlowFieldsBatch(SIZES, params, graph=True)
+            for _ in range(2):  # capture, then replay
+                got = g.run(frames)
+                for a, b in zip(ref, got):
+                    _same(a, b)
+    finally:
+        ffapi.set_exec_params(**before)
+
+
+def test_persistent_barrier_wait_runs_out_and_reports():
+    """Bounded-wait path of the persistent level kernel: the test hook keeps one
+    block away from the first grid barrier and sets a tiny wait limit, so every
+    other block's wait runs out. The launch must return, the device status word
+    must say timeout (code 3), and the GPU must stay usable: the next run without
+    the hook is correct again."""
+    p = synth.pair_shift(60, W=128, H=96)
+    I1, I2 = torch.from_numpy(p["I1"]).cuda(), torch.from_numpy(p["I2"]).cuda()
+    ff = ffapi.FlowFields(128, 96)
+    ref = {k: v.clone() for k, v in ff.run(I1, I2).items()}
+    torch.cuda.synchronize()
+    before = ffapi.get_exec_params()
+    L = ffapi.lib()
+    try:
+        ffapi.set_exec_params(persist_levels=1)
+        assert L.ff_set_barrier_test(200000, 0) == 0  # ~0.1 ms at 2 GHz
+        ff.run(I1, I2)
+        code, x, y = ff.device_status()
+        assert code == 3, (code, x, y)
+        assert L.ff_set_barrier_test(0, -1) == 0
+        got = ff.run(I1, I2)
+        code, _, _ = ff.device_status()
+        assert code == 0
+        _same(ref, got)
+    finally:
+        L.ff_set_barrier_test(0, -1)
         ffapi.set_exec_params(**before)
