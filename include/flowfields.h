@@ -65,6 +65,8 @@ typedef struct ff_params {
   int32_t tile; /* tile edge T of the parallel schedule (even, 2..32) */
   int32_t n_rs; /* random-search steps per level, after passes 0..n_rs-1 (0..3) */
   int32_t K;    /* proposals per coarsest grid point for the forward flow (0..8) */
+  int32_t color; /* 0: the input RGB channels; 1: integer CIELab (ff_rgb_to_lab) of
+                    both frames before every other step (Sec. 3.1, 3.3) */
   uint64_t seed; /* seed of the counter-based random search */
 } ff_params;
 
@@ -80,6 +82,17 @@ ff_status ff_params_preset(ff_params *p, int preset);
 
 /* Workspace bytes needed by ff_flow_fields for a W x H pair (host-only call). */
 ff_status ff_workspace_size(int W, int H, const ff_params *p, size_t *bytes);
+
+/* Sec. 3.1 / 3.3: the paper computes WHT features and census in CIELab. Integer
+ * CIELab of an 8-bit sRGB image (D65 white, IEC 61966-2-1 primaries), exact
+ * after a 256-entry decoding table lin = round(65536 g(v/255)) (g the sRGB
+ * decoding curve): t = (row . lin + 8192) >> 14 with the white-normalised
+ * sRGB->XYZ rows in Q14 (each summing to 16384); f(t) = the largest y with
+ * y^3 <= t * 2^32 when t * 29^3 > 6^3 * 65536, else (29*841*t + 108*4*65536 +
+ * 1566) / 3132; out = (L * 255/100, a + 128, b + 128) with L = 116 f_Y - 16,
+ * a = 500 (f_X - f_Y), b = 200 (f_Y - f_Z) in units of 65536, rounded half up
+ * and clamped to [0, 255]. img, out: H x W x 3 uint8 (device). */
+ff_status ff_rgb_to_lab(const uint8_t *img, int W, int H, uint8_t *out, void *stream);
 
 /* Sec. 3.2: the smoothed full-resolution image I^n: area downsampling by n
  * (block mean, (sum + cnt/2) / cnt over the in-image part of each block),
@@ -162,13 +175,15 @@ ff_status ff_search_level(const uint32_t *census_src, const uint32_t *census_tgt
 /* Sec. 3.4 / 3.5: outlier filtering of the forward flow F against the backward
  * flows Fb1 (radius r) and Fb2 (radius r2), all H x W x 2.
  *   Eq. 5: e_j = |F(p) + Fb_j(p + F(p))|^2; the pixel passes when e_1 and e_2 are
- *          both below eps^2; err_sum = e_1 + e_2.
+ *          both below eps^2; err_sum = e_1 + e_2 (squared errors; a diagnostic
+ *          output: INT32_MAX for a target outside the image).
  *   Region filter: passing pixels whose 4-neighbours differ in flow by less than
  *          3 px form regions; a region of fewer than s pixels is removed when one
  *          of its pixels has a 4-neighbour rejected by Eq. 5 whose flow is within
  *          3 px of it. Result: valid [H][W] (0/1).
  *   Sparsification: in each aligned 3x3 block with at least e valid pixels the
- *          one with the smallest err_sum (first in raster order on ties) is kept:
+ *          one whose two consistency errors sum to the least, sqrt(e_1) +
+ *          sqrt(e_2) compared exactly (first in raster order on ties), is kept:
  *          mask [H][W] and rows (x, y, dx, dy) int32 in block raster order in
  *          sparse [ceil(W/3)*ceil(H/3)][4]; *n_sparse (device int32) = row count.
  * Workspace: ff_filter_workspace_size. */
@@ -293,12 +308,18 @@ typedef struct ff_exec_params {
   int32_t reserved[1];
 } ff_exec_params;
 ff_status ff_set_exec_params(const ff_exec_params *e);
-/* Test hook of the persistent level kernel (not in the paper): limit of every
- * grid-barrier wait in clock cycles (0: the default, 2^31, about a second) and
- * the index of a block that never reaches the launch's first barrier (-1: none),
- * so that the other blocks' waits run out. Process-wide, like the execution
- * parameters. It exists to test the bounded-wait path without faulting the GPU. */
-ff_status ff_set_barrier_test(long long budget_cycles, int skip_block);
+/* Test hooks of the bounded waits (not in the paper); they exist to test the
+ * timeout paths without faulting the GPU. Process-wide, like the execution
+ * parameters; (0, -1, 0) turns them off.
+ *   budget_cycles    limit of every grid-barrier wait of the persistent level
+ *                    kernel in clock cycles (0: the default, 2^31, about a second)
+ *   skip_block       a block of that kernel that never reaches the launch's first
+ *                    barrier (-1: none), so that the other blocks' waits run out
+ *   net_stall_polls  > 0: every tensor-core kernel of the proposal net first waits
+ *                    that many polls on an mbarrier that nothing completes, then
+ *                    reports the timeout, issues no MMA and returns
+ * A wait that runs out sets device status code 3 (ff_device_status). */
+ff_status ff_set_wait_test(long long budget_cycles, int skip_block, int net_stall_polls);
 ff_status ff_get_exec_params(ff_exec_params *e);
 
 /* Learned proposal net (not in the paper). A small convolutional net reads the

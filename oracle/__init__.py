@@ -40,14 +40,14 @@ def build(force=False):
 
 class Params(C.Structure):
     _fields_ = [(n, C.c_int32) for n in
-                ("k", "r", "r2", "leaf", "R", "eps", "e", "s", "tile", "n_rs", "K")] + \
+                ("k", "r", "r2", "leaf", "R", "eps", "e", "s", "tile", "n_rs", "K", "color")] + \
                [("seed", C.c_uint64)]
 
 
 def default_params(**kw):
     """Sec. 4 parameters (k=3, R=1, l=8, r=8, r2=6; Sintel eps/e/s = 5/4/50),
     tile T=16 for the parallel schedule, 3 random-search steps, no proposals."""
-    d = dict(k=3, r=8, r2=6, leaf=8, R=1, eps=5, e=4, s=50, tile=16, n_rs=3, K=0, seed=0)
+    d = dict(k=3, r=8, r2=6, leaf=8, R=1, eps=5, e=4, s=50, tile=16, n_rs=3, K=0, color=0, seed=0)
     d.update(kw)
     return d
 
@@ -86,9 +86,15 @@ def lib():
             L.ffo_search_level.argtypes = [u32, u32, ci, ci, ci, ci, i32, ci, ci, ci,
                                            C.c_uint64, ci, i32, i32]
             L.ffo_search_level.restype = C.c_int64
-            L.ffo_consistency.argtypes = [i32, i32, i32, ci, ci, ci, u8, i32]
+            L.ffo_consistency.argtypes = [i32, i32, i32, ci, ci, ci, u8, i32, i32, i32]
+            L.ffo_sqrt_sum_less.argtypes = [C.c_int64] * 4
+            L.ffo_lab_gamma_table.argtypes = [i32]
+            L.ffo_lab_matrix.argtypes = [i32]
+            L.ffo_lab_f.argtypes = [C.c_int32]
+            L.ffo_lab_f.restype = C.c_int32
+            L.ffo_rgb_to_lab.argtypes = [u8, ci, ci, u8]
             L.ffo_region_filter.argtypes = [i32, u8, ci, ci, ci, u8]
-            L.ffo_sparsify.argtypes = [u8, i32, i32, ci, ci, ci, i32, u8]
+            L.ffo_sparsify.argtypes = [u8, i32, i32, i32, ci, ci, ci, i32, u8]
             L.ffo_flow_fields.argtypes = [u8, u8, ci, ci, C.POINTER(Params), i32, ci, i32, u8,
                                           i32, i32, u8, i64]
             _lib = L
@@ -237,6 +243,31 @@ def kd_init(tgt_feat, src_img, r, leaf, Cs, Ct, n, proposals=None):
     return flow, cost, int(ev)
 
 
+def lab_gamma_table():
+    t = np.empty(256, np.int32)
+    lib().ffo_lab_gamma_table(_p(t, C.c_int32))
+    return t
+
+
+def lab_matrix():
+    m = np.empty(9, np.int32)
+    lib().ffo_lab_matrix(_p(m, C.c_int32))
+    return m.reshape(3, 3)
+
+
+def lab_f(t):
+    return int(lib().ffo_lab_f(int(t)))
+
+
+def rgb_to_lab(img):
+    """Integer CIELab (L * 255/100, a + 128, b + 128 as uint8) of an sRGB image."""
+    img = _c(img, np.uint8)
+    H, W = img.shape[:2]
+    out = np.empty((H, W, 3), np.uint8)
+    lib().ffo_rgb_to_lab(_p(img, C.c_uint8), W, H, _p(out, C.c_uint8))
+    return out
+
+
 def splitmix64(z):
     return int(lib().ffo_splitmix64(C.c_uint64(z)))
 
@@ -268,14 +299,24 @@ def search_level(Cs, Ct, n, r, flow_coarse=None, flow=None, cost=None, tile=16, 
     return flow, cost, int(ev)
 
 
-def consistency(F, Fb1, Fb2, eps):
+def consistency(F, Fb1, Fb2, eps, errors=False):
+    """Eq. 5 check: (valid_cc, err_sum = e1 + e2), and with errors=True also the
+    squared errors e1, e2 against the two backward flows."""
     F, Fb1, Fb2 = _c(F, np.int32), _c(Fb1, np.int32), _c(Fb2, np.int32)
     H, W = F.shape[:2]
     v = np.empty((H, W), np.uint8)
     e = np.empty((H, W), np.int32)
+    e1 = np.empty((H, W), np.int32)
+    e2 = np.empty((H, W), np.int32)
     lib().ffo_consistency(_p(F, C.c_int32), _p(Fb1, C.c_int32), _p(Fb2, C.c_int32), W, H, eps,
-                          _p(v, C.c_uint8), _p(e, C.c_int32))
-    return v, e
+                          _p(v, C.c_uint8), _p(e, C.c_int32), _p(e1, C.c_int32),
+                          _p(e2, C.c_int32))
+    return (v, e, e1, e2) if errors else (v, e)
+
+
+def sqrt_sum_less(a, b, c, d):
+    """sqrt(a) + sqrt(b) < sqrt(c) + sqrt(d), exactly, for integers in [0, 2^28)."""
+    return bool(lib().ffo_sqrt_sum_less(int(a), int(b), int(c), int(d)))
 
 
 def region_filter(F, valid_cc, s):
@@ -287,13 +328,15 @@ def region_filter(F, valid_cc, s):
     return out
 
 
-def sparsify(valid, err_sum, F, e):
-    valid, err_sum, F = _c(valid, np.uint8), _c(err_sum, np.int32), _c(F, np.int32)
+def sparsify(valid, e1, e2, F, e):
+    """Sec. 3.5: per 3x3 block with >= e valid pixels the one with the smallest
+    sqrt(e1) + sqrt(e2) (raster-first on ties)."""
+    valid, e1, e2, F = _c(valid, np.uint8), _c(e1, np.int32), _c(e2, np.int32), _c(F, np.int32)
     H, W = valid.shape
     sp = np.empty((((W + 2) // 3) * ((H + 2) // 3), 4), np.int32)
     mask = np.empty((H, W), np.uint8)
-    n = lib().ffo_sparsify(_p(valid, C.c_uint8), _p(err_sum, C.c_int32), _p(F, C.c_int32), W, H,
-                           e, _p(sp, C.c_int32), _p(mask, C.c_uint8))
+    n = lib().ffo_sparsify(_p(valid, C.c_uint8), _p(e1, C.c_int32), _p(e2, C.c_int32),
+                           _p(F, C.c_int32), W, H, e, _p(sp, C.c_int32), _p(mask, C.c_uint8))
     return sp[:n].copy(), mask
 
 

@@ -10,7 +10,7 @@
  * silent or garbled the reading taken is stated beside the code.
  *
  * Conventions
- *   images       uint8, H x W x 3 (RGB), row major
+ *   images       uint8, H x W x 3 (RGB, or L a b after the colour step), row major
  *   census       uint32 per pixel, H x W
  *   level grids  at spacing n the grid has Gx = ceil(W/n) by Gy = ceil(H/n) points;
  *                grid point (gx, gy) sits on pixel (n*gx, n*gy)
@@ -34,6 +34,88 @@ static int64_t floor_div(int64_t a, int64_t b) {
   int64_t q = a / b;
   if ((a % b != 0) && (a < 0)) q -= 1;
   return q;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.1 / 3.3: the paper computes WHT features and census in CIELab.      */
+/* Integer CIELab of an 8-bit sRGB image (reading: D65 white, sRGB primaries   */
+/* of IEC 61966-2-1; everything after the 256-entry decoding table is exact   */
+/* integer arithmetic, so both implementations can agree bit for bit):         */
+/*   1. decode: lin = round(65536 * g(v / 255)), g(c) = c / 12.92 for          */
+/*      c <= 0.04045, else ((c + 0.055) / 1.055)^2.4 (1.0 = 65536)             */
+/*   2. X/Xn, Y/Yn, Z/Zn: the sRGB->XYZ matrix with each row divided by the     */
+/*      white point's component, in Q14, every row rounded so that it sums to  */
+/*      exactly 16384 (the residual on its largest entry): a grey pixel gives  */
+/*      three equal values. t = (row . lin + 8192) >> 14.                     */
+/*   3. f(t) in Q16 (t / 65536 in [0, 1]): the largest y with y^3 <= t * 2^32   */
+/*      (= floor(65536 cbrt(t / 65536))) when t / 65536 > (6/29)^3, i.e.       */
+/*      t * 29^3 > 6^3 * 65536; else the line t / (3 (6/29)^2) + 4/29, i.e.    */
+/*      (29 * 841 * t + 108 * 4 * 65536) / (108 * 29), rounded half up.        */
+/*   4. L = 116 f(Y) - 16, a = 500 (f(X) - f(Y)), b = 200 (f(Y) - f(Z));        */
+/*      stored as uint8: L * 255 / 100, a + 128, b + 128, each rounded half up */
+/*      and clamped to [0, 255].                                              */
+/* ------------------------------------------------------------------------ */
+static const double SRGB_TO_XYZ[3][3] = {
+    {0.4124, 0.3576, 0.1805}, {0.2126, 0.7152, 0.0722}, {0.0193, 0.1192, 0.9505}};
+
+/* Step 1: the decoding table. */
+void ffo_lab_gamma_table(int32_t *lin) {
+  for (int v = 0; v < 256; v++) {
+    double c = v / 255.0;
+    double g = c <= 0.04045 ? c / 12.92 : pow((c + 0.055) / 1.055, 2.4);
+    lin[v] = (int32_t)floor(g * 65536.0 + 0.5);
+  }
+}
+
+/* Step 2: the white-normalised matrix rows in Q14, each summing to 16384. */
+void ffo_lab_matrix(int32_t *m /* [3][3] */) {
+  for (int i = 0; i < 3; i++) {
+    double white = SRGB_TO_XYZ[i][0] + SRGB_TO_XYZ[i][1] + SRGB_TO_XYZ[i][2];
+    int sum = 0, big = 0;
+    for (int j = 0; j < 3; j++) {
+      m[3 * i + j] = (int32_t)floor(SRGB_TO_XYZ[i][j] / white * 16384.0 + 0.5);
+      sum += m[3 * i + j];
+      if (SRGB_TO_XYZ[i][j] > SRGB_TO_XYZ[i][big]) big = j;
+    }
+    m[3 * i + big] += 16384 - sum;
+  }
+}
+
+/* Step 3: f(t), t in [0, 65536]. The cube root by bisection on integers. */
+int32_t ffo_lab_f(int32_t t) {
+  if ((int64_t)t * 24389 > (int64_t)216 * 65536) { /* t/65536 > (6/29)^3 */
+    int64_t target = (int64_t)t << 32, lo = 0, hi = 65536; /* hi^3 = 2^48 >= target */
+    while (lo < hi) { /* largest y with y^3 <= target */
+      int64_t mid = (lo + hi + 1) / 2;
+      if (mid * mid * mid <= target) lo = mid;
+      else hi = mid - 1;
+    }
+    return (int32_t)lo;
+  }
+  return (int32_t)floor_div((int64_t)29 * 841 * t + (int64_t)108 * 4 * 65536 + 1566, 3132);
+}
+
+static int lab_round_clamp(int64_t num, int64_t den, int offset) { /* round half up */
+  int64_t v = floor_div(2 * num + den, 2 * den) + offset;
+  return v < 0 ? 0 : (v > 255 ? 255 : (int)v);
+}
+
+/* Steps 1-4 for every pixel: img (RGB) -> out (L, a, b as uint8), H x W x 3. */
+void ffo_rgb_to_lab(const uint8_t *img, int W, int H, uint8_t *out) {
+  int32_t lin[256], m[9];
+  ffo_lab_gamma_table(lin);
+  ffo_lab_matrix(m);
+  for (size_t p = 0; p < (size_t)W * H; p++) {
+    int64_t c[3] = {lin[img[3 * p]], lin[img[3 * p + 1]], lin[img[3 * p + 2]]};
+    int32_t f[3];
+    for (int i = 0; i < 3; i++) {
+      int64_t t = (m[3 * i] * c[0] + m[3 * i + 1] * c[1] + m[3 * i + 2] * c[2] + 8192) >> 14;
+      f[i] = ffo_lab_f((int32_t)t);
+    }
+    out[3 * p] = (uint8_t)lab_round_clamp(((int64_t)116 * f[1] - 16 * 65536) * 255, 100 * 65536, 0);
+    out[3 * p + 1] = (uint8_t)lab_round_clamp((int64_t)500 * (f[0] - f[1]), 65536, 128);
+    out[3 * p + 2] = (uint8_t)lab_round_clamp((int64_t)200 * (f[1] - f[2]), 65536, 128);
+  }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -580,12 +662,16 @@ int64_t ffo_search_level(const uint32_t *Cs, const uint32_t *Ct, int W, int H, i
 /* ------------------------------------------------------------------------ */
 /* Sec. 3.4: outlier filtering.                                               */
 /* Eq. 5 two-way check. Reading: the norm is Euclidean and compared strictly; */
-/* with integer flows |.|^2 < eps^2 is used. err_sum = e1 + e2 (squared      */
-/* errors), used by the sparsification. A target outside the image (never    */
-/* produced by the search) fails the check with err_sum = INT32_MAX.          */
+/* with integer flows |.|^2 < eps^2 is used. Per pixel the squared errors     */
+/* e_j = |F(p) + F^b_j(p + F(p))|^2 (e1, e2; may be NULL) and err_sum =       */
+/* e1 + e2 (a diagnostic output). A target outside the image (never produced  */
+/* by the search) fails the check; its errors are INT32_MAX.                  */
 /* ------------------------------------------------------------------------ */
+static int32_t clamp_i32(int64_t v) { return (int32_t)(v > INT32_MAX ? INT32_MAX : v); }
+
 void ffo_consistency(const int32_t *F, const int32_t *Fb1, const int32_t *Fb2, int W, int H,
-                     int eps, uint8_t *valid_cc, int32_t *err_sum) {
+                     int eps, uint8_t *valid_cc, int32_t *err_sum, int32_t *e1_out,
+                     int32_t *e2_out) {
   for (int y = 0; y < H; y++)
     for (int x = 0; x < W; x++) {
       size_t p = (size_t)y * W + x;
@@ -593,6 +679,8 @@ void ffo_consistency(const int32_t *F, const int32_t *Fb1, const int32_t *Fb2, i
       if (qx < 0 || qx >= W || qy < 0 || qy >= H) {
         valid_cc[p] = 0;
         err_sum[p] = INT32_MAX;
+        if (e1_out) e1_out[p] = INT32_MAX;
+        if (e2_out) e2_out[p] = INT32_MAX;
         continue;
       }
       size_t q = (size_t)qy * W + qx;
@@ -600,8 +688,44 @@ void ffo_consistency(const int32_t *F, const int32_t *Fb1, const int32_t *Fb2, i
       int64_t b0 = F[2 * p] + Fb2[2 * q], b1 = F[2 * p + 1] + Fb2[2 * q + 1];
       int64_t e1 = a0 * a0 + a1 * a1, e2 = b0 * b0 + b1 * b1;
       valid_cc[p] = (e1 < (int64_t)eps * eps) && (e2 < (int64_t)eps * eps);
-      err_sum[p] = (int32_t)((e1 + e2) > INT32_MAX ? INT32_MAX : (e1 + e2));
+      err_sum[p] = clamp_i32(e1 + e2);
+      if (e1_out) e1_out[p] = clamp_i32(e1);
+      if (e2_out) e2_out[p] = clamp_i32(e2);
     }
+}
+
+/* Is sqrt(a) + sqrt(b) < sqrt(c) + sqrt(d)?  Exact for integers 0 <= a..d < 2^28
+ * (the squared errors of pixels that pass Eq. 5 are below eps^2 <= 10^6).
+ * Both sides are non-negative, so squaring keeps the order:
+ *   a + b + 2 sqrt(ab)  <  c + d + 2 sqrt(cd)
+ *   <=>  u - v < t   with u = 2 sqrt(ab) = sqrt(4ab), v = sqrt(4cd), t = c + d - a - b.
+ * u - v has the sign of 4ab - 4cd, which settles every case except two, where
+ * one more squaring is needed:
+ *   u < v, t < 0:   v - u > -t  <=>  v > u + (-t)  <=>  (4cd - 4ab - t^2) > 2(-t) u
+ *   u > v, t > 0:   u - v <  t  <=>  u < v + t     <=>  (4ab - 4cd - t^2) < 2 t v
+ * and a comparison  L > 2 s sqrt(Z)  (s >= 0) holds iff L > 0 and L^2 > 4 s^2 Z.
+ * The products are formed in 128-bit integers. */
+typedef __int128 i128;
+
+static int gt_twice_sqrt(i128 L, i128 s, i128 Z) { /* L > 2 s sqrt(Z) */
+  if (L <= 0) return 0;
+  return L * L > 4 * s * s * Z;
+}
+
+int ffo_sqrt_sum_less(int64_t a, int64_t b, int64_t c, int64_t d) {
+  const i128 X = (i128)4 * a * b, Y = (i128)4 * c * d, t = (i128)c + d - a - b;
+  if (X == Y) return t > 0;
+  if (X < Y) {
+    if (t >= 0) return 1;
+    return gt_twice_sqrt(Y - X - t * t, -t, X);
+  }
+  if (t <= 0) return 0;
+  /* 4ab - 4cd - t^2 < 2 t sqrt(4cd)  <=>  not (4ab - 4cd - t^2 >= 2 t sqrt(4cd)) */
+  {
+    const i128 L = X - Y - t * t;
+    if (L < 0) return 1;
+    return L * L < 4 * t * t * Y;
+  }
 }
 
 static int close3(const int32_t *F, size_t p, size_t q) {
@@ -652,11 +776,12 @@ void ffo_region_filter(const int32_t *F, const uint8_t *valid_cc, int W, int H, 
 
 /* Sec. 3.5 sparsification. Aligned 3x3 blocks (partial blocks at the right and
  * bottom edge included); a block with at least e surviving pixels keeps the one
- * with the smallest err_sum, the first in raster order within the block on
- * ties. Output rows (x, y, dx, dy) in block raster order; mask marks them.
- * Returns the number of rows. */
-int ffo_sparsify(const uint8_t *valid, const int32_t *err_sum, const int32_t *F, int W, int H,
-                 int e, int32_t *sparse, uint8_t *mask) {
+ * for which the sum of its two consistency-check errors |.| (Eq. 5), i.e.
+ * sqrt(e1) + sqrt(e2), is the smallest, the first in raster order within the
+ * block on ties. Output rows (x, y, dx, dy) in block raster order; mask marks
+ * them. Returns the number of rows. */
+int ffo_sparsify(const uint8_t *valid, const int32_t *e1, const int32_t *e2, const int32_t *F,
+                 int W, int H, int e, int32_t *sparse, uint8_t *mask) {
   int cnt_out = 0;
   memset(mask, 0, (size_t)W * H);
   for (int by = 0; by < (H + 2) / 3; by++)
@@ -667,7 +792,7 @@ int ffo_sparsify(const uint8_t *valid, const int32_t *err_sum, const int32_t *F,
           int p = y * W + x;
           if (!valid[p]) continue;
           cnt++;
-          if (best < 0 || err_sum[p] < err_sum[best]) best = p;
+          if (best < 0 || ffo_sqrt_sum_less(e1[p], e2[p], e1[best], e2[best])) best = p;
         }
       if (cnt >= e && best >= 0) {
         mask[best] = 1;
@@ -688,6 +813,7 @@ int ffo_sparsify(const uint8_t *valid, const int32_t *err_sum, const int32_t *F,
 /* ------------------------------------------------------------------------ */
 typedef struct {
   int k, r, r2, leaf, R, eps, e, s, tile, n_rs, K;
+  int color; /* 0: the RGB channels; 1: integer CIELab (Sec. 3.1 / 3.3) */
   uint64_t seed;
 } ffo_params;
 
@@ -741,10 +867,22 @@ static void *run_flow(void *arg) {
  * proposals: NULL or int32 [Gy][Gx][K][2] at the coarsest grid (forward flow
  * only). threads > 1 runs the three flows concurrently. Returns the sparse
  * count; evals (optional) receives the number of E_d evaluations. */
-int ffo_flow_fields(const uint8_t *I1, const uint8_t *I2, int W, int H, const ffo_params *P,
-                    const int32_t *proposals, int threads, int32_t *flows, uint8_t *valid,
-                    int32_t *err_sum, int32_t *sparse, uint8_t *mask, int64_t *evals) {
+int ffo_flow_fields(const uint8_t *I1_in, const uint8_t *I2_in, int W, int H,
+                    const ffo_params *P, const int32_t *proposals, int threads, int32_t *flows,
+                    uint8_t *valid, int32_t *err_sum, int32_t *sparse, uint8_t *mask,
+                    int64_t *evals) {
   size_t N = (size_t)W * H;
+  /* the colour space of every later step: the input channels or CIELab */
+  uint8_t *lab1 = NULL, *lab2 = NULL;
+  const uint8_t *I1 = I1_in, *I2 = I2_in;
+  if (P->color == 1) {
+    lab1 = malloc(N * 3);
+    lab2 = malloc(N * 3);
+    ffo_rgb_to_lab(I1_in, W, H, lab1);
+    ffo_rgb_to_lab(I2_in, W, H, lab2);
+    I1 = lab1;
+    I2 = lab2;
+  }
   int nl = P->k + 1;
   uint32_t *C1[16], *C2[16];
   uint8_t *sm = malloc(N * 3);
@@ -775,9 +913,15 @@ int ffo_flow_fields(const uint8_t *I1, const uint8_t *I2, int W, int H, const ff
     free(C2[lv]);
   }
   uint8_t *vcc = malloc(N);
-  ffo_consistency(flows, flows + 2 * N, flows + 4 * N, W, H, P->eps, vcc, err_sum);
+  int32_t *e1 = malloc(sizeof(int32_t) * N), *e2 = malloc(sizeof(int32_t) * N);
+  ffo_consistency(flows, flows + 2 * N, flows + 4 * N, W, H, P->eps, vcc, err_sum, e1, e2);
   ffo_region_filter(flows, vcc, W, H, P->s, valid);
   free(vcc);
   if (evals) *evals = J[0].evals + J[1].evals + J[2].evals;
-  return ffo_sparsify(valid, err_sum, flows, W, H, P->e, sparse, mask);
+  int n = ffo_sparsify(valid, e1, e2, flows, W, H, P->e, sparse, mask);
+  free(e1);
+  free(e2);
+  free(lab1);
+  free(lab2);
+  return n;
 }

@@ -104,6 +104,7 @@ ff_status check_params(const ff_params *p) {
   if (p->eps < 1 || p->eps > 1000 || p->e < 1 || p->e > 9 || p->s < 0) return FF_ERR_INVALID_ARG;
   if (p->tile < 2 || p->tile > MAX_TILE || (p->tile & 1)) return FF_ERR_INVALID_ARG;
   if (p->n_rs < 0 || p->n_rs > 3 || p->K < 0 || p->K > MAX_K) return FF_ERR_INVALID_ARG;
+  if (p->color < 0 || p->color > 1) return FF_ERR_INVALID_ARG;
   return FF_OK;
 }
 
@@ -149,6 +150,7 @@ static ff_status clear_status(void *ws, cudaStream_t st) {
 constexpr int MAXLV = 5;
 
 struct PairPlan {
+  uint8_t *lab[2];  // both frames in CIELab (params.color == 1), else null
   uint32_t *planes[2][MAXLV];
   uint8_t *sm;
   void *smooth_scratch;
@@ -164,6 +166,7 @@ struct PairPlan {
 // Per-pair scratch (everything but the workspace header and the descriptors).
 static void plan_pair_body(Arena &a, int W, int H, const ff_params *p, PairPlan &P) {
   const size_t N = (size_t)W * H;
+  for (int f = 0; f < 2; f++) P.lab[f] = p->color == 1 ? a.take<uint8_t>(N * 3) : nullptr;
   for (int f = 0; f < 2; f++)
     for (int lv = 0; lv <= p->k; lv++) P.planes[f][lv] = a.take<uint32_t>(planes_words(W, H, 1 << lv));
   P.sm = a.take<uint8_t>(N * 3);
@@ -244,18 +247,28 @@ struct PairIO {
 // features, filtering) run per pair; the kd builds, kd queries and every search
 // level of one flow (forward r, backward r, backward r2) take that flow's problems
 // of all pairs in the same launches, each flow on a stream of its own.
-static ff_status run_pairs(int np, const PairIO *io, const ff_params *p, void *ws, size_t ws_bytes,
-                           cudaStream_t st) {
+static ff_status run_pairs(int np, const PairIO *io_in, const ff_params *p, void *ws,
+                           size_t ws_bytes, cudaStream_t st) {
   std::vector<int> Ws(np), Hs(np);
   for (int i = 0; i < np; i++) {
-    Ws[i] = io[i].W;
-    Hs[i] = io[i].H;
+    Ws[i] = io_in[i].W;
+    Hs[i] = io_in[i].H;
   }
   std::vector<PairPlan> plans(np);
   Arena a(ws, ws_bytes);
   const BatchDesc bd = plan_batch(a, np, Ws.data(), Hs.data(), p, plans.data());
   if (!a.fits()) return FF_ERR_WORKSPACE;
   FF_TRY(clear_status(ws, st));
+  // the colour space of every later step: the input channels, or both frames
+  // converted to CIELab first
+  std::vector<PairIO> io(io_in, io_in + np);
+  if (p->color == 1)
+    for (int i = 0; i < np; i++) {
+      FF_TRY(launch_rgb_to_lab(io_in[i].I1, io[i].W, io[i].H, plans[i].lab[0], st));
+      FF_TRY(launch_rgb_to_lab(io_in[i].I2, io[i].W, io[i].H, plans[i].lab[1], st));
+      io[i].I1 = plans[i].lab[0];
+      io[i].I2 = plans[i].lab[1];
+    }
   const int k = p->k, ntop = 1 << k;
   const int srcf[3] = {0, 1, 1}, tgtf[3] = {1, 0, 0}, rad[3] = {p->r, p->r, p->r2};
 
@@ -498,6 +511,7 @@ ff_status ff_params_preset(ff_params *p, int preset) {
   p->tile = 16;
   p->n_rs = 3;
   p->K = 0;
+  p->color = 0;
   p->seed = 0;
   switch (preset) {
     case FF_PRESET_SINTEL: p->eps = 5; p->e = 4; p->s = 50; break;
@@ -861,9 +875,9 @@ ff_status ff_set_exec_params(const ff_exec_params *e) {
   return FF_OK;
 }
 
-ff_status ff_set_barrier_test(long long budget_cycles, int skip_block) {
-  if (budget_cycles < 0 || skip_block < -1) return FF_ERR_INVALID_ARG;
-  set_barrier_test(budget_cycles, skip_block);
+ff_status ff_set_wait_test(long long budget_cycles, int skip_block, int net_stall_polls) {
+  if (budget_cycles < 0 || skip_block < -1 || net_stall_polls < 0) return FF_ERR_INVALID_ARG;
+  set_wait_test(budget_cycles, skip_block, net_stall_polls);
   return FF_OK;
 }
 

@@ -140,10 +140,10 @@ __global__ void k_region_apply(const uint8_t *__restrict__ vcc, int N, int s,
   valid[p] = v;
 }
 
-// Per 3x3 block: survivor count and the smallest-err pixel (raster-first).
 // Sec. 3.5 sparsification, in three parallel steps that keep the output in block
 // raster order: k_blocks picks each aligned 3x3 block's survivor (>= e valid
-// points, smallest err_sum, raster-first on ties) and counts the picks of its
+// points, the smallest sum of the two consistency errors, raster-first on ties)
+// and counts the picks of its
 // CTA; k_pick_scan turns the per-CTA counts into offsets; k_pick_write writes
 // every pick at its CTA's offset plus its rank inside the CTA.
 constexpr int PICK_CTA = 256;
@@ -162,8 +162,44 @@ __device__ __forceinline__ int cta_exclusive_rank(bool flag, int *s_warp, int &t
   return before + __popc(b & ((1u << lane) - 1));
 }
 
+// Sec. 3.5 ranks the samples of a block by the sum of their two consistency-check
+// errors |F(p) + Fb_j(p + F(p))| (Eq. 5): sqrt(e1) + sqrt(e2) of the squared
+// errors. sum_sqrt_lt(a, b, c, d) is sqrt(a) + sqrt(b) < sqrt(c) + sqrt(d),
+// exactly, for 0 <= a..d < 2^28 (a passing pixel has e_j < eps^2 <= 10^6):
+// squaring both non-negative sides gives sqrt(4ab) - sqrt(4cd) < (c+d) - (a+b);
+// the left side has the sign of 4ab - 4cd, and the two undecided cases are
+// squared once more, in 128-bit integers.
+__device__ __forceinline__ bool sum_sqrt_lt(long long a, long long b, long long c, long long d) {
+  const __int128 p = (__int128)4 * a * b, q = (__int128)4 * c * d;
+  const __int128 t = (__int128)(c + d) - (__int128)(a + b);
+  if (p == q) return t > 0;
+  if (p < q) {  // negative left side
+    if (t >= 0) return true;
+    const __int128 m = q - p - t * t;  // need sqrt(q) - sqrt(p) > -t: m > -2t sqrt(p)
+    return m > 0 && m * m > 4 * t * t * p;
+  }
+  if (t <= 0) return false;
+  const __int128 m = p - q - t * t;  // need sqrt(p) - sqrt(q) < t: m < 2t sqrt(q)
+  return m < 0 || m * m < 4 * t * t * q;
+}
+
+// Squared consistency errors of a pixel that passed Eq. 5 (target inside the image).
+__device__ __forceinline__ void pixel_errors(const uint32_t *F, const uint32_t *Fb1,
+                                             const uint32_t *Fb2, int W, int p, long long &e1,
+                                             long long &e2) {
+  const uint32_t f = F[p];
+  const int q = (p / W + flow_dy(f)) * W + (p % W + flow_dx(f));
+  const uint32_t b1 = Fb1[q], b2 = Fb2[q];
+  const long long a0 = flow_dx(f) + flow_dx(b1), a1 = flow_dy(f) + flow_dy(b1);
+  const long long c0 = flow_dx(f) + flow_dx(b2), c1 = flow_dy(f) + flow_dy(b2);
+  e1 = a0 * a0 + a1 * a1;
+  e2 = c0 * c0 + c1 * c1;
+}
+
 __global__ void __launch_bounds__(PICK_CTA) k_blocks(const uint8_t *__restrict__ valid,
-                                                     const int32_t *__restrict__ err, int W, int H,
+                                                     const uint32_t *__restrict__ F,
+                                                     const uint32_t *__restrict__ Fb1,
+                                                     const uint32_t *__restrict__ Fb2, int W, int H,
                                                      int e, int32_t *__restrict__ pick,
                                                      int32_t *__restrict__ cta_count) {
   __shared__ int s_warp[PICK_CTA / 32];
@@ -173,12 +209,19 @@ __global__ void __launch_bounds__(PICK_CTA) k_blocks(const uint8_t *__restrict__
   if (b < BX * BY) {
     const int bx = b % BX, by = b / BX;
     int cnt = 0, best = -1;
+    long long be1 = 0, be2 = 0;
     for (int y = 3 * by; y < min(3 * by + 3, H); y++)
       for (int x = 3 * bx; x < min(3 * bx + 3, W); x++) {
         const int p = y * W + x;
         if (!valid[p]) continue;
         cnt++;
-        if (best < 0 || err[p] < err[best]) best = p;
+        long long e1, e2;
+        pixel_errors(F, Fb1, Fb2, W, p, e1, e2);
+        if (best < 0 || sum_sqrt_lt(e1, e2, be1, be2)) {
+          best = p;
+          be1 = e1;
+          be2 = e2;
+        }
       }
     sel = (cnt >= e) ? best : -1;
     pick[b] = sel;
@@ -269,7 +312,7 @@ ff_status launch_filter(const uint32_t *F, const uint32_t *Fb1, const uint32_t *
   FF_CHECK_LAUNCH();
   k_region_apply<<<g, B, 0, st>>>(vcc, N, s, parent, size, touch, valid, mask);
   FF_CHECK_LAUNCH();
-  k_blocks<<<ncta, PICK_CTA, 0, st>>>(valid, err_sum, W, H, e, pick, cta_count);
+  k_blocks<<<ncta, PICK_CTA, 0, st>>>(valid, F, Fb1, Fb2, W, H, e, pick, cta_count);
   FF_CHECK_LAUNCH();
   k_pick_scan<<<1, 1024, 0, st>>>(cta_count, ncta, n_sparse);
   FF_CHECK_LAUNCH();

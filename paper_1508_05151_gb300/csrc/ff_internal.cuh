@@ -298,6 +298,9 @@ ff_status launch_smooth(const uint8_t *img, int W, int H, int n, uint8_t *out, v
 ff_status launch_census(const uint8_t *imgn, int W, int H, int n, uint32_t *out, cudaStream_t st);
 ff_status launch_planes(const uint32_t *census, Planes P, cudaStream_t st);
 
+// -------------------------------------------------------------- colour -------
+ff_status launch_rgb_to_lab(const uint8_t *img, int W, int H, uint8_t *out, cudaStream_t st);
+
 // ----------------------------------------------------------- features --------
 // pts != NULL: explicit (x, y) list; else grid of spacing grid_n (1 = all pixels).
 // packed (all pixels only): 16-word packed rows instead of [28] int32 rows.
@@ -387,9 +390,12 @@ struct SideSection {
 ff_status run_level_persistent(const SearchProblem *probs, SearchProblem *dev_desc, int nprob,
                                int32_t *tile_base, unsigned *bar, DeviceStatus *status, int tile,
                                int n_rs, int R, uint64_t seed, cudaStream_t st);
-// Test hook of the persistent kernel's barrier: wait limit in clock cycles (0:
-// the default) and a block that never reaches the first barrier (-1: none).
-void set_barrier_test(long long budget_cycles, int skip_block);
+// Test hooks of the bounded waits: the persistent kernel's barrier wait limit in
+// clock cycles (0: the default) and a block that never reaches the first barrier
+// (-1: none); net_stall > 0 makes every tcgen05 kernel of the net first wait that
+// many polls on an mbarrier nothing completes (0: off).
+void set_wait_test(long long budget_cycles, int skip_block, int net_stall);
+int net_stall_polls();
 ff_status run_level(const SearchProblem *probs, SearchProblem *dev_desc, int nprob, int tile,
                     int n_rs, int R, uint64_t seed, cudaStream_t st);
 

@@ -72,6 +72,7 @@ struct ConvArgs {
   __nv_bfloat16 *out_bf;       // [B][N][H][W] bf16 of relu(out) (or of out*mask) or null
   const float *mask_pre;       // dgrad: lower layer's pre-activation [B][N][H][W]; grad *= (pre > 0)
   int relu;
+  int stall;                   // test hook: > 0 polls of a wait that nothing completes
 };
 
 // ------------------------------------------------ forward / dgrad, tcgen05 --
@@ -114,8 +115,9 @@ __device__ __forceinline__ int umma_off(int row, int k) {
   return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (unsigned it = 0; it < UMMA_WAIT_LIMIT; it++) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity,
+                                          unsigned limit = UMMA_WAIT_LIMIT) {
+  for (unsigned it = 0; it < limit; it++) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -170,7 +172,12 @@ __global__ void __launch_bounds__(128) k_conv_umma(ConvArgs a, DeviceStatus *sta
   const int bn = tid & 63, bh = tid >> 6;
   const __nv_bfloat16 *actb = pb >= 0 ? a.act + (size_t)pb * a.C * HW : a.act;
   const uint32_t idesc = umma_idesc(UMMA_M, UMMA_N);
-  const int nsteps = a.Kp / UMMA_K;
+  int nsteps = a.Kp / UMMA_K;
+  if (a.stall > 0) {  // test hook: stage 0's barrier before any MMA (nothing completes it)
+    if (!mbar_wait(smem_u32(&mbar[0]), 0u, (unsigned)a.stall)) s_fail = 1;
+    __syncthreads();
+    if (s_fail) nsteps = 0;  // no MMA in flight: the accumulator is freed below
+  }
   uint32_t phase[2] = {0u, 0u};
   for (int step = 0; step < nsteps; step++) {
     const int st = step & 1, k0 = step * UMMA_K;
@@ -277,6 +284,7 @@ struct WgradArgs {
   float *dW;                 // [N][K]
   float *db;                 // [N]
   int pix_per_cta;
+  int stall;                 // test hook: > 0 polls of a wait that nothing completes
 };
 
 // Weight gradient on tcgen05: the transposed product D[k][n] = sum_m A[m][k] G[m][n]
@@ -329,7 +337,12 @@ __global__ void __launch_bounds__(128, 8) k_wgrad_umma(WgradArgs a, DeviceStatus
   // G^T rows 16w..16w+15. Byte offset of (row, pixel lane) inside a stage tile:
   const int a_lane = (lane >> 4) * WG_A_HALF, b_lane = (lane >> 4) * WG_B_HALF;
   const uint32_t idesc = umma_idesc(UMMA_M, UMMA_N);
-  const int nsteps = (p1 - p0 + WG_PIX - 1) / WG_PIX;
+  int nsteps = (p1 - p0 + WG_PIX - 1) / WG_PIX;
+  if (a.stall > 0) {  // test hook: stage 0's barrier before any MMA (nothing completes it)
+    if (!mbar_wait(smem_u32(&mbar[0]), 0u, (unsigned)a.stall)) s_fail = 1;
+    __syncthreads();
+    if (s_fail) nsteps = 0;  // no MMA in flight: the accumulator is freed below
+  }
   float bsum[16];  // this lane's share of the bias gradient of G^T rows 16w..16w+15
 #pragma unroll
   for (int i = 0; i < 16; i++) bsum[i] = 0.f;
@@ -567,8 +580,9 @@ static NetWs net_ws(Arena &a, const NetShape &s, int B, int Gx, int Gy) {
   return w;
 }
 
-static ff_status launch_conv(const ConvArgs &c, int M, DeviceStatus *status, cudaStream_t st) {
+static ff_status launch_conv(ConvArgs c, int M, DeviceStatus *status, cudaStream_t st) {
   dim3 g((M + UMMA_M - 1) / UMMA_M, c.Np / UMMA_N);
+  c.stall = net_stall_polls();
   k_conv_umma<<<g, 128, 0, st>>>(c, status);
   FF_CHECK_LAUNCH();
   return FF_OK;
@@ -696,6 +710,7 @@ ff_status ff_net_backward(const ff_net_desc *d, const float *params, const float
     ppc = ((ppc + WG_PIX - 1) / WG_PIX) * WG_PIX;
     wa.pix_per_cta = (int)(ppc < 64 ? 64 : ppc);
     dim3 gw((unsigned)((P + wa.pix_per_cta - 1) / wa.pix_per_cta), ky);
+    wa.stall = net_stall_polls();
     k_wgrad_umma<<<gw, 128, 0, st>>>(wa, (DeviceStatus *)ws);
     FF_CHECK_LAUNCH();
     if (l == 0) break;

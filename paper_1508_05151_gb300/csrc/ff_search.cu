@@ -1092,13 +1092,15 @@ ff_status SideSection::end() {
 
 // ---------------------------------------------------------- persistent level --
 static std::atomic<long long> g_bar_budget{0};
-static std::atomic<int> g_bar_skip{-1};
+static std::atomic<int> g_bar_skip{-1}, g_net_stall{0};
 constexpr long long BAR_BUDGET_DEFAULT = 1ll << 31;  // clock cycles, about a second
 
-void set_barrier_test(long long budget_cycles, int skip_block) {
+void set_wait_test(long long budget_cycles, int skip_block, int net_stall) {
   g_bar_budget.store(budget_cycles);
   g_bar_skip.store(skip_block);
+  g_net_stall.store(net_stall);
 }
+int net_stall_polls() { return g_net_stall.load(); }
 
 // k_level<RA, RB, SPLIT> for one radius (RA == RB, r = 1..8) or the paper's pair
 // (8, 6); nullptr for other pairs.

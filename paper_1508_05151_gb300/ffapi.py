@@ -53,11 +53,12 @@ class NetDesc(C.Structure):
 class Params(C.Structure):
     """ff_params; defaults are the Sintel preset of Sec. 4."""
     _fields_ = [(n, C.c_int32) for n in
-                ("k", "r", "r2", "leaf", "R", "eps", "e", "s", "tile", "n_rs", "K")] + \
+                ("k", "r", "r2", "leaf", "R", "eps", "e", "s", "tile", "n_rs", "K", "color")] + \
                [("seed", C.c_uint64)]
 
     def __init__(self, **kw):
-        d = dict(k=3, r=8, r2=6, leaf=8, R=1, eps=5, e=4, s=50, tile=16, n_rs=3, K=0, seed=0)
+        d = dict(k=3, r=8, r2=6, leaf=8, R=1, eps=5, e=4, s=50, tile=16, n_rs=3, K=0, color=0,
+                 seed=0)
         unknown = set(kw) - set(d)
         if unknown:
             raise TypeError(f"unknown parameters {sorted(unknown)}")
@@ -93,6 +94,7 @@ def lib():
             "ff_smooth_workspace_size": ([i32, i32, i32, C.POINTER(sz)], i32),
             "ff_smooth": ([vp, i32, i32, i32, vp, vp, sz, vp], i32),
             "ff_census": ([vp, i32, i32, i32, vp, vp], i32),
+            "ff_rgb_to_lab": ([vp, i32, i32, vp, vp], i32),
             "ff_features": ([vp, i32, i32, i32, vp, i32, vp, vp], i32),
             "ff_kdtree_size": ([i32, i32, C.POINTER(C.c_int), C.POINTER(sz)], i32),
             "ff_kdtree_build": ([vp, i32, i32, vp, vp, vp, vp, sz, vp], i32),
@@ -124,7 +126,7 @@ def lib():
                              vp], i32),
             "ff_net_proposals": ([C.POINTER(NetDesc), vp, i32, i32, i32, C.c_float, vp, vp], i32),
             "ff_get_exec_params": ([C.POINTER(ExecParams)], i32),
-            "ff_set_barrier_test": ([C.c_longlong, i32], i32),
+            "ff_set_wait_test": ([C.c_longlong, i32, i32], i32),
             "ff_device_status": ([vp, C.POINTER(C.c_uint32), C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int32), vp], i32),
             "ff_profile_enable": ([i32], i32),
@@ -198,6 +200,14 @@ def ff_smooth(img, n):
     ws = _ws(_size("ff_smooth_workspace_size", W, H, n), img.device)
     wp, wn = _ws_ptr(ws)
     _check("ff_smooth", lib().ff_smooth(_dev(img), W, H, n, _dev(out), wp, wn, _stream()))
+    return out
+
+
+def ff_rgb_to_lab(img):
+    """Integer CIELab (uint8 L*255/100, a+128, b+128) of an (H, W, 3) sRGB image."""
+    H, W = img.shape[:2]
+    out = torch.empty_like(img)
+    _check("ff_rgb_to_lab", lib().ff_rgb_to_lab(_dev(img), W, H, _dev(out), _stream()))
     return out
 
 
@@ -620,6 +630,12 @@ class NetRunner:
             C.byref(self.desc), _dev(params), _dev(self.dout if dout is None else dout), self.B,
             self.Gx, self.Gy, _dev(grads), wp, wn, _stream()))
         return grads
+
+    def device_status(self):
+        wp, _ = _ws_ptr(self.ws)
+        code, x, y = C.c_uint32(), C.c_int32(), C.c_int32()
+        lib().ff_device_status(wp, C.byref(code), C.byref(x), C.byref(y), _stream())
+        return code.value, x.value, y.value
 
     def proposals(self, flow_scale, out=None):
         o = self.out if out is None else out

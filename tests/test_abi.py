@@ -151,8 +151,9 @@ def test_exec_params_checks(L):
         assert L.ff_set_exec_params(C.byref(ffapi.ExecParams(pass_warps=2, serial_flows=v))) == 1
         assert L.ff_set_exec_params(C.byref(ffapi.ExecParams(pass_warps=2, kd_merge=v))) == 1
         assert L.ff_set_exec_params(C.byref(ffapi.ExecParams(pass_warps=2, persist_levels=v))) == 1
-    assert L.ff_set_barrier_test(-1, -1) == 1 and L.ff_set_barrier_test(0, -2) == 1
-    assert L.ff_set_barrier_test(0, -1) == 0
+    assert L.ff_set_wait_test(-1, -1, 0) == 1 and L.ff_set_wait_test(0, -2, 0) == 1
+    assert L.ff_set_wait_test(0, -1, -1) == 1
+    assert L.ff_set_wait_test(0, -1, 0) == 0
     assert L.ff_set_exec_params(None) == 1
     ok = ffapi.ExecParams(pass_warps=e.pass_warps, rs_min_n=4, wide_min_n=2, split8_min_n=8)
     assert L.ff_set_exec_params(C.byref(ok)) == 0

@@ -148,15 +148,15 @@ def test_persistent_barrier_wait_runs_out_and_reports():
     L = ffapi.lib()
     try:
         ffapi.set_exec_params(persist_levels=1)
-        assert L.ff_set_barrier_test(200000, 0) == 0  # ~0.1 ms at 2 GHz
+        assert L.ff_set_wait_test(200000, 0, 0) == 0  # ~0.1 ms at 2 GHz
         ff.run(I1, I2)
         code, x, y = ff.device_status()
         assert code == 3, (code, x, y)
-        assert L.ff_set_barrier_test(0, -1) == 0
+        assert L.ff_set_wait_test(0, -1, 0) == 0
         got = ff.run(I1, I2)
         code, _, _ = ff.device_status()
         assert code == 0
         _same(ref, got)
     finally:
-        L.ff_set_barrier_test(0, -1)
+        L.ff_set_wait_test(0, -1, 0)
         ffapi.set_exec_params(**before)

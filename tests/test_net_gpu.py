@@ -193,3 +193,38 @@ def test_learned_proposals_lower_the_coarse_data_cost():
     assert d["never_worse"]
     assert d["frac_won"] > 0.10, d
     assert d["cost_reduction"] > 0.05, d
+
+
+def test_net_bounded_waits_run_out_and_report():
+    """Bounded-wait path of the tensor-core kernels: with the test hook every
+    kernel first waits on an mbarrier that nothing completes; the wait must run out,
+    the forward and backward calls must return with device status 3 (timeout), and
+    the next calls without the hook must give the same results as before."""
+    d = DESCS[0]
+    desc = _desc(d)
+    B, W, H = 2, 160, 120
+    I1, I2 = _frames(B, W, H, 70)
+    x = ffapi.ff_net_input(torch.from_numpy(I1).cuda(), torch.from_numpy(I2).cuda())
+    Gy, Gx = x.shape[2:]
+    params = torch.from_numpy(_params(d, 71)).cuda()
+    run = ffapi.NetRunner(desc, B, Gx, Gy)
+    ref = run.forward(params, x).clone()
+    assert run.device_status()[0] == 0
+    dout = torch.ones_like(ref)
+    gref = run.backward(params, torch.empty_like(params), dout).clone()
+    assert run.device_status()[0] == 0
+    L = ffapi.lib()
+    try:
+        assert L.ff_set_wait_test(0, -1, 64) == 0
+        run.forward(params, x)
+        assert run.device_status()[0] == 3
+        run.backward(params, torch.empty_like(params), dout)
+        assert run.device_status()[0] == 3
+    finally:
+        assert L.ff_set_wait_test(0, -1, 0) == 0
+    out = run.forward(params, x)
+    assert run.device_status()[0] == 0
+    assert torch.equal(out, ref)
+    g = run.backward(params, torch.empty_like(params), dout)
+    assert run.device_status()[0] == 0
+    _close(g.cpu().numpy(), gref.cpu().numpy())

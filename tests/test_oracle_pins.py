@@ -306,6 +306,57 @@ def test_eval_count_matches_schedule_shape(ffo):
     assert 8 + 3 == 11
 
 
+def _line_search(ffo, L, vertical, tile):
+    """Level search (n = 1, r = 1, no random search) on a line of L grid points
+    where only point 0 holds a flow; returns which points hold one afterwards and
+    the flows."""
+    rng = np.random.default_rng(6)
+    W, H = (1, L) if vertical else (L, 1)
+    Cs = rng.integers(0, 1 << 24, size=(H, W)).astype(np.uint32)
+    Ct = rng.integers(0, 1 << 24, size=(H, W)).astype(np.uint32)
+    flow = np.zeros((H, W, 2), np.int32)
+    cost = np.full((H, W), 0x7fffffff, np.int32)
+    f0 = (0, 1) if vertical else (1, 0)
+    flow[0, 0] = f0
+    cost[0, 0] = 0
+    fl, co, _ = ffo.search_level(Cs, Ct, 1, 1, flow=flow, cost=cost, tile=tile, n_rs=0)
+    return [c != 0x7fffffff for c in co.reshape(-1)], fl.reshape(-1, 2), f0
+
+
+def test_tiled_schedule_two_tile_hand_case(ffo):
+    """Sec. 3.1 propagation in the tiled schedule (T = 2, no random search) on a
+    line of grid points where only point 0 holds a flow. Worked out by hand from
+    the rules: a source in another tile is read from the start-of-pass state, odd
+    passes shift the tiles by T / 2. Horizontal sources: pass 0 left, 1 right,
+    2 right, 3 left; vertical: 0 up, 1 down, 2 up, 3 down.
+    Horizontal line of 4:
+      pass 0 (left, tiles {0,1} {2,3}): 1 takes 0's flow; 2 reads 1 from the
+             start-of-pass state (unset), so 2 and 3 stay unset.
+      passes 1, 2 (right): every right-hand source of 2 and 3 is unset.
+      pass 3 (left, tiles {0} {1,2} {3}): 2 takes 1's flow inside its tile; 3
+             reads 2 from the start-of-pass state (unset).
+      -> 0, 1, 2 set, 3 unset. Without the start-of-pass rule (pass 0) or without
+      the shift (pass 3: tiles {0,1} {2,3}) all four would be set.
+    Vertical line of 8:
+      pass 0 (up, tiles {0,1} {2,3} ...): 1 set; 2 reads 1 from the start-of-pass
+             state: unset.
+      pass 1 (down): nothing below is set.
+      pass 2 (up, tiles {0,1} {2,3} {4,5} {6,7}): 2 reads 1 (set at the start of
+             the pass) and 3 follows inside the tile; 4 reads 3 from the
+             start-of-pass state: unset.
+      pass 3 (down): nothing below is set.
+      -> 0..3 set, 4..7 unset.
+    The paper's sequential scan sets every point in both cases."""
+    got, fl, f0 = _line_search(ffo, 4, False, 2)
+    assert got == [True, True, True, False]
+    assert all(tuple(fl[i]) == f0 for i in range(3))
+    got, fl, f0 = _line_search(ffo, 8, True, 2)
+    assert got == [True] * 4 + [False] * 4
+    assert all(tuple(fl[i]) == f0 for i in range(4))
+    for L, vertical in ((4, False), (8, True)):
+        assert all(_line_search(ffo, L, vertical, 0)[0])
+
+
 def test_tiled_schedule_reduces_to_sequential(ffo):
     # tiled(T) with T >= 2 max(Gx, Gy) keeps the whole grid in one tile in every
     # pass (odd passes shift the origin by T/2), so it equals the sequential scan.
@@ -483,11 +534,68 @@ def test_sparsify_hand_cases(ffo):
     err[2, 0] = 3  # tie with (2,1): raster-first wins -> (2, 1)
     valid[0:2, 3:6] = 1  # 6 valid, all err 50 -> first in raster order (3, 0)
     valid[3, 6] = 1  # partial block (6..6, 3..3) with 1 valid: needs e <= 1
-    sp, mask = ffo.sparsify(valid, err, F, 4)
+    zero = np.zeros_like(err)
+    sp, mask = ffo.sparsify(valid, err, zero, F, 4)
     assert sp.tolist() == [[2, 1, 2, 1], [3, 0, 3, 0]]
     assert mask.sum() == 2
-    sp1, _ = ffo.sparsify(valid, err, F, 1)
+    sp1, _ = ffo.sparsify(valid, err, zero, F, 1)
     assert sp1.tolist()[-1] == [6, 3, 6, 3]
+
+
+def test_sparsify_takes_the_sum_of_the_two_errors(ffo):
+    """Sec. 3.5 keeps the sample whose two consistency-check errors |.| (Eq. 5) sum
+    to the least: sqrt(e1) + sqrt(e2), not e1 + e2. Blocks where the two readings
+    disagree, and exact ties (rational and irrational) that go to raster order."""
+    W, H = 9, 3
+    valid = np.zeros((H, W), np.uint8)
+    e1 = np.zeros((H, W), np.int32)
+    e2 = np.zeros((H, W), np.int32)
+    F = np.zeros((H, W, 2), np.int32)
+    F[..., 0] = np.arange(W)[None, :]
+    # block 0: (0, 25) at x = 1 -> 5 beats (9, 9) at x = 0 -> 6, although 25 > 18
+    valid[0, 0] = valid[0, 1] = 1
+    e1[0, 1], e2[0, 1] = 0, 25
+    e1[0, 0], e2[0, 0] = 9, 9
+    # block 1: sqrt(4) + sqrt(9) = sqrt(1) + sqrt(16) = 5: tie, raster-first (3, 0)
+    valid[0, 3] = valid[0, 4] = 1
+    e1[0, 3], e2[0, 3] = 4, 9
+    e1[0, 4], e2[0, 4] = 1, 16
+    # block 2: sqrt(2) + sqrt(8) = sqrt(18) = 3 sqrt(2): tie, raster-first (7, 0);
+    # sqrt(17) < 3 sqrt(2) wins the block from row 2
+    valid[0, 7] = valid[0, 8] = valid[2, 6] = 1
+    e1[0, 7], e2[0, 7] = 2, 8
+    e1[0, 8], e2[0, 8] = 18, 0
+    e1[2, 6], e2[2, 6] = 17, 0
+    sp, _ = ffo.sparsify(valid, e1, e2, F, 1)
+    assert sp[:, :2].tolist() == [[1, 0], [3, 0], [6, 2]]
+    e2[2, 6] = 1  # sqrt(17) + 1 > 3 sqrt(2): the tie (7, 0) / (8, 0) decides
+    sp, _ = ffo.sparsify(valid, e1, e2, F, 1)
+    assert sp[:, :2].tolist() == [[1, 0], [3, 0], [7, 0]]
+
+
+def test_sqrt_sum_comparator_against_high_precision(ffo):
+    """The exact integer comparison of sqrt(a) + sqrt(b) and sqrt(c) + sqrt(d)
+    against 60-digit decimal square roots. For integers below 2^20 a nonzero
+    difference exceeds 1e-30, so smaller differences are ties."""
+    import decimal
+    decimal.getcontext().prec = 60
+    D = decimal.Decimal
+
+    def ref(a, b, c, d):
+        diff = (D(c).sqrt() + D(d).sqrt()) - (D(a).sqrt() + D(b).sqrt())
+        return diff > D("1e-30")
+
+    rng = np.random.default_rng(5)
+    cases = [tuple(int(v) for v in rng.integers(0, 1 << 20, size=4)) for _ in range(3000)]
+    cases += [tuple(int(v) for v in rng.integers(0, 40, size=4)) for _ in range(3000)]
+    # near-ties: c, d perturbed around a, b
+    for _ in range(2000):
+        a, b = (int(v) for v in rng.integers(0, 1 << 20, size=2))
+        cases.append((a, b, max(0, a + int(rng.integers(-2, 3))), max(0, b + int(rng.integers(-2, 3)))))
+    cases += [(4, 9, 1, 16), (1, 16, 4, 9), (2, 8, 18, 0), (18, 0, 2, 8), (0, 0, 0, 0),
+              (12, 3, 27, 0), (27, 0, 12, 3), (5, 5, 20, 0), (0, 20, 5, 5), (50, 0, 2, 32)]
+    for a, b, c, d in cases:
+        assert ffo.sqrt_sum_less(a, b, c, d) == ref(a, b, c, d), (a, b, c, d)
 
 
 # ------------------------------------------------------------- smoothing -------
@@ -541,3 +649,75 @@ def test_smooth_preserves_constants_and_is_a_lowpass(ffo):
     s = ffo.smooth(chk, 4)
     assert s[8:24, 8:24].std() < 0.05 * chk.std()
     assert abs(int(s[8:24, 8:24].mean()) - 120) <= 2
+
+
+# ------------------------------------------------------------- CIELab ----------
+def test_lab_decoding_table_and_matrix(ffo):
+    """Step 1 and 2 of the integer CIELab: the linear branch of the sRGB decoding
+    curve in closed form, the end points, monotonicity; matrix rows that sum to
+    exactly 16384 and stay within one unit of the published IEC 61966-2-1 matrix
+    divided by the D65 white."""
+    from fractions import Fraction
+    t = ffo.lab_gamma_table()
+    assert t[0] == 0 and t[255] == 65536
+    assert np.all(np.diff(t) > 0)
+    for v in range(11):  # v / 255 <= 0.04045: linear segment c / 12.92
+        x = Fraction(65536 * v * 100, 255 * 1292) + Fraction(1, 2)
+        assert t[v] == x.numerator // x.denominator
+    m = ffo.lab_matrix()
+    assert np.all(m.sum(1) == 16384)
+    M = np.array([[0.4124, 0.3576, 0.1805], [0.2126, 0.7152, 0.0722], [0.0193, 0.1192, 0.9505]])
+    assert np.all(np.abs(m - M / M.sum(1, keepdims=True) * 16384) <= 1.0)
+
+
+def test_lab_transfer_exact(ffo):
+    """Step 3: the cube-root branch is the exact integer cube root of t * 2^32;
+    below (6/29)^3 the line t / (3 (6/29)^2) + 4/29 (Q16, rounded)."""
+    from fractions import Fraction
+    assert ffo.lab_f(65536) == 65536
+    assert ffo.lab_f(0) == 9039  # round(65536 * 4 / 29)
+    rng = np.random.default_rng(7)
+    for t in list(range(570, 600)) + [int(x) for x in rng.integers(581, 65537, size=400)]:
+        y = ffo.lab_f(t)
+        if t * 29 ** 3 > 6 ** 3 * 65536:
+            assert y ** 3 <= t << 32 < (y + 1) ** 3, t
+        else:
+            x = Fraction(t, 65536) / (3 * Fraction(6, 29) ** 2) + Fraction(4, 29)
+            x = x * 65536 + Fraction(1, 2)
+            assert y == x.numerator // x.denominator, t
+
+
+def test_lab_grey_white_black_and_primaries(ffo):
+    """Step 4: greys have a = b = 0 exactly (128), white is L = 100 (255), black
+    L = 0; the sRGB primaries land within one unit of their published CIELab
+    (D65) values: red (53.24, 80.09, 67.20), green (87.73, -86.18, 83.18), blue
+    (32.30, 79.19, -107.86)."""
+    grey = np.repeat(np.arange(256, dtype=np.uint8)[None, :, None], 3, axis=2)
+    lab = ffo.rgb_to_lab(grey)[0]
+    assert np.all(lab[:, 1] == 128) and np.all(lab[:, 2] == 128)
+    assert lab[0, 0] == 0 and lab[255, 0] == 255
+    assert np.all(np.diff(lab[:, 0].astype(int)) >= 0)
+    prim = np.array([[[255, 0, 0], [0, 255, 0], [0, 0, 255]]], np.uint8)
+    got = ffo.rgb_to_lab(prim)[0].astype(float)
+    want = np.array([[53.24, 80.09, 67.20], [87.73, -86.18, 83.18], [32.30, 79.19, -107.86]])
+    enc = np.stack([want[:, 0] * 2.55, want[:, 1] + 128, want[:, 2] + 128], 1)
+    assert np.all(np.abs(got - enc) <= 1.0), (got, enc)
+
+
+def test_lab_against_float_formula(ffo):
+    """The integer conversion against the CIELab formulas in float64 on random
+    colours: every channel within one unit (the fixed-point rounding)."""
+    rng = np.random.default_rng(8)
+    img = rng.integers(0, 256, size=(64, 128, 3)).astype(np.uint8)
+    got = ffo.rgb_to_lab(img).astype(float)
+    c = img.astype(float) / 255.0
+    lin = np.where(c <= 0.04045, c / 12.92, ((c + 0.055) / 1.055) ** 2.4)
+    M = np.array([[0.4124, 0.3576, 0.1805], [0.2126, 0.7152, 0.0722], [0.0193, 0.1192, 0.9505]])
+    xyz = lin @ (M / M.sum(1, keepdims=True)).T
+    d = 6.0 / 29.0
+    f = np.where(xyz > d ** 3, np.cbrt(xyz), xyz / (3 * d * d) + 4.0 / 29.0)
+    L = 116 * f[..., 1] - 16
+    a = 500 * (f[..., 0] - f[..., 1])
+    b = 200 * (f[..., 1] - f[..., 2])
+    want = np.stack([np.clip(L * 2.55, 0, 255), np.clip(a + 128, 0, 255), np.clip(b + 128, 0, 255)], -1)
+    assert np.max(np.abs(got - want)) <= 1.0

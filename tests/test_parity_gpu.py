@@ -270,9 +270,9 @@ def test_consistency_filter(seed):
     flows[0][..., 1] = np.clip(ys + flows[0][..., 1], 0, H - 1) - ys
     for params in (dict(eps=5, e=4, s=50), dict(eps=1, e=7, s=50), dict(eps=2, e=1, s=500)):
         g = ffapi.ff_consistency_filter(*(tg(flows[j].astype(np.int16)) for j in range(3)), params)
-        vcc, err = O.consistency(flows[0], flows[1], flows[2], params["eps"])
+        vcc, err, e1, e2 = O.consistency(flows[0], flows[1], flows[2], params["eps"], errors=True)
         val = O.region_filter(flows[0], vcc, params["s"])
-        sp, mask = O.sparsify(val, err, flows[0], params["e"])
+        sp, mask = O.sparsify(val, e1, e2, flows[0], params["e"])
         assert np.array_equal(cpu(g["err_sum"]), err)
         assert np.array_equal(cpu(g["valid"]), val)
         assert np.array_equal(cpu(g["mask"]), mask)
@@ -410,3 +410,24 @@ def test_batch_64_mixed_full_size_sampled():
             i = 16 * k + j
             p = batch_pairs[i][1]
             _compare(outs[i], O.flow_fields(p["I1"], p["I2"], threads=3))
+
+
+# ------------------------------------------------------------- CIELab ---------
+def test_rgb_to_lab_every_colour():
+    """ff_rgb_to_lab against the oracle on all 2^24 sRGB colours (a 4096 x 4096
+    image holding each once): bit for bit."""
+    v = np.arange(1 << 24, dtype=np.uint32)
+    img = np.stack([(v >> 16) & 255, (v >> 8) & 255, v & 255], -1).astype(np.uint8)
+    img = img.reshape(4096, 4096, 3)
+    got = cpu(ffapi.ff_rgb_to_lab(tg(img)))
+    assert np.array_equal(got, O.rgb_to_lab(img))
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_flow_fields_lab_128x96(seed):
+    """The whole path in CIELab (params.color = 1) against the oracle."""
+    p = synth.pair_for_config(1, seed)
+    params = dict(color=1)
+    out = ffapi.FlowFields(128, 96, params).run(tg(p["I1"]), tg(p["I2"]))
+    torch.cuda.synchronize()
+    _compare(out, O.flow_fields(p["I1"], p["I2"], params=params, threads=3))
