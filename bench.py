@@ -475,12 +475,15 @@ def batch_measure(dev, params, pk, flush, reps=3):
 
 LEARNED_WORKLOADS = {
     2: ("1024x436", "Sintel-shaped 1024x436 pairs (3 textured layers, affine motion <= 200 px)"),
+    4: ("512x218", "512x218 pairs of the shifted-noise generator with an occluding square "
+                   "(the proposal-net training workload at its stated size)"),
     5: ("1242x375", "KITTI-shaped 1242x375 pairs (radial expansion <= 300 px, sky band, moving "
                     "boxes)"),
 }
 
 
-def learned_measure(config, train_pairs=256, epochs=40, eval_pairs=32):
+def learned_measure(config, train_pairs=256, epochs=40, eval_pairs=32, batch=32,
+                    eval_batch=32):
     """Learned proposals vs plain search on one generated workload (config 2:
     Sintel-shaped 1024x436; config 5: KITTI-shaped 1242x375).
 
@@ -489,11 +492,11 @@ def learned_measure(config, train_pairs=256, epochs=40, eval_pairs=32):
     both arms run on `eval_pairs` held-out pairs as batched CUDA-graph replays at
     random-search budgets n_rs = 1, 2, 3; the learned arm's time includes the net."""
     from paper_1508_05151_gb300 import train
-    net, info = train.train_for(config, train_pairs, epochs, batch=32, seed=2000)
-    E1, E2, gt, occ = train.make_pairs(config, range(3000, 3000 + eval_pairs))
-    ev = train.evaluate(net, E1, E2, gt, occ, (1, 2, 3), batch=min(eval_pairs, 32))
-    return {"workload": f"{eval_pairs} {LEARNED_WORKLOADS[config][1]}, 32 pairs per "
-                        "CUDA-graph replay",
+    net, info = train.train_for(config, train_pairs, epochs, batch=batch, seed=2000)
+    E1, E2, gt, occ = train.make_pairs(config, range(10**6, 10**6 + eval_pairs))
+    ev = train.evaluate(net, E1, E2, gt, occ, (1, 2, 3), batch=min(eval_pairs, eval_batch))
+    return {"workload": f"{eval_pairs} held-out {LEARNED_WORKLOADS[config][1]}, "
+                        f"{min(eval_pairs, eval_batch)} pairs per CUDA-graph replay",
             "train": info, "coarse_data_cost": ev["coarse"], "arms": ev["arms"],
             "equal_inliers": train.equal_inlier_point(ev),
             "note": "inliers_3px / epe of the raw forward flow vs ground truth on non-occluded "
@@ -617,6 +620,9 @@ def run_ours(args):
     batch = batch_measure(dev, PARAMS, pk, flush) if (rank == 0 and not args.no_batch) else None
     learned = {}
     if rank == 0 and not args.no_learned:
+        # the training workload at its stated size: 4096 generated pairs, 256 held out
+        learned[4] = learned_measure(4, train_pairs=4096, epochs=10, eval_pairs=256, batch=64,
+                                     eval_batch=128)
         for cfg in (2, 5):
             learned[cfg] = learned_measure(cfg, eval_pairs=64 if cfg == 2 else 32)
     if rank != 0:

@@ -140,15 +140,26 @@ constexpr int PASS_MAX_WARPS = 8;  // tiles per CTA: an execution parameter, 1..
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
 // Shared-memory layout of one tile (all sizes in 32-bit words).
+// Window pitches. For 16 x 16 tiles (the default) both windows use a pitch of
+// 2 mod 4 words (26 for r = 1, 38 for r = 2, 42 for r = 3..8): with the random
+// search's points taken column by column, the CTA-per-tile kernel's shared loads
+// (patch columns and rows of the wavefront's candidates, whole patches of the
+// random search) then fall in distinct banks; a model of those access patterns
+// over a coherent flow gives one wavefront per load instead of 1.7 with odd
+// pitches. Other tile edges keep odd pitches.
 struct TileLayout {
-  int sw, swp;   // source window edge and (odd) pitch
-  int tw, twp;   // target window edge and (odd) pitch
+  int sw, swp;   // source window edge and pitch
+  int tw, twp;   // target window edge and pitch
   int T;
   __host__ __device__ TileLayout(int T_, int R) : T(T_) {
     sw = T_ + 2 * R + 2;
-    swp = sw | 1;
     tw = T_ + 2 * R + 8;  // 3 entries of slack on each side of the tile's patches
-    twp = tw | 1;
+    if (T_ == 16) {
+      swp = twp = R <= 1 ? 26 : (R == 2 ? 38 : 42);
+    } else {
+      swp = sw | 1;
+      twp = tw | 1;
+    }
   }
   __host__ __device__ int words() const { return sw * swp + tw * twp + 2 * T * T + 4 * T; }
 };
@@ -770,10 +781,10 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
     __syncthreads();
   }
 
-  if (cfg.do_rs) {  // random search, one thread per point
+  if (cfg.do_rs) {  // random search, one thread per point, points column by column
     const int Rn = cfg.R * n;
     for (int i = t; i < tw * th; i += WIDE_THREADS) {
-      const int lx = i % tw, ly = i / tw;
+      const int ly = i % th, lx = i / th;
       const uint32_t cur = S.flow[ly * T + lx];
       const int32_t cc = S.cost[ly * T + lx];
       if (cc == COST_UNSET) continue;
