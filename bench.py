@@ -473,6 +473,55 @@ def batch_measure(dev, params, pk, flush, reps=3):
             "roofline": roof}
 
 
+def field_quality(dev, pairs=8, eps_list=(1, 2, 3, 4, 5, 6, 8, 10, 12, 15, 20)):
+    """Table 1 and Fig. 6 analogues on generated Sintel-shaped pairs with exact
+    ground truth, non-occluded pixels only:
+      raw / median: inliers@3px, EPE10 (EPE capped at 10) and EPE of the raw
+        forward field and of the field after the matching-error-weighted median
+        (ff_weighted_median, rho = 2; "k=3+median");
+      outlier_curves: for each eps, the fraction of outliers (EPE > 5 px) and of
+        inliers removed by the consistency check against one backward flow (1x),
+        against both (2x, Eq. 5) and by 2x plus the region filter (s = 50)."""
+    import torch
+    from paper_1508_05151_gb300 import ffapi, synth
+    ff = ffapi.FlowFields(W, H, PARAMS, dev)
+    acc = {"raw": [], "median": []}
+    curves = {v: {e: [0, 0, 0, 0] for e in eps_list} for v in ("1x", "2x", "2x_region")}
+    for i in range(pairs):
+        p = synth.pair_for_config(2, 4000 + i)
+        I1, I2 = torch.from_numpy(p["I1"]).to(dev), torch.from_numpy(p["I2"]).to(dev)
+        out = ff.run(I1, I2)
+        fl = out["flows"].clone()
+        med, _ = ffapi.ff_weighted_median(I1, I2, fl[0], PARAMS["r"], 2)
+        torch.cuda.synchronize()
+        gt, vis = p["flow"].astype(np.float64), ~p["occ"]
+        for name, f in (("raw", fl[0]), ("median", med)):
+            e = np.sqrt(((f.cpu().numpy().astype(np.float64) - gt) ** 2).sum(-1))[vis]
+            acc[name].append((float((e <= 3.0).mean()), float(np.minimum(e, 10.0).mean()),
+                              float(e.mean())))
+        e = np.sqrt(((fl[0].cpu().numpy().astype(np.float64) - gt) ** 2).sum(-1))
+        outl, inl = (e > 5.0) & vis, (e <= 5.0) & vis
+        for eps in eps_list:
+            for v, (b2, s) in (("1x", (fl[1], 0)), ("2x", (fl[2], 0)), ("2x_region", (fl[2], 50))):
+                r = ffapi.ff_consistency_filter(fl[0], fl[1], b2, dict(PARAMS, eps=eps, s=s))
+                kept = r["valid"].cpu().numpy().astype(bool)
+                c = curves[v][eps]
+                c[0] += int((outl & ~kept).sum())
+                c[1] += int(outl.sum())
+                c[2] += int((inl & ~kept).sum())
+                c[3] += int(inl.sum())
+    res = {"pairs": pairs, "workload": "generated Sintel-shaped 1024x436 pairs, non-occluded "
+                                       "pixels; outliers: EPE > 5 px"}
+    for name, v in acc.items():
+        a = np.array(v)
+        res[name] = {"inliers_3px": round(float(a[:, 0].mean()), 5),
+                     "epe10": round(float(a[:, 1].mean()), 4), "epe": round(float(a[:, 2].mean()), 4)}
+    res["outlier_curves"] = {v: [[e, round(c[0] / max(c[1], 1), 4), round(c[2] / max(c[3], 1), 5)]
+                                 for e, c in d.items()] for v, d in curves.items()}
+    res["outlier_curves_columns"] = ["eps", "outliers_removed", "inliers_removed"]
+    return res
+
+
 LEARNED_WORKLOADS = {
     2: ("1024x436", "Sintel-shaped 1024x436 pairs (3 textured layers, affine motion <= 200 px)"),
     4: ("512x218", "512x218 pairs of the shifted-noise generator with an occluding square "
@@ -618,6 +667,7 @@ def run_ours(args):
     assert int(h_ns.item()) > 0
 
     batch = batch_measure(dev, PARAMS, pk, flush) if (rank == 0 and not args.no_batch) else None
+    quality = field_quality(dev) if (rank == 0 and not args.no_quality) else None
     learned = {}
     if rank == 0 and not args.no_learned:
         # the training workload at its stated size: 4096 generated pairs, 256 held out
@@ -676,6 +726,8 @@ def run_ours(args):
     }
     if batch is not None:
         line["batch_64_mixed"] = batch
+    if quality is not None:
+        line["field_quality_1024x436"] = quality
     for cfg, lm in learned.items():
         eq = lm["equal_inliers"]
         if cfg == 2 and eq is not None:
@@ -729,6 +781,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-pair batch line")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip training and evaluating the proposal net")
+    ap.add_argument("--no-quality", action="store_true",
+                    help="skip the field-quality report (median field, outlier curves)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the library's default execution parameters (profiling runs)")
     ap.add_argument("--ncu-target", action="store_true",

@@ -218,6 +218,20 @@ ff_status ff_consistency_filter_static(const int16_t *F, const int16_t *Fb1, con
                                        int32_t *err_sum, int32_t *sparse, int32_t *n_sparse,
                                        uint8_t *mask, void *stream);
 
+/* Sec. 4.1 (Table 1, "k=3+median"): the raw forward field filtered by a median
+ * weighted by the matching error (the paper gives neither window nor weights;
+ * this is the library's reading). E(p) = E_d of pixel p's own flow at full
+ * resolution (census of I1 and I2 with spacing 1, patch radius r, taps clamped);
+ * weight w(q) = floor(65536 / (1 + E(q))); window: the in-image pixels q with
+ * max(|qx - px|, |qy - py|) <= rho (0..3); each component of out(p) is the
+ * smallest value v whose samples <= v carry at least half of the window's total
+ * weight. I1, I2: H x W x 3; flow, out: int16 [H][W][2] (out != flow);
+ * match_err: NULL or int32 [H][W] receiving E. ws: ff_median_workspace_size. */
+ff_status ff_median_workspace_size(int W, int H, size_t *bytes);
+ff_status ff_weighted_median(const uint8_t *I1, const uint8_t *I2, const int16_t *flow, int W,
+                             int H, int r, int rho, int16_t *out, int32_t *match_err, void *ws,
+                             size_t ws_bytes, void *stream);
+
 /* The whole path for one pair (Fig. 2): smoothed images and census for both
  * frames at every level, three flow fields (forward I1->I2 with r, backward
  * I2->I1 with r and with r2; flow ids 0, 1, 2), each from its own kd tree, then

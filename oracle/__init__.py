@@ -93,6 +93,8 @@ def lib():
             L.ffo_lab_f.argtypes = [C.c_int32]
             L.ffo_lab_f.restype = C.c_int32
             L.ffo_rgb_to_lab.argtypes = [u8, ci, ci, u8]
+            L.ffo_match_errors.argtypes = [u8, u8, i32, ci, ci, ci, i32]
+            L.ffo_weighted_median.argtypes = [i32, i32, ci, ci, ci, i32]
             L.ffo_region_filter.argtypes = [i32, u8, ci, ci, ci, u8]
             L.ffo_sparsify.argtypes = [u8, i32, i32, i32, ci, ci, ci, i32, u8]
             L.ffo_flow_fields.argtypes = [u8, u8, ci, ci, C.POINTER(Params), i32, ci, i32, u8,
@@ -265,6 +267,26 @@ def rgb_to_lab(img):
     H, W = img.shape[:2]
     out = np.empty((H, W, 3), np.uint8)
     lib().ffo_rgb_to_lab(_p(img, C.c_uint8), W, H, _p(out, C.c_uint8))
+    return out
+
+
+def match_errors(I1, I2, F, r):
+    """E_d of every pixel's own match at full resolution (census spacing 1)."""
+    I1, I2, F = _c(I1, np.uint8), _c(I2, np.uint8), _c(F, np.int32)
+    H, W = I1.shape[:2]
+    E = np.empty((H, W), np.int32)
+    lib().ffo_match_errors(_p(I1, C.c_uint8), _p(I2, C.c_uint8), _p(F, C.c_int32), W, H, r,
+                           _p(E, C.c_int32))
+    return E
+
+
+def weighted_median(F, E, rho=2):
+    """Component-wise median weighted by floor(2^16 / (1 + E)) over the in-image
+    (2 rho + 1)^2 window (the lower weighted median)."""
+    F, E = _c(F, np.int32), _c(E, np.int32)
+    H, W = E.shape
+    out = np.empty((H, W, 2), np.int32)
+    lib().ffo_weighted_median(_p(F, C.c_int32), _p(E, C.c_int32), W, H, rho, _p(out, C.c_int32))
     return out
 
 

@@ -807,6 +807,73 @@ int ffo_sparsify(const uint8_t *valid, const int32_t *e1, const int32_t *e2, con
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 4.1 (Table 1, "k=3+median"): the raw forward field filtered by a median */
+/* weighted by the matching error. Reading (the paper gives neither window nor  */
+/* weights): the matching error of pixel p is E(p) = E_d(P_r(p), P_r(p + F(p)))  */
+/* at full resolution (census of both frames with spacing 1, taps clamped);     */
+/* the weight w(q) = floor(2^16 / (1 + E(q))); the window holds the in-image    */
+/* pixels q with max(|qx - px|, |qy - py|) <= rho; each flow component takes    */
+/* the weighted lower median: the smallest value v with                        */
+/* 2 * (sum of the weights of samples <= v) >= (sum of all weights).           */
+/* ------------------------------------------------------------------------ */
+void ffo_match_errors(const uint8_t *I1, const uint8_t *I2, const int32_t *F, int W, int H, int r,
+                      int32_t *E) {
+  size_t N = (size_t)W * H;
+  uint32_t *C1 = malloc(sizeof(uint32_t) * N), *C2 = malloc(sizeof(uint32_t) * N);
+  ffo_census(I1, W, H, 1, C1);
+  ffo_census(I2, W, H, 1, C2);
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++) {
+      size_t p = (size_t)y * W + x;
+      E[p] = ffo_patch_cost(C1, C2, W, H, 1, r, x, y, x + F[2 * p], y + F[2 * p + 1]);
+    }
+  free(C1);
+  free(C2);
+}
+
+void ffo_weighted_median(const int32_t *F, const int32_t *E, int W, int H, int rho, int32_t *out) {
+  int cap = (2 * rho + 1) * (2 * rho + 1);
+  int32_t *val = malloc(sizeof(int32_t) * cap);
+  int64_t *wt = malloc(sizeof(int64_t) * cap);
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++)
+      for (int comp = 0; comp < 2; comp++) {
+        int m = 0;
+        int64_t total = 0;
+        for (int yy = y - rho; yy <= y + rho; yy++)
+          for (int xx = x - rho; xx <= x + rho; xx++) {
+            if (xx < 0 || xx >= W || yy < 0 || yy >= H) continue;
+            size_t q = (size_t)yy * W + xx;
+            val[m] = F[2 * q + comp];
+            wt[m] = 65536 / (1 + (int64_t)E[q]);
+            total += wt[m];
+            m++;
+          }
+        for (int i = 1; i < m; i++) /* insertion sort by value */
+          for (int j = i; j > 0 && val[j - 1] > val[j]; j--) {
+            int32_t tv = val[j];
+            val[j] = val[j - 1];
+            val[j - 1] = tv;
+            int64_t tw = wt[j];
+            wt[j] = wt[j - 1];
+            wt[j - 1] = tw;
+          }
+        int64_t cum = 0;
+        int32_t med = val[m - 1];
+        for (int i = 0; i < m; i++) {
+          cum += wt[i];
+          if (2 * cum >= total) {
+            med = val[i];
+            break;
+          }
+        }
+        out[2 * ((size_t)y * W + x) + comp] = med;
+      }
+  free(val);
+  free(wt);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Whole pipeline (Fig. 2 and Sec. 3.4/3.5): three flow fields (forward with   */
 /* radius r, backward with r, backward with r2), each from its own kd tree,   */
 /* then consistency check, region filter and sparsification.                 */

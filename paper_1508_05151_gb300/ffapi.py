@@ -95,6 +95,8 @@ def lib():
             "ff_smooth": ([vp, i32, i32, i32, vp, vp, sz, vp], i32),
             "ff_census": ([vp, i32, i32, i32, vp, vp], i32),
             "ff_rgb_to_lab": ([vp, i32, i32, vp, vp], i32),
+            "ff_median_workspace_size": ([i32, i32, C.POINTER(sz)], i32),
+            "ff_weighted_median": ([vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, sz, vp], i32),
             "ff_features": ([vp, i32, i32, i32, vp, i32, vp, vp], i32),
             "ff_kdtree_size": ([i32, i32, C.POINTER(C.c_int), C.POINTER(sz)], i32),
             "ff_kdtree_build": ([vp, i32, i32, vp, vp, vp, vp, sz, vp], i32),
@@ -209,6 +211,20 @@ def ff_rgb_to_lab(img):
     out = torch.empty_like(img)
     _check("ff_rgb_to_lab", lib().ff_rgb_to_lab(_dev(img), W, H, _dev(out), _stream()))
     return out
+
+
+def ff_weighted_median(I1, I2, flow, r=8, rho=2):
+    """The raw forward field filtered by the matching-error-weighted median
+    ("k=3+median" of Table 1). Returns (filtered flow int16 (H, W, 2), E int32)."""
+    H, W = I1.shape[:2]
+    nb = _size("ff_median_workspace_size", W, H)
+    ws = _ws(nb, I1.device)
+    wp, wn = _ws_ptr(ws)
+    out = torch.empty((H, W, 2), dtype=torch.int16, device=I1.device)
+    E = torch.empty((H, W), dtype=torch.int32, device=I1.device)
+    _check("ff_weighted_median", lib().ff_weighted_median(
+        _dev(I1), _dev(I2), _dev(flow), W, H, r, rho, _dev(out), _dev(E), wp, wn, _stream()))
+    return out, E
 
 
 def ff_census(img_n, n):

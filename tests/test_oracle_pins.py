@@ -721,3 +721,49 @@ def test_lab_against_float_formula(ffo):
     b = 200 * (f[..., 1] - f[..., 2])
     want = np.stack([np.clip(L * 2.55, 0, 255), np.clip(a + 128, 0, 255), np.clip(b + 128, 0, 255)], -1)
     assert np.max(np.abs(got - want)) <= 1.0
+
+
+# ------------------------------------------------- weighted median field -------
+def test_weighted_median_reduces_to_median_and_follows_weights(ffo):
+    """The weighted median of the "k=3+median" field: with equal matching errors
+    it is the plain lower median of the in-image window (numpy, brute force); a
+    constant field is a fixed point; one pixel whose weight outweighs the rest of
+    its window wins it; an isolated outlier in a smooth field is replaced."""
+    rng = np.random.default_rng(9)
+    H, W = 11, 13
+    F = rng.integers(-20, 21, size=(H, W, 2)).astype(np.int32)
+    E = np.full((H, W), 37, np.int32)
+    got = ffo.weighted_median(F, E, 2)
+    for y in range(H):
+        for x in range(W):
+            win = F[max(0, y - 2):y + 3, max(0, x - 2):x + 3].reshape(-1, 2)
+            srt = np.sort(win, axis=0)
+            k = (len(win) - 1) // 2  # lower median: first value with 2 * count >= total
+            assert tuple(got[y, x]) == (srt[k, 0], srt[k, 1]), (y, x)
+    const = np.full((H, W, 2), 7, np.int32)
+    assert np.array_equal(ffo.weighted_median(const, E, 2), const)
+    E2 = np.full((H, W), 6000, np.int32)
+    E2[5, 6] = 0  # weight 65536 against 24 * 10
+    got2 = ffo.weighted_median(F, E2, 2)
+    assert tuple(got2[5, 6]) == tuple(F[5, 6])
+    smooth = np.zeros((H, W, 2), np.int32)
+    smooth[..., 0] = 3
+    smooth[6, 6] = (40, -30)
+    assert np.array_equal(ffo.weighted_median(smooth, E, 1)[6, 6], [3, 0])
+
+
+def test_match_errors_are_the_data_term(ffo):
+    """E(p) is E_d of the pixel's own flow at full resolution: zero for a frame
+    paired with itself under the zero flow; equal to patch_cost otherwise."""
+    rng = np.random.default_rng(10)
+    I1 = rng.integers(0, 256, size=(20, 24, 3)).astype(np.uint8)
+    I2 = rng.integers(0, 256, size=(20, 24, 3)).astype(np.uint8)
+    Z = np.zeros((20, 24, 2), np.int32)
+    assert np.all(ffo.match_errors(I1, I1, Z, 3) == 0)
+    F = rng.integers(-4, 5, size=(20, 24, 2)).astype(np.int32)
+    F[..., 0] = np.clip(np.arange(24)[None, :] + F[..., 0], 0, 23) - np.arange(24)[None, :]
+    F[..., 1] = np.clip(np.arange(20)[:, None] + F[..., 1], 0, 19) - np.arange(20)[:, None]
+    E = ffo.match_errors(I1, I2, F, 3)
+    C1, C2 = ffo.census(I1, 1), ffo.census(I2, 1)
+    for (y, x) in [(0, 0), (5, 7), (19, 23), (10, 12)]:
+        assert E[y, x] == ffo.patch_cost(C1, C2, 1, 3, (x, y), (x + F[y, x, 0], y + F[y, x, 1]))

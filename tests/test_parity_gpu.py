@@ -431,3 +431,28 @@ def test_flow_fields_lab_128x96(seed):
     out = ffapi.FlowFields(128, 96, params).run(tg(p["I1"]), tg(p["I2"]))
     torch.cuda.synchronize()
     _compare(out, O.flow_fields(p["I1"], p["I2"], params=params, threads=3))
+
+
+# ------------------------------------------------- weighted median field ------
+@pytest.mark.parametrize("rho", [1, 2, 3])
+def test_weighted_median_field(rho):
+    """ff_weighted_median against the oracle on the forward field of the whole
+    path (128x96) and on a field with random outliers: flows and matching errors
+    bit for bit."""
+    p = synth.pair_for_config(1, 8)
+    out = ffapi.FlowFields(128, 96).run(tg(p["I1"]), tg(p["I2"]))
+    F = out["flows"][0].clone()
+    torch.cuda.synchronize()
+    Fn = cpu(F).astype(np.int32)
+    rng = np.random.default_rng(rho)
+    G = Fn.copy()
+    m = rng.random(G.shape[:2]) < 0.1
+    G[m] += rng.integers(-30, 31, size=(int(m.sum()), 2))
+    ys, xs = np.mgrid[0:96, 0:128]
+    G[..., 0] = np.clip(xs + G[..., 0], 0, 127) - xs
+    G[..., 1] = np.clip(ys + G[..., 1], 0, 95) - ys
+    for field in (Fn, G):
+        med, E = ffapi.ff_weighted_median(tg(p["I1"]), tg(p["I2"]), tg(field.astype(np.int16)), 8, rho)
+        Eo = O.match_errors(p["I1"], p["I2"], field, 8)
+        assert np.array_equal(cpu(E), Eo)
+        assert np.array_equal(cpu(med).astype(np.int32), O.weighted_median(field, Eo, rho))
