@@ -67,6 +67,12 @@ typedef struct ff_params {
   int32_t K;    /* proposals per coarsest grid point for the forward flow (0..8) */
   int32_t color; /* 0: the input RGB channels; 1: integer CIELab (ff_rgb_to_lab) of
                     both frames before every other step (Sec. 3.1, 3.3) */
+  int32_t subpel; /* 1, 2 or 4: flows in units of 1/subpel pixel. With 2 or 4 the
+                    random search draws subpixel offsets and every subpixel target
+                    reads the census of the target frame interpolated there
+                    (bilinear colours, Sec. 3.1), exactly in integers; the filter's
+                    thresholds scale likewise (ff_flow_fields / _batch / graphs;
+                    the per-level entry points take subpel = 1) */
   uint64_t seed; /* seed of the counter-based random search */
 } ff_params;
 

@@ -40,14 +40,16 @@ def build(force=False):
 
 class Params(C.Structure):
     _fields_ = [(n, C.c_int32) for n in
-                ("k", "r", "r2", "leaf", "R", "eps", "e", "s", "tile", "n_rs", "K", "color")] + \
+                ("k", "r", "r2", "leaf", "R", "eps", "e", "s", "tile", "n_rs", "K", "color",
+                 "subpel")] + \
                [("seed", C.c_uint64)]
 
 
 def default_params(**kw):
     """Sec. 4 parameters (k=3, R=1, l=8, r=8, r2=6; Sintel eps/e/s = 5/4/50),
     tile T=16 for the parallel schedule, 3 random-search steps, no proposals."""
-    d = dict(k=3, r=8, r2=6, leaf=8, R=1, eps=5, e=4, s=50, tile=16, n_rs=3, K=0, color=0, seed=0)
+    d = dict(k=3, r=8, r2=6, leaf=8, R=1, eps=5, e=4, s=50, tile=16, n_rs=3, K=0, color=0,
+             subpel=1, seed=0)
     d.update(kw)
     return d
 
@@ -86,7 +88,8 @@ def lib():
             L.ffo_search_level.argtypes = [u32, u32, ci, ci, ci, ci, i32, ci, ci, ci,
                                            C.c_uint64, ci, i32, i32]
             L.ffo_search_level.restype = C.c_int64
-            L.ffo_consistency.argtypes = [i32, i32, i32, ci, ci, ci, u8, i32, i32, i32]
+            L.ffo_consistency.argtypes = [i32, i32, i32, ci, ci, ci, ci, u8, i32, i32, i32]
+            L.ffo_census_subpel.argtypes = [u8, ci, ci, ci, ci, ci, ci, u32]
             L.ffo_sqrt_sum_less.argtypes = [C.c_int64] * 4
             L.ffo_lab_gamma_table.argtypes = [i32]
             L.ffo_lab_matrix.argtypes = [i32]
@@ -95,7 +98,7 @@ def lib():
             L.ffo_rgb_to_lab.argtypes = [u8, ci, ci, u8]
             L.ffo_match_errors.argtypes = [u8, u8, i32, ci, ci, ci, i32]
             L.ffo_weighted_median.argtypes = [i32, i32, ci, ci, ci, i32]
-            L.ffo_region_filter.argtypes = [i32, u8, ci, ci, ci, u8]
+            L.ffo_region_filter.argtypes = [i32, u8, ci, ci, ci, ci, u8]
             L.ffo_sparsify.argtypes = [u8, i32, i32, i32, ci, ci, ci, i32, u8]
             L.ffo_flow_fields.argtypes = [u8, u8, ci, ci, C.POINTER(Params), i32, ci, i32, u8,
                                           i32, i32, u8, i64]
@@ -321,9 +324,18 @@ def search_level(Cs, Ct, n, r, flow_coarse=None, flow=None, cost=None, tile=16, 
     return flow, cost, int(ev)
 
 
-def consistency(F, Fb1, Fb2, eps, errors=False):
+def census_subpel(imgn, n, q, a, b):
+    """Census (spacing n) of the image interpolated at (x + a/q, y + b/q)."""
+    imgn = _c(imgn, np.uint8)
+    H, W = imgn.shape[:2]
+    out = np.empty((H, W), np.uint32)
+    lib().ffo_census_subpel(_p(imgn, C.c_uint8), W, H, n, q, a, b, _p(out, C.c_uint32))
+    return out
+
+
+def consistency(F, Fb1, Fb2, eps, errors=False, subpel=1):
     """Eq. 5 check: (valid_cc, err_sum = e1 + e2), and with errors=True also the
-    squared errors e1, e2 against the two backward flows."""
+    squared errors e1, e2 against the two backward flows (flows in 1/subpel px)."""
     F, Fb1, Fb2 = _c(F, np.int32), _c(Fb1, np.int32), _c(Fb2, np.int32)
     H, W = F.shape[:2]
     v = np.empty((H, W), np.uint8)
@@ -331,7 +343,7 @@ def consistency(F, Fb1, Fb2, eps, errors=False):
     e1 = np.empty((H, W), np.int32)
     e2 = np.empty((H, W), np.int32)
     lib().ffo_consistency(_p(F, C.c_int32), _p(Fb1, C.c_int32), _p(Fb2, C.c_int32), W, H, eps,
-                          _p(v, C.c_uint8), _p(e, C.c_int32), _p(e1, C.c_int32),
+                          subpel, _p(v, C.c_uint8), _p(e, C.c_int32), _p(e1, C.c_int32),
                           _p(e2, C.c_int32))
     return (v, e, e1, e2) if errors else (v, e)
 
@@ -341,11 +353,11 @@ def sqrt_sum_less(a, b, c, d):
     return bool(lib().ffo_sqrt_sum_less(int(a), int(b), int(c), int(d)))
 
 
-def region_filter(F, valid_cc, s):
+def region_filter(F, valid_cc, s, subpel=1):
     F, valid_cc = _c(F, np.int32), _c(valid_cc, np.uint8)
     H, W = valid_cc.shape
     out = np.empty((H, W), np.uint8)
-    lib().ffo_region_filter(_p(F, C.c_int32), _p(valid_cc, C.c_uint8), W, H, s,
+    lib().ffo_region_filter(_p(F, C.c_int32), _p(valid_cc, C.c_uint8), W, H, s, subpel,
                             _p(out, C.c_uint8))
     return out
 

@@ -254,6 +254,48 @@ void ffo_census(const uint8_t *imgn, int W, int H, int n, uint32_t *out) {
     }
 }
 
+/* Sec. 3.1: the random search's subpixel targets take their colours from
+ * bilinear interpolation. Reading (subpel q in {1, 2, 4}): flows are kept in
+ * units of 1/q pixel; a target X = q x + a, Y = q y + b (0 <= a, b < q) reads
+ * the census of the image interpolated at (x + a/q, y + b/q):
+ *   J(x, y) = sum_{i,j in {0,1}} wx_i wy_j I^n(clamp(x + i), clamp(y + j)),
+ *   wx_0 = q - a, wx_1 = a, wy_0 = q - b, wy_1 = b
+ * (q^2 times the interpolated colour, kept exact), with the census of J at
+ * spacing n as in ffo_census. Phase (0, 0) is q^2 I^n: the plain census. */
+void ffo_census_subpel(const uint8_t *imgn, int W, int H, int n, int q, int a, int b,
+                       uint32_t *out) {
+  size_t N = (size_t)W * H;
+  int32_t *J = malloc(sizeof(int32_t) * N * 3);
+  int wx[2] = {q - a, a}, wy[2] = {q - b, b};
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++)
+      for (int c = 0; c < 3; c++) {
+        int32_t v = 0;
+        for (int j = 0; j < 2; j++)
+          for (int i = 0; i < 2; i++)
+            v += wx[i] * wy[j] *
+                 imgn[((size_t)clampi(y + j, 0, H - 1) * W + clampi(x + i, 0, W - 1)) * 3 + c];
+        J[((size_t)y * W + x) * 3 + c] = v;
+      }
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++) {
+      uint32_t code = 0;
+      for (int c = 0; c < 3; c++) {
+        int32_t centre = J[((size_t)y * W + x) * 3 + c];
+        int o = 0;
+        for (int dy = -1; dy <= 1; dy++)
+          for (int dx = -1; dx <= 1; dx++) {
+            if (dx == 0 && dy == 0) continue;
+            int xx = clampi(x + n * dx, 0, W - 1), yy = clampi(y + n * dy, 0, H - 1);
+            if (J[((size_t)yy * W + xx) * 3 + c] < centre) code |= 1u << (8 * c + o);
+            o++;
+          }
+      }
+      out[(size_t)y * W + x] = code;
+    }
+  free(J);
+}
+
 static int popcount32(uint32_t v) { return __builtin_popcount(v); }
 
 /* E_d of Eq. 1/3/4 with the census data term: the summed census Hamming
@@ -441,20 +483,25 @@ int ffo_kd_query(const int32_t *split_dim, const int32_t *split_val, int D, cons
 /* decreases", Sec. 3.1); earlier candidates win ties.                      */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-  const uint32_t *Cs, *Ct;
-  int W, H, n, r;
+  const uint32_t *Cs;
+  const uint32_t *const *Ct; /* target census per subpixel phase b * q + a */
+  int W, H, n, r, q;
   int64_t evals;
 } level_ctx;
 
+/* Flows are in units of 1/q pixel (q = 1: pixels). The target X = q px + fx is
+ * clamped to [0, q (W - 1)] (and Y likewise), so it stays inside the image. */
 static void try_candidate(level_ctx *L, int px, int py, int fx, int fy, int32_t *flow,
                           int32_t *cost) {
-  int tx = clampi(px + fx, 0, L->W - 1), ty = clampi(py + fy, 0, L->H - 1);
-  int32_t e = ffo_patch_cost(L->Cs, L->Ct, L->W, L->H, L->n, L->r, px, py, tx, ty);
+  int q = L->q;
+  int X = clampi(q * px + fx, 0, q * (L->W - 1)), Y = clampi(q * py + fy, 0, q * (L->H - 1));
+  const uint32_t *Ct = L->Ct[(Y % q) * q + X % q];
+  int32_t e = ffo_patch_cost(L->Cs, Ct, L->W, L->H, L->n, L->r, px, py, X / q, Y / q);
   L->evals++;
   if (e < *cost) {
     *cost = e;
-    flow[0] = tx - px;
-    flow[1] = ty - py;
+    flow[0] = X - q * px;
+    flow[1] = Y - q * py;
   }
 }
 
@@ -464,9 +511,22 @@ static void try_candidate(level_ctx *L, int px, int py, int fx, int fy, int32_t 
  * ascending pixel index. Optional proposals (K per grid point, int32 pairs)
  * are tried afterwards in index order under the same strict-less rule.
  * tgt_feat: features of every target pixel; the tree is built here. */
+static int64_t kd_init_q(const int32_t *tgt_feat, const uint8_t *src_img, int W, int H, int r,
+                         int leaf, const uint32_t *Cs, const uint32_t *const *Ct, int q, int n,
+                         const int32_t *proposals, int K, int32_t *flow, int32_t *cost);
+
 int64_t ffo_kd_init(const int32_t *tgt_feat, const uint8_t *src_img, int W, int H, int r,
                     int leaf, const uint32_t *Cs, const uint32_t *Ct, int n,
                     const int32_t *proposals, int K, int32_t *flow, int32_t *cost) {
+  const uint32_t *Ct1[1] = {Ct};
+  return kd_init_q(tgt_feat, src_img, W, H, r, leaf, Cs, Ct1, 1, n, proposals, K, flow, cost);
+}
+
+/* With subpel q the leaf pixels and the proposals (in pixels) become flows of
+ * q (x2 - px) in 1/q pixel units. */
+static int64_t kd_init_q(const int32_t *tgt_feat, const uint8_t *src_img, int W, int H, int r,
+                         int leaf, const uint32_t *Cs, const uint32_t *const *Ct, int q, int n,
+                         const int32_t *proposals, int K, int32_t *flow, int32_t *cost) {
   int N = W * H, Gx = (W + n - 1) / n, Gy = (H + n - 1) / n, G = Gx * Gy;
   int D = ffo_kd_depth(N, leaf);
   int32_t *perm = malloc(sizeof(int32_t) * N);
@@ -480,7 +540,7 @@ int64_t ffo_kd_init(const int32_t *tgt_feat, const uint8_t *src_img, int W, int 
     pts[2 * g + 1] = (g / Gx) * n;
   }
   ffo_wht_features(src_img, W, H, r, pts, G, qf);
-  level_ctx L = {Cs, Ct, W, H, n, r, 0};
+  level_ctx L = {Cs, Ct, W, H, n, r, q, 0};
   for (int g = 0; g < G; g++) {
     int px = pts[2 * g], py = pts[2 * g + 1];
     int lf = ffo_kd_query(sd, sv, D, qf + (size_t)g * NFEAT);
@@ -499,10 +559,10 @@ int64_t ffo_kd_init(const int32_t *tgt_feat, const uint8_t *src_img, int W, int 
     cost[g] = COST_UNSET;
     f[0] = f[1] = 0;
     for (int k = 0; k < m; k++)
-      try_candidate(&L, px, py, cand[k] % W - px, cand[k] / W - py, f, &cost[g]);
+      try_candidate(&L, px, py, q * (cand[k] % W - px), q * (cand[k] / W - py), f, &cost[g]);
     for (int k = 0; k < K; k++)
-      try_candidate(&L, px, py, proposals[((size_t)g * K + k) * 2],
-                    proposals[((size_t)g * K + k) * 2 + 1], f, &cost[g]);
+      try_candidate(&L, px, py, q * proposals[((size_t)g * K + k) * 2],
+                    q * proposals[((size_t)g * K + k) * 2 + 1], f, &cost[g]);
   }
   free(perm);
   free(sd);
@@ -606,8 +666,10 @@ static void prop_pass(level_ctx *L, int s, int tile, int32_t *flow, int32_t *cos
   free(snap_c);
 }
 
-/* Random search: F + O_rnd with O_rnd uniform in [-R_n, R_n]^2 (integer reading
- * of the paper's subpixel offset), kept only if E_d decreases. */
+/* Random search: F + O_rnd with O_rnd uniform in [-R_n, R_n]^2, kept only if
+ * E_d decreases. The offset is drawn in units of 1/q pixel: integer pixels for
+ * q = 1, the paper's subpixel offsets (with interpolated target colours) for
+ * q = 2, 4; Rn is passed in those units. */
 static void random_search(level_ctx *L, uint64_t seed, int flow_id, int level, int step, int Rn,
                           int32_t *flow, int32_t *cost) {
   int n = L->n, Gx = (L->W + n - 1) / n, Gy = (L->H + n - 1) / n;
@@ -645,18 +707,26 @@ static void seed_level(level_ctx *L, const int32_t *flow_coarse, int32_t *flow, 
  * alternation P, RS, P, RS, P, RS, P (4 propagations, n_rs <= 3 random
  * searches, Sec. 3.1) with R_n = R * n (Sec. 3.2). Returns the number of E_d
  * evaluations (no candidate is skipped here). */
-int64_t ffo_search_level(const uint32_t *Cs, const uint32_t *Ct, int W, int H, int n, int r,
-                         const int32_t *flow_coarse, int tile, int n_rs, int R, uint64_t seed,
-                         int flow_id, int32_t *flow, int32_t *cost) {
-  level_ctx L = {Cs, Ct, W, H, n, r, 0};
+static int64_t search_level_q(const uint32_t *Cs, const uint32_t *const *Ct, int q, int W, int H,
+                              int n, int r, const int32_t *flow_coarse, int tile, int n_rs, int R,
+                              uint64_t seed, int flow_id, int32_t *flow, int32_t *cost) {
+  level_ctx L = {Cs, Ct, W, H, n, r, q, 0};
   int level = 0;
   while ((1 << level) < n) level++;
   if (flow_coarse) seed_level(&L, flow_coarse, flow, cost);
   for (int s = 0; s < 4; s++) {
     prop_pass(&L, s, tile, flow, cost);
-    if (s < 3 && s < n_rs) random_search(&L, seed, flow_id, level, s, R * n, flow, cost);
+    if (s < 3 && s < n_rs) random_search(&L, seed, flow_id, level, s, R * n * q, flow, cost);
   }
   return L.evals;
+}
+
+int64_t ffo_search_level(const uint32_t *Cs, const uint32_t *Ct, int W, int H, int n, int r,
+                         const int32_t *flow_coarse, int tile, int n_rs, int R, uint64_t seed,
+                         int flow_id, int32_t *flow, int32_t *cost) {
+  const uint32_t *Ct1[1] = {Ct};
+  return search_level_q(Cs, Ct1, 1, W, H, n, r, flow_coarse, tile, n_rs, R, seed, flow_id, flow,
+                        cost);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -670,12 +740,16 @@ int64_t ffo_search_level(const uint32_t *Cs, const uint32_t *Ct, int W, int H, i
 static int32_t clamp_i32(int64_t v) { return (int32_t)(v > INT32_MAX ? INT32_MAX : v); }
 
 void ffo_consistency(const int32_t *F, const int32_t *Fb1, const int32_t *Fb2, int W, int H,
-                     int eps, uint8_t *valid_cc, int32_t *err_sum, int32_t *e1_out,
+                     int eps, int q, uint8_t *valid_cc, int32_t *err_sum, int32_t *e1_out,
                      int32_t *e2_out) {
+  /* flows in units of 1/q pixel: the backward flows are read at the pixel
+   * nearest to the target (half rounded up), errors and eps in the same units */
+  eps *= q;
   for (int y = 0; y < H; y++)
     for (int x = 0; x < W; x++) {
       size_t p = (size_t)y * W + x;
-      int qx = x + F[2 * p], qy = y + F[2 * p + 1];
+      int qx = (int)floor_div((int64_t)q * x + F[2 * p] + q / 2, q);
+      int qy = (int)floor_div((int64_t)q * y + F[2 * p + 1] + q / 2, q);
       if (qx < 0 || qx >= W || qy < 0 || qy >= H) {
         valid_cc[p] = 0;
         err_sum[p] = INT32_MAX;
@@ -728,9 +802,9 @@ int ffo_sqrt_sum_less(int64_t a, int64_t b, int64_t c, int64_t d) {
   }
 }
 
-static int close3(const int32_t *F, size_t p, size_t q) {
+static int close3(const int32_t *F, size_t p, size_t q, int sub) { /* < 3 px, flows in 1/sub px */
   int64_t a = F[2 * p] - F[2 * q], b = F[2 * p + 1] - F[2 * q + 1];
-  return a * a + b * b < 9;
+  return a * a + b * b < 9ll * sub * sub;
 }
 
 /* Region filter. Pixels kept by the consistency check form regions: 4-connected
@@ -738,7 +812,7 @@ static int close3(const int32_t *F, size_t p, size_t q) {
  * with fewer than s pixels is deleted if one of its pixels has a 4-neighbour that
  * the consistency check removed and whose (raw) flow is within 3 px of it, i.e.
  * the region could absorb that outlier by the same rule. */
-void ffo_region_filter(const int32_t *F, const uint8_t *valid_cc, int W, int H, int s,
+void ffo_region_filter(const int32_t *F, const uint8_t *valid_cc, int W, int H, int s, int sub,
                        uint8_t *valid) {
   size_t N = (size_t)W * H;
   int32_t *label = malloc(sizeof(int32_t) * N), *queue = malloc(sizeof(int32_t) * N);
@@ -756,7 +830,7 @@ void ffo_region_filter(const int32_t *F, const uint8_t *valid_cc, int W, int H, 
         int xx = x + NB[k][0], yy = y + NB[k][1];
         if (xx < 0 || xx >= W || yy < 0 || yy >= H) continue;
         size_t q = (size_t)yy * W + xx;
-        if (!close3(F, p, q)) continue;
+        if (!close3(F, p, q, sub)) continue;
         if (!valid_cc[q]) {
           touches = 1;
           continue;
@@ -881,12 +955,14 @@ void ffo_weighted_median(const int32_t *F, const int32_t *E, int W, int H, int r
 typedef struct {
   int k, r, r2, leaf, R, eps, e, s, tile, n_rs, K;
   int color; /* 0: the RGB channels; 1: integer CIELab (Sec. 3.1 / 3.3) */
+  int subpel; /* flows in units of 1/subpel pixel: 1, 2 or 4 (Sec. 3.1 subpixel search) */
   uint64_t seed;
 } ffo_params;
 
 typedef struct {
   const uint8_t *src, *tgt;
-  uint32_t **Cs, **Ct; /* census per level index 0..k */
+  uint32_t **Cs;         /* source census per level 0..k (phase 0) */
+  uint32_t *(*Ct)[16];   /* target census per level and subpixel phase */
   int W, H, r, flow_id;
   const ffo_params *P;
   const int32_t *proposals;
@@ -903,18 +979,20 @@ static void *run_flow(void *arg) {
   int Gx = (W + ntop - 1) / ntop, Gy = (H + ntop - 1) / ntop;
   int32_t *flow = malloc(sizeof(int32_t) * 2 * (size_t)Gx * Gy);
   int32_t *cost = malloc(sizeof(int32_t) * (size_t)Gx * Gy);
-  J->evals = ffo_kd_init(tf, J->src, W, H, J->r, P->leaf, J->Cs[P->k], J->Ct[P->k], ntop,
-                         J->proposals, J->proposals ? P->K : 0, flow, cost);
+  int q = P->subpel;
+  J->evals = kd_init_q(tf, J->src, W, H, J->r, P->leaf, J->Cs[P->k],
+                       (const uint32_t *const *)J->Ct[P->k], q, ntop, J->proposals,
+                       J->proposals ? P->K : 0, flow, cost);
   free(tf);
-  J->evals += ffo_search_level(J->Cs[P->k], J->Ct[P->k], W, H, ntop, J->r, NULL, P->tile,
-                               P->n_rs, P->R, P->seed, J->flow_id, flow, cost);
+  J->evals += search_level_q(J->Cs[P->k], (const uint32_t *const *)J->Ct[P->k], q, W, H, ntop,
+                             J->r, NULL, P->tile, P->n_rs, P->R, P->seed, J->flow_id, flow, cost);
   for (int lv = P->k - 1; lv >= 0; lv--) {
     int n = 1 << lv;
     int gx = (W + n - 1) / n, gy = (H + n - 1) / n;
     int32_t *f2 = malloc(sizeof(int32_t) * 2 * (size_t)gx * gy);
     int32_t *c2 = malloc(sizeof(int32_t) * (size_t)gx * gy);
-    J->evals += ffo_search_level(J->Cs[lv], J->Ct[lv], W, H, n, J->r, flow, P->tile, P->n_rs,
-                                 P->R, P->seed, J->flow_id, f2, c2);
+    J->evals += search_level_q(J->Cs[lv], (const uint32_t *const *)J->Ct[lv], q, W, H, n, J->r,
+                               flow, P->tile, P->n_rs, P->R, P->seed, J->flow_id, f2, c2);
     free(flow);
     free(cost);
     flow = f2;
@@ -950,23 +1028,29 @@ int ffo_flow_fields(const uint8_t *I1_in, const uint8_t *I2_in, int W, int H,
     I1 = lab1;
     I2 = lab2;
   }
-  int nl = P->k + 1;
-  uint32_t *C1[16], *C2[16];
+  int nl = P->k + 1, q = P->subpel, nph = q * q;
+  /* census per frame, level and subpixel phase (phase 0 = the plain census) */
+  uint32_t *C1[16][16], *C2[16][16], *C1s[16], *C2s[16];
   uint8_t *sm = malloc(N * 3);
   for (int lv = 0; lv < nl; lv++) {
     int n = 1 << lv;
-    C1[lv] = malloc(sizeof(uint32_t) * N);
-    C2[lv] = malloc(sizeof(uint32_t) * N);
-    ffo_smooth(I1, W, H, n, sm);
-    ffo_census(sm, W, H, n, C1[lv]);
-    ffo_smooth(I2, W, H, n, sm);
-    ffo_census(sm, W, H, n, C2[lv]);
+    for (int f = 0; f < 2; f++) {
+      ffo_smooth(f == 0 ? I1 : I2, W, H, n, sm);
+      for (int ph = 0; ph < nph; ph++) {
+        uint32_t *c = malloc(sizeof(uint32_t) * N);
+        if (ph == 0) ffo_census(sm, W, H, n, c);
+        else ffo_census_subpel(sm, W, H, n, q, ph % q, ph / q, c);
+        (f == 0 ? C1 : C2)[lv][ph] = c;
+      }
+    }
+    C1s[lv] = C1[lv][0];
+    C2s[lv] = C2[lv][0];
   }
   free(sm);
   flow_job J[3] = {
-      {I1, I2, C1, C2, W, H, P->r, 0, P, proposals, flows, 0},
-      {I2, I1, C2, C1, W, H, P->r, 1, P, NULL, flows + 2 * N, 0},
-      {I2, I1, C2, C1, W, H, P->r2, 2, P, NULL, flows + 4 * N, 0},
+      {I1, I2, C1s, C2, W, H, P->r, 0, P, proposals, flows, 0},
+      {I2, I1, C2s, C1, W, H, P->r, 1, P, NULL, flows + 2 * N, 0},
+      {I2, I1, C2s, C1, W, H, P->r2, 2, P, NULL, flows + 4 * N, 0},
   };
   if (threads > 1) {
     pthread_t th[3];
@@ -975,14 +1059,15 @@ int ffo_flow_fields(const uint8_t *I1_in, const uint8_t *I2_in, int W, int H,
   } else {
     for (int i = 0; i < 3; i++) run_flow(&J[i]);
   }
-  for (int lv = 0; lv < nl; lv++) {
-    free(C1[lv]);
-    free(C2[lv]);
-  }
+  for (int lv = 0; lv < nl; lv++)
+    for (int ph = 0; ph < nph; ph++) {
+      free(C1[lv][ph]);
+      free(C2[lv][ph]);
+    }
   uint8_t *vcc = malloc(N);
   int32_t *e1 = malloc(sizeof(int32_t) * N), *e2 = malloc(sizeof(int32_t) * N);
-  ffo_consistency(flows, flows + 2 * N, flows + 4 * N, W, H, P->eps, vcc, err_sum, e1, e2);
-  ffo_region_filter(flows, vcc, W, H, P->s, valid);
+  ffo_consistency(flows, flows + 2 * N, flows + 4 * N, W, H, P->eps, q, vcc, err_sum, e1, e2);
+  ffo_region_filter(flows, vcc, W, H, P->s, q, valid);
   free(vcc);
   if (evals) *evals = J[0].evals + J[1].evals + J[2].evals;
   int n = ffo_sparsify(valid, e1, e2, flows, W, H, P->e, sparse, mask);

@@ -105,6 +105,7 @@ ff_status check_params(const ff_params *p) {
   if (p->tile < 2 || p->tile > MAX_TILE || (p->tile & 1)) return FF_ERR_INVALID_ARG;
   if (p->n_rs < 0 || p->n_rs > 3 || p->K < 0 || p->K > MAX_K) return FF_ERR_INVALID_ARG;
   if (p->color < 0 || p->color > 1) return FF_ERR_INVALID_ARG;
+  if (p->subpel != 1 && p->subpel != 2 && p->subpel != 4) return FF_ERR_INVALID_ARG;
   return FF_OK;
 }
 
@@ -168,7 +169,8 @@ static void plan_pair_body(Arena &a, int W, int H, const ff_params *p, PairPlan 
   const size_t N = (size_t)W * H;
   for (int f = 0; f < 2; f++) P.lab[f] = p->color == 1 ? a.take<uint8_t>(N * 3) : nullptr;
   for (int f = 0; f < 2; f++)
-    for (int lv = 0; lv <= p->k; lv++) P.planes[f][lv] = a.take<uint32_t>(planes_words(W, H, 1 << lv));
+    for (int lv = 0; lv <= p->k; lv++)
+      P.planes[f][lv] = a.take<uint32_t>(planes_words(W, H, 1 << lv, p->subpel));
   P.sm = a.take<uint8_t>(N * 3);
   size_t ss = 0;
   for (int lv = 1; lv <= p->k; lv++) ss = ss > smooth_scratch_bytes(W, H, 1 << lv) ? ss : smooth_scratch_bytes(W, H, 1 << lv);
@@ -313,8 +315,15 @@ static ff_status run_pairs(int np, const PairIO *io_in, const ff_params *p, void
           FF_TRY(launch_smooth(img[f], W, H, n, P.sm, P.smooth_scratch, ps));
           src = P.sm;
         }
+        const Planes pl = make_planes(P.planes[f][lv], W, H, n, p->subpel);
         FF_TRY(launch_census(src, W, H, n, P.census, ps));
-        FF_TRY(launch_planes(P.census, make_planes(P.planes[f][lv], W, H, n), ps));
+        FF_TRY(launch_planes(P.census, phase_view(pl, 0), ps));
+        // subpixel targets (params.subpel > 1): the census of every other phase
+        for (int ph = 1; ph < p->subpel * p->subpel; ph++) {
+          FF_TRY(launch_census_subpel(src, W, H, n, p->subpel, ph % p->subpel, ph / p->subpel,
+                                      P.census, ps));
+          FF_TRY(launch_planes(P.census, phase_view(pl, ph), ps));
+        }
       }
   }
 
@@ -340,8 +349,8 @@ static ff_status run_pairs(int np, const PairIO *io_in, const ff_params *p, void
     Q.D = P.kd[j].D;
     Q.leaf = p->leaf;
     Q.qfeat = P.qfeat[j];
-    Q.src = make_planes(P.planes[srcf[j]][k], W, H, ntop);
-    Q.tgt = make_planes(P.planes[tgtf[j]][k], W, H, ntop);
+    Q.src = make_planes(P.planes[srcf[j]][k], W, H, ntop, p->subpel);
+    Q.tgt = make_planes(P.planes[tgtf[j]][k], W, H, ntop, p->subpel);
     Q.r = rad[j];
     Q.proposals = (j == 0 && p->K > 0) ? (const uint32_t *)io[i].proposals : nullptr;
     Q.K = (j == 0) ? p->K : 0;
@@ -361,8 +370,8 @@ static ff_status run_pairs(int np, const PairIO *io_in, const ff_params *p, void
     const int W = io[i].W, H = io[i].H;
     SearchProblem &s = sp[t];
     s = SearchProblem{};
-    s.src = make_planes(P.planes[srcf[j]][lv], W, H, n);
-    s.tgt = make_planes(P.planes[tgtf[j]][lv], W, H, n);
+    s.src = make_planes(P.planes[srcf[j]][lv], W, H, n, p->subpel);
+    s.tgt = make_planes(P.planes[tgtf[j]][lv], W, H, n, p->subpel);
     s.r = rad[j];
     s.flow_id = j;
     if (lv == k) {
@@ -457,7 +466,7 @@ static ff_status run_pairs(int np, const PairIO *io_in, const ff_params *p, void
     const size_t N = (size_t)io[i].W * io[i].H;
     FF_TRY(launch_filter((const uint32_t *)io[i].flows, (const uint32_t *)(io[i].flows + 2 * N),
                          (const uint32_t *)(io[i].flows + 4 * N), io[i].W, io[i].H, p->eps, p->e,
-                         p->s, io[i].valid, io[i].err_sum, io[i].sparse, io[i].n_sparse,
+                         p->s, p->subpel, io[i].valid, io[i].err_sum, io[i].sparse, io[i].n_sparse,
                          io[i].mask, plans[i].filter_scratch, st));
   }
   mark(st, 3, MK_FILTER);
@@ -473,6 +482,9 @@ static size_t batch_ws_bytes(int np, const int *Ws, const int *Hs, const ff_para
 
 static ff_status check_pair(const PairIO &io, const ff_params *p) {
   FF_TRY(check_shape(io.W, io.H));
+  // flows in units of 1/subpel pixel must fit int16
+  if ((long long)(io.W - 1) * p->subpel > 32767 || (long long)(io.H - 1) * p->subpel > 32767)
+    return FF_ERR_SHAPE;
   if (!io.I1 || !io.I2 || !io.flows || !io.valid || !io.err_sum || !io.sparse || !io.n_sparse ||
       !io.mask)
     return FF_ERR_INVALID_ARG;
@@ -512,6 +524,7 @@ ff_status ff_params_preset(ff_params *p, int preset) {
   p->n_rs = 3;
   p->K = 0;
   p->color = 0;
+  p->subpel = 1;
   p->seed = 0;
   switch (preset) {
     case FF_PRESET_SINTEL: p->eps = 5; p->e = 4; p->s = 50; break;
@@ -681,6 +694,7 @@ ff_status ff_search_level(const uint32_t *census_src, const uint32_t *census_tgt
                           void *stream) {
   FF_TRY(check_shape(W, H));
   FF_TRY(check_params(p));
+  if (p->subpel != 1) return FF_ERR_INVALID_ARG;  // this entry takes one census per frame
   if (!census_src || !census_tgt || !flow || !cost || !aligned(flow, 4)) return FF_ERR_INVALID_ARG;
   if (flow_coarse && !aligned(flow_coarse, 4)) return FF_ERR_INVALID_ARG;
   if (!pow2_upto(n, 16) || r < 1 || r > PLANE_PAD || flow_id < 0 || flow_id > 3)
@@ -728,7 +742,7 @@ ff_status ff_consistency_filter(const int16_t *F, const int16_t *Fb1, const int1
   cudaStream_t st = (cudaStream_t)stream;
   FF_TRY(clear_status(ws, st));
   return launch_filter((const uint32_t *)F, (const uint32_t *)Fb1, (const uint32_t *)Fb2, W, H,
-                       p->eps, p->e, p->s, valid, err_sum, sparse, n_sparse, mask,
+                       p->eps, p->e, p->s, p->subpel, valid, err_sum, sparse, n_sparse, mask,
                        (char *)ws + WS_HEADER, st);
 }
 

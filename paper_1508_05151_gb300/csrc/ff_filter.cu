@@ -8,26 +8,37 @@
 //                and the labelling is unique. Components smaller than s that touch
 //                a consistency-rejected neighbour within 3 px are removed.
 //   sparsify     one pixel per aligned 3x3 block with >= e survivors (smallest
-//                e_1 + e_2, raster-first on ties), compacted in block raster order
-//                (per-CTA counts, their scan, then ranked writes: deterministic).
+//                sum of the two consistency errors, raster-first on ties),
+//                compacted in block raster order (per-CTA counts, their scan, then
+//                ranked writes: deterministic).
+// Flows are in units of 1/q pixel (q = 2^lq; q = 1: pixels): thresholds scale
+// by q, and a subpixel target reads the backward flows at its nearest pixel.
 #include "ff_internal.cuh"
 
 namespace ff {
 
-__device__ __forceinline__ bool close3(uint32_t a, uint32_t b) {
+__device__ __forceinline__ bool close3(uint32_t a, uint32_t b, int lq) {
   const int dx = flow_dx(a) - flow_dx(b), dy = flow_dy(a) - flow_dy(b);
-  return dx * dx + dy * dy < 9;
+  return dx * dx + dy * dy < (9 << (2 * lq));
+}
+
+// The pixel nearest to the target of flow f at pixel (x, y) (halves rounded up).
+__device__ __forceinline__ void target_pixel(int x, int y, uint32_t f, int lq, int &qx, int &qy) {
+  const int half = (1 << lq) >> 1;
+  qx = ((x << lq) + flow_dx(f) + half) >> lq;  // arithmetic shift: floor
+  qy = ((y << lq) + flow_dy(f) + half) >> lq;
 }
 
 __global__ void k_consistency(const uint32_t *__restrict__ F, const uint32_t *__restrict__ Fb1,
-                              const uint32_t *__restrict__ Fb2, int W, int H, int eps,
+                              const uint32_t *__restrict__ Fb2, int W, int H, int eps, int lq,
                               uint8_t *__restrict__ vcc, int32_t *__restrict__ err,
                               int32_t *__restrict__ parent) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= W * H) return;
   const int x = p % W, y = p / W;
   const uint32_t f = F[p];
-  const int qx = x + flow_dx(f), qy = y + flow_dy(f);
+  int qx, qy;
+  target_pixel(x, y, f, lq, qx, qy);
   uint8_t ok = 0;
   int32_t es = 0x7fffffff;
   if (qx >= 0 && qx < W && qy >= 0 && qy < H) {
@@ -35,7 +46,8 @@ __global__ void k_consistency(const uint32_t *__restrict__ F, const uint32_t *__
     const uint32_t b1 = Fb1[q], b2 = Fb2[q];
     const long long a0 = flow_dx(f) + flow_dx(b1), a1 = flow_dy(f) + flow_dy(b1);
     const long long c0 = flow_dx(f) + flow_dx(b2), c1 = flow_dy(f) + flow_dy(b2);
-    const long long e1 = a0 * a0 + a1 * a1, e2 = c0 * c0 + c1 * c1, e2eps = (long long)eps * eps;
+    const long long epsq = (long long)eps << lq;
+    const long long e1 = a0 * a0 + a1 * a1, e2 = c0 * c0 + c1 * c1, e2eps = epsq * epsq;
     ok = (e1 < e2eps) && (e2 < e2eps);
     es = (int32_t)min(e1 + e2, (long long)0x7fffffff);
   }
@@ -75,13 +87,13 @@ __device__ void uf_unite(int32_t *parent, int a, int b) {
 }
 
 __global__ void k_union(const uint32_t *__restrict__ F, const uint8_t *__restrict__ vcc, int W, int H,
-                        int32_t *parent) {
+                        int lq, int32_t *parent) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= W * H || !vcc[p]) return;
   const int x = p % W, y = p / W;
   const uint32_t f = F[p];
-  if (x + 1 < W && vcc[p + 1] && close3(f, F[p + 1])) uf_unite(parent, p, p + 1);
-  if (y + 1 < H && vcc[p + W] && close3(f, F[p + W])) uf_unite(parent, p, p + W);
+  if (x + 1 < W && vcc[p + 1] && close3(f, F[p + 1], lq)) uf_unite(parent, p, p + 1);
+  if (y + 1 < H && vcc[p + W] && close3(f, F[p + W], lq)) uf_unite(parent, p, p + W);
 }
 
 // Root without compression. In k_flatten each thread stores the root of its own
@@ -106,7 +118,7 @@ __global__ void k_flatten(const uint8_t *__restrict__ vcc, int N, int32_t *paren
 }
 
 __global__ void k_region_stats(const uint32_t *__restrict__ F, const uint8_t *__restrict__ vcc, int W,
-                               int H, const int32_t *__restrict__ parent, int32_t *size,
+                               int H, int lq, const int32_t *__restrict__ parent, int32_t *size,
                                uint8_t *touch) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const bool act = p < W * H && vcc[p];
@@ -118,10 +130,10 @@ __global__ void k_region_stats(const uint32_t *__restrict__ F, const uint8_t *__
   const int x = p % W, y = p / W;
   const uint32_t f = F[p];
   bool t = false;
-  if (x > 0 && !vcc[p - 1] && close3(f, F[p - 1])) t = true;
-  if (x + 1 < W && !vcc[p + 1] && close3(f, F[p + 1])) t = true;
-  if (y > 0 && !vcc[p - W] && close3(f, F[p - W])) t = true;
-  if (y + 1 < H && !vcc[p + W] && close3(f, F[p + W])) t = true;
+  if (x > 0 && !vcc[p - 1] && close3(f, F[p - 1], lq)) t = true;
+  if (x + 1 < W && !vcc[p + 1] && close3(f, F[p + 1], lq)) t = true;
+  if (y > 0 && !vcc[p - W] && close3(f, F[p - W], lq)) t = true;
+  if (y + 1 < H && !vcc[p + W] && close3(f, F[p + W], lq)) t = true;
   if (t) touch[root] = 1;
 }
 
@@ -185,10 +197,12 @@ __device__ __forceinline__ bool sum_sqrt_lt(long long a, long long b, long long 
 
 // Squared consistency errors of a pixel that passed Eq. 5 (target inside the image).
 __device__ __forceinline__ void pixel_errors(const uint32_t *F, const uint32_t *Fb1,
-                                             const uint32_t *Fb2, int W, int p, long long &e1,
-                                             long long &e2) {
+                                             const uint32_t *Fb2, int W, int lq, int p,
+                                             long long &e1, long long &e2) {
   const uint32_t f = F[p];
-  const int q = (p / W + flow_dy(f)) * W + (p % W + flow_dx(f));
+  int qx, qy;
+  target_pixel(p % W, p / W, f, lq, qx, qy);
+  const int q = qy * W + qx;
   const uint32_t b1 = Fb1[q], b2 = Fb2[q];
   const long long a0 = flow_dx(f) + flow_dx(b1), a1 = flow_dy(f) + flow_dy(b1);
   const long long c0 = flow_dx(f) + flow_dx(b2), c1 = flow_dy(f) + flow_dy(b2);
@@ -200,7 +214,7 @@ __global__ void __launch_bounds__(PICK_CTA) k_blocks(const uint8_t *__restrict__
                                                      const uint32_t *__restrict__ F,
                                                      const uint32_t *__restrict__ Fb1,
                                                      const uint32_t *__restrict__ Fb2, int W, int H,
-                                                     int e, int32_t *__restrict__ pick,
+                                                     int lq, int e, int32_t *__restrict__ pick,
                                                      int32_t *__restrict__ cta_count) {
   __shared__ int s_warp[PICK_CTA / 32];
   const int BX = (W + 2) / 3, BY = (H + 2) / 3;
@@ -216,7 +230,7 @@ __global__ void __launch_bounds__(PICK_CTA) k_blocks(const uint8_t *__restrict__
         if (!valid[p]) continue;
         cnt++;
         long long e1, e2;
-        pixel_errors(F, Fb1, Fb2, W, p, e1, e2);
+        pixel_errors(F, Fb1, Fb2, W, lq, p, e1, e2);
         if (best < 0 || sum_sqrt_lt(e1, e2, be1, be2)) {
           best = p;
           be1 = e1;
@@ -289,8 +303,11 @@ size_t filter_scratch_bytes(int W, int H) {
 }
 
 ff_status launch_filter(const uint32_t *F, const uint32_t *Fb1, const uint32_t *Fb2, int W, int H,
-                        int eps, int e, int s, uint8_t *valid, int32_t *err_sum, int32_t *sparse,
-                        int32_t *n_sparse, uint8_t *mask, void *scratch, cudaStream_t st) {
+                        int eps, int e, int s, int q, uint8_t *valid, int32_t *err_sum,
+                        int32_t *sparse, int32_t *n_sparse, uint8_t *mask, void *scratch,
+                        cudaStream_t st) {
+  if (q != 1 && q != 2 && q != 4) return FF_ERR_INVALID_ARG;
+  const int lq = q == 4 ? 2 : q - 1;
   const int N = W * H, NB = ((W + 2) / 3) * ((H + 2) / 3);
   Arena a(scratch, (size_t)-1);
   uint8_t *vcc = a.take<uint8_t>(N);
@@ -302,17 +319,17 @@ ff_status launch_filter(const uint32_t *F, const uint32_t *Fb1, const uint32_t *
   int32_t *cta_count = a.take<int32_t>(ncta);
   const int B = 256, g = (N + B - 1) / B;
   if (cudaMemsetAsync(touch, 0, N, st) != cudaSuccess) return FF_ERR_CUDA;
-  k_consistency<<<g, B, 0, st>>>(F, Fb1, Fb2, W, H, eps, vcc, err_sum, parent);
+  k_consistency<<<g, B, 0, st>>>(F, Fb1, Fb2, W, H, eps, lq, vcc, err_sum, parent);
   FF_CHECK_LAUNCH();
-  k_union<<<g, B, 0, st>>>(F, vcc, W, H, parent);
+  k_union<<<g, B, 0, st>>>(F, vcc, W, H, lq, parent);
   FF_CHECK_LAUNCH();
   k_flatten<<<g, B, 0, st>>>(vcc, N, parent, size);
   FF_CHECK_LAUNCH();
-  k_region_stats<<<g, B, 0, st>>>(F, vcc, W, H, parent, size, touch);
+  k_region_stats<<<g, B, 0, st>>>(F, vcc, W, H, lq, parent, size, touch);
   FF_CHECK_LAUNCH();
   k_region_apply<<<g, B, 0, st>>>(vcc, N, s, parent, size, touch, valid, mask);
   FF_CHECK_LAUNCH();
-  k_blocks<<<ncta, PICK_CTA, 0, st>>>(valid, F, Fb1, Fb2, W, H, e, pick, cta_count);
+  k_blocks<<<ncta, PICK_CTA, 0, st>>>(valid, F, Fb1, Fb2, W, H, lq, e, pick, cta_count);
   FF_CHECK_LAUNCH();
   k_pick_scan<<<1, 1024, 0, st>>>(cta_count, ncta, n_sparse);
   FF_CHECK_LAUNCH();

@@ -93,9 +93,16 @@ __host__ __device__ __forceinline__ int clampi(int v, int lo, int hi) {
 }
 
 // ---------------------------------------------------------------- planes -----
+// With subpixel flows (q = params.subpel > 1, flows in units of 1/q pixel) a
+// frame carries the census of its image interpolated at each subpixel phase
+// (a, b) = (X mod q, Y mod q) of a target X = q x + a, Y = q y + b: the planes of
+// phase (a, b) follow those of the phases before it, plane index
+// (b q + a) n^2 + (py n + px). Phase (0, 0) is the plain census, so integer
+// positions (every source patch, every q = 1 target) use the first n^2 planes.
 struct Planes {
   uint32_t *base;  // plane (px, py) at base + (py * n + px) * plane_words
   int W, H, n, log2n;
+  int q, log2q;     // subpixel phases per axis (1, 2, 4)
   int NX, NY;       // ceil(W/n), ceil(H/n)
   int pitch;        // words per padded row (>= NX + 2P, multiple of 4)
   int rows;         // NY + 2P
@@ -107,7 +114,7 @@ struct Planes {
   size_t plane_wordsT;  // pitchT * (NX + 2P)
 };
 
-__host__ __device__ inline Planes make_planes(uint32_t *base, int W, int H, int n) {
+__host__ __device__ inline Planes make_planes(uint32_t *base, int W, int H, int n, int q = 1) {
   Planes p;
   p.base = base;
   p.W = W;
@@ -116,6 +123,8 @@ __host__ __device__ inline Planes make_planes(uint32_t *base, int W, int H, int 
   int l = 0;
   while ((1 << l) < n) l++;
   p.log2n = l;
+  p.q = q;
+  p.log2q = q >= 4 ? 2 : (q >= 2 ? 1 : 0);
   p.NX = (W + n - 1) / n;
   p.NY = (H + n - 1) / n;
   p.pitch = ((p.NX + 2 * PLANE_PAD) + 3) & ~3;
@@ -123,12 +132,23 @@ __host__ __device__ inline Planes make_planes(uint32_t *base, int W, int H, int 
   p.plane_words = (size_t)p.pitch * p.rows;
   p.pitchT = ((p.NY + 2 * PLANE_PAD) + 3) & ~3;
   p.plane_wordsT = (size_t)p.pitchT * (p.NX + 2 * PLANE_PAD);
-  p.baseT = base ? base + p.plane_words * (size_t)n * n : nullptr;
+  p.baseT = base ? base + p.plane_words * (size_t)n * n * q * q : nullptr;
   return p;
 }
-__host__ __device__ inline size_t planes_words(int W, int H, int n) {
+__host__ __device__ inline size_t planes_words(int W, int H, int n, int q = 1) {
   Planes p = make_planes(nullptr, W, H, n);
-  return (p.plane_words + p.plane_wordsT) * (size_t)n * n;
+  return (p.plane_words + p.plane_wordsT) * (size_t)n * n * q * q;
+}
+// The n^2 planes of subpixel phase ph (= b q + a) as a plane set of their own
+// (for writing them).
+__host__ __device__ inline Planes phase_view(const Planes &P, int ph) {
+  Planes v = P;
+  const size_t per = (size_t)P.n * P.n;
+  v.base = P.base + per * P.plane_words * ph;
+  v.baseT = P.baseT + per * P.plane_wordsT * ph;
+  v.q = 1;
+  v.log2q = 0;
+  return v;
 }
 
 // Address of the centre tap of the patch around pixel (x, y), inside the image.
@@ -136,6 +156,35 @@ __device__ __forceinline__ const uint32_t *plane_centre(const Planes &P, int x, 
   int m = P.n - 1;
   const uint32_t *pl = P.base + (size_t)(((y & m) << P.log2n) + (x & m)) * P.plane_words;
   return pl + (size_t)((y >> P.log2n) + PLANE_PAD) * P.pitch + (x >> P.log2n) + PLANE_PAD;
+}
+
+// Plane index and entry of the target (X, Y) in units of 1/q pixel (X, Y >= 0
+// inside the image; for q = 1 the pixel itself).
+__device__ __forceinline__ void target_plane(const Planes &P, int X, int Y, int &ph, int &ex,
+                                             int &ey) {
+  const int m = P.n - 1, qm = P.q - 1;
+  const int x = X >> P.log2q, y = Y >> P.log2q;
+  ph = ((((Y & qm) << P.log2q) + (X & qm)) << (2 * P.log2n)) + ((y & m) << P.log2n) + (x & m);
+  ex = (x >> P.log2n) + PLANE_PAD;
+  ey = (y >> P.log2n) + PLANE_PAD;
+}
+__device__ __forceinline__ const uint32_t *target_centre(const Planes &P, int X, int Y) {
+  int ph, ex, ey;
+  target_plane(P, X, Y, ph, ex, ey);
+  return P.base + (size_t)ph * P.plane_words + (size_t)ey * P.pitch + ex;
+}
+// Candidate flow (dx, dy) (units of 1/q pixel) at pixel (px, py) with its target
+// clamped into the image: X = clamp(q px + dx, 0, q (W - 1)), likewise Y; returns
+// the clamped flow, packed.
+__device__ __forceinline__ uint32_t clamp_target(const Planes &P, int px, int py, int dx, int dy,
+                                                 int &X, int &Y) {
+  X = clampi((px << P.log2q) + dx, 0, (P.W - 1) << P.log2q);
+  Y = clampi((py << P.log2q) + dy, 0, (P.H - 1) << P.log2q);
+  return pack_flow(X - (px << P.log2q), Y - (py << P.log2q));
+}
+__device__ __forceinline__ uint32_t clamp_target(const Planes &P, int px, int py, uint32_t f,
+                                                 int &X, int &Y) {
+  return clamp_target(P, px, py, flow_dx(f), flow_dy(f), X, Y);
 }
 
 // ------------------------------------------------------- patch cost ---------
@@ -296,6 +345,11 @@ size_t smooth_scratch_bytes(int W, int H, int n);
 ff_status launch_smooth(const uint8_t *img, int W, int H, int n, uint8_t *out, void *scratch,
                         cudaStream_t st);
 ff_status launch_census(const uint8_t *imgn, int W, int H, int n, uint32_t *out, cudaStream_t st);
+// Census (spacing n) of imgn interpolated at subpixel phase (a, b) of q: the
+// colours q^2-scaled bilinear sums of the pixel and its right, lower and
+// lower-right neighbours (clamped), exact in integers.
+ff_status launch_census_subpel(const uint8_t *imgn, int W, int H, int n, int q, int a, int b,
+                               uint32_t *out, cudaStream_t st);
 ff_status launch_planes(const uint32_t *census, Planes P, cudaStream_t st);
 
 // -------------------------------------------------------------- colour -------
@@ -401,8 +455,10 @@ ff_status run_level(const SearchProblem *probs, SearchProblem *dev_desc, int npr
 
 // -------------------------------------------------------------- filter -------
 size_t filter_scratch_bytes(int W, int H);
+// Flows in units of 1/q pixel (q = 1: pixels).
 ff_status launch_filter(const uint32_t *F, const uint32_t *Fb1, const uint32_t *Fb2, int W, int H,
-                        int eps, int e, int s, uint8_t *valid, int32_t *err_sum, int32_t *sparse,
-                        int32_t *n_sparse, uint8_t *mask, void *scratch, cudaStream_t st);
+                        int eps, int e, int s, int q, uint8_t *valid, int32_t *err_sum,
+                        int32_t *sparse, int32_t *n_sparse, uint8_t *mask, void *scratch,
+                        cudaStream_t st);
 
 }  // namespace ff

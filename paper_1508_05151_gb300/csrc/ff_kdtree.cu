@@ -1036,7 +1036,7 @@ ff_status launch_kd_build(const KdBuild *trees, KdBuild *dev, int ntrees, cudaSt
 template <int R>
 __global__ void __launch_bounds__(256) k_kd_query(const KdQuery *qs) {
   const KdQuery &Q = qs[blockIdx.y];
-  const int NX = Q.src.NX, G = NX * Q.src.NY, n = Q.src.n, W = Q.src.W, H = Q.src.H;
+  const int NX = Q.src.NX, G = NX * Q.src.NY, n = Q.src.n, W = Q.src.W;
   const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
   const int l16 = threadIdx.x & 15;
   const unsigned gmask = 0xffffu << (threadIdx.x & 16);
@@ -1074,20 +1074,22 @@ __global__ void __launch_bounds__(256) k_kd_query(const KdQuery *qs) {
       bidx = idx;
     }
   }
-  int fx = bidx % W - px, fy = bidx / W - py;
+  // flows in units of 1/q pixel: leaf pixels and proposals (in pixels) scale by q
+  const int lq = Q.tgt.log2q;
+  uint32_t fbest = pack_flow((bidx % W - px) << lq, (bidx / W - py) << lq);
   for (int k = 0; k < Q.K; k++) {
     const uint32_t pr = Q.proposals[(size_t)g * Q.K + k];
-    const int tx = clampi(px + flow_dx(pr), 0, W - 1), ty = clampi(py + flow_dy(pr), 0, H - 1);
-    const int cost = group_cost<R>(sc, Q.src.pitch, plane_centre(Q.tgt, tx, ty), Q.tgt.pitch, l16,
+    int X, Y;
+    const uint32_t cf = clamp_target(Q.tgt, px, py, flow_dx(pr) << lq, flow_dy(pr) << lq, X, Y);
+    const int cost = group_cost<R>(sc, Q.src.pitch, target_centre(Q.tgt, X, Y), Q.tgt.pitch, l16,
                                    gmask);
     if (cost < best) {
       best = cost;
-      fx = tx - px;
-      fy = ty - py;
+      fbest = cf;
     }
   }
   if (l16 == 0) {
-    Q.flow[g] = pack_flow(fx, fy);
+    Q.flow[g] = fbest;
     Q.cost[g] = best;
   }
 }

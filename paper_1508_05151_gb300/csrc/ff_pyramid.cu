@@ -153,6 +153,51 @@ ff_status launch_census(const uint8_t *imgn, int W, int H, int n, uint32_t *out,
   return FF_OK;
 }
 
+// Sec. 3.1, subpixel targets: the census of I^n interpolated at (x + a/q,
+// y + b/q). Colours are q^2 times the bilinear value, sum over i, j in {0, 1} of
+// (i ? a : q - a) (j ? b : q - b) I^n(clamp(x + i), clamp(y + j)), so every
+// comparison is exact; the census compares them as k_census compares pixels.
+__device__ __forceinline__ void interp_px(const uint8_t *__restrict__ img, int W, int H, int x,
+                                          int y, int q, int a, int b, int *c) {
+  const int x1 = min(x + 1, W - 1), y1 = min(y + 1, H - 1);
+  const uint8_t *p00 = img + ((size_t)y * W + x) * 3, *p10 = img + ((size_t)y * W + x1) * 3;
+  const uint8_t *p01 = img + ((size_t)y1 * W + x) * 3, *p11 = img + ((size_t)y1 * W + x1) * 3;
+  const int w00 = (q - a) * (q - b), w10 = a * (q - b), w01 = (q - a) * b, w11 = a * b;
+#pragma unroll
+  for (int ch = 0; ch < 3; ch++) c[ch] = w00 * p00[ch] + w10 * p10[ch] + w01 * p01[ch] + w11 * p11[ch];
+}
+
+__global__ void k_census_subpel(const uint8_t *__restrict__ img, int W, int H, int n, int q, int a,
+                                int b, uint32_t *__restrict__ out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= H) return;
+  int ctr[3];
+  interp_px(img, W, H, x, y, q, a, b, ctr);
+  uint32_t code = 0;
+  int o = 0;
+#pragma unroll
+  for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+    for (int dx = -1; dx <= 1; dx++) {
+      if (dx == 0 && dy == 0) continue;
+      int v[3];
+      interp_px(img, W, H, clampi(x + n * dx, 0, W - 1), clampi(y + n * dy, 0, H - 1), q, a, b, v);
+      code |= (uint32_t)(v[0] < ctr[0]) << o;
+      code |= (uint32_t)(v[1] < ctr[1]) << (8 + o);
+      code |= (uint32_t)(v[2] < ctr[2]) << (16 + o);
+      o++;
+    }
+  out[(size_t)y * W + x] = code;
+}
+
+ff_status launch_census_subpel(const uint8_t *imgn, int W, int H, int n, int q, int a, int b,
+                               uint32_t *out, cudaStream_t st) {
+  dim3 bl(32, 8), g((W + 31) / 32, (H + 7) / 8);
+  k_census_subpel<<<g, bl, 0, st>>>(imgn, W, H, n, q, a, b, out);
+  FF_CHECK_LAUNCH();
+  return FF_OK;
+}
+
 // Relayout of a plain census image into the padded phase planes and their
 // transposed copies.
 __global__ void k_planes(const uint32_t *__restrict__ census, Planes P) {

@@ -54,11 +54,12 @@ __device__ __forceinline__ void seed_block(const SearchProblem &P, int c, int l1
   }
   const uint32_t f = P.flow_coarse[c];
   const int px = gx * n, py = gy * n;
-  const int tx = clampi(px + flow_dx(f), 0, P.src.W - 1), ty = clampi(py + flow_dy(f), 0, P.src.H - 1);
+  int X, Y;
+  const uint32_t cf = clamp_target(P.tgt, px, py, f, X, Y);
   const int cost = group_cost<R>(plane_centre(P.src, px, py), P.src.pitch,
-                                 plane_centre(P.tgt, tx, ty), P.tgt.pitch, l16, gmask);
+                                 target_centre(P.tgt, X, Y), P.tgt.pitch, l16, gmask);
   if (l16 == 0) {
-    P.flow_a[(size_t)gy * NX + gx] = pack_flow(tx - px, ty - py);
+    P.flow_a[(size_t)gy * NX + gx] = cf;
     P.cost_a[(size_t)gy * NX + gx] = cost;
   }
 }
@@ -97,14 +98,12 @@ __global__ void __launch_bounds__(256) k_rs(const SearchProblem *probs, int s, i
   if (cc == COST_UNSET) return;
   const uint32_t cur = fl[g];
   const int gx = g % NX, gy = g / NX, px = gx * n, py = gy * n;
-  int ox, oy;
-  rs_offset(seed, P.flow_id, log2n, s, gx, gy, Rfull * n, ox, oy);
-  const int tx = clampi(px + flow_dx(cur) + ox, 0, P.src.W - 1);
-  const int ty = clampi(py + flow_dy(cur) + oy, 0, P.src.H - 1);
-  const uint32_t cf = pack_flow(tx - px, ty - py);
+  int ox, oy, X, Y;
+  rs_offset(seed, P.flow_id, log2n, s, gx, gy, (Rfull * n) << P.tgt.log2q, ox, oy);
+  const uint32_t cf = clamp_target(P.tgt, px, py, flow_dx(cur) + ox, flow_dy(cur) + oy, X, Y);
   if (cf == cur) return;
   const int cost = group_cost<R>(plane_centre(P.src, px, py), P.src.pitch,
-                                 plane_centre(P.tgt, tx, ty), P.tgt.pitch, l16, gmask);
+                                 target_centre(P.tgt, X, Y), P.tgt.pitch, l16, gmask);
   if (l16 == 0 && cost < cc) {
     fl[g] = cf;
     co[g] = cost;
@@ -200,7 +199,7 @@ __device__ __forceinline__ void stage_tile(const SearchProblem &P, const TileLay
                                            int vdy, const uint32_t *fin, const int32_t *cin,
                                            const TileSmem &S, int sl, int width, int &tox,
                                            int &toy, int &ph0) {
-  const int Gx = P.src.NX, Gy = P.src.NY, n = P.src.n, log2n = P.src.log2n;
+  const int Gx = P.src.NX, Gy = P.src.NY, n = P.src.n;
   const int tw = live ? x1 - x0 : 0, th = live ? y1 - y0 : 0;
   for (int i = sl; i < tw * th; i += width) {
     const int lx = i % tw, ly = i / tw;
@@ -246,12 +245,12 @@ __device__ __forceinline__ void stage_tile(const SearchProblem &P, const TileLay
     const size_t g = (size_t)gy * Gx + gx;
     if (cin[g] != COST_UNSET) {
       const uint32_t fc = fin[g];
-      const int m = n - 1;
-      const int cx = gx * n + flow_dx(fc), cy = gy * n + flow_dy(fc);
+      const int X = ((gx * n) << P.tgt.log2q) + flow_dx(fc), Y = ((gy * n) << P.tgt.log2q) + flow_dy(fc);
+      int cex, cey;
+      target_plane(P.tgt, X, Y, ph0, cex, cey);  // shifts floor: X, Y may be outside
       const int slack = Lt.tw - (tw + 2 * R + 2);
-      tox = (x0 - R - 1) + ((cx >> log2n) - gx) + PLANE_PAD - slack / 2;
-      toy = (y0 - R - 1) + ((cy >> log2n) - gy) + PLANE_PAD - slack / 2;
-      ph0 = ((cy & m) << log2n) + (cx & m);
+      tox = (x0 - R - 1) + (cex - gx) - slack / 2;
+      toy = (y0 - R - 1) + (cey - gy) - slack / 2;
     }
   }
   if (ph0 >= 0) {
@@ -327,7 +326,6 @@ __global__ void __launch_bounds__(PASS_MAX_WARPS * 32) k_pass(const SearchProble
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tpw = 1, width = 32, sub = 0, sl = lane;
   const int Gx = P.src.NX, Gy = P.src.NY, n = P.src.n, log2n = P.src.log2n;
-  const int W = P.src.W, H = P.src.H;
   const int T = cfg.tile, off = (cfg.s & 1) * (T >> 1);
   const int ntx = (Gx + off + T - 1) / T, nty = (Gy + off + T - 1) / T;
   const int tile = (blockIdx.x * (blockDim.x >> 5) + warp) * tpw + sub;
@@ -367,13 +365,10 @@ __global__ void __launch_bounds__(PASS_MAX_WARPS * 32) k_pass(const SearchProble
     int ph, ex, ey;
     bool win;
   };
-  auto locate = [&](int px, int py, uint32_t f) {
+  auto locate = [&](int px, int py, uint32_t f) {  // f: a clamped flow
     Tgt t;
-    const int txx = px + flow_dx(f), tyy = py + flow_dy(f);
-    const int m = n - 1;
-    t.ph = ((tyy & m) << log2n) + (txx & m);
-    t.ex = (txx >> log2n) + PLANE_PAD;
-    t.ey = (tyy >> log2n) + PLANE_PAD;
+    target_plane(P.tgt, (px << P.tgt.log2q) + flow_dx(f), (py << P.tgt.log2q) + flow_dy(f), t.ph,
+                 t.ex, t.ey);
     t.win = t.ph == ph0 && t.ex - R - 1 >= tox && t.ex + R + 1 < tox + Lt.tw &&
             t.ey - R - 1 >= toy && t.ey + R + 1 < toy + Lt.tw;
     return t;
@@ -387,8 +382,8 @@ __global__ void __launch_bounds__(PASS_MAX_WARPS * 32) k_pass(const SearchProble
   if (cfg.evals && lane < 4) scnt[lane] = 0;
   auto evaluate = [&](int c, int lx, int ly, int px, int py, uint32_t fq, int32_t cq, int &cost) {
     const uint32_t *sc = s_src + (ly + R + 1) * Lt.swp + (lx + R + 1);
-    const int tgx = clampi(px + flow_dx(fq), 0, W - 1), tgy = clampi(py + flow_dy(fq), 0, H - 1);
-    const uint32_t cf = pack_flow(tgx - px, tgy - py);
+    int X, Y;
+    const uint32_t cf = clamp_target(P.tgt, px, py, fq, X, Y);
     const Tgt t = locate(px, py, cf);
     if (cfg.evals) count_eval(scnt, cf != fq, t.win);
     if (cf == fq) {
@@ -438,8 +433,8 @@ __global__ void __launch_bounds__(PASS_MAX_WARPS * 32) k_pass(const SearchProble
     return cf;
   };
   auto clamp_flow = [&](int px, int py, uint32_t fq) {
-    const int tgx = clampi(px + flow_dx(fq), 0, W - 1), tgy = clampi(py + flow_dy(fq), 0, H - 1);
-    return pack_flow(tgx - px, tgy - py);
+    int X, Y;
+    return clamp_target(P.tgt, px, py, fq, X, Y);
   };
 
   // ---- wavefront over scan anti-diagonals ----
@@ -543,18 +538,16 @@ __global__ void __launch_bounds__(PASS_MAX_WARPS * 32) k_pass(const SearchProble
 
   // ---- random search: every lane evaluates the candidates of its own points ----
   if (cfg.do_rs) {
-    const int Rn = cfg.R * n;
+    const int Rn = (cfg.R * n) << P.tgt.log2q;  // offsets in units of 1/q pixel
     for (int i = sl; i < tw * th; i += width) {
       const int lx = i % tw, ly = i / tw;
       const uint32_t cur = s_flow[ly * T + lx];
       const int32_t cc = s_cost[ly * T + lx];
       if (cc == COST_UNSET) continue;
       const int gx = x0 + lx, gy = y0 + ly, px = gx * n, py = gy * n;
-      int ox, oy;
+      int ox, oy, X, Y;
       rs_offset(cfg.seed, P.flow_id, log2n, cfg.s, gx, gy, Rn, ox, oy);
-      const int tgx = clampi(px + flow_dx(cur) + ox, 0, W - 1);
-      const int tgy = clampi(py + flow_dy(cur) + oy, 0, H - 1);
-      const uint32_t cf = pack_flow(tgx - px, tgy - py);
+      const uint32_t cf = clamp_target(P.tgt, px, py, flow_dx(cur) + ox, flow_dy(cur) + oy, X, Y);
       if (cf == cur) continue;
       const Tgt t = locate(px, py, cf);
       if (cfg.evals) count_eval(scnt, true, t.win);
@@ -640,7 +633,6 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
   constexpr int WIDE_THREADS = 32 * SPLIT;
   const int t = threadIdx.x, lane = t & 31;
   const int Gx = P.src.NX, Gy = P.src.NY, n = P.src.n, log2n = P.src.log2n;
-  const int W = P.src.W, H = P.src.H;
   const int T = cfg.tile, off = (cfg.s & 1) * (T >> 1);
   const int ntx = (Gx + off + T - 1) / T;
   const int tx = tile % ntx, ty = tile / ntx;
@@ -674,8 +666,8 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
            ey + R + 1 < toy + Lt.tw;
   };
   auto clamp_flow = [&](int px, int py, uint32_t fq) {
-    const int tgx = clampi(px + flow_dx(fq), 0, W - 1), tgy = clampi(py + flow_dy(fq), 0, H - 1);
-    return pack_flow(tgx - px, tgy - py);
+    int X, Y;
+    return clamp_target(P.tgt, px, py, fq, X, Y);
   };
 
   const int row = t / (2 * SPLIT), cand = (t / SPLIT) & 1, u = t & (SPLIT - 1);
@@ -716,9 +708,9 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
       const uint32_t fq = cand == 0 ? fh : fv, cf = cand == 0 ? cfh : cfv;
       const int32_t cq = cand == 0 ? ch : cv;
       const uint32_t *sc = S.src + (ly + R + 1) * Lt.swp + (lx + R + 1);
-      const int txx = px + flow_dx(cf), tyy = py + flow_dy(cf), m = n - 1;
-      const int ph = ((tyy & m) << log2n) + (txx & m);
-      const int ex = (txx >> log2n) + PLANE_PAD, ey = (tyy >> log2n) + PLANE_PAD;
+      int ph, ex, ey;
+      target_plane(P.tgt, (px << P.tgt.log2q) + flow_dx(cf), (py << P.tgt.log2q) + flow_dy(cf), ph,
+                   ex, ey);
       const bool win = in_win(ph, ex, ey);
       if (cfg.evals && u == 0) count_eval(scnt, cf != fq, win);
       if (cf == fq) {  // incremental: E(q, f) - outgoing line + incoming line
@@ -782,7 +774,7 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
   }
 
   if (cfg.do_rs) {  // random search, one thread per point, points column by column
-    const int Rn = cfg.R * n;
+    const int Rn = (cfg.R * n) << P.tgt.log2q;  // offsets in units of 1/q pixel
     for (int i = t; i < tw * th; i += WIDE_THREADS) {
       const int ly = i % th, lx = i / th;
       const uint32_t cur = S.flow[ly * T + lx];
@@ -791,12 +783,11 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
       const int gx = x0 + lx, gy = y0 + ly, px = gx * n, py = gy * n;
       int ox, oy;
       rs_offset(cfg.seed, P.flow_id, log2n, cfg.s, gx, gy, Rn, ox, oy);
-      const int tgx = clampi(px + flow_dx(cur) + ox, 0, W - 1);
-      const int tgy = clampi(py + flow_dy(cur) + oy, 0, H - 1);
-      const uint32_t cf = pack_flow(tgx - px, tgy - py);
+      int X, Y;
+      const uint32_t cf = clamp_target(P.tgt, px, py, flow_dx(cur) + ox, flow_dy(cur) + oy, X, Y);
       if (cf == cur) continue;
-      const int m = n - 1, ph = ((tgy & m) << log2n) + (tgx & m);
-      const int ex = (tgx >> log2n) + PLANE_PAD, ey = (tgy >> log2n) + PLANE_PAD;
+      int ph, ex, ey;
+      target_plane(P.tgt, X, Y, ph, ex, ey);
       const uint32_t *sc = S.src + (ly + R + 1) * Lt.swp + (lx + R + 1);
       const bool win = in_win(ph, ex, ey);
       if (cfg.evals) count_eval(scnt, true, win);

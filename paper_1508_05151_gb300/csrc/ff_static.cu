@@ -68,6 +68,6 @@ extern "C" ff_status ff_consistency_filter_static(const int16_t *F, const int16_
   // launch_filter clears the per-region flags it needs zeroed on the stream and
   // writes every other scratch word before reading it.
   return launch_filter((const uint32_t *)F, (const uint32_t *)Fb1, (const uint32_t *)Fb2, W, H,
-                       p->eps, p->e, p->s, valid, err_sum, sparse, n_sparse, mask, scratch,
+                       p->eps, p->e, p->s, p->subpel, valid, err_sum, sparse, n_sparse, mask, scratch,
                        (cudaStream_t)stream);
 }

@@ -53,12 +53,12 @@ class NetDesc(C.Structure):
 class Params(C.Structure):
     """ff_params; defaults are the Sintel preset of Sec. 4."""
     _fields_ = [(n, C.c_int32) for n in
-                ("k", "r", "r2", "leaf", "R", "eps", "e", "s", "tile", "n_rs", "K", "color")] + \
-               [("seed", C.c_uint64)]
+                ("k", "r", "r2", "leaf", "R", "eps", "e", "s", "tile", "n_rs", "K", "color",
+                 "subpel")] + [("seed", C.c_uint64)]
 
     def __init__(self, **kw):
         d = dict(k=3, r=8, r2=6, leaf=8, R=1, eps=5, e=4, s=50, tile=16, n_rs=3, K=0, color=0,
-                 seed=0)
+                 subpel=1, seed=0)
         unknown = set(kw) - set(d)
         if unknown:
             raise TypeError(f"unknown parameters {sorted(unknown)}")

@@ -767,3 +767,77 @@ def test_match_errors_are_the_data_term(ffo):
     C1, C2 = ffo.census(I1, 1), ffo.census(I2, 1)
     for (y, x) in [(0, 0), (5, 7), (19, 23), (10, 12)]:
         assert E[y, x] == ffo.patch_cost(C1, C2, 1, 3, (x, y), (x + F[y, x, 0], y + F[y, x, 1]))
+
+
+# ------------------------------------------------ subpixel random search -------
+def _subpel_pair(q, axis, seed=11, W=96, H=72):
+    """Frame 1 is frame 2 sampled 1/q pixel further along `axis` (0: x, 1: y), with
+    frame 2 quantised so that the sample ((q - 1) I2(p) + I2(p + e)) / q is an
+    exact integer: the forward flow is 1/q pixel, i.e. 1 in units of 1/q."""
+    rng = np.random.default_rng(seed)
+    v = synth.value_noise(rng, H, W, lattices=(16, 8, 4), amps=(0.5, 0.25, 0.125))
+    I2 = (np.floor(v * (255 // q)) * q).astype(np.int64)  # multiples of q
+    nxt = np.concatenate([I2[:, 1:], I2[:, -1:]], 1) if axis == 0 else \
+        np.concatenate([I2[1:], I2[-1:]], 0)
+    I1 = ((q - 1) * I2 + nxt) // q
+    return I1.astype(np.uint8), I2.astype(np.uint8)
+
+
+def test_subpel_census_phase_zero_is_the_census(ffo):
+    rng = np.random.default_rng(12)
+    img = rng.integers(0, 256, size=(17, 23, 3)).astype(np.uint8)
+    for n in (1, 2, 4):
+        for q in (2, 4):
+            assert np.array_equal(ffo.census_subpel(img, n, q, 0, 0), ffo.census(img, n))
+
+
+@pytest.mark.parametrize("q,axis", [(2, 0), (2, 1), (4, 0)])
+def test_subpixel_translation_is_recovered(ffo, q, axis):
+    """Sec. 3.1, subpixel random search with bilinear target colours: on a pair
+    whose true flow is exactly 1/q pixel, the census of frame 2 interpolated at the
+    subpixel target equals frame 1's, so that flow has zero matching error and no
+    integer flow has. The search with subpel = q finds it (1 in units of 1/q) at
+    interior pixels; with integer flows (subpel = 1) it cannot."""
+    I1, I2 = _subpel_pair(q, axis)
+    m = np.zeros(I1.shape[:2], bool)
+    m[10:-10, 10:-10] = True
+    want = np.zeros(2, np.int32)
+    want[axis] = 1
+    out = ffo.flow_fields(I1, I2, params=dict(subpel=q), threads=3)
+    f = out["flows"][0]
+    hit = np.all(f == want, axis=-1)[m].mean()
+    assert hit > 0.95, hit
+    C1 = ffo.census(I1, 1)
+    for (y, x) in [(20, 30), (40, 50)]:  # zero matching error at the true subpixel target
+        Cq = ffo.census_subpel(I2, 1, q, want[0], want[1])
+        assert ffo.patch_cost(C1, Cq, 1, 8, (x, y), (x, y)) == 0
+    # integer flows can only take the neighbouring whole pixels, 0 or 1 px along the axis
+    f1 = ffo.flow_fields(I1, I2, params=dict(subpel=1), threads=3)["flows"][0]
+    assert np.isin(f1[m][:, axis], [0, 1]).mean() > 0.9
+
+
+def test_subpel_filter_thresholds(ffo):
+    """Eq. 5 and the region rule in units of 1/q pixel: a backward flow read at the
+    nearest pixel of a half-pixel target, eps and the 3-pixel region threshold
+    scaled by q."""
+    H, W = 6, 8
+    F = np.zeros((H, W, 2), np.int32)
+    F[..., 0] = 1  # +0.5 px with q = 2: target x + 0.5 rounds up to x + 1
+    Fb = np.zeros((H, W, 2), np.int32)
+    Fb[..., 0] = -1
+    v, e = ffo.consistency(F, Fb, Fb, 1, subpel=2)
+    assert np.all(v[:, :W - 1] == 1) and np.all(e[:, :W - 1] == 0)
+    assert np.all(v[:, W - 1] == 0)  # x + 1 = W: outside
+    Fb2 = Fb.copy()
+    Fb2[..., 0] = -4  # error 3 half pixels = 1.5 px: passes eps = 2, fails eps = 1
+    assert np.all(ffo.consistency(F, Fb2, Fb2, 2, subpel=2)[0][:, :W - 1] == 1)
+    assert np.all(ffo.consistency(F, Fb2, Fb2, 1, subpel=2)[0][:, :W - 1] == 0)
+    # region rule: flows differing by 2.5 px (5 half pixels) are neighbours, 3 px not
+    G = np.zeros((1, 3, 2), np.int32)
+    G[0, 1, 0] = 5
+    G[0, 2, 0] = 11
+    vcc = np.array([[1, 1, 0]], np.uint8)
+    out = ffo.region_filter(G, vcc, 5, subpel=2)
+    assert out.tolist() == [[1, 1, 0]]  # (1, 2) differ by 3 px: no touch, region kept
+    G[0, 2, 0] = 10  # 2.5 px: the rejected pixel touches the region -> removed
+    assert ffo.region_filter(G, vcc, 5, subpel=2).tolist() == [[0, 0, 0]]

@@ -456,3 +456,44 @@ def test_weighted_median_field(rho):
         Eo = O.match_errors(p["I1"], p["I2"], field, 8)
         assert np.array_equal(cpu(E), Eo)
         assert np.array_equal(cpu(med).astype(np.int32), O.weighted_median(field, Eo, rho))
+
+
+# ------------------------------------------------ subpixel random search ------
+@pytest.mark.parametrize("q", [2, 4])
+def test_flow_fields_subpel_128x96(q):
+    """The whole path with subpixel flows (params.subpel = q: interpolated target
+    census, offsets and thresholds in 1/q pixel) against the oracle, bit for bit."""
+    p = synth.pair_for_config(1, 9)
+    params = dict(subpel=q)
+    out = ffapi.FlowFields(128, 96, params).run(tg(p["I1"]), tg(p["I2"]))
+    torch.cuda.synchronize()
+    _compare(out, O.flow_fields(p["I1"], p["I2"], params=params, threads=3))
+
+
+def test_flow_fields_subpel_translation_and_batch():
+    """A pair whose true flow is half a pixel: GPU == oracle with subpel = 2; the
+    batched form, the graph replay and the persistent level kernel give the same
+    flows as the single pair."""
+    rng = np.random.default_rng(13)
+    v = synth.value_noise(rng, 72, 96, lattices=(16, 8, 4), amps=(0.5, 0.25, 0.125))
+    I2 = (np.floor(v * 127) * 2).astype(np.int64)
+    I1 = ((I2 + np.concatenate([I2[:, 1:], I2[:, -1:]], 1)) // 2).astype(np.uint8)
+    I2 = I2.astype(np.uint8)
+    params = dict(subpel=2)
+    single = ffapi.FlowFields(96, 72, params).run(tg(I1), tg(I2))
+    torch.cuda.synchronize()
+    _compare(single, O.flow_fields(I1, I2, params=params, threads=3))
+    ref = {k: v.clone() for k, v in single.items()}
+    before = ffapi.get_exec_params()
+    try:
+        for persist in (0, 1):
+            ffapi.set_exec_params(persist_levels=persist)
+            for graph in (False, True):
+                outs = ffapi.FlowFieldsBatch([(96, 72), (96, 72)], params, graph=graph).run(
+                    [(tg(I1), tg(I2)), (tg(I1), tg(I2))])
+                torch.cuda.synchronize()
+                for o in outs:
+                    for key in ("flows", "valid", "err_sum", "mask", "n_sparse"):
+                        assert torch.equal(o[key], ref[key]), (persist, graph, key)
+    finally:
+        ffapi.set_exec_params(**before)
