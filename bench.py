@@ -248,11 +248,11 @@ def pass_roofline(run, steps, flush, stream, taps_peak, l2_peak):
 
 
 # DRAM traffic of the pass kernels per launch, from one ncu capture of this
-# benchmark's pair (dram__bytes_read.sum + dram__bytes_write.sum averaged over 32
-# consecutive pass launches).
+# benchmark's pair (dram__bytes_read.sum + dram__bytes_write.sum averaged over the
+# 48 pass launches of one pair, one flow per launch).
 # It is reported only while the kernel sources hash to what was profiled.
-PASS_TRAFFIC = {"bytes_per_launch": 4664360,
-                "sources_sha256": "e1972e45274fac1a20251f4da8817f717fdccf09f6e39efd70d94964526acb94"}
+PASS_TRAFFIC = {"bytes_per_launch": 4685952,
+                "sources_sha256": "37bbfa1be0b7383d12afa93ebad3e0410077ee0250c74c244f4f238aa3c7424e"}
 PASS_SOURCES = ("paper_1508_05151_gb300/csrc/ff_search.cu", "paper_1508_05151_gb300/csrc/ff_internal.cuh")
 
 
@@ -522,6 +522,43 @@ def field_quality(dev, pairs=8, eps_list=(1, 2, 3, 4, 5, 6, 8, 10, 12, 15, 20)):
     return res
 
 
+def subpel_quality(dev, pairs=6):
+    """Integer flows vs the subpixel random search (params.subpel = 2, 4: offsets and
+    target colours at 1/q pixel) on generated Sintel-shaped (config 2) and
+    KITTI-shaped (config 5) pairs: inliers@3px, EPE10 and EPE of the raw forward
+    field on non-occluded pixels, and the device time per pair (direct call, median
+    of 5)."""
+    import torch
+    from paper_1508_05151_gb300 import ffapi, synth
+    out = {}
+    for cfg, name in ((2, "1024x436"), (5, "1242x375")):
+        ps = [synth.pair_for_config(cfg, 5000 + i) for i in range(pairs)]
+        H_, W_ = ps[0]["I1"].shape[:2]
+        frames = [(torch.from_numpy(p["I1"]).to(dev), torch.from_numpy(p["I2"]).to(dev)) for p in ps]
+        res = {}
+        for q in (1, 2, 4):
+            ff = ffapi.FlowFields(W_, H_, dict(PARAMS, subpel=q), dev)
+            acc, ts = [], []
+            for (a, b), p in zip(frames, ps):
+                ff.run(a, b)
+                torch.cuda.synchronize()
+                _, ms = _event_ms(lambda: ff.run(a, b), reps=5)
+                ts.append(ms)
+                f = ff.flows[0].cpu().numpy().astype(np.float64) / q
+                vis = ~p["occ"]
+                e = np.sqrt(((f - p["flow"]) ** 2).sum(-1))[vis]
+                acc.append((float((e <= 3.0).mean()), float(np.minimum(e, 10.0).mean()),
+                            float(e.mean())))
+            a = np.array(acc)
+            res[f"subpel{q}"] = {"inliers_3px": round(float(a[:, 0].mean()), 5),
+                                 "epe10": round(float(a[:, 1].mean()), 4),
+                                 "epe": round(float(a[:, 2].mean()), 4),
+                                 "ms_per_pair": round(float(np.median(ts)), 4)}
+        out[name] = res
+    out["pairs_per_workload"] = pairs
+    return out
+
+
 LEARNED_WORKLOADS = {
     2: ("1024x436", "Sintel-shaped 1024x436 pairs (3 textured layers, affine motion <= 200 px)"),
     4: ("512x218", "512x218 pairs of the shifted-noise generator with an occluding square "
@@ -668,6 +705,7 @@ def run_ours(args):
 
     batch = batch_measure(dev, PARAMS, pk, flush) if (rank == 0 and not args.no_batch) else None
     quality = field_quality(dev) if (rank == 0 and not args.no_quality) else None
+    subpel = subpel_quality(dev) if (rank == 0 and not args.no_quality) else None
     learned = {}
     if rank == 0 and not args.no_learned:
         # the training workload at its stated size: 4096 generated pairs, 256 held out
@@ -728,6 +766,8 @@ def run_ours(args):
         line["batch_64_mixed"] = batch
     if quality is not None:
         line["field_quality_1024x436"] = quality
+    if subpel is not None:
+        line["subpixel_search"] = subpel
     for cfg, lm in learned.items():
         eq = lm["equal_inliers"]
         if cfg == 2 and eq is not None:
