@@ -304,6 +304,9 @@ ff_status ff_graph_destroy(ff_graph *g);
  *   split8_min_n  0: that form uses 4 threads per candidate (128-thread CTAs);
  *               else levels with n >= split8_min_n (a power of two, 1..128) use 8
  *               (256-thread CTAs, 16 threads per scan row)
+ *   split2_max_n  0: as above; else levels with n <= split2_max_n (a power of
+ *               two, 1..128) use 2 threads per candidate (64-thread CTAs, 4
+ *               threads per scan row); takes precedence over split8_min_n
  *   serial_flows  0: the three flows of a pair and the image pyramid run on
  *               four streams concurrently; 1: all on the caller's stream, one
  *               after another (so that one kernel can be timed alone)
@@ -325,7 +328,7 @@ typedef struct ff_exec_params {
   int32_t serial_flows;
   int32_t kd_merge;
   int32_t persist_levels;
-  int32_t reserved[1];
+  int32_t split2_max_n;
 } ff_exec_params;
 ff_status ff_set_exec_params(const ff_exec_params *e);
 /* Test hooks of the bounded waits (not in the paper); they exist to test the

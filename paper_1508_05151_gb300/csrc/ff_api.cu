@@ -45,7 +45,7 @@ static ff_status evals_ptr(unsigned long long **out) {
   return FF_OK;
 }
 
-static ff_exec_params g_exec = {4, 0, 1, 2, 0, 0, 0, {0}};
+static ff_exec_params g_exec = {4, 0, 1, 2, 0, 0, 0, 0};
 const ff_exec_params &exec_params() { return g_exec; }
 
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
@@ -883,7 +883,7 @@ ff_status ff_set_exec_params(const ff_exec_params *e) {
   if (!e || e->pass_warps < 1 || e->pass_warps > 8 || !pow2_or_0(e->rs_min_n) ||
       !pow2_or_0(e->wide_min_n) || !pow2_or_0(e->split8_min_n) || e->serial_flows < 0 ||
       e->serial_flows > 1 || e->kd_merge < 0 || e->kd_merge > 1 || e->persist_levels < 0 ||
-      e->persist_levels > 1)
+      e->persist_levels > 1 || !pow2_or_0(e->split2_max_n))
     return FF_ERR_INVALID_ARG;
   g_exec = *e;
   return FF_OK;

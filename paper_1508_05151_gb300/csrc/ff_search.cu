@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(PASS_MAX_WARPS * 32) k_pass(const SearchProble
 // first thread applies both in order (strict less). Sources are read from the
 // tile state in shared memory, one barrier per diagonal. Same schedule and
 // results as k_pass.
-// SPLIT threads per candidate (4 or 8, an execution parameter): 32 * SPLIT
+// SPLIT threads per candidate (2, 4 or 8, an execution parameter): 32 * SPLIT
 // threads per CTA.
 template <int R, int SPLIT>
 __device__ __forceinline__ int part_line_delta(const uint32_t *so_, const uint32_t *si_, int ss,
@@ -961,17 +961,28 @@ static ff_status side_stream(SideStream **out) {
 }
 
 // Opt in to more than 48 KB of dynamic shared memory when a tile needs it.
+// wide: 0 k_pass, else the threads per candidate of k_pass_wide (2, 4 or 8).
 static ff_status set_pass_smem(int r, size_t bytes, int wide) {
-  if (r < 1 || r > 8 || wide < 0 || wide > 2) return FF_ERR_INVALID_ARG;
+  if (r < 1 || r > 8 || (wide != 0 && wide != 2 && wide != 4 && wide != 8)) return FF_ERR_INVALID_ARG;
   const void *fn = nullptr;
-  if (wide == 1) {
+  if (wide == 2) {
+    FF_DISPATCH_R(r, fn = (const void *)k_pass_wide<RR, 2>);
+  } else if (wide == 4) {
     FF_DISPATCH_R(r, fn = (const void *)k_pass_wide<RR, 4>);
-  } else if (wide == 2) {
+  } else if (wide == 8) {
     FF_DISPATCH_R(r, fn = (const void *)k_pass_wide<RR, 8>);
   } else {
     FF_DISPATCH_R(r, fn = (const void *)k_pass<RR>);
   }
   return smem_opt_in(fn, bytes);
+}
+
+// Threads per candidate of k_pass_wide at grid spacing n (execution parameters
+// split2_max_n and split8_min_n).
+static int pass_split(int n) {
+  const int s2 = exec_params().split2_max_n, s8 = exec_params().split8_min_n;
+  if (s2 > 0 && n <= s2) return 2;
+  return (s8 > 0 && n >= s8) ? 8 : 4;
 }
 
 // Multiprocessor count of the current device, looked up once per device.
@@ -1009,8 +1020,7 @@ static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d
   const TileLayout lay(tile, r);
   const int wide_min_n = exec_params().wide_min_n;
   const bool wide = wide_min_n > 0 && probs[0].src.n >= wide_min_n && tile <= 16;
-  const int s8 = exec_params().split8_min_n;
-  const int split = (s8 > 0 && probs[0].src.n >= s8) ? 8 : 4;
+  const int split = pass_split(probs[0].src.n);
   int pw = exec_params().pass_warps;
   while (pw > 1 && sizeof(uint32_t) * ((size_t)lay.words() + 4) * pw > 227u * 1024u) pw--;
   // a level with few tiles spreads them over the SMs (one CTA per SM at least)
@@ -1019,7 +1029,7 @@ static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d
   if (wide) pw = 1;
   // the tiles, then four evaluation counters per warp (k_pass) or per CTA
   const size_t smem = sizeof(uint32_t) * ((size_t)lay.words() * pw + 4 * pw);
-  FF_TRY(set_pass_smem(r, smem, wide ? (split == 8 ? 2 : 1) : 0));
+  FF_TRY(set_pass_smem(r, smem, wide ? split : 0));
   const int rs_min_n = exec_params().rs_min_n;
   const bool rs_kernel = rs_min_n > 0 && probs[0].src.n >= rs_min_n;
   const int log2n = probs[0].src.log2n;
@@ -1031,6 +1041,8 @@ static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d
     if (prof_enabled()) prof_begin(st, log2n);
     if (wide && split == 8) {
       FF_DISPATCH_R(r, (k_pass_wide<RR, 8><<<g, 256, smem, st>>>(d, cfg)));
+    } else if (wide && split == 2) {
+      FF_DISPATCH_R(r, (k_pass_wide<RR, 2><<<g, 64, smem, st>>>(d, cfg)));
     } else if (wide) {
       FF_DISPATCH_R(r, (k_pass_wide<RR, 4><<<g, 128, smem, st>>>(d, cfg)));
     } else {
@@ -1141,8 +1153,8 @@ ff_status run_level_persistent(const SearchProblem *probs, SearchProblem *dev, i
     }
   if (ra < rb) std::swap(ra, rb);
   const int log2n = probs[0].src.log2n;
-  const int s8 = exec_params().split8_min_n;
-  const int split = (s8 > 0 && probs[0].src.n >= s8) ? 8 : 4;
+  // the persistent form has 4 or 8 threads per candidate (2 runs as 4)
+  const int split = pass_split(probs[0].src.n) == 8 ? 8 : 4;
   const void *fn = level_kernel(ra, rb, split);
   if (!fn) {  // no fused kernel for these two radii: one launch per run of equal radius
     for (int i = 0; i < nprob;) {

@@ -41,7 +41,7 @@ class ExecParams(C.Structure):
     _fields_ = [("pass_warps", C.c_int32), ("rs_min_n", C.c_int32), ("wide_min_n", C.c_int32),
                 ("split8_min_n", C.c_int32), ("serial_flows", C.c_int32),
                 ("kd_merge", C.c_int32), ("persist_levels", C.c_int32),
-                ("reserved", C.c_int32 * 1)]
+                ("split2_max_n", C.c_int32)]
 
 
 class NetDesc(C.Structure):
@@ -474,7 +474,7 @@ def probe_l2_gather(buf, mode, sink, blocks, iters):
 
 
 EXEC_FIELDS = ("pass_warps", "rs_min_n", "wide_min_n", "split8_min_n", "serial_flows",
-               "kd_merge", "persist_levels")
+               "kd_merge", "persist_levels", "split2_max_n")
 
 
 def set_exec_params(**kw):

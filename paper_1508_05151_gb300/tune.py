@@ -20,9 +20,9 @@ import torch
 
 from . import ffapi, synth
 
-CANDIDATES = dict(wide_min_n=(0, 1, 2, 4, 8), split8_min_n=(0, 1, 2, 4, 8), pass_warps=(1, 2, 4, 8),
-                  rs_min_n=(0, 1, 2, 4, 8), serial_flows=(0, 1), kd_merge=(0, 1),
-                  persist_levels=(0, 1))
+CANDIDATES = dict(wide_min_n=(0, 1, 2, 4, 8), split8_min_n=(0, 1, 2, 4, 8), split2_max_n=(0, 1, 2),
+                  pass_warps=(1, 2, 4, 8), rs_min_n=(0, 1, 2, 4, 8), serial_flows=(0, 1),
+                  kd_merge=(0, 1), persist_levels=(0, 1))
 _CACHE = os.environ.get("FF_TUNE_CACHE",
                         os.path.join(os.path.expanduser("~"), ".cache", "flowfields_tune.json"))
 
@@ -89,7 +89,7 @@ def tune(sizes, params=None, frames=None, reps=3, use_cache=True, seed=0):
     before = ffapi.get_exec_params()
     timings = {}
     choice = dict(pass_warps=4, rs_min_n=0, wide_min_n=1, split8_min_n=0, serial_flows=0,
-                  kd_merge=0, persist_levels=0)
+                  kd_merge=0, persist_levels=0, split2_max_n=0)
     best_t = None
     for name in CANDIDATES:  # one parameter at a time
         for v in CANDIDATES[name]:

@@ -147,6 +147,7 @@ def test_exec_params_checks(L):
         assert L.ff_set_exec_params(C.byref(ffapi.ExecParams(pass_warps=2, wide_min_n=rs))) == 1
     for sp in (-1, 3, 256):
         assert L.ff_set_exec_params(C.byref(ffapi.ExecParams(pass_warps=2, split8_min_n=sp))) == 1
+        assert L.ff_set_exec_params(C.byref(ffapi.ExecParams(pass_warps=2, split2_max_n=sp))) == 1
     for v in (-1, 2):
         assert L.ff_set_exec_params(C.byref(ffapi.ExecParams(pass_warps=2, serial_flows=v))) == 1
         assert L.ff_set_exec_params(C.byref(ffapi.ExecParams(pass_warps=2, kd_merge=v))) == 1

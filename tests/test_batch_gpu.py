@@ -72,6 +72,13 @@ def test_execution_parameters_do_not_change_results():
             got = batch.run(frames)
             for a, b in zip(ref, got):
                 _same(a, b)
+        # 2 threads per candidate at the finest levels (with 8 above, and with the
+        # persistent launch, which runs them as 4)
+        for s2, s8, persist in ((1, 0, 0), (2, 4, 0), (128, 0, 0), (2, 4, 1)):
+            ffapi.set_exec_params(split2_max_n=s2, split8_min_n=s8, persist_levels=persist)
+            got = batch.run(frames)
+            for a, b in zip(ref, got):
+                _same(a, b)
         # stream layouts: flows serialised on one stream, kd trees of all flows in
         # one launch chain, both
         ffapi.set_exec_params(**before)
@@ -105,6 +112,7 @@ def test_autotuner_picks_a_candidate(tmp_path, monkeypatch):
         assert r["choice"]["serial_flows"] in tune.CANDIDATES["serial_flows"]
         assert r["choice"]["kd_merge"] in tune.CANDIDATES["kd_merge"]
         assert r["choice"]["persist_levels"] in tune.CANDIDATES["persist_levels"]
+        assert r["choice"]["split2_max_n"] in tune.CANDIDATES["split2_max_n"]
         assert ffapi.get_exec_params() == r["choice"]
         r2 = tune.tune([(128, 96), (97, 71)], reps=1)
         assert r2["cached"] and r2["choice"] == r["choice"]

@@ -197,14 +197,16 @@ def test_search_level_seeded(W, H, n, r, tile, n_rs):
         assert np.array_equal(cpu(f).astype(np.int32), fr)
 
 
-@pytest.mark.parametrize("W,H,n,r,tile,pw,rs_min_n,wide,split", [
-    (128, 96, 1, 8, 16, 1, 1, 0, 0), (200, 150, 4, 6, 16, 8, 2, 0, 0),
-    (97, 71, 2, 8, 6, 3, 2, 0, 0), (128, 96, 1, 8, 16, 1, 0, 1, 0),
-    (200, 150, 4, 6, 16, 8, 8, 2, 2), (97, 71, 2, 8, 6, 3, 0, 2, 0),
-    (300, 170, 8, 8, 10, 4, 2, 8, 8), (130, 97, 1, 3, 14, 4, 0, 1, 1)])
-def test_search_level_execution_variants(W, H, n, r, tile, pw, rs_min_n, wide, split):
+@pytest.mark.parametrize("W,H,n,r,tile,pw,rs_min_n,wide,split,split2", [
+    (128, 96, 1, 8, 16, 1, 1, 0, 0, 0), (200, 150, 4, 6, 16, 8, 2, 0, 0, 0),
+    (97, 71, 2, 8, 6, 3, 2, 0, 0, 0), (128, 96, 1, 8, 16, 1, 0, 1, 0, 0),
+    (200, 150, 4, 6, 16, 8, 8, 2, 2, 0), (97, 71, 2, 8, 6, 3, 0, 2, 0, 0),
+    (300, 170, 8, 8, 10, 4, 2, 8, 8, 0), (130, 97, 1, 3, 14, 4, 0, 1, 1, 0),
+    (128, 96, 1, 8, 16, 1, 0, 1, 0, 1), (97, 71, 2, 6, 6, 3, 0, 2, 0, 2),
+    (130, 97, 1, 3, 14, 4, 0, 1, 1, 1), (200, 150, 4, 5, 16, 8, 4, 1, 0, 4)])
+def test_search_level_execution_variants(W, H, n, r, tile, pw, rs_min_n, wide, split, split2):
     """The random search as a kernel of its own and the CTA-per-tile propagation
-    (execution parameters) equal the oracle."""
+    with 2, 4 or 8 threads per candidate (execution parameters) equal the oracle."""
     p = synth.pair_shift(W + 11 * H, W=W, H=H, max_shift=(10, 10), square=min(24, W, H),
                          square_move=9)
     C1g, _ = gpu_census(p["I1"], n)
@@ -218,7 +220,8 @@ def test_search_level_execution_variants(W, H, n, r, tile, pw, rs_min_n, wide, s
     coarse[..., 1] = np.clip(ys + coarse[..., 1], 0, H - 1) - ys
     before = ffapi.get_exec_params()
     try:
-        ffapi.set_exec_params(pass_warps=pw, rs_min_n=rs_min_n, wide_min_n=wide, split8_min_n=split)
+        ffapi.set_exec_params(pass_warps=pw, rs_min_n=rs_min_n, wide_min_n=wide, split8_min_n=split,
+                              split2_max_n=split2)
         f, c = ffapi.ff_search_level(C1g, C2g, n, r, dict(tile=tile, seed=77), flow_id=1,
                                      flow_coarse=tg(coarse.astype(np.int16)))
         torch.cuda.synchronize()
