@@ -160,13 +160,19 @@ __device__ __forceinline__ const uint32_t *plane_centre(const Planes &P, int x, 
 
 // Plane index and entry of the target (X, Y) in units of 1/q pixel (X, Y >= 0
 // inside the image; for q = 1 the pixel itself).
-__device__ __forceinline__ void target_plane(const Planes &P, int X, int Y, int &ph, int &ex,
-                                             int &ey) {
-  const int m = P.n - 1, qm = P.q - 1;
-  const int x = X >> P.log2q, y = Y >> P.log2q;
-  ph = ((((Y & qm) << P.log2q) + (X & qm)) << (2 * P.log2n)) + ((y & m) << P.log2n) + (x & m);
+// lq = P.log2q, passed explicitly so that a caller that knows q = 1 at compile
+// time (lq a constant 0) drops the phase arithmetic.
+__device__ __forceinline__ void target_plane_lq(const Planes &P, int X, int Y, int lq, int &ph,
+                                                int &ex, int &ey) {
+  const int m = P.n - 1, qm = (1 << lq) - 1;
+  const int x = X >> lq, y = Y >> lq;
+  ph = ((((Y & qm) << lq) + (X & qm)) << (2 * P.log2n)) + ((y & m) << P.log2n) + (x & m);
   ex = (x >> P.log2n) + PLANE_PAD;
   ey = (y >> P.log2n) + PLANE_PAD;
+}
+__device__ __forceinline__ void target_plane(const Planes &P, int X, int Y, int &ph, int &ex,
+                                             int &ey) {
+  target_plane_lq(P, X, Y, P.log2q, ph, ex, ey);
 }
 __device__ __forceinline__ const uint32_t *target_centre(const Planes &P, int X, int Y) {
   int ph, ex, ey;
@@ -176,11 +182,15 @@ __device__ __forceinline__ const uint32_t *target_centre(const Planes &P, int X,
 // Candidate flow (dx, dy) (units of 1/q pixel) at pixel (px, py) with its target
 // clamped into the image: X = clamp(q px + dx, 0, q (W - 1)), likewise Y; returns
 // the clamped flow, packed.
+__device__ __forceinline__ uint32_t clamp_target_lq(const Planes &P, int px, int py, int dx,
+                                                    int dy, int lq, int &X, int &Y) {
+  X = clampi((px << lq) + dx, 0, (P.W - 1) << lq);
+  Y = clampi((py << lq) + dy, 0, (P.H - 1) << lq);
+  return pack_flow(X - (px << lq), Y - (py << lq));
+}
 __device__ __forceinline__ uint32_t clamp_target(const Planes &P, int px, int py, int dx, int dy,
                                                  int &X, int &Y) {
-  X = clampi((px << P.log2q) + dx, 0, (P.W - 1) << P.log2q);
-  Y = clampi((py << P.log2q) + dy, 0, (P.H - 1) << P.log2q);
-  return pack_flow(X - (px << P.log2q), Y - (py << P.log2q));
+  return clamp_target_lq(P, px, py, dx, dy, P.log2q, X, Y);
 }
 __device__ __forceinline__ uint32_t clamp_target(const Planes &P, int px, int py, uint32_t f,
                                                  int &X, int &Y) {

@@ -43,7 +43,11 @@ constexpr int SUB_MAX = 1024;  // largest segment finished by one CTA
 constexpr int DIGIT = 12;
 constexpr int NBINS = 1 << DIGIT;
 constexpr int KD_CHUNK = 1024;      // positions per CTA of the top-level kernels (<= 2 segments)
-constexpr int SEL_SORT_MAX = 2048;  // longest collected list selected by a shared-memory sort
+// Longest collected list selected by a shared-memory sort, and the digit of the
+// radix passes over longer lists. Both keep the collect kernel's shared memory
+// small (about 5 KB), so that its CTAs do not crowd out the other streams' work.
+constexpr int SEL_SORT_MAX = 512;
+constexpr int SEL_DIGIT = 8;
 
 int kd_depth(int N, int leaf) {
   int d = 0;
@@ -509,8 +513,9 @@ __global__ void __launch_bounds__(256) k_kd_hist(KdBuild *trees, int d) {
 
 // Exact key of the remaining rank S[4] among segment s's collected keys (the
 // bucket of the top digit), by all 256 threads of one CTA: a bitonic sort in
-// shared memory for lists of up to SEL_SORT_MAX keys, else radix passes of DIGIT
-// bits over the list in global memory. The result becomes the selected key.
+// shared memory for lists of up to SEL_SORT_MAX keys, else radix passes of
+// SEL_DIGIT bits over the list in global memory. The result becomes the selected
+// key.
 __device__ void seg_select(KdBuild &T, int d, int s) {
   int32_t *S = sel_at(T, d, s);
   const int B = S[2];
@@ -521,7 +526,7 @@ __device__ void seg_select(KdBuild &T, int d, int s) {
   const int tid = threadIdx.x;
   __shared__ unsigned long long sk[SEL_SORT_MAX];
   __shared__ unsigned long long s_key, s_pre;
-  __shared__ uint32_t hs[NBINS];
+  __shared__ uint32_t hs[1 << SEL_DIGIT];
   __shared__ uint32_t s_k;
   __shared__ int s_used;
   const uint32_t k0 = (uint32_t)S[4];
@@ -553,9 +558,9 @@ __device__ void seg_select(KdBuild &T, int d, int s) {
     }
     __syncthreads();
     while (s_used < B) {  // s_used is shared: the loop is uniform
-      const int hi = B - s_used, lo = max(hi - DIGIT, 0), nb = 1 << (hi - lo);
+      const int hi = B - s_used, lo = max(hi - SEL_DIGIT, 0), nb = 1 << (hi - lo);
       const unsigned long long pre = s_pre;
-      for (int i = tid; i < NBINS; i += blockDim.x) hs[i] = 0;
+      for (int i = tid; i < (1 << SEL_DIGIT); i += blockDim.x) hs[i] = 0;
       __syncthreads();
       for (int i = tid; i < c; i += blockDim.x) {
         const unsigned long long K = __ldcg(list + i);

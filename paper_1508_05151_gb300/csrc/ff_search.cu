@@ -626,8 +626,9 @@ __device__ __forceinline__ int pass_tiles(const SearchProblem &P, int T, int s) 
 
 // One tile (index `tile` < pass_tiles) of pass cfg.s of problem P by the whole
 // CTA (32 * SPLIT threads); smem holds the tile layout and then four evaluation
-// counters.
-template <int R, int SPLIT>
+// counters. GEN = false is the form for integer flows (q = 1) without evaluation
+// counting: the subpixel phase arithmetic and the counters compile away.
+template <int R, int SPLIT, bool GEN>
 __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg &cfg, int tile,
                                           uint32_t *smem) {
   constexpr int WIDE_THREADS = 32 * SPLIT;
@@ -653,8 +654,10 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
   const int tpitch = P.tgt.pitch, tpitchT = P.tgt.pitchT;
   const size_t tpw_ = P.tgt.plane_words, tpwT = P.tgt.plane_wordsT;
   const TileSmem S = carve_tile(smem, Lt, T);
+  const int lq = GEN ? P.tgt.log2q : 0;         // subpixel phases per axis: 1 << lq
+  const bool counting = GEN && cfg.evals != nullptr;
   unsigned *scnt = smem + cfg.words_per_tile;  // evaluation counters (PassCfg::evals)
-  if (cfg.evals && t < 4) scnt[t] = 0;
+  if (counting && t < 4) scnt[t] = 0;
   int tox, toy, ph0;
   stage_tile<R>(P, Lt, T, true, x0, y0, x1, y1, hdx, vdy, fin, cin, S, t, WIDE_THREADS, tox, toy,
                 ph0);
@@ -667,7 +670,7 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
   };
   auto clamp_flow = [&](int px, int py, uint32_t fq) {
     int X, Y;
-    return clamp_target(P.tgt, px, py, fq, X, Y);
+    return clamp_target_lq(P.tgt, px, py, flow_dx(fq), flow_dy(fq), lq, X, Y);
   };
 
   const int row = t / (2 * SPLIT), cand = (t / SPLIT) & 1, u = t & (SPLIT - 1);
@@ -709,10 +712,9 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
       const int32_t cq = cand == 0 ? ch : cv;
       const uint32_t *sc = S.src + (ly + R + 1) * Lt.swp + (lx + R + 1);
       int ph, ex, ey;
-      target_plane(P.tgt, (px << P.tgt.log2q) + flow_dx(cf), (py << P.tgt.log2q) + flow_dy(cf), ph,
-                   ex, ey);
+      target_plane_lq(P.tgt, (px << lq) + flow_dx(cf), (py << lq) + flow_dy(cf), lq, ph, ex, ey);
       const bool win = in_win(ph, ex, ey);
-      if (cfg.evals && u == 0) count_eval(scnt, cf != fq, win);
+      if (counting && u == 0) count_eval(scnt, cf != fq, win);
       if (cf == fq) {  // incremental: E(q, f) - outgoing line + incoming line
         const int step = cand == 0 ? hdx : vdy;
         const int oo = step + step * R, oi = -step * R;
@@ -774,7 +776,7 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
   }
 
   if (cfg.do_rs) {  // random search, one thread per point, points column by column
-    const int Rn = (cfg.R * n) << P.tgt.log2q;  // offsets in units of 1/q pixel
+    const int Rn = (cfg.R * n) << lq;  // offsets in units of 1/q pixel
     for (int i = t; i < tw * th; i += WIDE_THREADS) {
       const int ly = i % th, lx = i / th;
       const uint32_t cur = S.flow[ly * T + lx];
@@ -784,13 +786,13 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
       int ox, oy;
       rs_offset(cfg.seed, P.flow_id, log2n, cfg.s, gx, gy, Rn, ox, oy);
       int X, Y;
-      const uint32_t cf = clamp_target(P.tgt, px, py, flow_dx(cur) + ox, flow_dy(cur) + oy, X, Y);
+      const uint32_t cf = clamp_target_lq(P.tgt, px, py, flow_dx(cur) + ox, flow_dy(cur) + oy, lq, X, Y);
       if (cf == cur) continue;
       int ph, ex, ey;
-      target_plane(P.tgt, X, Y, ph, ex, ey);
+      target_plane_lq(P.tgt, X, Y, lq, ph, ex, ey);
       const uint32_t *sc = S.src + (ly + R + 1) * Lt.swp + (lx + R + 1);
       const bool win = in_win(ph, ex, ey);
-      if (cfg.evals) count_eval(scnt, true, win);
+      if (counting) count_eval(scnt, true, win);
       const int cost = win
                            ? lane_full<R>(sc, Lt.swp, S.tgt + (ey - toy) * Lt.twp + (ex - tox), Lt.twp)
                            : lane_full<R>(sc, Lt.swp, tbase + (size_t)ph * tpw_ + (size_t)ey * tpitch + ex,
@@ -808,18 +810,18 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
     fout[g] = S.flow[ly * T + lx];
     cout[g] = S.cost[ly * T + lx];
   }
-  if (cfg.evals) {
+  if (counting) {
     __syncthreads();
     if (t < 4 && scnt[t]) atomicAdd(cfg.evals + t, (unsigned long long)scnt[t]);
   }
 }
 
-template <int R, int SPLIT>
+template <int R, int SPLIT, bool GEN>
 __global__ void __launch_bounds__(32 * SPLIT, 32 / SPLIT) k_pass_wide(const SearchProblem *probs, PassCfg cfg) {
   extern __shared__ uint32_t smem[];
   const SearchProblem &P = probs[blockIdx.y];
   if ((int)blockIdx.x >= pass_tiles(P, cfg.tile, cfg.s)) return;  // whole CTA
-  wide_tile<R, SPLIT>(P, cfg, blockIdx.x, smem);
+  wide_tile<R, SPLIT, GEN>(P, cfg, blockIdx.x, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -912,10 +914,10 @@ __global__ void __launch_bounds__(32 * SPLIT, 24 / SPLIT) k_level(const SearchPr
       const SearchProblem &P = probs[lo];
       if (RA == RB || P.r == RA) {
         cfg.evals = lc.evals_a;
-        wide_tile<RA, SPLIT>(P, cfg, item - tb[lo], smem);
+        wide_tile<RA, SPLIT, true>(P, cfg, item - tb[lo], smem);
       } else {
         cfg.evals = lc.evals_b;
-        wide_tile<RB, SPLIT>(P, cfg, item - tb[lo], smem);
+        wide_tile<RB, SPLIT, true>(P, cfg, item - tb[lo], smem);
       }
       __syncthreads();  // the tile's shared memory is reused by the next item
     }
@@ -960,20 +962,29 @@ static ff_status side_stream(SideStream **out) {
   return FF_OK;
 }
 
-// Opt in to more than 48 KB of dynamic shared memory when a tile needs it.
-// wide: 0 k_pass, else the threads per candidate of k_pass_wide (2, 4 or 8).
-static ff_status set_pass_smem(int r, size_t bytes, int wide) {
-  if (r < 1 || r > 8 || (wide != 0 && wide != 2 && wide != 4 && wide != 8)) return FF_ERR_INVALID_ARG;
-  const void *fn = nullptr;
-  if (wide == 2) {
-    FF_DISPATCH_R(r, fn = (const void *)k_pass_wide<RR, 2>);
-  } else if (wide == 4) {
-    FF_DISPATCH_R(r, fn = (const void *)k_pass_wide<RR, 4>);
-  } else if (wide == 8) {
-    FF_DISPATCH_R(r, fn = (const void *)k_pass_wide<RR, 8>);
+// The pass kernel for radius r: k_pass (wide = 0) or k_pass_wide with `wide`
+// threads per candidate (2, 4 or 8), in its general form (gen: subpixel flows or
+// evaluation counting) or its integer-only form.
+static ff_status pass_kernel(int r, int wide, bool gen, const void **fn) {
+  *fn = nullptr;
+  if (wide == 0) {
+    FF_DISPATCH_R(r, *fn = (const void *)k_pass<RR>);
+  } else if (gen) {
+    if (wide == 2) FF_DISPATCH_R(r, *fn = (const void *)k_pass_wide<RR, 2, true>);
+    if (wide == 4) FF_DISPATCH_R(r, *fn = (const void *)k_pass_wide<RR, 4, true>);
+    if (wide == 8) FF_DISPATCH_R(r, *fn = (const void *)k_pass_wide<RR, 8, true>);
   } else {
-    FF_DISPATCH_R(r, fn = (const void *)k_pass<RR>);
+    if (wide == 2) FF_DISPATCH_R(r, *fn = (const void *)k_pass_wide<RR, 2, false>);
+    if (wide == 4) FF_DISPATCH_R(r, *fn = (const void *)k_pass_wide<RR, 4, false>);
+    if (wide == 8) FF_DISPATCH_R(r, *fn = (const void *)k_pass_wide<RR, 8, false>);
   }
+  return *fn ? FF_OK : FF_ERR_INVALID_ARG;
+}
+
+// Opt in to more than 48 KB of dynamic shared memory when a tile needs it.
+static ff_status set_pass_smem(int r, size_t bytes, int wide, bool gen) {
+  const void *fn = nullptr;
+  FF_TRY(pass_kernel(r, wide, gen, &fn));
   return smem_opt_in(fn, bytes);
 }
 
@@ -1029,25 +1040,26 @@ static ff_status launch_group(const SearchProblem *probs, const SearchProblem *d
   if (wide) pw = 1;
   // the tiles, then four evaluation counters per warp (k_pass) or per CTA
   const size_t smem = sizeof(uint32_t) * ((size_t)lay.words() * pw + 4 * pw);
-  FF_TRY(set_pass_smem(r, smem, wide ? split : 0));
-  const int rs_min_n = exec_params().rs_min_n;
-  const bool rs_kernel = rs_min_n > 0 && probs[0].src.n >= rs_min_n;
   const int log2n = probs[0].src.log2n;
   unsigned long long *evals = prof_evals(r, log2n);
+  // the integer-only kernels unless some problem has subpixel flows or the
+  // evaluations are counted
+  bool gen = evals != nullptr;
+  for (int j = 0; j < np; j++) gen = gen || probs[j].tgt.q > 1;
+  FF_TRY(set_pass_smem(r, smem, wide ? split : 0, gen));
+  const void *fn = nullptr;
+  FF_TRY(pass_kernel(r, wide ? split : 0, gen, &fn));
+  const dim3 block(wide ? 32 * split : pw * 32);
+  const int rs_min_n = exec_params().rs_min_n;
+  const bool rs_kernel = rs_min_n > 0 && probs[0].src.n >= rs_min_n;
   for (int s = 0; s < 4; s++) {
     const bool do_rs = s < 3 && s < n_rs;
     PassCfg cfg{s, tile, (do_rs && !rs_kernel) ? 1 : 0, R, seed, s == 3, lay.words(), evals};
     dim3 g((maxT + pw - 1) / pw, np);
     if (prof_enabled()) prof_begin(st, log2n);
-    if (wide && split == 8) {
-      FF_DISPATCH_R(r, (k_pass_wide<RR, 8><<<g, 256, smem, st>>>(d, cfg)));
-    } else if (wide && split == 2) {
-      FF_DISPATCH_R(r, (k_pass_wide<RR, 2><<<g, 64, smem, st>>>(d, cfg)));
-    } else if (wide) {
-      FF_DISPATCH_R(r, (k_pass_wide<RR, 4><<<g, 128, smem, st>>>(d, cfg)));
-    } else {
-      FF_DISPATCH_R(r, k_pass<RR><<<g, pw * 32, smem, st>>>(d, cfg));
-    }
+    const SearchProblem *dp = d;
+    void *args[] = {(void *)&dp, (void *)&cfg};
+    (void)cudaLaunchKernel(fn, g, block, args, smem, st);
     FF_CHECK_LAUNCH();
     if (prof_enabled()) prof_end(st);
     if (do_rs && rs_kernel) {

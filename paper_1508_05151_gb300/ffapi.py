@@ -265,7 +265,10 @@ def _grid(W, H, n):
     return (W + n - 1) // n, (H + n - 1) // n
 
 
-def ff_kdtree_init(tree, leaf, src_img, census_src, census_tgt, n, r, proposals=None):
+def ff_kdtree_init(tree, leaf, src_img, census_src, census_tgt, n, r, proposals=None,
+                   with_status=False):
+    """Initial flow at the grid of spacing n from a kd tree (Eq. 1 / Eq. 4).
+    Returns (flow, cost), plus the device status (code, x, y) with with_status."""
     H, W = src_img.shape[:2]
     Gx, Gy = _grid(W, H, n)
     dev = src_img.device
@@ -279,6 +282,11 @@ def ff_kdtree_init(tree, leaf, src_img, census_src, census_tgt, n, r, proposals=
         _dev(tree["perm"]), _dev(sd), _dev(sv), leaf, _dev(src_img), _dev(census_src),
         _dev(census_tgt), W, H, n, r, _opt(proposals), K, _dev(flow), _dev(cost), wp, wn,
         _stream()))
+    if with_status:
+        code, x, y = C.c_uint32(), C.c_int32(), C.c_int32()
+        # the call itself returns an error status when a device check failed
+        lib().ff_device_status(wp, C.byref(code), C.byref(x), C.byref(y), _stream())
+        return flow, cost, (code.value, x.value, y.value)
     return flow, cost
 
 

@@ -169,6 +169,31 @@ def test_kdtree_init(W, H, n, r, leaf, K):
     assert np.array_equal(cpu(f).astype(np.int32), fr)
 
 
+def test_kdtree_init_reports_a_corrupt_tree():
+    """A caller's tree with a split dimension outside [0, 27) or a leaf entry outside
+    [0, N): the query's own checks skip the access and report device status 1
+    (DEV_ERR_BOUNDS) with the grid point and the node or leaf position; a sound tree
+    reports 0."""
+    W, H, n, r, leaf = 64, 48, 4, 4, 8
+    p = synth.pair_shift(5, W=W, H=H, max_shift=(6, 6), square=16, square_move=4)
+    C1g, _ = gpu_census(p["I1"], n)
+    C2g, _ = gpu_census(p["I2"], n)
+    T = ffapi.ff_kdtree_build(ffapi.ff_features(tg(p["I2"]), r), leaf)
+    _, _, st = ffapi.ff_kdtree_init(T, leaf, tg(p["I1"]), C1g, C2g, n, r, with_status=True)
+    assert st == (0, 0, 0)
+    N = T["N"]
+    sd, _ = T["_keep"]
+    sd[0] = 99  # root split dimension out of range: every grid point meets it
+    _, _, st = ffapi.ff_kdtree_init(T, leaf, tg(p["I1"]), C1g, C2g, n, r, with_status=True)
+    assert st[0] == 1 and st[2] == 0
+    T2 = ffapi.ff_kdtree_build(ffapi.ff_features(tg(p["I2"]), r), leaf)
+    T2["perm"][:] = N + 7  # every leaf entry out of range
+    f, c, st = ffapi.ff_kdtree_init(T2, leaf, tg(p["I1"]), C1g, C2g, n, r, with_status=True)
+    assert st[0] == 1 and 0 <= st[2] < N
+    assert bool((c == O.COST_UNSET).all())  # no candidate was evaluated
+    torch.cuda.synchronize()
+
+
 # ---------------------------------------------------------------- A7 / A8 -----
 @pytest.mark.parametrize("W,H,n,r,tile,n_rs", [(64, 48, 1, 3, 8, 3), (128, 96, 1, 8, 32, 3),
                                                (128, 96, 2, 8, 32, 3), (128, 96, 4, 6, 32, 2),
