@@ -138,14 +138,10 @@ __device__ __forceinline__ void count_eval(unsigned *scnt, bool full, bool windo
 constexpr int PASS_MAX_WARPS = 8;  // tiles per CTA: an execution parameter, 1..8
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
-// Shared-memory layout of one tile (all sizes in 32-bit words).
-// Window pitches. For 16 x 16 tiles (the default) both windows use a pitch of
-// 2 mod 4 words (26 for r = 1, 38 for r = 2, 42 for r = 3..8): with the random
-// search's points taken column by column, the CTA-per-tile kernel's shared loads
-// (patch columns and rows of the wavefront's candidates, whole patches of the
-// random search) then fall in distinct banks; a model of those access patterns
-// over a coherent flow gives one wavefront per load instead of 1.7 with odd
-// pitches. Other tile edges keep odd pitches.
+// Shared-memory layout of one tile (all sizes in 32-bit words). Both windows use
+// odd pitches. (Pitches of 2 mod 4 with the random search's points taken column
+// by column halve the shared-memory bank conflicts of the 16 x 16 tile, but
+// measured slower: 4.24 against 4.20 ms per 1024x436 pair.)
 struct TileLayout {
   int sw, swp;   // source window edge and pitch
   int tw, twp;   // target window edge and pitch
@@ -153,12 +149,8 @@ struct TileLayout {
   __host__ __device__ TileLayout(int T_, int R) : T(T_) {
     sw = T_ + 2 * R + 2;
     tw = T_ + 2 * R + 8;  // 3 entries of slack on each side of the tile's patches
-    if (T_ == 16) {
-      swp = twp = R <= 1 ? 26 : (R == 2 ? 38 : 42);
-    } else {
-      swp = sw | 1;
-      twp = tw | 1;
-    }
+    swp = sw | 1;
+    twp = tw | 1;
   }
   __host__ __device__ int words() const { return sw * swp + tw * twp + 2 * T * T + 4 * T; }
 };
@@ -775,10 +767,10 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
     __syncthreads();
   }
 
-  if (cfg.do_rs) {  // random search, one thread per point, points column by column
+  if (cfg.do_rs) {  // random search, one thread per point, points row by row
     const int Rn = (cfg.R * n) << lq;  // offsets in units of 1/q pixel
     for (int i = t; i < tw * th; i += WIDE_THREADS) {
-      const int ly = i % th, lx = i / th;
+      const int lx = i % tw, ly = i / tw;
       const uint32_t cur = S.flow[ly * T + lx];
       const int32_t cc = S.cost[ly * T + lx];
       if (cc == COST_UNSET) continue;
