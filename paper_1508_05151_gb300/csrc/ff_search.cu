@@ -624,7 +624,7 @@ template <int R, int SPLIT, bool GEN>
 __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg &cfg, int tile,
                                           uint32_t *smem) {
   constexpr int WIDE_THREADS = 32 * SPLIT;
-  const int t = threadIdx.x, lane = t & 31;
+  const int t = threadIdx.x;
   const int Gx = P.src.NX, Gy = P.src.NY, n = P.src.n, log2n = P.src.log2n;
   const int T = cfg.tile, off = (cfg.s & 1) * (T >> 1);
   const int ntx = (Gx + off + T - 1) / T;
@@ -665,34 +665,36 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
     return clamp_target_lq(P.tgt, px, py, flow_dx(fq), flow_dy(fq), lq, X, Y);
   };
 
-  const int row = t / (2 * SPLIT), cand = (t / SPLIT) & 1, u = t & (SPLIT - 1);
-  const int rbase = lane & ~(2 * SPLIT - 1);
+  // Thread t serves scan row jp = t / (2 SPLIT) (tile row ly), candidate `cand`
+  // (0: horizontal source, 1: vertical), part u of it. The row's pixel at diagonal
+  // d is ip = d - jp. Its horizontal source is the row's previous pixel, whose
+  // result every thread of the row keeps (pf, pc); at ip = 0 it is the staged
+  // neighbour outside the tile (cost COST_UNSET where there is none).
+  const int jp = t / (2 * SPLIT), cand = (t / SPLIT) & 1, u = t & (SPLIT - 1);
+  const bool lead = (t & (2 * SPLIT - 1)) == 0;
+  const bool row_on = jp < th;
+  const int ly = vdy < 0 ? jp : th - 1 - jp;
+  const int py = (y0 + ly) * n;
+  uint32_t pf = row_on ? S.hf[ly] : 0u;
+  int32_t pc = row_on ? S.hc[ly] : COST_UNSET;
   for (int d = 0; d < tw + th - 1; d++) {
-    const int jp = row, ip = d - row;
-    const bool on = jp < th && ip >= 0 && ip < tw;
-    int lx = 0, ly = 0, px = 0, py = 0;
+    const int ip = d - jp;
+    const bool on = row_on && ip >= 0 && ip < tw;
+    int lx = 0, px = 0;
     uint32_t f0 = 0, fh = 0, fv = 0;
     int32_t c0 = COST_UNSET, ch = COST_UNSET, cv = COST_UNSET;
-    bool hv = false, vv = false;
     if (on) {
       lx = hdx < 0 ? ip : tw - 1 - ip;
-      ly = vdy < 0 ? jp : th - 1 - jp;
-      const int gx = x0 + lx, gy = y0 + ly;
-      px = gx * n;
-      py = gy * n;
+      px = (x0 + lx) * n;
       f0 = S.flow[ly * T + lx];
       c0 = S.cost[ly * T + lx];
-      if (gx + hdx >= 0 && gx + hdx < Gx) {
-        fh = ip > 0 ? S.flow[ly * T + lx + hdx] : S.hf[ly];
-        ch = ip > 0 ? S.cost[ly * T + lx + hdx] : S.hc[ly];
-        hv = ch != COST_UNSET;
-      }
-      if (gy + vdy >= 0 && gy + vdy < Gy) {
-        fv = jp > 0 ? S.flow[(ly + vdy) * T + lx] : S.vf[lx];
-        cv = jp > 0 ? S.cost[(ly + vdy) * T + lx] : S.vc[lx];
-        vv = cv != COST_UNSET;
-      }
+      fh = pf;
+      ch = pc;
+      // inside the tile, or the staged neighbour above / below it
+      fv = jp > 0 ? S.flow[(ly + vdy) * T + lx] : S.vf[lx];
+      cv = jp > 0 ? S.cost[(ly + vdy) * T + lx] : S.vc[lx];
     }
+    const bool hv = ch != COST_UNSET, vv = cv != COST_UNSET;
     const bool set = c0 != COST_UNSET;
     const uint32_t cfh = hv ? clamp_flow(px, py, fh) : 0u;
     const bool useh = hv && !(set && cfh == f0);
@@ -708,37 +710,31 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
       const bool win = in_win(ph, ex, ey);
       if (counting && u == 0) count_eval(scnt, cf != fq, win);
       if (cf == fq) {  // incremental: E(q, f) - outgoing line + incoming line
+        // horizontal sources give column lines, vertical ones row lines: `sa`/`ta`
+        // step along a line, `sx`/`tx` from one line to the next
         const int step = cand == 0 ? hdx : vdy;
         const int oo = step + step * R, oi = -step * R;
-        const uint32_t *so_, *si_, *to_, *ti_;
-        int ss, ts;
-        if (cand == 0) {  // column lines
-          ss = Lt.swp;
-          so_ = sc - R * Lt.swp + oo;
-          si_ = sc - R * Lt.swp + oi;
-          if (win) {
-            const uint32_t *tc = S.tgt + (ey - toy) * Lt.twp + (ex - tox);
-            ts = Lt.twp;
-            to_ = tc - R * Lt.twp + oo;
-            ti_ = tc - R * Lt.twp + oi;
-          } else {  // rows of the transposed plane
-            const uint32_t *tc = tbaseT + (size_t)ph * tpwT + (size_t)ex * tpitchT + ey;
-            ts = 1;
-            to_ = tc + oo * tpitchT - R;
-            ti_ = tc + oi * tpitchT - R;
-          }
-        } else {  // row lines
-          ss = 1;
-          so_ = sc + oo * Lt.swp - R;
-          si_ = sc + oi * Lt.swp - R;
-          const uint32_t *tc = win ? S.tgt + (ey - toy) * Lt.twp + (ex - tox)
-                                   : tbase + (size_t)ph * tpw_ + (size_t)ey * tpitch + ex;
-          const int tp = win ? Lt.twp : tpitch;
-          ts = 1;
-          to_ = tc + oo * tp - R;
-          ti_ = tc + oi * tp - R;
+        const int sa = cand == 0 ? Lt.swp : 1, sx = cand == 0 ? 1 : Lt.swp;
+        const uint32_t *tb;
+        int ta, tx;
+        if (win) {
+          tb = S.tgt + (ey - toy) * Lt.twp + (ex - tox);
+          ta = cand == 0 ? Lt.twp : 1;
+          tx = cand == 0 ? 1 : Lt.twp;
+        } else if (cand == 0) {  // column lines are rows of the transposed plane
+          tb = tbaseT + (size_t)ph * tpwT + (size_t)ex * tpitchT + ey;
+          ta = 1;
+          tx = tpitchT;
+        } else {
+          tb = tbase + (size_t)ph * tpw_ + (size_t)ey * tpitch + ex;
+          ta = 1;
+          tx = tpitch;
         }
-        part = part_line_delta<R, SPLIT>(so_, si_, ss, to_, ti_, ts, u) + (u == 0 ? cq : 0);
+        const uint32_t *sb = sc - R * sa;
+        tb -= R * ta;
+        part = part_line_delta<R, SPLIT>(sb + oo * sx, sb + oi * sx, sa, tb + oo * tx, tb + oi * tx,
+                                         ta, u) +
+               (u == 0 ? cq : 0);
       } else if (win) {
         part = part_full<R, SPLIT>(sc, Lt.swp, S.tgt + (ey - toy) * Lt.twp + (ex - tox), Lt.twp, u);
       } else {
@@ -746,11 +742,12 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
                                    tpitch, u);
       }
     }
+    // sum over the candidate's SPLIT threads, then swap with the other candidate's
 #pragma unroll
     for (int o = 1; o < SPLIT; o <<= 1) part += __shfl_xor_sync(FULL_MASK, part, o);
-    const int cost_h = __shfl_sync(FULL_MASK, part, rbase);
-    const int cost_v = __shfl_sync(FULL_MASK, part, rbase | SPLIT);
-    if (on && (t & (2 * SPLIT - 1)) == 0) {
+    const int other = __shfl_xor_sync(FULL_MASK, part, SPLIT);
+    const int cost_h = cand == 0 ? part : other, cost_v = cand == 0 ? other : part;
+    if (on) {  // every thread of the row applies both candidates, in order
       uint32_t nf = f0;
       int32_t nc = c0;
       if (useh && cost_h < nc) {
@@ -761,8 +758,12 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
         nc = cost_v;
         nf = cfv;
       }
-      S.flow[ly * T + lx] = nf;
-      S.cost[ly * T + lx] = nc;
+      if (lead) {
+        S.flow[ly * T + lx] = nf;
+        S.cost[ly * T + lx] = nc;
+      }
+      pf = nf;
+      pc = nc;
     }
     __syncthreads();
   }
