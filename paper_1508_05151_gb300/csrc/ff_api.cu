@@ -153,9 +153,9 @@ constexpr int MAXLV = 5;
 struct PairPlan {
   uint8_t *lab[2];  // both frames in CIELab (params.color == 1), else null
   uint32_t *planes[2][MAXLV];
-  uint8_t *sm;
-  void *smooth_scratch;
-  uint32_t *census;
+  uint8_t *sm[2];            // per frame: I^n, its smoothing scratch, its census
+  void *smooth_scratch[2];
+  uint32_t *census[2];
   int32_t *feat[3], *qfeat[3];
   int32_t *perm[3], *split_dim[3], *split_val[3];
   KdBuild kd[3];
@@ -171,11 +171,13 @@ static void plan_pair_body(Arena &a, int W, int H, const ff_params *p, PairPlan 
   for (int f = 0; f < 2; f++)
     for (int lv = 0; lv <= p->k; lv++)
       P.planes[f][lv] = a.take<uint32_t>(planes_words(W, H, 1 << lv, p->subpel));
-  P.sm = a.take<uint8_t>(N * 3);
   size_t ss = 0;
   for (int lv = 1; lv <= p->k; lv++) ss = ss > smooth_scratch_bytes(W, H, 1 << lv) ? ss : smooth_scratch_bytes(W, H, 1 << lv);
-  P.smooth_scratch = a.take<char>(ss);
-  P.census = a.take<uint32_t>(N);
+  for (int f = 0; f < 2; f++) {
+    P.sm[f] = a.take<uint8_t>(N * 3);
+    P.smooth_scratch[f] = a.take<char>(ss);
+    P.census[f] = a.take<uint32_t>(N);
+  }
   const int ntop = 1 << p->k;
   const size_t Gtop = (size_t)((W + ntop - 1) / ntop) * ((H + ntop - 1) / ntop);
   const int D = kd_depth((int)N, p->leaf);
@@ -218,6 +220,7 @@ struct BatchDesc {
   KdBuild *d_kd;
   KdQuery *d_q;
   SearchProblem *d_sp;
+  PyrJob *d_pyr;       // per level: the pyramid jobs (both frames of every pair)
   int32_t *tile_base;  // per level: tile prefix sums of the persistent level kernel
   unsigned *bar;       // per level: its grid-barrier counter (64 words apart)
 };
@@ -229,6 +232,7 @@ static BatchDesc plan_batch(Arena &a, int np, const int *Ws, const int *Hs, cons
   d.d_kd = a.take<KdBuild>(3 * (size_t)np);
   d.d_q = a.take<KdQuery>(3 * (size_t)np);
   d.d_sp = a.take<SearchProblem>(3 * (size_t)np * MAXLV);
+  d.d_pyr = a.take<PyrJob>(2 * (size_t)np * MAXLV);
   d.tile_base = a.take<int32_t>((size_t)MAXLV * 2 * (3 * (size_t)np + 1));
   d.bar = a.take<unsigned>((size_t)MAXLV * 64);
   return d;
@@ -303,28 +307,65 @@ static ff_status run_pairs(int np, const PairIO *io_in, const ff_params *p, void
   // queries, so the pyramid overlaps their features and kd builds
   const cudaStream_t ps = serial ? st : sec.side[2];
   mark(st, 3, MK_START);
-  for (int i = 0; i < np; i++) {
-    const PairPlan &P = plans[i];
-    const int W = io[i].W, H = io[i].H;
-    const uint8_t *img[2] = {io[i].I1, io[i].I2};
-    for (int f = 0; f < 2; f++)
-      for (int lv = 0; lv <= k; lv++) {
-        const int n = 1 << lv;
-        const uint8_t *src = img[f];
-        if (n > 1) {
-          FF_TRY(launch_smooth(img[f], W, H, n, P.sm, P.smooth_scratch, ps));
-          src = P.sm;
-        }
+  // A batch runs one launch per step and level over both frames of every pair
+  // (a 64-pair batch: 34 launches instead of 2,176, and the pyramid no longer
+  // trails the kd builds). A single pair runs its frames one after the other, in
+  // smaller launches that slot in beside the kd builds (measured faster there).
+  std::vector<PyrJob> jobs(2 * (size_t)np);
+  for (int lv = 0; lv <= k && np == 1; lv++) {
+    const PairPlan &P = plans[0];
+    const int W = io[0].W, H = io[0].H, n = 1 << lv;
+    const uint8_t *img[2] = {io[0].I1, io[0].I2};
+    for (int f = 0; f < 2; f++) {
+      const uint8_t *src = img[f];
+      if (n > 1) {
+        FF_TRY(launch_smooth(img[f], W, H, n, P.sm[f], P.smooth_scratch[f], ps));
+        src = P.sm[f];
+      }
+      const Planes pl = make_planes(P.planes[f][lv], W, H, n, p->subpel);
+      FF_TRY(launch_census(src, W, H, n, P.census[f], ps));
+      FF_TRY(launch_planes(P.census[f], phase_view(pl, 0), ps));
+      for (int ph = 1; ph < p->subpel * p->subpel; ph++) {
+        FF_TRY(launch_census_subpel(src, W, H, n, p->subpel, ph % p->subpel, ph / p->subpel,
+                                    P.census[f], ps));
+        FF_TRY(launch_planes(P.census[f], phase_view(pl, ph), ps));
+      }
+    }
+  }
+  for (int lv = 0; lv <= k && np > 1; lv++) {
+    const int n = 1 << lv;
+    for (int i = 0; i < np; i++) {
+      const PairPlan &P = plans[i];
+      const int W = io[i].W, H = io[i].H;
+      const uint8_t *img[2] = {io[i].I1, io[i].I2};
+      for (int f = 0; f < 2; f++) {
+        const size_t Wc = (W + n - 1) / n, Hc = (H + n - 1) / n;
+        PyrJob &J = jobs[2 * (size_t)i + f];
+        J.img = img[f];
+        J.down = (uint8_t *)P.smooth_scratch[f];
+        J.h = (int32_t *)((char *)P.smooth_scratch[f] + ((Wc * Hc * 3 + 255) & ~(size_t)255));
+        J.sm = P.sm[f];
+        J.census = P.census[f];
+        J.pl = phase_view(make_planes(P.planes[f][lv], W, H, n, p->subpel), 0);
+        J.W = W;
+        J.H = H;
+      }
+    }
+    FF_TRY(launch_pyramid_level(jobs.data(), bd.d_pyr + 2 * (size_t)np * lv, 2 * np, n, ps));
+    // subpixel targets (params.subpel > 1): the census of every other phase
+    for (int i = 0; i < np && p->subpel > 1; i++) {
+      const PairPlan &P = plans[i];
+      const int W = io[i].W, H = io[i].H;
+      for (int f = 0; f < 2; f++) {
+        const uint8_t *src = n > 1 ? P.sm[f] : (f == 0 ? io[i].I1 : io[i].I2);
         const Planes pl = make_planes(P.planes[f][lv], W, H, n, p->subpel);
-        FF_TRY(launch_census(src, W, H, n, P.census, ps));
-        FF_TRY(launch_planes(P.census, phase_view(pl, 0), ps));
-        // subpixel targets (params.subpel > 1): the census of every other phase
         for (int ph = 1; ph < p->subpel * p->subpel; ph++) {
           FF_TRY(launch_census_subpel(src, W, H, n, p->subpel, ph % p->subpel, ph / p->subpel,
-                                      P.census, ps));
-          FF_TRY(launch_planes(P.census, phase_view(pl, ph), ps));
+                                      P.census[f], ps));
+          FF_TRY(launch_planes(P.census[f], phase_view(pl, ph), ps));
         }
       }
+    }
   }
 
   mark(ps, 3, MK_PYRAMID);
@@ -462,13 +503,20 @@ static ff_status run_pairs(int np, const PairIO *io_in, const ff_params *p, void
   }
   mark(st, 3, MK_JOINED);
 
+  // the filters of a batch's pairs are independent: round-robin over the caller's
+  // stream and the three side streams
+  SideSection fsec;
+  const bool fork = np > 1 && !serial;
+  if (fork) FF_TRY(fsec.begin(st, 3));
   for (int i = 0; i < np; i++) {
     const size_t N = (size_t)io[i].W * io[i].H;
+    const cudaStream_t fs = (!fork || i % 4 == 0) ? st : fsec.side[i % 4 - 1];
     FF_TRY(launch_filter((const uint32_t *)io[i].flows, (const uint32_t *)(io[i].flows + 2 * N),
                          (const uint32_t *)(io[i].flows + 4 * N), io[i].W, io[i].H, p->eps, p->e,
                          p->s, p->subpel, io[i].valid, io[i].err_sum, io[i].sparse, io[i].n_sparse,
-                         io[i].mask, plans[i].filter_scratch, st));
+                         io[i].mask, plans[i].filter_scratch, fs));
   }
+  if (fork) FF_TRY(fsec.end());
   mark(st, 3, MK_FILTER);
   return FF_OK;
 }

@@ -361,6 +361,21 @@ ff_status launch_census(const uint8_t *imgn, int W, int H, int n, uint32_t *out,
 ff_status launch_census_subpel(const uint8_t *imgn, int W, int H, int n, int q, int a, int b,
                                uint32_t *out, cudaStream_t st);
 ff_status launch_planes(const uint32_t *census, Planes P, cudaStream_t st);
+// One frame of one pair at one pyramid level (the batched pyramid): the frame,
+// its scratch (area-down image, horizontal Lanczos pass, I^n, census) and the
+// phase-0 view of its census planes at spacing n.
+struct PyrJob {
+  const uint8_t *img;
+  uint8_t *down;
+  int32_t *h;
+  uint8_t *sm;
+  uint32_t *census;
+  Planes pl;
+  int W, H;
+};
+// I^n (n > 1), its census and the phase planes of every job, one launch per step
+// over all jobs. host/dev: the jobs (dev: device copy written on the stream).
+ff_status launch_pyramid_level(const PyrJob *host, PyrJob *dev, int njobs, int n, cudaStream_t st);
 
 // -------------------------------------------------------------- colour -------
 ff_status launch_rgb_to_lab(const uint8_t *img, int W, int H, uint8_t *out, cudaStream_t st);

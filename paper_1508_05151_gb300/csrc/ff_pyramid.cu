@@ -45,10 +45,8 @@ void lanczos_table(int n, LanczosTable *t) {
   }
 }
 
-__global__ void k_area_down(const uint8_t *__restrict__ img, int W, int H, int n,
-                            uint8_t *__restrict__ out, int Wc, int Hc) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= Wc * Hc * 3) return;
+__device__ __forceinline__ void area_down_at(const uint8_t *__restrict__ img, int W, int H, int n,
+                                             uint8_t *__restrict__ out, int Wc, int t) {
   int c = t % 3, i = (t / 3) % Wc, j = t / (3 * Wc);
   int x0 = i * n, y0 = j * n, x1 = min(x0 + n, W), y1 = min(y0 + n, H);
   int s = 0;
@@ -57,12 +55,17 @@ __global__ void k_area_down(const uint8_t *__restrict__ img, int W, int H, int n
   int cnt = (x1 - x0) * (y1 - y0);
   out[t] = (uint8_t)((s + cnt / 2) / cnt);
 }
+__global__ void k_area_down(const uint8_t *__restrict__ img, int W, int H, int n,
+                            uint8_t *__restrict__ out, int Wc, int Hc) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= Wc * Hc * 3) return;
+  area_down_at(img, W, H, n, out, Wc, t);
+}
 
 // Horizontal pass on the coarse rows: h[yc][x][c] = sum_k w_k(x mod n) D[yc][clamp(j0+k)].
-__global__ void k_lanczos_h(const uint8_t *__restrict__ down, int Wc, int Hc, int W, int n,
-                            LanczosTable tab, int32_t *__restrict__ h) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= Hc * W * 3) return;
+__device__ __forceinline__ void lanczos_h_at(const uint8_t *__restrict__ down, int Wc, int W, int n,
+                                             const LanczosTable &tab, int32_t *__restrict__ h,
+                                             int t) {
   int c = t % 3, x = (t / 3) % W, yc = t / (3 * W);
   int ph = x % n, j0 = x / n + tab.base[ph];
   int32_t acc = 0;
@@ -73,12 +76,17 @@ __global__ void k_lanczos_h(const uint8_t *__restrict__ down, int Wc, int Hc, in
   }
   h[t] = acc;
 }
+__global__ void k_lanczos_h(const uint8_t *__restrict__ down, int Wc, int Hc, int W, int n,
+                            LanczosTable tab, int32_t *__restrict__ h) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= Hc * W * 3) return;
+  lanczos_h_at(down, Wc, W, n, tab, h, t);
+}
 
 // Vertical pass to full resolution, rounded (acc + 2^27) >> 28 and clamped.
-__global__ void k_lanczos_v(const int32_t *__restrict__ h, int Hc, int W, int H, int n,
-                            LanczosTable tab, uint8_t *__restrict__ out) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= H * W * 3) return;
+__device__ __forceinline__ void lanczos_v_at(const int32_t *__restrict__ h, int Hc, int W, int n,
+                                             const LanczosTable &tab, uint8_t *__restrict__ out,
+                                             int t) {
   int c = t % 3, x = (t / 3) % W, y = t / (3 * W);
   int ph = y % n, j0 = y / n + tab.base[ph];
   long long acc = 0;
@@ -89,6 +97,12 @@ __global__ void k_lanczos_v(const int32_t *__restrict__ h, int Hc, int W, int H,
   }
   long long v = (acc + (1ll << 27)) >> 28;  // arithmetic shift = floor division
   out[t] = (uint8_t)(v < 0 ? 0 : (v > 255 ? 255 : v));
+}
+__global__ void k_lanczos_v(const int32_t *__restrict__ h, int Hc, int W, int H, int n,
+                            LanczosTable tab, uint8_t *__restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= H * W * 3) return;
+  lanczos_v_at(h, Hc, W, n, tab, out, t);
 }
 
 size_t smooth_scratch_bytes(int W, int H, int n) {
@@ -123,10 +137,8 @@ ff_status launch_smooth(const uint8_t *img, int W, int H, int n, uint8_t *out, v
 
 // Census: bit 8c + o set when channel c of neighbour o (raster order of the
 // 3x3 neighbourhood at spacing n, centre skipped, clamped) is below the centre.
-__global__ void k_census(const uint8_t *__restrict__ img, int W, int H, int n,
-                         uint32_t *__restrict__ out) {
-  int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= W || y >= H) return;
+__device__ __forceinline__ void census_at(const uint8_t *__restrict__ img, int W, int H, int n,
+                                          uint32_t *__restrict__ out, int x, int y) {
   const uint8_t *ctr = img + ((size_t)y * W + x) * 3;
   int c0 = ctr[0], c1 = ctr[1], c2 = ctr[2];
   uint32_t code = 0;
@@ -144,6 +156,12 @@ __global__ void k_census(const uint8_t *__restrict__ img, int W, int H, int n,
       o++;
     }
   out[(size_t)y * W + x] = code;
+}
+__global__ void k_census(const uint8_t *__restrict__ img, int W, int H, int n,
+                         uint32_t *__restrict__ out) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= H) return;
+  census_at(img, W, H, n, out, x, y);
 }
 
 ff_status launch_census(const uint8_t *imgn, int W, int H, int n, uint32_t *out, cudaStream_t st) {
@@ -200,10 +218,8 @@ ff_status launch_census_subpel(const uint8_t *imgn, int W, int H, int n, int q, 
 
 // Relayout of a plain census image into the padded phase planes and their
 // transposed copies.
-__global__ void k_planes(const uint32_t *__restrict__ census, Planes P) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int pl = blockIdx.z;
-  if (i >= P.pitch || j >= P.rows) return;
+__device__ __forceinline__ void planes_at(const uint32_t *__restrict__ census, const Planes &P,
+                                          int i, int j, int pl) {
   const int px = pl % P.n, py = pl / P.n;
   const int x = clampi(px + P.n * (i - PLANE_PAD), 0, P.W - 1);
   const int y = clampi(py + P.n * (j - PLANE_PAD), 0, P.H - 1);
@@ -211,10 +227,91 @@ __global__ void k_planes(const uint32_t *__restrict__ census, Planes P) {
   P.base[(size_t)pl * P.plane_words + (size_t)j * P.pitch + i] = v;
   if (i < P.NX + 2 * PLANE_PAD) P.baseT[(size_t)pl * P.plane_wordsT + (size_t)i * P.pitchT + j] = v;
 }
+__global__ void k_planes(const uint32_t *__restrict__ census, Planes P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= P.pitch || j >= P.rows) return;
+  planes_at(census, P, i, j, blockIdx.z);
+}
 
 ff_status launch_planes(const uint32_t *census, Planes P, cudaStream_t st) {
   dim3 b(64, 4), g((P.pitch + 63) / 64, (P.rows + 3) / 4, P.n * P.n);
   k_planes<<<g, b, 0, st>>>(census, P);
+  FF_CHECK_LAUNCH();
+  return FF_OK;
+}
+
+// ---------------------------------------------------------- batched form ----
+// The same steps over many frames per launch (blockIdx.y, or blockIdx.z for the
+// planes, selects the job); blocks past a smaller job's extent return.
+__global__ void k_area_down_b(const PyrJob *J, int n) {
+  const PyrJob &j = J[blockIdx.y];
+  const int Wc = (j.W + n - 1) / n, Hc = (j.H + n - 1) / n;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= Wc * Hc * 3) return;
+  area_down_at(j.img, j.W, j.H, n, j.down, Wc, t);
+}
+__global__ void k_lanczos_h_b(const PyrJob *J, int n, LanczosTable tab) {
+  const PyrJob &j = J[blockIdx.y];
+  const int Wc = (j.W + n - 1) / n, Hc = (j.H + n - 1) / n;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= Hc * j.W * 3) return;
+  lanczos_h_at(j.down, Wc, j.W, n, tab, j.h, t);
+}
+__global__ void k_lanczos_v_b(const PyrJob *J, int n, LanczosTable tab) {
+  const PyrJob &j = J[blockIdx.y];
+  const int Hc = (j.H + n - 1) / n;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= j.H * j.W * 3) return;
+  lanczos_v_at(j.h, Hc, j.W, n, tab, j.sm, t);
+}
+__global__ void k_census_b(const PyrJob *J, int n) {
+  const PyrJob &j = J[blockIdx.y];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= j.W * j.H) return;
+  census_at(n > 1 ? j.sm : j.img, j.W, j.H, n, j.census, t % j.W, t / j.W);
+}
+__global__ void k_planes_b(const PyrJob *J, int nn) {
+  const PyrJob &j = J[blockIdx.z / nn];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= j.pl.pitch || r >= j.pl.rows) return;
+  planes_at(j.census, j.pl, i, r, blockIdx.z % nn);
+}
+
+ff_status launch_pyramid_level(const PyrJob *host, PyrJob *dev, int njobs, int n, cudaStream_t st) {
+  if (njobs <= 0) return FF_OK;
+  if (n < 1 || n > 16 || (n & (n - 1))) return FF_ERR_INVALID_ARG;
+  const int chunk = 65535 / (n * n);  // grid.y / grid.z limits
+  if (njobs > chunk) {
+    for (int i = 0; i < njobs; i += chunk)
+      FF_TRY(launch_pyramid_level(host + i, dev + i, min(chunk, njobs - i), n, st));
+    return FF_OK;
+  }
+  int maxA = 0, maxH = 0, maxV = 0, maxP = 0, maxPitch = 0, maxRows = 0;
+  for (int i = 0; i < njobs; i++) {
+    const int W = host[i].W, H = host[i].H, Wc = (W + n - 1) / n, Hc = (H + n - 1) / n;
+    maxA = max(maxA, Wc * Hc * 3);
+    maxH = max(maxH, Hc * W * 3);
+    maxV = max(maxV, H * W * 3);
+    maxP = max(maxP, W * H);
+    maxPitch = max(maxPitch, host[i].pl.pitch);
+    maxRows = max(maxRows, host[i].pl.rows);
+  }
+  FF_TRY(upload_desc(host, dev, njobs, st));
+  const int B = 256;
+  if (n > 1) {
+    LanczosTable tab;
+    lanczos_table(n, &tab);
+    k_area_down_b<<<dim3((maxA + B - 1) / B, njobs), B, 0, st>>>(dev, n);
+    FF_CHECK_LAUNCH();
+    k_lanczos_h_b<<<dim3((maxH + B - 1) / B, njobs), B, 0, st>>>(dev, n, tab);
+    FF_CHECK_LAUNCH();
+    k_lanczos_v_b<<<dim3((maxV + B - 1) / B, njobs), B, 0, st>>>(dev, n, tab);
+    FF_CHECK_LAUNCH();
+  }
+  k_census_b<<<dim3((maxP + B - 1) / B, njobs), B, 0, st>>>(dev, n);
+  FF_CHECK_LAUNCH();
+  const dim3 pb(64, 4), pg((maxPitch + 63) / 64, (maxRows + 3) / 4, njobs * n * n);
+  k_planes_b<<<pg, pb, 0, st>>>(dev, n * n);
   FF_CHECK_LAUNCH();
   return FF_OK;
 }
