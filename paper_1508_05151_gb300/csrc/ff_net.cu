@@ -6,7 +6,11 @@
 //
 // Layers l = 0..3: 3x3 convolution, dilation dil[l], zero padding dil[l], bias,
 // ReLU except after the last layer. Channels cin(=6) -> c1 -> c2 -> c3 -> 2K.
-// Activations are NCHW; every convolution input is BF16 and accumulates in FP32.
+// The public input and output are NCHW FP32. Inside the workspace activations and
+// gradients are channels-last (pixel-major, channels padded to a multiple of 8
+// with zeros), so the 8 channels of one pixel are 16 contiguous bytes; every
+// convolution input is BF16 and accumulates in FP32. The reduction index of the
+// convolutions is tap-major, k = tap * Cpad + c.
 // Parameters (FP32 master copy) per layer: W [cout][cin][3][3], then b [cout].
 //
 // All three convolution products are implicit GEMMs on the 5th-generation
@@ -16,12 +20,13 @@
 //   dgrad     din[m][n]  = sum_k G[m][k] Bd[k][n], m = pixel, n = cin,  k = (cout, tap), taps mirrored
 //   wgrad     dW[n][k]   = sum_m G[m][n] A[m][k]   (reduction over pixels, split across CTAs)
 // where A is the im2col view of the layer input and G the gradient at the
-// pre-activation. A CTA of 128 threads computes a 128 x 64 tile: the threads
-// stage both operands in shared memory (16 deep for the convolutions; 32 pixels,
-// two MMAs, per stage for the weight gradient), one thread issues the MMAs, an
-// mbarrier reports their completion, and the epilogue reads the accumulator back
-// with tcgen05.ld. Waits are bounded; a wait that runs out sets the device status
-// word at the start of the workspace.
+// pre-activation. A CTA of 128 threads computes a 128 x 64 tile: both operands
+// are staged in shared memory (the convolutions: 16-byte cp.async copies into a
+// four-stage pipeline, 16 deep per stage; the weight gradient: 32 pixels, two
+// MMAs, per stage), one thread issues the MMAs, an mbarrier reports their
+// completion, and the epilogue reads the accumulator back with tcgen05.ld. Waits
+// are bounded; a wait that runs out sets the device status word at the start of
+// the workspace.
 #include <cuda_bf16.h>
 
 #include "ff_internal.cuh"
@@ -54,40 +59,52 @@ static bool net_shape(const ff_net_desc *d, NetShape &s) {
   return true;
 }
 
-static int pad16(int v) { return (v + 15) & ~15; }
 static int pad64(int v) { return (v + 63) & ~63; }
+static int padk(int v);  // K padded to whole stages of the convolution kernel
+__host__ __device__ __forceinline__ int cpad8(int c) { return (c + 7) & ~7; }
 
 // ------------------------------------------------------- forward / dgrad -----
-// out[b][n][y][x] = bias[n] + sum_{c, tap} Bmat[(c,tap)][n] * act[b][c][y + s*oy][x + s*ox]
-// with (oy, ox) = ((tap/3)-1, (tap%3)-1) * dil and s = +1 (forward) or -1 (dgrad).
-// Optionally writes the pre-activation (fp32) and relu'd BF16 copy, or, for
-// dgrad, multiplies by the ReLU mask of the lower layer's pre-activation.
+// out[m][n] = bias[n] + sum_{tap, c} Bt[n][tap * Ca + c] * act[pixel m + s * off(tap)][c]
+// with off(tap) = ((tap/3)-1, (tap%3)-1) * dil and s = +1 (forward) or -1 (dgrad),
+// m = (b, y, x). Writes the pre-activation (FP32, channels-last, or NCHW for the
+// net's output) and a BF16 channels-last copy: relu(out) in the forward pass, or
+// out times the ReLU mask of the lower layer's pre-activation in dgrad.
 struct ConvArgs {
-  const __nv_bfloat16 *act;  // [B][C][H][W]
-  int B, C, H, W, dil, sign;
-  const __nv_bfloat16 *Bmat;  // [Kp][Np] row-major, K = C*9 (zero rows up to Kp)
-  int K, Kp, N, Np;
-  const float *bias;           // [N] or null
-  float *out;                  // [B][N][H][W] fp32 or null
-  __nv_bfloat16 *out_bf;       // [B][N][H][W] bf16 of relu(out) (or of out*mask) or null
-  const float *mask_pre;       // dgrad: lower layer's pre-activation [B][N][H][W]; grad *= (pre > 0)
+  const __nv_bfloat16 *act;  // [B][H][W][Ca] channels-last, Ca = cpad8(C)
+  int B, Ca, H, W, dil, sign;
+  const __nv_bfloat16 *Bt;   // [Np][Kp] K-major (zero rows and columns up to Np, Kp)
+  int K, Kp, N, Np;          // K = 9 * Ca
+  const float *bias;         // [N] or null
+  float *out;                // [B][H][W][cpad8(N)] fp32, or [B][N][H][W] with out_nchw, or null
+  int out_nchw;
+  __nv_bfloat16 *out_bf;     // [B][H][W][cpad8(N)] bf16 or null
+  const float *mask_pre;     // dgrad: [B][H][W][cpad8(N)] lower pre-activation; grad *= (pre > 0)
   int relu;
-  int stall;                   // test hook: > 0 polls of a wait that nothing completes
+  int stall;                 // test hook: > 0 polls of a wait that nothing completes
 };
 
 // ------------------------------------------------ forward / dgrad, tcgen05 --
-// The same product on the 5th-generation tensor cores: one CTA (128 threads)
-// computes a 128-pixel x 64-column tile. Per K step of 16 the threads stage the
-// A tile (128 x 16, im2col gather) and the B^T tile (64 x 16) in shared memory
-// in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core
-// matrix; the two core matrices of a row group are 128 B apart along K, row
-// groups 256 B apart), one thread issues tcgen05.mma (BF16 x BF16 -> FP32, the
-// accumulator in tensor memory) and tcgen05.commit signals an mbarrier when the
-// MMA has consumed the tiles. Two stages: the next tiles are gathered while the
-// previous MMA runs. The epilogue reads the accumulator with tcgen05.ld (warp w
-// owns TMEM lanes = tile rows 32w..32w+31).
+// One CTA (128 threads) computes a 128-pixel x 64-column tile. A stage holds
+// CONV_KSTEP of K (CONV_SUB MMAs of 16): thread t copies the 16-byte groups (8
+// channels of one tap each) of A row t (pixel m0 + t) and CONV_SUB 16-byte pieces
+// of the B^T tile straight into shared memory with cp.async, in the no-swizzle
+// K-major core-matrix layout (per 16-deep slice: 8 rows x 16 bytes per core
+// matrix, the two core matrices of a row group 128 B apart along K, row groups
+// 256 B apart). Taps outside the image are zero-filled by the copy. Four stages
+// of 16, filled three ahead: while one thread issues the tcgen05.mma of a stage
+// (BF16 x BF16 -> FP32, the accumulator in tensor memory) the next three stages'
+// copies are in flight; tcgen05.commit signals a stage's mbarrier when its MMA is
+// done, and the stage is refilled. (Stages of 64 filled two ahead, 96 KB per CTA,
+// measured slower: 0.278 against 0.263 ms for the forward pass of 64 pairs.) The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
+// lanes = tile rows 32w..32w+31) and writes 8 channels of a pixel as one vector
+// store.
 constexpr int UMMA_M = 128, UMMA_N = 64, UMMA_K = 16;
 constexpr int UMMA_A_BYTES = UMMA_M * UMMA_K * 2, UMMA_B_BYTES = UMMA_N * UMMA_K * 2;
+constexpr int CONV_STAGES = 4, CONV_AHEAD = 3, CONV_SUB = 1;  // stages, fill distance, MMAs per stage
+constexpr int CONV_KSTEP = UMMA_K * CONV_SUB;
+constexpr int CONV_A_STAGE = UMMA_A_BYTES * CONV_SUB, CONV_B_STAGE = UMMA_B_BYTES * CONV_SUB;
+constexpr size_t CONV_SMEM = (size_t)CONV_STAGES * (CONV_A_STAGE + CONV_B_STAGE);
+static int padk(int v) { return (v + CONV_KSTEP - 1) / CONV_KSTEP * CONV_KSTEP; }
 constexpr unsigned UMMA_WAIT_LIMIT = 1u << 22;  // bounded mbarrier waits (polls)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -130,10 +147,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity,
   return false;
 }
 
+// 16-byte global -> shared copy; `bytes` = 0 fills the destination with zeros
+// (src is then not read).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 __global__ void __launch_bounds__(128) k_conv_umma(ConvArgs a, DeviceStatus *status) {
-  __shared__ __align__(1024) uint8_t sA[2][UMMA_A_BYTES];
-  __shared__ __align__(1024) uint8_t sB[2][UMMA_B_BYTES];
-  __shared__ __align__(8) uint64_t mbar[2];
+  extern __shared__ __align__(1024) uint8_t conv_smem[];  // stages: A tiles, then B tiles
+  __shared__ __align__(8) uint64_t mbar[CONV_STAGES];
   __shared__ uint32_t tmem_holder;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -149,7 +179,7 @@ __global__ void __launch_bounds__(128) k_conv_umma(ConvArgs a, DeviceStatus *sta
   }
   if (tid == 0) {
     s_fail = 0;
-    for (int i = 0; i < 2; i++)
+    for (int i = 0; i < CONV_STAGES; i++)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[i])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -158,9 +188,8 @@ __global__ void __launch_bounds__(128) k_conv_umma(ConvArgs a, DeviceStatus *sta
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_holder;
 
-  // thread t stages row t of the A tile (pixel m0 + t, 16 consecutive k: each
-  // warp load reads 32 neighbouring pixels of one channel and tap) as two
-  // 16-byte shared stores, and half a row of the B^T tile (row t % 64)
+  // this thread's A row (pixel m0 + tid) and B^T row tid % 64 (its pieces:
+  // (tid / 64) + 2 i, i < CONV_SUB, numbering the stage's 16-k slice halves)
   const int ms = m0 + tid;
   int pb = -1, py = 0, px = 0;
   if (ms < M) {
@@ -169,75 +198,85 @@ __global__ void __launch_bounds__(128) k_conv_umma(ConvArgs a, DeviceStatus *sta
     py = p / a.W;
     px = p - py * a.W;
   }
-  const int bn = tid & 63, bh = tid >> 6;
-  const __nv_bfloat16 *actb = pb >= 0 ? a.act + (size_t)pb * a.C * HW : a.act;
+  const int bn = tid & 63, bq = tid >> 6;
+  const __nv_bfloat16 *brow = a.Bt + (size_t)(n0 + bn) * a.Kp;
+  const uint32_t sA0 = smem_u32(conv_smem), sB0 = sA0 + CONV_STAGES * CONV_A_STAGE;
+  auto issue = [&](int s) {  // the copies of stage s (K from s * CONV_KSTEP) into buffer s % CONV_STAGES
+    const int buf = s % CONV_STAGES, k0 = s * CONV_KSTEP;
+    const uint32_t aS = sA0 + buf * CONV_A_STAGE, bS = sB0 + buf * CONV_B_STAGE;
+#pragma unroll
+    for (int g = 0; g < CONV_KSTEP / 8; g++) {
+      const int kk = k0 + 8 * g;
+      const __nv_bfloat16 *src = a.act;
+      int bytes = 0;
+      if (pb >= 0 && kk < a.K) {
+        const int tap = kk / a.Ca, c0 = kk - tap * a.Ca;
+        const int yy = py + a.sign * ((tap / 3) - 1) * a.dil;
+        const int xx = px + a.sign * ((tap % 3) - 1) * a.dil;
+        if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
+          src = a.act + (((size_t)pb * a.H + yy) * a.W + xx) * a.Ca + c0;
+          bytes = 16;
+        }
+      }
+      cp_async16(aS + (g >> 1) * UMMA_A_BYTES + umma_off(tid, 8 * (g & 1)), src, bytes);
+    }
+#pragma unroll
+    for (int i = 0; i < CONV_SUB; i++) {  // piece (row bn, 16-k slice, half) of the B^T stage
+      const int rest = bq + 2 * i, sub = rest >> 1, e = rest & 1;
+      cp_async16(bS + sub * UMMA_B_BYTES + umma_off(bn, 8 * e), brow + k0 + UMMA_K * sub + 8 * e, 16);
+    }
+  };
   const uint32_t idesc = umma_idesc(UMMA_M, UMMA_N);
-  int nsteps = a.Kp / UMMA_K;
+  int nsteps = a.Kp / CONV_KSTEP;
   if (a.stall > 0) {  // test hook: stage 0's barrier before any MMA (nothing completes it)
     if (!mbar_wait(smem_u32(&mbar[0]), 0u, (unsigned)a.stall)) s_fail = 1;
     __syncthreads();
     if (s_fail) nsteps = 0;  // no MMA in flight: the accumulator is freed below
   }
-  uint32_t phase[2] = {0u, 0u};
+  uint32_t phase = 0u;  // bit i: parity of stage i's next mbarrier phase
+#pragma unroll
+  for (int s = 0; s < CONV_AHEAD; s++) {
+    if (s < nsteps) issue(s);
+    cp_async_commit();
+  }
   for (int step = 0; step < nsteps; step++) {
-    const int st = step & 1, k0 = step * UMMA_K;
-    if (step >= 2) {  // the MMA issued two steps ago has released this stage
-      if (!mbar_wait(smem_u32(&mbar[st]), phase[st])) s_fail = 1;
-      phase[st] ^= 1u;
-    }
-    {
-      uint32_t pk[8];
-#pragma unroll
-      for (int kk = 0; kk < UMMA_K; kk += 2) {
-        unsigned short h2[2];
-#pragma unroll
-        for (int u = 0; u < 2; u++) {
-          const int k = k0 + kk + u;
-          __nv_bfloat16 v = __float2bfloat16(0.f);
-          if (k < a.K && pb >= 0) {
-            const int c = k / 9, tap = k - 9 * c;
-            const int yy = py + a.sign * ((tap / 3) - 1) * a.dil, xx = px + a.sign * ((tap % 3) - 1) * a.dil;
-            if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) v = actb[(size_t)c * HW + (size_t)yy * a.W + xx];
-          }
-          h2[u] = __bfloat16_as_ushort(v);
-        }
-        pk[kk >> 1] = (uint32_t)h2[0] | ((uint32_t)h2[1] << 16);
+    const int ns = step + CONV_AHEAD;
+    if (ns < nsteps) {
+      const int nb = ns % CONV_STAGES;
+      if (ns >= CONV_STAGES) {  // the MMAs of step ns - CONV_STAGES read stage nb
+        if (!mbar_wait(smem_u32(&mbar[nb]), (phase >> nb) & 1u)) s_fail = 1;
+        phase ^= 1u << nb;
       }
-      *(uint4 *)(sA[st] + umma_off(tid, 0)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-      *(uint4 *)(sA[st] + umma_off(tid, 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-      uint32_t qb[4];
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        const int k = k0 + 8 * bh + 2 * i;
-        const __nv_bfloat16 lo = a.Bmat[(size_t)k * a.Np + n0 + bn], hi = a.Bmat[(size_t)(k + 1) * a.Np + n0 + bn];
-        qb[i] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-      }
-      *(uint4 *)(sB[st] + umma_off(bn, 8 * bh)) = make_uint4(qb[0], qb[1], qb[2], qb[3]);
+      issue(ns);
     }
+    cp_async_commit();
+    cp_async_wait<CONV_AHEAD>();  // this thread's copies of stage `step` landed
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
     if (tid == 0) {
+      const int buf = step % CONV_STAGES;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint64_t adesc = umma_desc(smem_u32(sA[st]), 128, 256);
-      const uint64_t bdesc = umma_desc(smem_u32(sB[st]), 128, 256);
-      const uint32_t acc = step > 0 ? 1u : 0u;
-      asm volatile(
-          "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-          "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-          : "memory");
+#pragma unroll
+      for (int sub = 0; sub < CONV_SUB; sub++) {
+        const uint64_t adesc = umma_desc(sA0 + buf * CONV_A_STAGE + sub * UMMA_A_BYTES, 128, 256);
+        const uint64_t bdesc = umma_desc(sB0 + buf * CONV_B_STAGE + sub * UMMA_B_BYTES, 128, 256);
+        const uint32_t acc = (step > 0 || sub > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+      }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                       smem_u32(&mbar[st]))
+                       smem_u32(&mbar[buf]))
                    : "memory");
     }
   }
-  // wait for the last MMA of each stage still in flight
-  for (int st = 0; st < 2; st++) {
-    const int uses = (nsteps - st + 1) / 2;  // MMAs issued on this stage; all but the last waited
-    if (uses > 0) {
-      if (!mbar_wait(smem_u32(&mbar[st]), phase[st])) s_fail = 1;
-      phase[st] ^= 1u;
-    }
+  cp_async_wait<0>();
+  // the last MMAs (commits complete in order, so every earlier MMA is done too)
+  if (nsteps > 0) {
+    const int lb = (nsteps - 1) % CONV_STAGES;
+    if (!mbar_wait(smem_u32(&mbar[lb]), (phase >> lb) & 1u)) s_fail = 1;
   }
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -246,7 +285,7 @@ __global__ void __launch_bounds__(128) k_conv_umma(ConvArgs a, DeviceStatus *sta
 
   // epilogue: row m0 + 32 warp + lane, eight columns per tcgen05.ld
   const int m = m0 + warp * 32 + lane;
-  const int b = m / HW, p = m - b * HW;
+  const int b = m / HW, p = m - b * HW, Cs = cpad8(a.N);
 #pragma unroll 1
   for (int c0 = 0; c0 < UMMA_N; c0 += 8) {
     uint32_t r[8];
@@ -257,16 +296,42 @@ __global__ void __launch_bounds__(128) k_conv_umma(ConvArgs a, DeviceStatus *sta
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-    if (!ok || m >= M) continue;
+    const int nb = n0 + c0;
+    if (!ok || m >= M || nb >= Cs) continue;
+    float v[8];
 #pragma unroll
     for (int j = 0; j < 8; j++) {
-      const int n = n0 + c0 + j;
-      if (n >= a.N) continue;
-      const size_t o = ((size_t)b * a.N + n) * HW + p;
-      float v = __uint_as_float(r[j]) + (a.bias ? a.bias[n] : 0.f);
-      if (a.mask_pre && !(a.mask_pre[o] > 0.f)) v = 0.f;
-      if (a.out) a.out[o] = v;
-      if (a.out_bf) a.out_bf[o] = __float2bfloat16(a.relu ? fmaxf(v, 0.f) : v);
+      const int n = nb + j;
+      v[j] = n < a.N ? __uint_as_float(r[j]) + (a.bias ? a.bias[n] : 0.f) : 0.f;
+    }
+    if (a.out_nchw) {
+#pragma unroll
+      for (int j = 0; j < 8; j++)
+        if (nb + j < a.N) a.out[((size_t)b * a.N + nb + j) * HW + p] = v[j];
+      continue;
+    }
+    const size_t o = (size_t)m * Cs + nb;  // 8 channels of pixel m: 32 / 16 aligned bytes
+    if (a.mask_pre) {
+      const float4 q0 = *(const float4 *)(a.mask_pre + o), q1 = *(const float4 *)(a.mask_pre + o + 4);
+      const float q[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+      for (int j = 0; j < 8; j++)
+        if (!(q[j] > 0.f)) v[j] = 0.f;
+    }
+    if (a.out) {
+      *(float4 *)(a.out + o) = make_float4(v[0], v[1], v[2], v[3]);
+      *(float4 *)(a.out + o + 4) = make_float4(v[4], v[5], v[6], v[7]);
+    }
+    if (a.out_bf) {
+      uint32_t w[4];
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const float lo = a.relu ? fmaxf(v[2 * j], 0.f) : v[2 * j];
+        const float hi = a.relu ? fmaxf(v[2 * j + 1], 0.f) : v[2 * j + 1];
+        w[j] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(lo)) |
+               ((uint32_t)__bfloat16_as_ushort(__float2bfloat16(hi)) << 16);
+      }
+      *(uint4 *)(a.out_bf + o) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -278,32 +343,32 @@ __global__ void __launch_bounds__(128) k_conv_umma(ConvArgs a, DeviceStatus *sta
 
 // ------------------------------------------------------------------ wgrad ---
 struct WgradArgs {
-  const __nv_bfloat16 *g;    // [B][N][H][W] gradient at the pre-activation
-  const __nv_bfloat16 *act;  // [B][C][H][W] layer input
-  int B, C, H, W, dil, N, K;
-  float *dW;                 // [N][K]
+  const __nv_bfloat16 *g;    // [B][H][W][Cg] gradient at the pre-activation (channels-last)
+  const __nv_bfloat16 *act;  // [B][H][W][Ca] layer input (channels-last)
+  int B, C, Ca, H, W, dil, N, Cg, K;  // K = 9 * Ca rows, k = tap * Ca + c
+  float *dW;                 // [N][C][3][3]
   float *db;                 // [N]
   int pix_per_cta;
   int stall;                 // test hook: > 0 polls of a wait that nothing completes
 };
 
 // Weight gradient on tcgen05: the transposed product D[k][n] = sum_m A[m][k] G[m][n]
-// (k = (cin, tap) rows, 128 per CTA; n = cout columns, 64; the reduction runs over
+// (k = (tap, c) rows, 128 per CTA; n = cout columns, 64; the reduction runs over
 // the CTA's pixel range, WG_PIX pixels per stage = two MMAs of 16). A^T tile row k =
 // the layer input at tap(k) of channel c(k) for the stage's pixels; G^T tile row n =
-// the gradient of channel n for the same pixels. Lane = pixel when staging, so each
-// warp load reads 64 contiguous bytes of one row. Each 16-pixel half of a tile is
-// K-major in the same core-matrix layout as the forward kernel; the FP32 result is
-// added into dW with atomics (the summation order over CTAs is unspecified).
+// the gradient of channel n for the same pixels. Lane = pixel when staging: a
+// thread loads the 8 channels (16 bytes) of a row group of its pixel and stores
+// them down the tile's column. Each 16-pixel half of a tile is K-major in the same
+// core-matrix layout as the convolution kernel; the FP32 result is added into dW
+// with atomics (the summation order over CTAs is unspecified).
 constexpr int WG_PIX = 32;
 constexpr int WG_A_HALF = UMMA_M * 16 * 2, WG_B_HALF = UMMA_N * 16 * 2;
-__global__ void __launch_bounds__(128, 8) k_wgrad_umma(WgradArgs a, DeviceStatus *status) {
+__global__ void __launch_bounds__(128, 6) k_wgrad_umma(WgradArgs a, DeviceStatus *status) {
   __shared__ __align__(1024) uint8_t sA[2][2 * WG_A_HALF];
   __shared__ __align__(1024) uint8_t sB[2][2 * WG_B_HALF];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_holder;
   __shared__ int s_fail;
-  __shared__ int s_koff[UMMA_M], s_kdy[UMMA_M], s_kdx[UMMA_M];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int HW = a.H * a.W, M = a.B * HW;
   const int kt0 = blockIdx.y * UMMA_M;
@@ -322,20 +387,24 @@ __global__ void __launch_bounds__(128, 8) k_wgrad_umma(WgradArgs a, DeviceStatus
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[i])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  {  // per A^T row: channel offset (-1 past K) and tap displacement
-    const int k = kt0 + tid, tap = k % 9;
-    s_koff[tid] = k < a.K ? (k / 9) * HW : -1;
-    s_kdy[tid] = ((tap / 3) - 1) * a.dil;
-    s_kdx[tid] = ((tap % 3) - 1) * a.dil;
+  // this thread's A^T row groups rg = warp + 4 q (q = 0..3): tap, first channel,
+  // displacement (tap < 0: past K)
+  int rtap[4], rc0[4], rdy[4], rdx[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int k = kt0 + 8 * (warp + 4 * q);
+    rtap[q] = k < a.K ? k / a.Ca : -1;
+    rc0[q] = k < a.K ? k - rtap[q] * a.Ca : 0;
+    rdy[q] = rtap[q] >= 0 ? ((rtap[q] / 3) - 1) * a.dil : 0;
+    rdx[q] = rtap[q] >= 0 ? ((rtap[q] % 3) - 1) * a.dil : 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_holder;
 
-  // staging: lane = pixel of the stage; warp w fills A^T rows 32w..32w+31 and
-  // G^T rows 16w..16w+15. Byte offset of (row, pixel lane) inside a stage tile:
-  const int a_lane = (lane >> 4) * WG_A_HALF, b_lane = (lane >> 4) * WG_B_HALF;
+  // staging: lane = pixel of the stage; byte offset of the lane's 16-pixel half
+  const int a_lane = (lane >> 4) * WG_A_HALF, b_lane = (lane >> 4) * WG_B_HALF, col = lane & 15;
   const uint32_t idesc = umma_idesc(UMMA_M, UMMA_N);
   int nsteps = (p1 - p0 + WG_PIX - 1) / WG_PIX;
   if (a.stall > 0) {  // test hook: stage 0's barrier before any MMA (nothing completes it)
@@ -343,9 +412,11 @@ __global__ void __launch_bounds__(128, 8) k_wgrad_umma(WgradArgs a, DeviceStatus
     __syncthreads();
     if (s_fail) nsteps = 0;  // no MMA in flight: the accumulator is freed below
   }
-  float bsum[16];  // this lane's share of the bias gradient of G^T rows 16w..16w+15
+  float bsum[2][8];  // this lane's share of the bias gradient of G^T rows 8 (warp + 4 q) + i
 #pragma unroll
-  for (int i = 0; i < 16; i++) bsum[i] = 0.f;
+  for (int q = 0; q < 2; q++)
+#pragma unroll
+    for (int i = 0; i < 8; i++) bsum[q][i] = 0.f;
   uint32_t phase[2] = {0u, 0u};
   for (int step = 0; step < nsteps; step++) {
     const int st = step & 1;
@@ -356,22 +427,38 @@ __global__ void __launch_bounds__(128, 8) k_wgrad_umma(WgradArgs a, DeviceStatus
     const int m = p0 + step * WG_PIX + lane;
     const bool pin = m < p1;
     const int b = pin ? m / HW : 0, pp = m - b * HW, y = pp / a.W, x = pp - y * a.W;
-    const __nv_bfloat16 *actp = a.act + (size_t)b * a.C * HW + pp;
-    const __nv_bfloat16 *gp = a.g + (size_t)b * a.N * HW + pp;
-#pragma unroll 8
-    for (int i = 0; i < 32; i++) {
-      const int row = warp * 32 + i, koff = s_koff[row], dy = s_kdy[row], dx = s_kdx[row];
-      __nv_bfloat16 v = __float2bfloat16(0.f);
-      if (pin && koff >= 0 && (unsigned)(y + dy) < (unsigned)a.H && (unsigned)(x + dx) < (unsigned)a.W)
-        v = actp[koff + dy * a.W + dx];
-      *(__nv_bfloat16 *)(sA[st] + a_lane + umma_off(row, lane & 15)) = v;
+    uint4 va[4], vg[2];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      va[q] = make_uint4(0, 0, 0, 0);
+      const int yy = y + rdy[q], xx = x + rdx[q];
+      if (pin && rtap[q] >= 0 && (unsigned)yy < (unsigned)a.H && (unsigned)xx < (unsigned)a.W)
+        va[q] = *(const uint4 *)(a.act + (((size_t)b * a.H + yy) * a.W + xx) * a.Ca + rc0[q]);
     }
 #pragma unroll
-    for (int i = 0; i < 16; i++) {
-      const int n = warp * 16 + i;
-      const __nv_bfloat16 v = (pin && n < a.N) ? gp[(size_t)n * HW] : __float2bfloat16(0.f);
-      *(__nv_bfloat16 *)(sB[st] + b_lane + umma_off(n, lane & 15)) = v;
-      bsum[i] += __bfloat162float(v);
+    for (int q = 0; q < 2; q++) {
+      const int n8 = 8 * (warp + 4 * q);
+      vg[q] = (pin && n8 < a.Cg) ? *(const uint4 *)(a.g + (size_t)m * a.Cg + n8) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const uint32_t w[4] = {va[q].x, va[q].y, va[q].z, va[q].w};
+      const int r0 = 8 * (warp + 4 * q);
+#pragma unroll
+      for (int i = 0; i < 8; i++)
+        *(unsigned short *)(sA[st] + a_lane + umma_off(r0 + i, col)) =
+            (unsigned short)(w[i >> 1] >> (16 * (i & 1)));
+    }
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+      const uint32_t w[4] = {vg[q].x, vg[q].y, vg[q].z, vg[q].w};
+      const int r0 = 8 * (warp + 4 * q);
+#pragma unroll
+      for (int i = 0; i < 8; i++) {
+        const unsigned short h = (unsigned short)(w[i >> 1] >> (16 * (i & 1)));
+        *(unsigned short *)(sB[st] + b_lane + umma_off(r0 + i, col)) = h;
+        bsum[q][i] += __bfloat162float(__ushort_as_bfloat16(h));
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
@@ -404,7 +491,8 @@ __global__ void __launch_bounds__(128, 8) k_wgrad_umma(WgradArgs a, DeviceStatus
   __syncthreads();
   const bool ok = s_fail == 0 && nsteps > 0;
   if (s_fail && tid == 0) raise_status(status, DEV_ERR_TIMEOUT, blockIdx.x, blockIdx.y);
-  const int kr = kt0 + warp * 32 + lane;  // this thread's accumulator row
+  const int kr = kt0 + warp * 32 + lane;  // this thread's accumulator row: (tap, c)
+  const int ktap = kr / a.Ca, kc = kr - ktap * a.Ca;
 #pragma unroll 1
   for (int c0 = 0; c0 < UMMA_N; c0 += 8) {
     uint32_t r[8];
@@ -415,11 +503,11 @@ __global__ void __launch_bounds__(128, 8) k_wgrad_umma(WgradArgs a, DeviceStatus
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-    if (!ok || kr >= a.K) continue;
+    if (!ok || kr >= a.K || kc >= a.C) continue;
 #pragma unroll
     for (int j = 0; j < 8; j++) {
       const int n = c0 + j;
-      if (n < a.N) atomicAdd(&a.dW[(size_t)n * a.K + kr], __uint_as_float(r[j]));
+      if (n < a.N) atomicAdd(&a.dW[((size_t)n * a.C + kc) * 9 + ktap], __uint_as_float(r[j]));
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -430,36 +518,42 @@ __global__ void __launch_bounds__(128, 8) k_wgrad_umma(WgradArgs a, DeviceStatus
   // bias gradient (first row block only): the sums of the staged G^T values
   if (blockIdx.y == 0 && a.db) {
 #pragma unroll
-    for (int i = 0; i < 16; i++) {
-      float v = bsum[i];
-      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      const int n = warp * 16 + i;
-      if (lane == 0 && n < a.N) atomicAdd(&a.db[n], v);
-    }
+    for (int q = 0; q < 2; q++)
+#pragma unroll
+      for (int i = 0; i < 8; i++) {
+        float v = bsum[q][i];
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int n = 8 * (warp + 4 * q) + i;
+        if (lane == 0 && n < a.N) atomicAdd(&a.db[n], v);
+      }
   }
 }
 
 // ------------------------------------------------------------- helpers ------
-// Forward weight matrix: Bf[(c*9 + tap)][n] = W[n][c][tap] (bf16, zero padded).
-// Dgrad weight matrix:   Bd[(n*9 + tap)][c] = W[n][c][tap] (taps applied mirrored).
-__global__ void k_pack_weights(const float *W, int N, int C, __nv_bfloat16 *Bf, int Npf,
-                               __nv_bfloat16 *Bd, int Npd, int Kpf, int Kpd) {
+// Forward weights, K-major: Bf[n][tap * Ca + c] = W[n][c][tap]; dgrad weights:
+// Bd[c][tap * Cg + n] = W[n][c][tap] (the taps are applied mirrored). BF16, zero
+// outside the layer's channels.
+__global__ void k_pack_weights(const float *W, int N, int C, int Ca, int Cg, __nv_bfloat16 *Bf,
+                               int Npf, int Kpf, __nv_bfloat16 *Bd, int Npd, int Kpd) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int total = max(Kpf * Npf, Kpd * Npd);
-  if (i >= total) return;
-  if (i < Kpf * Npf) {
-    const int k = i / Npf, n = i % Npf, c = k / 9, tap = k % 9;
-    Bf[i] = __float2bfloat16((k < C * 9 && n < N) ? W[((size_t)n * C + c) * 9 + tap] : 0.f);
+  if (i < Npf * Kpf) {
+    const int n = i / Kpf, k = i % Kpf, tap = k / Ca, c = k % Ca;
+    Bf[i] = __float2bfloat16((n < N && tap < 9 && c < C) ? W[((size_t)n * C + c) * 9 + tap] : 0.f);
   }
-  if (Bd && i < Kpd * Npd) {
-    const int k = i / Npd, c = i % Npd, n = k / 9, tap = k % 9;
-    Bd[i] = __float2bfloat16((k < N * 9 && c < C) ? W[((size_t)n * C + c) * 9 + tap] : 0.f);
+  if (Bd && i < Npd * Kpd) {
+    const int c = i / Kpd, k = i % Kpd, tap = k / Cg, n = k % Cg;
+    Bd[i] = __float2bfloat16((c < C && tap < 9 && n < N) ? W[((size_t)n * C + c) * 9 + tap] : 0.f);
   }
 }
 
-__global__ void k_to_bf16(const float *x, size_t n, __nv_bfloat16 *y) {
+// NCHW fp32 [B][C][HW] -> channels-last bf16 [B][HW][Cp], zero channels C..Cp-1.
+__global__ void k_to_nhwc_bf16(const float *x, int B, int C, int HW, int Cp, __nv_bfloat16 *y) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = __float2bfloat16(x[i]);
+  if (i >= (size_t)B * HW * Cp) return;
+  const int c = (int)(i % Cp);
+  const size_t pix = i / Cp;
+  const size_t b = pix / HW, p = pix % HW;
+  y[i] = __float2bfloat16(c < C ? x[(b * C + c) * HW + p] : 0.f);
 }
 
 // Net input: area mean of each 8x8 block (integer, as for I^n) of both frames,
@@ -555,10 +649,11 @@ __global__ void k_proposals(const float *out, int B, int K, int Gx, int Gy, floa
 
 // ------------------------------------------------------------ workspace ----
 struct NetWs {
-  __nv_bfloat16 *act[NET_LAYERS + 1];  // bf16 input of layer l (act[0] = x); act[4] unused
-  float *pre[NET_LAYERS];              // fp32 pre-activation of layer l
+  __nv_bfloat16 *act[NET_LAYERS + 1];  // bf16 input of layer l, [P][Ca[l]]; act[4] unused
+  float *pre[NET_LAYERS];              // fp32 pre-activation of layer l, [P][Cg[l]]
   __nv_bfloat16 *Bf[NET_LAYERS], *Bd[NET_LAYERS];
-  __nv_bfloat16 *gbf[NET_LAYERS];      // bf16 gradient at the pre-activation of layer l
+  __nv_bfloat16 *gbf[NET_LAYERS];      // bf16 gradient at the pre-activation of layer l, [P][Cg[l]]
+  int Ca[NET_LAYERS], Cg[NET_LAYERS];  // channel strides: cin, cout padded to 8
   int Kpf[NET_LAYERS], Npf[NET_LAYERS], Kpd[NET_LAYERS], Npd[NET_LAYERS];
 };
 
@@ -566,12 +661,14 @@ static NetWs net_ws(Arena &a, const NetShape &s, int B, int Gx, int Gy) {
   NetWs w;
   const size_t P = (size_t)B * Gx * Gy;
   for (int l = 0; l < NET_LAYERS; l++) {
-    w.act[l] = a.take<__nv_bfloat16>(P * s.cin[l]);
-    w.pre[l] = a.take<float>(P * s.cout[l]);
-    w.gbf[l] = a.take<__nv_bfloat16>(P * s.cout[l]);
-    w.Kpf[l] = pad16(s.cin[l] * 9);
+    w.Ca[l] = cpad8(s.cin[l]);
+    w.Cg[l] = cpad8(s.cout[l]);
+    w.act[l] = a.take<__nv_bfloat16>(P * w.Ca[l]);
+    w.pre[l] = a.take<float>(P * w.Cg[l]);
+    w.gbf[l] = a.take<__nv_bfloat16>(P * w.Cg[l]);
+    w.Kpf[l] = padk(9 * w.Ca[l]);
     w.Npf[l] = pad64(s.cout[l]);
-    w.Kpd[l] = pad16(s.cout[l] * 9);
+    w.Kpd[l] = padk(9 * w.Cg[l]);
     w.Npd[l] = pad64(s.cin[l]);
     w.Bf[l] = a.take<__nv_bfloat16>((size_t)w.Kpf[l] * w.Npf[l]);
     w.Bd[l] = a.take<__nv_bfloat16>((size_t)w.Kpd[l] * w.Npd[l]);
@@ -583,7 +680,8 @@ static NetWs net_ws(Arena &a, const NetShape &s, int B, int Gx, int Gy) {
 static ff_status launch_conv(ConvArgs c, int M, DeviceStatus *status, cudaStream_t st) {
   dim3 g((M + UMMA_M - 1) / UMMA_M, c.Np / UMMA_N);
   c.stall = net_stall_polls();
-  k_conv_umma<<<g, 128, 0, st>>>(c, status);
+  FF_TRY(smem_opt_in((const void *)k_conv_umma, CONV_SMEM));
+  k_conv_umma<<<g, 128, CONV_SMEM, st>>>(c, status);
   FF_CHECK_LAUNCH();
   return FF_OK;
 }
@@ -635,30 +733,35 @@ ff_status ff_net_forward(const ff_net_desc *d, const float *params, const float 
   a.take<char>(WS_HEADER);
   NetWs w = net_ws(a, s, B, Gx, Gy);
   const size_t P = (size_t)B * Gx * Gy;
-  k_to_bf16<<<(unsigned)((P * s.cin[0] + 255) / 256), 256, 0, st>>>(x, P * s.cin[0], w.act[0]);
-  FF_CHECK_LAUNCH();
+  {
+    const size_t tot = P * w.Ca[0];
+    k_to_nhwc_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(x, B, s.cin[0], Gx * Gy, w.Ca[0],
+                                                                  w.act[0]);
+    FF_CHECK_LAUNCH();
+  }
   for (int l = 0; l < NET_LAYERS; l++) {
     const int tot = max(w.Kpf[l] * w.Npf[l], w.Kpd[l] * w.Npd[l]);
     k_pack_weights<<<(tot + 255) / 256, 256, 0, st>>>(params + s.woff[l], s.cout[l], s.cin[l],
-                                                     w.Bf[l], w.Npf[l], w.Bd[l], w.Npd[l],
-                                                     w.Kpf[l], w.Kpd[l]);
+                                                     w.Ca[l], w.Cg[l], w.Bf[l], w.Npf[l],
+                                                     w.Kpf[l], w.Bd[l], w.Npd[l], w.Kpd[l]);
     FF_CHECK_LAUNCH();
     const bool last = l == NET_LAYERS - 1;
     ConvArgs c{};
     c.act = w.act[l];
     c.B = B;
-    c.C = s.cin[l];
+    c.Ca = w.Ca[l];
     c.H = Gy;
     c.W = Gx;
     c.dil = s.dil[l];
     c.sign = 1;
-    c.Bmat = w.Bf[l];
-    c.K = s.cin[l] * 9;
+    c.Bt = w.Bf[l];
+    c.K = 9 * w.Ca[l];
     c.Kp = w.Kpf[l];
     c.N = s.cout[l];
     c.Np = w.Npf[l];
     c.bias = params + s.boff[l];
     c.out = last ? out : w.pre[l];
+    c.out_nchw = last ? 1 : 0;
     c.out_bf = last ? nullptr : w.act[l + 1];
     c.relu = last ? 0 : 1;
     FF_TRY(launch_conv(c, (int)P, (DeviceStatus *)ws, st));
@@ -687,25 +790,31 @@ ff_status ff_net_backward(const ff_net_desc *d, const float *params, const float
   if (cudaMemsetAsync(ws, 0, sizeof(DeviceStatus), st) != cudaSuccess) return FF_ERR_CUDA;
   // gradient at the last pre-activation (the output has no ReLU)
   const int L = NET_LAYERS - 1;
-  k_to_bf16<<<(unsigned)((P * s.cout[L] + 255) / 256), 256, 0, st>>>(dout, P * s.cout[L], w.gbf[L]);
-  FF_CHECK_LAUNCH();
+  {
+    const size_t tot = P * w.Cg[L];
+    k_to_nhwc_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(dout, B, s.cout[L], Gx * Gy,
+                                                                  w.Cg[L], w.gbf[L]);
+    FF_CHECK_LAUNCH();
+  }
   for (int l = L; l >= 0; l--) {
     WgradArgs wa{};
     wa.g = w.gbf[l];
     wa.act = w.act[l];
     wa.B = B;
     wa.C = s.cin[l];
+    wa.Ca = w.Ca[l];
     wa.H = Gy;
     wa.W = Gx;
     wa.dil = s.dil[l];
     wa.N = s.cout[l];
-    wa.K = s.cin[l] * 9;
+    wa.Cg = w.Cg[l];
+    wa.K = 9 * w.Ca[l];
     wa.dW = grads + s.woff[l];
     wa.db = grads + s.boff[l];
-    // pixel range per CTA: about eight CTAs per SM over the whole grid (the
+    // pixel range per CTA: about six CTAs per SM over the whole grid (the
     // staging is load-latency bound), whole 32-pixel stages, at least 64 pixels
     const int ky = (wa.K + UMMA_M - 1) / UMMA_M;
-    const long long want = (long long)nsm * 8;
+    const long long want = (long long)nsm * 6;
     long long ppc = ((long long)P * ky + want - 1) / want;
     ppc = ((ppc + WG_PIX - 1) / WG_PIX) * WG_PIX;
     wa.pix_per_cta = (int)(ppc < 64 ? 64 : ppc);
@@ -718,13 +827,13 @@ ff_status ff_net_backward(const ff_net_desc *d, const float *params, const float
     ConvArgs c{};
     c.act = w.gbf[l];
     c.B = B;
-    c.C = s.cout[l];
+    c.Ca = w.Cg[l];
     c.H = Gy;
     c.W = Gx;
     c.dil = s.dil[l];
     c.sign = -1;
-    c.Bmat = w.Bd[l];
-    c.K = s.cout[l] * 9;
+    c.Bt = w.Bd[l];
+    c.K = 9 * w.Cg[l];
     c.Kp = w.Kpd[l];
     c.N = s.cin[l];
     c.Np = w.Npd[l];
