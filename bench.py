@@ -186,8 +186,11 @@ def pass_roofline(run, steps, flush, stream, taps_peak, l2_peak):
     every pass launch on its own stream), against the measured shared-memory tap
     rate (popcount issue: one popcount per tap). The same launches with the three
     flows on one stream give the rate of a
-    launch timed alone. The L2 figure counts the taps gathered from the census
-    planes (4 B each) over the same time."""
+    launch timed alone. The L2 figure counts the taps read from the census planes
+    (4 B each) over the same time, and l2_frac sets it against the measured
+    contiguous L2 read rate, the L2's upper bound (a lane reads a patch row as one
+    run of 2r+1 words, partly served by L1, so the random-gather rates are no
+    bound)."""
     from paper_1508_05151_gb300 import ffapi
     import torch
     # evaluation counts of one step (the search is deterministic: every step is
@@ -450,7 +453,7 @@ def batch_measure(dev, params, pk, flush, reps=3):
     direct.run(frames)
     torch.cuda.synchronize()
     pr = pass_roofline(lambda i: direct.run(frames), reps, flush, stream, pk["popc_per_s"],
-                       pk["l2_word_gather_gbs"])
+                       pk["l2_coalesced_gbs"])
     tap_bytes = sum(gather_bytes_prop(W, H, params) for W, H in sizes)
     roof = {"bound": "alu", "achieved": round(pr["achieved_gtaps"], 1),
             "peak": round(pk["popc_per_s"] / 1e9, 1), "unit": "Gtap/s",
@@ -674,7 +677,7 @@ def run_ours(args):
     pk = measure_peaks(dev) if rank == 0 else None
     pr = pass_roofline(lambda i: direct.run(*dI[i % 2]), args.steps, flush, stream,
                        pk["popc_per_s"] if pk else 1.0,
-                       pk["l2_word_gather_gbs"] if pk else 1.0)
+                       pk["l2_coalesced_gbs"] if pk else 1.0)
     timeline = phase_timeline(lambda i: direct.run(*dI[i % 2]), flush, stream)
 
     # ---- end to end through the public graph API with host buffers ----
