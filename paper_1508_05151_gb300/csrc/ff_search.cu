@@ -416,11 +416,10 @@ __global__ void __launch_bounds__(PASS_MAX_WARPS * 32) k_pass(const SearchProble
         ti_ = tc + oi * tp - R;
       }
       cost = cq + lane_line_delta<R>(so_, si_, ss, to_, ti_, ts);
-    } else if (t.win) {
-      cost = lane_full<R>(sc, Lt.swp, s_tgt + (t.ey - toy) * Lt.twp + (t.ex - tox), Lt.twp);
-    } else {
-      cost = lane_full<R>(sc, Lt.swp, tbase + (size_t)t.ph * tpw_ + (size_t)t.ey * tpitch + t.ex,
-                          tpitch);
+    } else {  // one call for both sources, so that a warp never runs the loop twice
+      const uint32_t *tc = t.win ? s_tgt + (t.ey - toy) * Lt.twp + (t.ex - tox)
+                                 : tbase + (size_t)t.ph * tpw_ + (size_t)t.ey * tpitch + t.ex;
+      cost = lane_full<R>(sc, Lt.swp, tc, t.win ? Lt.twp : tpitch);
     }
     return cf;
   };
@@ -544,8 +543,9 @@ __global__ void __launch_bounds__(PASS_MAX_WARPS * 32) k_pass(const SearchProble
       const Tgt t = locate(px, py, cf);
       if (cfg.evals) count_eval(scnt, true, t.win);
       const uint32_t *sc = s_src + (ly + R + 1) * Lt.swp + (lx + R + 1);
-      const int cost = t.win ? lane_full<R>(sc, Lt.swp, s_tgt + (t.ey - toy) * Lt.twp + (t.ex - tox), Lt.twp)
-                             : lane_full<R>(sc, Lt.swp, tbase + (size_t)t.ph * tpw_ + (size_t)t.ey * tpitch + t.ex, tpitch);
+      const uint32_t *tc = t.win ? s_tgt + (t.ey - toy) * Lt.twp + (t.ex - tox)
+                                 : tbase + (size_t)t.ph * tpw_ + (size_t)t.ey * tpitch + t.ex;
+      const int cost = lane_full<R>(sc, Lt.swp, tc, t.win ? Lt.twp : tpitch);
       if (cost < cc) {
         s_flow[ly * T + lx] = cf;
         s_cost[ly * T + lx] = cost;
@@ -735,11 +735,10 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
         part = part_line_delta<R, SPLIT>(sb + oo * sx, sb + oi * sx, sa, tb + oo * tx, tb + oi * tx,
                                          ta, u) +
                (u == 0 ? cq : 0);
-      } else if (win) {
-        part = part_full<R, SPLIT>(sc, Lt.swp, S.tgt + (ey - toy) * Lt.twp + (ex - tox), Lt.twp, u);
-      } else {
-        part = part_full<R, SPLIT>(sc, Lt.swp, tbase + (size_t)ph * tpw_ + (size_t)ey * tpitch + ex,
-                                   tpitch, u);
+      } else {  // one call for both sources, so that a warp never runs the loop twice
+        const uint32_t *tc = win ? S.tgt + (ey - toy) * Lt.twp + (ex - tox)
+                                 : tbase + (size_t)ph * tpw_ + (size_t)ey * tpitch + ex;
+        part = part_full<R, SPLIT>(sc, Lt.swp, tc, win ? Lt.twp : tpitch, u);
       }
     }
     // sum over the candidate's SPLIT threads, then swap with the other candidate's
@@ -786,10 +785,10 @@ __device__ __forceinline__ void wide_tile(const SearchProblem &P, const PassCfg 
       const uint32_t *sc = S.src + (ly + R + 1) * Lt.swp + (lx + R + 1);
       const bool win = in_win(ph, ex, ey);
       if (counting) count_eval(scnt, true, win);
-      const int cost = win
-                           ? lane_full<R>(sc, Lt.swp, S.tgt + (ey - toy) * Lt.twp + (ex - tox), Lt.twp)
-                           : lane_full<R>(sc, Lt.swp, tbase + (size_t)ph * tpw_ + (size_t)ey * tpitch + ex,
-                                          tpitch);
+      // one call for both sources, so that a warp never runs the 289-tap loop twice
+      const uint32_t *tc = win ? S.tgt + (ey - toy) * Lt.twp + (ex - tox)
+                               : tbase + (size_t)ph * tpw_ + (size_t)ey * tpitch + ex;
+      const int cost = lane_full<R>(sc, Lt.swp, tc, win ? Lt.twp : tpitch);
       if (cost < cc) {
         S.flow[ly * T + lx] = cf;
         S.cost[ly * T + lx] = cost;
