@@ -477,7 +477,7 @@ __device__ void seg_digit(KdBuild &T, int d, int s) {
 // Level d's radix pass over the top digit: every position's key (gathered from
 // its feature row, cached in T.keys) counted in its segment's histogram; the last
 // chunk of a segment runs its digit step.
-__global__ void __launch_bounds__(256) k_kd_hist(KdBuild *trees, int d) {
+__global__ void __launch_bounds__(256, 5) k_kd_hist(KdBuild *trees, int d) {
   KdBuild &T = trees[blockIdx.y];
   if (d >= T.top_levels) return;
   const int start = blockIdx.x * KD_CHUNK;
@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(256) k_kd_collect(KdBuild *trees, int d) {
 constexpr int PART_ROUNDS = KD_CHUNK / 256;
 
 template <bool PACKED>
-__global__ void __launch_bounds__(256, 3) k_kd_partition(KdBuild *trees, int d) {
+__global__ void __launch_bounds__(256, 5) k_kd_partition(KdBuild *trees, int d) {
   KdBuild &T = trees[blockIdx.y];
   if (d >= T.top_levels) return;
   const int start = blockIdx.x * KD_CHUNK;
