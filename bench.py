@@ -365,7 +365,7 @@ def run_reference(args):
     cores = usable_cores()
     per_round = max(1, cores // 3)
     total = args.warmup + args.steps
-    pairs = [synth.pair_for_config(2, 1000 + i) for i in range(min(per_round, total))]
+    pairs = [synth.workload_pair("layers_1024x436", 1000 + i) for i in range(min(per_round, total))]
     done, times = 0, []
     while done < total:
         m = min(per_round, total - done)
@@ -491,7 +491,7 @@ def field_quality(dev, pairs=8, eps_list=(1, 2, 3, 4, 5, 6, 8, 10, 12, 15, 20)):
     acc = {"raw": [], "median": []}
     curves = {v: {e: [0, 0, 0, 0] for e in eps_list} for v in ("1x", "2x", "2x_region")}
     for i in range(pairs):
-        p = synth.pair_for_config(2, 4000 + i)
+        p = synth.workload_pair("layers_1024x436", 4000 + i)
         I1, I2 = torch.from_numpy(p["I1"]).to(dev), torch.from_numpy(p["I2"]).to(dev)
         out = ff.run(I1, I2)
         fl = out["flows"].clone()
@@ -527,15 +527,15 @@ def field_quality(dev, pairs=8, eps_list=(1, 2, 3, 4, 5, 6, 8, 10, 12, 15, 20)):
 
 def subpel_quality(dev, pairs=6):
     """Integer flows vs the subpixel random search (params.subpel = 2, 4: offsets and
-    target colours at 1/q pixel) on generated Sintel-shaped (config 2) and
-    KITTI-shaped (config 5) pairs: inliers@3px, EPE10 and EPE of the raw forward
+    target colours at 1/q pixel) on generated Sintel-shaped 1024x436 and
+    KITTI-shaped 1242x375 pairs: inliers@3px, EPE10 and EPE of the raw forward
     field on non-occluded pixels, and the device time per pair (direct call, median
     of 5)."""
     import torch
     from paper_1508_05151_gb300 import ffapi, synth
     out = {}
-    for cfg, name in ((2, "1024x436"), (5, "1242x375")):
-        ps = [synth.pair_for_config(cfg, 5000 + i) for i in range(pairs)]
+    for wl, name in (("layers_1024x436", "1024x436"), ("kitti_1242x375", "1242x375")):
+        ps = [synth.workload_pair(wl, 5000 + i) for i in range(pairs)]
         H_, W_ = ps[0]["I1"].shape[:2]
         frames = [(torch.from_numpy(p["I1"]).to(dev), torch.from_numpy(p["I2"]).to(dev)) for p in ps]
         res = {}
@@ -563,28 +563,29 @@ def subpel_quality(dev, pairs=6):
 
 
 LEARNED_WORKLOADS = {
-    2: ("1024x436", "Sintel-shaped 1024x436 pairs (3 textured layers, affine motion <= 200 px)"),
-    4: ("512x218", "512x218 pairs of the shifted-noise generator with an occluding square "
-                   "(the proposal-net training workload at its stated size)"),
-    5: ("1242x375", "KITTI-shaped 1242x375 pairs (radial expansion <= 300 px, sky band, moving "
-                    "boxes)"),
+    "layers_1024x436": ("1024x436", "Sintel-shaped 1024x436 pairs (3 textured layers, affine "
+                                    "motion <= 200 px)"),
+    "noise_512x218": ("512x218", "512x218 pairs of the shifted-noise generator with an occluding "
+                                 "square (the proposal-net training workload at its stated size)"),
+    "kitti_1242x375": ("1242x375", "KITTI-shaped 1242x375 pairs (radial expansion <= 300 px, sky "
+                                   "band, moving boxes)"),
 }
 
 
-def learned_measure(config, train_pairs=256, epochs=40, eval_pairs=32, batch=32,
+def learned_measure(workload, train_pairs=256, epochs=40, eval_pairs=32, batch=32,
                     eval_batch=32):
-    """Learned proposals vs plain search on one generated workload (config 2:
-    Sintel-shaped 1024x436; config 5: KITTI-shaped 1242x375).
+    """Learned proposals vs plain search on one generated workload (a name of
+    LEARNED_WORKLOADS).
 
     The net is trained here on `train_pairs` generated pairs of the workload,
     labelled by the plain search (seeds disjoint from the evaluation pairs), then
     both arms run on `eval_pairs` held-out pairs as batched CUDA-graph replays at
     random-search budgets n_rs = 1, 2, 3; the learned arm's time includes the net."""
     from paper_1508_05151_gb300 import train
-    net, info = train.train_for(config, train_pairs, epochs, batch=batch, seed=2000)
-    E1, E2, gt, occ = train.make_pairs(config, range(10**6, 10**6 + eval_pairs))
+    net, info = train.train_for(workload, train_pairs, epochs, batch=batch, seed=2000)
+    E1, E2, gt, occ = train.make_pairs(workload, range(10**6, 10**6 + eval_pairs))
     ev = train.evaluate(net, E1, E2, gt, occ, (1, 2, 3), batch=min(eval_pairs, eval_batch))
-    return {"workload": f"{eval_pairs} held-out {LEARNED_WORKLOADS[config][1]}, "
+    return {"workload": f"{eval_pairs} held-out {LEARNED_WORKLOADS[workload][1]}, "
                         f"{min(eval_pairs, eval_batch)} pairs per CUDA-graph replay",
             "train": info, "coarse_data_cost": ev["coarse"], "arms": ev["arms"],
             "equal_inliers": train.equal_inlier_point(ev),
@@ -636,7 +637,7 @@ def run_ours(args):
     def rank_max(x):
         return max_over_ranks(x, world, dev)
 
-    pairs = [synth.pair_for_config(2, sd) for sd in rank_pair_seeds(rank)]
+    pairs = [synth.workload_pair("layers_1024x436", sd) for sd in rank_pair_seeds(rank)]
     dI = [(torch.from_numpy(p["I1"]).to(dev), torch.from_numpy(p["I2"]).to(dev)) for p in pairs]
     flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
@@ -712,10 +713,10 @@ def run_ours(args):
     learned = {}
     if rank == 0 and not args.no_learned:
         # the training workload at its stated size: 4096 generated pairs, 256 held out
-        learned[4] = learned_measure(4, train_pairs=4096, epochs=10, eval_pairs=256, batch=64,
-                                     eval_batch=128)
-        for cfg in (2, 5):
-            learned[cfg] = learned_measure(cfg, eval_pairs=64 if cfg == 2 else 32)
+        learned["noise_512x218"] = learned_measure("noise_512x218", train_pairs=4096, epochs=10,
+                                                   eval_pairs=256, batch=64, eval_batch=128)
+        for wl in ("layers_1024x436", "kitti_1242x375"):
+            learned[wl] = learned_measure(wl, eval_pairs=64 if wl == "layers_1024x436" else 32)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -771,17 +772,17 @@ def run_ours(args):
         line["field_quality_1024x436"] = quality
     if subpel is not None:
         line["subpixel_search"] = subpel
-    for cfg, lm in learned.items():
+    for wl, lm in learned.items():
         eq = lm["equal_inliers"]
-        if cfg == 2 and eq is not None:
+        if wl == "layers_1024x436" and eq is not None:
             # the plain search as a single pair per graph replay (this line's value):
             # results do not depend on batching, so its inliers are plain_rs3's
             eq["headline_plain_ms_per_pair"] = round(value, 4)
             eq["speedup_vs_headline"] = round(value / eq["ms_per_pair"], 4)
-        line[f"learned_vs_plain_{LEARNED_WORKLOADS[cfg][0]}"] = lm
+        line[f"learned_vs_plain_{LEARNED_WORKLOADS[wl][0]}"] = lm
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(
-            lambda m: [synth.pair_for_config(2, 1000 + i) for i in range(m)], PARAMS)
+            lambda m: [synth.workload_pair("layers_1024x436", 1000 + i) for i in range(m)], PARAMS)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -796,7 +797,7 @@ def run_ncu_target(args):
     import torch
     from paper_1508_05151_gb300 import ffapi, synth
     dev = torch.device("cuda:0")
-    p = synth.pair_for_config(2, 1000)
+    p = synth.workload_pair("layers_1024x436", 1000)
     I1, I2 = torch.from_numpy(p["I1"]).to(dev), torch.from_numpy(p["I2"]).to(dev)
     ffapi.set_exec_params(serial_flows=1)
     ff = ffapi.FlowFields(W, H, PARAMS, dev)

@@ -21,7 +21,8 @@ __all__ = [
     "pair_shift",
     "pair_layers",
     "pair_kitti",
-    "pair_for_config",
+    "workload_pair",
+    "WORKLOADS",
     "mixed_batch",
     "BATCH_SIZES",
 ]
@@ -348,29 +349,32 @@ def pair_kitti(seed, W=1242, H=375, max_disp=300.0):
     return dict(I1=I1, I2=I2, flow=flow.astype(np.float32), occ=occ)
 
 
-def pair_for_config(config, seed, size=None):
-    """The pair generator for each evaluation workload.
+WORKLOADS = ("noise_128x96", "layers_1024x436", "mixed", "noise_512x218", "kitti_1242x375")
 
-    config 1: 128x96 shifted value noise with an occluding square.
-    config 2: 1024x436 three-layer affine scene.
-    config 3: a pair of the mixed-size batch; ``size`` = (W, H) from BATCH_SIZES,
-              shift bounds 0.2 W horizontally and 0.2 H vertically.
-    config 4: 512x218 shifted value noise (proposal-net training data).
-    config 5: 1242x375 ground plane with radial expansion.
+
+def workload_pair(workload, seed, size=None):
+    """A generated pair of one evaluation workload:
+
+    noise_128x96     128x96 shifted value noise with an occluding square;
+    layers_1024x436  Sintel-shaped 1024x436 three-layer affine scene;
+    mixed            a pair of the mixed-size batch, ``size`` = (W, H) from
+                     BATCH_SIZES, shift bounds 0.2 W horizontally, 0.2 H vertically;
+    noise_512x218    512x218 shifted value noise (proposal-net training data);
+    kitti_1242x375   KITTI-shaped 1242x375 ground plane with radial expansion.
     """
-    if config == 1:
+    if workload == "noise_128x96":
         return pair_shift(seed)
-    if config == 2:
+    if workload == "layers_1024x436":
         return pair_layers(seed)
-    if config == 3:
+    if workload == "mixed":
         W, H = size
         return pair_shift(seed, W=W, H=H,
                           max_shift=(int(round(0.2 * W)), int(round(0.2 * H))))
-    if config == 4:
+    if workload == "noise_512x218":
         return pair_shift(seed, W=512, H=218)
-    if config == 5:
+    if workload == "kitti_1242x375":
         return pair_kitti(seed)
-    raise ValueError(f"unknown config {config}")
+    raise ValueError(f"unknown workload {workload}")
 
 
 def mixed_batch(seed0=500, per_size=16):
@@ -380,5 +384,5 @@ def mixed_batch(seed0=500, per_size=16):
     out = []
     for k, (W, H) in enumerate(BATCH_SIZES):
         for i in range(per_size):
-            out.append(((W, H), pair_for_config(3, seed0 + 100 * k + i, (W, H))))
+            out.append(((W, H), workload_pair("mixed", seed0 + 100 * k + i, (W, H))))
     return out

@@ -30,19 +30,19 @@ FLOW_SCALE = 8.0   # net outputs are in units of grid cells (8 px)
 
 
 def _gen(args):
-    config, seed, size = args
-    p = synth.pair_for_config(config, seed, size)
+    workload, seed, size = args
+    p = synth.workload_pair(workload, seed, size)
     return p["I1"], p["I2"], p["flow"], p["occ"]
 
 
-def make_pairs(config, seeds, size=None, workers=None):
+def make_pairs(workload, seeds, size=None, workers=None):
     """Generate pairs of one workload with a spawn pool (safe after CUDA init).
 
     Returns (I1, I2, flow, occ) stacked over the seeds: uint8 [N][H][W][3] x2,
     flow [N][H][W][2] (the generator's ground truth), occ bool [N][H][W]."""
     seeds = list(seeds)
     workers = workers or min(len(seeds), os.cpu_count() or 1, 16)
-    args = [(config, s, size) for s in seeds]
+    args = [(workload, s, size) for s in seeds]
     if workers <= 1:
         res = [_gen(a) for a in args]
     else:
@@ -342,11 +342,11 @@ def level_budget_study(net, I1, I2, gt, occ, budgets, params=None, device="cuda"
     return out
 
 
-def train_for(config, n_train, epochs, batch=64, lr=2e-3, seed=1000, size=None, log=None):
+def train_for(workload, n_train, epochs, batch=64, lr=2e-3, seed=1000, size=None, log=None):
     """Generate pairs, label them with plain Flow Fields and train a net."""
     import time
     t0 = time.time()
-    I1, I2, _, _ = make_pairs(config, range(seed, seed + n_train), size)
+    I1, I2, _, _ = make_pairs(workload, range(seed, seed + n_train), size)
     t1 = time.time()
     label, valid = plain_labels(I1, I2)
     x = ffapi.ff_net_input(torch.from_numpy(I1).cuda(), torch.from_numpy(I2).cuda())
@@ -356,7 +356,7 @@ def train_for(config, n_train, epochs, batch=64, lr=2e-3, seed=1000, size=None, 
     losses = net.train(x, label, valid, epochs=epochs, batch=batch, lr=lr)
     torch.cuda.synchronize()
     t3 = time.time()
-    info = dict(config=config, pairs=n_train, epochs=epochs, batch=min(batch, n_train),
+    info = dict(workload=workload, pairs=n_train, epochs=epochs, batch=min(batch, n_train),
                 steps=len(losses), gen_s=round(t1 - t0, 2), label_s=round(t2 - t1, 2),
                 train_s=round(t3 - t2, 2), loss_first=round(float(losses[:10].mean()), 4),
                 loss_last=round(float(losses[-10:].mean()), 4))
@@ -367,7 +367,7 @@ def main(argv=None):
     import argparse
     import json
     ap = argparse.ArgumentParser(description="train the proposal net on plain-FF labels")
-    ap.add_argument("--config", type=int, default=4)
+    ap.add_argument("--workload", default="noise_512x218", choices=[w for w in synth.WORKLOADS if w != "mixed"])
     ap.add_argument("--train", type=int, default=4096)
     ap.add_argument("--eval", type=int, default=256)
     ap.add_argument("--epochs", type=int, default=10)
@@ -384,10 +384,10 @@ def main(argv=None):
     if a.load:
         net, info = ProposalNet.load(a.load), dict(loaded=a.load)
     else:
-        net, info = train_for(a.config, a.train, a.epochs, a.batch, a.lr, a.seed)
+        net, info = train_for(a.workload, a.train, a.epochs, a.batch, a.lr, a.seed)
     if a.save:
         net.save(a.save)
-    E1, E2, Egt, Eocc = make_pairs(a.config, range(a.seed + 10**6, a.seed + 10**6 + a.eval))
+    E1, E2, Egt, Eocc = make_pairs(a.workload, range(a.seed + 10**6, a.seed + 10**6 + a.eval))
     ev = evaluate(net, E1, E2, Egt, Eocc, tuple(int(v) for v in a.n_rs.split(",")))
     res = dict(train=info, eval=ev, equal_inliers=equal_inlier_point(ev))
     if a.level_budgets:

@@ -445,7 +445,7 @@ def test_hierarchy_removes_background_outliers(ffo):
     # than the coarse patches (radius 8n), so it is left out of this comparison.
     out = {0: [], 3: []}
     for seed in range(4):
-        p = synth.pair_for_config(1, 100 + seed)
+        p = synth.workload_pair("noise_128x96", 100 + seed)
         px, py = p["square_pos"]
         bg = ~p["occ"]
         bg[max(py - 8, 0):py + 40, max(px - 8, 0):px + 40] = False

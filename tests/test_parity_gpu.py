@@ -285,7 +285,7 @@ def test_search_level_from_state(W, H, n, r, tile):
 # ------------------------------------------------------------ A11 - A13 -------
 @pytest.mark.parametrize("seed", [1, 2])
 def test_consistency_filter(seed):
-    p = synth.pair_for_config(1, seed)
+    p = synth.workload_pair("noise_128x96", seed)
     ref = O.flow_fields(p["I1"], p["I2"])
     flows = ref["flows"].copy()
     rng = np.random.default_rng(seed)
@@ -322,7 +322,7 @@ def _compare(out, ref):
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
 def test_flow_fields_128x96(seed):
-    p = synth.pair_for_config(1, seed)
+    p = synth.workload_pair("noise_128x96", seed)
     params = dict(seed=seed)
     out = ffapi.ff_flow_fields(tg(p["I1"]), tg(p["I2"]), params)
     _compare(out, O.flow_fields(p["I1"], p["I2"], params=params))
@@ -341,13 +341,13 @@ def test_flow_fields_edge_shapes(W, H, params):
 
 def test_flow_fields_1024x436_full_size():
     # the benchmark workload, whole-field bit-exact comparison
-    p = synth.pair_for_config(2, 1)
+    p = synth.workload_pair("layers_1024x436", 1)
     out = ffapi.ff_flow_fields(tg(p["I1"]), tg(p["I2"]))
     _compare(out, O.flow_fields(p["I1"], p["I2"], threads=3))
 
 
 def test_flow_fields_is_deterministic_and_stream_independent():
-    p = synth.pair_for_config(1, 9)
+    p = synth.workload_pair("noise_128x96", 9)
     ff = ffapi.FlowFields(128, 96)
     a = {k: v.clone() for k, v in ff.run(tg(p["I1"]), tg(p["I2"])).items()}
     s = torch.cuda.Stream()
@@ -397,7 +397,7 @@ def test_flow_fields_with_proposals_kitti_full_size():
     bit-exact against the oracle given the same proposals. Two proposals are the
     rounded ground-truth flow (one jittered by a few pixels), so they often win the
     data term; two are random within +-300 px, so targets are clamped."""
-    p = synth.pair_for_config(5, 11)
+    p = synth.workload_pair("kitti_1242x375", 11)
     H, W = p["I1"].shape[:2]
     Gx, Gy = O.grid(W, H, 8)
     rng = np.random.default_rng(12)
@@ -454,7 +454,7 @@ def test_rgb_to_lab_every_colour():
 @pytest.mark.parametrize("seed", [4, 5])
 def test_flow_fields_lab_128x96(seed):
     """The whole path in CIELab (params.color = 1) against the oracle."""
-    p = synth.pair_for_config(1, seed)
+    p = synth.workload_pair("noise_128x96", seed)
     params = dict(color=1)
     out = ffapi.FlowFields(128, 96, params).run(tg(p["I1"]), tg(p["I2"]))
     torch.cuda.synchronize()
@@ -467,7 +467,7 @@ def test_weighted_median_field(rho):
     """ff_weighted_median against the oracle on the forward field of the whole
     path (128x96) and on a field with random outliers: flows and matching errors
     bit for bit."""
-    p = synth.pair_for_config(1, 8)
+    p = synth.workload_pair("noise_128x96", 8)
     out = ffapi.FlowFields(128, 96).run(tg(p["I1"]), tg(p["I2"]))
     F = out["flows"][0].clone()
     torch.cuda.synchronize()
@@ -491,7 +491,7 @@ def test_weighted_median_field(rho):
 def test_flow_fields_subpel_128x96(q):
     """The whole path with subpixel flows (params.subpel = q: interpolated target
     census, offsets and thresholds in 1/q pixel) against the oracle, bit for bit."""
-    p = synth.pair_for_config(1, 9)
+    p = synth.workload_pair("noise_128x96", 9)
     params = dict(subpel=q)
     out = ffapi.FlowFields(128, 96, params).run(tg(p["I1"]), tg(p["I2"]))
     torch.cuda.synchronize()
