@@ -282,10 +282,14 @@ def evaluate(net, I1, I2, gt, occ, n_rs_list=(1, 2, 3), params=None, batch=32,
     return out
 
 
-def equal_inlier_point(ev, ref="plain_rs3"):
+def equal_inlier_point(ev, ref=None):
     """The cheapest learned arm whose inliers@3px reach the reference arm's; None
-    if no learned budget reaches it."""
+    if no learned budget reaches it. The reference defaults to the plain arm with
+    the largest random-search budget evaluated."""
     arms = ev["arms"]
+    if ref is None:
+        plain = [k for k in arms if k.startswith("plain_rs")]
+        ref = max(plain, key=lambda k: int(k[len("plain_rs"):]))
     target = arms[ref]["inliers_3px"]
     ok = [(v["ms_per_pair"], k) for k, v in arms.items()
           if k.startswith("learned_") and v["inliers_3px"] >= target]

@@ -37,6 +37,14 @@ def test_equal_inlier_point_none_when_no_learned_arm_reaches_it():
     assert train.equal_inlier_point(ev) is None
 
 
+def test_equal_inlier_point_defaults_to_the_largest_plain_budget():
+    ev = _arms(plain_rs1=(3.0, 0.80), learned_rs1=(3.1, 0.81))
+    eq = train.equal_inlier_point(ev)
+    assert eq["ref"] == "plain_rs1" and eq["arm"] == "learned_rs1"
+    ev = _arms(plain_rs1=(3.0, 0.80), plain_rs12=(5.0, 0.95), learned_rs1=(3.1, 0.81))
+    assert train.equal_inlier_point(ev) is None
+
+
 def test_paired_inlier_delta():
     gt = np.zeros((3, 1, 4, 2))
     occ = np.zeros((3, 1, 4), bool)
