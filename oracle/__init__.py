@@ -102,6 +102,25 @@ def lib():
             L.ffo_sparsify.argtypes = [u8, i32, i32, i32, ci, ci, ci, i32, u8]
             L.ffo_flow_fields.argtypes = [u8, u8, ci, ci, C.POINTER(Params), i32, ci, i32, u8,
                                           i32, i32, u8, i64]
+            u64, i16 = C.POINTER(C.c_uint64), C.POINTER(C.c_int16)
+            L.ffo_isqrt.argtypes = [C.c_uint64]
+            L.ffo_isqrt.restype = C.c_uint64
+            L.ffo_sift_orient.argtypes = [u8, ci, ci, i32]
+            L.ffo_sift_descriptors.argtypes = [u8, ci, ci, u8]
+            L.ffo_sift_moments.argtypes = [u8, ci, u64, u64]
+            L.ffo_sift_pca_offset.argtypes = [i16, ci, u64, C.c_int64, i32]
+            L.ffo_sift_colors.argtypes = [u8, ci, ci, i16, i32, ci, u8]
+            L.ffo_sift_tap.argtypes = [u8, u8, ci, C.c_size_t, C.c_size_t, C.c_size_t]
+            L.ffo_sift_tap.restype = C.c_int32
+            L.ffo_sift_patch_cost.argtypes = [u8, u8, ci, ci, ci, ci, ci, ci, ci, ci, ci]
+            L.ffo_sift_patch_cost.restype = C.c_int32
+            L.ffo_sift_kd_init.argtypes = [i32, u8, ci, ci, ci, ci, u8, u8, ci, ci, i32, i32]
+            L.ffo_sift_kd_init.restype = C.c_int64
+            L.ffo_sift_search_level.argtypes = [u8, u8, ci, ci, ci, ci, ci, i32, ci, ci, ci,
+                                                C.c_uint64, ci, i32, i32]
+            L.ffo_sift_search_level.restype = C.c_int64
+            L.ffo_sift_flow_fields.argtypes = [u8, u8, ci, ci, C.POINTER(Params), i16, i32, ci,
+                                               i16, i32, ci, ci, i32, u8, i32, i32, u8, i64]
             _lib = L
     return _lib
 
@@ -392,5 +411,175 @@ def flow_fields(I1, I2, params=None, proposals=None, threads=3):
                               _p(pr, C.c_int32), threads, _p(flows, C.c_int32),
                               _p(valid, C.c_uint8), _p(err, C.c_int32), _p(sp, C.c_int32),
                               _p(mask, C.c_uint8), C.byref(ev))
+    return dict(flows=flows, valid=valid, err_sum=err, sparse=sp[:n].copy(), mask=mask,
+                evals=ev.value)
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.3, the SIFT flow data term (readings in ffo.c).
+
+SIFT_DIM = 128
+SIFT_SHIFT = 12  # basis components in units of 2^-12
+
+
+def isqrt(x):
+    return int(lib().ffo_isqrt(C.c_uint64(int(x))))
+
+
+def sift_orient(img):
+    """The 8 rectified orientation responses per pixel, (H, W, 8) int32."""
+    img = _c(img, np.uint8)
+    H, W = img.shape[:2]
+    out = np.empty((H, W, 8), np.int32)
+    lib().ffo_sift_orient(_p(img, C.c_uint8), W, H, _p(out, C.c_int32))
+    return out
+
+
+def sift_descriptors(img):
+    """Dense SIFT vectors, (H, W, 128) uint8."""
+    img = _c(img, np.uint8)
+    H, W = img.shape[:2]
+    out = np.empty((H, W, SIFT_DIM), np.uint8)
+    lib().ffo_sift_descriptors(_p(img, C.c_uint8), W, H, _p(out, C.c_uint8))
+    return out
+
+
+def sift_moments(desc, acc=None):
+    """Exact sums and Gram matrix of the descriptors (added to acc = (sum, gram)
+    when given). Returns (sum uint64 [128], gram uint64 [128, 128], count)."""
+    d = _c(desc, np.uint8).reshape(-1, SIFT_DIM)
+    if acc is None:
+        sm, gram, count = np.zeros(SIFT_DIM, np.uint64), np.zeros((SIFT_DIM, SIFT_DIM), np.uint64), 0
+    else:
+        sm, gram, count = acc[0].copy(), acc[1].copy(), acc[2]
+    lib().ffo_sift_moments(_p(d, C.c_uint8), d.shape[0], _p(sm, C.c_uint64), _p(gram, C.c_uint64))
+    return sm, gram, count + d.shape[0]
+
+
+def sift_pca(sm, gram, count, S):
+    """Sec. 3.3: PCA of the descriptors from their moments, reduced to S
+    dimensions and quantised. Readings: covariance C = gram / count - mu mu^T
+    (mu = sum / count) in float64; its eigenvectors by eigenvalue, largest first
+    (numpy's symmetric eigensolver), each signed so that its entry of largest
+    magnitude (lowest index on ties) is positive; one gain for all components,
+    g = 127 / (3 sqrt(max(lambda_1, 1))), so that distances between colours stay
+    proportional to distances between descriptors; B_si = clamp(floor(2^12 g e_si
+    + 1/2), -32767, 32767); offsets from ffo_sift_pca_offset. Returns dict(basis
+    int16 [S, 128], offset int32 [S], eigval float64 [128] (descending), exact
+    float64 [S, 128] = the unrounded 2^12 g e_si)."""
+    sm = np.asarray(sm, np.uint64)
+    gram = np.asarray(gram, np.uint64)
+    mu = sm.astype(np.float64) / count
+    Cm = gram.astype(np.float64) / count - np.outer(mu, mu)
+    w, V = np.linalg.eigh(Cm)
+    order = np.argsort(-w, kind="stable")
+    w, V = w[order], V[:, order]
+    E = V[:, :S].T.copy()
+    for s in range(S):
+        i = int(np.argmax(np.abs(E[s])))
+        if E[s, i] < 0:
+            E[s] = -E[s]
+    g = 127.0 / (3.0 * np.sqrt(max(float(w[0]), 1.0)))
+    exact = float(1 << SIFT_SHIFT) * g * E
+    B = np.clip(np.floor(exact + 0.5), -32767, 32767).astype(np.int16)
+    off = sift_pca_offset(B, sm, count)
+    return dict(basis=B, offset=off, eigval=w, exact=exact)
+
+
+def sift_pca_offset(B, sm, count):
+    B = _c(B, np.int16)
+    sm = _c(sm, np.uint64)
+    off = np.empty(B.shape[0], np.int32)
+    lib().ffo_sift_pca_offset(_p(B, C.c_int16), B.shape[0], _p(sm, C.c_uint64), int(count),
+                              _p(off, C.c_int32))
+    return off
+
+
+def sift_colors(desc, B, off):
+    """SIFT flow colours in S/3 groups: (S/3, H, W, 3) uint8."""
+    desc = _c(desc, np.uint8)
+    H, W = desc.shape[:2]
+    B, off = _c(B, np.int16), _c(off, np.int32)
+    S = B.shape[0]
+    out = np.empty((S // 3, H, W, 3), np.uint8)
+    lib().ffo_sift_colors(_p(desc, C.c_uint8), W, H, _p(B, C.c_int16), _p(off, C.c_int32), S,
+                          _p(out, C.c_uint8))
+    return out
+
+
+def sift_smooth(col, n):
+    """Each colour group smoothed like I^n (Sec. 3.2)."""
+    return np.stack([smooth(g, n) for g in col])
+
+
+def sift_tap(a, b):
+    """Distance of two colours given as length-S uint8 vectors."""
+    a, b = _c(a, np.uint8), _c(b, np.uint8)
+    S = a.shape[0]
+    ga = _c(a.reshape(S // 3, 1, 3), np.uint8)
+    gb = _c(b.reshape(S // 3, 1, 3), np.uint8)
+    return int(lib().ffo_sift_tap(_p(ga, C.c_uint8), _p(gb, C.c_uint8), S, 1, 0, 0))
+
+
+def sift_patch_cost(Ks, Kt, n, r, p1, p2):
+    Ks, Kt = _c(Ks, np.uint8), _c(Kt, np.uint8)
+    G, H, W = Ks.shape[:3]
+    return int(lib().ffo_sift_patch_cost(_p(Ks, C.c_uint8), _p(Kt, C.c_uint8), 3 * G, W, H, n, r,
+                                         p1[0], p1[1], p2[0], p2[1]))
+
+
+def sift_kd_init(tgt_feat, src_img, r, leaf, Ks, Kt, n):
+    """Top-level initialisation (Eq. 1/4) with the SIFT flow data term."""
+    src_img = _c(src_img, np.uint8)
+    H, W = src_img.shape[:2]
+    Gx, Gy = grid(W, H, n)
+    tgt_feat, Ks, Kt = _c(tgt_feat, np.int32), _c(Ks, np.uint8), _c(Kt, np.uint8)
+    flow = np.empty((Gy, Gx, 2), np.int32)
+    cost = np.empty((Gy, Gx), np.int32)
+    ev = lib().ffo_sift_kd_init(_p(tgt_feat, C.c_int32), _p(src_img, C.c_uint8), W, H, r, leaf,
+                                _p(Ks, C.c_uint8), _p(Kt, C.c_uint8), 3 * Ks.shape[0], n,
+                                _p(flow, C.c_int32), _p(cost, C.c_int32))
+    return flow, cost, int(ev)
+
+
+def sift_search_level(Ks, Kt, n, r, flow_coarse=None, flow=None, cost=None, tile=16, n_rs=3, R=1,
+                      seed=0, flow_id=0):
+    """One hierarchy level with the SIFT flow data term (as search_level)."""
+    Ks, Kt = _c(Ks, np.uint8), _c(Kt, np.uint8)
+    G, H, W = Ks.shape[:3]
+    Gx, Gy = grid(W, H, n)
+    if flow_coarse is not None:
+        fc = _c(flow_coarse, np.int32)
+        flow = np.empty((Gy, Gx, 2), np.int32)
+        cost = np.empty((Gy, Gx), np.int32)
+    else:
+        fc = None
+        flow = _c(flow, np.int32).copy()
+        cost = _c(cost, np.int32).copy()
+    ev = lib().ffo_sift_search_level(_p(Ks, C.c_uint8), _p(Kt, C.c_uint8), 3 * G, W, H, n, r,
+                                     _p(fc, C.c_int32), tile, n_rs, R, C.c_uint64(seed), flow_id,
+                                     _p(flow, C.c_int32), _p(cost, C.c_int32))
+    return flow, cost, int(ev)
+
+
+def sift_flow_fields(I1, I2, B1, off1, B2, off2, params=None, threads=3):
+    """Whole pipeline with the SIFT flow data term. Returns the dict of flow_fields."""
+    P = default_params(**(params or {}))
+    I1, I2 = _c(I1, np.uint8), _c(I2, np.uint8)
+    H, W = I1.shape[:2]
+    B1, B2 = _c(B1, np.int16), _c(B2, np.int16)
+    off1, off2 = _c(off1, np.int32), _c(off2, np.int32)
+    flows = np.empty((3, H, W, 2), np.int32)
+    valid = np.empty((H, W), np.uint8)
+    err = np.empty((H, W), np.int32)
+    sp = np.empty((((W + 2) // 3) * ((H + 2) // 3), 4), np.int32)
+    mask = np.empty((H, W), np.uint8)
+    ev = C.c_int64()
+    n = lib().ffo_sift_flow_fields(_p(I1, C.c_uint8), _p(I2, C.c_uint8), W, H,
+                                   C.byref(Params(**P)), _p(B1, C.c_int16), _p(off1, C.c_int32),
+                                   B1.shape[0], _p(B2, C.c_int16), _p(off2, C.c_int32),
+                                   B2.shape[0], threads, _p(flows, C.c_int32),
+                                   _p(valid, C.c_uint8), _p(err, C.c_int32), _p(sp, C.c_int32),
+                                   _p(mask, C.c_uint8), C.byref(ev))
     return dict(flows=flows, valid=valid, err_sum=err, sparse=sp[:n].copy(), mask=mask,
                 evals=ev.value)

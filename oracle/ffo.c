@@ -314,6 +314,170 @@ int32_t ffo_patch_cost(const uint32_t *Cs, const uint32_t *Ct, int W, int H, int
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 3.3, the second data term: SIFT flow. Every pixel gets a 128-D SIFT  */
+/* vector, reduced by PCA to S dimensions ("SIFT flow colours"); E_d is the  */
+/* L2 distance between colours, summed over the patch taps. The paper names  */
+/* the descriptor only; readings (all integer, so both sides agree exactly): */
+/*   grey      g = R + G + B of the input frame (0..765)                       */
+/*   gradient  gx = g(x+1, y) - g(x-1, y), gy = g(x, y+1) - g(x, y-1),         */
+/*             coordinates clamped                                           */
+/*   8 orientations: the half-wave rectified derivative along direction k*45  */
+/*             degrees (x right, y down): o_k = max(0, gx C_k + gy S_k), with */
+/*             (C_k, S_k) = 256 (cos, sin) rounded, 1/sqrt 2 -> 181/256       */
+/*   4 x 4 cells of SIFT_CELL x SIFT_CELL pixels: cell (i, j) of pixel p sums */
+/*             o_k over x in [px + (i-2) c, px + (i-1) c), y likewise with j, */
+/*             coordinates clamped (flat spatial weights)                     */
+/*   element   d = (4 j + i) * 8 + k                                          */
+/*   normalise Lowe's unit length, clip at 0.2, unit length again, x 512,     */
+/*             clamp 255, in integers: N2 = sum h^2, t = isqrt(N2 / 25),      */
+/*             h' = min(h, t), M2 = sum h'^2, q = min(255, isqrt(2^18 h'^2 /  */
+/*             M2)) (integer divisions); M2 = 0 gives q = 0                   */
+/* ------------------------------------------------------------------------ */
+#define SIFT_CELL 3
+#define SIFT_DIM 128
+
+static const int SIFT_C[8] = {256, 181, 0, -181, -256, -181, 0, 181};
+static const int SIFT_S[8] = {0, 181, 256, 181, 0, -181, -256, -181};
+
+/* floor(sqrt(x)) by bisection on the integers */
+static uint64_t isqrt_u64(uint64_t x) {
+  uint64_t lo = 0, hi = 1ull << 32; /* hi^2 > x for every x < 2^64 */
+  while (hi - lo > 1) {
+    uint64_t mid = lo + (hi - lo) / 2;
+    if ((unsigned __int128)mid * mid <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+uint64_t ffo_isqrt(uint64_t x) { return isqrt_u64(x); }
+
+static int grey_at(const uint8_t *img, int W, int H, int x, int y) {
+  const uint8_t *p = img + 3 * ((size_t)clampi(y, 0, H - 1) * W + clampi(x, 0, W - 1));
+  return p[0] + p[1] + p[2];
+}
+
+/* The 8 orientation responses at every pixel: o[(y W + x) 8 + k]. */
+void ffo_sift_orient(const uint8_t *img, int W, int H, int32_t *o) {
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++) {
+      int gx = grey_at(img, W, H, x + 1, y) - grey_at(img, W, H, x - 1, y);
+      int gy = grey_at(img, W, H, x, y + 1) - grey_at(img, W, H, x, y - 1);
+      for (int k = 0; k < 8; k++) {
+        int v = gx * SIFT_C[k] + gy * SIFT_S[k];
+        o[((size_t)y * W + x) * 8 + k] = v > 0 ? v : 0;
+      }
+    }
+}
+
+/* Dense SIFT: desc[(y W + x) 128 + d], uint8. */
+void ffo_sift_descriptors(const uint8_t *img, int W, int H, uint8_t *desc) {
+  size_t N = (size_t)W * H;
+  int32_t *o = malloc(sizeof(int32_t) * 8 * N);
+  ffo_sift_orient(img, W, H, o);
+  int64_t h[SIFT_DIM];
+  for (int py = 0; py < H; py++)
+    for (int px = 0; px < W; px++) {
+      for (int j = 0; j < 4; j++)
+        for (int i = 0; i < 4; i++)
+          for (int k = 0; k < 8; k++) {
+            int64_t acc = 0;
+            for (int v = (j - 2) * SIFT_CELL; v < (j - 1) * SIFT_CELL; v++)
+              for (int u = (i - 2) * SIFT_CELL; u < (i - 1) * SIFT_CELL; u++) {
+                int x = clampi(px + u, 0, W - 1), y = clampi(py + v, 0, H - 1);
+                acc += o[((size_t)y * W + x) * 8 + k];
+              }
+            h[(4 * j + i) * 8 + k] = acc;
+          }
+      uint64_t N2 = 0;
+      for (int d = 0; d < SIFT_DIM; d++) N2 += (uint64_t)(h[d] * h[d]);
+      uint64_t t = isqrt_u64(N2 / 25);
+      uint64_t M2 = 0;
+      for (int d = 0; d < SIFT_DIM; d++) {
+        if ((uint64_t)h[d] > t) h[d] = (int64_t)t;
+        M2 += (uint64_t)(h[d] * h[d]);
+      }
+      uint8_t *out = desc + ((size_t)py * W + px) * SIFT_DIM;
+      for (int d = 0; d < SIFT_DIM; d++) {
+        uint64_t qv = 0;
+        if (M2 > 0) qv = isqrt_u64(((uint64_t)(h[d] * h[d]) << 18) / M2);
+        out[d] = (uint8_t)(qv > 255 ? 255 : qv);
+      }
+    }
+  free(o);
+}
+
+/* PCA statistics of N descriptors, added to the outputs: sum[i] += sum of q_i,
+ * gram[i 128 + j] += sum of q_i q_j (exact). */
+void ffo_sift_moments(const uint8_t *desc, int N, uint64_t *sum, uint64_t *gram) {
+  for (int p = 0; p < N; p++) {
+    const uint8_t *q = desc + (size_t)p * SIFT_DIM;
+    for (int i = 0; i < SIFT_DIM; i++) {
+      sum[i] += q[i];
+      for (int j = 0; j < SIFT_DIM; j++) gram[i * SIFT_DIM + j] += (uint64_t)q[i] * q[j];
+    }
+  }
+}
+
+/* Centring offsets of a quantised basis B[S][128] (components in units of
+ * 2^-12): o_s = 2^11 - round(sum_i B_si mean_i), the rounding half up, exact
+ * from the integer sums of `count` descriptors. */
+void ffo_sift_pca_offset(const int16_t *B, int S, const uint64_t *sum, int64_t count,
+                         int32_t *off) {
+  for (int s = 0; s < S; s++) {
+    int64_t num = 0;
+    for (int i = 0; i < SIFT_DIM; i++) num += (int64_t)B[s * SIFT_DIM + i] * (int64_t)sum[i];
+    off[s] = (int32_t)(2048 - floor_div(2 * num + count, 2 * count));
+  }
+}
+
+/* SIFT flow colours: channel s of pixel p is clamp(128 + floor((sum_i B_si q_i
+ * + o_s) / 2^12), 0, 255). Stored in S/3 groups of three channels, each group an
+ * H x W x 3 image (so that each group smooths like a colour image, Sec. 3.2):
+ * col[(s/3) N 3 + p 3 + s%3]. */
+void ffo_sift_colors(const uint8_t *desc, int W, int H, const int16_t *B, const int32_t *off,
+                     int S, uint8_t *col) {
+  size_t N = (size_t)W * H;
+  for (size_t p = 0; p < N; p++) {
+    const uint8_t *q = desc + p * SIFT_DIM;
+    for (int s = 0; s < S; s++) {
+      int64_t acc = off[s];
+      for (int i = 0; i < SIFT_DIM; i++) acc += (int64_t)B[s * SIFT_DIM + i] * q[i];
+      int64_t v = 128 + floor_div(acc, 4096);
+      col[(size_t)(s / 3) * N * 3 + p * 3 + s % 3] = (uint8_t)(v < 0 ? 0 : (v > 255 ? 255 : v));
+    }
+  }
+}
+
+/* Distance of two SIFT flow colours: the Euclidean norm in fixed point with 4
+ * fractional bits, floor(16 sqrt(sum (a_s - b_s)^2)). */
+int32_t ffo_sift_tap(const uint8_t *Ks, const uint8_t *Kt, int S, size_t N, size_t ps,
+                     size_t pt) {
+  uint64_t acc = 0;
+  for (int s = 0; s < S; s++) {
+    size_t g = (size_t)(s / 3) * N * 3;
+    int d = (int)Ks[g + ps * 3 + s % 3] - (int)Kt[g + pt * 3 + s % 3];
+    acc += (uint64_t)(d * d);
+  }
+  return (int32_t)isqrt_u64(acc * 256);
+}
+
+/* E_d with the SIFT flow data term: the tap distances over the (2r+1)^2 taps of
+ * P^n_r (Eq. 3) of the level-n colours, each tap clamped into the image. */
+int32_t ffo_sift_patch_cost(const uint8_t *Ks, const uint8_t *Kt, int S, int W, int H, int n,
+                            int r, int x1, int y1, int x2, int y2) {
+  int32_t e = 0;
+  size_t N = (size_t)W * H;
+  for (int v = -r; v <= r; v++)
+    for (int u = -r; u <= r; u++) {
+      int xs = clampi(x1 + n * u, 0, W - 1), ys = clampi(y1 + n * v, 0, H - 1);
+      int xt = clampi(x2 + n * u, 0, W - 1), yt = clampi(y2 + n * v, 0, H - 1);
+      e += ffo_sift_tap(Ks, Kt, S, N, (size_t)ys * W + xs, (size_t)yt * W + xt);
+    }
+  return e;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sec. 3.1: Walsh-Hadamard patch features.                                 */
 /* Reading: the window of L = 2r+1 pixels is split into halves floor(L/2),  */
 /* ceil(L/2) (the paper's uneven r / r+1 split), and each half the same way,*/
@@ -487,6 +651,9 @@ typedef struct {
   const uint32_t *const *Ct; /* target census per subpixel phase b * q + a */
   int W, H, n, r, q;
   int64_t evals;
+  /* S > 0: the SIFT flow data term on the level-n colours Ks, Kt (q = 1) */
+  const uint8_t *Ks, *Kt;
+  int S;
 } level_ctx;
 
 /* Flows are in units of 1/q pixel (q = 1: pixels). The target X = q px + fx is
@@ -495,8 +662,13 @@ static void try_candidate(level_ctx *L, int px, int py, int fx, int fy, int32_t 
                           int32_t *cost) {
   int q = L->q;
   int X = clampi(q * px + fx, 0, q * (L->W - 1)), Y = clampi(q * py + fy, 0, q * (L->H - 1));
-  const uint32_t *Ct = L->Ct[(Y % q) * q + X % q];
-  int32_t e = ffo_patch_cost(L->Cs, Ct, L->W, L->H, L->n, L->r, px, py, X / q, Y / q);
+  int32_t e;
+  if (L->S > 0) {
+    e = ffo_sift_patch_cost(L->Ks, L->Kt, L->S, L->W, L->H, L->n, L->r, px, py, X, Y);
+  } else {
+    const uint32_t *Ct = L->Ct[(Y % q) * q + X % q];
+    e = ffo_patch_cost(L->Cs, Ct, L->W, L->H, L->n, L->r, px, py, X / q, Y / q);
+  }
   L->evals++;
   if (e < *cost) {
     *cost = e;
@@ -513,20 +685,23 @@ static void try_candidate(level_ctx *L, int px, int py, int fx, int fy, int32_t 
  * tgt_feat: features of every target pixel; the tree is built here. */
 static int64_t kd_init_q(const int32_t *tgt_feat, const uint8_t *src_img, int W, int H, int r,
                          int leaf, const uint32_t *Cs, const uint32_t *const *Ct, int q, int n,
-                         const int32_t *proposals, int K, int32_t *flow, int32_t *cost);
+                         const int32_t *proposals, int K, int32_t *flow, int32_t *cost,
+                         const uint8_t *Ks, const uint8_t *Kt, int S);
 
 int64_t ffo_kd_init(const int32_t *tgt_feat, const uint8_t *src_img, int W, int H, int r,
                     int leaf, const uint32_t *Cs, const uint32_t *Ct, int n,
                     const int32_t *proposals, int K, int32_t *flow, int32_t *cost) {
   const uint32_t *Ct1[1] = {Ct};
-  return kd_init_q(tgt_feat, src_img, W, H, r, leaf, Cs, Ct1, 1, n, proposals, K, flow, cost);
+  return kd_init_q(tgt_feat, src_img, W, H, r, leaf, Cs, Ct1, 1, n, proposals, K, flow, cost,
+                   NULL, NULL, 0);
 }
 
 /* With subpel q the leaf pixels and the proposals (in pixels) become flows of
  * q (x2 - px) in 1/q pixel units. */
 static int64_t kd_init_q(const int32_t *tgt_feat, const uint8_t *src_img, int W, int H, int r,
                          int leaf, const uint32_t *Cs, const uint32_t *const *Ct, int q, int n,
-                         const int32_t *proposals, int K, int32_t *flow, int32_t *cost) {
+                         const int32_t *proposals, int K, int32_t *flow, int32_t *cost,
+                         const uint8_t *Ks, const uint8_t *Kt, int S) {
   int N = W * H, Gx = (W + n - 1) / n, Gy = (H + n - 1) / n, G = Gx * Gy;
   int D = ffo_kd_depth(N, leaf);
   int32_t *perm = malloc(sizeof(int32_t) * N);
@@ -540,7 +715,7 @@ static int64_t kd_init_q(const int32_t *tgt_feat, const uint8_t *src_img, int W,
     pts[2 * g + 1] = (g / Gx) * n;
   }
   ffo_wht_features(src_img, W, H, r, pts, G, qf);
-  level_ctx L = {Cs, Ct, W, H, n, r, q, 0};
+  level_ctx L = {Cs, Ct, W, H, n, r, q, 0, Ks, Kt, S};
   for (int g = 0; g < G; g++) {
     int px = pts[2 * g], py = pts[2 * g + 1];
     int lf = ffo_kd_query(sd, sv, D, qf + (size_t)g * NFEAT);
@@ -709,8 +884,9 @@ static void seed_level(level_ctx *L, const int32_t *flow_coarse, int32_t *flow, 
  * evaluations (no candidate is skipped here). */
 static int64_t search_level_q(const uint32_t *Cs, const uint32_t *const *Ct, int q, int W, int H,
                               int n, int r, const int32_t *flow_coarse, int tile, int n_rs, int R,
-                              uint64_t seed, int flow_id, int32_t *flow, int32_t *cost) {
-  level_ctx L = {Cs, Ct, W, H, n, r, q, 0};
+                              uint64_t seed, int flow_id, int32_t *flow, int32_t *cost,
+                              const uint8_t *Ks, const uint8_t *Kt, int S) {
+  level_ctx L = {Cs, Ct, W, H, n, r, q, 0, Ks, Kt, S};
   int level = 0;
   while ((1 << level) < n) level++;
   if (flow_coarse) seed_level(&L, flow_coarse, flow, cost);
@@ -726,7 +902,7 @@ int64_t ffo_search_level(const uint32_t *Cs, const uint32_t *Ct, int W, int H, i
                          int flow_id, int32_t *flow, int32_t *cost) {
   const uint32_t *Ct1[1] = {Ct};
   return search_level_q(Cs, Ct1, 1, W, H, n, r, flow_coarse, tile, n_rs, R, seed, flow_id, flow,
-                        cost);
+                        cost, NULL, NULL, 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -968,6 +1144,9 @@ typedef struct {
   const int32_t *proposals;
   int32_t *flow_out; /* [H][W][2] */
   int64_t evals;
+  /* S > 0: the SIFT flow data term, level-lv colours Ks[lv] (source) and Kt[lv] */
+  uint8_t **Ks, **Kt;
+  int S;
 } flow_job;
 
 static void *run_flow(void *arg) {
@@ -980,19 +1159,23 @@ static void *run_flow(void *arg) {
   int32_t *flow = malloc(sizeof(int32_t) * 2 * (size_t)Gx * Gy);
   int32_t *cost = malloc(sizeof(int32_t) * (size_t)Gx * Gy);
   int q = P->subpel;
-  J->evals = kd_init_q(tf, J->src, W, H, J->r, P->leaf, J->Cs[P->k],
-                       (const uint32_t *const *)J->Ct[P->k], q, ntop, J->proposals,
-                       J->proposals ? P->K : 0, flow, cost);
+  int S = J->S;
+  J->evals = kd_init_q(tf, J->src, W, H, J->r, P->leaf, S ? NULL : J->Cs[P->k],
+                       S ? NULL : (const uint32_t *const *)J->Ct[P->k], q, ntop, J->proposals,
+                       J->proposals ? P->K : 0, flow, cost, S ? J->Ks[P->k] : NULL,
+                       S ? J->Kt[P->k] : NULL, S);
   free(tf);
-  J->evals += search_level_q(J->Cs[P->k], (const uint32_t *const *)J->Ct[P->k], q, W, H, ntop,
-                             J->r, NULL, P->tile, P->n_rs, P->R, P->seed, J->flow_id, flow, cost);
+  J->evals += search_level_q(S ? NULL : J->Cs[P->k], S ? NULL : (const uint32_t *const *)J->Ct[P->k],
+                             q, W, H, ntop, J->r, NULL, P->tile, P->n_rs, P->R, P->seed, J->flow_id,
+                             flow, cost, S ? J->Ks[P->k] : NULL, S ? J->Kt[P->k] : NULL, S);
   for (int lv = P->k - 1; lv >= 0; lv--) {
     int n = 1 << lv;
     int gx = (W + n - 1) / n, gy = (H + n - 1) / n;
     int32_t *f2 = malloc(sizeof(int32_t) * 2 * (size_t)gx * gy);
     int32_t *c2 = malloc(sizeof(int32_t) * (size_t)gx * gy);
-    J->evals += search_level_q(J->Cs[lv], (const uint32_t *const *)J->Ct[lv], q, W, H, n, J->r,
-                               flow, P->tile, P->n_rs, P->R, P->seed, J->flow_id, f2, c2);
+    J->evals += search_level_q(S ? NULL : J->Cs[lv], S ? NULL : (const uint32_t *const *)J->Ct[lv],
+                               q, W, H, n, J->r, flow, P->tile, P->n_rs, P->R, P->seed, J->flow_id,
+                               f2, c2, S ? J->Ks[lv] : NULL, S ? J->Kt[lv] : NULL, S);
     free(flow);
     free(cost);
     flow = f2;
@@ -1048,9 +1231,9 @@ int ffo_flow_fields(const uint8_t *I1_in, const uint8_t *I2_in, int W, int H,
   }
   free(sm);
   flow_job J[3] = {
-      {I1, I2, C1s, C2, W, H, P->r, 0, P, proposals, flows, 0},
-      {I2, I1, C2s, C1, W, H, P->r, 1, P, NULL, flows + 2 * N, 0},
-      {I2, I1, C2s, C1, W, H, P->r2, 2, P, NULL, flows + 4 * N, 0},
+      {I1, I2, C1s, C2, W, H, P->r, 0, P, proposals, flows, 0, NULL, NULL, 0},
+      {I2, I1, C2s, C1, W, H, P->r, 1, P, NULL, flows + 2 * N, 0, NULL, NULL, 0},
+      {I2, I1, C2s, C1, W, H, P->r2, 2, P, NULL, flows + 4 * N, 0, NULL, NULL, 0},
   };
   if (threads > 1) {
     pthread_t th[3];
@@ -1068,6 +1251,104 @@ int ffo_flow_fields(const uint8_t *I1_in, const uint8_t *I2_in, int W, int H,
   int32_t *e1 = malloc(sizeof(int32_t) * N), *e2 = malloc(sizeof(int32_t) * N);
   ffo_consistency(flows, flows + 2 * N, flows + 4 * N, W, H, P->eps, q, vcc, err_sum, e1, e2);
   ffo_region_filter(flows, vcc, W, H, P->s, q, valid);
+  free(vcc);
+  if (evals) *evals = J[0].evals + J[1].evals + J[2].evals;
+  int n = ffo_sparsify(valid, e1, e2, flows, W, H, P->e, sparse, mask);
+  free(e1);
+  free(e2);
+  free(lab1);
+  free(lab2);
+  return n;
+}
+
+/* Level search and kd initialisation with the SIFT flow data term (Sec. 3.3):
+ * the census steps above with E_d on the level-n colours Ks (source frame) and
+ * Kt (target frame), S channels in S/3 groups (ffo_sift_colors), q = 1. */
+int64_t ffo_sift_kd_init(const int32_t *tgt_feat, const uint8_t *src_img, int W, int H, int r,
+                         int leaf, const uint8_t *Ks, const uint8_t *Kt, int S, int n,
+                         int32_t *flow, int32_t *cost) {
+  return kd_init_q(tgt_feat, src_img, W, H, r, leaf, NULL, NULL, 1, n, NULL, 0, flow, cost, Ks,
+                   Kt, S);
+}
+
+int64_t ffo_sift_search_level(const uint8_t *Ks, const uint8_t *Kt, int S, int W, int H, int n,
+                              int r, const int32_t *flow_coarse, int tile, int n_rs, int R,
+                              uint64_t seed, int flow_id, int32_t *flow, int32_t *cost) {
+  return search_level_q(NULL, NULL, 1, W, H, n, r, flow_coarse, tile, n_rs, R, seed, flow_id, flow,
+                        cost, Ks, Kt, S);
+}
+
+/* The whole path with the SIFT flow data term (Sec. 3.3, Sec. 5 KITTI): SIFT
+ * vectors of both input frames; colours with basis B1 (S1 channels) for the
+ * forward and first backward flow, with B2 (S2 channels) for the second
+ * backward flow (radius r2); per level the colour groups smoothed like I^n
+ * (Sec. 3.2); the kd trees over WHT features as in ffo_flow_fields (CIELab
+ * when P->color = 1); then the same consistency check, region filter and
+ * sparsification. P->subpel and P->K are ignored (integer flows, no proposals).
+ * B*: int16 [S][128], off*: int32 [S] (ffo_sift_pca_offset). Outputs as
+ * ffo_flow_fields. */
+int ffo_sift_flow_fields(const uint8_t *I1_in, const uint8_t *I2_in, int W, int H,
+                         const ffo_params *P, const int16_t *B1, const int32_t *off1, int S1,
+                         const int16_t *B2, const int32_t *off2, int S2, int threads,
+                         int32_t *flows, uint8_t *valid, int32_t *err_sum, int32_t *sparse,
+                         uint8_t *mask, int64_t *evals) {
+  size_t N = (size_t)W * H;
+  uint8_t *lab1 = NULL, *lab2 = NULL;
+  const uint8_t *I1 = I1_in, *I2 = I2_in;
+  if (P->color == 1) {
+    lab1 = malloc(N * 3);
+    lab2 = malloc(N * 3);
+    ffo_rgb_to_lab(I1_in, W, H, lab1);
+    ffo_rgb_to_lab(I2_in, W, H, lab2);
+    I1 = lab1;
+    I2 = lab2;
+  }
+  int nl = P->k + 1;
+  uint8_t *d1 = malloc(N * SIFT_DIM), *d2 = malloc(N * SIFT_DIM);
+  ffo_sift_descriptors(I1_in, W, H, d1);
+  ffo_sift_descriptors(I2_in, W, H, d2);
+  /* colours [set][frame][level]: set 0 = (B1, S1), set 1 = (B2, S2) */
+  uint8_t *K[2][2][16];
+  const int16_t *Bs[2] = {B1, B2};
+  const int32_t *offs[2] = {off1, off2};
+  int Ss[2] = {S1, S2};
+  for (int c = 0; c < 2; c++)
+    for (int f = 0; f < 2; f++) {
+      size_t bytes = N * (size_t)Ss[c];
+      uint8_t *full = malloc(bytes);
+      ffo_sift_colors(f == 0 ? d1 : d2, W, H, Bs[c], offs[c], Ss[c], full);
+      for (int lv = 0; lv < nl; lv++) {
+        K[c][f][lv] = malloc(bytes);
+        for (int g = 0; g < Ss[c] / 3; g++)
+          ffo_smooth(full + (size_t)g * N * 3, W, H, 1 << lv, K[c][f][lv] + (size_t)g * N * 3);
+      }
+      free(full);
+    }
+  free(d1);
+  free(d2);
+  flow_job J[3] = {
+      {I1, I2, NULL, NULL, W, H, P->r, 0, P, NULL, flows, 0, K[0][0], K[0][1], S1},
+      {I2, I1, NULL, NULL, W, H, P->r, 1, P, NULL, flows + 2 * N, 0, K[0][1], K[0][0], S1},
+      {I2, I1, NULL, NULL, W, H, P->r2, 2, P, NULL, flows + 4 * N, 0, K[1][1], K[1][0], S2},
+  };
+  ffo_params P1 = *P;
+  P1.subpel = 1;
+  P1.K = 0;
+  for (int i = 0; i < 3; i++) J[i].P = &P1;
+  if (threads > 1) {
+    pthread_t th[3];
+    for (int i = 0; i < 3; i++) pthread_create(&th[i], NULL, run_flow, &J[i]);
+    for (int i = 0; i < 3; i++) pthread_join(th[i], NULL);
+  } else {
+    for (int i = 0; i < 3; i++) run_flow(&J[i]);
+  }
+  for (int c = 0; c < 2; c++)
+    for (int f = 0; f < 2; f++)
+      for (int lv = 0; lv < nl; lv++) free(K[c][f][lv]);
+  uint8_t *vcc = malloc(N);
+  int32_t *e1 = malloc(sizeof(int32_t) * N), *e2 = malloc(sizeof(int32_t) * N);
+  ffo_consistency(flows, flows + 2 * N, flows + 4 * N, W, H, P->eps, 1, vcc, err_sum, e1, e2);
+  ffo_region_filter(flows, vcc, W, H, P->s, 1, valid);
   free(vcc);
   if (evals) *evals = J[0].evals + J[1].evals + J[2].evals;
   int n = ffo_sparsify(valid, e1, e2, flows, W, H, P->e, sparse, mask);
