@@ -238,6 +238,90 @@ ff_status ff_weighted_median(const uint8_t *I1, const uint8_t *I2, const int16_t
                              int H, int r, int rho, int16_t *out, int32_t *match_err, void *ws,
                              size_t ws_bytes, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Sec. 3.3, the second data term: SIFT flow (used by the paper for KITTI, Sec. 5,
+ * with r = 3, r2 = 2 and S = 12, S2 = 18 colour channels). Each pixel gets a
+ * 128-D SIFT vector, reduced by PCA to S "SIFT flow colours"; E_d sums the L2
+ * distance of the colours over the patch taps; the images I^n are the colours
+ * smoothed like the frames (Sec. 3.2). The paper names the descriptor only; the
+ * library's reading, exact in integers:
+ *   - grey g = R + G + B; gx = g(x+1, y) - g(x-1, y), gy likewise (clamped);
+ *   - 8 orientations: o_k = max(0, gx C_k + gy S_k), (C_k, S_k) = 256 (cos, sin)
+ *     of k * 45 degrees (x right, y down), 1/sqrt 2 as 181/256;
+ *   - 4 x 4 cells of 3 x 3 pixels: cell (i, j) sums o_k over x in
+ *     [px + 3 (i - 2), px + 3 (i - 1)), y likewise with j (clamped); element
+ *     d = (4 j + i) 8 + k;
+ *   - normalisation (unit length, clip at 0.2, unit length, x 512, clamp 255) in
+ *     integers: N2 = sum h^2, t = isqrt(N2 / 25), h' = min(h, t), M2 = sum h'^2,
+ *     q = min(255, isqrt(2^18 h'^2 / M2)), 0 when M2 = 0.
+ * ------------------------------------------------------------------------- */
+
+/* Dense SIFT vectors of an RGB frame. img: H x W x 3; desc: uint8 [H][W][128]
+ * (16-byte aligned). */
+ff_status ff_sift_descriptors(const uint8_t *img, int W, int H, uint8_t *desc, void *stream);
+
+/* PCA statistics of N descriptors (desc: uint8 [N][128], 16-byte aligned), ADDED
+ * to sum (uint64 [128]: sum of q_i) and gram (uint64 [128][128]: sum of q_i q_j),
+ * exactly; the caller zeroes them before the first call. N < 2^31. */
+ff_status ff_sift_moments(const uint8_t *desc, int N, uint64_t *sum, uint64_t *gram,
+                          void *stream);
+
+/* The PCA basis of Sec. 3.3 from the statistics of `count` descriptors (count is a
+ * host value). Covariance C = gram / count - mu mu^T in float64 (mu = sum / count);
+ * its eigenvectors by cyclic Jacobi rotations (round-robin order), sorted by
+ * eigenvalue, largest first (ties: lower index), each signed so that its entry
+ * of largest magnitude (lowest index on ties) is positive. One gain for all
+ * components, g = 127 / (3 sqrt(max(lambda_1, 1))), keeps colour distances
+ * proportional to descriptor distances. Outputs (device): basis int16 [S][128],
+ * B_si = clamp(floor(4096 g e_si + 1/2), -32767, 32767); offset int32 [S],
+ * o_s = 2048 - round_half_up(sum_i B_si sum_i / count) (exact); eigval float64
+ * [128] (descending; may be NULL). S is 3..30, a multiple of 3. Device status 3
+ * (ff_device_status) if the rotations have not converged after 40 sweeps.
+ * ws: ff_sift_pca_workspace_size. */
+ff_status ff_sift_pca_workspace_size(size_t *bytes);
+ff_status ff_sift_pca(const uint64_t *sum, const uint64_t *gram, int64_t count, int S,
+                      int16_t *basis, int32_t *offset, double *eigval, void *ws, size_t ws_bytes,
+                      void *stream);
+
+/* SIFT flow colours: channel s of pixel p is clamp(128 + floor((sum_i B_si q_i +
+ * o_s) / 4096), 0, 255), stored in S/3 groups of three channels, each group an
+ * H x W x 3 image: colors[(s/3)][y][x][s%3] (so ff_smooth gives I^n per group).
+ * desc: uint8 [H][W][128]; basis, offset as ff_sift_pca writes them. */
+ff_status ff_sift_colors(const uint8_t *desc, int W, int H, const int16_t *basis,
+                         const int32_t *offset, int S, uint8_t *colors, void *stream);
+
+/* The kd initialisation (as ff_kdtree_init, K = 0) and one hierarchy level (as
+ * ff_search_level) with the SIFT flow data term: E_d = sum over the (2r+1)^2
+ * taps of P^n_r (clamped) of floor(16 |c_src - c_tgt|_2), the colours taken
+ * from colors_src / colors_tgt (level-n colour groups, S/3 x H x W x 3, as
+ * ff_sift_colors writes them after ff_smooth per group). The kd tree is built
+ * over WHT features as for the census path. ws: ff_sift_level_workspace_size. */
+ff_status ff_sift_level_workspace_size(int W, int H, int n, int S, size_t *bytes);
+ff_status ff_sift_kdtree_init(const int32_t *perm, const int32_t *split_dim,
+                              const int32_t *split_val, int leaf, const uint8_t *src_img,
+                              const uint8_t *colors_src, const uint8_t *colors_tgt, int S, int W,
+                              int H, int n, int r, int16_t *flow, int32_t *cost, void *ws,
+                              size_t ws_bytes, void *stream);
+ff_status ff_sift_search_level(const uint8_t *colors_src, const uint8_t *colors_tgt, int S, int W,
+                               int H, int n, int r, const int16_t *flow_coarse, const ff_params *p,
+                               int flow_id, int16_t *flow, int32_t *cost, void *ws,
+                               size_t ws_bytes, void *stream);
+
+/* The whole path of ff_flow_fields with the SIFT flow data term: SIFT vectors of
+ * both input frames; colours with (basis1, offset1, S1) for the forward and the
+ * first backward flow and with (basis2, offset2, S2) for the second backward
+ * flow (radius r2); per level every colour group smoothed like I^n; kd trees over
+ * WHT features (CIELab when p->color = 1); then ff_consistency_filter. Integer
+ * flows only (p->subpel must be 1) and no proposals (p->K is ignored). Outputs as
+ * ff_flow_fields. ws: ff_sift_workspace_size. */
+ff_status ff_sift_workspace_size(int W, int H, const ff_params *p, int S1, int S2, size_t *bytes);
+ff_status ff_sift_flow_fields(const uint8_t *I1, const uint8_t *I2, int W, int H,
+                              const ff_params *p, const int16_t *basis1, const int32_t *offset1,
+                              int S1, const int16_t *basis2, const int32_t *offset2, int S2,
+                              int16_t *flows, uint8_t *valid, int32_t *err_sum, int32_t *sparse,
+                              int32_t *n_sparse, uint8_t *mask, void *ws, size_t ws_bytes,
+                              void *stream);
+
 /* The whole path for one pair (Fig. 2): smoothed images and census for both
  * frames at every level, three flow fields (forward I1->I2 with r, backward
  * I2->I1 with r and with r2; flow ids 0, 1, 2), each from its own kd tree, then

@@ -93,7 +93,6 @@ enum { MK_START = 0, MK_PYRAMID = 1, MK_FEATURES = 2, MK_KD_BUILD = 3, MK_KD_QUE
        MK_LEVEL = 10, MK_JOINED = 20, MK_FILTER = 21 };
 
 // ------------------------------------------------------------ checks --------
-static bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 ff_status check_params(const ff_params *p) {
   if (!p) return FF_ERR_INVALID_ARG;
@@ -133,19 +132,8 @@ ff_status smem_opt_in(const void *func, size_t bytes) {
   return FF_OK;
 }
 
-static bool pow2_upto(int n, int hi) { return n >= 1 && n <= hi && (n & (n - 1)) == 0; }
 
-static ff_status check_ws(void *ws, size_t have, size_t need) {
-  if (need == 0) return FF_OK;
-  if (!ws || !aligned(ws, 256)) return FF_ERR_WORKSPACE;
-  if (have < need) return FF_ERR_WORKSPACE;
-  return FF_OK;
-}
 
-static ff_status clear_status(void *ws, cudaStream_t st) {
-  if (cudaMemsetAsync(ws, 0, sizeof(DeviceStatus), st) != cudaSuccess) return FF_ERR_CUDA;
-  return FF_OK;
-}
 
 // ------------------------------------------------------------ pair plan ------
 constexpr int MAXLV = 5;

@@ -308,6 +308,20 @@ struct Arena {
 // Parameter and image-shape checks shared by every entry point.
 ff_status check_params(const ff_params *p);
 ff_status check_shape(int W, int H);
+inline bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+inline bool pow2_upto(int n, int hi) { return n >= 1 && n <= hi && (n & (n - 1)) == 0; }
+// The caller's workspace: present, 256-byte aligned and at least `need` bytes.
+inline ff_status check_ws(void *ws, size_t have, size_t need) {
+  if (need == 0) return FF_OK;
+  if (!ws || !aligned(ws, 256)) return FF_ERR_WORKSPACE;
+  if (have < need) return FF_ERR_WORKSPACE;
+  return FF_OK;
+}
+// Zeroes the device status word at the start of the workspace.
+inline ff_status clear_status(void *ws, cudaStream_t st) {
+  if (cudaMemsetAsync(ws, 0, sizeof(DeviceStatus), st) != cudaSuccess) return FF_ERR_CUDA;
+  return FF_OK;
+}
 
 // Raises `func`'s dynamic shared-memory limit to at least `bytes` on the current
 // device. The setting is per device and per kernel; it is remembered per
@@ -427,6 +441,19 @@ struct KdQuery {
   DeviceStatus *status;  // DEV_ERR_BOUNDS: a split dimension or leaf entry out of range
 };
 ff_status launch_kd_query(const KdQuery *q, KdQuery *dev_desc, int nq, cudaStream_t st);
+
+// Start of segment i of depth d when [0, N) is halved d times, the left half
+// taking floor(m/2) (the kd tree's leaf ranges).
+__host__ __device__ __forceinline__ int seg_begin(int N, int d, int i) {
+  if (i >= (1 << d)) return N;
+  int b = 0, e = N;
+  for (int k = d - 1; k >= 0; k--) {
+    int half = (e - b) >> 1;
+    if ((i >> k) & 1) b += half;
+    else e = b + half;
+  }
+  return b;
+}
 
 // -------------------------------------------------------------- search -------
 struct SearchProblem {

@@ -94,17 +94,6 @@ void kd_bind_scratch(KdBuild &b, Arena &a) {
   b.coll = a.take<unsigned long long>(T > 0 ? n1 : 1);
 }
 
-// Offsets of segment i at depth d (i in [0, 2^d]) by halving along i's bits.
-__device__ __forceinline__ int seg_begin(int N, int d, int i) {
-  if (i >= (1 << d)) return N;
-  int b = 0, e = N;
-  for (int k = d - 1; k >= 0; k--) {
-    int half = (e - b) >> 1;
-    if ((i >> k) & 1) b += half;
-    else e = b + half;
-  }
-  return b;
-}
 __host__ __device__ __forceinline__ int seg_base(int d) { return (1 << d) - 1 + d; }
 
 // Levels ping-pong between perm and perm_tmp: level d reads cur_perm(d) and its

@@ -138,6 +138,19 @@ def lib():
             "ff_profile_evals": ([C.POINTER(u64)], i32),
             "ff_profile_marks": ([C.POINTER(C.c_int32), C.POINTER(C.c_double), i32,
                                   C.POINTER(C.c_int)], i32),
+            "ff_sift_descriptors": ([vp, i32, i32, vp, vp], i32),
+            "ff_sift_moments": ([vp, i32, vp, vp, vp], i32),
+            "ff_sift_pca_workspace_size": ([C.POINTER(sz)], i32),
+            "ff_sift_pca": ([vp, vp, C.c_int64, i32, vp, vp, vp, vp, sz, vp], i32),
+            "ff_sift_colors": ([vp, i32, i32, vp, vp, i32, vp, vp], i32),
+            "ff_sift_level_workspace_size": ([i32, i32, i32, i32, C.POINTER(sz)], i32),
+            "ff_sift_kdtree_init": ([vp, vp, vp, i32, vp, vp, vp, i32, i32, i32, i32, i32, vp, vp,
+                                     vp, sz, vp], i32),
+            "ff_sift_search_level": ([vp, vp, i32, i32, i32, i32, i32, vp, P, i32, vp, vp, vp, sz,
+                                      vp], i32),
+            "ff_sift_workspace_size": ([i32, i32, P, i32, i32, C.POINTER(sz)], i32),
+            "ff_sift_flow_fields": ([vp, vp, i32, i32, P, vp, vp, i32, vp, vp, i32, vp, vp, vp,
+                                     vp, vp, vp, vp, sz, vp], i32),
             "ff_probe_popc": ([vp, i32, i32, vp], i32),
             "ff_probe_smem_taps": ([vp, i32, i32, vp], i32),
             "ff_probe_l2_gather": ([vp, sz, i32, vp, i32, i32, C.POINTER(u64), vp], i32),
@@ -390,6 +403,141 @@ class FlowFields:
 def ff_flow_fields(I1, I2, params=None, proposals=None):
     H, W = I1.shape[:2]
     return FlowFields(W, H, params, I1.device).run(I1, I2, proposals)
+
+
+# ------------------------------------------------------------ SIFT flow ----
+# Sec. 3.3, the second data term. Colours are uint8 (S/3, H, W, 3) groups.
+
+def ff_sift_descriptors(img):
+    """Dense SIFT vectors of an RGB frame: uint8 (H, W, 128)."""
+    H, W = img.shape[:2]
+    desc = torch.empty((H, W, 128), dtype=torch.uint8, device=img.device)
+    _check("ff_sift_descriptors", lib().ff_sift_descriptors(_dev(img), W, H, _dev(desc),
+                                                            _stream()))
+    return desc
+
+
+def ff_sift_moments(desc, acc=None):
+    """Exact PCA statistics of the descriptors, added to acc = (sum, gram, count)
+    when given. Returns (sum uint64 [128] as int64, gram [128, 128], count)."""
+    dev = desc.device
+    if acc is None:
+        sm = torch.zeros(128, dtype=torch.int64, device=dev)
+        gram = torch.zeros((128, 128), dtype=torch.int64, device=dev)
+        count = 0
+    else:
+        sm, gram, count = acc
+    N = desc.numel() // 128
+    _check("ff_sift_moments", lib().ff_sift_moments(_dev(desc), N, _dev(sm), _dev(gram),
+                                                    _stream()))
+    return sm, gram, count + N
+
+
+def ff_sift_pca(sm, gram, count, S, with_status=False):
+    """PCA basis (int16 [S, 128]), offsets (int32 [S]) and eigenvalues (float64
+    [128], descending) from the moments."""
+    dev = sm.device
+    basis = torch.empty((S, 128), dtype=torch.int16, device=dev)
+    off = torch.empty(S, dtype=torch.int32, device=dev)
+    eig = torch.empty(128, dtype=torch.float64, device=dev)
+    ws = _ws(_size("ff_sift_pca_workspace_size"), dev)
+    wp, wn = _ws_ptr(ws)
+    _check("ff_sift_pca", lib().ff_sift_pca(_dev(sm), _dev(gram), int(count), S, _dev(basis),
+                                            _dev(off), _dev(eig), wp, wn, _stream()))
+    if with_status:
+        code, x, y = C.c_uint32(), C.c_int32(), C.c_int32()
+        lib().ff_device_status(wp, C.byref(code), C.byref(x), C.byref(y), _stream())
+        return basis, off, eig, (code.value, x.value, y.value)
+    return basis, off, eig
+
+
+def ff_sift_colors(desc, basis, offset):
+    H, W = desc.shape[:2]
+    S = int(basis.shape[0])
+    col = torch.empty((S // 3, H, W, 3), dtype=torch.uint8, device=desc.device)
+    _check("ff_sift_colors", lib().ff_sift_colors(_dev(desc), W, H, _dev(basis), _dev(offset), S,
+                                                  _dev(col), _stream()))
+    return col
+
+
+def ff_sift_smooth(col, n):
+    """Every colour group smoothed like I^n (Sec. 3.2), by ff_smooth."""
+    return torch.stack([ff_smooth(g.contiguous(), n) for g in col])
+
+
+def ff_sift_kdtree_init(tree, leaf, src_img, col_src, col_tgt, n, r):
+    G3, H, W = col_src.shape[:3]
+    Gx, Gy = _grid(W, H, n)
+    dev = src_img.device
+    flow = torch.empty((Gy, Gx, 2), dtype=torch.int16, device=dev)
+    cost = torch.empty((Gy, Gx), dtype=torch.int32, device=dev)
+    ws = _ws(_size("ff_sift_level_workspace_size", W, H, n, 3 * G3), dev)
+    wp, wn = _ws_ptr(ws)
+    sd, sv = tree["_keep"]
+    _check("ff_sift_kdtree_init", lib().ff_sift_kdtree_init(
+        _dev(tree["perm"]), _dev(sd), _dev(sv), leaf, _dev(src_img), _dev(col_src),
+        _dev(col_tgt), 3 * G3, W, H, n, r, _dev(flow), _dev(cost), wp, wn, _stream()))
+    return flow, cost
+
+
+def ff_sift_search_level(col_src, col_tgt, n, r, params=None, flow_id=0, flow_coarse=None,
+                         flow=None, cost=None):
+    """One level with the SIFT flow data term (as ff_search_level)."""
+    G3, H, W = col_src.shape[:3]
+    Gx, Gy = _grid(W, H, n)
+    dev = col_src.device
+    if flow_coarse is not None:
+        flow = torch.empty((Gy, Gx, 2), dtype=torch.int16, device=dev)
+        cost = torch.empty((Gy, Gx), dtype=torch.int32, device=dev)
+    P = _params(params)
+    ws = _ws(_size("ff_sift_level_workspace_size", W, H, n, 3 * G3), dev)
+    wp, wn = _ws_ptr(ws)
+    _check("ff_sift_search_level", lib().ff_sift_search_level(
+        _dev(col_src), _dev(col_tgt), 3 * G3, W, H, n, r, _opt(flow_coarse), C.byref(P), flow_id,
+        _dev(flow), _dev(cost), wp, wn, _stream()))
+    return flow, cost
+
+
+class SiftFlowFields:
+    """The whole path with the SIFT flow data term for W x H pairs: bases
+    (basis, offset) of S1 channels for the forward and first backward flow and of
+    S2 channels for the second backward flow. ``run`` returns the dict of
+    FlowFields.run."""
+
+    def __init__(self, W, H, basis1, offset1, basis2, offset2, params=None, device="cuda"):
+        self.W, self.H = W, H
+        self.params = _params(params)
+        self.device = torch.device(device)
+        self.b = (basis1.contiguous(), offset1.contiguous(), basis2.contiguous(),
+                  offset2.contiguous())
+        self.S1, self.S2 = int(basis1.shape[0]), int(basis2.shape[0])
+        self.ws_bytes = _size("ff_sift_workspace_size", W, H, C.byref(self.params), self.S1,
+                              self.S2)
+        self.ws = _ws(self.ws_bytes, self.device)
+        nb = ((W + 2) // 3) * ((H + 2) // 3)
+        d = self.device
+        self.flows = torch.empty((3, H, W, 2), dtype=torch.int16, device=d)
+        self.valid = torch.empty((H, W), dtype=torch.uint8, device=d)
+        self.err_sum = torch.empty((H, W), dtype=torch.int32, device=d)
+        self.sparse = torch.empty((nb, 4), dtype=torch.int32, device=d)
+        self.n_sparse = torch.zeros(1, dtype=torch.int32, device=d)
+        self.mask = torch.empty((H, W), dtype=torch.uint8, device=d)
+
+    def run(self, I1, I2):
+        wp, wn = _ws_ptr(self.ws)
+        b1, o1, b2, o2 = self.b
+        _check("ff_sift_flow_fields", lib().ff_sift_flow_fields(
+            _dev(I1), _dev(I2), self.W, self.H, C.byref(self.params), _dev(b1), _dev(o1),
+            self.S1, _dev(b2), _dev(o2), self.S2, _dev(self.flows), _dev(self.valid),
+            _dev(self.err_sum), _dev(self.sparse), _dev(self.n_sparse), _dev(self.mask), wp, wn,
+            _stream()))
+        return dict(flows=self.flows, valid=self.valid, err_sum=self.err_sum,
+                    sparse=self.sparse, n_sparse=self.n_sparse, mask=self.mask)
+
+
+def ff_sift_flow_fields(I1, I2, basis1, offset1, basis2, offset2, params=None):
+    H, W = I1.shape[:2]
+    return SiftFlowFields(W, H, basis1, offset1, basis2, offset2, params, I1.device).run(I1, I2)
 
 
 def profile_enable(on=True, count_evals=False, marks=False):

@@ -181,3 +181,44 @@ def test_static_filter_applies_the_workspace_filters_checks(L):
         assert call(64, 48, ffapi.Params(**bad)) == 1, bad
     assert L.ff_consistency_filter_static(None, fake, fake, 64, 48, C.byref(ok), fake, fake, fake,
                                           fake, fake, None) == 1
+
+
+def test_sift_argument_checks(L):
+    """The SIFT flow entry points refuse bad channel counts, sizes and pointers on
+    the host, before any CUDA call."""
+    fake = C.c_void_p(0x1000)
+    sz = C.c_size_t()
+    assert L.ff_sift_pca_workspace_size(None) == 1
+    assert L.ff_sift_pca_workspace_size(C.byref(sz)) == 0 and sz.value >= 128 * 128 * 8
+    for S in (0, 2, 4, 33):
+        assert L.ff_sift_pca(fake, fake, 10, S, fake, fake, None, C.c_void_p(0x100000), 1 << 30,
+                             None) == 1, S
+        assert L.ff_sift_colors(C.c_void_p(0x1000), 64, 48, fake, fake, S, fake, None) == 1, S
+        assert L.ff_sift_level_workspace_size(64, 48, 2, S, C.byref(sz)) == 1, S
+    assert L.ff_sift_pca(fake, fake, 0, 12, fake, fake, None, C.c_void_p(0x100000), 1 << 30,
+                         None) == 1
+    assert L.ff_sift_pca(fake, fake, 10, 12, fake, fake, None, C.c_void_p(0x100001), 1 << 30,
+                         None) == 3
+    assert L.ff_sift_descriptors(fake, 64, 48, C.c_void_p(0x1008), None) == 1  # desc not 16-aligned
+    assert L.ff_sift_descriptors(fake, 0, 48, fake, None) == 2
+    assert L.ff_sift_moments(fake, -1, fake, fake, None) == 1
+    assert L.ff_sift_level_workspace_size(64, 48, 3, 12, C.byref(sz)) == 1
+    assert L.ff_sift_level_workspace_size(64, 48, 4, 12, C.byref(sz)) == 0
+    p = ffapi.Params(k=3, r=3, r2=2)
+    a, b = C.c_size_t(), C.c_size_t()
+    assert L.ff_sift_workspace_size(1242, 375, C.byref(p), 12, 18, C.byref(a)) == 0
+    assert L.ff_sift_workspace_size(1242, 375, C.byref(p), 3, 3, C.byref(b)) == 0
+    assert a.value > b.value > 128 * 1242 * 375 * 2  # two frames of SIFT vectors at least
+    assert L.ff_sift_workspace_size(1242, 375, C.byref(p), 12, 19, C.byref(a)) == 1
+    ps = ffapi.Params(k=3, r=3, r2=2, subpel=2)
+    args = (fake, fake, 12, fake, fake, 18, fake, fake, fake, fake, fake, fake)
+    assert L.ff_sift_flow_fields(fake, fake, 64, 48, C.byref(ps), *args, C.c_void_p(0x100000),
+                                 1 << 40, None) == 1
+    assert L.ff_sift_flow_fields(None, fake, 64, 48, C.byref(p), *args, C.c_void_p(0x100000),
+                                 1 << 40, None) == 1
+    assert L.ff_sift_flow_fields(fake, fake, 64, 48, C.byref(p), *args, C.c_void_p(0x100001),
+                                 1 << 40, None) == 3
+    assert L.ff_sift_search_level(fake, fake, 12, 64, 48, 1, 3, None, C.byref(ps), 0, fake, fake,
+                                  C.c_void_p(0x100000), 1 << 30, None) == 1
+    assert L.ff_sift_kdtree_init(fake, fake, fake, 8, fake, fake, fake, 12, 64, 48, 1, 9, fake,
+                                 fake, C.c_void_p(0x100000), 1 << 30, None) == 1
