@@ -710,6 +710,7 @@ def run_ours(args):
     batch = batch_measure(dev, PARAMS, pk, flush) if (rank == 0 and not args.no_batch) else None
     quality = field_quality(dev) if (rank == 0 and not args.no_quality) else None
     subpel = subpel_quality(dev) if (rank == 0 and not args.no_quality) else None
+    sift = sift_measure(dev) if (rank == 0 and not args.no_sift) else None
     learned = {}
     if rank == 0 and not args.no_learned:
         # the training workload at its stated size: 4096 generated pairs, 256 held out
@@ -772,6 +773,8 @@ def run_ours(args):
         line["field_quality_1024x436"] = quality
     if subpel is not None:
         line["subpixel_search"] = subpel
+    if sift is not None:
+        line["sift_flow_1242x375"] = sift
     for wl, lm in learned.items():
         eq = lm["equal_inliers"]
         if wl == "layers_1024x436" and eq is not None:
@@ -815,6 +818,163 @@ def run_ncu_target(args):
     print("ncu target done", flush=True)
 
 
+SIFT_PARAMS = dict(k=3, r=3, r2=2, leaf=8, R=1, eps=1, e=9, s=150, tile=16, n_rs=3)
+SIFT_S = (12, 18)
+
+
+def sift_bases(dev, seeds=(9000, 9001)):
+    """The SIFT flow PCA bases (S = 12 and 18 channels) fitted through the library
+    (ff_sift_moments, ff_sift_pca) on the descriptors of the first frames of
+    generated KITTI-shaped pairs; returns (basis1, offset1, basis2, offset2,
+    fit_ms)."""
+    import torch
+    from paper_1508_05151_gb300 import ffapi, synth
+    frames = [torch.from_numpy(synth.workload_pair("kitti_1242x375", s)["I1"]).to(dev)
+              for s in seeds]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    acc = None
+    for f in frames:
+        acc = ffapi.ff_sift_moments(ffapi.ff_sift_descriptors(f), acc=acc)
+    b1, o1, _ = ffapi.ff_sift_pca(acc[0], acc[1], acc[2], SIFT_S[0])
+    b2, o2, _ = ffapi.ff_sift_pca(acc[0], acc[1], acc[2], SIFT_S[1])
+    torch.cuda.synchronize()
+    return b1, o1, b2, o2, (time.perf_counter() - t0) * 1e3
+
+
+def sift_measure(dev, pairs=4, reps=5):
+    """Sec. 3.3 / Sec. 5: the whole path with the SIFT flow data term on generated
+    KITTI-shaped 1242x375 pairs in the paper's KITTI setting (r = 3, r2 = 2, S = 12,
+    S2 = 18, eps/e/s = 1/9/150), beside the census path with the KITTI preset
+    (r = 8, r2 = 6) on the same pairs: device time per pair (ff_sift_flow_fields /
+    ff_flow_fields, CUDA events, median of `reps` after a warm-up run), and the raw
+    forward field's inliers@3px / EPE against the generator's ground truth on
+    non-occluded pixels. The bases are fitted once on two other generated frames.
+
+    Roofline of the dominant kernel (k_sift_pass, the tiled propagation passes):
+    target bytes gathered (evaluations from the device counters x (2r+1)^2 taps x
+    16 or 32 bytes per tap) over the summed pass-launch time (CUDA events around
+    every launch on its stream), against the measured L2 rate for random 16-byte
+    gathers; 'alone' is the same with the three flows on one stream."""
+    import torch
+    from paper_1508_05151_gb300 import ffapi, synth
+    b1, o1, b2, o2, fit_ms = sift_bases(dev)
+    ps = [synth.workload_pair("kitti_1242x375", 5000 + i) for i in range(pairs)]
+    frames = [(torch.from_numpy(p["I1"]).to(dev), torch.from_numpy(p["I2"]).to(dev)) for p in ps]
+    sift = ffapi.SiftFlowFields(1242, 375, b1, o1, b2, o2, SIFT_PARAMS, dev)
+    census_p = dict(PARAMS, eps=1, e=9, s=150)
+    census = ffapi.FlowFields(1242, 375, census_p, dev)
+
+    def quality(ff, p):
+        f = ff.flows[0].cpu().numpy().astype(np.float64)
+        vis = ~p["occ"]
+        e = np.sqrt(((f - p["flow"]) ** 2).sum(-1))
+        valid = ff.valid.cpu().numpy().astype(bool)
+        return (float((e[vis] <= 3.0).mean()), float(e[vis].mean()), float(valid.mean()),
+                float((e[valid & vis] <= 3.0).mean()) if (valid & vis).any() else 0.0)
+
+    arms = {}
+    for name, ff in (("sift_flow", sift), ("census", census)):
+        ts, qs = [], []
+        for (a, b), p in zip(frames, ps):
+            ff.run(a, b)
+            torch.cuda.synchronize()
+            _, ms = _event_ms(lambda: ff.run(a, b), reps=reps)
+            ts.append(ms)
+            qs.append(quality(ff, p))
+        q = np.array(qs)
+        arms[name] = {"ms_per_pair": round(float(np.median(ts)), 4),
+                      "inliers_3px": round(float(q[:, 0].mean()), 5),
+                      "epe": round(float(q[:, 1].mean()), 4),
+                      "valid_frac": round(float(q[:, 2].mean()), 4),
+                      "valid_inliers_3px": round(float(q[:, 3].mean()), 5)}
+    arms["census"]["params"] = "r=8, r2=6 (the KITTI preset)"
+    arms["sift_flow"]["params"] = "r=3, r2=2, S=12, S2=18"
+
+    # roofline of the pass kernels
+    ffapi.profile_enable(False, count_evals=True)
+    ffapi.profile_reset()
+    for a, b in frames:
+        sift.run(a, b)
+    torch.cuda.synchronize()
+    counts = ffapi.profile_evals()
+    ffapi.profile_enable(False)
+    nw4 = {SIFT_PARAMS["r"]: 1 if SIFT_S[0] <= 16 else 2, SIFT_PARAMS["r2"]: 1 if SIFT_S[1] <= 16 else 2}
+    taps, tbytes = {}, {}
+    for (r, l), c in counts.items():
+        t = c["full_planes"] * (2 * r + 1) ** 2
+        taps[l] = taps.get(l, 0) + t
+        tbytes[l] = tbytes.get(l, 0) + t * 16 * nw4[r]
+
+    def timed(serial):
+        prev = ffapi.get_exec_params()["serial_flows"]
+        ffapi.set_exec_params(serial_flows=serial)
+        try:
+            ffapi.profile_enable(True)
+            ffapi.profile_reset()
+            for a, b in frames:
+                sift.run(a, b)
+            torch.cuda.synchronize()
+            lv = ffapi.profile_levels()
+        finally:
+            ffapi.profile_enable(False)
+            ffapi.set_exec_params(serial_flows=prev)
+        return lv
+
+    pk = measure_peaks(dev)
+    peak = pk["l2_line16_gather_gbs"]
+
+    def summarise(lv):
+        rows, T, B, MS, NL = [], 0, 0, 0.0, 0
+        for l in sorted(taps):
+            ms, nl = lv[l]["ms"], lv[l]["launches"]
+            if nl == 0:
+                continue
+            gbs = tbytes[l] / (ms * 1e-3) / 1e9
+            rows.append({"n": 1 << l, "launches_per_pair": nl // pairs,
+                         "taps_per_launch": round(taps[l] / nl), "ms_per_launch": round(ms / nl, 5),
+                         "gtaps_per_s": round(taps[l] / (ms * 1e-3) / 1e9, 1),
+                         "gather_gbs": round(gbs, 1), "frac": round(gbs / peak, 4)})
+            T, B, MS, NL = T + taps[l], B + tbytes[l], MS + ms, NL + nl
+        return rows, B / (MS * 1e-3) / 1e9, T, MS, NL
+
+    rows, gbs, T, MS, NL = summarise(timed(0))
+    rows_a, gbs_a, _, _, _ = summarise(timed(1))
+    roof = {"kernel": "k_sift_pass (tiled wavefront propagation, SIFT flow colours)",
+            "bound": "l2", "achieved": round(gbs, 1), "peak": round(peak, 1), "unit": "GB/s",
+            "frac": round(gbs / peak, 4), "traffic": None,
+            "peak_kind": "measured: own L2 probe, random 16-byte lines from an L2-resident "
+                         "32 MB buffer (a tap gathers one or two 16-byte colour words)",
+            "l2_coalesced_gbs": round(pk["l2_coalesced_gbs"], 1),
+            "taps_per_pair": round(T / pairs), "ms_per_launch": round(MS / NL, 5),
+            "per_level": rows,
+            "alone": {"achieved": round(gbs_a, 1), "frac": round(gbs_a / peak, 4),
+                      "per_level": rows_a}}
+    return {"workload": f"{pairs} generated KITTI-shaped 1242x375 pairs (seeds 5000..), "
+                        "bases fitted on two other generated frames",
+            "fit_ms": round(fit_ms, 2), "arms": arms,
+            "speed_ratio_census_over_sift": round(arms["census"]["ms_per_pair"]
+                                                  / arms["sift_flow"]["ms_per_pair"], 3),
+            "roofline": roof}
+
+
+def run_sift_ncu_target(args):
+    """A short fixed workload for ncu captures of the SIFT flow path: the bases
+    fitted once, then one KITTI-shaped 1242x375 pair twice through
+    ff_sift_flow_fields."""
+    import torch
+    from paper_1508_05151_gb300 import ffapi, synth
+    dev = torch.device("cuda:0")
+    b1, o1, b2, o2, _ = sift_bases(dev)
+    p = synth.workload_pair("kitti_1242x375", 1000)
+    I1, I2 = torch.from_numpy(p["I1"]).to(dev), torch.from_numpy(p["I2"]).to(dev)
+    ff = ffapi.SiftFlowFields(1242, 375, b1, o1, b2, o2, SIFT_PARAMS, dev)
+    for _ in range(2):
+        ff.run(I1, I2)
+        torch.cuda.synchronize()
+    print("sift ncu target done", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -831,9 +991,16 @@ def main():
                     help="keep the library's default execution parameters (profiling runs)")
     ap.add_argument("--ncu-target", action="store_true",
                     help="run a short fixed workload for ncu captures and exit (no timing)")
+    ap.add_argument("--no-sift", action="store_true",
+                    help="skip the SIFT flow data-term section")
+    ap.add_argument("--sift-ncu-target", action="store_true",
+                    help="the same for the SIFT flow path (one 1242x375 pair, twice)")
     args = ap.parse_args()
     if args.ncu_target:
         run_ncu_target(args)
+        return
+    if args.sift_ncu_target:
+        run_sift_ncu_target(args)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -390,6 +390,8 @@ struct PyrJob {
 // I^n (n > 1), its census and the phase planes of every job, one launch per step
 // over all jobs. host/dev: the jobs (dev: device copy written on the stream).
 ff_status launch_pyramid_level(const PyrJob *host, PyrJob *dev, int njobs, int n, cudaStream_t st);
+// Only the smoothing steps of the jobs (img -> down -> h -> sm), n > 1.
+ff_status launch_smooth_batch(const PyrJob *host, PyrJob *dev, int njobs, int n, cudaStream_t st);
 
 // -------------------------------------------------------------- colour -------
 ff_status launch_rgb_to_lab(const uint8_t *img, int W, int H, uint8_t *out, cudaStream_t st);

@@ -277,6 +277,31 @@ __global__ void k_planes_b(const PyrJob *J, int nn) {
   planes_at(j.census, j.pl, i, r, blockIdx.z % nn);
 }
 
+// I^n (n > 1) of every job (img -> down -> h -> sm), three launches; census and
+// planes are not touched.
+ff_status launch_smooth_batch(const PyrJob *host, PyrJob *dev, int njobs, int n, cudaStream_t st) {
+  if (njobs <= 0) return FF_OK;
+  if (n < 2 || n > 16 || (n & (n - 1)) || njobs > 65535) return FF_ERR_INVALID_ARG;
+  int maxA = 0, maxH = 0, maxV = 0;
+  for (int i = 0; i < njobs; i++) {
+    const int W = host[i].W, H = host[i].H, Wc = (W + n - 1) / n, Hc = (H + n - 1) / n;
+    maxA = max(maxA, Wc * Hc * 3);
+    maxH = max(maxH, Hc * W * 3);
+    maxV = max(maxV, H * W * 3);
+  }
+  FF_TRY(upload_desc(host, dev, njobs, st));
+  const int B = 256;
+  LanczosTable tab;
+  lanczos_table(n, &tab);
+  k_area_down_b<<<dim3((maxA + B - 1) / B, njobs), B, 0, st>>>(dev, n);
+  FF_CHECK_LAUNCH();
+  k_lanczos_h_b<<<dim3((maxH + B - 1) / B, njobs), B, 0, st>>>(dev, n, tab);
+  FF_CHECK_LAUNCH();
+  k_lanczos_v_b<<<dim3((maxV + B - 1) / B, njobs), B, 0, st>>>(dev, n, tab);
+  FF_CHECK_LAUNCH();
+  return FF_OK;
+}
+
 ff_status launch_pyramid_level(const PyrJob *host, PyrJob *dev, int njobs, int n, cudaStream_t st) {
   if (njobs <= 0) return FF_OK;
   if (n < 1 || n > 16 || (n & (n - 1))) return FF_ERR_INVALID_ARG;

@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "ff_internal.cuh"
@@ -21,7 +22,7 @@ constexpr int SIFT_DIM = 128;
 constexpr int SIFT_CELL = 3;       // cell edge in pixels
 constexpr int SIFT_SHIFT = 12;     // basis components in units of 2^-12
 constexpr int SIFT_MAX_S = 30;
-constexpr int SIFT_GROUP = 8;      // lanes per patch evaluation in the search
+constexpr int SIFT_GROUP = 16;     // lanes per patch evaluation in the search (half a warp)
 
 __constant__ int c_dir_c[8] = {256, 181, 0, -181, -256, -181, 0, 181};
 __constant__ int c_dir_s[8] = {0, 181, 256, 181, 0, -181, -256, -181};
@@ -387,43 +388,130 @@ struct SiftLevel {
   int W, H, n, Gx, Gy, flow_id;
   const uint32_t *flow_coarse;  // level-2n flows or nullptr
   int Gxc;
+  unsigned long long *evals;    // evaluation counters of the pass kernel or nullptr
 };
 
+// Squared colour distance of one tap from its loaded words, then the fixed-point
+// norm.
 template <int NW4>
-__device__ __forceinline__ int sift_tap(const uint4 *a, const uint4 *b) {
+__device__ __forceinline__ int sift_tap_words(const uint4 *a, const uint4 *b) {
   uint32_t acc = 0;
 #pragma unroll
   for (int w = 0; w < NW4; w++) {
-    const uint4 x = __ldg(a + w), y = __ldg(b + w);
-    uint32_t d = __vabsdiffu4(x.x, y.x);
+    uint32_t d = __vabsdiffu4(a[w].x, b[w].x);
     acc = __dp4a(d, d, acc);
-    d = __vabsdiffu4(x.y, y.y);
+    d = __vabsdiffu4(a[w].y, b[w].y);
     acc = __dp4a(d, d, acc);
-    d = __vabsdiffu4(x.z, y.z);
+    d = __vabsdiffu4(a[w].z, b[w].z);
     acc = __dp4a(d, d, acc);
-    d = __vabsdiffu4(x.w, y.w);
+    d = __vabsdiffu4(a[w].w, b[w].w);
     acc = __dp4a(d, d, acc);
   }
   return (int)isqrt_u32(acc << 8);  // acc <= 30 * 255^2
 }
 
-// E_d of source pixel (px, py) against target (X, Y): a group of 8 lanes (mask
-// gmask) splits the (2R+1)^2 taps; the sum is complete in every lane.
-template <int R, int NW4>
-__device__ __forceinline__ int sift_cost(const SiftLevel &L, int px, int py, int X, int Y, int l8,
-                                         unsigned gmask) {
-  constexpr int D = 2 * R + 1, DD = D * D;
-  int acc = 0;
-  for (int t = l8; t < DD; t += SIFT_GROUP) {
-    const int v = t / D - R, u = t % D - R;
-    const int xs = clampi(px + L.n * u, 0, L.W - 1), ys = clampi(py + L.n * v, 0, L.H - 1);
-    const int xt = clampi(X + L.n * u, 0, L.W - 1), yt = clampi(Y + L.n * v, 0, L.H - 1);
-    acc += sift_tap<NW4>(L.Ks + ((size_t)ys * L.W + xs) * NW4, L.Kt + ((size_t)yt * L.W + xt) * NW4);
+// E_d of source pixel (px, py) against up to two targets (X0, Y0), (X1, Y1) at
+// once: a group of 16 lanes (mask gmask) splits the (2R+1)^2 taps, tap
+// t = lane + 16 k. Taps are processed SIFT_CHUNK per lane at a time: every
+// load of a chunk is issued first (the source word once for both targets;
+// taps past the patch or of an unused target read a valid address and are
+// masked out), then the distances are summed. Sums are complete in every lane;
+// a target with use* false gets no defined cost. use0 / use1 are uniform over
+// the group.
+// CH = 1: the form for full grids (fewer registers, more resident groups); CH > 1
+// (SIFT_CHUNK): the form for grids of a few CTAs per SM, where each wavefront
+// step waits on its gathers.
+constexpr int SIFT_CHUNK = 4;
+
+template <int R, int NW4, int CH, bool TWO>
+__device__ __forceinline__ void sift_costs(const SiftLevel &L, int px, int py, int X0, int Y0,
+                                           bool use0, int X1, int Y1, bool use1, int lg,
+                                           unsigned gmask, int &e0, int &e1) {
+  constexpr int D = 2 * R + 1, DD = D * D, KT = (DD + SIFT_GROUP - 1) / SIFT_GROUP;
+  int a0 = 0, a1 = 0;
+  if (CH == 1) {
+#pragma unroll 4
+    for (int k = 0; k < KT; k++) {
+      const int t = lg + SIFT_GROUP * k;
+      if (t < DD) {
+        const int v = t / D - R, u = t % D - R;
+        const int xs = clampi(px + L.n * u, 0, L.W - 1), ys = clampi(py + L.n * v, 0, L.H - 1);
+        uint4 sv[NW4], tv[NW4];
+        const uint4 *src = L.Ks + ((size_t)ys * L.W + xs) * NW4;
+#pragma unroll
+        for (int w = 0; w < NW4; w++) sv[w] = __ldg(src + w);
+        if (use0) {
+          const int xt = clampi(X0 + L.n * u, 0, L.W - 1), yt = clampi(Y0 + L.n * v, 0, L.H - 1);
+          const uint4 *g = L.Kt + ((size_t)yt * L.W + xt) * NW4;
+#pragma unroll
+          for (int w = 0; w < NW4; w++) tv[w] = __ldg(g + w);
+          a0 += sift_tap_words<NW4>(sv, tv);
+        }
+        if (TWO && use1) {
+          const int xt = clampi(X1 + L.n * u, 0, L.W - 1), yt = clampi(Y1 + L.n * v, 0, L.H - 1);
+          const uint4 *g = L.Kt + ((size_t)yt * L.W + xt) * NW4;
+#pragma unroll
+          for (int w = 0; w < NW4; w++) tv[w] = __ldg(g + w);
+          a1 += sift_tap_words<NW4>(sv, tv);
+        }
+      }
+    }
+  } else {
+#pragma unroll 1
+    for (int k0 = 0; k0 < KT; k0 += CH) {
+      uint4 sv[CH][NW4], t0[CH][NW4], t1[CH][TWO ? NW4 : 1];
+      bool ok[CH];
+#pragma unroll
+      for (int c = 0; c < CH; c++) {
+        const int t = lg + SIFT_GROUP * (k0 + c);
+        ok[c] = k0 + c < KT && t < DD;
+        const int tt = ok[c] ? t : DD / 2;  // the centre tap: always inside the patch
+        const int v = tt / D - R, u = tt % D - R;
+        const int xs = clampi(px + L.n * u, 0, L.W - 1), ys = clampi(py + L.n * v, 0, L.H - 1);
+        const uint4 *src = L.Ks + ((size_t)ys * L.W + xs) * NW4;
+        const int x0 = clampi(X0 + L.n * u, 0, L.W - 1), y0 = clampi(Y0 + L.n * v, 0, L.H - 1);
+        const uint4 *g0 = L.Kt + ((size_t)y0 * L.W + x0) * NW4;
+#pragma unroll
+        for (int w = 0; w < NW4; w++) {
+          sv[c][w] = __ldg(src + w);
+          t0[c][w] = __ldg(g0 + w);
+        }
+        if (TWO) {
+          const int x1 = clampi(X1 + L.n * u, 0, L.W - 1), y1 = clampi(Y1 + L.n * v, 0, L.H - 1);
+          const uint4 *g1 = L.Kt + ((size_t)y1 * L.W + x1) * NW4;
+#pragma unroll
+          for (int w = 0; w < NW4; w++) t1[c][w] = __ldg(g1 + w);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CH; c++) {
+        if (ok[c] && use0) a0 += sift_tap_words<NW4>(sv[c], t0[c]);
+        if (TWO && ok[c] && use1) a1 += sift_tap_words<NW4>(sv[c], t1[c]);
+      }
+    }
   }
-  acc += __shfl_xor_sync(gmask, acc, 4);
-  acc += __shfl_xor_sync(gmask, acc, 2);
-  acc += __shfl_xor_sync(gmask, acc, 1);
-  return acc;
+#pragma unroll
+  for (int o = SIFT_GROUP / 2; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(gmask, a0, o);
+    if (TWO) a1 += __shfl_xor_sync(gmask, a1, o);
+  }
+  e0 = a0;
+  e1 = a1;
+}
+
+template <int R, int NW4, int CH>
+__device__ __forceinline__ int sift_cost(const SiftLevel &L, int px, int py, int X, int Y, int lg,
+                                         unsigned gmask) {
+  int e0, e1;
+  sift_costs<R, NW4, CH, false>(L, px, py, X, Y, true, X, Y, false, lg, gmask, e0, e1);
+  return e0;
+}
+
+template <int R, int NW4, int CH>
+__device__ __forceinline__ void sift_cost2(const SiftLevel &L, int px, int py, int X0, int Y0,
+                                           bool use0, int X1, int Y1, bool use1, int lg,
+                                           unsigned gmask, int &e0, int &e1) {
+  sift_costs<R, NW4, CH, true>(L, px, py, X0, Y0, use0, X1, Y1, use1, lg, gmask, e0, e1);
 }
 
 struct SiftKdQuery {
@@ -437,16 +525,16 @@ struct SiftKdQuery {
 
 // Eq. 1 / Eq. 4 with the SIFT flow data term: descend the tree with the grid
 // point's WHT vector, rerank the leaf by E_d (ties to the lower pixel index).
-template <int R, int NW4>
+template <int R, int NW4, int CH>
 __global__ void __launch_bounds__(256) k_sift_kd_query(SiftLevel L, SiftKdQuery Q) {
   const int G = L.Gx * L.Gy;
   const int g = (blockIdx.x * blockDim.x + threadIdx.x) / SIFT_GROUP;
-  const int l8 = threadIdx.x & (SIFT_GROUP - 1);
-  const unsigned gmask = 0xffu << (threadIdx.x & 24);
+  const int lg = threadIdx.x & (SIFT_GROUP - 1);
+  const unsigned gmask = 0xffffu << (threadIdx.x & 16);
   if (g >= G) return;  // uniform per group
   const int px = (g % L.Gx) * L.n, py = (g / L.Gx) * L.n;
   int leaf = 0;
-  if (l8 == 0) {
+  if (lg == 0) {
     const int32_t *q = Q.qfeat + (size_t)g * FEAT_STRIDE;
     int node = 0;
     for (int d = 0; d < Q.D; d++) {
@@ -459,22 +547,27 @@ __global__ void __launch_bounds__(256) k_sift_kd_query(SiftLevel L, SiftKdQuery 
     }
     leaf = node - ((1 << Q.D) - 1);
   }
-  leaf = __shfl_sync(gmask, leaf, threadIdx.x & 24);
+  leaf = __shfl_sync(gmask, leaf, threadIdx.x & 16);
   const int b = seg_begin(Q.N, Q.D, leaf), e = seg_begin(Q.N, Q.D, leaf + 1);
   int best = COST_UNSET, bidx = 0x7fffffff;
-  for (int c = b; c < e; c++) {
-    const int idx = Q.perm[c];
-    if ((unsigned)idx >= (unsigned)Q.N) {  // uniform over the group
-      if (l8 == 0) raise_status(Q.status, DEV_ERR_BOUNDS, g, c);
-      continue;
+  for (int c = b; c < e; c += 2) {
+    int idx[2] = {Q.perm[c], c + 1 < e ? Q.perm[c + 1] : -1};
+    bool use[2];
+    for (int i = 0; i < 2; i++) {
+      use[i] = (unsigned)idx[i] < (unsigned)Q.N;  // uniform over the group
+      if (!use[i] && (i == 0 || c + 1 < e) && lg == 0) raise_status(Q.status, DEV_ERR_BOUNDS, g, c + i);
     }
-    const int cost = sift_cost<R, NW4>(L, px, py, idx % L.W, idx / L.W, l8, gmask);
-    if (cost < best || (cost == best && idx < bidx)) {
-      best = cost;
-      bidx = idx;
-    }
+    int cost[2];
+    sift_cost2<R, NW4, CH>(L, px, py, use[0] ? idx[0] % L.W : 0, use[0] ? idx[0] / L.W : 0, use[0],
+                       use[1] ? idx[1] % L.W : 0, use[1] ? idx[1] / L.W : 0, use[1], lg, gmask,
+                       cost[0], cost[1]);
+    for (int i = 0; i < 2; i++)
+      if (use[i] && (cost[i] < best || (cost[i] == best && idx[i] < bidx))) {
+        best = cost[i];
+        bidx = idx[i];
+      }
   }
-  if (l8 == 0) {
+  if (lg == 0) {
     Q.flow[g] = pack_flow(bidx % L.W - px, bidx / L.W - py);
     Q.cost[g] = best;
   }
@@ -482,12 +575,12 @@ __global__ void __launch_bounds__(256) k_sift_kd_query(SiftLevel L, SiftKdQuery 
 
 // Sec. 3.2 level transition: grid points with both coordinates even take the
 // coarser level's flow (cost re-evaluated), all others start without a flow.
-template <int R, int NW4>
+template <int R, int NW4, int CH>
 __global__ void __launch_bounds__(256) k_sift_seed(SiftLevel L, uint32_t *flow, int32_t *cost) {
   const int G = L.Gx * L.Gy;
   const int g = (blockIdx.x * blockDim.x + threadIdx.x) / SIFT_GROUP;
-  const int l8 = threadIdx.x & (SIFT_GROUP - 1);
-  const unsigned gmask = 0xffu << (threadIdx.x & 24);
+  const int lg = threadIdx.x & (SIFT_GROUP - 1);
+  const unsigned gmask = 0xffffu << (threadIdx.x & 16);
   if (g >= G) return;
   const int gx = g % L.Gx, gy = g / L.Gx, px = gx * L.n, py = gy * L.n;
   uint32_t f = 0;
@@ -495,23 +588,23 @@ __global__ void __launch_bounds__(256) k_sift_seed(SiftLevel L, uint32_t *flow, 
   if (!(gx & 1) && !(gy & 1)) {
     const uint32_t fc = L.flow_coarse[(size_t)(gy >> 1) * L.Gxc + (gx >> 1)];
     const int X = clampi(px + flow_dx(fc), 0, L.W - 1), Y = clampi(py + flow_dy(fc), 0, L.H - 1);
-    c = sift_cost<R, NW4>(L, px, py, X, Y, l8, gmask);
+    c = sift_cost<R, NW4, CH>(L, px, py, X, Y, lg, gmask);
     f = pack_flow(X - px, Y - py);
   }
-  if (l8 == 0) {
+  if (lg == 0) {
     flow[g] = f;
     cost[g] = c;
   }
 }
 
 // Random search step (Sec. 3.1): F + O_rnd, kept if E_d decreases; in place.
-template <int R, int NW4>
+template <int R, int NW4, int CH>
 __global__ void __launch_bounds__(256) k_sift_rs(SiftLevel L, uint32_t *flow, int32_t *cost,
                                                  int step, int level, int Rn, uint64_t seed) {
   const int G = L.Gx * L.Gy;
   const int g = (blockIdx.x * blockDim.x + threadIdx.x) / SIFT_GROUP;
-  const int l8 = threadIdx.x & (SIFT_GROUP - 1);
-  const unsigned gmask = 0xffu << (threadIdx.x & 24);
+  const int lg = threadIdx.x & (SIFT_GROUP - 1);
+  const unsigned gmask = 0xffffu << (threadIdx.x & 16);
   if (g >= G) return;
   const int c = cost[g];
   if (c == COST_UNSET) return;  // uniform per group
@@ -521,8 +614,8 @@ __global__ void __launch_bounds__(256) k_sift_rs(SiftLevel L, uint32_t *flow, in
   rs_offset(seed, L.flow_id, level, step, gx, gy, Rn, dx, dy);
   const int X = clampi(px + flow_dx(f) + dx, 0, L.W - 1);
   const int Y = clampi(py + flow_dy(f) + dy, 0, L.H - 1);
-  const int e = sift_cost<R, NW4>(L, px, py, X, Y, l8, gmask);
-  if (e < c && l8 == 0) {
+  const int e = sift_cost<R, NW4, CH>(L, px, py, X, Y, lg, gmask);
+  if (e < c && lg == 0) {
     flow[g] = pack_flow(X - px, Y - py);
     cost[g] = e;
   }
@@ -537,12 +630,14 @@ __constant__ int c_pass_src[4][2] = {{-1, -1}, {1, 1}, {1, -1}, {-1, 1}};
 // two sources lie on the previous diagonal, so this equals the sequential scan),
 // one 8-lane group per point of a diagonal. Sources outside the tile are read
 // from the start-of-pass state (fin, cin); results go to (fout, cout).
-template <int R, int NW4>
-__global__ void __launch_bounds__(256) k_sift_pass(SiftLevel L, const uint32_t *fin,
+template <int R, int NW4, int CH>
+__global__ void __launch_bounds__(SIFT_GROUP * MAX_TILE) k_sift_pass(SiftLevel L, const uint32_t *fin,
                                                    const int32_t *cin, uint32_t *fout,
                                                    int32_t *cout, int s, int T) {
   __shared__ uint32_t sf[MAX_TILE * MAX_TILE];
   __shared__ int32_t sc[MAX_TILE * MAX_TILE];
+  __shared__ unsigned s_evals;
+  if (threadIdx.x == 0) s_evals = 0;
   const int off = (s & 1) * (T / 2);
   const int ntx = (L.Gx + off + T - 1) / T;
   const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
@@ -557,8 +652,8 @@ __global__ void __launch_bounds__(256) k_sift_pass(SiftLevel L, const uint32_t *
   }
   __syncthreads();
   const int sx = c_pass_src[s][0], sy = c_pass_src[s][1];
-  const int gi = threadIdx.x / SIFT_GROUP, l8 = threadIdx.x & (SIFT_GROUP - 1);
-  const unsigned gmask = 0xffu << (threadIdx.x & 24);
+  const int gi = threadIdx.x / SIFT_GROUP, lg = threadIdx.x & (SIFT_GROUP - 1);
+  const unsigned gmask = 0xffffu << (threadIdx.x & 16);
   for (int d = 0; d < tw + th - 1; d++) {
     const int iy = gi, ix = d - gi;
     if (iy < th && ix >= 0 && ix < tw) {  // uniform per group
@@ -567,23 +662,34 @@ __global__ void __launch_bounds__(256) k_sift_pass(SiftLevel L, const uint32_t *
       const int li = (gy - y0) * T + (gx - x0);
       uint32_t f = sf[li];
       int c = sc[li];
-#pragma unroll 1
+      // candidates in order: the horizontal source, then the vertical one
+      bool use[2];
+      int X[2], Y[2];
+#pragma unroll
       for (int cand = 0; cand < 2; cand++) {
         const int qx = gx + (cand == 0 ? sx : 0), qy = gy + (cand == 0 ? 0 : sy);
-        if (qx < 0 || qx >= L.Gx || qy < 0 || qy >= L.Gy) continue;
-        const bool inside = qx >= x0 && qx < x1 && qy >= y0 && qy < y1;
-        const size_t qg = (size_t)qy * L.Gx + qx;
-        const uint32_t fq = inside ? sf[(qy - y0) * T + (qx - x0)] : fin[qg];
-        const int cq = inside ? sc[(qy - y0) * T + (qx - x0)] : cin[qg];
-        if (cq == COST_UNSET) continue;
-        const int X = clampi(px + flow_dx(fq), 0, L.W - 1), Y = clampi(py + flow_dy(fq), 0, L.H - 1);
-        const int e = sift_cost<R, NW4>(L, px, py, X, Y, l8, gmask);
-        if (e < c) {
-          c = e;
-          f = pack_flow(X - px, Y - py);
+        use[cand] = qx >= 0 && qx < L.Gx && qy >= 0 && qy < L.Gy;
+        X[cand] = Y[cand] = 0;
+        if (use[cand]) {
+          const bool inside = qx >= x0 && qx < x1 && qy >= y0 && qy < y1;
+          const size_t qg = (size_t)qy * L.Gx + qx;
+          const uint32_t fq = inside ? sf[(qy - y0) * T + (qx - x0)] : fin[qg];
+          const int cq = inside ? sc[(qy - y0) * T + (qx - x0)] : cin[qg];
+          use[cand] = cq != COST_UNSET;
+          X[cand] = clampi(px + flow_dx(fq), 0, L.W - 1);
+          Y[cand] = clampi(py + flow_dy(fq), 0, L.H - 1);
         }
       }
-      if (l8 == 0) {
+      int e[2];
+      sift_cost2<R, NW4, CH>(L, px, py, X[0], Y[0], use[0], X[1], Y[1], use[1], lg, gmask, e[0], e[1]);
+      if (L.evals && lg == 0) atomicAdd(&s_evals, (unsigned)use[0] + (unsigned)use[1]);
+#pragma unroll
+      for (int cand = 0; cand < 2; cand++)
+        if (use[cand] && e[cand] < c) {
+          c = e[cand];
+          f = pack_flow(X[cand] - px, Y[cand] - py);
+        }
+      if (lg == 0) {
         sf[li] = f;
         sc[li] = c;
       }
@@ -596,17 +702,45 @@ __global__ void __launch_bounds__(256) k_sift_pass(SiftLevel L, const uint32_t *
     fout[g] = sf[ly * T + lx];
     cout[g] = sc[ly * T + lx];
   }
+  // evaluations are full E_d with targets gathered from the colour array
+  if (L.evals && threadIdx.x == 0 && s_evals) atomicAdd(L.evals + 3, (unsigned long long)s_evals);
 }
 
 // ------------------------------------------------------------ launchers ------
-#define FF_DISPATCH_SIFT(r, nw4, KERNEL, GRID, BLOCK, SMEM, ST, ...)              \
-  do {                                                                           \
-    FF_DISPATCH_R(r, {                                                           \
-      if ((nw4) == 1) KERNEL<RR, 1><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);     \
-      else KERNEL<RR, 2><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);                \
-    });                                                                          \
-    FF_CHECK_LAUNCH();                                                           \
+#define FF_DISPATCH_SIFT(r, nw4, ch, KERNEL, GRID, BLOCK, SMEM, ST, ...)                \
+  do {                                                                                 \
+    FF_DISPATCH_R(r, {                                                                 \
+      if ((nw4) == 1 && (ch) == 1) KERNEL<RR, 1, 1><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__); \
+      else if ((nw4) == 1) KERNEL<RR, 1, SIFT_CHUNK><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__); \
+      else if ((ch) == 1) KERNEL<RR, 2, 1><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);     \
+      else KERNEL<RR, 2, SIFT_CHUNK><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);           \
+    });                                                                                \
+    FF_CHECK_LAUNCH();                                                                 \
   } while (0)
+
+// The fully parallel kernels (kd query, seeding, random search) in the CH = 1 form.
+#define FF_DISPATCH_SIFT1(r, nw4, KERNEL, GRID, BLOCK, SMEM, ST, ...)                   \
+  do {                                                                                 \
+    FF_DISPATCH_R(r, {                                                                 \
+      if ((nw4) == 1) KERNEL<RR, 1, 1><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);         \
+      else KERNEL<RR, 2, 1><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);                    \
+    });                                                                                \
+    FF_CHECK_LAUNCH();                                                                 \
+  } while (0)
+
+// Streaming multiprocessors of the current device (cached per device).
+static int sift_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+      v = 1;
+    cache[dev].store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
 
 static int sift_nw4(int S) { return S <= 16 ? 1 : 2; }
 static bool sift_S_ok(int S) { return S >= 3 && S <= SIFT_MAX_S && S % 3 == 0; }
@@ -663,13 +797,14 @@ static SiftLevel make_sift_level(const uint4 *Ks, const uint4 *Kt, int W, int H,
   L.flow_id = flow_id;
   L.flow_coarse = flow_coarse;
   L.Gxc = (W + 2 * n - 1) / (2 * n);
+  L.evals = nullptr;
   return L;
 }
 
 ff_status launch_sift_kd_query(const SiftLevel &L, const SiftKdQuery &Q, int r, int nw4,
                                cudaStream_t st) {
   const int G = L.Gx * L.Gy;
-  FF_DISPATCH_SIFT(r, nw4, k_sift_kd_query, grid_blocks((long long)G * SIFT_GROUP), 256, 0, st, L,
+  FF_DISPATCH_SIFT1(r, nw4, k_sift_kd_query, grid_blocks((long long)G * SIFT_GROUP), 256, 0, st, L,
                    Q);
   return FF_OK;
 }
@@ -681,31 +816,41 @@ ff_status run_sift_level(const SiftLevel &L, int r, int nw4, uint32_t *fa, int32
                          cudaStream_t st) {
   const int G = L.Gx * L.Gy;
   const int blocks = grid_blocks((long long)G * SIFT_GROUP);
-  if (L.flow_coarse) FF_DISPATCH_SIFT(r, nw4, k_sift_seed, blocks, 256, 0, st, L, fa, ca);
+  if (L.flow_coarse) FF_DISPATCH_SIFT1(r, nw4, k_sift_seed, blocks, 256, 0, st, L, fa, ca);
   int level = 0;
   while ((1 << level) < L.n) level++;
+  SiftLevel Lp = L;  // the pass kernels count their evaluations when profiling
+  Lp.evals = prof_evals(r, level);
   uint32_t *f[2] = {fa, fb};
   int32_t *c[2] = {ca, cb};
   for (int s = 0; s < 4; s++) {
     const int off = (s & 1) * (tile / 2);
     const int ntiles = ((L.Gx + off + tile - 1) / tile) * ((L.Gy + off + tile - 1) / tile);
-    FF_DISPATCH_SIFT(r, nw4, k_sift_pass, ntiles, SIFT_GROUP * tile, 0, st, L, f[s & 1],
+    // at most about two CTAs per SM: the wavefront steps wait on their gathers,
+    // so each lane issues a chunk of taps' loads at once
+    const int ch = (long long)ntiles * SIFT_GROUP * tile <= 512ll * sift_sm_count() ? SIFT_CHUNK : 1;
+    if (prof_enabled()) prof_begin(st, level);
+    FF_DISPATCH_SIFT(r, nw4, ch, k_sift_pass, ntiles, SIFT_GROUP * tile, 0, st, Lp, f[s & 1],
                      c[s & 1], f[(s + 1) & 1], c[(s + 1) & 1], s, tile);
+    if (prof_enabled()) prof_end(st);
     if (s < 3 && s < n_rs)
-      FF_DISPATCH_SIFT(r, nw4, k_sift_rs, blocks, 256, 0, st, L, f[(s + 1) & 1], c[(s + 1) & 1],
+      FF_DISPATCH_SIFT1(r, nw4, k_sift_rs, blocks, 256, 0, st, L, f[(s + 1) & 1], c[(s + 1) & 1],
                        s, level, R * L.n, seed);
   }
   return FF_OK;
 }
 
 // ------------------------------------------------------------- whole path ----
+constexpr int SIFT_MAXLV = 5;
+
 struct SiftPlan {
   uint8_t *lab[2];
   uint8_t *desc[2];
   uint8_t *col[2][2];     // [colour set][frame] full-resolution colour groups
-  uint8_t *col_n;         // one level-n colour group set being smoothed
-  void *smooth_scratch;
-  uint4 *K[2][2];         // [colour set][frame] packed level-n colours
+  uint8_t *col_n[2][2];   // the same smoothed at the current level
+  uint8_t *down[2][2], *hbuf[2][2];  // smoothing scratch per (set, frame): one slice per group
+  size_t down_stride, h_stride;      // bytes per group slice
+  uint4 *K[SIFT_MAXLV][2][2];        // [level][colour set][frame] packed colours
   int32_t *feat[3], *qfeat[3];
   int32_t *perm[3], *split_dim[3], *split_val[3];
   KdBuild kd[3];
@@ -713,22 +858,35 @@ struct SiftPlan {
   int32_t *cs[3][3];
   void *filter_scratch;
   KdBuild *d_kd;
+  PyrJob *d_jobs;         // per level: the smoothing jobs (one per colour group and frame)
 };
+
+static int sift_groups(const int Ss[2]) { return 2 * (Ss[0] / 3 + Ss[1] / 3); }
 
 static void plan_sift(Arena &a, int W, int H, const ff_params *p, int S1, int S2, SiftPlan &P) {
   const size_t N = (size_t)W * H;
+  const int Ss[2] = {S1, S2};
   a.take<char>(WS_HEADER);
   for (int f = 0; f < 2; f++) P.lab[f] = p->color == 1 ? a.take<uint8_t>(N * 3) : nullptr;
   for (int f = 0; f < 2; f++) P.desc[f] = a.take<uint8_t>(N * SIFT_DIM);
-  const int Ss[2] = {S1, S2};
+  // smoothing scratch of one group at the finest smoothed level (n = 2) bounds all
+  const int Wc = (W + 1) / 2, Hc = (H + 1) / 2;
+  P.down_stride = ((size_t)Wc * Hc * 3 + 255) & ~(size_t)255;
+  P.h_stride = ((size_t)Hc * W * 3 * sizeof(int32_t) + 255) & ~(size_t)255;
   for (int c = 0; c < 2; c++)
-    for (int f = 0; f < 2; f++) P.col[c][f] = a.take<uint8_t>(N * Ss[c]);
-  P.col_n = a.take<uint8_t>(N * std::max(S1, S2));
-  size_t ss = 0;
-  for (int lv = 1; lv <= p->k; lv++) ss = std::max(ss, smooth_scratch_bytes(W, H, 1 << lv));
-  P.smooth_scratch = a.take<char>(ss);
-  for (int c = 0; c < 2; c++)
-    for (int f = 0; f < 2; f++) P.K[c][f] = a.take<uint4>(N * sift_nw4(Ss[c]));
+    for (int f = 0; f < 2; f++) {
+      P.col[c][f] = a.take<uint8_t>(N * Ss[c]);
+      P.col_n[c][f] = a.take<uint8_t>(N * Ss[c]);
+      if (p->k > 0) {
+        P.down[c][f] = a.take<uint8_t>(P.down_stride * (Ss[c] / 3));
+        P.hbuf[c][f] = a.take<uint8_t>(P.h_stride * (Ss[c] / 3));
+      } else {
+        P.down[c][f] = P.hbuf[c][f] = nullptr;
+      }
+    }
+  for (int lv = 0; lv <= p->k; lv++)
+    for (int c = 0; c < 2; c++)
+      for (int f = 0; f < 2; f++) P.K[lv][c][f] = a.take<uint4>(N * sift_nw4(Ss[c]));
   const int ntop = 1 << p->k;
   const size_t Gtop = (size_t)((W + ntop - 1) / ntop) * ((H + ntop - 1) / ntop);
   const int D = kd_depth((int)N, p->leaf);
@@ -763,20 +921,39 @@ static void plan_sift(Arena &a, int W, int H, const ff_params *p, int S1, int S2
   }
   P.filter_scratch = a.take<char>(filter_scratch_bytes(W, H));
   P.d_kd = a.take<KdBuild>(3);
+  P.d_jobs = a.take<PyrJob>((size_t)SIFT_MAXLV * sift_groups(Ss));
 }
 
-// Each of the S/3 colour groups of `src` smoothed at spacing n into dst, then
-// packed into K.
-static ff_status level_colours(const uint8_t *src, int W, int H, int S, int n, uint8_t *dst,
-                               void *scratch, uint4 *K, cudaStream_t st) {
+// The packed colours of every level: per level n > 1 every colour group of both
+// frames smoothed like I^n in one batched launch sequence, then packed.
+static ff_status sift_pyramid(const SiftPlan &P, int W, int H, int k, const int Ss[2],
+                              cudaStream_t st) {
   const size_t N = (size_t)W * H;
-  const uint8_t *use = src;
-  if (n > 1) {
-    for (int g = 0; g < S / 3; g++)
-      FF_TRY(launch_smooth(src + (size_t)g * N * 3, W, H, n, dst + (size_t)g * N * 3, scratch, st));
-    use = dst;
+  const int ng = sift_groups(Ss);
+  for (int lv = 0; lv <= k; lv++) {
+    const int n = 1 << lv;
+    if (n > 1) {
+      std::vector<PyrJob> jobs;
+      for (int c = 0; c < 2; c++)
+        for (int f = 0; f < 2; f++)
+          for (int g = 0; g < Ss[c] / 3; g++) {
+            PyrJob j{};
+            j.img = P.col[c][f] + (size_t)g * N * 3;
+            j.down = P.down[c][f] + P.down_stride * g;
+            j.h = (int32_t *)(P.hbuf[c][f] + P.h_stride * g);
+            j.sm = P.col_n[c][f] + (size_t)g * N * 3;
+            j.W = W;
+            j.H = H;
+            jobs.push_back(j);
+          }
+      FF_TRY(launch_smooth_batch(jobs.data(), P.d_jobs + (size_t)lv * ng, (int)jobs.size(), n, st));
+    }
+    for (int c = 0; c < 2; c++)
+      for (int f = 0; f < 2; f++)
+        FF_TRY(launch_sift_pack(n > 1 ? P.col_n[c][f] : P.col[c][f], (int)N, Ss[c], P.K[lv][c][f],
+                                st));
   }
-  return launch_sift_pack(use, (int)N, S, K, st);
+  return FF_OK;
 }
 
 static ff_status run_sift_pair(const uint8_t *I1_in, const uint8_t *I2_in, int W, int H,
@@ -797,36 +974,48 @@ static ff_status run_sift_pair(const uint8_t *I1_in, const uint8_t *I2_in, int W
     I1 = P.lab[0];
     I2 = P.lab[1];
   }
-  // SIFT vectors of the input frames and their colours under both bases
-  const uint8_t *in[2] = {I1_in, I2_in};
-  for (int f = 0; f < 2; f++) {
-    FF_TRY(launch_sift_descriptors(in[f], W, H, P.desc[f], st));
-    for (int c = 0; c < 2; c++)
-      FF_TRY(launch_sift_colors(P.desc[f], (int)N, B[c], O[c], Ss[c], P.col[c][f], st));
-  }
-  // flows: forward I1 -> I2 (r, set 0), backward I2 -> I1 (r, set 0), (r2, set 1)
+  const bool serial = exec_params().serial_flows != 0;
   const int k = p->k, ntop = 1 << k;
+  // SIFT vectors of the input frames, their colours under both bases and the
+  // colour pyramid on a side stream, beside the WHT features and the three kd
+  // trees (one launch chain) on the caller's stream
+  {
+    SideSection pre;
+    if (!serial) FF_TRY(pre.begin(st, 1));
+    const cudaStream_t cs = serial ? st : pre.side[0];
+    const uint8_t *in[2] = {I1_in, I2_in};
+    for (int f = 0; f < 2; f++) {
+      FF_TRY(launch_sift_descriptors(in[f], W, H, P.desc[f], cs));
+      for (int c = 0; c < 2; c++)
+        FF_TRY(launch_sift_colors(P.desc[f], (int)N, B[c], O[c], Ss[c], P.col[c][f], cs));
+    }
+    FF_TRY(sift_pyramid(P, W, H, k, Ss, cs));
+    const int srcf[3] = {0, 1, 1}, tgtf[3] = {1, 0, 0}, rad[3] = {p->r, p->r, p->r2};
+    const uint8_t *img[2] = {I1, I2};
+    for (int j = 0; j < 3; j++) {
+      FF_TRY(launch_features(img[tgtf[j]], W, H, rad[j], nullptr, 0, 1, P.feat[j], st, true));
+      FF_TRY(launch_features(img[srcf[j]], W, H, rad[j], nullptr, 0, ntop, P.qfeat[j], st));
+    }
+    FF_TRY(launch_kd_build(P.kd, P.d_kd, 3, st));
+    if (!serial) FF_TRY(pre.end());
+  }
+  // flows: forward I1 -> I2 (r, set 0), backward I2 -> I1 (r, set 0), (r2, set 1),
+  // each flow's kd query and levels on a stream of its own
   const int srcf[3] = {0, 1, 1}, tgtf[3] = {1, 0, 0}, rad[3] = {p->r, p->r, p->r2};
   const int cset[3] = {0, 0, 1};
-  const uint8_t *img[2] = {I1, I2};
-  for (int j = 0; j < 3; j++) {
-    FF_TRY(launch_features(img[tgtf[j]], W, H, rad[j], nullptr, 0, 1, P.feat[j], st, true));
-    FF_TRY(launch_features(img[srcf[j]], W, H, rad[j], nullptr, 0, ntop, P.qfeat[j], st));
-  }
-  FF_TRY(launch_kd_build(P.kd, P.d_kd, 3, st));
+  SideSection sec;
+  if (!serial) FF_TRY(sec.begin(st, 2));
   int cur[3] = {0, 0, 0};
-  for (int lv = k; lv >= 0; lv--) {
-    const int n = 1 << lv;
-    for (int c = 0; c < 2; c++)
-      for (int f = 0; f < 2; f++)
-        FF_TRY(level_colours(P.col[c][f], W, H, Ss[c], n, P.col_n, P.smooth_scratch, P.K[c][f], st));
-    for (int j = 0; j < 3; j++) {
-      const int c = cset[j], nw4 = sift_nw4(Ss[c]);
+  for (int j = 0; j < 3; j++) {
+    const cudaStream_t fs = (serial || j == 0) ? st : sec.side[j - 1];
+    const int c = cset[j], nw4 = sift_nw4(Ss[c]);
+    for (int lv = k; lv >= 0; lv--) {
+      const int n = 1 << lv;
       // three buffers per flow: the coarser level's final state, this level's
       // state and its ping-pong partner
       const int a0 = lv == k ? 0 : (cur[j] + 1) % 3, b0 = (a0 + 1) % 3;
       const uint32_t *coarse = lv == k ? nullptr : P.fl[j][cur[j]];
-      SiftLevel L = make_sift_level(P.K[c][srcf[j]], P.K[c][tgtf[j]], W, H, n, j, coarse);
+      SiftLevel L = make_sift_level(P.K[lv][c][srcf[j]], P.K[lv][c][tgtf[j]], W, H, n, j, coarse);
       if (lv == k) {
         SiftKdQuery Q;
         Q.perm = P.perm[j];
@@ -838,17 +1027,17 @@ static ff_status run_sift_pair(const uint8_t *I1_in, const uint8_t *I2_in, int W
         Q.flow = P.fl[j][a0];
         Q.cost = P.cs[j][a0];
         Q.status = (DeviceStatus *)ws;
-        FF_TRY(launch_sift_kd_query(L, Q, rad[j], nw4, st));
+        FF_TRY(launch_sift_kd_query(L, Q, rad[j], nw4, fs));
       }
       FF_TRY(run_sift_level(L, rad[j], nw4, P.fl[j][a0], P.cs[j][a0], P.fl[j][b0], P.cs[j][b0],
-                            p->tile, p->n_rs, p->R, p->seed, st));
+                            p->tile, p->n_rs, p->R, p->seed, fs));
       cur[j] = a0;
     }
-  }
-  for (int j = 0; j < 3; j++)
     if (cudaMemcpyAsync(flows + 2 * N * j, P.fl[j][cur[j]], N * sizeof(uint32_t),
-                        cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                        cudaMemcpyDeviceToDevice, fs) != cudaSuccess)
       return FF_ERR_CUDA;
+  }
+  if (!serial) FF_TRY(sec.end());
   return launch_filter((const uint32_t *)flows, (const uint32_t *)(flows + 2 * N),
                        (const uint32_t *)(flows + 4 * N), W, H, p->eps, p->e, p->s, 1, valid,
                        err_sum, sparse, n_sparse, mask, P.filter_scratch, st);
