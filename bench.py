@@ -852,8 +852,8 @@ def sift_measure(dev, pairs=4, reps=5):
     non-occluded pixels. The bases are fitted once on two other generated frames.
 
     Roofline of the dominant kernel (k_sift_pass, the tiled propagation passes):
-    target bytes gathered (evaluations from the device counters x (2r+1)^2 taps x
-    16 or 32 bytes per tap) over the summed pass-launch time (CUDA events around
+    target bytes gathered (evaluations from the device counters: (2r+1)^2 taps for
+    a full one, 2 (2r+1) for an incremental one; 16 or 32 bytes per tap) over the summed pass-launch time (CUDA events around
     every launch on its stream), against the measured L2 rate for random 16-byte
     gathers; 'alone' is the same with the three flows on one stream."""
     import torch
@@ -902,7 +902,8 @@ def sift_measure(dev, pairs=4, reps=5):
     nw4 = {SIFT_PARAMS["r"]: 1 if SIFT_S[0] <= 16 else 2, SIFT_PARAMS["r2"]: 1 if SIFT_S[1] <= 16 else 2}
     taps, tbytes = {}, {}
     for (r, l), c in counts.items():
-        t = c["full_planes"] * (2 * r + 1) ** 2
+        # incremental evaluations read the leaving and entering patch line
+        t = c["full_planes"] * (2 * r + 1) ** 2 + c["inc_planes"] * 2 * (2 * r + 1)
         taps[l] = taps.get(l, 0) + t
         tbytes[l] = tbytes.get(l, 0) + t * 16 * nw4[r]
 

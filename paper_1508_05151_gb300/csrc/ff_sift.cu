@@ -11,7 +11,6 @@
 #include <stdint.h>
 
 #include <algorithm>
-#include <atomic>
 #include <vector>
 
 #include "ff_internal.cuh"
@@ -412,81 +411,38 @@ __device__ __forceinline__ int sift_tap_words(const uint4 *a, const uint4 *b) {
 
 // E_d of source pixel (px, py) against up to two targets (X0, Y0), (X1, Y1) at
 // once: a group of 16 lanes (mask gmask) splits the (2R+1)^2 taps, tap
-// t = lane + 16 k. Taps are processed SIFT_CHUNK per lane at a time: every
-// load of a chunk is issued first (the source word once for both targets;
-// taps past the patch or of an unused target read a valid address and are
-// masked out), then the distances are summed. Sums are complete in every lane;
-// a target with use* false gets no defined cost. use0 / use1 are uniform over
-// the group.
-// CH = 1: the form for full grids (fewer registers, more resident groups); CH > 1
-// (SIFT_CHUNK): the form for grids of a few CTAs per SM, where each wavefront
-// step waits on its gathers.
-constexpr int SIFT_CHUNK = 4;
-
-template <int R, int NW4, int CH, bool TWO>
+// t = lane + 16 k; the source word of a tap is loaded once for both targets. Sums
+// are complete in every lane; a target with use* false gets no defined cost.
+// use0 / use1 are uniform over the group.
+template <int R, int NW4, bool TWO>
 __device__ __forceinline__ void sift_costs(const SiftLevel &L, int px, int py, int X0, int Y0,
                                            bool use0, int X1, int Y1, bool use1, int lg,
                                            unsigned gmask, int &e0, int &e1) {
   constexpr int D = 2 * R + 1, DD = D * D, KT = (DD + SIFT_GROUP - 1) / SIFT_GROUP;
   int a0 = 0, a1 = 0;
-  if (CH == 1) {
 #pragma unroll 4
-    for (int k = 0; k < KT; k++) {
-      const int t = lg + SIFT_GROUP * k;
-      if (t < DD) {
-        const int v = t / D - R, u = t % D - R;
-        const int xs = clampi(px + L.n * u, 0, L.W - 1), ys = clampi(py + L.n * v, 0, L.H - 1);
-        uint4 sv[NW4], tv[NW4];
-        const uint4 *src = L.Ks + ((size_t)ys * L.W + xs) * NW4;
+  for (int k = 0; k < KT; k++) {
+    const int t = lg + SIFT_GROUP * k;
+    if (t < DD) {
+      const int v = t / D - R, u = t % D - R;
+      const int xs = clampi(px + L.n * u, 0, L.W - 1), ys = clampi(py + L.n * v, 0, L.H - 1);
+      uint4 sv[NW4], tv[NW4];
+      const uint4 *src = L.Ks + ((size_t)ys * L.W + xs) * NW4;
 #pragma unroll
-        for (int w = 0; w < NW4; w++) sv[w] = __ldg(src + w);
-        if (use0) {
-          const int xt = clampi(X0 + L.n * u, 0, L.W - 1), yt = clampi(Y0 + L.n * v, 0, L.H - 1);
-          const uint4 *g = L.Kt + ((size_t)yt * L.W + xt) * NW4;
+      for (int w = 0; w < NW4; w++) sv[w] = __ldg(src + w);
+      if (use0) {
+        const int xt = clampi(X0 + L.n * u, 0, L.W - 1), yt = clampi(Y0 + L.n * v, 0, L.H - 1);
+        const uint4 *g = L.Kt + ((size_t)yt * L.W + xt) * NW4;
 #pragma unroll
-          for (int w = 0; w < NW4; w++) tv[w] = __ldg(g + w);
-          a0 += sift_tap_words<NW4>(sv, tv);
-        }
-        if (TWO && use1) {
-          const int xt = clampi(X1 + L.n * u, 0, L.W - 1), yt = clampi(Y1 + L.n * v, 0, L.H - 1);
-          const uint4 *g = L.Kt + ((size_t)yt * L.W + xt) * NW4;
-#pragma unroll
-          for (int w = 0; w < NW4; w++) tv[w] = __ldg(g + w);
-          a1 += sift_tap_words<NW4>(sv, tv);
-        }
+        for (int w = 0; w < NW4; w++) tv[w] = __ldg(g + w);
+        a0 += sift_tap_words<NW4>(sv, tv);
       }
-    }
-  } else {
-#pragma unroll 1
-    for (int k0 = 0; k0 < KT; k0 += CH) {
-      uint4 sv[CH][NW4], t0[CH][NW4], t1[CH][TWO ? NW4 : 1];
-      bool ok[CH];
+      if (TWO && use1) {
+        const int xt = clampi(X1 + L.n * u, 0, L.W - 1), yt = clampi(Y1 + L.n * v, 0, L.H - 1);
+        const uint4 *g = L.Kt + ((size_t)yt * L.W + xt) * NW4;
 #pragma unroll
-      for (int c = 0; c < CH; c++) {
-        const int t = lg + SIFT_GROUP * (k0 + c);
-        ok[c] = k0 + c < KT && t < DD;
-        const int tt = ok[c] ? t : DD / 2;  // the centre tap: always inside the patch
-        const int v = tt / D - R, u = tt % D - R;
-        const int xs = clampi(px + L.n * u, 0, L.W - 1), ys = clampi(py + L.n * v, 0, L.H - 1);
-        const uint4 *src = L.Ks + ((size_t)ys * L.W + xs) * NW4;
-        const int x0 = clampi(X0 + L.n * u, 0, L.W - 1), y0 = clampi(Y0 + L.n * v, 0, L.H - 1);
-        const uint4 *g0 = L.Kt + ((size_t)y0 * L.W + x0) * NW4;
-#pragma unroll
-        for (int w = 0; w < NW4; w++) {
-          sv[c][w] = __ldg(src + w);
-          t0[c][w] = __ldg(g0 + w);
-        }
-        if (TWO) {
-          const int x1 = clampi(X1 + L.n * u, 0, L.W - 1), y1 = clampi(Y1 + L.n * v, 0, L.H - 1);
-          const uint4 *g1 = L.Kt + ((size_t)y1 * L.W + x1) * NW4;
-#pragma unroll
-          for (int w = 0; w < NW4; w++) t1[c][w] = __ldg(g1 + w);
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < CH; c++) {
-        if (ok[c] && use0) a0 += sift_tap_words<NW4>(sv[c], t0[c]);
-        if (TWO && ok[c] && use1) a1 += sift_tap_words<NW4>(sv[c], t1[c]);
+        for (int w = 0; w < NW4; w++) tv[w] = __ldg(g + w);
+        a1 += sift_tap_words<NW4>(sv, tv);
       }
     }
   }
@@ -499,19 +455,19 @@ __device__ __forceinline__ void sift_costs(const SiftLevel &L, int px, int py, i
   e1 = a1;
 }
 
-template <int R, int NW4, int CH>
+template <int R, int NW4>
 __device__ __forceinline__ int sift_cost(const SiftLevel &L, int px, int py, int X, int Y, int lg,
                                          unsigned gmask) {
   int e0, e1;
-  sift_costs<R, NW4, CH, false>(L, px, py, X, Y, true, X, Y, false, lg, gmask, e0, e1);
+  sift_costs<R, NW4, false>(L, px, py, X, Y, true, X, Y, false, lg, gmask, e0, e1);
   return e0;
 }
 
-template <int R, int NW4, int CH>
+template <int R, int NW4>
 __device__ __forceinline__ void sift_cost2(const SiftLevel &L, int px, int py, int X0, int Y0,
                                            bool use0, int X1, int Y1, bool use1, int lg,
                                            unsigned gmask, int &e0, int &e1) {
-  sift_costs<R, NW4, CH, true>(L, px, py, X0, Y0, use0, X1, Y1, use1, lg, gmask, e0, e1);
+  sift_costs<R, NW4, true>(L, px, py, X0, Y0, use0, X1, Y1, use1, lg, gmask, e0, e1);
 }
 
 struct SiftKdQuery {
@@ -525,7 +481,7 @@ struct SiftKdQuery {
 
 // Eq. 1 / Eq. 4 with the SIFT flow data term: descend the tree with the grid
 // point's WHT vector, rerank the leaf by E_d (ties to the lower pixel index).
-template <int R, int NW4, int CH>
+template <int R, int NW4>
 __global__ void __launch_bounds__(256) k_sift_kd_query(SiftLevel L, SiftKdQuery Q) {
   const int G = L.Gx * L.Gy;
   const int g = (blockIdx.x * blockDim.x + threadIdx.x) / SIFT_GROUP;
@@ -558,7 +514,7 @@ __global__ void __launch_bounds__(256) k_sift_kd_query(SiftLevel L, SiftKdQuery 
       if (!use[i] && (i == 0 || c + 1 < e) && lg == 0) raise_status(Q.status, DEV_ERR_BOUNDS, g, c + i);
     }
     int cost[2];
-    sift_cost2<R, NW4, CH>(L, px, py, use[0] ? idx[0] % L.W : 0, use[0] ? idx[0] / L.W : 0, use[0],
+    sift_cost2<R, NW4>(L, px, py, use[0] ? idx[0] % L.W : 0, use[0] ? idx[0] / L.W : 0, use[0],
                        use[1] ? idx[1] % L.W : 0, use[1] ? idx[1] / L.W : 0, use[1], lg, gmask,
                        cost[0], cost[1]);
     for (int i = 0; i < 2; i++)
@@ -575,7 +531,7 @@ __global__ void __launch_bounds__(256) k_sift_kd_query(SiftLevel L, SiftKdQuery 
 
 // Sec. 3.2 level transition: grid points with both coordinates even take the
 // coarser level's flow (cost re-evaluated), all others start without a flow.
-template <int R, int NW4, int CH>
+template <int R, int NW4>
 __global__ void __launch_bounds__(256) k_sift_seed(SiftLevel L, uint32_t *flow, int32_t *cost) {
   const int G = L.Gx * L.Gy;
   const int g = (blockIdx.x * blockDim.x + threadIdx.x) / SIFT_GROUP;
@@ -588,7 +544,7 @@ __global__ void __launch_bounds__(256) k_sift_seed(SiftLevel L, uint32_t *flow, 
   if (!(gx & 1) && !(gy & 1)) {
     const uint32_t fc = L.flow_coarse[(size_t)(gy >> 1) * L.Gxc + (gx >> 1)];
     const int X = clampi(px + flow_dx(fc), 0, L.W - 1), Y = clampi(py + flow_dy(fc), 0, L.H - 1);
-    c = sift_cost<R, NW4, CH>(L, px, py, X, Y, lg, gmask);
+    c = sift_cost<R, NW4>(L, px, py, X, Y, lg, gmask);
     f = pack_flow(X - px, Y - py);
   }
   if (lg == 0) {
@@ -598,7 +554,7 @@ __global__ void __launch_bounds__(256) k_sift_seed(SiftLevel L, uint32_t *flow, 
 }
 
 // Random search step (Sec. 3.1): F + O_rnd, kept if E_d decreases; in place.
-template <int R, int NW4, int CH>
+template <int R, int NW4>
 __global__ void __launch_bounds__(256) k_sift_rs(SiftLevel L, uint32_t *flow, int32_t *cost,
                                                  int step, int level, int Rn, uint64_t seed) {
   const int G = L.Gx * L.Gy;
@@ -614,11 +570,83 @@ __global__ void __launch_bounds__(256) k_sift_rs(SiftLevel L, uint32_t *flow, in
   rs_offset(seed, L.flow_id, level, step, gx, gy, Rn, dx, dy);
   const int X = clampi(px + flow_dx(f) + dx, 0, L.W - 1);
   const int Y = clampi(py + flow_dy(f) + dy, 0, L.H - 1);
-  const int e = sift_cost<R, NW4, CH>(L, px, py, X, Y, lg, gmask);
+  const int e = sift_cost<R, NW4>(L, px, py, X, Y, lg, gmask);
   if (e < c && lg == 0) {
     flow[g] = pack_flow(X - px, Y - py);
     cost[g] = e;
   }
+}
+
+// Incremental costs. A propagation candidate repeats the flow f of a neighbour q
+// one grid step away (q = p + sd n along x or y). When p + f needs no clamping, the
+// candidate's flow is f itself, and since every tap is clamped in absolute
+// coordinates, E_d(p, f) = E_d(q, f) minus the patch column (or row) that q covers
+// and p does not, plus the one p covers and q does not: offsets sd (R + 1) and
+// -sd R. That is 2 (2R+1) taps instead of (2R+1)^2, exact in integers.
+//
+// Tap t of a candidate's list: the whole patch (mode 0), or the leaving (sign -1,
+// t < 2R+1) and entering (sign +1) line of a horizontal (mode 1) or vertical
+// (mode 2) source at offset sd.
+template <int R>
+__device__ __forceinline__ void pass_tap(int mode, int sd, int t, int &u, int &v, int &sign) {
+  constexpr int D = 2 * R + 1;
+  if (mode == 0) {
+    u = t % D - R;
+    v = t / D - R;
+    sign = 1;
+    return;
+  }
+  const bool enter = t >= D;
+  const int k = (enter ? t - D : t) - R, edge = enter ? -sd * R : sd * (R + 1);
+  sign = enter ? 1 : -1;
+  u = mode == 1 ? edge : k;
+  v = mode == 1 ? k : edge;
+}
+
+// The tap sums of both candidates of a pass (ntap[c] taps of mode[c]; 0 for an
+// unused candidate), split over the 16 lanes of a group, one round of 16 taps at a
+// time with both candidates' gathers issued before use. Complete in every lane.
+template <int R, int NW4>
+__device__ __forceinline__ void sift_pass_sums(const SiftLevel &L, int px, int py, const int *X,
+                                               const int *Y, const int *ntap, const int *mode,
+                                               const int *sd, int lg, unsigned gmask,
+                                               int *sum) {
+  int acc[2] = {0, 0};
+  const int tmax = max(ntap[0], ntap[1]);
+#pragma unroll 2
+  for (int t0 = 0; t0 < tmax; t0 += SIFT_GROUP) {
+    const int t = t0 + lg;
+    uint4 sv[2][NW4], tv[2][NW4];
+    int sg[2];
+    bool ok[2];
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+      ok[c] = t < ntap[c];
+      int u, v;
+      pass_tap<R>(mode[c], sd[c], ok[c] ? t : 0, u, v, sg[c]);
+      if (ok[c]) {
+        const int xs = clampi(px + L.n * u, 0, L.W - 1), ys = clampi(py + L.n * v, 0, L.H - 1);
+        const int xt = clampi(X[c] + L.n * u, 0, L.W - 1), yt = clampi(Y[c] + L.n * v, 0, L.H - 1);
+        const uint4 *a = L.Ks + ((size_t)ys * L.W + xs) * NW4;
+        const uint4 *b = L.Kt + ((size_t)yt * L.W + xt) * NW4;
+#pragma unroll
+        for (int w = 0; w < NW4; w++) {
+          sv[c][w] = __ldg(a + w);
+          tv[c][w] = __ldg(b + w);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 2; c++)
+      if (ok[c]) acc[c] += sg[c] * sift_tap_words<NW4>(sv[c], tv[c]);
+  }
+#pragma unroll
+  for (int o = SIFT_GROUP / 2; o > 0; o >>= 1) {
+    acc[0] += __shfl_xor_sync(gmask, acc[0], o);
+    acc[1] += __shfl_xor_sync(gmask, acc[1], o);
+  }
+  sum[0] = acc[0];
+  sum[1] = acc[1];
 }
 
 // Sources of pass s (Fig. 3c reading): horizontal (dx, 0) and vertical (0, dy).
@@ -630,14 +658,14 @@ __constant__ int c_pass_src[4][2] = {{-1, -1}, {1, 1}, {1, -1}, {-1, 1}};
 // two sources lie on the previous diagonal, so this equals the sequential scan),
 // one 8-lane group per point of a diagonal. Sources outside the tile are read
 // from the start-of-pass state (fin, cin); results go to (fout, cout).
-template <int R, int NW4, int CH>
+template <int R, int NW4>
 __global__ void __launch_bounds__(SIFT_GROUP * MAX_TILE) k_sift_pass(SiftLevel L, const uint32_t *fin,
                                                    const int32_t *cin, uint32_t *fout,
                                                    int32_t *cout, int s, int T) {
   __shared__ uint32_t sf[MAX_TILE * MAX_TILE];
   __shared__ int32_t sc[MAX_TILE * MAX_TILE];
-  __shared__ unsigned s_evals;
-  if (threadIdx.x == 0) s_evals = 0;
+  __shared__ unsigned s_inc, s_full;
+  if (threadIdx.x == 0) s_inc = s_full = 0;
   const int off = (s & 1) * (T / 2);
   const int ntx = (L.Gx + off + T - 1) / T;
   const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
@@ -664,25 +692,38 @@ __global__ void __launch_bounds__(SIFT_GROUP * MAX_TILE) k_sift_pass(SiftLevel L
       int c = sc[li];
       // candidates in order: the horizontal source, then the vertical one
       bool use[2];
-      int X[2], Y[2];
+      int X[2], Y[2], base[2], ntap[2], mode[2];
+      const int sd[2] = {sx, sy};
 #pragma unroll
       for (int cand = 0; cand < 2; cand++) {
         const int qx = gx + (cand == 0 ? sx : 0), qy = gy + (cand == 0 ? 0 : sy);
         use[cand] = qx >= 0 && qx < L.Gx && qy >= 0 && qy < L.Gy;
-        X[cand] = Y[cand] = 0;
+        X[cand] = Y[cand] = base[cand] = ntap[cand] = mode[cand] = 0;
         if (use[cand]) {
           const bool inside = qx >= x0 && qx < x1 && qy >= y0 && qy < y1;
           const size_t qg = (size_t)qy * L.Gx + qx;
           const uint32_t fq = inside ? sf[(qy - y0) * T + (qx - x0)] : fin[qg];
           const int cq = inside ? sc[(qy - y0) * T + (qx - x0)] : cin[qg];
           use[cand] = cq != COST_UNSET;
-          X[cand] = clampi(px + flow_dx(fq), 0, L.W - 1);
-          Y[cand] = clampi(py + flow_dy(fq), 0, L.H - 1);
+          const int xu = px + flow_dx(fq), yu = py + flow_dy(fq);
+          X[cand] = clampi(xu, 0, L.W - 1);
+          Y[cand] = clampi(yu, 0, L.H - 1);
+          if (use[cand]) {
+            const bool inc = X[cand] == xu && Y[cand] == yu;  // the neighbour's flow unchanged
+            mode[cand] = inc ? 1 + cand : 0;
+            base[cand] = inc ? cq : 0;
+            ntap[cand] = inc ? 2 * (2 * R + 1) : (2 * R + 1) * (2 * R + 1);
+          }
         }
       }
       int e[2];
-      sift_cost2<R, NW4, CH>(L, px, py, X[0], Y[0], use[0], X[1], Y[1], use[1], lg, gmask, e[0], e[1]);
-      if (L.evals && lg == 0) atomicAdd(&s_evals, (unsigned)use[0] + (unsigned)use[1]);
+      sift_pass_sums<R, NW4>(L, px, py, X, Y, ntap, mode, sd, lg, gmask, e);
+      e[0] += base[0];
+      e[1] += base[1];
+      if (L.evals && lg == 0) {
+        atomicAdd(&s_inc, (unsigned)(mode[0] != 0) + (unsigned)(mode[1] != 0));
+        atomicAdd(&s_full, (unsigned)(use[0] && mode[0] == 0) + (unsigned)(use[1] && mode[1] == 0));
+      }
 #pragma unroll
       for (int cand = 0; cand < 2; cand++)
         if (use[cand] && e[cand] < c) {
@@ -702,45 +743,23 @@ __global__ void __launch_bounds__(SIFT_GROUP * MAX_TILE) k_sift_pass(SiftLevel L
     fout[g] = sf[ly * T + lx];
     cout[g] = sc[ly * T + lx];
   }
-  // evaluations are full E_d with targets gathered from the colour array
-  if (L.evals && threadIdx.x == 0 && s_evals) atomicAdd(L.evals + 3, (unsigned long long)s_evals);
+  // incremental (kind 1) and full (kind 3) evaluations, targets gathered from the
+  // colour array
+  if (L.evals && threadIdx.x == 0) {
+    if (s_inc) atomicAdd(L.evals + 1, (unsigned long long)s_inc);
+    if (s_full) atomicAdd(L.evals + 3, (unsigned long long)s_full);
+  }
 }
 
 // ------------------------------------------------------------ launchers ------
-#define FF_DISPATCH_SIFT(r, nw4, ch, KERNEL, GRID, BLOCK, SMEM, ST, ...)                \
+#define FF_DISPATCH_SIFT(r, nw4, KERNEL, GRID, BLOCK, SMEM, ST, ...)                    \
   do {                                                                                 \
     FF_DISPATCH_R(r, {                                                                 \
-      if ((nw4) == 1 && (ch) == 1) KERNEL<RR, 1, 1><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__); \
-      else if ((nw4) == 1) KERNEL<RR, 1, SIFT_CHUNK><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__); \
-      else if ((ch) == 1) KERNEL<RR, 2, 1><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);     \
-      else KERNEL<RR, 2, SIFT_CHUNK><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);           \
+      if ((nw4) == 1) KERNEL<RR, 1><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);            \
+      else KERNEL<RR, 2><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);                       \
     });                                                                                \
     FF_CHECK_LAUNCH();                                                                 \
   } while (0)
-
-// The fully parallel kernels (kd query, seeding, random search) in the CH = 1 form.
-#define FF_DISPATCH_SIFT1(r, nw4, KERNEL, GRID, BLOCK, SMEM, ST, ...)                   \
-  do {                                                                                 \
-    FF_DISPATCH_R(r, {                                                                 \
-      if ((nw4) == 1) KERNEL<RR, 1, 1><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);         \
-      else KERNEL<RR, 2, 1><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);                    \
-    });                                                                                \
-    FF_CHECK_LAUNCH();                                                                 \
-  } while (0)
-
-// Streaming multiprocessors of the current device (cached per device).
-static int sift_sm_count() {
-  static std::atomic<int> cache[64];
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-  int v = cache[dev].load(std::memory_order_relaxed);
-  if (v == 0) {
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
-      v = 1;
-    cache[dev].store(v, std::memory_order_relaxed);
-  }
-  return v;
-}
 
 static int sift_nw4(int S) { return S <= 16 ? 1 : 2; }
 static bool sift_S_ok(int S) { return S >= 3 && S <= SIFT_MAX_S && S % 3 == 0; }
@@ -804,7 +823,7 @@ static SiftLevel make_sift_level(const uint4 *Ks, const uint4 *Kt, int W, int H,
 ff_status launch_sift_kd_query(const SiftLevel &L, const SiftKdQuery &Q, int r, int nw4,
                                cudaStream_t st) {
   const int G = L.Gx * L.Gy;
-  FF_DISPATCH_SIFT1(r, nw4, k_sift_kd_query, grid_blocks((long long)G * SIFT_GROUP), 256, 0, st, L,
+  FF_DISPATCH_SIFT(r, nw4, k_sift_kd_query, grid_blocks((long long)G * SIFT_GROUP), 256, 0, st, L,
                    Q);
   return FF_OK;
 }
@@ -816,7 +835,7 @@ ff_status run_sift_level(const SiftLevel &L, int r, int nw4, uint32_t *fa, int32
                          cudaStream_t st) {
   const int G = L.Gx * L.Gy;
   const int blocks = grid_blocks((long long)G * SIFT_GROUP);
-  if (L.flow_coarse) FF_DISPATCH_SIFT1(r, nw4, k_sift_seed, blocks, 256, 0, st, L, fa, ca);
+  if (L.flow_coarse) FF_DISPATCH_SIFT(r, nw4, k_sift_seed, blocks, 256, 0, st, L, fa, ca);
   int level = 0;
   while ((1 << level) < L.n) level++;
   SiftLevel Lp = L;  // the pass kernels count their evaluations when profiling
@@ -826,15 +845,12 @@ ff_status run_sift_level(const SiftLevel &L, int r, int nw4, uint32_t *fa, int32
   for (int s = 0; s < 4; s++) {
     const int off = (s & 1) * (tile / 2);
     const int ntiles = ((L.Gx + off + tile - 1) / tile) * ((L.Gy + off + tile - 1) / tile);
-    // at most about two CTAs per SM: the wavefront steps wait on their gathers,
-    // so each lane issues a chunk of taps' loads at once
-    const int ch = (long long)ntiles * SIFT_GROUP * tile <= 512ll * sift_sm_count() ? SIFT_CHUNK : 1;
     if (prof_enabled()) prof_begin(st, level);
-    FF_DISPATCH_SIFT(r, nw4, ch, k_sift_pass, ntiles, SIFT_GROUP * tile, 0, st, Lp, f[s & 1],
+    FF_DISPATCH_SIFT(r, nw4, k_sift_pass, ntiles, SIFT_GROUP * tile, 0, st, Lp, f[s & 1],
                      c[s & 1], f[(s + 1) & 1], c[(s + 1) & 1], s, tile);
     if (prof_enabled()) prof_end(st);
     if (s < 3 && s < n_rs)
-      FF_DISPATCH_SIFT1(r, nw4, k_sift_rs, blocks, 256, 0, st, L, f[(s + 1) & 1], c[(s + 1) & 1],
+      FF_DISPATCH_SIFT(r, nw4, k_sift_rs, blocks, 256, 0, st, L, f[(s + 1) & 1], c[(s + 1) & 1],
                        s, level, R * L.n, seed);
   }
   return FF_OK;
