@@ -710,7 +710,8 @@ def run_ours(args):
     batch = batch_measure(dev, PARAMS, pk, flush) if (rank == 0 and not args.no_batch) else None
     quality = field_quality(dev) if (rank == 0 and not args.no_quality) else None
     subpel = subpel_quality(dev) if (rank == 0 and not args.no_quality) else None
-    sift = sift_measure(dev) if (rank == 0 and not args.no_sift) else None
+    sift = (sift_measure(dev, with_oracle=not args.no_cpu_baseline)
+            if (rank == 0 and not args.no_sift) else None)
     learned = {}
     if rank == 0 and not args.no_learned:
         # the training workload at its stated size: 4096 generated pairs, 256 held out
@@ -842,7 +843,7 @@ def sift_bases(dev, seeds=(9000, 9001)):
     return b1, o1, b2, o2, (time.perf_counter() - t0) * 1e3
 
 
-def sift_measure(dev, pairs=4, reps=5):
+def sift_measure(dev, pairs=4, reps=5, with_oracle=True):
     """Sec. 3.3 / Sec. 5: the whole path with the SIFT flow data term on generated
     KITTI-shaped 1242x375 pairs in the paper's KITTI setting (r = 3, r2 = 2, S = 12,
     S2 = 18, eps/e/s = 1/9/150), beside the census path with the KITTI preset
@@ -850,6 +851,8 @@ def sift_measure(dev, pairs=4, reps=5):
     ff_flow_fields, CUDA events, median of `reps` after a warm-up run), and the raw
     forward field's inliers@3px / EPE against the generator's ground truth on
     non-occluded pixels. The bases are fitted once on two other generated frames.
+    With `with_oracle` (the CPU baseline), the C oracle of the same path times the
+    first pair on the host, one thread per flow.
 
     Roofline of the dominant kernel (k_sift_pass, the tiled propagation passes):
     target bytes gathered (evaluations from the device counters: (2r+1)^2 taps for
@@ -951,8 +954,27 @@ def sift_measure(dev, pairs=4, reps=5):
             "per_level": rows,
             "alone": {"achieved": round(gbs_a, 1), "frac": round(gbs_a / peak, 4),
                       "per_level": rows_a}}
+    # CPU baseline: the C oracle of the same path on the first pair, one thread per
+    # flow, with bases the oracle fits itself on 311x94 crops of the training frames
+    oracle_s = None
+    if with_oracle:
+        import oracle
+        acc = None
+        for sd in (9000, 9001):
+            crop = synth.workload_pair("kitti_1242x375", sd)["I1"][:94, :311]
+            acc = oracle.sift_moments(oracle.sift_descriptors(crop), acc=acc)
+        P1, P2 = oracle.sift_pca(*acc, SIFT_S[0]), oracle.sift_pca(*acc, SIFT_S[1])
+        t0 = time.perf_counter()
+        oracle.sift_flow_fields(ps[0]["I1"], ps[0]["I2"], P1["basis"], P1["offset"],
+                                P2["basis"], P2["offset"], params=SIFT_PARAMS, threads=3)
+        oracle_s = time.perf_counter() - t0
     return {"workload": f"{pairs} generated KITTI-shaped 1242x375 pairs (seeds 5000..), "
                         "bases fitted on two other generated frames",
+            "cpu_baseline": None if oracle_s is None else {
+                "kind": "oracle", "value": round(oracle_s * 1e3, 1), "unit": "ms/pair",
+                "cores": 3, "host_cores": usable_cores(),
+                "sample": "the first pair, one thread per flow; bases fitted by the oracle on "
+                          "311x94 crops of the training frames"},
             "fit_ms": round(fit_ms, 2), "arms": arms,
             "speed_ratio_census_over_sift": round(arms["census"]["ms_per_pair"]
                                                   / arms["sift_flow"]["ms_per_pair"], 3),
