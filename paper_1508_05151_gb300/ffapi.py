@@ -465,7 +465,9 @@ def ff_sift_smooth(col, n):
     return torch.stack([ff_smooth(g.contiguous(), n) for g in col])
 
 
-def ff_sift_kdtree_init(tree, leaf, src_img, col_src, col_tgt, n, r):
+def ff_sift_kdtree_init(tree, leaf, src_img, col_src, col_tgt, n, r, with_status=False):
+    """Initial flow at the grid of spacing n with the SIFT flow data term. Returns
+    (flow, cost), plus the device status (code, x, y) with with_status."""
     G3, H, W = col_src.shape[:3]
     Gx, Gy = _grid(W, H, n)
     dev = src_img.device
@@ -477,6 +479,10 @@ def ff_sift_kdtree_init(tree, leaf, src_img, col_src, col_tgt, n, r):
     _check("ff_sift_kdtree_init", lib().ff_sift_kdtree_init(
         _dev(tree["perm"]), _dev(sd), _dev(sv), leaf, _dev(src_img), _dev(col_src),
         _dev(col_tgt), 3 * G3, W, H, n, r, _dev(flow), _dev(cost), wp, wn, _stream()))
+    if with_status:
+        code, x, y = C.c_uint32(), C.c_int32(), C.c_int32()
+        lib().ff_device_status(wp, C.byref(code), C.byref(x), C.byref(y), _stream())
+        return flow, cost, (code.value, x.value, y.value)
     return flow, cost
 
 

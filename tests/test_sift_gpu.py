@@ -131,6 +131,28 @@ def test_kd_init_bit_exact(n, r, S):
     assert np.array_equal(cpu(gf).astype(np.int32), of)
 
 
+def test_kd_init_reports_a_corrupt_tree():
+    """The SIFT kd query's own checks: a split dimension outside [0, 27) or a leaf
+    entry outside [0, N) is skipped and reported as device status 1 with the grid
+    point; a sound tree reports 0."""
+    I1, I2 = vimg(51, 48, 64), vimg(52, 48, 64)
+    n, r, S = 4, 3, 12
+    B, off = oracle_basis([I1, I2], S)
+    K1, K2 = tg(_colours(I1, B, off, n)), tg(_colours(I2, B, off, n))
+    T = ffapi.ff_kdtree_build(ffapi.ff_features(tg(I2), r), 8)
+    _, _, st = ffapi.ff_sift_kdtree_init(T, 8, tg(I1), K1, K2, n, r, with_status=True)
+    assert st == (0, 0, 0)
+    sd, _ = T["_keep"]
+    sd[0] = 99
+    _, _, st = ffapi.ff_sift_kdtree_init(T, 8, tg(I1), K1, K2, n, r, with_status=True)
+    assert st[0] == 1 and st[2] == 0
+    T2 = ffapi.ff_kdtree_build(ffapi.ff_features(tg(I2), r), 8)
+    T2["perm"][:] = T2["N"] + 7
+    _, c, st = ffapi.ff_sift_kdtree_init(T2, 8, tg(I1), K1, K2, n, r, with_status=True)
+    assert st[0] == 1 and 0 <= st[2] < T2["N"]
+    assert bool((c == O.COST_UNSET).all())
+
+
 @pytest.mark.parametrize("W,H,n,r,S,tile,n_rs,seeded", [
     (128, 96, 1, 3, 12, 16, 3, True),
     (128, 96, 2, 2, 18, 16, 3, True),
