@@ -90,17 +90,19 @@ struct ConvArgs {
 // of the B^T tile straight into shared memory with cp.async, in the no-swizzle
 // K-major core-matrix layout (per 16-deep slice: 8 rows x 16 bytes per core
 // matrix, the two core matrices of a row group 128 B apart along K, row groups
-// 256 B apart). Taps outside the image are zero-filled by the copy. Four stages
-// of 16, filled three ahead: while one thread issues the tcgen05.mma of a stage
-// (BF16 x BF16 -> FP32, the accumulator in tensor memory) the next three stages'
+// 256 B apart). Taps outside the image are zero-filled by the copy. Six stages
+// of 16, filled four ahead: while one thread issues the tcgen05.mma of a stage
+// (BF16 x BF16 -> FP32, the accumulator in tensor memory) the next four stages'
 // copies are in flight; tcgen05.commit signals a stage's mbarrier when its MMA is
-// done, and the stage is refilled. (Stages of 64 filled two ahead, 96 KB per CTA,
-// measured slower: 0.278 against 0.263 ms for the forward pass of 64 pairs.) The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
+// done, and the stage is refilled, so a refill waits on the MMA of two steps
+// before. (Forward pass of 64 pairs: 0.248 ms, against 0.260 with four stages
+// filled three ahead, 0.295 with eight filled four ahead, and 0.278 with stages
+// of 64 filled two ahead, 96 KB per CTA.) The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
 // lanes = tile rows 32w..32w+31) and writes 8 channels of a pixel as one vector
 // store.
 constexpr int UMMA_M = 128, UMMA_N = 64, UMMA_K = 16;
 constexpr int UMMA_A_BYTES = UMMA_M * UMMA_K * 2, UMMA_B_BYTES = UMMA_N * UMMA_K * 2;
-constexpr int CONV_STAGES = 4, CONV_AHEAD = 3, CONV_SUB = 1;  // stages, fill distance, MMAs per stage
+constexpr int CONV_STAGES = 6, CONV_AHEAD = 4, CONV_SUB = 1;  // stages, fill distance, MMAs per stage
 constexpr int CONV_KSTEP = UMMA_K * CONV_SUB;
 constexpr int CONV_A_STAGE = UMMA_A_BYTES * CONV_SUB, CONV_B_STAGE = UMMA_B_BYTES * CONV_SUB;
 constexpr size_t CONV_SMEM = (size_t)CONV_STAGES * (CONV_A_STAGE + CONV_B_STAGE);
@@ -201,16 +203,20 @@ __global__ void __launch_bounds__(128) k_conv_umma(ConvArgs a, DeviceStatus *sta
   const int bn = tid & 63, bq = tid >> 6;
   const __nv_bfloat16 *brow = a.Bt + (size_t)(n0 + bn) * a.Kp;
   const uint32_t sA0 = smem_u32(conv_smem), sB0 = sA0 + CONV_STAGES * CONV_A_STAGE;
+  // (tap, channel) of the first 8-channel group of the next stage to issue; stages
+  // are issued in order, so it advances by CONV_KSTEP channels per stage (Ca, the
+  // padded channel count, is a multiple of 8)
+  int nx_tap = 0, nx_c0 = 0;
   auto issue = [&](int s) {  // the copies of stage s (K from s * CONV_KSTEP) into buffer s % CONV_STAGES
     const int buf = s % CONV_STAGES, k0 = s * CONV_KSTEP;
     const uint32_t aS = sA0 + buf * CONV_A_STAGE, bS = sB0 + buf * CONV_B_STAGE;
+    int tap = nx_tap, c0 = nx_c0;
 #pragma unroll
     for (int g = 0; g < CONV_KSTEP / 8; g++) {
       const int kk = k0 + 8 * g;
       const __nv_bfloat16 *src = a.act;
       int bytes = 0;
       if (pb >= 0 && kk < a.K) {
-        const int tap = kk / a.Ca, c0 = kk - tap * a.Ca;
         const int yy = py + a.sign * ((tap / 3) - 1) * a.dil;
         const int xx = px + a.sign * ((tap % 3) - 1) * a.dil;
         if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
@@ -219,7 +225,14 @@ __global__ void __launch_bounds__(128) k_conv_umma(ConvArgs a, DeviceStatus *sta
         }
       }
       cp_async16(aS + (g >> 1) * UMMA_A_BYTES + umma_off(tid, 8 * (g & 1)), src, bytes);
+      c0 += 8;
+      if (c0 >= a.Ca) {
+        c0 -= a.Ca;
+        tap++;
+      }
     }
+    nx_tap = tap;
+    nx_c0 = c0;
 #pragma unroll
     for (int i = 0; i < CONV_SUB; i++) {  // piece (row bn, 16-k slice, half) of the B^T stage
       const int rest = bq + 2 * i, sub = rest >> 1, e = rest & 1;
@@ -239,19 +252,19 @@ __global__ void __launch_bounds__(128) k_conv_umma(ConvArgs a, DeviceStatus *sta
     if (s < nsteps) issue(s);
     cp_async_commit();
   }
+  // One CTA barrier per step. Before it, every thread's copies of stage `step` have
+  // landed, and thread 0 (alone: it tracks the mbarrier phases) has seen the MMA that
+  // last read the buffer of stage step + CONV_AHEAD complete; after it, thread 0
+  // issues stage `step`'s MMA and every thread the copies of stage step + CONV_AHEAD.
   for (int step = 0; step < nsteps; step++) {
     const int ns = step + CONV_AHEAD;
-    if (ns < nsteps) {
-      const int nb = ns % CONV_STAGES;
-      if (ns >= CONV_STAGES) {  // the MMAs of step ns - CONV_STAGES read stage nb
-        if (!mbar_wait(smem_u32(&mbar[nb]), (phase >> nb) & 1u)) s_fail = 1;
-        phase ^= 1u << nb;
-      }
-      issue(ns);
-    }
-    cp_async_commit();
-    cp_async_wait<CONV_AHEAD>();  // this thread's copies of stage `step` landed
+    cp_async_wait<CONV_AHEAD - 1>();  // this thread's copies of stage `step` landed
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    if (tid == 0 && ns < nsteps && ns >= CONV_STAGES) {  // the MMA of step ns - CONV_STAGES
+      const int nb = ns % CONV_STAGES;
+      if (!mbar_wait(smem_u32(&mbar[nb]), (phase >> nb) & 1u)) s_fail = 1;
+      phase ^= 1u << nb;
+    }
     __syncthreads();
     if (tid == 0) {
       const int buf = step % CONV_STAGES;
@@ -271,10 +284,12 @@ __global__ void __launch_bounds__(128) k_conv_umma(ConvArgs a, DeviceStatus *sta
                        smem_u32(&mbar[buf]))
                    : "memory");
     }
+    if (ns < nsteps) issue(ns);
+    cp_async_commit();
   }
   cp_async_wait<0>();
   // the last MMAs (commits complete in order, so every earlier MMA is done too)
-  if (nsteps > 0) {
+  if (tid == 0 && nsteps > 0) {
     const int lb = (nsteps - 1) % CONV_STAGES;
     if (!mbar_wait(smem_u32(&mbar[lb]), (phase >> lb) & 1u)) s_fail = 1;
   }
