@@ -161,6 +161,7 @@ def test_kd_init_reports_a_corrupt_tree():
     (77, 53, 4, 8, 30, 32, 1, False),
     (150, 100, 1, 3, 12, 2, 0, True),
     (33, 17, 2, 2, 18, 6, 3, True),
+    (600, 400, 1, 2, 12, 8, 3, True),   # 3750 tiles, more than one wave of CTAs
 ])
 def test_search_level_bit_exact(W, H, n, r, S, tile, n_rs, seeded):
     I1, I2 = vimg(41 + W, H, W), vimg(42 + W, H, W)
