@@ -511,8 +511,8 @@ ff_status ff_device_status(const void *ws, uint32_t *code, int32_t *x, int32_t *
  *                        in the kernel's staged shared-memory window, 1 incremental
  *                        with the target gathered from the census planes, 2 full
  *                        E_d in the window, 3 full E_d gathered (the SIFT flow
- *                        pass kernels count every evaluation here); 180 uint64 in
- *                        total. An incremental evaluation reads 2 (2r+1) target
+ *                        pass kernels gather every target from the colour array:
+ *                        kinds 1 and 3); 180 uint64 in total. An incremental evaluation reads 2 (2r+1) target
  *                        taps, a full one (2r+1)^2. Synchronises the device. */
 ff_status ff_profile_enable(int on);
 ff_status ff_profile_reset(void);
