@@ -194,6 +194,24 @@ def test_colors_hand_basis_and_centring(ffo):
     assert (col == 128).all()
 
 
+def test_pca_offsets_centre_a_fractional_mean(ffo):
+    # Over the descriptors the offsets were fitted on, the mean unfloored projection
+    # B q + o equals B mu + o, which rounding B mu half up puts in (2048 - 1/2,
+    # 2048 + 1/2] (exact fractions; 3 descriptors give a mean in thirds).
+    from fractions import Fraction
+    rng = np.random.default_rng(13)
+    rows = rng.integers(0, 256, size=(3, 128))
+    s = rows.astype(np.uint64).sum(0)
+    B = rng.integers(-3000, 3000, (9, 128)).astype(np.int16)
+    off = ffo.sift_pca_offset(B, s, 3)
+    fr = []
+    for k in range(9):
+        m = Fraction(int(np.dot(B[k].astype(np.int64), s.astype(np.int64))), 3) + int(off[k])
+        assert Fraction(-1, 2) < m - 2048 <= Fraction(1, 2)
+        fr.append(m - 2048)
+    assert any(abs(f) > Fraction(1, 4) for f in fr)  # the case is not trivially integral
+
+
 # -------------------------------------------------------------------- cost ----
 def test_tap_is_fixed_point_euclidean_norm(ffo):
     a = np.zeros(12, np.uint8)
