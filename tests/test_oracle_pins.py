@@ -357,6 +357,26 @@ def test_tiled_schedule_two_tile_hand_case(ffo):
         assert all(_line_search(ffo, L, vertical, 0)[0])
 
 
+def test_random_search_radius_scales_with_the_level(ffo):
+    # Sec. 3.2: the random-search radius at spacing n is R_n = R n. From an all-zero
+    # field on a pair shifted by 4 px, at n = 4 with R = 1, propagation alone keeps
+    # the zero flow; only offsets of up to +-4 px reach the true flow, and
+    # propagation then spreads it. With an unscaled radius (+-1) it is never found.
+    W, H, n, sh = 128, 96, 4, 4
+    canvas = synth._to_u8(synth.value_noise(np.random.default_rng(3), H + 40, W + 40))
+    I1 = canvas[20:20 + H, 20:20 + W]
+    I2 = canvas[20:20 + H, 20 - sh:20 - sh + W]
+    C1, C2 = ffo.census(ffo.smooth(I1, n), n), ffo.census(ffo.smooth(I2, n), n)
+    Gxc, Gyc = ffo.grid(W, H, 2 * n)
+    Gx, Gy = ffo.grid(W, H, n)
+    inner = np.zeros((Gy, Gx), bool)
+    inner[2:-2, 2:-3] = True
+    for seed in (0, 1):
+        f, _, _ = ffo.search_level(C1, C2, n, 2, flow_coarse=np.zeros((Gyc, Gxc, 2), np.int32),
+                                   tile=16, n_rs=3, R=1, seed=seed, flow_id=0)
+        assert ((f[..., 0] == sh) & (f[..., 1] == 0))[inner].mean() >= 0.9
+
+
 def test_tiled_schedule_reduces_to_sequential(ffo):
     # tiled(T) with T >= 2 max(Gx, Gy) keeps the whole grid in one tile in every
     # pass (odd passes shift the origin by T/2), so it equals the sequential scan.
