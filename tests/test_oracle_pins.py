@@ -117,6 +117,10 @@ def test_wht_blocks_follow_uneven_split():
     assert list(O.wht_blocks(17)) == [4, 4, 4, 5]
     assert list(O.wht_blocks(13)) == [3, 3, 3, 4]
     assert list(O.wht_blocks(4)) == [1, 1, 1, 1]
+    # an odd half splits again r | r + 1, the smaller block first
+    assert list(O.wht_blocks(7)) == [1, 2, 2, 2]
+    assert list(O.wht_blocks(5)) == [1, 1, 1, 2]
+    assert list(O.wht_blocks(11)) == [2, 3, 3, 3]
 
 
 def test_wht_basis_is_walsh_in_sequency_order(ffo):
