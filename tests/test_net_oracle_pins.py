@@ -92,6 +92,11 @@ def test_adam_first_step_closed_form():
     p, g = rng.normal(size=50), rng.normal(size=50)
     p1, m, v = N.adam(p, g, np.zeros(50), np.zeros(50), 1, 0.01, eps=0.0)
     assert np.allclose(p1, p - 0.01 * np.sign(g))
+    # epsilon is added to sqrt(v_hat) (Kingma & Ba): with |g| = eps the first step is
+    # g / (|g| + eps) = 1/2 of the learning rate
+    e = 1e-8
+    p1, _, _ = N.adam(np.zeros(2), np.array([e, -e]), np.zeros(2), np.zeros(2), 1, 0.01, eps=e)
+    assert np.allclose(p1, [-0.005, 0.005], rtol=1e-9, atol=0)
 
 
 def test_net_input_block_means():
