@@ -70,7 +70,9 @@ def gather_bytes_prop(W, H, p):
 
 
 class Clocks:
-    """Samples nvidia-smi every 200 ms while the timed region runs."""
+    """Samples nvidia-smi every 50 ms while the timed region runs. The timed region
+    starts only once the sampler has produced its first line (at most 5 s), so that
+    its samples cover the region rather than nvidia-smi's start-up."""
     Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -78,24 +80,41 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.lines = []
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if line.strip():
+                self.lines.append(line)
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return self
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+        t0 = time.perf_counter()
+        while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 5.0:
+            time.sleep(0.01)
+        self.skip = len(self.lines)  # samples taken before the timed region
         return self
 
     def __exit__(self, *a):
-        self.lines = []
         if self.proc:
-            time.sleep(0.25)
+            time.sleep(0.06)
             self.proc.terminate()
-            out, _ = self.proc.communicate(timeout=10)
-            self.lines = [l for l in out.splitlines() if l.strip()]
+            try:
+                self.proc.wait(timeout=10)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.reader.join(timeout=10)
+            self.lines = self.lines[self.skip:]
 
     def summary(self):
         sm, mx, reasons = [], None, set()
