@@ -298,3 +298,31 @@ def test_sift_search_never_increases_cost(ffo):
             t = (p[0] + f1[gy, gx, 0], p[1] + f1[gy, gx, 1])
             assert 0 <= t[0] < 52 and 0 <= t[1] < 40
             assert ffo.sift_patch_cost(Ks, Kt, 4, 3, p, t) == c1[gy, gx]
+
+
+def test_sift_whole_path_is_the_composition_of_its_steps(ffo):
+    # The whole path wires its inputs as Sec. 3.3 / Sec. 5 prescribe: per level the
+    # colours smoothed like I^n; forward (I1 -> I2) and first backward flow with
+    # radius r and the first colour set, second backward flow with r2 and the second
+    # set (S2 channels); kd trees over the target frame's WHT features. Each flow
+    # must equal its steps composed by hand.
+    W, H = 48, 40
+    I1, I2 = smooth_img(31, H, W), smooth_img(32, H, W)
+    B1, o1 = _basis(ffo, [I1, I2], 6)
+    B2, o2 = _basis(ffo, [I1, I2], 9)
+    P = dict(k=2, r=2, r2=1, tile=8, n_rs=3, R=1, seed=5, eps=1, e=9, s=150)
+    res = ffo.sift_flow_fields(I1, I2, B1, o1, B2, o2, params=P)
+    col = {(c, f): ffo.sift_colors(ffo.sift_descriptors(img), B, o)
+           for c, (B, o) in enumerate(((B1, o1), (B2, o2))) for f, img in enumerate((I1, I2))}
+    for j, (src, tgt, r, c) in enumerate(((0, 1, 2, 0), (1, 0, 2, 0), (1, 0, 1, 1))):
+        imgs = (I1, I2)
+        lv = {n: (ffo.sift_smooth(col[(c, src)], n) if n > 1 else col[(c, src)],
+                  ffo.sift_smooth(col[(c, tgt)], n) if n > 1 else col[(c, tgt)]) for n in (1, 2, 4)}
+        feat = ffo.wht_features(imgs[tgt], r)
+        f, cst, _ = ffo.sift_kd_init(feat, imgs[src], r, 8, lv[4][0], lv[4][1], 4)
+        f, cst, _ = ffo.sift_search_level(lv[4][0], lv[4][1], 4, r, flow=f, cost=cst, tile=8,
+                                          n_rs=3, R=1, seed=5, flow_id=j)
+        for n in (2, 1):
+            f, cst, _ = ffo.sift_search_level(lv[n][0], lv[n][1], n, r, flow_coarse=f, tile=8,
+                                              n_rs=3, R=1, seed=5, flow_id=j)
+        assert np.array_equal(f, res["flows"][j]), j
