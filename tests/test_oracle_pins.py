@@ -865,3 +865,29 @@ def test_subpel_filter_thresholds(ffo):
     assert out.tolist() == [[1, 1, 0]]  # (1, 2) differ by 3 px: no touch, region kept
     G[0, 2, 0] = 10  # 2.5 px: the rejected pixel touches the region -> removed
     assert ffo.region_filter(G, vcc, 5, subpel=2).tolist() == [[0, 0, 0]]
+
+
+@pytest.mark.parametrize("color", [0, 1])
+def test_whole_path_is_the_composition_of_its_steps(ffo, color):
+    # Fig. 2 / Sec. 3.4 wiring: (with color = 1 both frames in CIELab first); per
+    # level the census of I^n; forward flow I1 -> I2 and first backward flow with
+    # radius r, second backward flow with r2, each from a kd tree over the target
+    # frame's WHT features, flow ids 0, 1, 2. Each flow must equal its steps
+    # composed by hand.
+    W, H = 56, 44
+    rng = np.random.default_rng(41)
+    I1 = synth._to_u8(synth.value_noise(rng, H, W))
+    I2 = synth._to_u8(synth.value_noise(rng, H, W))
+    P = dict(k=2, r=3, r2=2, tile=8, n_rs=2, R=1, seed=9, color=color)
+    res = ffo.flow_fields(I1, I2, params=P)
+    A = (ffo.rgb_to_lab(I1), ffo.rgb_to_lab(I2)) if color else (I1, I2)
+    Cn = {(f, n): ffo.census(ffo.smooth(A[f], n), n) for f in (0, 1) for n in (1, 2, 4)}
+    for j, (src, tgt, r) in enumerate(((0, 1, 3), (1, 0, 3), (1, 0, 2))):
+        f, c, _ = ffo.kd_init(ffo.wht_features(A[tgt], r), A[src], r, 8, Cn[(src, 4)],
+                              Cn[(tgt, 4)], 4)
+        f, c, _ = ffo.search_level(Cn[(src, 4)], Cn[(tgt, 4)], 4, r, flow=f, cost=c, tile=8,
+                                   n_rs=2, R=1, seed=9, flow_id=j)
+        for n in (2, 1):
+            f, c, _ = ffo.search_level(Cn[(src, n)], Cn[(tgt, n)], n, r, flow_coarse=f, tile=8,
+                                       n_rs=2, R=1, seed=9, flow_id=j)
+        assert np.array_equal(f, res["flows"][j]), j
