@@ -867,6 +867,19 @@ def test_subpel_filter_thresholds(ffo):
     assert ffo.region_filter(G, vcc, 5, subpel=2).tolist() == [[0, 0, 0]]
 
 
+def _assert_filter_composed(ffo, res, eps, s, e):
+    """valid, err_sum, sparse and mask of a whole-path result equal Eq. 5 against
+    both backward flows, the region filter and the sparsification composed by hand
+    on its flows (Sec. 3.4, 3.5)."""
+    F, Fb1, Fb2 = res["flows"]
+    v, err, e1, e2 = ffo.consistency(F, Fb1, Fb2, eps, errors=True)
+    valid = ffo.region_filter(F, v, s)
+    sp, mask = ffo.sparsify(valid, e1, e2, F, e)
+    assert np.array_equal(valid, res["valid"])
+    assert np.array_equal(err, res["err_sum"])
+    assert np.array_equal(sp, res["sparse"]) and np.array_equal(mask, res["mask"])
+
+
 @pytest.mark.parametrize("color", [0, 1])
 def test_whole_path_is_the_composition_of_its_steps(ffo, color):
     # Fig. 2 / Sec. 3.4 wiring: (with color = 1 both frames in CIELab first); per
@@ -891,3 +904,4 @@ def test_whole_path_is_the_composition_of_its_steps(ffo, color):
             f, c, _ = ffo.search_level(Cn[(src, n)], Cn[(tgt, n)], n, r, flow_coarse=f, tile=8,
                                        n_rs=2, R=1, seed=9, flow_id=j)
         assert np.array_equal(f, res["flows"][j]), j
+    _assert_filter_composed(ffo, res, 5, 50, 4)

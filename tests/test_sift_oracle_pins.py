@@ -300,6 +300,19 @@ def test_sift_search_never_increases_cost(ffo):
             assert ffo.sift_patch_cost(Ks, Kt, 4, 3, p, t) == c1[gy, gx]
 
 
+def _assert_filter_composed(ffo, res, eps, s, e):
+    """valid, err_sum, sparse and mask of a whole-path result equal Eq. 5 against
+    both backward flows, the region filter and the sparsification composed by hand
+    on its flows (Sec. 3.4, 3.5)."""
+    F, Fb1, Fb2 = res["flows"]
+    v, err, e1, e2 = ffo.consistency(F, Fb1, Fb2, eps, errors=True)
+    valid = ffo.region_filter(F, v, s)
+    sp, mask = ffo.sparsify(valid, e1, e2, F, e)
+    assert np.array_equal(valid, res["valid"])
+    assert np.array_equal(err, res["err_sum"])
+    assert np.array_equal(sp, res["sparse"]) and np.array_equal(mask, res["mask"])
+
+
 def test_sift_whole_path_is_the_composition_of_its_steps(ffo):
     # The whole path wires its inputs as Sec. 3.3 / Sec. 5 prescribe: per level the
     # colours smoothed like I^n; forward (I1 -> I2) and first backward flow with
@@ -326,3 +339,4 @@ def test_sift_whole_path_is_the_composition_of_its_steps(ffo):
             f, cst, _ = ffo.sift_search_level(lv[n][0], lv[n][1], n, r, flow_coarse=f, tile=8,
                                               n_rs=3, R=1, seed=5, flow_id=j)
         assert np.array_equal(f, res["flows"][j]), j
+    _assert_filter_composed(ffo, res, 1, 150, 9)
