@@ -656,8 +656,10 @@ __constant__ int c_pass_src[4][2] = {{-1, -1}, {1, 1}, {1, -1}, {-1, 1}};
 // (origin shifted by T/2 in odd passes), the tile's state in shared memory, its
 // grid points in anti-diagonal wavefronts along the scan direction (each point's
 // two sources lie on the previous diagonal, so this equals the sequential scan),
-// one 8-lane group per point of a diagonal. Sources outside the tile are read
-// from the start-of-pass state (fin, cin); results go to (fout, cout).
+// one 16-lane group per point of a diagonal, both candidates costed together and
+// incrementally where the neighbour's flow needs no clamping. Sources outside the
+// tile are read from the start-of-pass state (fin, cin); results go to
+// (fout, cout).
 template <int R, int NW4>
 __global__ void __launch_bounds__(SIFT_GROUP * MAX_TILE) k_sift_pass(SiftLevel L, const uint32_t *fin,
                                                    const int32_t *cin, uint32_t *fout,
